@@ -1,0 +1,241 @@
+"""FP64 CPU oracle for per-ping coherent echo formation (TEST INFRASTRUCTURE ONLY).
+
+Only tests/, __graft_entry__.smoke() and bench.py's cpu_baseline / reference legs may
+import this package. It wraps oracle/sonar_oracle.c (built with gcc by oracle/build.py)
+through ctypes; it imports nothing from the CUDA product package, and the product
+package imports nothing from here. Inputs are plain numpy arrays and dicts as produced
+by the seeded input generators.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+
+class OrcParams(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("pitch", C.c_double), ("f0", C.c_double),
+                ("bw", C.c_double), ("pulse", C.c_double), ("c_ref", C.c_double),
+                ("hfov", C.c_double), ("vfov", C.c_double), ("n_beam_az", C.c_int32),
+                ("n_beam_el", C.c_int32), ("n_range", C.c_int32), ("r_min", C.c_double),
+                ("r_max", C.c_double), ("r_blank", C.c_double), ("n_ray_az", C.c_int32),
+                ("n_ray_el", C.c_int32), ("n_sub", C.c_int32), ("max_bounces", C.c_int32),
+                ("surface_z", C.c_double), ("r_surface", C.c_double), ("r_seabed", C.c_double),
+                ("alpha", C.c_double), ("seed", C.c_uint64), ("thr_mode", C.c_int32),
+                ("thr", C.c_double)]
+
+
+class OrcScene(C.Structure):
+    _fields_ = [("n_verts", C.c_int64), ("verts", C.c_void_p), ("n_tris", C.c_int64),
+                ("tris", C.c_void_p), ("mu", C.c_void_p), ("flags", C.c_void_p),
+                ("n_points", C.c_int64), ("points", C.c_void_p), ("sigma", C.c_void_p),
+                ("n_planes", C.c_int64), ("planes", C.c_void_p)]
+
+
+_HIT_I32 = ("ray", "sub", "seg", "prim")
+_HIT_F64 = ("tau", "len", "amp", "psi", "phi", "ux", "uy", "uz", "cr", "ci", "margin", "gap")
+
+
+class OrcHits(C.Structure):
+    _fields_ = ([("cap", C.c_int64), ("n", C.c_int64)]
+                + [(k, C.c_void_p) for k in _HIT_I32] + [(k, C.c_void_p) for k in _HIT_F64]
+                + [("c_ref", C.c_double)])
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(_build.build())
+        vp, i64, i32, d = C.c_void_p, C.c_int64, C.c_int32, C.c_double
+        _lib.orc_trace.argtypes = [vp, vp, vp, vp, vp, vp, i32, C.c_int, vp]
+        _lib.orc_synth.argtypes = [vp, vp, vp, i64, vp]
+        _lib.orc_beamform.argtypes = [vp, d, vp, vp, i64, vp, i64, vp]
+        _lib.orc_envelope.argtypes = [vp, vp, vp, i64, i64, vp]
+        _lib.orc_peaks.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        _lib.orc_peaks.restype = i64
+        _lib.orc_pulse_acf.argtypes = [d, d, d, vp, vp]
+        _lib.orc_pcg4d.argtypes = [vp]
+        _lib.orc_closest_hit.argtypes = [vp, vp, vp, d, d, i32, C.c_int, vp, vp, vp]
+        _lib.orc_closest_hit.restype = i32
+        _lib.orc_arc_nodes.argtypes = [vp, vp, i32, vp, vp, d, i32, vp, vp, vp]
+        _lib.orc_eigen_arc.argtypes = [vp, vp, i32, vp, vp, vp, vp, vp]
+        _lib.orc_eigen_arc.restype = C.c_int
+        _lib.orc_num_threads.restype = C.c_int
+    return _lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(C.c_void_p) if a is not None and a.size else None
+
+
+def num_threads() -> int:
+    return lib().orc_num_threads()
+
+
+def make_params(p: dict) -> OrcParams:
+    o = OrcParams()
+    for name, _ in OrcParams._fields_:
+        v = p[name]
+        if name == "surface_z" and v is None:
+            v = math.nan
+        setattr(o, name, v)
+    return o
+
+
+class _SceneHold:
+    """Keeps the numpy arrays referenced by an OrcScene alive."""
+
+    def __init__(self, sc):
+        self.verts = np.ascontiguousarray(sc.verts, np.float32)
+        self.tris = np.ascontiguousarray(sc.tris, np.int32)
+        self.mu = np.ascontiguousarray(sc.mu, np.float32)
+        self.flags = np.ascontiguousarray(sc.flags, np.uint8)
+        self.points = np.ascontiguousarray(sc.points, np.float32).reshape(-1, 3)
+        self.sigma = np.ascontiguousarray(sc.sigma, np.float32)
+        self.planes = np.ascontiguousarray(sc.planes, np.float64).reshape(-1, 4)
+        self.s = OrcScene(len(self.verts), _ptr(self.verts), len(self.tris), _ptr(self.tris),
+                          _ptr(self.mu), _ptr(self.flags), len(self.points), _ptr(self.points),
+                          _ptr(self.sigma), len(self.planes), _ptr(self.planes))
+
+
+def trace(scene, params: dict, pose: dict, ssp: dict, use_bvh: bool = True) -> dict:
+    """Hit list of one ping (Sec. II.A ray casting + Sec. II.B per-hit backscatter)."""
+    L = lib()
+    sh = _SceneHold(scene)
+    op = make_params(params)
+    t = np.ascontiguousarray(pose["t"], np.float64)
+    q = np.ascontiguousarray(pose["q"], np.float64)
+    z = np.ascontiguousarray(ssp["z"], np.float64)
+    c = np.ascontiguousarray(ssp["c"], np.float64)
+    cap = 1 << 16
+    while True:
+        arrs = {k: np.zeros(cap, np.int32) for k in _HIT_I32}
+        arrs.update({k: np.zeros(cap, np.float64) for k in _HIT_F64})
+        h = OrcHits(cap, 0, *[_ptr(arrs[k]) for k in _HIT_I32], *[_ptr(arrs[k]) for k in _HIT_F64], 0.0)
+        rc = L.orc_trace(C.byref(sh.s), C.byref(op), _ptr(t), _ptr(q), _ptr(z), _ptr(c), len(z),
+                         1 if use_bvh else 0, C.byref(h))
+        if rc < 0:
+            cap = int(h.n) + 16
+            continue
+        if rc != 0:
+            raise RuntimeError(f"orc_trace failed with code {rc}")
+        n = int(h.n)
+        out = {k: v[:n].copy() for k, v in arrs.items()}
+        out["n"] = n
+        out["c_ref"] = float(h.c_ref)
+        return out
+
+
+def _hits_struct(h: dict):
+    keep = {k: np.ascontiguousarray(h[k], np.int32) for k in _HIT_I32}
+    keep.update({k: np.ascontiguousarray(h[k], np.float64) for k in _HIT_F64})
+    s = OrcHits(h["n"], h["n"], *[_ptr(keep[k]) for k in _HIT_I32],
+                *[_ptr(keep[k]) for k in _HIT_F64], h["c_ref"])
+    return s, keep
+
+
+def synth(params: dict, hits: dict, ns) -> np.ndarray:
+    """Element echoes s_m[n] for the requested samples: complex128 [len(ns), M]."""
+    ns = np.ascontiguousarray(ns, np.int32)
+    M = params["nx"] * params["ny"]
+    out = np.zeros((len(ns), M, 2), np.float64)
+    hs, keep = _hits_struct(hits)
+    lib().orc_synth(C.byref(make_params(params)), C.byref(hs), _ptr(ns), len(ns), _ptr(out))
+    return out[..., 0] + 1j * out[..., 1]
+
+
+def beamform(params: dict, c_ref: float, s: np.ndarray, beams=None, taper=None) -> np.ndarray:
+    """Beams B[b, i] for element echoes s [n_ns, M]: complex128 [n_beams, n_ns]."""
+    nb = params["n_beam_az"] * params["n_beam_el"]
+    beams = np.arange(nb, dtype=np.int32) if beams is None else np.ascontiguousarray(beams, np.int32)
+    s = np.ascontiguousarray(s, np.complex128)
+    sr = np.ascontiguousarray(np.stack([s.real, s.imag], -1))
+    out = np.zeros((len(beams), s.shape[0], 2), np.float64)
+    tp = None if taper is None else np.ascontiguousarray(taper, np.float32)
+    lib().orc_beamform(C.byref(make_params(params)), c_ref, _ptr(tp), _ptr(sr), s.shape[0],
+                       _ptr(beams), len(beams), _ptr(out))
+    return out[..., 0] + 1j * out[..., 1]
+
+
+def envelope(params: dict, B: np.ndarray, ns) -> np.ndarray:
+    ns = np.ascontiguousarray(ns, np.int32)
+    Br = np.ascontiguousarray(np.stack([B.real, B.imag], -1))
+    out = np.zeros(B.shape, np.float64)
+    lib().orc_envelope(C.byref(make_params(params)), _ptr(Br), _ptr(ns), len(ns), B.shape[0], _ptr(out))
+    return out
+
+
+def volume(params: dict, hits: dict, ns=None, beams=None, taper=None):
+    """Envelope E[b, i] (and beams B, element echoes s) for the requested samples/beams."""
+    ns = np.arange(params["n_range"], dtype=np.int32) if ns is None else np.asarray(ns, np.int32)
+    s = synth(params, hits, ns)
+    B = beamform(params, hits["c_ref"], s, beams, taper)
+    E = envelope(params, B, ns)
+    return E, B, s
+
+
+def peaks(params: dict, pose: dict, E: np.ndarray) -> dict:
+    """Point cloud from a full envelope volume E [Nb, Nr]."""
+    E = np.ascontiguousarray(E, np.float64)
+    nb = E.shape[0]
+    pts = np.zeros((nb, 4), np.float64)
+    pb = np.zeros(nb, np.int32)
+    pn = np.zeros(nb, np.int32)
+    t = np.ascontiguousarray(pose["t"], np.float64)
+    q = np.ascontiguousarray(pose["q"], np.float64)
+    n = lib().orc_peaks(C.byref(make_params(params)), _ptr(t), _ptr(q), _ptr(E), _ptr(pts), _ptr(pb), _ptr(pn))
+    return {"xyzi": pts[:n], "beam": pb[:n], "bin": pn[:n]}
+
+
+def pulse_acf(u, T: float, B: float) -> np.ndarray:
+    u = np.atleast_1d(np.asarray(u, np.float64))
+    out = np.zeros(u.shape, np.complex128)
+    re, im = C.c_double(), C.c_double()
+    for i, x in enumerate(u.ravel()):
+        lib().orc_pulse_acf(float(x), T, B, C.byref(re), C.byref(im))
+        out.ravel()[i] = re.value + 1j * im.value
+    return out
+
+
+def pcg4d(v) -> np.ndarray:
+    a = np.ascontiguousarray(np.asarray(v, np.uint32).copy())
+    lib().orc_pcg4d(_ptr(a))
+    return a
+
+
+def closest_hit(scene, o, d, tmin=1e-7, tmax=math.inf, exclude=-1, use_bvh=True):
+    sh = _SceneHold(scene)
+    o = np.ascontiguousarray(o, np.float64)
+    d = np.ascontiguousarray(d, np.float64)
+    t, m, t2 = C.c_double(), C.c_double(), C.c_double()
+    prim = lib().orc_closest_hit(C.byref(sh.s), _ptr(o), _ptr(d), tmin, tmax, exclude,
+                                 1 if use_bvh else 0, C.byref(t), C.byref(m), C.byref(t2))
+    return prim, t.value, m.value, t2.value
+
+
+def arc_nodes(ssp: dict, o, d, h: float, n: int):
+    z = np.ascontiguousarray(ssp["z"], np.float64)
+    c = np.ascontiguousarray(ssp["c"], np.float64)
+    pos = np.zeros((n, 3))
+    tt = np.zeros(n)
+    th = np.zeros(n)
+    lib().orc_arc_nodes(_ptr(z), _ptr(c), len(z), _ptr(np.asarray(o, np.float64)),
+                        _ptr(np.asarray(d, np.float64)), h, n, _ptr(pos), _ptr(tt), _ptr(th))
+    return pos, tt, th
+
+
+def eigen_arc(ssp: dict, o, x):
+    z = np.ascontiguousarray(ssp["z"], np.float64)
+    c = np.ascontiguousarray(ssp["c"], np.float64)
+    d = np.zeros(3)
+    t, s = C.c_double(), C.c_double()
+    rc = lib().orc_eigen_arc(_ptr(z), _ptr(c), len(z), _ptr(np.asarray(o, np.float64)),
+                             _ptr(np.asarray(x, np.float64)), _ptr(d), C.byref(t), C.byref(s))
+    if rc != 0:
+        raise RuntimeError("eigen_arc failed")
+    return d, t.value, s.value

@@ -1,0 +1,991 @@
+/*
+ * FP64 CPU oracle for per-ping coherent echo formation in a volumetric 3D sonar
+ * ("Towards Realistic 3D Sonar Simulation", Sec. II.A-II.B, Sec. III Eq. 1-3).
+ *
+ * TEST INFRASTRUCTURE ONLY: loaded by tests/, __graft_entry__.smoke() and the
+ * cpu_baseline leg of bench.py. The product path never loads it. It is written
+ * plainly (no blocking, no fusion, FP64 everywhere, closed forms evaluated directly)
+ * so that each step can be checked against the reading of the paper stated beside it.
+ *
+ * Parity unpinned: Lambertian amplitudes on meshes, speckle statistics, multi-bounce
+ * mesh routes and curved-ray mesh hits have no closed form or brute-force check.
+ */
+#include "sonar_oracle.h"
+
+#include <complex.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef double complex cplx;
+#define PI 3.14159265358979323846
+#define TWO_PI (2.0 * PI)
+#define EPS_HIT 1e-7          /* a hit must lie beyond this distance along a segment [m] */
+#define ARC_EPS_SAGITTA 1e-4  /* chord sagitta bound for curved rays [m] */
+#define ARC_H_MAX 2.0         /* maximum chord arc length [m] */
+
+int orc_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+/* ------------------------------------------------------------------ small vector math */
+static double dot3(const double a[3], const double b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+static void cross3(const double a[3], const double b[3], double r[3]) {
+  r[0] = a[1] * b[2] - a[2] * b[1];
+  r[1] = a[2] * b[0] - a[0] * b[2];
+  r[2] = a[0] * b[1] - a[1] * b[0];
+}
+static void sub3(const double a[3], const double b[3], double r[3]) {
+  r[0] = a[0] - b[0]; r[1] = a[1] - b[1]; r[2] = a[2] - b[2];
+}
+static double norm3(const double a[3]) { return sqrt(dot3(a, a)); }
+
+/* Rotation matrix of the unit quaternion q = (w, x, y, z): sonar frame -> world. */
+static void quat_to_matrix(const double q[4], double R[9]) {
+  double w = q[0], x = q[1], y = q[2], z = q[3];
+  R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z);     R[2] = 2 * (x * z + w * y);
+  R[3] = 2 * (x * y + w * z);     R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+  R[6] = 2 * (x * z - w * y);     R[7] = 2 * (y * z + w * x);     R[8] = 1 - 2 * (x * x + y * y);
+}
+static void mat_vec(const double R[9], const double v[3], double r[3]) {
+  r[0] = R[0] * v[0] + R[1] * v[1] + R[2] * v[2];
+  r[1] = R[3] * v[0] + R[4] * v[1] + R[5] * v[2];
+  r[2] = R[6] * v[0] + R[7] * v[1] + R[8] * v[2];
+}
+static void mat_t_vec(const double R[9], const double v[3], double r[3]) {
+  r[0] = R[0] * v[0] + R[3] * v[1] + R[6] * v[2];
+  r[1] = R[1] * v[0] + R[4] * v[1] + R[7] * v[2];
+  r[2] = R[2] * v[0] + R[5] * v[1] + R[8] * v[2];
+}
+
+static double sinc(double x) { return fabs(x) < 1e-4 ? 1.0 - x * x / 6.0 : sin(x) / x; }
+static double frac(double x) { return x - floor(x); }
+static double wrap_pi(double a) { return a - TWO_PI * floor((a + PI) / TWO_PI); }
+
+/* ------------------------------------------------------------------ hash (Sec. II.B speckle) */
+/* pcg4d from Jarzynski & Olano, "Hash Functions for GPU Rendering", JCGT 9(3), 2020. */
+void orc_pcg4d(uint32_t v[4]) {
+  for (int i = 0; i < 4; ++i) v[i] = v[i] * 1664525u + 1013904223u;
+  v[0] += v[1] * v[3]; v[1] += v[2] * v[0]; v[2] += v[0] * v[1]; v[3] += v[1] * v[2];
+  for (int i = 0; i < 4; ++i) v[i] ^= v[i] >> 16;
+  v[0] += v[1] * v[3]; v[1] += v[2] * v[0]; v[2] += v[0] * v[1]; v[3] += v[1] * v[2];
+}
+static uint32_t seed32(uint64_t s) { return (uint32_t)(s ^ (s >> 32)); }
+static double u24(uint32_t h) { return (double)(h >> 8) * (1.0 / 16777216.0); }
+
+/* ------------------------------------------------------------------ pulse (Sec. II.B) */
+/* Pulse p(t) = w(t) exp(j pi (B/T) t^2), |t| <= T/2, Hann w(t) = (1 + cos(2 pi t/T))/2.
+   R(u) = (1/E) int p(v+u) conj(p(v)) dv with E = 3T/8. Writing w as three complex
+   exponentials (c0 = 1/2, c+-1 = 1/4) turns the integrand into nine exponentials in v,
+   each integrated exactly over the overlap [L, U] of the two pulse supports. */
+void orc_pulse_acf(double u, double T, double B, double* re, double* im) {
+  if (!(fabs(u) < T)) { *re = 0; *im = 0; return; }
+  const double kappa = B / T, Om = TWO_PI / T, E = 3.0 * T / 8.0;
+  const double L = fmax(-T / 2, -T / 2 - u), U = fmin(T / 2, T / 2 - u);
+  cplx sum = 0;
+  for (int a = -1; a <= 1; ++a) {
+    for (int b = -1; b <= 1; ++b) {
+      double ca = a == 0 ? 0.5 : 0.25, cb = b == 0 ? 0.5 : 0.25;
+      double beta = (a + b) * Om + TWO_PI * kappa * u;
+      /* int_L^U e^{j beta v} dv = (U-L) sinc(beta (U-L)/2) e^{j beta (U+L)/2} */
+      cplx integral = (U - L) * sinc(beta * (U - L) / 2) * cexp(I * beta * (U + L) / 2);
+      sum += ca * cb * cexp(I * a * Om * u) * integral;
+    }
+  }
+  cplx r = cexp(I * PI * kappa * u * u) * sum / E;
+  *re = creal(r);
+  *im = cimag(r);
+}
+
+/* ------------------------------------------------------------------ geometry */
+static void tri_verts(const orc_scene* sc, int32_t prim, double a[3], double b[3], double c[3]) {
+  const int32_t* t = sc->tris + 3 * (int64_t)prim;
+  for (int k = 0; k < 3; ++k) {
+    a[k] = sc->verts[3 * (int64_t)t[0] + k];
+    b[k] = sc->verts[3 * (int64_t)t[1] + k];
+    c[k] = sc->verts[3 * (int64_t)t[2] + k];
+  }
+}
+
+/* Two-sided ray/triangle test (Moller & Trumbore 1997), inclusive edges. */
+static int tri_test(const double o[3], const double d[3], const double a[3], const double b[3],
+                    const double c[3], double* t, double* margin) {
+  double e1[3], e2[3], p[3], s[3], q[3];
+  sub3(b, a, e1);
+  sub3(c, a, e2);
+  cross3(d, e2, p);
+  double det = dot3(e1, p);
+  if (det == 0.0) return 0;
+  sub3(o, a, s);
+  double u = dot3(s, p) / det;
+  if (!(u >= 0.0 && u <= 1.0)) return 0;
+  cross3(s, e1, q);
+  double v = dot3(d, q) / det;
+  if (!(v >= 0.0 && u + v <= 1.0)) return 0;
+  *t = dot3(e2, q) / det;
+  double w = 1.0 - u - v;
+  *margin = fmin(u, fmin(v, w));
+  return 1;
+}
+
+static void tri_normal(const orc_scene* sc, int32_t prim, double n[3]) {
+  double a[3], b[3], c[3], e1[3], e2[3];
+  tri_verts(sc, prim, a, b, c);
+  sub3(b, a, e1);
+  sub3(c, a, e2);
+  cross3(e1, e2, n);
+  double l = norm3(n);
+  n[0] /= l; n[1] /= l; n[2] /= l;
+}
+
+/* Median-split BVH over triangle centroids, FP64 boxes. */
+typedef struct { double lo[3], hi[3]; int32_t left, right, first, count; } bnode;
+typedef struct { bnode* nodes; int32_t n_nodes; int32_t* order; double* cent; } bvh_t;
+
+static int cmp_axis_g;
+static const double* cmp_cent_g;
+static int cmp_prims(const void* x, const void* y) {
+  int32_t a = *(const int32_t*)x, b = *(const int32_t*)y;
+  double ca = cmp_cent_g[3 * (int64_t)a + cmp_axis_g], cb = cmp_cent_g[3 * (int64_t)b + cmp_axis_g];
+  if (ca < cb) return -1;
+  if (ca > cb) return 1;
+  return a < b ? -1 : (a > b);
+}
+
+static int32_t bvh_build_rec(bvh_t* bv, const orc_scene* sc, int32_t first, int32_t count) {
+  int32_t id = bv->n_nodes++;
+  bnode* nd = &bv->nodes[id];
+  for (int k = 0; k < 3; ++k) { nd->lo[k] = INFINITY; nd->hi[k] = -INFINITY; }
+  double clo[3] = {INFINITY, INFINITY, INFINITY}, chi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int32_t i = first; i < first + count; ++i) {
+    double a[3], b[3], c[3];
+    tri_verts(sc, bv->order[i], a, b, c);
+    for (int k = 0; k < 3; ++k) {
+      nd->lo[k] = fmin(nd->lo[k], fmin(a[k], fmin(b[k], c[k])));
+      nd->hi[k] = fmax(nd->hi[k], fmax(a[k], fmax(b[k], c[k])));
+      double ce = bv->cent[3 * (int64_t)bv->order[i] + k];
+      clo[k] = fmin(clo[k], ce);
+      chi[k] = fmax(chi[k], ce);
+    }
+  }
+  if (count <= 4) {
+    nd->left = nd->right = -1;
+    nd->first = first;
+    nd->count = count;
+    return id;
+  }
+  int axis = 0;
+  for (int k = 1; k < 3; ++k)
+    if (chi[k] - clo[k] > chi[axis] - clo[axis]) axis = k;
+  cmp_axis_g = axis;
+  cmp_cent_g = bv->cent;
+  qsort(bv->order + first, (size_t)count, sizeof(int32_t), cmp_prims);
+  int32_t half = count / 2;
+  int32_t l = bvh_build_rec(bv, sc, first, half);
+  int32_t r = bvh_build_rec(bv, sc, first + half, count - half);
+  nd = &bv->nodes[id];
+  nd->left = l;
+  nd->right = r;
+  nd->first = -1;
+  nd->count = 0;
+  return id;
+}
+
+static void bvh_build(bvh_t* bv, const orc_scene* sc) {
+  int64_t n = sc->n_tris;
+  bv->nodes = (bnode*)malloc(sizeof(bnode) * (size_t)(2 * n + 1));
+  bv->order = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n + 1));
+  bv->cent = (double*)malloc(sizeof(double) * (size_t)(3 * n + 1));
+  bv->n_nodes = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    double a[3], b[3], c[3];
+    tri_verts(sc, (int32_t)i, a, b, c);
+    bv->order[i] = (int32_t)i;
+    for (int k = 0; k < 3; ++k) bv->cent[3 * i + k] = (a[k] + b[k] + c[k]) / 3.0;
+  }
+  if (n > 0) bvh_build_rec(bv, sc, 0, (int32_t)n);
+}
+static void bvh_free(bvh_t* bv) {
+  free(bv->nodes);
+  free(bv->order);
+  free(bv->cent);
+}
+
+/* Conservative slab test; boxes are padded by a relative 1e-9 so that no hit is lost. */
+static int box_test(const double lo[3], const double hi[3], const double o[3], const double d[3],
+                    double tmin, double tmax) {
+  double t0 = tmin, t1 = tmax;
+  for (int k = 0; k < 3; ++k) {
+    double pad = 1e-9 * (fabs(lo[k]) + fabs(hi[k]) + 1.0);
+    double l = lo[k] - pad, h = hi[k] + pad;
+    if (d[k] == 0.0) {
+      if (o[k] < l || o[k] > h) return 0;
+      continue;
+    }
+    double ta = (l - o[k]) / d[k], tb = (h - o[k]) / d[k];
+    if (ta > tb) { double tmp = ta; ta = tb; tb = tmp; }
+    ta -= 1e-12 * (fabs(ta) + 1.0);
+    tb += 1e-12 * (fabs(tb) + 1.0);
+    if (ta > t0) t0 = ta;
+    if (tb < t1) t1 = tb;
+    if (t0 > t1) return 0;
+  }
+  return 1;
+}
+
+typedef struct {
+  double t, margin, t2;
+  int32_t prim;
+} hitq;
+
+static void consider(hitq* hq, int32_t prim, double t, double margin) {
+  if (t < hq->t || (t == hq->t && prim < hq->prim)) {
+    hq->t2 = hq->t;
+    hq->t = t;
+    hq->prim = prim;
+    hq->margin = margin;
+  } else if (t < hq->t2) {
+    hq->t2 = t;
+  }
+}
+
+/* Nearest hit with t in (tmin, tmax], ties to the lowest prim id; also the runner-up
+   distance among all other hits in the same interval. */
+static hitq closest(const orc_scene* sc, const bvh_t* bv, const double o[3], const double d[3],
+                    double tmin, double tmax, int32_t exclude) {
+  hitq hq = {INFINITY, 0.0, INFINITY, -1};
+  if (bv == NULL) {
+    for (int64_t i = 0; i < sc->n_tris; ++i) {
+      if ((int32_t)i == exclude) continue;
+      double a[3], b[3], c[3], t, m;
+      tri_verts(sc, (int32_t)i, a, b, c);
+      if (tri_test(o, d, a, b, c, &t, &m) && t > tmin && t <= tmax) consider(&hq, (int32_t)i, t, m);
+    }
+    return hq;
+  }
+  if (bv->n_nodes == 0) return hq;
+  int32_t stack[256];
+  int sp = 0;
+  stack[sp++] = 0;
+  while (sp > 0) {
+    const bnode* nd = &bv->nodes[stack[--sp]];
+    double lim = fmin(tmax, hq.t2);
+    if (!box_test(nd->lo, nd->hi, o, d, tmin, lim)) continue;
+    if (nd->count > 0) {
+      for (int32_t i = nd->first; i < nd->first + nd->count; ++i) {
+        int32_t prim = bv->order[i];
+        if (prim == exclude) continue;
+        double a[3], b[3], c[3], t, m;
+        tri_verts(sc, prim, a, b, c);
+        if (tri_test(o, d, a, b, c, &t, &m) && t > tmin && t <= tmax) consider(&hq, prim, t, m);
+      }
+    } else {
+      stack[sp++] = nd->left;
+      stack[sp++] = nd->right;
+    }
+  }
+  return hq;
+}
+
+int32_t orc_closest_hit(const orc_scene* sc, const double o[3], const double d[3], double tmin,
+                        double tmax, int32_t exclude, int use_bvh, double* t, double* margin,
+                        double* t_second) {
+  bvh_t bv;
+  const bvh_t* pb = NULL;
+  if (use_bvh) {
+    bvh_build(&bv, sc);
+    pb = &bv;
+  }
+  hitq hq = closest(sc, pb, o, d, tmin, tmax, exclude);
+  if (use_bvh) bvh_free(&bv);
+  *t = hq.t;
+  *margin = hq.margin;
+  *t_second = hq.t2;
+  return hq.prim;
+}
+
+/* ------------------------------------------------------------------ sound-speed profile */
+/* Sec. II.A: rays bend by Snell's law in a depth-dependent sound speed. Supported
+   profiles: isovelocity (n_ssp <= 1) and one linear gradient c(z) = c0 + g (z - z0)
+   through two nodes (z up, extended linearly beyond the nodes). */
+typedef struct { double z0, c0, g; int curved; } ssp_t;
+
+static int ssp_make(const double* z, const double* c, int32_t n, double c_default, ssp_t* s) {
+  s->z0 = 0.0;
+  s->g = 0.0;
+  s->curved = 0;
+  if (n <= 0) {
+    s->c0 = c_default;
+    return c_default > 0 ? 0 : 1;
+  }
+  if (n == 1) {
+    s->c0 = c[0];
+    return c[0] > 0 ? 0 : 1;
+  }
+  if (n > 2 || z[1] == z[0]) return 2;
+  s->z0 = z[0];
+  s->c0 = c[0];
+  s->g = (c[1] - c[0]) / (z[1] - z[0]);
+  s->curved = s->g != 0.0;
+  return 0;
+}
+static double ssp_c(const ssp_t* s, double z) { return s->c0 + s->g * (z - s->z0); }
+
+/* Exact circular-arc advance by arc length ds in a linear profile (curvature -xi g):
+   theta' = theta - xi g ds; horizontal and vertical displacements
+   ds cos(theta_m) sinc(delta/2) and ds sin(theta_m) sinc(delta/2), theta_m the mean angle;
+   one-way time (atanh(sin theta) - atanh(sin theta'))/g written through
+   X = (sin theta - sin theta')/(1 - sin theta sin theta') so that g -> 0 stays finite. */
+static void arc_advance(const ssp_t* s, double z, double theta, double xi, double ds,
+                        double* dh, double* dz, double* theta_new, double* dt) {
+  double delta = xi * s->g * ds;
+  double thm = theta - delta / 2;
+  double sc = sinc(delta / 2);
+  *dh = ds * cos(thm) * sc;
+  *dz = ds * sin(thm) * sc;
+  *theta_new = theta - delta;
+  double cm = cos(thm);
+  if (fabs(cos(theta)) < 1e-12) {
+    /* vertical ray: straight line, time = ln(c1/c0)/(g sin theta) */
+    double c0 = ssp_c(s, z), c1 = ssp_c(s, z + *dz);
+    *dt = s->g == 0.0 ? ds / c0 : log(c1 / c0) / (s->g * sin(theta));
+    return;
+  }
+  double sh = sin(delta / 2);
+  double x_over_g = cm * xi * ds * sc / (sh * sh + cm * cm);
+  double x = s->g * x_over_g;
+  double ratio = fabs(x) < 1e-6 ? 1.0 + x * x / 3.0 : atanh(x) / x;
+  *dt = ratio * x_over_g;
+}
+
+static double arc_step(const ssp_t* s, double xi) {
+  double k = xi * fabs(s->g);
+  if (k <= 0.0) return ARC_H_MAX;
+  return fmin(ARC_H_MAX, sqrt(8.0 / k * ARC_EPS_SAGITTA));
+}
+
+/* Decompose a unit direction into horizontal unit e and grazing angle theta. */
+static void dir_split(const double d[3], double e[2], double* theta) {
+  double hz = sqrt(d[0] * d[0] + d[1] * d[1]);
+  if (hz > 0) {
+    e[0] = d[0] / hz;
+    e[1] = d[1] / hz;
+  } else {
+    e[0] = 1.0;
+    e[1] = 0.0;
+  }
+  *theta = atan2(d[2], hz);
+}
+
+void orc_arc_nodes(const double* ssp_z, const double* ssp_cc, int32_t n_ssp, const double o[3],
+                   const double d[3], double h, int32_t n_nodes, double* pos, double* times,
+                   double* theta_out) {
+  ssp_t s;
+  ssp_make(ssp_z, ssp_cc, n_ssp, 1500.0, &s);
+  double p[3] = {o[0], o[1], o[2]}, e[2], th, T = 0;
+  dir_split(d, e, &th);
+  double xi = cos(th) / ssp_c(&s, p[2]);
+  for (int32_t i = 0; i < n_nodes; ++i) {
+    pos[3 * i] = p[0]; pos[3 * i + 1] = p[1]; pos[3 * i + 2] = p[2];
+    times[i] = T;
+    theta_out[i] = th;
+    double dh, dz, thn, dt;
+    arc_advance(&s, p[2], th, xi, h, &dh, &dz, &thn, &dt);
+    p[0] += dh * e[0];
+    p[1] += dh * e[1];
+    p[2] += dz;
+    th = thn;
+    T += dt;
+  }
+}
+
+/* Eigen-arc between o and x: the circle through both points whose centre lies on the
+   height where the linear profile reaches c = 0 (every ray of a linear profile is such
+   a circle). */
+int orc_eigen_arc(const double* ssp_z, const double* ssp_cc, int32_t n_ssp, const double o[3],
+                  const double x[3], double d_out[3], double* t_out, double* s_out) {
+  ssp_t s;
+  if (ssp_make(ssp_z, ssp_cc, n_ssp, 1500.0, &s) != 0 || !s.curved) return 1;
+  double dx = x[0] - o[0], dy = x[1] - o[1];
+  double D = sqrt(dx * dx + dy * dy);
+  double co = ssp_c(&s, o[2]), cx = ssp_c(&s, x[2]);
+  if (D == 0.0) {
+    double dz = x[2] - o[2];
+    d_out[0] = 0; d_out[1] = 0; d_out[2] = dz > 0 ? 1.0 : -1.0;
+    *t_out = log(cx / co) / (s.g * d_out[2]);
+    *s_out = fabs(dz);
+    return 0;
+  }
+  double e[2] = {dx / D, dy / D};
+  double a = co / s.g, b = cx / s.g; /* heights above the c = 0 line */
+  double hc = (D * D + b * b - a * a) / (2 * D);
+  double R = sqrt(hc * hc + a * a);
+  double sg = s.g > 0 ? 1.0 : -1.0;
+  double th0 = atan2(sg * hc, sg * a);
+  double th1 = atan2(sg * (hc - D), sg * b);
+  d_out[0] = cos(th0) * e[0];
+  d_out[1] = cos(th0) * e[1];
+  d_out[2] = sin(th0);
+  double s0 = sin(th0), s1 = sin(th1);
+  double X = (s0 - s1) / (1 - s0 * s1);
+  *t_out = atanh(X) / s.g;
+  /* arc length: radius times the angle between the radii to o and to x */
+  double r0[2] = {-hc, a}, r1[2] = {D - hc, b};
+  double ang = atan2(fabs(r0[0] * r1[1] - r0[1] * r1[0]), r0[0] * r1[0] + r0[1] * r1[1]);
+  *s_out = R * ang;
+  return 0;
+}
+
+/* ------------------------------------------------------------------ hit list */
+typedef struct {
+  int32_t ray, sub, seg, prim;
+  double tau, len, amp, psi, phi, u[3], margin, gap;
+} ohit;
+typedef struct { ohit* v; int64_t n, cap; } hbuf;
+static void hb_push(hbuf* b, const ohit* h) {
+  if (b->n == b->cap) {
+    b->cap = b->cap ? 2 * b->cap : 16;
+    b->v = (ohit*)realloc(b->v, sizeof(ohit) * (size_t)b->cap);
+  }
+  b->v[b->n++] = *h;
+}
+
+typedef struct {
+  const orc_scene* sc;
+  const orc_params* p;
+  const bvh_t* bv;
+  ssp_t ssp;
+  double c_ref, T_stop, R[9], t[3];
+  uint32_t s32;
+  int has_surface;
+} tctx;
+
+/* Sec. II.B per-hit backscatter: Lambertian intensity mu cos^2(k) over the footprint
+   L^2 dOmega / cos(k) gives amplitude Gamma^2 sqrt(mu cos(k) dOmega)/L, two-way
+   attenuation exp(-2 alpha L); speckle phase psi uniform from the hash; carrier phase
+   set by the two-way delay: c = a exp(j (psi - 2 pi frac(f0 tau))). */
+static void emit_mesh_hit(const tctx* c, hbuf* hb, int32_t ray, int32_t sub, int32_t seg,
+                          int32_t prim, double T_oneway, double L, double gam, double kinc,
+                          double dOmega, const double us[3], double margin, double gap) {
+  ohit h;
+  h.ray = ray; h.sub = sub; h.seg = seg; h.prim = prim;
+  h.tau = 2.0 * T_oneway;
+  h.len = L;
+  double mu = c->sc->mu[prim];
+  h.amp = gam * gam * sqrt(mu * kinc * dOmega) / L * exp(-2.0 * c->p->alpha * L);
+  uint32_t v[4] = {(uint32_t)ray, (uint32_t)sub, (uint32_t)(1 + seg), c->s32};
+  orc_pcg4d(v);
+  h.psi = TWO_PI * u24(v[0]);
+  h.phi = wrap_pi(h.psi - TWO_PI * frac(c->p->f0 * h.tau));
+  h.u[0] = us[0]; h.u[1] = us[1]; h.u[2] = us[2];
+  h.margin = margin;
+  h.gap = gap;
+  hb_push(hb, &h);
+}
+
+static void reflect(double d[3], const double n[3]) {
+  double k = 2.0 * dot3(d, n);
+  d[0] -= k * n[0]; d[1] -= k * n[1]; d[2] -= k * n[2];
+}
+
+/* Isovelocity route (Sec. II.A ray casting, Sec. II.B limited secondary reflections):
+   straight segments; a triangle hit scatters and, when the triangle is a specular
+   mirror and bounces remain, the ray reflects about the geometric normal; the sea
+   surface only reflects. Stops at the one-way time T_stop. */
+static void route_straight(const tctx* c, const double o[3], const double d0[3], const double us[3],
+                           int32_t ray, int32_t sub, double dOmega, hbuf* hb) {
+  const orc_params* p = c->p;
+  double cw = c->ssp.c0;
+  double L_stop = c->T_stop * cw;
+  double pos[3] = {o[0], o[1], o[2]}, dir[3] = {d0[0], d0[1], d0[2]};
+  double L = 0.0, gam = 1.0;
+  int32_t bounce = 0, prev = -1;
+  for (;;) {
+    double tlim = L_stop - L;
+    if (!(tlim > 0)) break;
+    hitq hq = closest(c->sc, c->bv, pos, dir, EPS_HIT, tlim, prev);
+    double ts = INFINITY;
+    if (c->has_surface && prev != -2 && dir[2] != 0.0) {
+      double t = (p->surface_z - pos[2]) / dir[2];
+      if (t > EPS_HIT && t <= tlim) ts = t;
+    }
+    if (hq.prim < 0 && ts == INFINITY) break;
+    if (ts < hq.t) {
+      if (bounce >= p->max_bounces) break;
+      for (int k = 0; k < 3; ++k) pos[k] += ts * dir[k];
+      L += ts;
+      dir[2] = -dir[2];
+      gam *= p->r_surface;
+      bounce++;
+      prev = -2;
+      continue;
+    }
+    double n[3];
+    tri_normal(c->sc, hq.prim, n);
+    for (int k = 0; k < 3; ++k) pos[k] += hq.t * dir[k];
+    L += hq.t;
+    double kinc = fabs(dot3(dir, n));
+    emit_mesh_hit(c, hb, ray, sub, bounce, hq.prim, L / cw, L, gam, kinc, dOmega, us, hq.margin,
+                  hq.t2 - hq.t);
+    if ((c->sc->flags[hq.prim] & 1) && bounce < p->max_bounces) {
+      reflect(dir, n);
+      gam *= p->r_seabed;
+      bounce++;
+      prev = hq.prim;
+      continue;
+    }
+    break;
+  }
+}
+
+/* Refracting route in a linear profile: the ray is an exact circular arc, intersected
+   as chords between arc nodes spaced h = min(h_max, sqrt(8 R eps)) (sagitta <= eps);
+   the hit time interpolates the node times linearly in the chord fraction. A specular
+   reflection reflects the arc tangent at the hit; the Snell invariant is recomputed. */
+static void route_curved(const tctx* c, const double o[3], const double d0[3], const double us[3],
+                         int32_t ray, int32_t sub, double dOmega, hbuf* hb) {
+  const orc_params* p = c->p;
+  const ssp_t* s = &c->ssp;
+  double pos[3] = {o[0], o[1], o[2]}, e[2], th;
+  dir_split(d0, e, &th);
+  double xi = cos(th) / ssp_c(s, pos[2]);
+  double T = 0.0, sarc = 0.0, gam = 1.0;
+  int32_t bounce = 0, prev = -1;
+  for (int iter = 0; iter < 1000000; ++iter) {
+    if (!(T < c->T_stop)) break;
+    double h = arc_step(s, xi);
+    double dh, dz, thn, dt;
+    arc_advance(s, pos[2], th, xi, h, &dh, &dz, &thn, &dt);
+    double nxt[3] = {pos[0] + dh * e[0], pos[1] + dh * e[1], pos[2] + dz};
+    double ch[3];
+    sub3(nxt, pos, ch);
+    double len = norm3(ch);
+    double dc[3] = {ch[0] / len, ch[1] / len, ch[2] / len};
+    hitq hq = closest(c->sc, c->bv, pos, dc, EPS_HIT, len, prev >= 0 ? prev : -1);
+    double ts = INFINITY;
+    if (c->has_surface && prev != -2 && dc[2] != 0.0) {
+      double t = (p->surface_z - pos[2]) / dc[2];
+      if (t > EPS_HIT && t <= len) ts = t;
+    }
+    if (hq.prim < 0 && ts == INFINITY) {
+      pos[0] = nxt[0]; pos[1] = nxt[1]; pos[2] = nxt[2];
+      th = thn;
+      T += dt;
+      sarc += h;
+      prev = -1;
+      continue;
+    }
+    int surf = ts < hq.t;
+    double thit = surf ? ts : hq.t;
+    double f = thit / len;
+    double T_hit = T + f * dt, s_hit = sarc + f * h;
+    if (!(T_hit <= c->T_stop)) break;
+    double hp[3] = {pos[0] + thit * dc[0], pos[1] + thit * dc[1], pos[2] + thit * dc[2]};
+    double n[3];
+    if (surf) {
+      if (bounce >= p->max_bounces) break;
+      n[0] = 0; n[1] = 0; n[2] = 1;
+      gam *= p->r_surface;
+    } else {
+      tri_normal(c->sc, hq.prim, n);
+      double kinc = fabs(dot3(dc, n));
+      emit_mesh_hit(c, hb, ray, sub, bounce, hq.prim, T_hit, s_hit, gam, kinc, dOmega, us,
+                    hq.margin, hq.t2 - hq.t);
+      if (!((c->sc->flags[hq.prim] & 1) && bounce < p->max_bounces)) break;
+      gam *= p->r_seabed;
+    }
+    /* reflect the arc tangent at the hit point */
+    double thh = th - xi * s->g * (f * h);
+    double tg[3] = {cos(thh) * e[0], cos(thh) * e[1], sin(thh)};
+    reflect(tg, n);
+    dir_split(tg, e, &th);
+    pos[0] = hp[0]; pos[1] = hp[1]; pos[2] = hp[2];
+    xi = cos(th) / ssp_c(s, pos[2]);
+    T = T_hit;
+    sarc = s_hit;
+    bounce++;
+    prev = surf ? -2 : hq.prim;
+  }
+}
+
+/* Shadow test of the straight leg a -> b against the mesh (endpoints excluded). */
+static int leg_clear(const tctx* c, const double a[3], const double b[3]) {
+  double d[3];
+  sub3(b, a, d);
+  double len = norm3(d);
+  if (len <= 2e-6) return 1;
+  d[0] /= len; d[1] /= len; d[2] /= len;
+  hitq hq = closest(c->sc, c->bv, a, d, 1e-6, len - 1e-6, -1);
+  return hq.prim < 0;
+}
+
+static void mirror_point(const double pl[4], const double x[3], double r[3]) {
+  double k = 2.0 * (pl[0] * x[0] + pl[1] * x[1] + pl[2] * x[2] - pl[3]);
+  r[0] = x[0] - k * pl[0]; r[1] = x[1] - k * pl[1]; r[2] = x[2] - k * pl[2];
+}
+
+/* Point scatterers: monostatic image-source eigen-routes (Sec. II.B limited secondary
+   reflections). Mirror planes: the sea surface (reflection r_surface) then the scene's
+   planes (reflection r_seabed). Routes are plane sequences without immediate repeats,
+   enumerated by length then lexicographically; each leg is shadow-tested. Amplitude
+   sigma Gamma^2 / L^2, no speckle. */
+static void point_routes(const tctx* c, hbuf* hb) {
+  const orc_scene* sc = c->sc;
+  const orc_params* p = c->p;
+  int np = (c->has_surface ? 1 : 0) + (int)sc->n_planes;
+  double planes[64][4], gams[64];
+  if (np > 64) np = 64;
+  int q = 0;
+  if (c->has_surface) {
+    planes[q][0] = 0; planes[q][1] = 0; planes[q][2] = 1; planes[q][3] = p->surface_z;
+    gams[q++] = p->r_surface;
+  }
+  for (int64_t i = 0; i < sc->n_planes && q < np; ++i, ++q) {
+    for (int k = 0; k < 4; ++k) planes[q][k] = sc->planes[4 * i + k];
+    gams[q] = p->r_seabed;
+  }
+  int maxb = p->max_bounces > 3 ? 3 : p->max_bounces;
+  for (int64_t ip = 0; ip < sc->n_points; ++ip) {
+    double x[3] = {sc->points[3 * ip], sc->points[3 * ip + 1], sc->points[3 * ip + 2]};
+    double sigma = sc->sigma[ip];
+    if (c->ssp.curved) {
+      /* linear profile: direct eigen-arc only */
+      double dw[3], T, sarc;
+      double zz[2] = {c->ssp.z0, c->ssp.z0 + 1.0}, cc[2] = {c->ssp.c0, c->ssp.c0 + c->ssp.g};
+      if (orc_eigen_arc(zz, cc, 2, c->t, x, dw, &T, &sarc) != 0) continue;
+      if (!(T <= c->T_stop)) continue;
+      /* shadow test along chords of the arc */
+      double pos[3] = {c->t[0], c->t[1], c->t[2]}, e[2], th;
+      dir_split(dw, e, &th);
+      double xi = cos(th) / ssp_c(&c->ssp, pos[2]);
+      double left = sarc;
+      int clear = 1;
+      while (left > 0 && clear) {
+        double h = fmin(arc_step(&c->ssp, xi), left);
+        double dh, dz, thn, dt;
+        arc_advance(&c->ssp, pos[2], th, xi, h, &dh, &dz, &thn, &dt);
+        double nxt[3] = {pos[0] + dh * e[0], pos[1] + dh * e[1], pos[2] + dz};
+        if (left - h <= 0) { nxt[0] = x[0]; nxt[1] = x[1]; nxt[2] = x[2]; }
+        clear = leg_clear(c, pos, nxt);
+        pos[0] = nxt[0]; pos[1] = nxt[1]; pos[2] = nxt[2];
+        th = thn;
+        left -= h;
+      }
+      if (!clear) continue;
+      ohit h;
+      h.ray = (int32_t)ip; h.sub = 0; h.seg = 0; h.prim = -1;
+      h.tau = 2.0 * T;
+      h.len = sarc;
+      h.amp = sigma / (sarc * sarc) * exp(-2.0 * p->alpha * sarc);
+      h.psi = 0.0;
+      h.phi = wrap_pi(-TWO_PI * frac(p->f0 * h.tau));
+      mat_t_vec(c->R, dw, h.u);
+      h.margin = INFINITY;
+      h.gap = INFINITY;
+      hb_push(hb, &h);
+      continue;
+    }
+    int32_t route = 0;
+    for (int len = 0; len <= maxb; ++len) {
+      int64_t count = len == 0 ? 1 : np;
+      for (int k = 1; k < len; ++k) count *= (np - 1);
+      if (len > 0 && np == 0) count = 0;
+      for (int64_t r = 0; r < count; ++r, ++route) {
+        int seq[4];
+        int64_t rem = r, div = 1;
+        for (int k = 1; k < len; ++k) div *= (np - 1);
+        for (int k = 0; k < len; ++k) {
+          int64_t digit = rem / div;
+          rem %= div;
+          if (k + 1 < len) div /= (np - 1);
+          if (k == 0) seq[k] = (int)digit;
+          else seq[k] = (int)digit < seq[k - 1] ? (int)digit : (int)digit + 1;
+        }
+        double img[3] = {x[0], x[1], x[2]};
+        double gam = 1.0;
+        for (int k = len - 1; k >= 0; --k) {
+          mirror_point(planes[seq[k]], img, img);
+          gam *= gams[seq[k]];
+        }
+        double dv[3];
+        sub3(img, c->t, dv);
+        double L = norm3(dv);
+        if (!(L > 0) || !(L / c->ssp.c0 <= c->T_stop)) continue;
+        /* walk the unfolded route: reflection points in order */
+        double a[3] = {c->t[0], c->t[1], c->t[2]}, tgt[3] = {img[0], img[1], img[2]};
+        int ok = 1;
+        for (int k = 0; k < len && ok; ++k) {
+          const double* pl = planes[seq[k]];
+          double da = pl[0] * a[0] + pl[1] * a[1] + pl[2] * a[2] - pl[3];
+          double dt_ = pl[0] * tgt[0] + pl[1] * tgt[1] + pl[2] * tgt[2] - pl[3];
+          if (!(da * dt_ < 0)) { ok = 0; break; }
+          double f = da / (da - dt_);
+          double sp[3] = {a[0] + f * (tgt[0] - a[0]), a[1] + f * (tgt[1] - a[1]), a[2] + f * (tgt[2] - a[2])};
+          if (!leg_clear(c, a, sp)) { ok = 0; break; }
+          mirror_point(pl, tgt, tgt);
+          a[0] = sp[0]; a[1] = sp[1]; a[2] = sp[2];
+        }
+        if (!ok || !leg_clear(c, a, x)) continue;
+        ohit h;
+        h.ray = (int32_t)ip; h.sub = route; h.seg = len; h.prim = -1;
+        h.tau = 2.0 * L / c->ssp.c0;
+        h.len = L;
+        h.amp = sigma * gam * gam / (L * L) * exp(-2.0 * p->alpha * L);
+        h.psi = 0.0;
+        h.phi = wrap_pi(-TWO_PI * frac(p->f0 * h.tau));
+        double dw[3] = {dv[0] / L, dv[1] / L, dv[2] / L};
+        mat_t_vec(c->R, dw, h.u);
+        h.margin = INFINITY;
+        h.gap = INFINITY;
+        hb_push(hb, &h);
+      }
+    }
+  }
+}
+
+int orc_trace(const orc_scene* sc, const orc_params* p, const double pose_t[3], const double pose_q[4],
+              const double* ssp_z, const double* ssp_cc, int32_t n_ssp, int use_bvh, orc_hits* out) {
+  tctx c;
+  memset(&c, 0, sizeof(c));
+  c.sc = sc;
+  c.p = p;
+  if (p->n_sub != 1 && p->n_sub != 4) return 3;
+  if (ssp_make(ssp_z, ssp_cc, n_ssp, p->c_ref, &c.ssp) != 0) return 2;
+  c.c_ref = p->c_ref > 0 ? p->c_ref : ssp_c(&c.ssp, pose_t[2]);
+  /* one-way time after which no echo reaches the last range sample */
+  c.T_stop = p->r_max / c.c_ref + p->pulse / 2.0;
+  double qn = sqrt(pose_q[0] * pose_q[0] + pose_q[1] * pose_q[1] + pose_q[2] * pose_q[2] + pose_q[3] * pose_q[3]);
+  double q[4] = {pose_q[0] / qn, pose_q[1] / qn, pose_q[2] / qn, pose_q[3] / qn};
+  quat_to_matrix(q, c.R);
+  c.t[0] = pose_t[0]; c.t[1] = pose_t[1]; c.t[2] = pose_t[2];
+  c.s32 = seed32(p->seed);
+  c.has_surface = !isnan(p->surface_z);
+  bvh_t bv;
+  if (use_bvh) {
+    bvh_build(&bv, sc);
+    c.bv = &bv;
+  }
+  out->c_ref = c.c_ref;
+
+  /* Sec. III Eq. 2-3 sampling grid, cell-centred: n_ray_az x n_ray_el cells over the
+     fields of view; n_sub = 4 splits a cell into 2x2 quarters, each sampled at a
+     hash-jittered point. */
+  const int32_t nra = p->n_ray_az, nre = p->n_ray_el;
+  const double daz = p->hfov / nra, del = p->vfov / nre;
+  hbuf* rows = (hbuf*)calloc((size_t)nre + 1, sizeof(hbuf));
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int32_t j = 0; j < nre; ++j) {
+    double el_lo = -p->vfov / 2 + j * del, el_hi = el_lo + del;
+    double dOmega = daz * (sin(el_hi) - sin(el_lo)) / p->n_sub;
+    for (int32_t i = 0; i < nra; ++i) {
+      int32_t ray = j * nra + i;
+      for (int32_t s = 0; s < p->n_sub; ++s) {
+        double ox = 0.0, oy = 0.0;
+        if (p->n_sub == 4) {
+          uint32_t v[4] = {(uint32_t)ray, (uint32_t)s, 0u, c.s32};
+          orc_pcg4d(v);
+          ox = ((s & 1) + u24(v[0])) / 2.0 - 0.5;
+          oy = ((s >> 1) + u24(v[1])) / 2.0 - 0.5;
+        }
+        double az = -p->hfov / 2 + (i + 0.5 + ox) * daz;
+        double el = -p->vfov / 2 + (j + 0.5 + oy) * del;
+        double us[3] = {cos(el) * cos(az), cos(el) * sin(az), sin(el)};
+        double dw[3];
+        mat_vec(c.R, us, dw);
+        if (c.ssp.curved) route_curved(&c, c.t, dw, us, ray, s, dOmega, &rows[j]);
+        else route_straight(&c, c.t, dw, us, ray, s, dOmega, &rows[j]);
+      }
+    }
+  }
+  point_routes(&c, &rows[nre]);
+  if (use_bvh) bvh_free(&bv);
+
+  int64_t total = 0;
+  for (int32_t j = 0; j <= nre; ++j) total += rows[j].n;
+  out->n = total;
+  int rc = 0;
+  if (total > out->cap) {
+    rc = (int)(-total > -2147483647 ? -total : -2147483647);
+  } else {
+    int64_t w = 0;
+    for (int32_t j = 0; j <= nre; ++j) {
+      for (int64_t k = 0; k < rows[j].n; ++k, ++w) {
+        const ohit* h = &rows[j].v[k];
+        out->ray[w] = h->ray; out->sub[w] = h->sub; out->seg[w] = h->seg; out->prim[w] = h->prim;
+        out->tau[w] = h->tau; out->len[w] = h->len; out->amp[w] = h->amp;
+        out->psi[w] = h->psi; out->phi[w] = h->phi;
+        out->ux[w] = h->u[0]; out->uy[w] = h->u[1]; out->uz[w] = h->u[2];
+        out->cr[w] = h->amp * cos(h->phi); out->ci[w] = h->amp * sin(h->phi);
+        out->margin[w] = h->margin; out->gap[w] = h->gap;
+      }
+    }
+  }
+  for (int32_t j = 0; j <= nre; ++j) free(rows[j].v);
+  free(rows);
+  return rc;
+}
+
+/* ------------------------------------------------------------------ element echoes */
+/* Sec. II.B complex baseband accumulated along rays, already pulse-compressed:
+   s_m[n] = sum_k c_k R(t_n - tau_k) exp(j k_a u_k . p_m), k_a = 2 pi f0 / c_ref,
+   t_n = 2 (r_min + (n + 1/2) dr) / c_ref, elements p_m = (0, y_m, z_m) on a centred
+   nx x ny grid of the given pitch, m = my * nx + mx. */
+void orc_synth(const orc_params* p, const orc_hits* h, const int32_t* ns, int64_t n_ns, double* s_out) {
+  const int32_t nx = p->nx, ny = p->ny, M = nx * ny;
+  const double c_ref = h->c_ref, dr = (p->r_max - p->r_min) / p->n_range;
+  const double ka = TWO_PI * p->f0 / c_ref;
+  memset(s_out, 0, sizeof(double) * 2 * (size_t)M * (size_t)n_ns);
+  /* per hit, the requested samples inside its pulse window and c_k R(t_n - tau_k) */
+  int64_t* cnt = (int64_t*)calloc((size_t)h->n + 1, sizeof(int64_t));
+#pragma omp parallel for schedule(static)
+  for (int64_t k = 0; k < h->n; ++k) {
+    int64_t c = 0;
+    for (int64_t i = 0; i < n_ns; ++i) {
+      double tn = 2.0 * (p->r_min + (ns[i] + 0.5) * dr) / c_ref;
+      if (fabs(tn - h->tau[k]) < p->pulse) ++c;
+    }
+    cnt[k + 1] = c;
+  }
+  for (int64_t k = 0; k < h->n; ++k) cnt[k + 1] += cnt[k];
+  int64_t npairs = cnt[h->n];
+  int64_t* pi = (int64_t*)malloc(sizeof(int64_t) * (size_t)(npairs + 1));
+  cplx* pg = (cplx*)malloc(sizeof(cplx) * (size_t)(npairs + 1));
+#pragma omp parallel for schedule(static)
+  for (int64_t k = 0; k < h->n; ++k) {
+    int64_t w = cnt[k];
+    cplx ck = h->cr[k] + I * h->ci[k];
+    for (int64_t i = 0; i < n_ns; ++i) {
+      double tn = 2.0 * (p->r_min + (ns[i] + 0.5) * dr) / c_ref;
+      double u = tn - h->tau[k];
+      if (fabs(u) < p->pulse) {
+        double re, im;
+        orc_pulse_acf(u, p->pulse, p->bw, &re, &im);
+        pi[w] = i;
+        pg[w] = ck * (re + I * im);
+        ++w;
+      }
+    }
+  }
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int32_t m = 0; m < M; ++m) {
+    int32_t mx = m % nx, my = m / nx;
+    double ym = (mx - (nx - 1) / 2.0) * p->pitch, zm = (my - (ny - 1) / 2.0) * p->pitch;
+    for (int64_t k = 0; k < h->n; ++k) {
+      if (cnt[k + 1] == cnt[k]) continue;
+      cplx ph = cexp(I * ka * (h->uy[k] * ym + h->uz[k] * zm));
+      for (int64_t w = cnt[k]; w < cnt[k + 1]; ++w) {
+        cplx v = pg[w] * ph;
+        s_out[2 * ((size_t)pi[w] * M + m)] += creal(v);
+        s_out[2 * ((size_t)pi[w] * M + m) + 1] += cimag(v);
+      }
+    }
+  }
+  free(cnt);
+  free(pi);
+  free(pg);
+}
+
+/* Beam directions (Sec. III Eq. 2-3, cell-centred): az_i = -HFOV/2 + (i+1/2) HFOV/N_az,
+   el_j likewise, b = j N_az + i, u_b = (cos el cos az, cos el sin az, sin el). */
+static void beam_dir(const orc_params* p, int32_t b, double u[3]) {
+  int32_t i = b % p->n_beam_az, j = b / p->n_beam_az;
+  double az = -p->hfov / 2 + (i + 0.5) * p->hfov / p->n_beam_az;
+  double el = -p->vfov / 2 + (j + 0.5) * p->vfov / p->n_beam_el;
+  u[0] = cos(el) * cos(az);
+  u[1] = cos(el) * sin(az);
+  u[2] = sin(el);
+}
+
+/* Sec. II.B coherent summation into beams: phase-shift beamforming
+   B[b][n] = sum_m w_m exp(-j k_a u_b . p_m) s_m[n] / sum_m w_m. */
+void orc_beamform(const orc_params* p, double c_ref, const float* taper, const double* s, int64_t n_ns,
+                  const int32_t* beams, int64_t n_beams, double* b_out) {
+  const int32_t nx = p->nx, ny = p->ny, M = nx * ny;
+  const double ka = TWO_PI * p->f0 / c_ref;
+  double wsum = 0;
+  for (int32_t m = 0; m < M; ++m) wsum += taper ? taper[m] : 1.0;
+  cplx* W = (cplx*)malloc(sizeof(cplx) * (size_t)n_beams * M);
+#pragma omp parallel for schedule(static)
+  for (int64_t bi = 0; bi < n_beams; ++bi) {
+    double u[3];
+    beam_dir(p, beams[bi], u);
+    for (int32_t m = 0; m < M; ++m) {
+      int32_t mx = m % nx, my = m / nx;
+      double ym = (mx - (nx - 1) / 2.0) * p->pitch, zm = (my - (ny - 1) / 2.0) * p->pitch;
+      double w = taper ? taper[m] : 1.0;
+      W[bi * M + m] = w * cexp(-I * ka * (u[1] * ym + u[2] * zm)) / wsum;
+    }
+  }
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t i = 0; i < n_ns; ++i) {
+    const double* si = s + 2 * (size_t)i * M;
+    for (int64_t bi = 0; bi < n_beams; ++bi) {
+      cplx acc = 0;
+      for (int32_t m = 0; m < M; ++m) acc += W[bi * M + m] * (si[2 * m] + I * si[2 * m + 1]);
+      b_out[2 * ((size_t)bi * n_ns + i)] = creal(acc);
+      b_out[2 * ((size_t)bi * n_ns + i) + 1] = cimag(acc);
+    }
+  }
+  free(W);
+}
+
+/* Envelope with time-varied gain TVG(r) = r exp(2 alpha r), r_n at bin centres. */
+void orc_envelope(const orc_params* p, const double* b, const int32_t* ns, int64_t n_ns, int64_t n_beams,
+                  double* e_out) {
+  const double dr = (p->r_max - p->r_min) / p->n_range;
+  for (int64_t bi = 0; bi < n_beams; ++bi) {
+    for (int64_t i = 0; i < n_ns; ++i) {
+      double r = p->r_min + (ns[i] + 0.5) * dr;
+      double re = b[2 * ((size_t)bi * n_ns + i)], im = b[2 * ((size_t)bi * n_ns + i) + 1];
+      e_out[(size_t)bi * n_ns + i] = hypot(re, im) * r * exp(2.0 * p->alpha * r);
+    }
+  }
+}
+
+/* Sec. II.A volumetric output as a point cloud: per beam the strongest bin at or beyond
+   r_blank (first on ties), kept when it reaches the threshold (absolute, or relative to
+   the ping maximum over the same bins); position R(q) (r_n u_b) + t. */
+int64_t orc_peaks(const orc_params* p, const double pose_t[3], const double pose_q[4], const double* e,
+                  double* pts, int32_t* pbeam, int32_t* pbin) {
+  const int32_t Nb = p->n_beam_az * p->n_beam_el, Nr = p->n_range;
+  const double dr = (p->r_max - p->r_min) / Nr;
+  int32_t nb0 = 0;
+  while (nb0 < Nr && p->r_min + (nb0 + 0.5) * dr < p->r_blank) ++nb0;
+  double vmax = 0;
+  for (int32_t b = 0; b < Nb; ++b)
+    for (int32_t n = nb0; n < Nr; ++n) vmax = fmax(vmax, e[(size_t)b * Nr + n]);
+  double thr = p->thr_mode == 1 ? p->thr * vmax : p->thr;
+  double qn = sqrt(pose_q[0] * pose_q[0] + pose_q[1] * pose_q[1] + pose_q[2] * pose_q[2] + pose_q[3] * pose_q[3]);
+  double q[4] = {pose_q[0] / qn, pose_q[1] / qn, pose_q[2] / qn, pose_q[3] / qn}, R[9];
+  quat_to_matrix(q, R);
+  int64_t cnt = 0;
+  for (int32_t b = 0; b < Nb; ++b) {
+    int32_t best = -1;
+    double bv = -1;
+    for (int32_t n = nb0; n < Nr; ++n) {
+      double v = e[(size_t)b * Nr + n];
+      if (v > bv) { bv = v; best = n; }
+    }
+    if (best < 0 || !(bv >= thr)) continue;
+    double u[3], w[3];
+    beam_dir(p, b, u);
+    double r = p->r_min + (best + 0.5) * dr;
+    double v[3] = {r * u[0], r * u[1], r * u[2]};
+    mat_vec(R, v, w);
+    pts[4 * cnt] = w[0] + pose_t[0];
+    pts[4 * cnt + 1] = w[1] + pose_t[1];
+    pts[4 * cnt + 2] = w[2] + pose_t[2];
+    pts[4 * cnt + 3] = bv;
+    pbeam[cnt] = b;
+    pbin[cnt] = best;
+    ++cnt;
+  }
+  return cnt;
+}
