@@ -1,0 +1,190 @@
+/*
+ * sonar.h — C ABI of the GB300 (sm_103a) per-ping coherent echo-formation library.
+ *
+ * The library forms the volumetric output of a 3D sonar ("Towards Realistic 3D Sonar
+ * Simulation", Sec. II.A: an azimuth x elevation x range intensity volume and a point
+ * cloud) by phase-aware signal formation (Sec. II.B): rays cast into a triangle mesh
+ * along direct, refracted (Sec. II.A, Snell in a sound-speed profile) and mirror
+ * multipath routes; per-hit backscatter with speckle; complex baseband echoes per
+ * receive element with the phase set by the two-way delay; coherent summation into
+ * beams. The sampling grid follows Sec. III Eq. 1-3 (cell-centred beams and bins).
+ *
+ * Conventions
+ *  - World frame z up, sea surface at z = surface_z. Sonar frame x forward, y left,
+ *    z up. A pose rotates sonar-frame vectors into the world frame.
+ *  - Every function returns SONAR_OK (0) or a negative SONAR_E_* code; the message of
+ *    the last failure is available from sonar_last_error().
+ *  - All GPU work of a call is enqueued on the context stream. Calls that return host
+ *    results (cloud counts, debug exports) synchronise that stream before returning.
+ *  - Output buffers belong to the caller and may be device or host memory (pageable
+ *    or pinned); host outputs are filled by a device-to-host copy inside the call.
+ *    Input arrays are host memory and are copied during the call.
+ *  - One context per host thread; a context is bound to one device.
+ */
+#ifndef SONAR_H
+#define SONAR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SONAR_API __attribute__((visibility("default")))
+#else
+#define SONAR_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- error codes */
+#define SONAR_OK 0
+#define SONAR_E_ARG (-1)          /* invalid argument or parameter combination */
+#define SONAR_E_NOMEM (-2)        /* device or host allocation failed */
+#define SONAR_E_CUDA (-3)         /* CUDA runtime or driver error */
+#define SONAR_E_CAPACITY (-4)     /* caller buffer too small; needed size in last_error */
+#define SONAR_E_TIMEOUT (-5)      /* a device-side bounded wait or loop hit its limit */
+#define SONAR_E_NOSCENE (-6)      /* sonar_ping before sonar_scene_upload */
+#define SONAR_E_UNSUPPORTED (-7)  /* parameters outside what the kernels implement */
+
+/* ---------------------------------------------------------------- precision forms */
+/* Beamforming contraction precision. Every form accumulates in FP32 on the tensor
+   cores; geometry, delays and carrier phase are FP64, echoes are synthesised in FP32.
+   SONAR_FP32: each operand split into BF16 hi + lo, three products hi*hi + hi*lo +
+               lo*hi (relative operand error ~2^-17).
+   SONAR_BF16 / SONAR_FP16: one product of BF16 / FP16 operands. */
+#define SONAR_FP32 0
+#define SONAR_BF16 1
+#define SONAR_FP16 2
+
+/* ---------------------------------------------------------------- types */
+typedef struct sonar_ctx sonar_ctx;
+
+/* Sonar pose: position t (world, metres) and unit quaternion q = (w, x, y, z). */
+typedef struct {
+  double t[3];
+  double q[4];
+} sonar_pose;
+
+/* Sound-speed profile c(z), z up. n_nodes = 0: isovelocity at params.c_ref;
+   1: isovelocity at c[0]; 2: one linear gradient through (z[0], c[0]), (z[1], c[1]),
+   extended linearly (curved rays, Sec. II.A). Host pointers. */
+typedef struct {
+  int32_t n_nodes;
+  const double* z;
+  const double* c;
+} sonar_ssp;
+
+/* Sensor and run parameters. Beams and rays are cell-centred grids over the fields
+   of view (Sec. III Eq. 2-3); range bins are n_range cells of (r_max - r_min)/n_range
+   (Eq. 1), sampled at their centres. */
+typedef struct {
+  int32_t nx, ny;            /* receive elements along sonar y and z (nx % 4 == 0) */
+  double pitch_m;            /* element pitch */
+  double f0_hz, bw_hz;       /* carrier and LFM bandwidth */
+  double pulse_s;            /* pulse length T_p (Hann-windowed up-chirp) */
+  double c_ref;              /* sound speed of range bins and steering; <= 0: c(z_sonar) */
+  double hfov_rad, vfov_rad;
+  int32_t n_beam_az, n_beam_el, n_range;
+  double r_min_m, r_max_m, r_blank_m;
+  int32_t n_ray_az, n_ray_el, n_sub;  /* rays per cell grid; n_sub in {1, 4} jittered */
+  int32_t max_bounces;                /* specular reflections per route, 0..3 */
+  double surface_z;                   /* NaN: no sea surface */
+  double r_surface, r_seabed;         /* reflection coefficients (surface, mirror tris) */
+  double alpha_np_per_m;              /* amplitude attenuation */
+  uint64_t seed;                      /* speckle / jitter hash seed */
+  int32_t precision;                  /* SONAR_FP32 | SONAR_BF16 | SONAR_FP16 */
+  int32_t thr_mode;                   /* 0: absolute threshold, 1: relative to ping max */
+  double thr;
+  const float* taper;                 /* host [ny][nx] element weights; NULL = uniform */
+} sonar_params;
+
+/* One point of the cloud: strongest return of a beam (Sec. II.A point-cloud output). */
+typedef struct {
+  float x, y, z, intensity;
+  int32_t beam, bin;
+} sonar_point;
+
+/* Debug/parity export of one hit (32 bytes). key: mesh hits ((ray * n_sub + sub) << 2
+   | bounce); point scatterers 0x80000000 | (point << 8) | route. */
+typedef struct {
+  uint32_t key;
+  int32_t prim;   /* triangle id, or -1 for a point scatterer */
+  double tau;     /* two-way delay [s] (FP64) */
+  float amp, phi; /* |c_k| and arg c_k */
+  float uy, uz;   /* sonar-frame arrival direction (y, z) */
+} sonar_hit;
+
+/* Counters of the last ping or batch. */
+typedef struct {
+  int64_t n_hits;            /* hits over all pings */
+  int64_t hit_capacity;
+  int32_t n_pings;
+  int32_t taps;              /* pulse-window taps per hit */
+  float ms_trace, ms_bin, ms_synth, ms_beamform, ms_peaks; /* per stage, when timing is on */
+} sonar_stats;
+
+/* ---------------------------------------------------------------- context */
+/* Creates a context on `device` that enqueues on `cuda_stream` (a cudaStream_t; NULL
+   is the legacy default stream). Fails with SONAR_E_UNSUPPORTED on a device that is
+   not sm_103. The context owns the scene, BVH, steering matrix and workspaces. */
+SONAR_API int sonar_create(sonar_ctx** out, int device, void* cuda_stream);
+SONAR_API int sonar_set_stream(sonar_ctx* ctx, void* cuda_stream);
+/* Frees every resource of the context (after synchronising its stream). NULL is ok. */
+SONAR_API int sonar_destroy(sonar_ctx* ctx);
+/* Message of the last failure of this context ("" if none). Valid until the next call. */
+SONAR_API const char* sonar_last_error(const sonar_ctx* ctx);
+
+/* Options. SONAR_OPT_DEBUG: 1 keeps FP64 delays of hits and element echoes of the
+   last call for sonar_get_hits / sonar_get_echoes. SONAR_OPT_TIMING: 1 records
+   per-stage CUDA-event times in sonar_stats (adds synchronisation).
+   SONAR_OPT_GRAPH: 1 (default) replays the ping pipeline as a captured CUDA graph.
+   SONAR_OPT_TILE_N: beamforming N tile (128 or 256; 0 = autotuned). */
+#define SONAR_OPT_DEBUG 1
+#define SONAR_OPT_TIMING 2
+#define SONAR_OPT_GRAPH 3
+#define SONAR_OPT_TILE_N 4
+SONAR_API int sonar_set_option(sonar_ctx* ctx, int32_t option, int64_t value);
+
+/* ---------------------------------------------------------------- scene */
+/* Uploads a static scene (Sec. II.A ray casting target) and builds its BVH on the
+   device. verts [n_verts][3] f32 (metres); tris [n_tris][3] i32 vertex indices;
+   mu [n_tris] backscatter coefficient; flags [n_tris] bit0 = specular mirror
+   (reflects with r_seabed); points [n_points][3] f32 point scatterers with amplitude
+   coefficients sigma [n_points]; planes [n_planes][4] f64 unit normal and offset
+   (n.x = d) of mirror planes used for point-scatterer image routes. Any count may be
+   0 (its pointers may then be NULL). Replaces a previous scene. */
+SONAR_API int sonar_scene_upload(sonar_ctx* ctx, const float* verts, int64_t n_verts, const int32_t* tris,
+                       int64_t n_tris, const float* mu, const uint8_t* flags, const float* points,
+                       const float* sigma, int64_t n_points, const double* planes, int64_t n_planes);
+
+/* ---------------------------------------------------------------- pings */
+/* One ping. env: [n_beam_el][n_beam_az][n_range] f32 envelope |B| * TVG (device or
+   host). cloud: up to cloud_cap points ordered by beam (device or host; may be NULL
+   with cloud_cap 0). n_cloud (host, may be NULL): number of points found, even when it
+   exceeds cloud_cap (then SONAR_E_CAPACITY is returned and cloud holds the first
+   cloud_cap points). */
+SONAR_API int sonar_ping(sonar_ctx* ctx, const sonar_pose* pose, const sonar_params* params,
+               const sonar_ssp* ssp, float* env, sonar_point* cloud, int64_t cloud_cap,
+               int64_t* n_cloud);
+
+/* n_pings pings along a trajectory in one pipeline (every stage runs over all pings in
+   one launch; the sequence replays as one CUDA graph). env: [n_pings][n_beam_el]
+   [n_beam_az][n_range]; cloud: [n_pings][cloud_cap_per_ping]; n_cloud: host
+   [n_pings]. */
+SONAR_API int sonar_ping_batch(sonar_ctx* ctx, const sonar_pose* poses, int32_t n_pings,
+                     const sonar_params* params, const sonar_ssp* ssp, float* env,
+                     sonar_point* cloud, int64_t cloud_cap_per_ping, int64_t* n_cloud);
+
+/* ---------------------------------------------------------------- debug / parity */
+/* Hits of the last call (requires SONAR_OPT_DEBUG). host_out [cap]; *n = total. */
+SONAR_API int sonar_get_hits(sonar_ctx* ctx, sonar_hit* host_out, int64_t cap, int64_t* n);
+/* Element echoes s_m[n] of the last call (requires SONAR_OPT_DEBUG), host
+   [n_pings][n_range][ny*nx][2] f32 (m = my * nx + mx). */
+SONAR_API int sonar_get_echoes(sonar_ctx* ctx, float* host_out, int64_t cap_floats);
+SONAR_API int sonar_get_stats(const sonar_ctx* ctx, sonar_stats* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SONAR_H */

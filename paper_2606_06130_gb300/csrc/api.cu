@@ -1,0 +1,877 @@
+// C ABI of the echo-formation library: context, validation, workspaces, the ping
+// pipeline (trace -> bin -> synthesise -> convert -> beamform -> peaks) and its
+// replay as a captured CUDA graph.
+#include <cudaTypedefs.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+using namespace sonar;
+
+namespace {
+
+constexpr int kTileDefault = 256;
+
+template <typename T>
+void dfree(T*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+
+struct Derived {
+  double c_ref, dr, dt, t0, hw, T_stop, pitch_over_lambda, ssp_z0, ssp_c0, ssp_g, wsum, wmax;
+  int taps, nr, nr_pad, nr_x, M, k_pad, nb, nb_pad, tile_n, n_phase, n_blank, n_routes, curved;
+  int64_t n_subrays, hit_cap_per_ping;
+};
+
+}  // namespace
+
+struct sonar_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;       // private work stream (capturable)
+  cudaStream_t user_stream = nullptr;  // caller's stream, ordered with events
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  int sm_count = 0;
+  std::string err;
+  bool debug = false, timing = false, use_graph = true;
+  int tile_opt = 0;
+
+  // scene
+  bool has_scene = false;
+  DevScene sc{};
+  float4* tri32 = nullptr;
+  float* triv = nullptr;
+  int32_t* tri_prim = nullptr;
+  float* tri_mu = nullptr;
+  uint8_t* tri_flags = nullptr;
+  BvhNode* nodes = nullptr;
+  float4* points = nullptr;
+  double4* planes = nullptr;
+  uint64_t scene_version = 0;
+
+  // parameter-derived tables
+  std::vector<uint8_t> ray_key, steer_key, rtab_key;
+  double* ray_dirs = nullptr;
+  float* row_domega = nullptr;
+  void* y_hi = nullptr;
+  void* y_lo = nullptr;
+  size_t y_elems = 0;
+  float2* rtab = nullptr;
+  float* taper_dev = nullptr;
+  double y_gain = 1.0;
+
+  // workspaces
+  int p_cap = 0;
+  double* raw_host = nullptr;  // pinned [p][7]
+  double* raw_dev = nullptr;
+  DevPose* poses = nullptr;
+  HitRec* hits = nullptr;
+  HitRec* sorted = nullptr;
+  double* dbg_tau = nullptr;
+  int64_t hit_cap = 0;
+  unsigned long long* n_hits = nullptr;
+  int32_t* counts = nullptr;
+  int32_t* offsets = nullptr;
+  int64_t keys_cap = 0;
+  float2* S = nullptr;
+  int64_t s_elems = 0;
+  void* x_hi = nullptr;
+  void* x_lo = nullptr;
+  int64_t x_elems = 0;
+  float* gain = nullptr;
+  float* env_stage = nullptr;
+  int64_t env_cap = 0;
+  unsigned long long* keys = nullptr;
+  unsigned int* pmax = nullptr;
+  sonar_point* cloud_stage = nullptr;
+  int64_t cloud_stage_cap = 0;
+  long long* n_cloud_dev = nullptr;
+  long long* n_cloud_host = nullptr;  // pinned
+  int* err_dev = nullptr;
+  int64_t ws_hits = 0, ws_bins = 0, ws_s = 0, ws_x = 0;
+
+  // graph
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<uint8_t> gkey;
+
+  // last call
+  int last_p = 0;
+  Derived last_d{};
+  sonar_params last_params{};
+  sonar_stats stats{};
+};
+
+namespace {
+
+int fail(sonar_ctx* c, int code, const char* fmt, ...) __attribute__((format(printf, 3, 4)));
+int fail(sonar_ctx* c, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return code;
+}
+
+#define CU(call)                                                                                      \
+  do {                                                                                                \
+    cudaError_t e_ = (call);                                                                          \
+    if (e_ != cudaSuccess) return fail(ctx, SONAR_E_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                                       __FILE__, __LINE__);                                           \
+  } while (0)
+
+template <typename T>
+void key_add(std::vector<uint8_t>& k, const T& v) {
+  const uint8_t* p = reinterpret_cast<const uint8_t*>(&v);
+  k.insert(k.end(), p, p + sizeof(T));
+}
+
+int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+int validate(sonar_ctx* ctx, const sonar_params* p, const sonar_ssp* ssp) {
+  if (!p) return fail(ctx, SONAR_E_ARG, "params is NULL");
+  if (p->nx < 4 || p->ny < 1 || p->nx % 4 != 0 || p->nx > 64 || p->ny > 64)
+    return fail(ctx, SONAR_E_UNSUPPORTED, "array %dx%d: need nx %% 4 == 0, 4 <= nx <= 64, 1 <= ny <= 64", p->nx, p->ny);
+  if (!(p->pitch_m > 0) || !(p->f0_hz > 0) || !(p->bw_hz >= 0) || !(p->pulse_s > 0))
+    return fail(ctx, SONAR_E_ARG, "pitch, f0 and pulse must be positive, bw non-negative");
+  if (!(p->hfov_rad > 0 && p->hfov_rad < M_PI) || !(p->vfov_rad > 0 && p->vfov_rad < M_PI))
+    return fail(ctx, SONAR_E_ARG, "fields of view must lie in (0, pi)");
+  if (p->n_beam_az < 1 || p->n_beam_el < 1 || p->n_range < 1)
+    return fail(ctx, SONAR_E_ARG, "beam and range counts must be >= 1");
+  if ((int64_t)p->n_beam_az * p->n_beam_el > (1 << 24) || p->n_range > (1 << 20))
+    return fail(ctx, SONAR_E_UNSUPPORTED, "beam or range count too large");
+  if (!(p->r_min_m >= 0) || !(p->r_max_m > p->r_min_m)) return fail(ctx, SONAR_E_ARG, "need 0 <= r_min < r_max");
+  if (p->n_ray_az < 1 || p->n_ray_el < 1) return fail(ctx, SONAR_E_ARG, "ray counts must be >= 1");
+  if (p->n_sub != 1 && p->n_sub != 4) return fail(ctx, SONAR_E_ARG, "n_sub must be 1 or 4");
+  if ((int64_t)p->n_ray_az * p->n_ray_el * p->n_sub > (1 << 29))
+    return fail(ctx, SONAR_E_UNSUPPORTED, "too many sub-rays per ping");
+  if (p->max_bounces < 0 || p->max_bounces > 3) return fail(ctx, SONAR_E_ARG, "max_bounces must be 0..3");
+  if (p->precision < SONAR_FP32 || p->precision > SONAR_FP16) return fail(ctx, SONAR_E_ARG, "unknown precision");
+  if (p->thr_mode != 0 && p->thr_mode != 1) return fail(ctx, SONAR_E_ARG, "thr_mode must be 0 or 1");
+  if (ssp) {
+    if (ssp->n_nodes < 0 || ssp->n_nodes > 2)
+      return fail(ctx, SONAR_E_UNSUPPORTED, "sound-speed profiles with %d nodes are not supported", ssp->n_nodes);
+    if (ssp->n_nodes > 0 && !ssp->c) return fail(ctx, SONAR_E_ARG, "ssp.c is NULL");
+    if (ssp->n_nodes == 2 && (!ssp->z || ssp->z[0] == ssp->z[1]))
+      return fail(ctx, SONAR_E_ARG, "ssp nodes need distinct depths");
+    for (int i = 0; i < ssp->n_nodes; ++i)
+      if (!(ssp->c[i] > 0)) return fail(ctx, SONAR_E_ARG, "ssp speeds must be positive");
+  }
+  return SONAR_OK;
+}
+
+int derive(sonar_ctx* ctx, const sonar_params* p, const sonar_ssp* ssp, double z_sonar, Derived& d) {
+  d.ssp_z0 = 0.0;
+  d.ssp_g = 0.0;
+  int nn = ssp ? ssp->n_nodes : 0;
+  if (nn == 0) {
+    if (!(p->c_ref > 0)) return fail(ctx, SONAR_E_ARG, "isovelocity without a profile needs c_ref > 0");
+    d.ssp_c0 = p->c_ref;
+  } else if (nn == 1) {
+    d.ssp_c0 = ssp->c[0];
+  } else {
+    d.ssp_z0 = ssp->z[0];
+    d.ssp_c0 = ssp->c[0];
+    d.ssp_g = (ssp->c[1] - ssp->c[0]) / (ssp->z[1] - ssp->z[0]);
+  }
+  d.curved = d.ssp_g != 0.0;
+  d.c_ref = p->c_ref > 0 ? p->c_ref : d.ssp_c0 + d.ssp_g * (z_sonar - d.ssp_z0);
+  if (!(d.c_ref > 0)) return fail(ctx, SONAR_E_ARG, "non-positive reference sound speed");
+  d.nr = p->n_range;
+  d.dr = (p->r_max_m - p->r_min_m) / p->n_range;
+  d.dt = 2.0 * d.dr / d.c_ref;
+  d.t0 = 2.0 * (p->r_min_m + 0.5 * d.dr) / d.c_ref;
+  d.hw = p->pulse_s / d.dt;
+  d.taps = (int)floor(2.0 * d.hw) + 1;
+  if (d.taps > 16)
+    return fail(ctx, SONAR_E_UNSUPPORTED, "pulse spans %d range samples; at most 16 are supported", d.taps);
+  d.T_stop = p->r_max_m / d.c_ref + p->pulse_s / 2.0;
+  d.pitch_over_lambda = p->pitch_m * p->f0_hz / d.c_ref;
+  d.nr_pad = d.nr + 2 * kPad;
+  d.nr_x = (int)round_up(d.nr, 128);
+  d.M = p->nx * p->ny;
+  d.k_pad = (int)round_up(2LL * d.M, 64);
+  d.nb = p->n_beam_az * p->n_beam_el;
+  d.tile_n = ctx->tile_opt == 128 ? 128 : kTileDefault;
+  d.nb_pad = (int)round_up(d.nb, d.tile_n / 2);
+  d.n_phase = p->precision == SONAR_FP32 ? 3 : 1;
+  d.n_blank = 0;
+  while (d.n_blank < d.nr && p->r_min_m + (d.n_blank + 0.5) * d.dr < p->r_blank_m) ++d.n_blank;
+  int np = (isnan(p->surface_z) ? 0 : 1) + (ctx->has_scene ? ctx->sc.n_planes : 0);
+  int mb = p->max_bounces > 3 ? 3 : p->max_bounces;
+  if (d.curved) {
+    d.n_routes = 1;
+  } else {
+    int64_t total = 1, cnt = 1;
+    for (int len = 1; len <= mb && np > 0; ++len) {
+      cnt = len == 1 ? np : cnt * (np - 1);
+      total += cnt;
+    }
+    d.n_routes = (int)total;
+  }
+  if (d.n_routes > 256) return fail(ctx, SONAR_E_UNSUPPORTED, "too many point-scatterer routes");
+  d.wsum = 0.0;
+  d.wmax = 0.0;
+  for (int m = 0; m < d.M; ++m) {
+    double w = p->taper ? (double)p->taper[m] : 1.0;
+    if (!(w >= 0)) return fail(ctx, SONAR_E_ARG, "taper weights must be non-negative");
+    d.wsum += w;
+    d.wmax = fmax(d.wmax, w);
+  }
+  if (!(d.wsum > 0)) return fail(ctx, SONAR_E_ARG, "taper weights sum to zero");
+  d.n_subrays = (int64_t)p->n_ray_az * p->n_ray_el * p->n_sub;
+  int64_t npts = ctx->has_scene ? ctx->sc.n_points : 0;
+  d.hit_cap_per_ping = d.n_subrays * (1 + p->max_bounces) + npts * d.n_routes;
+  return SONAR_OK;
+}
+
+uint32_t seed32(uint64_t s) { return (uint32_t)(s ^ (s >> 32)); }
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void* f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  }
+  return fn;
+}
+
+int make_map(sonar_ctx* ctx, CUtensorMap* m, void* base, int64_t rows, int64_t cols, int box_rows, bool f16) {
+  auto fn = encode_fn();
+  if (!fn) return fail(ctx, SONAR_E_CUDA, "cuTensorMapEncodeTiled unavailable");
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+  cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = fn(m, f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides,
+                  box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(ctx, SONAR_E_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return SONAR_OK;
+}
+
+// (Re)build ray table, pulse table and steering matrix when their parameters change.
+int ensure_tables(sonar_ctx* ctx, const sonar_params* p, const Derived& d) {
+  std::vector<uint8_t> k;
+  key_add(k, p->n_ray_az); key_add(k, p->n_ray_el); key_add(k, p->n_sub);
+  key_add(k, p->hfov_rad); key_add(k, p->vfov_rad); key_add(k, p->seed);
+  if (k != ctx->ray_key) {
+    dfree(ctx->ray_dirs);
+    dfree(ctx->row_domega);
+    CU(cudaMalloc(&ctx->ray_dirs, sizeof(double) * 3 * d.n_subrays));
+    CU(cudaMalloc(&ctx->row_domega, sizeof(float) * p->n_ray_el));
+    CU(launch_ray_table(ctx->ray_dirs, ctx->row_domega, p->n_ray_az, p->n_ray_el, p->n_sub, p->hfov_rad,
+                        p->vfov_rad, seed32(p->seed), ctx->stream));
+    ctx->ray_key = k;
+  }
+  k.clear();
+  key_add(k, p->pulse_s); key_add(k, p->bw_hz);
+  if (k != ctx->rtab_key) {
+    if (!ctx->rtab) CU(cudaMalloc(&ctx->rtab, sizeof(float2) * (kRTab + 1)));
+    CU(launch_rtab(ctx->rtab, p->pulse_s, p->bw_hz, d.dt, ctx->stream));
+    ctx->rtab_key = k;
+  }
+  k.clear();
+  key_add(k, p->nx); key_add(k, p->ny); key_add(k, d.pitch_over_lambda); key_add(k, p->hfov_rad);
+  key_add(k, p->vfov_rad); key_add(k, p->n_beam_az); key_add(k, p->n_beam_el); key_add(k, p->precision);
+  key_add(k, d.tile_n);
+  for (int m = 0; m < d.M; ++m) key_add(k, p->taper ? p->taper[m] : 1.0f);
+  if (k != ctx->steer_key) {
+    size_t elems = (size_t)2 * d.nb_pad * d.k_pad;
+    if (elems != ctx->y_elems) {
+      dfree(ctx->y_hi);
+      dfree(ctx->y_lo);
+      CU(cudaMalloc(&ctx->y_hi, elems * 2));
+      CU(cudaMalloc(&ctx->y_lo, elems * 2));
+      ctx->y_elems = elems;
+    }
+    dfree(ctx->taper_dev);
+    if (p->taper) {
+      CU(cudaMalloc(&ctx->taper_dev, sizeof(float) * d.M));
+      CU(cudaMemcpyAsync(ctx->taper_dev, p->taper, sizeof(float) * d.M, cudaMemcpyHostToDevice, ctx->stream));
+    }
+    ctx->y_gain = d.wsum / d.wmax;  // steering entries scaled to at most 1
+    SteerArgs sa;
+    sa.nx = p->nx; sa.ny = p->ny; sa.n_beam_az = p->n_beam_az; sa.n_beam_el = p->n_beam_el;
+    sa.nb_pad = d.nb_pad; sa.k_pad = d.k_pad; sa.hfov = p->hfov_rad; sa.vfov = p->vfov_rad;
+    sa.pitch_over_lambda = d.pitch_over_lambda; sa.taper = ctx->taper_dev; sa.wsum = d.wsum;
+    sa.gain = ctx->y_gain; sa.mode = p->precision; sa.y_hi = ctx->y_hi; sa.y_lo = ctx->y_lo;
+    CU(launch_steer(sa, ctx->stream));
+    ctx->steer_key = k;
+  }
+  return SONAR_OK;
+}
+
+template <typename T>
+int grow(sonar_ctx* ctx, T*& ptr, int64_t& cap, int64_t need, size_t elem, bool zero) {
+  if (need <= cap && ptr) return SONAR_OK;
+  dfree(ptr);
+  cudaError_t e = cudaMalloc((void**)&ptr, (size_t)need * elem);
+  if (e != cudaSuccess) {
+    cap = 0;
+    return fail(ctx, SONAR_E_NOMEM, "cudaMalloc of %lld bytes failed: %s", (long long)(need * elem), cudaGetErrorString(e));
+  }
+  if (zero) CU(cudaMemsetAsync(ptr, 0, (size_t)need * elem, ctx->stream));
+  cap = need;
+  return SONAR_OK;
+}
+
+int ensure_workspace(sonar_ctx* ctx, int P, const Derived& d) {
+  int rc;
+  if (P > ctx->p_cap) {
+    if (ctx->raw_host) cudaFreeHost(ctx->raw_host);
+    if (ctx->n_cloud_host) cudaFreeHost(ctx->n_cloud_host);
+    ctx->raw_host = nullptr;
+    ctx->n_cloud_host = nullptr;
+    dfree(ctx->raw_dev); dfree(ctx->poses); dfree(ctx->gain); dfree(ctx->pmax); dfree(ctx->n_cloud_dev);
+    CU(cudaMallocHost(&ctx->raw_host, sizeof(double) * 7 * P));
+    CU(cudaMallocHost(&ctx->n_cloud_host, sizeof(long long) * P));
+    CU(cudaMalloc(&ctx->raw_dev, sizeof(double) * 7 * P));
+    CU(cudaMalloc(&ctx->poses, sizeof(DevPose) * P));
+    CU(cudaMalloc(&ctx->gain, sizeof(float) * P));
+    CU(cudaMalloc(&ctx->pmax, sizeof(unsigned) * P));
+    CU(cudaMalloc(&ctx->n_cloud_dev, sizeof(long long) * P));
+    ctx->p_cap = P;
+  }
+  if (!ctx->n_hits) CU(cudaMalloc(&ctx->n_hits, sizeof(unsigned long long)));
+  if (!ctx->err_dev) CU(cudaMalloc(&ctx->err_dev, sizeof(int)));
+  int64_t hit_need = (int64_t)P * d.hit_cap_per_ping;
+  if (hit_need < 1) hit_need = 1;
+  if (hit_need > ctx->ws_hits || !ctx->hits) {
+    int64_t c0 = 0, c1 = 0, c2 = 0;
+    dfree(ctx->hits); dfree(ctx->sorted); dfree(ctx->dbg_tau);
+    if ((rc = grow(ctx, ctx->hits, c0, hit_need, sizeof(HitRec), false))) return rc;
+    if ((rc = grow(ctx, ctx->sorted, c1, hit_need, sizeof(HitRec), false))) return rc;
+    if ((rc = grow(ctx, ctx->dbg_tau, c2, hit_need, sizeof(double), false))) return rc;
+    ctx->ws_hits = hit_need;
+  }
+  ctx->hit_cap = hit_need;
+  int64_t bins = (int64_t)P * d.nr_pad + 1;
+  if (bins > ctx->ws_bins || !ctx->counts) {
+    int64_t c0 = 0, c1 = 0;
+    dfree(ctx->counts); dfree(ctx->offsets);
+    if ((rc = grow(ctx, ctx->counts, c0, bins, sizeof(int32_t), false))) return rc;
+    if ((rc = grow(ctx, ctx->offsets, c1, bins, sizeof(int32_t), false))) return rc;
+    ctx->ws_bins = bins;
+  }
+  int64_t s_need = ((int64_t)P * d.nr_pad + 2 * kPad) * d.M;
+  if (s_need > ctx->ws_s || !ctx->S) {
+    int64_t c0 = 0;
+    dfree(ctx->S);
+    if ((rc = grow(ctx, ctx->S, c0, s_need, sizeof(float2), false))) return rc;
+    ctx->ws_s = s_need;
+  }
+  ctx->s_elems = s_need;
+  int64_t x_need = (int64_t)P * d.nr_x * d.k_pad;
+  if (x_need != ctx->ws_x || !ctx->x_hi) {
+    int64_t c0 = 0, c1 = 0;
+    dfree(ctx->x_hi); dfree(ctx->x_lo);
+    if ((rc = grow(ctx, ctx->x_hi, c0, x_need, 2, true))) return rc;
+    if ((rc = grow(ctx, ctx->x_lo, c1, x_need, 2, true))) return rc;
+    ctx->ws_x = x_need;
+  }
+  ctx->x_elems = x_need;
+  int64_t keys_need = (int64_t)P * d.nb;
+  if (!ctx->keys || keys_need > ctx->keys_cap) {
+    dfree(ctx->keys);
+    CU(cudaMalloc(&ctx->keys, sizeof(unsigned long long) * keys_need));
+    ctx->keys_cap = keys_need;
+  }
+  return SONAR_OK;
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+struct Outputs {
+  float* env;
+  sonar_point* cloud;
+  int64_t cap;
+};
+
+// Enqueue the whole pipeline for P pings on the context stream (graph-capturable:
+// no host synchronisation, fixed grids that read device-side counts).
+int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, const Outputs& o,
+            cudaEvent_t* ev) {
+  cudaStream_t st = ctx->stream;
+  auto mark = [&](int i) {
+    if (ev) cudaEventRecord(ev[i], st);
+  };
+  mark(0);
+  CU(cudaMemsetAsync(ctx->n_hits, 0, sizeof(unsigned long long), st));
+  CU(cudaMemsetAsync(ctx->err_dev, 0, sizeof(int), st));
+  CU(launch_poses(ctx->raw_dev, ctx->poses, P, st));
+  TraceArgs ta;
+  memset(&ta, 0, sizeof(ta));
+  ta.sc = ctx->sc;
+  ta.poses = ctx->poses;
+  ta.ray_dirs = ctx->ray_dirs;
+  ta.row_domega = ctx->row_domega;
+  ta.n_pings = P;
+  ta.n_ray_az = p->n_ray_az;
+  ta.n_ray_el = p->n_ray_el;
+  ta.n_sub = p->n_sub;
+  ta.n_subrays = (int32_t)d.n_subrays;
+  ta.max_bounces = p->max_bounces;
+  ta.has_surface = isnan(p->surface_z) ? 0 : 1;
+  ta.curved = d.curved;
+  ta.surface_z = p->surface_z;
+  ta.r_surface = p->r_surface;
+  ta.r_seabed = p->r_seabed;
+  ta.alpha = p->alpha_np_per_m;
+  ta.seed32 = seed32(p->seed);
+  ta.ssp_z0 = d.ssp_z0;
+  ta.ssp_c0 = d.ssp_c0;
+  ta.ssp_g = d.ssp_g;
+  ta.T_stop = d.T_stop;
+  ta.t0 = d.t0;
+  ta.inv_dt = 1.0 / d.dt;
+  ta.hw = d.hw;
+  ta.f0 = p->f0_hz;
+  ta.nr_pad = d.nr_pad;
+  ta.n_routes = d.n_routes;
+  ta.hits = ctx->hits;
+  ta.dbg_tau = ctx->debug ? ctx->dbg_tau : nullptr;
+  ta.n_hits = ctx->n_hits;
+  ta.hit_cap = ctx->hit_cap;
+  ta.err = ctx->err_dev;
+  CU(launch_trace(ta, ctx->sm_count, st));
+  CU(launch_points(ta, st));
+  mark(1);
+  const int32_t n_bins = P * d.nr_pad;
+  CU(launch_bin(ctx->hits, ctx->n_hits, n_bins, ctx->counts, ctx->offsets, ctx->sorted, ctx->sm_count, st));
+  mark(2);
+  CU(cudaMemsetAsync(ctx->S, 0, sizeof(float2) * ctx->s_elems, st));
+  SynthArgs sa;
+  sa.hits_sorted = ctx->sorted;
+  sa.n_valid = ctx->offsets + n_bins;
+  sa.rtab = ctx->rtab;
+  sa.rtab_scale = (float)(d.dt * kRTab / (2.0 * p->pulse_s));
+  sa.taps = d.taps;
+  sa.nx = p->nx;
+  sa.ny = p->ny;
+  sa.pitch_over_lambda = (float)d.pitch_over_lambda;
+  sa.S = ctx->S;
+  sa.total_rows = (int64_t)P * d.nr_pad;
+  sa.err = ctx->err_dev;
+  CU(launch_synth(sa, ctx->sm_count, st));
+  ConvertArgs ca;
+  ca.S = ctx->S;
+  ca.n_pings = P;
+  ca.nr = d.nr;
+  ca.nr_pad = d.nr_pad;
+  ca.nr_x = d.nr_x;
+  ca.M = d.M;
+  ca.k_pad = d.k_pad;
+  ca.mode = p->precision;
+  ca.gain = ctx->gain;
+  ca.x_hi = ctx->x_hi;
+  ca.x_lo = ctx->x_lo;
+  CU(launch_convert(ca, ctx->sm_count, st));
+  mark(3);
+  CU(cudaMemsetAsync(ctx->keys, 0, sizeof(unsigned long long) * (size_t)P * d.nb, st));
+  CU(cudaMemsetAsync(ctx->pmax, 0, sizeof(unsigned) * P, st));
+  GemmArgs ga;
+  memset(&ga, 0, sizeof(ga));
+  const bool f16 = p->precision == SONAR_FP16;
+  int rc;
+  if ((rc = make_map(ctx, &ga.map_xh, ctx->x_hi, (int64_t)P * d.nr_x, d.k_pad, 128, f16))) return rc;
+  if ((rc = make_map(ctx, &ga.map_xl, ctx->x_lo, (int64_t)P * d.nr_x, d.k_pad, 128, f16))) return rc;
+  if ((rc = make_map(ctx, &ga.map_yh, ctx->y_hi, 2LL * d.nb_pad, d.k_pad, d.tile_n, f16))) return rc;
+  if ((rc = make_map(ctx, &ga.map_yl, ctx->y_lo, 2LL * d.nb_pad, d.k_pad, d.tile_n, f16))) return rc;
+  ga.tiles_m = P * d.nr_x / 128;
+  ga.tiles_n = 2 * d.nb_pad / d.tile_n;
+  ga.k_blocks = d.k_pad / 64;
+  ga.n_phase = d.n_phase;
+  ga.tile_n = d.tile_n;
+  ga.f16 = f16 ? 1 : 0;
+  ga.nr = d.nr;
+  ga.nr_x = d.nr_x;
+  ga.n_beams = d.nb;
+  ga.n_blank = d.n_blank;
+  ga.r_min = (float)p->r_min_m;
+  ga.dr = (float)d.dr;
+  ga.alpha2 = (float)(2.0 * p->alpha_np_per_m);
+  ga.gain = ctx->gain;
+  ga.y_gain_inv = (float)(1.0 / ctx->y_gain);
+  ga.env = o.env;
+  ga.peak_keys = ctx->keys;
+  ga.ping_max = ctx->pmax;
+  ga.err = ctx->err_dev;
+  CU(launch_gemm(ga, ctx->sm_count, st));
+  mark(4);
+  PeakArgs pa;
+  pa.peak_keys = ctx->keys;
+  pa.ping_max = ctx->pmax;
+  pa.poses = ctx->poses;
+  pa.n_pings = P;
+  pa.n_beam_az = p->n_beam_az;
+  pa.n_beam_el = p->n_beam_el;
+  pa.nr = d.nr;
+  pa.hfov = p->hfov_rad;
+  pa.vfov = p->vfov_rad;
+  pa.r_min = p->r_min_m;
+  pa.dr = d.dr;
+  pa.thr_mode = p->thr_mode;
+  pa.thr = (float)p->thr;
+  pa.cloud = o.cloud;
+  pa.cap = o.cap;
+  pa.n_cloud = ctx->n_cloud_dev;
+  CU(launch_peaks(pa, st));
+  mark(5);
+  return SONAR_OK;
+}
+
+int run(sonar_ctx* ctx, const sonar_pose* poses, int P, const sonar_params* p, const sonar_ssp* ssp, float* env,
+        sonar_point* cloud, int64_t cloud_cap, int64_t* n_cloud) {
+  if (!ctx) return SONAR_E_ARG;
+  ctx->err.clear();
+  if (!poses || P < 1) return fail(ctx, SONAR_E_ARG, "need at least one pose");
+  if (!env) return fail(ctx, SONAR_E_ARG, "env is NULL");
+  if (cloud_cap < 0 || (cloud_cap > 0 && !cloud)) return fail(ctx, SONAR_E_ARG, "bad cloud buffer");
+  if (!ctx->has_scene) return fail(ctx, SONAR_E_NOSCENE, "no scene uploaded");
+  int rc = validate(ctx, p, ssp);
+  if (rc) return rc;
+  for (int i = 0; i < P; ++i) {
+    const double* q = poses[i].q;
+    double n2 = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
+    if (!(n2 > 1e-12) || !isfinite(poses[i].t[0] + poses[i].t[1] + poses[i].t[2]))
+      return fail(ctx, SONAR_E_ARG, "pose %d is not finite or has a zero quaternion", i);
+  }
+  CU(cudaSetDevice(ctx->device));
+  // the work stream starts after everything already queued on the caller's stream
+  CU(cudaEventRecord(ctx->ev_in, ctx->user_stream));
+  CU(cudaStreamWaitEvent(ctx->stream, ctx->ev_in, 0));
+  Derived d;
+  if ((rc = derive(ctx, p, ssp, poses[0].t[2], d))) return rc;
+  if ((int64_t)P * d.nr_pad + 1 > (1LL << 31) - 1) return fail(ctx, SONAR_E_UNSUPPORTED, "batch too large");
+  if ((rc = ensure_tables(ctx, p, d))) return rc;
+  if ((rc = ensure_workspace(ctx, P, d))) return rc;
+
+  // outputs: device buffers are written in place, host buffers through staging
+  const bool env_dev = is_device_ptr(env);
+  const bool cloud_dev = cloud_cap == 0 || is_device_ptr(cloud);
+  const int64_t env_elems = (int64_t)P * d.nb * d.nr;
+  Outputs o;
+  o.env = env;
+  if (!env_dev) {
+    if ((rc = grow(ctx, ctx->env_stage, ctx->env_cap, env_elems, sizeof(float), false))) return rc;
+    o.env = ctx->env_stage;
+  }
+  o.cap = cloud_cap;
+  o.cloud = cloud;
+  if (!cloud_dev) {
+    if ((rc = grow(ctx, ctx->cloud_stage, ctx->cloud_stage_cap, (int64_t)P * cloud_cap, sizeof(sonar_point), false)))
+      return rc;
+    o.cloud = ctx->cloud_stage;
+  }
+
+  for (int i = 0; i < P; ++i) {
+    double* r = ctx->raw_host + 7 * i;
+    r[0] = poses[i].t[0]; r[1] = poses[i].t[1]; r[2] = poses[i].t[2];
+    r[3] = poses[i].q[0]; r[4] = poses[i].q[1]; r[5] = poses[i].q[2]; r[6] = poses[i].q[3];
+  }
+  CU(cudaMemcpyAsync(ctx->raw_dev, ctx->raw_host, sizeof(double) * 7 * P, cudaMemcpyHostToDevice, ctx->stream));
+
+  cudaEvent_t ev[6];
+  const bool timed = ctx->timing;
+  if (timed) {
+    for (auto& e : ev) CU(cudaEventCreate(&e));
+    rc = enqueue(ctx, P, p, d, o, ev);
+  } else if (ctx->use_graph) {
+    std::vector<uint8_t> k;
+    key_add(k, P); key_add(k, *p); key_add(k, o.env); key_add(k, o.cloud); key_add(k, o.cap);
+    key_add(k, ctx->debug); key_add(k, ctx->scene_version); key_add(k, d.c_ref);
+    if (ssp) {
+      key_add(k, ssp->n_nodes);
+      for (int i = 0; i < ssp->n_nodes; ++i) { key_add(k, ssp->c[i]); if (ssp->z) key_add(k, ssp->z[i]); }
+    }
+    key_add(k, ctx->hits); key_add(k, ctx->S); key_add(k, ctx->x_hi); key_add(k, ctx->y_hi); key_add(k, ctx->keys);
+    if (!ctx->gexec || k != ctx->gkey) {
+      if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; }
+      cudaGraph_t g;
+      CU(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+      rc = enqueue(ctx, P, p, d, o, nullptr);
+      cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
+      if (rc) { if (ce == cudaSuccess) cudaGraphDestroy(g); return rc; }
+      CU(ce);
+      cudaError_t ie = cudaGraphInstantiate(&ctx->gexec, g, 0);
+      cudaGraphDestroy(g);
+      CU(ie);
+      ctx->gkey = k;
+    }
+    CU(cudaGraphLaunch(ctx->gexec, ctx->stream));
+  } else {
+    rc = enqueue(ctx, P, p, d, o, nullptr);
+  }
+  if (rc) return rc;
+  if (!env_dev)
+    CU(cudaMemcpyAsync(env, o.env, sizeof(float) * env_elems, cudaMemcpyDeviceToHost, ctx->stream));
+  if (!cloud_dev && cloud_cap > 0)
+    CU(cudaMemcpyAsync(cloud, o.cloud, sizeof(sonar_point) * P * cloud_cap, cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaMemcpyAsync(ctx->n_cloud_host, ctx->n_cloud_dev, sizeof(long long) * P, cudaMemcpyDeviceToHost, ctx->stream));
+  unsigned long long nh = 0;
+  int errw = 0;
+  CU(cudaMemcpyAsync(&nh, ctx->n_hits, sizeof(nh), cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaMemcpyAsync(&errw, ctx->err_dev, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaEventRecord(ctx->ev_out, ctx->stream));
+  CU(cudaStreamWaitEvent(ctx->user_stream, ctx->ev_out, 0));
+  CU(cudaStreamSynchronize(ctx->stream));
+  ctx->last_p = P;
+  ctx->last_d = d;
+  ctx->last_params = *p;
+  ctx->stats.n_hits = (int64_t)nh;
+  ctx->stats.hit_capacity = ctx->hit_cap;
+  ctx->stats.n_pings = P;
+  ctx->stats.taps = d.taps;
+  if (timed) {
+    float t[5];
+    for (int i = 0; i < 5; ++i) cudaEventElapsedTime(&t[i], ev[i], ev[i + 1]);
+    ctx->stats.ms_trace = t[0];
+    ctx->stats.ms_bin = t[1];
+    ctx->stats.ms_synth = t[2];
+    ctx->stats.ms_beamform = t[3];
+    ctx->stats.ms_peaks = t[4];
+    for (auto& e : ev) cudaEventDestroy(e);
+  }
+  if (errw & kErrTimeout) return fail(ctx, SONAR_E_TIMEOUT, "a device-side wait exceeded its limit");
+  if (errw & kErrLoop) return fail(ctx, SONAR_E_TIMEOUT, "a ray-marching loop exceeded its step limit");
+  if (errw & kErrStack) return fail(ctx, SONAR_E_TIMEOUT, "BVH traversal stack overflow");
+  if (errw & kErrCapacity) return fail(ctx, SONAR_E_CAPACITY, "hit capacity %lld exceeded", (long long)ctx->hit_cap);
+  int over = 0;
+  for (int i = 0; i < P; ++i) {
+    if (n_cloud) n_cloud[i] = ctx->n_cloud_host[i];
+    if (ctx->n_cloud_host[i] > cloud_cap) over = 1;
+  }
+  if (over && (cloud_cap > 0 || cloud))
+    return fail(ctx, SONAR_E_CAPACITY, "cloud needs more than %lld points per ping", (long long)cloud_cap);
+  return SONAR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sonar_create(sonar_ctx** out, int device, void* cuda_stream) {
+  if (!out) return SONAR_E_ARG;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+    cudaGetLastError();
+    return SONAR_E_CUDA;
+  }
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return SONAR_E_CUDA;
+  if (!(prop.major == 10 && prop.minor == 3)) return SONAR_E_UNSUPPORTED;
+  if (cudaSetDevice(device) != cudaSuccess) return SONAR_E_CUDA;
+  if (prepare_gemm() != cudaSuccess) return SONAR_E_CUDA;
+  sonar_ctx* c = new (std::nothrow) sonar_ctx();
+  if (!c) return SONAR_E_NOMEM;
+  c->device = device;
+  c->user_stream = (cudaStream_t)cuda_stream;
+  if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+    delete c;
+    return SONAR_E_CUDA;
+  }
+  c->sm_count = prop.multiProcessorCount;
+  *out = c;
+  return SONAR_OK;
+}
+
+int sonar_set_stream(sonar_ctx* ctx, void* cuda_stream) {
+  if (!ctx) return SONAR_E_ARG;
+  ctx->user_stream = (cudaStream_t)cuda_stream;
+  return SONAR_OK;
+}
+
+const char* sonar_last_error(const sonar_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int sonar_set_option(sonar_ctx* ctx, int32_t option, int64_t value) {
+  if (!ctx) return SONAR_E_ARG;
+  switch (option) {
+    case SONAR_OPT_DEBUG: ctx->debug = value != 0; break;
+    case SONAR_OPT_TIMING: ctx->timing = value != 0; break;
+    case SONAR_OPT_GRAPH: ctx->use_graph = value != 0; break;
+    case SONAR_OPT_TILE_N:
+      if (value != 0 && value != 128 && value != 256) return fail(ctx, SONAR_E_ARG, "tile_n must be 0, 128 or 256");
+      ctx->tile_opt = (int)value;
+      break;
+    default: return fail(ctx, SONAR_E_ARG, "unknown option %d", option);
+  }
+  if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; ctx->gkey.clear(); }
+  return SONAR_OK;
+}
+
+static void free_scene(sonar_ctx* c) {
+  dfree(c->tri32); dfree(c->triv); dfree(c->tri_prim); dfree(c->tri_mu); dfree(c->tri_flags);
+  dfree(c->nodes); dfree(c->points); dfree(c->planes);
+  c->has_scene = false;
+  memset(&c->sc, 0, sizeof(c->sc));
+}
+
+int sonar_destroy(sonar_ctx* c) {
+  if (!c) return SONAR_OK;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->ev_in) cudaEventDestroy(c->ev_in);
+  if (c->ev_out) cudaEventDestroy(c->ev_out);
+  if (c->stream) cudaStreamDestroy(c->stream);
+  free_scene(c);
+  dfree(c->ray_dirs); dfree(c->row_domega); dfree(c->y_hi); dfree(c->y_lo); dfree(c->rtab); dfree(c->taper_dev);
+  if (c->raw_host) cudaFreeHost(c->raw_host);
+  if (c->n_cloud_host) cudaFreeHost(c->n_cloud_host);
+  dfree(c->raw_dev); dfree(c->poses); dfree(c->hits); dfree(c->sorted); dfree(c->dbg_tau); dfree(c->n_hits);
+  dfree(c->counts); dfree(c->offsets); dfree(c->S); dfree(c->x_hi); dfree(c->x_lo); dfree(c->gain);
+  dfree(c->env_stage); dfree(c->keys); dfree(c->pmax); dfree(c->cloud_stage); dfree(c->n_cloud_dev); dfree(c->err_dev);
+  delete c;
+  return SONAR_OK;
+}
+
+int sonar_scene_upload(sonar_ctx* ctx, const float* verts, int64_t n_verts, const int32_t* tris, int64_t n_tris,
+                       const float* mu, const uint8_t* flags, const float* points, const float* sigma,
+                       int64_t n_points, const double* planes, int64_t n_planes) {
+  if (!ctx) return SONAR_E_ARG;
+  ctx->err.clear();
+  if (n_verts < 0 || n_tris < 0 || n_points < 0 || n_planes < 0) return fail(ctx, SONAR_E_ARG, "negative count");
+  if (n_tris > 0 && (!verts || !tris || !mu || !flags)) return fail(ctx, SONAR_E_ARG, "mesh arrays missing");
+  if (n_points > 0 && (!points || !sigma)) return fail(ctx, SONAR_E_ARG, "point arrays missing");
+  if (n_planes > 0 && !planes) return fail(ctx, SONAR_E_ARG, "plane array missing");
+  if (n_tris >= (1LL << 30) || n_points >= (1LL << 23) || n_planes > 62)
+    return fail(ctx, SONAR_E_UNSUPPORTED, "scene too large");
+  for (int64_t i = 0; i < 3 * n_tris; ++i)
+    if (tris[i] < 0 || tris[i] >= n_verts) return fail(ctx, SONAR_E_ARG, "triangle %lld has a bad vertex index", (long long)(i / 3));
+  for (int64_t i = 0; i < 3 * n_verts; ++i)
+    if (!isfinite(verts[i])) return fail(ctx, SONAR_E_ARG, "vertex %lld is not finite", (long long)(i / 3));
+  CU(cudaSetDevice(ctx->device));
+  CU(cudaStreamSynchronize(ctx->user_stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  free_scene(ctx);
+  if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; ctx->gkey.clear(); }
+  if (n_tris > 0) {
+    float* dv = nullptr;
+    int32_t* dt = nullptr;
+    float* dm = nullptr;
+    uint8_t* df = nullptr;
+    CU(cudaMalloc(&dv, sizeof(float) * 3 * n_verts));
+    CU(cudaMalloc(&dt, sizeof(int32_t) * 3 * n_tris));
+    CU(cudaMalloc(&dm, sizeof(float) * n_tris));
+    CU(cudaMalloc(&df, n_tris));
+    CU(cudaMemcpyAsync(dv, verts, sizeof(float) * 3 * n_verts, cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(dt, tris, sizeof(int32_t) * 3 * n_tris, cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(dm, mu, sizeof(float) * n_tris, cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(df, flags, n_tris, cudaMemcpyHostToDevice, ctx->stream));
+    cudaError_t e = build_bvh(dv, dt, dm, df, (int32_t)n_tris, &ctx->tri32, &ctx->triv, &ctx->tri_prim, &ctx->tri_mu,
+                              &ctx->tri_flags, &ctx->nodes, &ctx->sc.root, ctx->stream);
+    cudaFree(dv);
+    cudaFree(dt);
+    cudaFree(dm);
+    cudaFree(df);
+    CU(e);
+  }
+  if (n_points > 0) {
+    std::vector<float4> pts(n_points);
+    for (int64_t i = 0; i < n_points; ++i) pts[i] = make_float4(points[3 * i], points[3 * i + 1], points[3 * i + 2], sigma[i]);
+    CU(cudaMalloc(&ctx->points, sizeof(float4) * n_points));
+    CU(cudaMemcpy(ctx->points, pts.data(), sizeof(float4) * n_points, cudaMemcpyHostToDevice));
+  }
+  if (n_planes > 0) {
+    CU(cudaMalloc(&ctx->planes, sizeof(double4) * n_planes));
+    CU(cudaMemcpy(ctx->planes, planes, sizeof(double4) * n_planes, cudaMemcpyHostToDevice));
+  }
+  ctx->sc.tri32 = ctx->tri32;
+  ctx->sc.triv = ctx->triv;
+  ctx->sc.tri_prim = ctx->tri_prim;
+  ctx->sc.tri_mu = ctx->tri_mu;
+  ctx->sc.tri_flags = ctx->tri_flags;
+  ctx->sc.nodes = ctx->nodes;
+  ctx->sc.n_tris = (int32_t)n_tris;
+  ctx->sc.points = ctx->points;
+  ctx->sc.n_points = (int32_t)n_points;
+  ctx->sc.planes = ctx->planes;
+  ctx->sc.n_planes = (int32_t)n_planes;
+  ctx->has_scene = true;
+  ctx->scene_version++;
+  return SONAR_OK;
+}
+
+int sonar_ping(sonar_ctx* ctx, const sonar_pose* pose, const sonar_params* params, const sonar_ssp* ssp, float* env,
+               sonar_point* cloud, int64_t cloud_cap, int64_t* n_cloud) {
+  return run(ctx, pose, 1, params, ssp, env, cloud, cloud_cap, n_cloud);
+}
+
+int sonar_ping_batch(sonar_ctx* ctx, const sonar_pose* poses, int32_t n_pings, const sonar_params* params,
+                     const sonar_ssp* ssp, float* env, sonar_point* cloud, int64_t cloud_cap_per_ping,
+                     int64_t* n_cloud) {
+  return run(ctx, poses, n_pings, params, ssp, env, cloud, cloud_cap_per_ping, n_cloud);
+}
+
+int sonar_get_hits(sonar_ctx* ctx, sonar_hit* out, int64_t cap, int64_t* n) {
+  if (!ctx) return SONAR_E_ARG;
+  if (!ctx->debug) return fail(ctx, SONAR_E_ARG, "enable SONAR_OPT_DEBUG before the ping");
+  if (ctx->last_p == 0) return fail(ctx, SONAR_E_ARG, "no ping yet");
+  CU(cudaSetDevice(ctx->device));
+  int64_t total = ctx->stats.n_hits;
+  if (n) *n = total;
+  int64_t k = total < cap ? total : cap;
+  if (k > 0 && out) {
+    std::vector<HitRec> h(k);
+    std::vector<double> tau(k);
+    CU(cudaMemcpyAsync(h.data(), ctx->hits, sizeof(HitRec) * k, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaMemcpyAsync(tau.data(), ctx->dbg_tau, sizeof(double) * k, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    for (int64_t i = 0; i < k; ++i) {
+      out[i].key = h[i].key;
+      out[i].prim = h[i].prim;
+      out[i].tau = tau[i];
+      out[i].amp = hypotf(h[i].cr, h[i].ci);
+      out[i].phi = atan2f(h[i].ci, h[i].cr);
+      out[i].uy = h[i].uy;
+      out[i].uz = h[i].uz;
+    }
+  }
+  if (total > cap) return fail(ctx, SONAR_E_CAPACITY, "%lld hits", (long long)total);
+  return SONAR_OK;
+}
+
+int sonar_get_echoes(sonar_ctx* ctx, float* out, int64_t cap_floats) {
+  if (!ctx || !out) return SONAR_E_ARG;
+  if (ctx->last_p == 0) return fail(ctx, SONAR_E_ARG, "no ping yet");
+  const Derived& d = ctx->last_d;
+  const int64_t per_ping = (int64_t)d.nr * d.M * 2;
+  if (cap_floats < per_ping * ctx->last_p) return fail(ctx, SONAR_E_CAPACITY, "need %lld floats", (long long)(per_ping * ctx->last_p));
+  CU(cudaSetDevice(ctx->device));
+  for (int p = 0; p < ctx->last_p; ++p) {
+    const float2* src = ctx->S + ((int64_t)p * d.nr_pad + kPad) * d.M;
+    CU(cudaMemcpyAsync(out + p * per_ping, src, sizeof(float) * per_ping, cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  CU(cudaStreamSynchronize(ctx->stream));
+  return SONAR_OK;
+}
+
+int sonar_get_stats(const sonar_ctx* ctx, sonar_stats* out) {
+  if (!ctx || !out) return SONAR_E_ARG;
+  *out = ctx->stats;
+  return SONAR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,401 @@
+// Phase-shift beamforming (Sec. II.B coherent summation into beams) as one dense
+// contraction on the 5th-generation tensor cores, with the envelope, time-varied gain
+// and per-beam peak search fused into the epilogue.
+//
+// Complex B[b][n] = sum_m W[b][m] s_m[n] is run as a real GEMM
+//   C[n][2b + r] = sum_k X[n][k] Y[2b + r][k],  k = 2m + c,
+// X = element echoes with (re, im) interleaved per element (K-major), and Y the static
+// real 4-form of the steering matrix: row 2b = (Wr, -Wi) pairs, row 2b+1 = (Wi, Wr).
+// A thread of the epilogue then holds (Re, Im) of a beam in adjacent accumulator
+// columns. Tiles: 128 range samples x (tile_n / 2) beams, K step 64 (one 128-byte
+// swizzle atom), operands staged by TMA into a 4-stage ring, MMAs issued by one thread
+// into a double-buffered TMEM accumulator (2 x tile_n columns) so the epilogue of one
+// tile overlaps the MMAs of the next. Persistent CTAs, one per SM.
+//
+// FP32 form: X = Xh + Xl, Y = Yh + Yl in BF16; three passes hi*hi, hi*lo, lo*hi
+// accumulate into the same FP32 accumulator.
+#include <math.h>
+
+#include "common.cuh"
+
+namespace sonar {
+namespace {
+
+constexpr int BM = 128;
+constexpr int BK = 64;
+constexpr int STAGES = 4;
+constexpr int kGemmThreads = 192;  // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+
+// ----------------------------------------------------------------- PTX wrappers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: gives up after ~2^31 cycles (about a second), flags the error.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err) {
+  if (mbar_try(bar, parity)) return true;
+  long long t0 = clock64();
+  for (;;) {
+    for (int i = 0; i < 64; ++i)
+      if (mbar_try(bar, parity)) return true;
+    if (clock64() - t0 > (1ll << 31)) {
+      atomicOr(err, kErrTimeout);
+      return false;
+    }
+  }
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+      ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+// UMMA shared-memory descriptor, K-major, 128-byte swizzle: 8-row core groups 1024 B
+// apart (SBO), leading offset unused (1), descriptor version 1 (bits 46-47).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+// Instruction descriptor, kind::f16: D F32, A/B F16 (0) or BF16 (1), both K-major.
+__host__ __device__ constexpr uint32_t make_idesc(int ab_format, int M, int N) {
+  return (1u << 4) | ((uint32_t)ab_format << 7) | ((uint32_t)ab_format << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+#define TMEM_LD_32(taddr, r)                                                                                  \
+  asm volatile(                                                                                               \
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17," \
+      "%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"                                        \
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),       \
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), \
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),            \
+        "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),            \
+        "=r"(r[30]), "=r"(r[31])                                                                              \
+      : "r"(taddr))
+
+// Tile order: groups of up to 16 row tiles; inside a group the column tiles run in
+// the outer loop, so concurrently running CTAs share one steering block through L2.
+__device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int& mb, int& nb) {
+  const int G = 16;
+  int group = t / (G * tiles_n);
+  int gm0 = group * G;
+  int gsz = min(G, tiles_m - gm0);
+  int r = t - group * G * tiles_n;
+  nb = r / gsz;
+  mb = gm0 + r % gsz;
+}
+
+template <int BN>
+__global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant__ GemmArgs a, uint32_t idesc) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  constexpr uint32_t A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + STAGES * A_BYTES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sB + STAGES * B_BYTES);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + STAGES;
+  uint64_t* tfull = bars + 2 * STAGES;
+  uint64_t* tempty = bars + 2 * STAGES + 2;
+  uint64_t* done = bars + 2 * STAGES + 4;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 5);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n_tiles = a.tiles_m * a.tiles_n;
+  const int k_iters = a.n_phase * a.k_blocks;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) { mbar_init(smem_u32(&full[s]), 1); mbar_init(smem_u32(&empty[s]), 1); }
+    for (int s = 0; s < 2; ++s) { mbar_init(smem_u32(&tfull[s]), 1); mbar_init(smem_u32(&tempty[s]), 4); }
+    mbar_init(smem_u32(done), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(2 * BN) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------- TMA producer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      int issued = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+        int mb, nb;
+        tile_coords(t, a.tiles_m, a.tiles_n, mb, nb);
+        for (int it = 0; it < k_iters && ok; ++it) {
+          const int ph = it / a.k_blocks, kb = it % a.k_blocks;
+          const CUtensorMap* ma = ph == 2 ? &a.map_xl : &a.map_xh;
+          const CUtensorMap* mbm = ph == 1 ? &a.map_yl : &a.map_yh;
+          if (!mbar_wait(smem_u32(&empty[stage]), phase ^ 1, a.err)) { ok = false; break; }
+          mbar_expect_tx(smem_u32(&full[stage]), A_BYTES + B_BYTES);
+          tma_load_2d(smem_u32(sA + stage * A_BYTES), ma, kb * BK, mb * BM, smem_u32(&full[stage]));
+          tma_load_2d(smem_u32(sB + stage * B_BYTES), mbm, kb * BK, nb * BN, smem_u32(&full[stage]));
+          ++issued;
+          if (++stage == STAGES) { stage = 0; phase ^= 1; }
+        }
+      }
+      if (!ok) {
+        // wait (bounded) for copies still in flight before the CTA exits
+        for (int j = 0; j < STAGES && j < issued; ++j) {
+          if (--stage < 0) { stage = STAGES - 1; phase ^= 1; }
+          mbar_wait(smem_u32(&full[stage]), phase, a.err);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      int acc = 0;
+      uint32_t acc_phase = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+        if (!mbar_wait(smem_u32(&tempty[acc]), acc_phase ^ 1, a.err)) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN);
+        for (int it = 0; it < k_iters; ++it) {
+          if (!mbar_wait(smem_u32(&full[stage]), phase, a.err)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t a0 = smem_u32(sA + stage * A_BYTES), b0 = smem_u32(sB + stage * B_BYTES);
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk)
+            tc_mma(d_tmem, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32), idesc, (it | kk) != 0);
+          tc_commit(smem_u32(&empty[stage]));
+          if (++stage == STAGES) { stage = 0; phase ^= 1; }
+        }
+        if (!ok) break;
+        tc_commit(smem_u32(&tfull[acc]));
+        if (++acc == 2) { acc = 0; acc_phase ^= 1; }
+      }
+      // all issued MMAs complete before TMEM is released
+      tc_commit(smem_u32(done));
+      mbar_wait(smem_u32(done), 0, a.err);
+    }
+  } else {
+    // ------------------------------------------------------------- epilogue
+    const int q = warp & 3;  // TMEM lane quarter this warp may access
+    int acc = 0;
+    uint32_t acc_phase = 0;
+    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+      int mb, nb;
+      tile_coords(t, a.tiles_m, a.tiles_n, mb, nb);
+      if (!mbar_wait(smem_u32(&tfull[acc]), acc_phase, a.err)) break;
+      tc_fence_after();
+      const int row = mb * BM + q * 32 + lane;
+      const int p = row / a.nr_x, n = row % a.nr_x;
+      const bool vn = n < a.nr;
+      const bool elig = vn && n >= a.n_blank;
+      const float r = a.r_min + ((float)n + 0.5f) * a.dr;
+      const float scale = r * __expf(a.alpha2 * r) * a.y_gain_inv / a.gain[p];
+      float* env_p = a.env + (size_t)p * a.n_beams * a.nr;
+      unsigned long long* keys_p = a.peak_keys + (size_t)p * a.n_beams;
+      float pmax = 0.f;
+#pragma unroll 1
+      for (int c = 0; c < BN / 32; ++c) {
+        uint32_t v[32];
+        const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + c * 32);
+        TMEM_LD_32(taddr, v);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int beam = nb * (BN / 2) + c * 16 + j;
+          const float re = __uint_as_float(v[2 * j]), im = __uint_as_float(v[2 * j + 1]);
+          const float e = sqrtf(re * re + im * im) * scale;
+          const bool vb = beam < a.n_beams;
+          if (vn && vb) env_p[(size_t)beam * a.nr + n] = e;
+          unsigned long long key = (elig && vb)
+              ? (((unsigned long long)__float_as_uint(e) << 32) | (unsigned long long)(0xFFFFFFFFu - (uint32_t)n))
+              : 0ull;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            unsigned long long other = __shfl_xor_sync(0xffffffffu, key, o);
+            key = other > key ? other : key;
+          }
+          if (lane == 0 && key != 0ull) atomicMax(&keys_p[beam], key);
+          if (elig && vb) pmax = fmaxf(pmax, e);
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&tempty[acc]));
+      for (int o = 16; o > 0; o >>= 1) pmax = fmaxf(pmax, __shfl_xor_sync(0xffffffffu, pmax, o));
+      if (lane == 0) atomicMax(&a.ping_max[p], __float_as_uint(pmax));
+      if (++acc == 2) { acc = 0; acc_phase ^= 1; }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(2 * BN) : "memory");
+  }
+}
+
+template <int BN>
+constexpr size_t gemm_smem() {
+  return 1024 + (size_t)STAGES * (BM * BK * 2 + BN * BK * 2) + 256;
+}
+
+// ----------------------------------------------------------------- steering matrix
+// W[b][m] = w_m exp(-j k_a u_b . p_m) / sum w, beams cell-centred (Sec. III Eq. 2-3),
+// scaled by `gain`; phase in FP64 cycles reduced modulo one before the FP32 sincos.
+__global__ void k_steer(SteerArgs a) {
+  const int64_t rows = 2LL * a.nb_pad;
+  const int64_t total = rows * a.k_pad;
+  const int M = a.nx * a.ny, Nb = a.n_beam_az * a.n_beam_el;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = i / a.k_pad;
+    const int k = (int)(i % a.k_pad);
+    const int b = (int)(j / 2), part = (int)(j % 2);
+    const int m = k / 2, cpart = k % 2;
+    float val = 0.f;
+    if (b < Nb && m < M) {
+      const int bi = b % a.n_beam_az, bj = b / a.n_beam_az;
+      const double az = -a.hfov / 2 + (bi + 0.5) * a.hfov / a.n_beam_az;
+      const double el = -a.vfov / 2 + (bj + 0.5) * a.vfov / a.n_beam_el;
+      const double uy = cos(el) * sin(az), uz = sin(el);
+      const int mx = m % a.nx, my = m / a.nx;
+      const double cyc = a.pitch_over_lambda * ((mx - 0.5 * (a.nx - 1)) * uy + (my - 0.5 * (a.ny - 1)) * uz);
+      const double fr = cyc - floor(cyc);
+      float s, c;
+      sincospif((float)(2.0 * fr), &s, &c);
+      const double w = (a.taper ? (double)a.taper[m] : 1.0) / a.wsum * a.gain;
+      const float wr = (float)(w * c), wi = (float)(-w * s);  // W = w e^{-j phi}
+      if (part == 0) val = cpart == 0 ? wr : -wi;
+      else val = cpart == 0 ? wi : wr;
+    }
+    if (a.mode == SONAR_FP16) {
+      reinterpret_cast<__half*>(a.y_hi)[i] = __float2half_rn(val);
+    } else {
+      __nv_bfloat16 hi = __float2bfloat16_rn(val);
+      reinterpret_cast<__nv_bfloat16*>(a.y_hi)[i] = hi;
+      if (a.mode == SONAR_FP32)
+        reinterpret_cast<__nv_bfloat16*>(a.y_lo)[i] = __float2bfloat16_rn(val - __bfloat162float(hi));
+    }
+  }
+}
+
+// ----------------------------------------------------------------- peaks -> cloud
+// Per ping: decode each beam's packed (value, first index) maximum, apply the absolute
+// or ping-relative threshold, and write points in beam order.
+__global__ void __launch_bounds__(1024) k_peaks(PeakArgs a) {
+  __shared__ int s_scan[1024];
+  __shared__ long long s_base;
+  const int p = blockIdx.x, t = threadIdx.x;
+  const int Nb = a.n_beam_az * a.n_beam_el;
+  const float vmax = __uint_as_float(a.ping_max[p]);
+  const float thr = a.thr_mode == 1 ? a.thr * vmax : a.thr;
+  const DevPose& P = a.poses[p];
+  if (t == 0) s_base = 0;
+  __syncthreads();
+  for (int b0 = 0; b0 < Nb; b0 += 1024) {
+    const int b = b0 + t;
+    unsigned long long key = b < Nb ? a.peak_keys[(size_t)p * Nb + b] : 0ull;
+    const float val = __uint_as_float((uint32_t)(key >> 32));
+    const bool keep = key != 0ull && val >= thr;
+    s_scan[t] = keep ? 1 : 0;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+      int v = t >= off ? s_scan[t - off] : 0;
+      __syncthreads();
+      s_scan[t] += v;
+      __syncthreads();
+    }
+    const long long pos = s_base + s_scan[t] - (keep ? 1 : 0);
+    if (keep && pos < a.cap) {
+      const int n = (int)(0xFFFFFFFFu - (uint32_t)(key & 0xFFFFFFFFull));
+      const int bi = b % a.n_beam_az, bj = b / a.n_beam_az;
+      const double az = -a.hfov / 2 + (bi + 0.5) * a.hfov / a.n_beam_az;
+      const double el = -a.vfov / 2 + (bj + 0.5) * a.vfov / a.n_beam_el;
+      const double r = a.r_min + (n + 0.5) * a.dr;
+      const double v[3] = {r * cos(el) * cos(az), r * cos(el) * sin(az), r * sin(el)};
+      sonar_point pt;
+      pt.x = (float)(P.R[0] * v[0] + P.R[1] * v[1] + P.R[2] * v[2] + P.t[0]);
+      pt.y = (float)(P.R[3] * v[0] + P.R[4] * v[1] + P.R[5] * v[2] + P.t[1]);
+      pt.z = (float)(P.R[6] * v[0] + P.R[7] * v[1] + P.R[8] * v[2] + P.t[2]);
+      pt.intensity = val;
+      pt.beam = b;
+      pt.bin = n;
+      a.cloud[(size_t)p * a.cap + pos] = pt;
+    }
+    __syncthreads();
+    if (t == 1023) s_base += s_scan[1023];
+    __syncthreads();
+  }
+  if (t == 0) a.n_cloud[p] = s_base;
+}
+
+}  // namespace
+
+cudaError_t launch_steer(const SteerArgs& a, cudaStream_t st) {
+  k_steer<<<1024, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+// Dynamic shared-memory opt-in of the GEMM kernels (once per device, outside capture).
+cudaError_t prepare_gemm() {
+  cudaError_t e = cudaFuncSetAttribute(k_gemm<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem<256>());
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_gemm<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem<128>());
+}
+
+cudaError_t launch_gemm(const GemmArgs& a, int sm_count, cudaStream_t st) {
+  const int n_tiles = a.tiles_m * a.tiles_n;
+  const int grid = n_tiles < sm_count ? n_tiles : sm_count;
+  const uint32_t idesc_bf16_256 = make_idesc(1, BM, 256), idesc_f16_256 = make_idesc(0, BM, 256);
+  const uint32_t idesc_bf16_128 = make_idesc(1, BM, 128), idesc_f16_128 = make_idesc(0, BM, 128);
+  const bool is_f16 = a.f16 != 0;
+  const int tn = a.tile_n;
+  if (tn == 256) {
+    k_gemm<256><<<grid, kGemmThreads, gemm_smem<256>(), st>>>(a, is_f16 ? idesc_f16_256 : idesc_bf16_256);
+  } else {
+    k_gemm<128><<<grid, kGemmThreads, gemm_smem<128>(), st>>>(a, is_f16 ? idesc_f16_128 : idesc_bf16_128);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_peaks(const PeakArgs& a, cudaStream_t st) {
+  k_peaks<<<a.n_pings, 1024, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace sonar

@@ -1,0 +1,193 @@
+// Shared device-side definitions of the echo-formation library (sm_103a only).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sonar.h"
+
+#if defined(__CUDA_ARCH__) && (__CUDA_ARCH__ != 1030)
+#error "this library is written for sm_103a only"
+#endif
+
+namespace sonar {
+
+constexpr int kPad = 16;          // guard rows before/after each ping's samples in S
+constexpr int kRTab = 16384;      // intervals of the pulse-autocorrelation table
+constexpr double kEpsHit = 1e-7;  // minimum hit distance along a segment [m]
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kMaxStack = 64;     // BVH traversal stack depth
+
+// Device error word bits (reported as SONAR_E_TIMEOUT / SONAR_E_CAPACITY).
+constexpr int kErrTimeout = 1;
+constexpr int kErrStack = 2;
+constexpr int kErrCapacity = 4;
+constexpr int kErrLoop = 8;
+
+// One hit as consumed by echo synthesis (32 bytes).
+struct HitRec {
+  int32_t nglob;  // ping * nr_pad + n_first + kPad: global index of the first tap's sample
+  float u0;       // n_first - q: tap i samples R((u0 + i) * dt)
+  float cr, ci;   // complex coefficient c_k
+  float uy, uz;   // sonar-frame arrival direction
+  int32_t prim;   // triangle id, -1 for points
+  uint32_t key;   // route identity (see sonar_hit)
+};
+static_assert(sizeof(HitRec) == 32, "HitRec must be 32 bytes");
+
+// Binary BVH node holding both children's boxes (64 bytes).
+// a = (L.lo.x, L.hi.x, L.lo.y, L.hi.y), b = (R.lo.x, R.hi.x, R.lo.y, R.hi.y),
+// c = (L.lo.z, L.hi.z, R.lo.z, R.hi.z), d = (left, right, -, -); a child >= 0 is an
+// internal node, a child < 0 is the leaf ~child (one triangle in leaf order).
+struct BvhNode {
+  float4 a, b, c;
+  int4 d;
+};
+
+struct DevScene {
+  const float4* tri32;     // [n_tris][3]: v0, e1, e2 (leaf order), FP32 filter
+  const float* triv;       // [n_tris][9]: original vertices a, b, c (leaf order), FP64 test
+  const int32_t* tri_prim; // leaf -> original triangle id
+  const float* tri_mu;     // leaf order
+  const uint8_t* tri_flags;// leaf order
+  const BvhNode* nodes;
+  int32_t n_tris;
+  int32_t root;            // internal node index, or ~leaf for a one-triangle scene
+  const float4* points;    // x, y, z, sigma
+  int32_t n_points;
+  const double4* planes;   // unit normal, offset
+  int32_t n_planes;
+};
+
+// Per-ping pose on the device: sonar -> world rotation (row-major) and position.
+struct DevPose {
+  double R[9];
+  double t[3];
+};
+
+// Everything the trace kernels need, passed by value.
+struct TraceArgs {
+  DevScene sc;
+  const DevPose* poses;
+  const double* ray_dirs;   // [n_subrays][3] sonar-frame sub-ray directions
+  const float* row_domega;  // [n_ray_el] sub-ray solid angle per elevation row
+  int32_t n_pings, n_ray_az, n_ray_el, n_sub, n_subrays;
+  int32_t max_bounces, has_surface, curved;
+  double surface_z, r_surface, r_seabed, alpha;
+  uint32_t seed32;
+  double ssp_z0, ssp_c0, ssp_g;  // c(z) = c0 + g (z - z0)
+  double T_stop;                 // one-way time limit
+  double t0, inv_dt, hw, f0;     // sample-grid mapping of delays
+  int32_t nr_pad;
+  int32_t n_routes;              // point-scatterer routes per point
+  HitRec* hits;
+  double* dbg_tau;               // nullable: FP64 delay per hit
+  unsigned long long* n_hits;    // device counter
+  int64_t hit_cap;
+  int* err;
+};
+
+// ------------------------------------------------------------------ small helpers
+__host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// pcg4d (Jarzynski & Olano, JCGT 2020), 32-bit.
+__host__ __device__ inline void pcg4d(uint32_t& x, uint32_t& y, uint32_t& z, uint32_t& w) {
+  x = x * 1664525u + 1013904223u;
+  y = y * 1664525u + 1013904223u;
+  z = z * 1664525u + 1013904223u;
+  w = w * 1664525u + 1013904223u;
+  x += y * w; y += z * x; z += x * y; w += y * z;
+  x ^= x >> 16; y ^= y >> 16; z ^= z >> 16; w ^= w >> 16;
+  x += y * w; y += z * x; z += x * y; w += y * z;
+}
+
+__host__ __device__ inline double u24(uint32_t h) { return (double)(h >> 8) * (1.0 / 16777216.0); }
+
+}  // namespace sonar
+
+// Host-side launchers implemented in the .cu files.
+namespace sonar {
+struct BvhBuild;
+cudaError_t build_bvh(const float* d_verts, const int32_t* d_tris, const float* d_mu,
+                      const uint8_t* d_flags, int32_t n_tris, float4** tri32, float** triv,
+                      int32_t** tri_prim, float** tri_mu, uint8_t** tri_flags, BvhNode** nodes,
+                      int32_t* root, cudaStream_t st);
+cudaError_t launch_ray_table(double* dirs, float* row_domega, int32_t n_ray_az, int32_t n_ray_el,
+                             int32_t n_sub, double hfov, double vfov, uint32_t seed32,
+                             cudaStream_t st);
+cudaError_t launch_poses(const double* raw, DevPose* poses, int32_t n, cudaStream_t st);
+cudaError_t launch_trace(const TraceArgs& a, int sm_count, cudaStream_t st);
+cudaError_t launch_points(const TraceArgs& a, cudaStream_t st);
+
+struct SynthArgs {
+  const HitRec* hits_sorted;
+  const int32_t* n_valid;   // hits with at least one tap in range (binning total)
+  const float2* rtab;       // [kRTab + 1]
+  float rtab_scale;         // table index per unit of (u0 + i)
+  int32_t taps;             // W
+  int32_t nx, ny;
+  float pitch_over_lambda;  // element pitch in carrier wavelengths (at c_ref)
+  float2* S;                // [n_pings * nr_pad][M] element echoes
+  int64_t total_rows;       // n_pings * nr_pad
+  int* err;
+};
+cudaError_t launch_bin(const HitRec* hits, const unsigned long long* n_hits, int32_t n_bins,
+                       int32_t* counts, int32_t* offsets, HitRec* sorted, int sm_count,
+                       cudaStream_t st);
+cudaError_t launch_synth(const SynthArgs& a, int sm_count, cudaStream_t st);
+cudaError_t launch_rtab(float2* rtab, double pulse, double bw, double dt, cudaStream_t st);
+
+struct ConvertArgs {
+  const float2* S;          // [n_pings][nr_pad][M]
+  int32_t n_pings, nr, nr_pad, nr_x, M, k_pad;
+  int32_t mode;             // SONAR_FP32 / BF16 / FP16
+  float* gain;              // [n_pings] power-of-two gain applied (FP16), else 1
+  void* x_hi;               // [n_pings * nr_x][k_pad] 16-bit
+  void* x_lo;               // FP32 form only
+};
+cudaError_t launch_convert(const ConvertArgs& a, int sm_count, cudaStream_t st);
+
+struct SteerArgs {
+  int32_t nx, ny, n_beam_az, n_beam_el, nb_pad, k_pad;
+  double hfov, vfov, pitch_over_lambda;
+  const float* taper;       // device [M] or null
+  double wsum, gain;
+  int32_t mode;
+  void* y_hi;               // [nb_pad*2][k_pad]
+  void* y_lo;
+};
+cudaError_t launch_steer(const SteerArgs& a, cudaStream_t st);
+
+struct GemmArgs {
+  CUtensorMap map_xh, map_xl, map_yh, map_yl;
+  int32_t tiles_m, tiles_n, k_blocks, n_phase, tile_n;
+  int32_t f16;               // operands FP16 (1) or BF16 (0)
+  int32_t nr, nr_x, n_beams, n_blank;
+  float r_min, dr, alpha2;   // TVG(r) = r exp(alpha2 r)
+  const float* gain;         // [n_pings]: element-echo gain
+  float y_gain_inv;
+  float* env;                // [n_pings][Nb][Nr]
+  unsigned long long* peak_keys;  // [n_pings][Nb]
+  unsigned int* ping_max;    // [n_pings] float bits
+  int* err;
+};
+cudaError_t prepare_gemm();
+cudaError_t launch_gemm(const GemmArgs& a, int sm_count, cudaStream_t st);
+
+struct PeakArgs {
+  const unsigned long long* peak_keys;
+  const unsigned int* ping_max;
+  const DevPose* poses;
+  int32_t n_pings, n_beam_az, n_beam_el, nr;
+  double hfov, vfov, r_min, dr;
+  int32_t thr_mode;
+  float thr;
+  sonar_point* cloud;       // [n_pings][cap]
+  int64_t cap;
+  long long* n_cloud;       // [n_pings]
+};
+cudaError_t launch_peaks(const PeakArgs& a, cudaStream_t st);
+}  // namespace sonar

@@ -1,0 +1,318 @@
+// Delay binning and element-echo synthesis (Sec. II.B: complex baseband accumulated per
+// element with the phase set by the delay; echoes are formed already pulse-compressed,
+// i.e. each hit contributes c_k R(t_n - tau_k) to the samples inside its pulse window).
+//
+// Binning is a counting sort of hits by the global index of their first tap. The
+// synthesis runs persistent CTAs over equal chunks of the sorted hit list; a thread
+// owns four elements and keeps a sliding window of `taps` samples in registers, so the
+// inner loop is 4 FMAs per (hit, element, tap). Finished samples are flushed with
+// vector atomics into S [rows][M] (FP32 complex), rows padded per ping.
+#include "common.cuh"
+
+namespace sonar {
+namespace {
+
+__global__ void k_hist(const HitRec* hits, const unsigned long long* n_hits, int32_t n_bins, int32_t* counts) {
+  int64_t n = (int64_t)*n_hits;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    int g = hits[i].nglob;
+    if (g >= 0 && g < n_bins) atomicAdd(&counts[g], 1);
+  }
+}
+
+// Exclusive scan of counts (single CTA of 1024 threads); offsets[n_bins] = total.
+__global__ void __launch_bounds__(1024) k_scan(const int32_t* counts, int32_t n_bins, int32_t* offsets, int32_t* cursor) {
+  __shared__ int32_t part[1024];
+  const int t = threadIdx.x;
+  const int per = (n_bins + 1023) / 1024;
+  const int b0 = t * per, b1 = min(b0 + per, n_bins);
+  int32_t s = 0;
+  for (int b = b0; b < b1; ++b) s += counts[b];
+  part[t] = s;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {
+    int32_t v = t >= off ? part[t - off] : 0;
+    __syncthreads();
+    part[t] += v;
+    __syncthreads();
+  }
+  int32_t run = part[t] - s;
+  for (int b = b0; b < b1; ++b) {
+    const int32_t cnt = counts[b];  // counts and cursor may alias
+    offsets[b] = run;
+    cursor[b] = run;
+    run += cnt;
+  }
+  if (t == 1023) offsets[n_bins] = part[1023];
+}
+
+__global__ void k_scatter(const HitRec* hits, const unsigned long long* n_hits, int32_t n_bins, int32_t* cursor,
+                          HitRec* sorted) {
+  int64_t n = (int64_t)*n_hits;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    HitRec h = hits[i];
+    if (h.nglob >= 0 && h.nglob < n_bins) sorted[atomicAdd(&cursor[h.nglob], 1)] = h;
+  }
+}
+
+constexpr int kSub = 32;        // hits staged per round
+constexpr int kThreads = 256;   // 4 elements per thread -> 1024 elements per CTA
+constexpr int kMaxAxis = 64;    // nx, ny <= 64
+
+__device__ __forceinline__ void red_add4(float* dst, float a, float b, float c, float d) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst), "f"(a), "f"(b), "f"(c), "f"(d) : "memory");
+}
+
+template <int WT>
+__global__ void __launch_bounds__(kThreads, 1) k_synth(SynthArgs a, const int32_t* total_ptr) {
+  __shared__ int s_n[kSub];
+  __shared__ float2 s_g[kSub][WT];
+  __shared__ float2 s_ey[kSub][kMaxAxis];
+  __shared__ float2 s_ez[kSub][kMaxAxis];
+
+  const int nx = a.nx, ny = a.ny, M = nx * ny;
+  const int64_t H = *total_ptr;
+  const int n_eb = (M + 4 * kThreads - 1) / (4 * kThreads);
+  // equal chunks, about four work items per resident CTA
+  int64_t target = (int64_t)gridDim.x * 4;
+  int64_t chunk = ((H * n_eb + target - 1) / target + kSub - 1) / kSub * kSub;
+  if (chunk < kSub) chunk = kSub;
+  if (chunk > 8192) chunk = 8192;
+  const int64_t n_chunks = (H + chunk - 1) / chunk;
+  const int64_t n_items = n_chunks * n_eb;
+  const int tid = threadIdx.x;
+
+  for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+    const int64_t c = item / n_eb;
+    const int eb = (int)(item % n_eb);
+    const int m0 = eb * 4 * kThreads + 4 * tid;
+    const bool active = m0 < M;
+    const int mx0 = active ? m0 % nx : 0, my = active ? m0 / nx : 0;
+    const int64_t h0 = c * chunk, h1 = min(h0 + chunk, H);
+    float2 acc[WT][4];
+#pragma unroll
+    for (int i = 0; i < WT; ++i)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[i][e] = make_float2(0.f, 0.f);
+    int base = -1;
+    float2* S = a.S;
+
+    auto flush_row = [&](int row) {
+      if (active) {
+        float* dst = reinterpret_cast<float*>(S + (int64_t)row * M + m0);
+        red_add4(dst, acc[0][0].x, acc[0][0].y, acc[0][1].x, acc[0][1].y);
+        red_add4(dst + 4, acc[0][2].x, acc[0][2].y, acc[0][3].x, acc[0][3].y);
+      }
+    };
+
+    for (int64_t s0 = h0; s0 < h1; s0 += kSub) {
+      const int nsub = (int)(h1 - s0 < kSub ? h1 - s0 : kSub);
+      __syncthreads();
+      // stage taps c_k R((u0 + i) dt) and the separable element phasors of each hit
+      const int per_hit = WT + nx + ny;
+      for (int idx = tid; idx < nsub * per_hit; idx += kThreads) {
+        const int k = idx / per_hit, j = idx % per_hit;
+        const HitRec& h = a.hits_sorted[s0 + k];
+        if (j == 0) s_n[k] = h.nglob;
+        if (j < WT) {
+          float2 g = make_float2(0.f, 0.f);
+          if (j < a.taps) {
+            float x = (h.u0 + (float)j) * a.rtab_scale + (float)(kRTab / 2);
+            if (x >= 0.f && x < (float)kRTab) {
+              int i0 = (int)x;
+              float f = x - (float)i0;
+              float2 r0 = __ldg(&a.rtab[i0]), r1 = __ldg(&a.rtab[i0 + 1]);
+              float rr = r0.x + f * (r1.x - r0.x), ri = r0.y + f * (r1.y - r0.y);
+              g = make_float2(h.cr * rr - h.ci * ri, h.cr * ri + h.ci * rr);
+            }
+          }
+          s_g[k][j] = g;
+        } else if (j < WT + nx) {
+          const int q = j - WT;
+          float s, cc;
+          sincospif(2.0f * a.pitch_over_lambda * ((float)q - 0.5f * (float)(nx - 1)) * h.uy, &s, &cc);
+          s_ey[k][q] = make_float2(cc, s);
+        } else {
+          const int q = j - WT - nx;
+          float s, cc;
+          sincospif(2.0f * a.pitch_over_lambda * ((float)q - 0.5f * (float)(ny - 1)) * h.uz, &s, &cc);
+          s_ez[k][q] = make_float2(cc, s);
+        }
+      }
+      __syncthreads();
+      for (int k = 0; k < nsub; ++k) {
+        const int g = s_n[k];
+        if (base < 0) base = g;
+        if (g - base >= WT) {
+#pragma unroll
+          for (int i = 0; i < WT; ++i) {
+            flush_row(base);
+#pragma unroll
+            for (int r = 0; r < WT - 1; ++r)
+#pragma unroll
+              for (int e = 0; e < 4; ++e) acc[r][e] = acc[r + 1][e];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[WT - 1][e] = make_float2(0.f, 0.f);
+            ++base;
+          }
+          base = g;
+        }
+        while (base < g) {
+          flush_row(base);
+#pragma unroll
+          for (int r = 0; r < WT - 1; ++r)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[r][e] = acc[r + 1][e];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) acc[WT - 1][e] = make_float2(0.f, 0.f);
+          ++base;
+        }
+        const float2 ez = s_ez[k][my];
+        float2 E[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float2 ey = s_ey[k][mx0 + e];
+          E[e] = make_float2(ey.x * ez.x - ey.y * ez.y, ey.x * ez.y + ey.y * ez.x);
+        }
+#pragma unroll
+        for (int i = 0; i < WT; ++i) {
+          const float2 gi = s_g[k][i];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            acc[i][e].x = fmaf(gi.x, E[e].x, fmaf(-gi.y, E[e].y, acc[i][e].x));
+            acc[i][e].y = fmaf(gi.x, E[e].y, fmaf(gi.y, E[e].x, acc[i][e].y));
+          }
+        }
+      }
+    }
+    if (base >= 0) {
+#pragma unroll
+      for (int i = 0; i < WT; ++i) {
+        flush_row(base);
+#pragma unroll
+        for (int r = 0; r < WT - 1; ++r)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) acc[r][e] = acc[r + 1][e];
+        ++base;
+      }
+    }
+  }
+}
+
+// Pulse autocorrelation table R(u), u in [-T_p, T_p], kRTab intervals, evaluated in
+// FP64 from the closed form: the Hann window as three complex exponentials turns
+// R(u) into nine exponential integrals over the overlap of the two pulse supports.
+__device__ inline double sinc_d(double x) { return fabs(x) < 1e-4 ? 1.0 - x * x / 6.0 : sin(x) / x; }
+__global__ void k_rtab(float2* tab, double T, double B) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > kRTab) return;
+  double u = -T + 2.0 * T * (double)i / (double)kRTab;
+  if (!(fabs(u) < T)) { tab[i] = make_float2(0.f, 0.f); return; }
+  const double kappa = B / T, Om = 2.0 * kPi / T, E = 3.0 * T / 8.0;
+  const double L = fmax(-T / 2, -T / 2 - u), U = fmin(T / 2, T / 2 - u);
+  double sr = 0.0, si = 0.0;
+  for (int aa = -1; aa <= 1; ++aa) {
+    for (int bb = -1; bb <= 1; ++bb) {
+      double ca = aa == 0 ? 0.5 : 0.25, cb = bb == 0 ? 0.5 : 0.25;
+      double beta = (aa + bb) * Om + 2.0 * kPi * kappa * u;
+      double mag = (U - L) * sinc_d(beta * (U - L) / 2);
+      double ph = beta * (U + L) / 2 + aa * Om * u;
+      sr += ca * cb * mag * cos(ph);
+      si += ca * cb * mag * sin(ph);
+    }
+  }
+  double ph0 = kPi * kappa * u * u;
+  double c0 = cos(ph0), s0 = sin(ph0);
+  tab[i] = make_float2((float)((c0 * sr - s0 * si) / E), (float)((c0 * si + s0 * sr) / E));
+}
+
+// S (FP32, padded rows) -> 16-bit GEMM operand X [n_pings * nr_x][k_pad], interleaved
+// (re, im) per element; FP32 form also writes the residual lo = x - hi.
+__global__ void k_absmax(const float2* S, int32_t nr, int32_t nr_pad, int32_t M, float* gain) {
+  int p = blockIdx.y;
+  float mx = 0.f;
+  int64_t n = (int64_t)nr * M;
+  const float2* base = S + ((int64_t)p * nr_pad + kPad) * M;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    float2 v = base[i];
+    mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<int*>(gain + p), __float_as_int(mx));
+}
+
+__global__ void k_convert(ConvertArgs a) {
+  const int64_t rows = (int64_t)a.n_pings * a.nr;
+  const int M = a.M;
+  const int64_t total = rows * M;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / M;
+    const int m = (int)(i % M);
+    const int p = (int)(r / a.nr), n = (int)(r % a.nr);
+    float2 v = a.S[((int64_t)p * a.nr_pad + kPad + n) * M + m];
+    const int64_t dst = ((int64_t)p * a.nr_x + n) * a.k_pad + 2 * m;
+    if (a.mode == SONAR_FP16) {
+      float gn = a.gain[p];
+      __half2 h = __floats2half2_rn(v.x * gn, v.y * gn);
+      *reinterpret_cast<__half2*>(reinterpret_cast<__half*>(a.x_hi) + dst) = h;
+    } else {
+      __nv_bfloat162 hi = __floats2bfloat162_rn(v.x, v.y);
+      *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(a.x_hi) + dst) = hi;
+      if (a.mode == SONAR_FP32) {
+        float2 hf = __bfloat1622float2(hi);
+        __nv_bfloat162 lo = __floats2bfloat162_rn(v.x - hf.x, v.y - hf.y);
+        *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(a.x_lo) + dst) = lo;
+      }
+    }
+  }
+}
+
+// Power-of-two gain so that the largest |component| lands near 2^14 in FP16.
+__global__ void k_gain_pow2(float* gain, int n, int mode) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  if (mode != SONAR_FP16) { gain[p] = 1.0f; return; }
+  float mx = gain[p];
+  int e = 0;
+  if (mx > 0.f) frexpf(mx, &e);
+  gain[p] = ldexpf(1.0f, 14 - e);
+}
+
+}  // namespace
+
+cudaError_t launch_bin(const HitRec* hits, const unsigned long long* n_hits, int32_t n_bins, int32_t* counts,
+                       int32_t* offsets, HitRec* sorted, int sm_count, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(int32_t) * n_bins, st);
+  if (e != cudaSuccess) return e;
+  k_hist<<<sm_count * 8, 256, 0, st>>>(hits, n_hits, n_bins, counts);
+  k_scan<<<1, 1024, 0, st>>>(counts, n_bins, offsets, counts);
+  // counts now doubles as the scatter cursor
+  k_scatter<<<sm_count * 8, 256, 0, st>>>(hits, n_hits, n_bins, counts, sorted);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_synth(const SynthArgs& a, int sm_count, cudaStream_t st) {
+  const int32_t* total = a.n_valid;  // offsets[n_bins] of the binning step
+  if (a.taps <= 8) k_synth<8><<<sm_count, kThreads, 0, st>>>(a, total);
+  else if (a.taps <= 12) k_synth<12><<<sm_count, kThreads, 0, st>>>(a, total);
+  else k_synth<16><<<sm_count, kThreads, 0, st>>>(a, total);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rtab(float2* rtab, double pulse, double bw, double, cudaStream_t st) {
+  k_rtab<<<(kRTab + 1 + 255) / 256, 256, 0, st>>>(rtab, pulse, bw);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert(const ConvertArgs& a, int sm_count, cudaStream_t st) {
+  if (a.mode == SONAR_FP16) {
+    cudaError_t e = cudaMemsetAsync(a.gain, 0, sizeof(float) * a.n_pings, st);
+    if (e != cudaSuccess) return e;
+    k_absmax<<<dim3(sm_count, a.n_pings), 256, 0, st>>>(a.S, a.nr, a.nr_pad, a.M, a.gain);
+  }
+  k_gain_pow2<<<(a.n_pings + 63) / 64, 64, 0, st>>>(a.gain, a.n_pings, a.mode);
+  k_convert<<<sm_count * 8, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace sonar

@@ -1,0 +1,607 @@
+// Ray casting along multipath routes and per-hit backscatter (Sec. II.A-II.B).
+//
+// One thread traces one sub-ray of one ping through the whole route: closest hit by
+// BVH traversal, optional specular continuation off mirror triangles and the sea
+// surface (limited secondary reflections, maximum depth max_bounces), and, for every
+// scattering hit, the FP64 two-way delay, the carrier phase reduced modulo one cycle,
+// the Lambertian amplitude and the hashed speckle phase. Rays bend in a linear
+// sound-speed profile as exact circular arcs intersected chord by chord.
+//
+// Precision: the traversal culls in FP32 with widened boxes and a slack barycentric
+// test; every triangle that survives the slack test is decided by an FP64 ray/triangle
+// test written with explicitly rounded operations (no contraction), so the chosen
+// primitive and its distance are those of an FP64 evaluation of the same test.
+#include "common.cuh"
+
+namespace sonar {
+namespace {
+
+// ----------------------------------------------------------------- FP64, no contraction
+__device__ __forceinline__ double dm(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double da(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double ds(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double dd(double a, double b) { return __ddiv_rn(a, b); }
+
+struct D3 { double x, y, z; };
+__device__ __forceinline__ D3 d3(double x, double y, double z) { D3 r = {x, y, z}; return r; }
+__device__ __forceinline__ D3 sub(D3 a, D3 b) { return d3(ds(a.x, b.x), ds(a.y, b.y), ds(a.z, b.z)); }
+__device__ __forceinline__ double dot(D3 a, D3 b) { return da(da(dm(a.x, b.x), dm(a.y, b.y)), dm(a.z, b.z)); }
+__device__ __forceinline__ D3 cross(D3 a, D3 b) {
+  return d3(ds(dm(a.y, b.z), dm(a.z, b.y)), ds(dm(a.z, b.x), dm(a.x, b.z)), ds(dm(a.x, b.y), dm(a.y, b.x)));
+}
+__device__ __forceinline__ D3 axpy(D3 p, double t, D3 d) {  // p + t d, as p[k] += t * d[k]
+  return d3(da(p.x, dm(t, d.x)), da(p.y, dm(t, d.y)), da(p.z, dm(t, d.z)));
+}
+__device__ __forceinline__ D3 rot(const double* R, D3 v) {
+  return d3(da(da(dm(R[0], v.x), dm(R[1], v.y)), dm(R[2], v.z)),
+            da(da(dm(R[3], v.x), dm(R[4], v.y)), dm(R[5], v.z)),
+            da(da(dm(R[6], v.x), dm(R[7], v.y)), dm(R[8], v.z)));
+}
+__device__ __forceinline__ D3 rot_t(const double* R, D3 v) {
+  return d3(da(da(dm(R[0], v.x), dm(R[3], v.y)), dm(R[6], v.z)),
+            da(da(dm(R[1], v.x), dm(R[4], v.y)), dm(R[7], v.z)),
+            da(da(dm(R[2], v.x), dm(R[5], v.y)), dm(R[8], v.z)));
+}
+
+__device__ __forceinline__ D3 tri_vert(const float* v, int k) {
+  return d3((double)v[3 * k], (double)v[3 * k + 1], (double)v[3 * k + 2]);
+}
+
+// FP64 two-sided ray/triangle test (Moller-Trumbore), inclusive edges.
+__device__ bool tri_test64(const float* tv, D3 o, D3 d, double& t) {
+  D3 a = tri_vert(tv, 0), b = tri_vert(tv, 1), c = tri_vert(tv, 2);
+  D3 e1 = sub(b, a), e2 = sub(c, a);
+  D3 p = cross(d, e2);
+  double det = dot(e1, p);
+  if (det == 0.0) return false;
+  D3 s = sub(o, a);
+  double u = dd(dot(s, p), det);
+  if (!(u >= 0.0 && u <= 1.0)) return false;
+  D3 q = cross(s, e1);
+  double v = dd(dot(d, q), det);
+  if (!(v >= 0.0 && da(u, v) <= 1.0)) return false;
+  t = dd(dot(e2, q), det);
+  return true;
+}
+
+__device__ D3 tri_normal64(const float* tv) {
+  D3 a = tri_vert(tv, 0), b = tri_vert(tv, 1), c = tri_vert(tv, 2);
+  D3 n = cross(sub(b, a), sub(c, a));
+  double l = __dsqrt_rn(dot(n, n));
+  return d3(dd(n.x, l), dd(n.y, l), dd(n.z, l));
+}
+
+// ----------------------------------------------------------------- traversal
+struct Ray32 {
+  float ox, oy, oz, ix, iy, iz, dx, dy, dz;
+};
+
+__device__ __forceinline__ void slab(float lox, float hix, float loy, float hiy, float loz, float hiz,
+                                     const Ray32& r, float tlo, float thi, float& tn, float& tf) {
+  float x0 = (lox - r.ox) * r.ix, x1 = (hix - r.ox) * r.ix;
+  float y0 = (loy - r.oy) * r.iy, y1 = (hiy - r.oy) * r.iy;
+  float z0 = (loz - r.oz) * r.iz, z1 = (hiz - r.oz) * r.iz;
+  tn = fmaxf(fmaxf(fminf(x0, x1), fminf(y0, y1)), fmaxf(fminf(z0, z1), tlo));
+  tf = fminf(fminf(fmaxf(x0, x1), fmaxf(y0, y1)), fminf(fmaxf(z0, z1), thi));
+}
+
+struct Hit {
+  double t;
+  int prim;  // original id, -1 none
+  int leaf;
+};
+
+// Nearest triangle with FP64 distance in (kEpsHit, tmax], excluding `exclude`
+// (original id), ties to the lowest id.
+__device__ Hit closest_hit(const DevScene& sc, D3 o, D3 d, double tmin, double tmax, int exclude, int* err) {
+  Hit best = {INFINITY, -1, -1};
+  if (sc.n_tris == 0) return best;
+  Ray32 r;
+  r.ox = (float)o.x; r.oy = (float)o.y; r.oz = (float)o.z;
+  r.dx = (float)d.x; r.dy = (float)d.y; r.dz = (float)d.z;
+  r.ix = 1.0f / r.dx; r.iy = 1.0f / r.dy; r.iz = 1.0f / r.dz;
+  const float tmax_f = (float)tmax * (1.0f + 1e-6f) + 1e-4f;
+  float tcull = tmax_f;
+  int stack[kMaxStack];
+  int sp = 0;
+  int node = sc.root;
+  const int max_visits = 2 * sc.n_tris + 64;  // a tree visits each node at most once
+  for (int visits = 0;; ++visits) {
+    if (visits > max_visits) { atomicOr(err, kErrLoop); return best; }
+    const BvhNode* nd = sc.nodes + node;
+    float4 A = __ldg(&nd->a), B = __ldg(&nd->b), Cz = __ldg(&nd->c);
+    int4 ch = __ldg(&nd->d);
+    float ln, lf, rn, rf;
+    slab(A.x, A.y, A.z, A.w, Cz.x, Cz.y, r, -1e-4f, tcull, ln, lf);
+    slab(B.x, B.y, B.z, B.w, Cz.z, Cz.w, r, -1e-4f, tcull, rn, rf);
+    bool hl = ln <= lf, hr = rn <= rf;
+    int kids[2] = {ch.x, ch.y};
+    bool hit2[2] = {hl, hr};
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      if (!hit2[c] || kids[c] >= 0) continue;
+      hit2[c] = false;
+      int leaf = ~kids[c];
+      // FP32 slack filter
+      float4 v0 = __ldg(&sc.tri32[3 * leaf]), e1 = __ldg(&sc.tri32[3 * leaf + 1]), e2 = __ldg(&sc.tri32[3 * leaf + 2]);
+      float px = r.dy * e2.z - r.dz * e2.y, py = r.dz * e2.x - r.dx * e2.z, pz = r.dx * e2.y - r.dy * e2.x;
+      float det = e1.x * px + e1.y * py + e1.z * pz;
+      float n1 = e1.x * e1.x + e1.y * e1.y + e1.z * e1.z, n2 = e2.x * e2.x + e2.y * e2.y + e2.z * e2.z;
+      bool pass;
+      if (det * det <= 1e-12f * n1 * n2) {
+        pass = true;  // nearly parallel: let FP64 decide
+      } else {
+        float inv = 1.0f / det;
+        float sx = r.ox - v0.x, sy = r.oy - v0.y, sz = r.oz - v0.z;
+        float u = (sx * px + sy * py + sz * pz) * inv;
+        float qx = sy * e1.z - sz * e1.y, qy = sz * e1.x - sx * e1.z, qz = sx * e1.y - sy * e1.x;
+        float v = (r.dx * qx + r.dy * qy + r.dz * qz) * inv;
+        float t = (e2.x * qx + e2.y * qy + e2.z * qz) * inv;
+        float eps = 1e-3f + 1e-5f * sqrtf(n1 * n2 / (det * det)) * (1.0f + fabsf(t));
+        pass = u >= -eps && v >= -eps && u + v <= 1.0f + eps && t <= tcull && t >= -1e-3f;
+      }
+      if (!pass) continue;
+      int prim = __ldg(&sc.tri_prim[leaf]);
+      if (prim == exclude) continue;
+      double t64;
+      if (tri_test64(sc.triv + 9 * leaf, o, d, t64) && t64 > tmin && t64 <= tmax) {
+        if (t64 < best.t || (t64 == best.t && prim < best.prim)) {
+          best.t = t64;
+          best.prim = prim;
+          best.leaf = leaf;
+          tcull = fminf(tcull, (float)t64 * (1.0f + 1e-6f) + 1e-4f);
+        }
+      }
+    }
+    hl = hit2[0];
+    hr = hit2[1];
+    if (hl && hr) {
+      int nearc = ln <= rn ? ch.x : ch.y, farc = ln <= rn ? ch.y : ch.x;
+      if (sp >= kMaxStack) { atomicOr(err, kErrStack); return best; }
+      stack[sp++] = farc;
+      node = nearc;
+    } else if (hl) {
+      node = ch.x;
+    } else if (hr) {
+      node = ch.y;
+    } else {
+      if (sp == 0) break;
+      node = stack[--sp];
+    }
+  }
+  return best;
+}
+
+// ----------------------------------------------------------------- hit emission
+__device__ __forceinline__ unsigned long long warp_reserve(unsigned long long* counter) {
+  unsigned mask = __activemask();
+  int lane = threadIdx.x & 31;
+  int leader = __ffs(mask) - 1;
+  unsigned rank = __popc(mask & ((1u << lane) - 1u));
+  unsigned long long base = 0;
+  if (lane == leader) base = atomicAdd(counter, (unsigned long long)__popc(mask));
+  base = __shfl_sync(mask, base, leader);
+  return base + rank;
+}
+
+__device__ __forceinline__ double wrap_pi(double a) {
+  return ds(a, dm(2.0 * kPi, floor(dd(da(a, kPi), 2.0 * kPi))));
+}
+
+// tau: FP64 two-way delay; amp: |c_k|; psi: speckle; u: sonar-frame arrival direction.
+__device__ void emit(const TraceArgs& A, int ping, double tau, double amp, double psi, D3 u, int prim, uint32_t key) {
+  unsigned long long slot = warp_reserve(A.n_hits);
+  if ((int64_t)slot >= A.hit_cap) { atomicOr(A.err, kErrCapacity); return; }
+  // carrier phase reduced modulo one cycle in FP64 before forming the phasor
+  double fc = dm(A.f0, tau);
+  double phi = wrap_pi(ds(psi, dm(2.0 * kPi, ds(fc, floor(fc)))));
+  double q = dm(ds(tau, A.t0), A.inv_dt);
+  double nf = floor(ds(q, A.hw)) + 1.0;
+  HitRec h;
+  // a hit whose first tap lies outside this ping's padded rows has no tap in range
+  const bool in_rows = nf + kPad >= 0.0 && nf + kPad < (double)A.nr_pad;
+  h.nglob = in_rows ? ping * A.nr_pad + (int)nf + kPad : -1;
+  h.u0 = (float)(nf - q);
+  float s, c;
+  sincosf((float)phi, &s, &c);
+  h.cr = (float)amp * c;
+  h.ci = (float)amp * s;
+  h.uy = (float)u.y;
+  h.uz = (float)u.z;
+  h.prim = prim;
+  h.key = key;
+  A.hits[slot] = h;
+  if (A.dbg_tau) A.dbg_tau[slot] = tau;
+}
+
+__device__ __forceinline__ double speckle(const TraceArgs& A, uint32_t ray, uint32_t sub, uint32_t bounce) {
+  uint32_t x = ray, y = sub, z = 1u + bounce, w = A.seed32;
+  pcg4d(x, y, z, w);
+  return dm(2.0 * kPi, u24(x));
+}
+
+// Lambertian amplitude Gamma^2 sqrt(mu cos(k) dOmega) / L exp(-2 alpha L).
+__device__ __forceinline__ double lambert(const TraceArgs& A, double gam, double mu, double kinc, double dOmega, double L) {
+  return gam * gam * sqrt(mu * kinc * dOmega) / L * exp(-2.0 * A.alpha * L);
+}
+
+// ----------------------------------------------------------------- curved rays
+__device__ __forceinline__ double sincd(double x) { return fabs(x) < 1e-4 ? 1.0 - x * x / 6.0 : sin(x) / x; }
+
+struct Arc {
+  double dh, dz, theta, dt;
+};
+__device__ Arc arc_advance(const TraceArgs& A, double z, double theta, double xi, double step) {
+  Arc r;
+  double g = A.ssp_g;
+  double delta = xi * g * step;
+  double thm = theta - delta / 2;
+  double sc = sincd(delta / 2);
+  double cm = cos(thm);
+  r.dh = step * cm * sc;
+  r.dz = step * sin(thm) * sc;
+  r.theta = theta - delta;
+  if (fabs(cos(theta)) < 1e-12) {
+    double c0 = A.ssp_c0 + g * (z - A.ssp_z0), c1 = A.ssp_c0 + g * (z + r.dz - A.ssp_z0);
+    r.dt = g == 0.0 ? step / c0 : log(c1 / c0) / (g * sin(theta));
+    return r;
+  }
+  double sh = sin(delta / 2);
+  double xg = cm * xi * step * sc / (sh * sh + cm * cm);
+  double x = g * xg;
+  double ratio = fabs(x) < 1e-6 ? 1.0 + x * x / 3.0 : atanh(x) / x;
+  r.dt = ratio * xg;
+  return r;
+}
+__device__ __forceinline__ double arc_step(const TraceArgs& A, double xi) {
+  double k = xi * fabs(A.ssp_g);
+  if (k <= 0.0) return 2.0;
+  return fmin(2.0, sqrt(8.0 / k * 1e-4));
+}
+__device__ __forceinline__ void dir_split(D3 d, double& ex, double& ey, double& theta) {
+  double hz = sqrt(d.x * d.x + d.y * d.y);
+  if (hz > 0) { ex = d.x / hz; ey = d.y / hz; } else { ex = 1.0; ey = 0.0; }
+  theta = atan2(d.z, hz);
+}
+__device__ __forceinline__ double ssp_c(const TraceArgs& A, double z) { return A.ssp_c0 + A.ssp_g * (z - A.ssp_z0); }
+
+__device__ void route_curved(const TraceArgs& A, int ping, D3 o, D3 d0, D3 us, uint32_t ray, uint32_t sub,
+                             double dOmega, uint32_t keybase) {
+  D3 pos = o;
+  double ex, ey, th;
+  dir_split(d0, ex, ey, th);
+  double xi = cos(th) / ssp_c(A, pos.z);
+  double T = 0.0, sarc = 0.0, gam = 1.0;
+  int bounce = 0, prev = -1;
+  for (int iter = 0;; ++iter) {
+    if (iter >= 100000) { atomicOr(A.err, kErrLoop); return; }
+    if (!(T < A.T_stop)) break;
+    double h = arc_step(A, xi);
+    Arc ar = arc_advance(A, pos.z, th, xi, h);
+    D3 nxt = d3(pos.x + ar.dh * ex, pos.y + ar.dh * ey, pos.z + ar.dz);
+    D3 chv = d3(nxt.x - pos.x, nxt.y - pos.y, nxt.z - pos.z);
+    double len = sqrt(chv.x * chv.x + chv.y * chv.y + chv.z * chv.z);
+    D3 dc = d3(chv.x / len, chv.y / len, chv.z / len);
+    Hit hq = closest_hit(A.sc, pos, dc, kEpsHit, len, prev >= 0 ? prev : -1, A.err);
+    double ts = INFINITY;
+    if (A.has_surface && prev != -2 && dc.z != 0.0) {
+      double t = (A.surface_z - pos.z) / dc.z;
+      if (t > kEpsHit && t <= len) ts = t;
+    }
+    if (hq.prim < 0 && ts == INFINITY) {
+      pos = nxt;
+      th = ar.theta;
+      T += ar.dt;
+      sarc += h;
+      prev = -1;
+      continue;
+    }
+    bool surf = ts < hq.t;
+    double thit = surf ? ts : hq.t;
+    double f = thit / len;
+    double T_hit = T + f * ar.dt, s_hit = sarc + f * h;
+    if (!(T_hit <= A.T_stop)) break;
+    D3 hp = d3(pos.x + thit * dc.x, pos.y + thit * dc.y, pos.z + thit * dc.z);
+    D3 n;
+    if (surf) {
+      if (bounce >= A.max_bounces) break;
+      n = d3(0.0, 0.0, 1.0);
+      gam *= A.r_surface;
+    } else {
+      n = tri_normal64(A.sc.triv + 9 * hq.leaf);
+      double kinc = fabs(dc.x * n.x + dc.y * n.y + dc.z * n.z);
+      double amp = lambert(A, gam, (double)A.sc.tri_mu[hq.leaf], kinc, dOmega, s_hit);
+      emit(A, ping, 2.0 * T_hit, amp, speckle(A, ray, sub, bounce), us, hq.prim, keybase | (uint32_t)bounce);
+      if (!((A.sc.tri_flags[hq.leaf] & 1) && bounce < A.max_bounces)) break;
+      gam *= A.r_seabed;
+    }
+    double thh = th - xi * A.ssp_g * (f * h);
+    D3 tg = d3(cos(thh) * ex, cos(thh) * ey, sin(thh));
+    double k = 2.0 * (tg.x * n.x + tg.y * n.y + tg.z * n.z);
+    tg = d3(tg.x - k * n.x, tg.y - k * n.y, tg.z - k * n.z);
+    dir_split(tg, ex, ey, th);
+    pos = hp;
+    xi = cos(th) / ssp_c(A, pos.z);
+    T = T_hit;
+    sarc = s_hit;
+    bounce++;
+    prev = surf ? -2 : hq.prim;
+  }
+}
+
+__device__ void route_straight(const TraceArgs& A, int ping, D3 o, D3 d0, D3 us, uint32_t ray, uint32_t sub,
+                               double dOmega, uint32_t keybase) {
+  const double cw = A.ssp_c0;
+  const double L_stop = dm(A.T_stop, cw);
+  D3 pos = o, dir = d0;
+  double L = 0.0, gam = 1.0;
+  int bounce = 0, prev = -1;
+  for (int iter = 0; iter < 8; ++iter) {
+    double tlim = ds(L_stop, L);
+    if (!(tlim > 0)) break;
+    Hit hq = closest_hit(A.sc, pos, dir, kEpsHit, tlim, prev, A.err);
+    double ts = INFINITY;
+    if (A.has_surface && prev != -2 && dir.z != 0.0) {
+      double t = dd(ds(A.surface_z, pos.z), dir.z);
+      if (t > kEpsHit && t <= tlim) ts = t;
+    }
+    if (hq.prim < 0 && ts == INFINITY) break;
+    if (ts < hq.t) {
+      if (bounce >= A.max_bounces) break;
+      pos = axpy(pos, ts, dir);
+      L = da(L, ts);
+      dir.z = -dir.z;
+      gam *= A.r_surface;
+      bounce++;
+      prev = -2;
+      continue;
+    }
+    D3 n = tri_normal64(A.sc.triv + 9 * hq.leaf);
+    pos = axpy(pos, hq.t, dir);
+    L = da(L, hq.t);
+    double kinc = fabs(dot(dir, n));
+    double amp = lambert(A, gam, (double)A.sc.tri_mu[hq.leaf], kinc, dOmega, L);
+    emit(A, ping, 2.0 * dd(L, cw), amp, speckle(A, ray, sub, bounce), us, hq.prim, keybase | (uint32_t)bounce);
+    if ((A.sc.tri_flags[hq.leaf] & 1) && bounce < A.max_bounces) {
+      double k = dm(2.0, dot(dir, n));
+      dir = d3(ds(dir.x, dm(k, n.x)), ds(dir.y, dm(k, n.y)), ds(dir.z, dm(k, n.z)));
+      gam *= A.r_seabed;
+      bounce++;
+      prev = hq.prim;
+      continue;
+    }
+    break;
+  }
+}
+
+__global__ void __launch_bounds__(128) k_trace(TraceArgs A) {
+  const int64_t total = (int64_t)A.n_pings * A.n_subrays;
+  for (int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gid < total; gid += (int64_t)gridDim.x * blockDim.x) {
+    int ping = (int)(gid / A.n_subrays);
+    int sr = (int)(gid % A.n_subrays);
+    uint32_t ray = (uint32_t)(sr / A.n_sub), sub = (uint32_t)(sr % A.n_sub);
+    int row = (int)(ray / A.n_ray_az);
+    const DevPose& P = A.poses[ping];
+    D3 us = d3(A.ray_dirs[3 * sr], A.ray_dirs[3 * sr + 1], A.ray_dirs[3 * sr + 2]);
+    D3 dw = rot(P.R, us);
+    D3 o = d3(P.t[0], P.t[1], P.t[2]);
+    double dOmega = (double)A.row_domega[row];
+    uint32_t keybase = ((uint32_t)sr) << 2;
+    if (A.curved) route_curved(A, ping, o, dw, us, ray, sub, dOmega, keybase);
+    else route_straight(A, ping, o, dw, us, ray, sub, dOmega, keybase);
+  }
+}
+
+// ----------------------------------------------------------------- point scatterers
+__device__ bool leg_clear(const TraceArgs& A, D3 a, D3 b) {
+  D3 d = sub(b, a);
+  double len = sqrt(dot(d, d));
+  if (len <= 2e-6) return true;
+  d = d3(d.x / len, d.y / len, d.z / len);
+  Hit h = closest_hit(A.sc, a, d, 1e-6, len - 1e-6, -1, A.err);
+  return h.prim < 0;
+}
+
+__device__ D3 mirror(const double4 pl, D3 x) {
+  double k = 2.0 * (pl.x * x.x + pl.y * x.y + pl.z * x.z - pl.w);
+  return d3(x.x - k * pl.x, x.y - k * pl.y, x.z - k * pl.z);
+}
+
+__device__ double4 plane_of(const TraceArgs& A, int idx, double& gam) {
+  if (A.has_surface) {
+    if (idx == 0) { gam = A.r_surface; return make_double4(0.0, 0.0, 1.0, A.surface_z); }
+    idx -= 1;
+  }
+  gam = A.r_seabed;
+  return A.sc.planes[idx];
+}
+
+// Monostatic image-source eigen-routes of a point scatterer (isovelocity), or its
+// direct eigen-arc in a linear profile. Routes are plane sequences without immediate
+// repeats, enumerated by length then lexicographically.
+__global__ void k_points(TraceArgs A) {
+  int64_t total = (int64_t)A.n_pings * A.sc.n_points * A.n_routes;
+  int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gid >= total) return;
+  int route = (int)(gid % A.n_routes);
+  int ip = (int)((gid / A.n_routes) % A.sc.n_points);
+  int ping = (int)(gid / ((int64_t)A.n_routes * A.sc.n_points));
+  const DevPose& P = A.poses[ping];
+  float4 xp = A.sc.points[ip];
+  D3 x = d3(xp.x, xp.y, xp.z);
+  D3 o = d3(P.t[0], P.t[1], P.t[2]);
+  double sigma = xp.w;
+  uint32_t key = 0x80000000u | ((uint32_t)ip << 8) | (uint32_t)route;
+  if (A.curved) {
+    if (route != 0) return;
+    double dx = x.x - o.x, dy = x.y - o.y;
+    double D = sqrt(dx * dx + dy * dy);
+    double co = ssp_c(A, o.z), cx = ssp_c(A, x.z);
+    double g = A.ssp_g;
+    D3 dw;
+    double T, sarc;
+    if (D == 0.0) {
+      double dzz = x.z - o.z;
+      dw = d3(0.0, 0.0, dzz > 0 ? 1.0 : -1.0);
+      T = log(cx / co) / (g * dw.z);
+      sarc = fabs(dzz);
+    } else {
+      double ex = dx / D, ey = dy / D;
+      double a = co / g, b = cx / g;
+      double hc = (D * D + b * b - a * a) / (2 * D);
+      double Rr = sqrt(hc * hc + a * a);
+      double sg = g > 0 ? 1.0 : -1.0;
+      double th0 = atan2(sg * hc, sg * a), th1 = atan2(sg * (hc - D), sg * b);
+      dw = d3(cos(th0) * ex, cos(th0) * ey, sin(th0));
+      double s0 = sin(th0), s1 = sin(th1);
+      double X = (s0 - s1) / (1 - s0 * s1);
+      T = atanh(X) / g;
+      double ang = atan2(fabs(-hc * b - a * (D - hc)), -hc * (D - hc) + a * b);
+      sarc = Rr * ang;
+    }
+    if (!(T <= A.T_stop)) return;
+    D3 pos = o;
+    double ex, ey, th;
+    dir_split(dw, ex, ey, th);
+    double xi = cos(th) / ssp_c(A, pos.z);
+    double left = sarc;
+    for (int it = 0; left > 0 && it < 100000; ++it) {
+      double h = fmin(arc_step(A, xi), left);
+      Arc ar = arc_advance(A, pos.z, th, xi, h);
+      D3 nxt = d3(pos.x + ar.dh * ex, pos.y + ar.dh * ey, pos.z + ar.dz);
+      if (left - h <= 0) nxt = x;
+      if (!leg_clear(A, pos, nxt)) return;
+      pos = nxt;
+      th = ar.theta;
+      left -= h;
+    }
+    double amp = sigma / (sarc * sarc) * exp(-2.0 * A.alpha * sarc);
+    emit(A, ping, 2.0 * T, amp, 0.0, rot_t(P.R, dw), -1, key);
+    return;
+  }
+  int np = (A.has_surface ? 1 : 0) + A.sc.n_planes;
+  // decode the route index into a plane sequence
+  int len = 0;
+  int64_t r = route, count = 1;
+  while (r >= count) {
+    r -= count;
+    ++len;
+    count = np;
+    for (int k = 1; k < len; ++k) count *= (np - 1);
+    if (np == 0 || len > A.max_bounces) return;
+  }
+  int seq[4];
+  int64_t div = 1;
+  for (int k = 1; k < len; ++k) div *= (np - 1);
+  for (int k = 0; k < len; ++k) {
+    int64_t digit = r / div;
+    r %= div;
+    if (k + 1 < len) div /= (np - 1);
+    seq[k] = k == 0 ? (int)digit : ((int)digit < seq[k - 1] ? (int)digit : (int)digit + 1);
+  }
+  D3 img = x;
+  double gam = 1.0;
+  for (int k = len - 1; k >= 0; --k) {
+    double gk;
+    img = mirror(plane_of(A, seq[k], gk), img);
+    gam *= gk;
+  }
+  D3 dv = sub(img, o);
+  double L = sqrt(dot(dv, dv));
+  if (!(L > 0) || !(L / A.ssp_c0 <= A.T_stop)) return;
+  D3 a = o, tgt = img;
+  for (int k = 0; k < len; ++k) {
+    double gk;
+    double4 pl = plane_of(A, seq[k], gk);
+    double dA = pl.x * a.x + pl.y * a.y + pl.z * a.z - pl.w;
+    double dT = pl.x * tgt.x + pl.y * tgt.y + pl.z * tgt.z - pl.w;
+    if (!(dA * dT < 0)) return;
+    double f = dA / (dA - dT);
+    D3 sp = d3(a.x + f * (tgt.x - a.x), a.y + f * (tgt.y - a.y), a.z + f * (tgt.z - a.z));
+    if (!leg_clear(A, a, sp)) return;
+    tgt = mirror(pl, tgt);
+    a = sp;
+  }
+  if (!leg_clear(A, a, x)) return;
+  double amp = sigma * gam * gam / (L * L) * exp(-2.0 * A.alpha * L);
+  D3 dw = d3(dv.x / L, dv.y / L, dv.z / L);
+  emit(A, ping, 2.0 * L / A.ssp_c0, amp, 0.0, rot_t(P.R, dw), -1, key);
+}
+
+// Sonar-frame sub-ray directions (Sec. III Eq. 2-3 grid, cell-centred) with hashed
+// jitter inside 2x2 quarter cells, and the sub-ray solid angle per elevation row.
+__global__ void k_ray_table(double* dirs, float* row_domega, int nra, int nre, int nsub, double hfov,
+                            double vfov, uint32_t seed32) {
+  int64_t n = (int64_t)nra * nre * nsub;
+  int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double daz = hfov / nra, del = vfov / nre;
+  if (gid < nre) {
+    double el_lo = -vfov / 2 + gid * del, el_hi = el_lo + del;
+    row_domega[gid] = (float)(daz * (sin(el_hi) - sin(el_lo)) / nsub);
+  }
+  if (gid >= n) return;
+  int s = (int)(gid % nsub);
+  int ray = (int)(gid / nsub);
+  int i = ray % nra, j = ray / nra;
+  double ox = 0.0, oy = 0.0;
+  if (nsub == 4) {
+    uint32_t x = (uint32_t)ray, y = (uint32_t)s, z = 0u, w = seed32;
+    pcg4d(x, y, z, w);
+    ox = ((s & 1) + u24(x)) / 2.0 - 0.5;
+    oy = ((s >> 1) + u24(y)) / 2.0 - 0.5;
+  }
+  double az = -hfov / 2 + (i + 0.5 + ox) * daz;
+  double el = -vfov / 2 + (j + 0.5 + oy) * del;
+  dirs[3 * gid] = cos(el) * cos(az);
+  dirs[3 * gid + 1] = cos(el) * sin(az);
+  dirs[3 * gid + 2] = sin(el);
+}
+
+// Rotation matrix of each ping's unit quaternion (w, x, y, z), normalised first.
+__global__ void k_poses(const double* raw, DevPose* poses, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double* p = raw + 7 * i;
+  double qn = sqrt(p[3] * p[3] + p[4] * p[4] + p[5] * p[5] + p[6] * p[6]);
+  double w = p[3] / qn, x = p[4] / qn, y = p[5] / qn, z = p[6] / qn;
+  DevPose P;
+  P.R[0] = 1 - 2 * (y * y + z * z); P.R[1] = 2 * (x * y - w * z);     P.R[2] = 2 * (x * z + w * y);
+  P.R[3] = 2 * (x * y + w * z);     P.R[4] = 1 - 2 * (x * x + z * z); P.R[5] = 2 * (y * z - w * x);
+  P.R[6] = 2 * (x * z - w * y);     P.R[7] = 2 * (y * z + w * x);     P.R[8] = 1 - 2 * (x * x + y * y);
+  P.t[0] = p[0]; P.t[1] = p[1]; P.t[2] = p[2];
+  poses[i] = P;
+}
+
+}  // namespace
+
+cudaError_t launch_ray_table(double* dirs, float* row_domega, int32_t nra, int32_t nre, int32_t nsub,
+                             double hfov, double vfov, uint32_t seed32, cudaStream_t st) {
+  int64_t n = (int64_t)nra * nre * nsub;
+  if (n < nre) n = nre;
+  k_ray_table<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(dirs, row_domega, nra, nre, nsub, hfov, vfov, seed32);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_poses(const double* raw, DevPose* poses, int32_t n, cudaStream_t st) {
+  k_poses<<<(unsigned)ceil_div(n, 64), 64, 0, st>>>(raw, poses, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_trace(const TraceArgs& a, int sm_count, cudaStream_t st) {
+  int64_t total = (int64_t)a.n_pings * a.n_subrays;
+  int64_t blocks = ceil_div(total, 128);
+  int64_t cap = (int64_t)sm_count * 16;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  k_trace<<<(unsigned)blocks, 128, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_points(const TraceArgs& a, cudaStream_t st) {
+  int64_t total = (int64_t)a.n_pings * a.sc.n_points * a.n_routes;
+  if (total == 0) return cudaSuccess;
+  k_points<<<(unsigned)ceil_div(total, 64), 64, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace sonar

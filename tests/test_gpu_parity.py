@@ -1,0 +1,115 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances: hit prim ids bit-exact outside the near-tie margins (barycentric 1e-5,
+runner-up gap 1e-6 m); delays to 1e-12 relative; envelope normalised L2 <= 1e-4 for the
+FP32 form and <= 1e-2 for BF16/FP16; peak (beam, bin) bit-exact where the oracle's peak
+beats its runner-up and the threshold by 1e-3 (FP32) or 2e-2 (BF16/FP16).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2606_06130_gb300 import inputs
+from tests import parity
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def sonar():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2606_06130_gb300.sonar import Sonar, SONAR_OPT_DEBUG
+    s = Sonar(0)
+    s.set_option(SONAR_OPT_DEBUG, 1)
+    yield s
+    s.close()
+
+
+def run(s, scene, params, pose, ssp, precision="fp32"):
+    s.upload(scene)
+    env, cloud, n = s.ping(pose, params, ssp, precision=precision)
+    torch.cuda.synchronize()
+    return env.reshape(-1, params["n_range"]).double().cpu().numpy(), cloud, n
+
+
+def cloud_check(cloud, n, params, pose, E_ref, rel):
+    from paper_2606_06130_gb300.sonar import cloud_records
+    pk = oracle.peaks(params, pose, E_ref)
+    pts = cloud_records(cloud, n)
+    nb = parity.n_blank(params)
+    vmax = E_ref[:, nb:].max()
+    thr = params["thr"] * vmax if params["thr_mode"] == 1 else params["thr"]
+    ok = parity.peak_margin_mask(E_ref, nb, thr, rel)
+    gpu = {int(b): int(k) for b, k in zip(pts["beam"], pts["bin"])}
+    ref = {int(b): int(k) for b, k in zip(pk["beam"], pk["bin"])}
+    checked = 0
+    for b in np.nonzero(ok)[0]:
+        assert gpu.get(int(b)) == ref.get(int(b)), (b, gpu.get(int(b)), ref.get(int(b)))
+        checked += 1
+    assert list(pts["beam"]) == sorted(pts["beam"])
+    return checked, int(np.count_nonzero(~ok))
+
+
+# ------------------------------------------------------------------ C1: tiny plain ping
+def test_c1_fp32_full_parity(sonar):
+    scene, params, poses, ssp = inputs.workload("c1")
+    E, cloud, n = run(sonar, scene, params, poses[0], ssp)
+    ref = oracle.trace(scene, params, poses[0], ssp)
+    excluded, matched = parity.check_hits(sonar.hits(), ref, params["n_sub"])
+    assert matched == ref["n"]
+    E_ref, _, s_ref = oracle.volume(params, ref)
+    s_gpu = sonar.echoes(params)[0]
+    assert parity.nl2(s_gpu, s_ref) < 2e-5
+    assert parity.nl2(E, E_ref) <= 1e-4
+    checked, _ = cloud_check(cloud, n, params, poses[0], E_ref, 1e-3)
+    assert checked > 0.8 * params["n_beam_az"] * params["n_beam_el"]
+
+
+@pytest.mark.parametrize("precision,tol", [("bf16", 1e-2), ("fp16", 1e-2)])
+def test_c1_reduced_precision(sonar, precision, tol):
+    scene, params, poses, ssp = inputs.workload("c1")
+    E, cloud, n = run(sonar, scene, params, poses[0], ssp, precision)
+    ref = oracle.trace(scene, params, poses[0], ssp)
+    E_ref, _, _ = oracle.volume(params, ref)
+    assert parity.nl2(E, E_ref) <= tol
+    cloud_check(cloud, n, params, poses[0], E_ref, 2e-2)
+
+
+# ------------------------------------------------------------------ C3: curved rays, 2 bounces
+@pytest.mark.parametrize("precision,tol", [("fp32", 1e-4), ("bf16", 1e-2), ("fp16", 1e-2)])
+def test_c3_refraction_precision_forms(sonar, precision, tol):
+    scene, params, poses, ssp = inputs.workload("c3")
+    E, cloud, n = run(sonar, scene, params, poses[0], ssp, precision)
+    ref = oracle.trace(scene, params, poses[0], ssp)
+    assert ref["c_ref"] != 1500.0
+    parity.check_hits(sonar.hits(), ref, params["n_sub"])
+    E_ref, _, _ = oracle.volume(params, ref)
+    err = parity.nl2(E, E_ref)
+    assert err <= tol, err
+    cloud_check(cloud, n, params, poses[0], E_ref, 1e-3 if precision == "fp32" else 2e-2)
+
+
+# ------------------------------------------------------------------ C2: harbour wall, full size
+def test_c2_fp32_sampled_parity(sonar):
+    scene, params, poses, ssp = inputs.workload("c2")
+    E, cloud, n = run(sonar, scene, params, poses[0], ssp)
+    ref = oracle.trace(scene, params, poses[0], ssp)
+    excluded, matched = parity.check_hits(sonar.hits(), ref, params["n_sub"])
+    assert matched >= ref["n"] - 2 * (excluded + 1)
+    # sampled range samples: the densest echo region plus random ones
+    dr = params["r_max"] / params["n_range"]
+    n_hit = np.floor(ref["tau"] * ref["c_ref"] / 2 / dr).astype(int)
+    dense = np.argsort(np.bincount(n_hit, minlength=params["n_range"]))[-12:]
+    rng = np.random.default_rng(5)
+    ns = np.unique(np.concatenate([dense, rng.integers(0, params["n_range"], 8)])).astype(np.int32)
+    E_ref, _, s_ref = oracle.volume(params, ref, ns=ns)
+    s_gpu = sonar.echoes(params)[0][ns]
+    assert parity.nl2(s_gpu, s_ref) < 2e-5
+    assert parity.nl2(E[:, ns], E_ref) <= 1e-4
