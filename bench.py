@@ -1,0 +1,397 @@
+"""Benchmark: pings/s of per-ping coherent echo formation at 8192 beams x 1024 range bins.
+
+Workload (one step = one ping through the whole path: ray casting, shading, binning,
+element-echo synthesis, beamforming GEMM with fused envelope/TVG/peak search, point
+cloud): the harbour sheet-pile scene (32x32 array, 128x64 beams, 1024 bins to 15 m,
+512x256 rays x 4 sub-rays, direct + one surface/seabed bounce), FP32 form, synthetic
+data. Inputs are resident in HBM; L2 is flushed (256 MB write) before every timed step
+outside the timed events. ``--impl reference`` times the FP64 CPU oracle instead.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                [--precision fp32|bf16|fp16]
+Under torchrun each rank runs an independent replica (weak scaling, no collective on
+the data path); rank 0 prints one JSON line.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pings/s at 8192 beams x 1024 range bins (harbour wall, 32x32 array)"
+UNIT = "pings/s"
+WORKLOAD = ("harbour sheet-pile wall (20.5k tri) over fBm seabed (130k tri); 32x32 array at lambda/2, "
+            "128x64 beams over 90x40 deg, 1024 bins to 15 m, 512x256 rays x 4 jittered sub-rays, "
+            "direct + 1 surface/seabed bounce; 1 ping per step")
+FP32_PEAK_NOTE = "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"
+
+
+def peaks_file():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ------------------------------------------------------------------ oracle sample
+def oracle_sample_params(p):
+    """1/8 of a ping: the central 1/8 of the vertical field of view (ray and beam rows),
+    all range bins, all elements."""
+    q = dict(p)
+    q["vfov"] = p["vfov"] / 8
+    q["n_ray_el"] = p["n_ray_el"] // 8
+    q["n_beam_el"] = p["n_beam_el"] // 8
+    return q, 1.0 / 8.0
+
+
+def oracle_ping(scene, params, pose, ssp):
+    import oracle
+    h = oracle.trace(scene, params, pose, ssp)
+    E, _, _ = oracle.volume(params, h)
+    oracle.peaks(params, pose, E)
+    return h["n"]
+
+
+def time_oracle(steps, warmup):
+    import oracle
+    from paper_2606_06130_gb300 import inputs
+    scene, params, poses, ssp = inputs.workload("c2")
+    q, frac = oracle_sample_params(params)
+    for _ in range(warmup):
+        oracle_ping(scene, q, poses[0], ssp)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        oracle_ping(scene, q, poses[0], ssp)
+    dt = time.perf_counter() - t0
+    return {"value": steps * frac / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "1/8 of the ping per step: central 1/8 of the vertical field of view (32 of 256 ray rows, "
+                      "8 of 64 beam rows), all 1024 bins and 1024 elements; FP64 C oracle, OpenMP",
+            "seconds": dt, "steps": steps}
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.rows = []
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_id), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[3 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# ------------------------------------------------------------------ roofline
+def stage_work(stage, params, stats, n_pings):
+    """Algorithmic work of one launch of a stage: (amount, unit, bound)."""
+    M = params["nx"] * params["ny"]
+    nb = params["n_beam_az"] * params["n_beam_el"]
+    nr = params["n_range"]
+    if stage == "beamform":
+        # complex [Nb x M] . [M x Nr] as a real GEMM: 8 Nb M Nr flop per ping
+        return 8.0 * nb * M * nr * n_pings, "flop", "tensor"
+    if stage == "synth":
+        # per (hit, element): phasor product (6 flop) + W complex MACs (8 flop each)
+        return float(stats["n_hits"]) * M * (8 * stats["taps"] + 6), "flop", "alu"
+    if stage == "convert":
+        return float(n_pings) * nr * M * (8 + 8), "byte", "hbm"
+    return None
+
+
+def read_traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary, or None."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    try:
+        src_hash = None
+        for line in open(path):
+            if line.startswith("#") or not line.strip():
+                continue
+            k, nbytes, h = line.split()[:3]
+            if k == kernel:
+                src_hash = h
+                break
+        if src_hash is None:
+            return None
+        import hashlib
+        unit = {"synth": "synth.cu", "beamform": "beamform.cu", "trace": "trace.cu"}.get(kernel)
+        cur = hashlib.sha1(open(os.path.join(ROOT, "paper_2606_06130_gb300", "csrc", unit), "rb").read()).hexdigest()[:12]
+        return float(nbytes) if cur == src_hash else None
+    except (OSError, ValueError):
+        return None
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args, ws, rank, local):
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2606_06130_gb300 import inputs
+    from paper_2606_06130_gb300.sonar import Sonar, SONAR_OPT_TIMING
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    scene, params, poses, ssp = inputs.workload("c2")
+    s = Sonar(local)
+    s.upload(scene)
+    nb = params["n_beam_az"] * params["n_beam_el"]
+    env = torch.empty((params["n_beam_el"], params["n_beam_az"], params["n_range"]), dtype=torch.float32, device=dev)
+    cloud = torch.empty((nb, 6), dtype=torch.int32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    pose = poses[0]
+
+    def ping():
+        return s.ping_batch([pose], params, ssp, precision=args.precision, env=env[None], cloud=cloud[None],
+                            cloud_cap=nb)
+
+    s.set_option(SONAR_OPT_TIMING, 1)
+    for _ in range(max(args.warmup, 3)):
+        ping()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stages = {k: [] for k in ("trace", "bin", "synth", "convert", "beamform", "peaks")}
+    launches = 0
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    gpu_id = torch.cuda.get_device_properties(local).uuid if hasattr(torch.cuda.get_device_properties(local), "uuid") else local
+    clocks = ClockSampler(f"GPU-{gpu_id}" if not isinstance(gpu_id, int) else gpu_id)
+    for i in range(args.steps):
+        flush.zero_()  # L2 flush outside the timed events
+        ev[i][0].record(stream)
+        ping()
+        ev[i][1].record(stream)
+        st = s.stats()
+        for k in stages:
+            stages[k].append(st["ms_" + k])
+        launches += st["kernels"]
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    t_ms = sum(a.elapsed_time(b) for a, b in ev)
+    if ws > 1:
+        t = torch.tensor([t_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_ms = float(t.item())
+    stats = s.stats()
+
+    # end to end through the C ABI with host buffers: pinned env, host cloud
+    env_h = torch.empty(env.shape, dtype=torch.float32, pin_memory=True)
+    cloud_h = np.zeros((nb, 6), np.int32)
+    for _ in range(2):
+        s.ping_batch([pose], params, ssp, precision=args.precision, env=env_h[None], cloud=cloud_h[None], cloud_cap=nb)
+    k_e2e = max(3, min(args.steps, 20))
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    for _ in range(k_e2e):
+        s.ping_batch([pose], params, ssp, precision=args.precision, env=env_h[None], cloud=cloud_h[None], cloud_cap=nb)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - e0
+    if ws > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    # the same ping replayed as a captured CUDA graph (no stage events)
+    s.set_option(SONAR_OPT_TIMING, 0)
+    for _ in range(3):
+        ping()
+    torch.cuda.synchronize()
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g_ms = 0.0
+    for i in range(args.steps):
+        flush.zero_()
+        g0.record(stream)
+        ping()
+        g1.record(stream)
+        g1.synchronize()
+        g_ms += g0.elapsed_time(g1)
+
+    # other forms (same run): BF16 single ping, BF16 64-ping trajectory batch
+    forms = {}
+    if rank == 0 and not args.no_forms:
+        forms = other_forms(torch, s, inputs, dev)
+
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.barrier()
+            torch.distributed.destroy_process_group()
+        return
+
+    mean_stage = {k: float(np.mean(v)) for k, v in stages.items()}
+    dom = max(("synth", "beamform", "convert"), key=lambda k: mean_stage[k])
+    pk, pk_kind = peaks_file()
+    amount, unit, bound = stage_work(dom, params, stats, 1)
+    dt_s = mean_stage[dom] / 1e3
+    if bound == "tensor":
+        peak, punit, achieved = pk["bf16_tflops"], "TFLOP/s", amount / dt_s / 1e12
+        pnote = f"bf16 dense burst, {pk_kind}"
+    elif bound == "alu":
+        peak, punit, achieved = 152 * 128 * 2 * 2.070e9 / 1e12, "TFLOP/s", amount / dt_s / 1e12
+        pnote = f"FP32 FMA: {FP32_PEAK_NOTE}"
+    else:
+        peak, punit, achieved = pk["hbm_gbs"], "GB/s", amount / dt_s / 1e9
+        pnote = f"HBM copy, {pk_kind}"
+    traffic = read_traffic(dom)
+    roof = {"kernel": {"synth": "k_synth", "beamform": "k_gemm", "convert": "k_convert"}[dom],
+            "bound": bound, "achieved": achieved, "peak": peak, "unit": punit, "frac": achieved / peak,
+            "peak_source": pnote, "traffic": traffic,
+            "algorithmic_per_launch": amount, "algorithmic_unit": unit, "launch_ms": mean_stage[dom]}
+
+    err = oracle_error(scene, params, pose, ssp, env, args.precision) if not args.no_oracle else None
+    cpu = None
+    if ws == 1 and not args.no_oracle:
+        cpu = time_oracle(1, 0)
+    value = ws * args.steps / (t_ms / 1e3)
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": max(args.warmup, 3), "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else args.precision,
+           "data": "synthetic",
+           "config": {"workload": WORKLOAD, "precision": args.precision,
+                      "beamform_operands": {"fp32": "bf16 hi/lo split, 3 tensor products, fp32 accumulate",
+                                            "bf16": "bf16, fp32 accumulate", "fp16": "fp16, fp32 accumulate"}[args.precision],
+                      "l2": "flushed before every timed step (256 MB write, outside the events)",
+                      "parallelism": f"replicas x{ws}"},
+           "roofline": roof,
+           "stages_ms": mean_stage,
+           "hits_per_ping": stats["n_hits"],
+           "gpu_launches": launches,
+           "graph_replay": {"value": ws * args.steps / (g_ms / 1e3), "unit": UNIT,
+                            "note": "same steps replayed as one CUDA graph per ping, no stage events"},
+           "e2e": {"value": ws * k_e2e / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 56,
+                   "d2h_bytes_per_step": int(env.numel() * 4 + nb * 24 + 8), "steps": k_e2e,
+                   "path": "sonar_ping_batch with pinned host env and pageable host cloud"},
+           "clocks": clk,
+           "error_vs_oracle": err,
+           "forms": forms,
+           "cpu_baseline": cpu}
+    print(json.dumps(out), flush=True)
+    if ws > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+def oracle_error(scene, params, pose, ssp, env, precision):
+    """Envelope normalised L2 against the FP64 oracle on sampled range bins (all beams)."""
+    import oracle
+    h = oracle.trace(scene, params, pose, ssp)
+    dr = params["r_max"] / params["n_range"]
+    n_hit = np.floor(h["tau"] * h["c_ref"] / 2 / dr).astype(int)
+    dense = np.argsort(np.bincount(n_hit, minlength=params["n_range"]))[-8:]
+    ns = np.unique(np.concatenate([dense, np.arange(0, params["n_range"], 128)])).astype(np.int32)
+    E_ref, _, _ = oracle.volume(params, h, ns=ns)
+    E = env.reshape(-1, params["n_range"]).double().cpu().numpy()[:, ns]
+    return {"env_nl2": float(np.linalg.norm(E - E_ref) / np.linalg.norm(E_ref)), "sampled_bins": len(ns),
+            "beams": int(E.shape[0]), "precision": precision}
+
+
+def other_forms(torch, s, inputs, dev):
+    out = {}
+    scene, params, poses, ssp = inputs.workload("c2")
+    for prec in ("bf16", "fp16"):
+        for _ in range(3):
+            s.ping(poses[0], params, ssp, precision=prec)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(10):
+            s.ping(poses[0], params, ssp, precision=prec)
+        torch.cuda.synchronize()
+        out[f"c2_single_{prec}"] = {"value": 10 / (time.perf_counter() - t0), "unit": UNIT}
+    sc4, p4, poses4, ssp4 = inputs.workload("c4")
+    s.upload(sc4)
+    for prec in ("fp32", "bf16"):
+        env = torch.empty((len(poses4), p4["n_beam_el"], p4["n_beam_az"], p4["n_range"]), dtype=torch.float32, device=dev)
+        s.ping_batch(poses4, p4, ssp4, precision=prec, env=env)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        reps = 3
+        for _ in range(reps):
+            s.ping_batch(poses4, p4, ssp4, precision=prec, env=env)
+        torch.cuda.synchronize()
+        st = s.stats()
+        out[f"c4_batch64_{prec}"] = {"value": reps * len(poses4) / (time.perf_counter() - t0), "unit": UNIT,
+                                     "hits_total": st["n_hits"]}
+        del env
+    s.upload(scene)
+    return out
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    r = time_oracle(args.steps, args.warmup)
+    out = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * r["seconds"] / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "precision": "fp64 oracle"}, "impl": "reference",
+           "cpu_baseline": {"value": r["value"], "unit": UNIT, "cores": r["cores"], "kind": "oracle",
+                            "sample": r["sample"]},
+           "e2e": {"value": r["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16"])
+    ap.add_argument("--no-oracle", action="store_true", help="skip the oracle error and CPU baseline")
+    ap.add_argument("--no-forms", action="store_true", help="skip the BF16/FP16/batch side measurements")
+    args = ap.parse_args()
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -121,7 +121,11 @@ typedef struct {
   int64_t hit_capacity;
   int32_t n_pings;
   int32_t taps;              /* pulse-window taps per hit */
-  float ms_trace, ms_bin, ms_synth, ms_beamform, ms_peaks; /* per stage, when timing is on */
+  int32_t kernels;           /* kernel launches of the last call */
+  /* per-stage device time of the last call (CUDA events on the work stream, recorded
+     only with SONAR_OPT_TIMING): ray casting, binning, synthesis, operand conversion,
+     beamforming GEMM, peak extraction */
+  float ms_trace, ms_bin, ms_synth, ms_convert, ms_beamform, ms_peaks;
 } sonar_stats;
 
 /* ---------------------------------------------------------------- context */
@@ -137,7 +141,9 @@ SONAR_API const char* sonar_last_error(const sonar_ctx* ctx);
 
 /* Options. SONAR_OPT_DEBUG: 1 keeps FP64 delays of hits and element echoes of the
    last call for sonar_get_hits / sonar_get_echoes. SONAR_OPT_TIMING: 1 records
-   per-stage CUDA-event times in sonar_stats (adds synchronisation).
+   per-stage CUDA events on the work stream and reports the stage times in
+   sonar_stats; calls then launch their kernels directly instead of replaying the
+   graph (graph event nodes cannot be timed).
    SONAR_OPT_GRAPH: 1 (default) replays the ping pipeline as a captured CUDA graph.
    SONAR_OPT_TILE_N: beamforming N tile (128 or 256; 0 = autotuned). */
 #define SONAR_OPT_DEBUG 1

@@ -37,6 +37,8 @@ struct sonar_ctx {
   cudaStream_t stream = nullptr;       // private work stream (capturable)
   cudaStream_t user_stream = nullptr;  // caller's stream, ordered with events
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaEvent_t stage_ev[7] = {};
+  int graph_kernels = 0;
   int sm_count = 0;
   std::string err;
   bool debug = false, timing = false, use_graph = true;
@@ -408,12 +410,14 @@ struct Outputs {
 
 // Enqueue the whole pipeline for P pings on the context stream (graph-capturable:
 // no host synchronisation, fixed grids that read device-side counts).
-int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, const Outputs& o,
-            cudaEvent_t* ev) {
+int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, const Outputs& o, int* kernels) {
   cudaStream_t st = ctx->stream;
+  // stage boundaries: 0 trace 1 bin 2 synth 3 convert 4 beamform 5 peaks 6
   auto mark = [&](int i) {
-    if (ev) cudaEventRecord(ev[i], st);
+    if (ctx->timing) cudaEventRecord(ctx->stage_ev[i], st);
   };
+  const bool fp16 = p->precision == SONAR_FP16;
+  *kernels = 9 + (ctx->sc.n_points > 0 ? 1 : 0) + (fp16 ? 1 : 0);
   mark(0);
   CU(cudaMemsetAsync(ctx->n_hits, 0, sizeof(unsigned long long), st));
   CU(cudaMemsetAsync(ctx->err_dev, 0, sizeof(int), st));
@@ -457,8 +461,10 @@ int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, cons
   mark(1);
   const int32_t n_bins = P * d.nr_pad;
   CU(launch_bin(ctx->hits, ctx->n_hits, n_bins, ctx->counts, ctx->offsets, ctx->sorted, ctx->sm_count, st));
-  mark(2);
   CU(cudaMemsetAsync(ctx->S, 0, sizeof(float2) * ctx->s_elems, st));
+  CU(cudaMemsetAsync(ctx->keys, 0, sizeof(unsigned long long) * (size_t)P * d.nb, st));
+  CU(cudaMemsetAsync(ctx->pmax, 0, sizeof(unsigned) * P, st));
+  mark(2);
   SynthArgs sa;
   sa.hits_sorted = ctx->sorted;
   sa.n_valid = ctx->offsets + n_bins;
@@ -472,6 +478,7 @@ int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, cons
   sa.total_rows = (int64_t)P * d.nr_pad;
   sa.err = ctx->err_dev;
   CU(launch_synth(sa, ctx->sm_count, st));
+  mark(3);
   ConvertArgs ca;
   ca.S = ctx->S;
   ca.n_pings = P;
@@ -485,12 +492,10 @@ int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, cons
   ca.x_hi = ctx->x_hi;
   ca.x_lo = ctx->x_lo;
   CU(launch_convert(ca, ctx->sm_count, st));
-  mark(3);
-  CU(cudaMemsetAsync(ctx->keys, 0, sizeof(unsigned long long) * (size_t)P * d.nb, st));
-  CU(cudaMemsetAsync(ctx->pmax, 0, sizeof(unsigned) * P, st));
+  mark(4);
   GemmArgs ga;
   memset(&ga, 0, sizeof(ga));
-  const bool f16 = p->precision == SONAR_FP16;
+  const bool f16 = fp16;
   int rc;
   if ((rc = make_map(ctx, &ga.map_xh, ctx->x_hi, (int64_t)P * d.nr_x, d.k_pad, 128, f16))) return rc;
   if ((rc = make_map(ctx, &ga.map_xl, ctx->x_lo, (int64_t)P * d.nr_x, d.k_pad, 128, f16))) return rc;
@@ -516,7 +521,7 @@ int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, cons
   ga.ping_max = ctx->pmax;
   ga.err = ctx->err_dev;
   CU(launch_gemm(ga, ctx->sm_count, st));
-  mark(4);
+  mark(5);
   PeakArgs pa;
   pa.peak_keys = ctx->keys;
   pa.ping_max = ctx->pmax;
@@ -535,7 +540,7 @@ int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, cons
   pa.cap = o.cap;
   pa.n_cloud = ctx->n_cloud_dev;
   CU(launch_peaks(pa, st));
-  mark(5);
+  mark(6);
   return SONAR_OK;
 }
 
@@ -590,15 +595,13 @@ int run(sonar_ctx* ctx, const sonar_pose* poses, int P, const sonar_params* p, c
   }
   CU(cudaMemcpyAsync(ctx->raw_dev, ctx->raw_host, sizeof(double) * 7 * P, cudaMemcpyHostToDevice, ctx->stream));
 
-  cudaEvent_t ev[6];
   const bool timed = ctx->timing;
-  if (timed) {
-    for (auto& e : ev) CU(cudaEventCreate(&e));
-    rc = enqueue(ctx, P, p, d, o, ev);
-  } else if (ctx->use_graph) {
+  int kernels = 0;
+  // stage events cannot be timed when recorded by graph nodes: timing runs eagerly
+  if (ctx->use_graph && !timed) {
     std::vector<uint8_t> k;
     key_add(k, P); key_add(k, *p); key_add(k, o.env); key_add(k, o.cloud); key_add(k, o.cap);
-    key_add(k, ctx->debug); key_add(k, ctx->scene_version); key_add(k, d.c_ref);
+    key_add(k, ctx->debug); key_add(k, ctx->timing); key_add(k, ctx->scene_version); key_add(k, d.c_ref);
     if (ssp) {
       key_add(k, ssp->n_nodes);
       for (int i = 0; i < ssp->n_nodes; ++i) { key_add(k, ssp->c[i]); if (ssp->z) key_add(k, ssp->z[i]); }
@@ -608,7 +611,7 @@ int run(sonar_ctx* ctx, const sonar_pose* poses, int P, const sonar_params* p, c
       if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; }
       cudaGraph_t g;
       CU(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-      rc = enqueue(ctx, P, p, d, o, nullptr);
+      rc = enqueue(ctx, P, p, d, o, &ctx->graph_kernels);
       cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
       if (rc) { if (ce == cudaSuccess) cudaGraphDestroy(g); return rc; }
       CU(ce);
@@ -618,8 +621,9 @@ int run(sonar_ctx* ctx, const sonar_pose* poses, int P, const sonar_params* p, c
       ctx->gkey = k;
     }
     CU(cudaGraphLaunch(ctx->gexec, ctx->stream));
+    kernels = ctx->graph_kernels;
   } else {
-    rc = enqueue(ctx, P, p, d, o, nullptr);
+    rc = enqueue(ctx, P, p, d, o, &kernels);
   }
   if (rc) return rc;
   if (!env_dev)
@@ -641,15 +645,16 @@ int run(sonar_ctx* ctx, const sonar_pose* poses, int P, const sonar_params* p, c
   ctx->stats.hit_capacity = ctx->hit_cap;
   ctx->stats.n_pings = P;
   ctx->stats.taps = d.taps;
+  ctx->stats.kernels = kernels;
   if (timed) {
-    float t[5];
-    for (int i = 0; i < 5; ++i) cudaEventElapsedTime(&t[i], ev[i], ev[i + 1]);
+    float t[6];
+    for (int i = 0; i < 6; ++i) CU(cudaEventElapsedTime(&t[i], ctx->stage_ev[i], ctx->stage_ev[i + 1]));
     ctx->stats.ms_trace = t[0];
     ctx->stats.ms_bin = t[1];
     ctx->stats.ms_synth = t[2];
-    ctx->stats.ms_beamform = t[3];
-    ctx->stats.ms_peaks = t[4];
-    for (auto& e : ev) cudaEventDestroy(e);
+    ctx->stats.ms_convert = t[3];
+    ctx->stats.ms_beamform = t[4];
+    ctx->stats.ms_peaks = t[5];
   }
   if (errw & kErrTimeout) return fail(ctx, SONAR_E_TIMEOUT, "a device-side wait exceeded its limit");
   if (errw & kErrLoop) return fail(ctx, SONAR_E_TIMEOUT, "a ray-marching loop exceeded its step limit");
@@ -689,6 +694,11 @@ int sonar_create(sonar_ctx** out, int device, void* cuda_stream) {
   if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+    delete c;
+    return SONAR_E_CUDA;
+  }
+  for (auto& e : c->stage_ev)
+    if (cudaEventCreate(&e) != cudaSuccess) {
     delete c;
     return SONAR_E_CUDA;
   }
@@ -735,6 +745,8 @@ int sonar_destroy(sonar_ctx* c) {
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   if (c->ev_in) cudaEventDestroy(c->ev_in);
   if (c->ev_out) cudaEventDestroy(c->ev_out);
+  for (auto& e : c->stage_ev)
+    if (e) cudaEventDestroy(e);
   if (c->stream) cudaStreamDestroy(c->stream);
   free_scene(c);
   dfree(c->ray_dirs); dfree(c->row_domega); dfree(c->y_hi); dfree(c->y_lo); dfree(c->rtab); dfree(c->taper_dev);

@@ -68,8 +68,9 @@ class sonar_hit(C.Structure):
 
 class sonar_stats(C.Structure):
     _fields_ = [("n_hits", C.c_int64), ("hit_capacity", C.c_int64), ("n_pings", C.c_int32),
-                ("taps", C.c_int32), ("ms_trace", C.c_float), ("ms_bin", C.c_float),
-                ("ms_synth", C.c_float), ("ms_beamform", C.c_float), ("ms_peaks", C.c_float)]
+                ("taps", C.c_int32), ("kernels", C.c_int32), ("ms_trace", C.c_float), ("ms_bin", C.c_float),
+                ("ms_synth", C.c_float), ("ms_convert", C.c_float), ("ms_beamform", C.c_float),
+                ("ms_peaks", C.c_float)]
 
 
 POINT_DTYPE = np.dtype([("x", "<f4"), ("y", "<f4"), ("z", "<f4"), ("intensity", "<f4"),
