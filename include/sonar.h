@@ -190,6 +190,34 @@ SONAR_API int sonar_get_hits(sonar_ctx* ctx, sonar_hit* host_out, int64_t cap, i
 SONAR_API int sonar_get_echoes(sonar_ctx* ctx, float* host_out, int64_t cap_floats);
 SONAR_API int sonar_get_stats(const sonar_ctx* ctx, sonar_stats* out);
 
+/* ---------------------------------------------------------------- allocation-free cloud */
+/* Point cloud of n_pings envelope volumes that are already on the device, computed
+   without allocating anything. The paper has no counterpart: this exists for callers
+   that cannot call cudaMalloc (code inside an allocator or memory-pool callback, a
+   real-time loop with a frozen memory budget, a process that must not grow device
+   memory after start-up). It needs no context.
+   env: device [n_pings][n_beam_el][n_beam_az][n_range] f32 (as written by sonar_ping /
+   sonar_ping_batch); params: the beam grid, range, r_blank and threshold fields are
+   used; poses: host [n_pings]; cloud: device [n_pings][cloud_cap]; n_cloud: host
+   [n_pings] (may be NULL), the number of points found per ping; cuda_stream: the
+   stream to enqueue on (NULL = legacy default stream). The call synchronises that
+   stream before returning. Produces the same points, in the same beam order, as the
+   cloud of the sonar_ping call that wrote env.
+   Scratch (per-beam peak keys, per-ping maxima and counts) lives in one file-scope
+   device array of about 4 MiB that every GPU loading the library holds until the
+   process exits; the call makes no cudaMalloc/cudaFree or allocating library call.
+   Limits: n_pings <= 64 and n_pings * n_beam_az * n_beam_el <= 524288, otherwise
+   SONAR_E_CAPACITY is returned before any work. The first call on a device resolves
+   the array's device address (cudaGetSymbolAddress, with that device current); make
+   that first call before any stream capture. All calls share the array: calls whose
+   GPU work overlaps (other streams, other threads) race and must be serialised by the
+   caller. Returns SONAR_E_ARG on bad arguments, SONAR_E_CAPACITY also when a ping has
+   more than cloud_cap points (cloud then holds the first cloud_cap), SONAR_E_CUDA on a
+   CUDA error. */
+SONAR_API int sonar_cloud_noalloc(const float* env, int32_t n_pings, const sonar_params* params,
+                                  const sonar_pose* poses, sonar_point* cloud, int64_t cloud_cap,
+                                  int64_t* n_cloud, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -96,6 +96,8 @@ _SIGS = {
     "sonar_get_hits": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]),
     "sonar_get_echoes": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
     "sonar_get_stats": (C.c_int, [C.c_void_p, C.POINTER(sonar_stats)]),
+    "sonar_cloud_noalloc": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(sonar_params), C.POINTER(sonar_pose),
+                                      C.c_void_p, C.c_int64, C.POINTER(C.c_int64), C.c_void_p]),
 }
 
 
