@@ -150,6 +150,10 @@ SONAR_API const char* sonar_last_error(const sonar_ctx* ctx);
 #define SONAR_OPT_TIMING 2
 #define SONAR_OPT_GRAPH 3
 #define SONAR_OPT_TILE_N 4
+/* SONAR_OPT_SYNTH: 0 (default) synthesises element echoes on the tensor cores where the
+   array allows it (nx a power of two, ny % 8 == 0, ny <= 32), 1 always uses the FP32
+   SIMT synthesis kernel. */
+#define SONAR_OPT_SYNTH 5
 SONAR_API int sonar_set_option(sonar_ctx* ctx, int32_t option, int64_t value);
 
 /* ---------------------------------------------------------------- scene */

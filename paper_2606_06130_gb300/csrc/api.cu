@@ -43,6 +43,7 @@ struct sonar_ctx {
   std::string err;
   bool debug = false, timing = false, use_graph = true;
   int tile_opt = 0;
+  int synth_opt = 0;  // 0: tensor-core synthesis where supported, 1: FP32 SIMT synthesis
 
   // scene
   bool has_scene = false;
@@ -52,6 +53,8 @@ struct sonar_ctx {
   int32_t* tri_prim = nullptr;
   float* tri_mu = nullptr;
   uint8_t* tri_flags = nullptr;
+  double4* tri_plane = nullptr;
+  float* tri_inv_n = nullptr;
   BvhNode* nodes = nullptr;
   float4* points = nullptr;
   double4* planes = nullptr;
@@ -75,6 +78,7 @@ struct sonar_ctx {
   DevPose* poses = nullptr;
   HitRec* hits = nullptr;
   HitRec* sorted = nullptr;
+  int32_t* sorted_n = nullptr;
   double* dbg_tau = nullptr;
   int64_t hit_cap = 0;
   unsigned long long* n_hits = nullptr;
@@ -279,8 +283,8 @@ int ensure_tables(sonar_ctx* ctx, const sonar_params* p, const Derived& d) {
   k.clear();
   key_add(k, p->pulse_s); key_add(k, p->bw_hz);
   if (k != ctx->rtab_key) {
-    if (!ctx->rtab) CU(cudaMalloc(&ctx->rtab, sizeof(float2) * (kRTab + 1)));
-    CU(launch_rtab(ctx->rtab, p->pulse_s, p->bw_hz, d.dt, ctx->stream));
+    if (!ctx->rtab) CU(cudaMalloc(&ctx->rtab, sizeof(float2) * (kRTab + 1 + kRTabS + 5)));
+    CU(launch_rtab(ctx->rtab, ctx->rtab + kRTab + 1, p->pulse_s, p->bw_hz, ctx->stream));
     ctx->rtab_key = k;
   }
   k.clear();
@@ -350,8 +354,9 @@ int ensure_workspace(sonar_ctx* ctx, int P, const Derived& d) {
   int64_t hit_need = (int64_t)P * d.hit_cap_per_ping;
   if (hit_need < 1) hit_need = 1;
   if (hit_need > ctx->ws_hits || !ctx->hits) {
-    int64_t c0 = 0, c1 = 0, c2 = 0;
-    dfree(ctx->hits); dfree(ctx->sorted); dfree(ctx->dbg_tau);
+    int64_t c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+    dfree(ctx->hits); dfree(ctx->sorted); dfree(ctx->dbg_tau); dfree(ctx->sorted_n);
+    if ((rc = grow(ctx, ctx->sorted_n, c3, hit_need, sizeof(int32_t), false))) return rc;
     if ((rc = grow(ctx, ctx->hits, c0, hit_need, sizeof(HitRec), false))) return rc;
     if ((rc = grow(ctx, ctx->sorted, c1, hit_need, sizeof(HitRec), false))) return rc;
     if ((rc = grow(ctx, ctx->dbg_tau, c2, hit_need, sizeof(double), false))) return rc;
@@ -366,7 +371,8 @@ int ensure_workspace(sonar_ctx* ctx, int P, const Derived& d) {
     if ((rc = grow(ctx, ctx->offsets, c1, bins, sizeof(int32_t), false))) return rc;
     ctx->ws_bins = bins;
   }
-  int64_t s_need = ((int64_t)P * d.nr_pad + 2 * kPad) * d.M;
+  // guard rows: taps past the last ping and whole tensor-core tiles (up to 32 rows)
+  int64_t s_need = ((int64_t)P * d.nr_pad + 2 * kPad + 64) * d.M;
   if (s_need > ctx->ws_s || !ctx->S) {
     int64_t c0 = 0;
     dfree(ctx->S);
@@ -444,6 +450,7 @@ int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, cons
   ta.ssp_z0 = d.ssp_z0;
   ta.ssp_c0 = d.ssp_c0;
   ta.ssp_g = d.ssp_g;
+  ta.inv_c0 = 1.0 / d.ssp_c0;
   ta.T_stop = d.T_stop;
   ta.t0 = d.t0;
   ta.inv_dt = 1.0 / d.dt;
@@ -460,24 +467,30 @@ int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, cons
   CU(launch_points(ta, st));
   mark(1);
   const int32_t n_bins = P * d.nr_pad;
-  CU(launch_bin(ctx->hits, ctx->n_hits, n_bins, ctx->counts, ctx->offsets, ctx->sorted, ctx->sm_count, st));
+  CU(launch_bin(ctx->hits, ctx->n_hits, n_bins, ctx->counts, ctx->offsets, ctx->sorted, ctx->sorted_n, ctx->sm_count,
+                st));
   CU(cudaMemsetAsync(ctx->S, 0, sizeof(float2) * ctx->s_elems, st));
   CU(cudaMemsetAsync(ctx->keys, 0, sizeof(unsigned long long) * (size_t)P * d.nb, st));
   CU(cudaMemsetAsync(ctx->pmax, 0, sizeof(unsigned) * P, st));
   mark(2);
   SynthArgs sa;
   sa.hits_sorted = ctx->sorted;
+  sa.sorted_n = ctx->sorted_n;
   sa.n_valid = ctx->offsets + n_bins;
   sa.rtab = ctx->rtab;
   sa.rtab_scale = (float)(d.dt * kRTab / (2.0 * p->pulse_s));
+  sa.rtab_s = ctx->rtab + kRTab + 1;
+  sa.rtab_s_scale = (float)(d.dt * kRTabS / (2.0 * p->pulse_s));
   sa.taps = d.taps;
   sa.nx = p->nx;
   sa.ny = p->ny;
   sa.pitch_over_lambda = (float)d.pitch_over_lambda;
   sa.S = ctx->S;
   sa.total_rows = (int64_t)P * d.nr_pad;
+  sa.n_pass = p->precision == SONAR_FP32 ? 3 : 1;
   sa.err = ctx->err_dev;
-  CU(launch_synth(sa, ctx->sm_count, st));
+  if (ctx->synth_opt == 0 && synth_tc_supported(p->nx, p->ny, d.taps)) CU(launch_synth_tc(sa, ctx->sm_count, st));
+  else CU(launch_synth(sa, ctx->sm_count, st));
   mark(3);
   ConvertArgs ca;
   ca.S = ctx->S;
@@ -601,7 +614,8 @@ int run(sonar_ctx* ctx, const sonar_pose* poses, int P, const sonar_params* p, c
   if (ctx->use_graph && !timed) {
     std::vector<uint8_t> k;
     key_add(k, P); key_add(k, *p); key_add(k, o.env); key_add(k, o.cloud); key_add(k, o.cap);
-    key_add(k, ctx->debug); key_add(k, ctx->timing); key_add(k, ctx->scene_version); key_add(k, d.c_ref);
+    key_add(k, ctx->debug); key_add(k, ctx->timing); key_add(k, ctx->synth_opt); key_add(k, ctx->scene_version);
+    key_add(k, d.c_ref);
     if (ssp) {
       key_add(k, ssp->n_nodes);
       for (int i = 0; i < ssp->n_nodes; ++i) { key_add(k, ssp->c[i]); if (ssp->z) key_add(k, ssp->z[i]); }
@@ -686,7 +700,7 @@ int sonar_create(sonar_ctx** out, int device, void* cuda_stream) {
   if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return SONAR_E_CUDA;
   if (!(prop.major == 10 && prop.minor == 3)) return SONAR_E_UNSUPPORTED;
   if (cudaSetDevice(device) != cudaSuccess) return SONAR_E_CUDA;
-  if (prepare_gemm() != cudaSuccess) return SONAR_E_CUDA;
+  if (prepare_gemm() != cudaSuccess || prepare_synth_tc() != cudaSuccess) return SONAR_E_CUDA;
   sonar_ctx* c = new (std::nothrow) sonar_ctx();
   if (!c) return SONAR_E_NOMEM;
   c->device = device;
@@ -721,6 +735,10 @@ int sonar_set_option(sonar_ctx* ctx, int32_t option, int64_t value) {
     case SONAR_OPT_DEBUG: ctx->debug = value != 0; break;
     case SONAR_OPT_TIMING: ctx->timing = value != 0; break;
     case SONAR_OPT_GRAPH: ctx->use_graph = value != 0; break;
+    case SONAR_OPT_SYNTH:
+      if (value != 0 && value != 1) return fail(ctx, SONAR_E_ARG, "synthesis option must be 0 or 1");
+      ctx->synth_opt = (int)value;
+      break;
     case SONAR_OPT_TILE_N:
       if (value != 0 && value != 128 && value != 256) return fail(ctx, SONAR_E_ARG, "tile_n must be 0, 128 or 256");
       ctx->tile_opt = (int)value;
@@ -733,6 +751,7 @@ int sonar_set_option(sonar_ctx* ctx, int32_t option, int64_t value) {
 
 static void free_scene(sonar_ctx* c) {
   dfree(c->tri32); dfree(c->triv); dfree(c->tri_prim); dfree(c->tri_mu); dfree(c->tri_flags);
+  dfree(c->tri_plane); dfree(c->tri_inv_n);
   dfree(c->nodes); dfree(c->points); dfree(c->planes);
   c->has_scene = false;
   memset(&c->sc, 0, sizeof(c->sc));
@@ -752,7 +771,8 @@ int sonar_destroy(sonar_ctx* c) {
   dfree(c->ray_dirs); dfree(c->row_domega); dfree(c->y_hi); dfree(c->y_lo); dfree(c->rtab); dfree(c->taper_dev);
   if (c->raw_host) cudaFreeHost(c->raw_host);
   if (c->n_cloud_host) cudaFreeHost(c->n_cloud_host);
-  dfree(c->raw_dev); dfree(c->poses); dfree(c->hits); dfree(c->sorted); dfree(c->dbg_tau); dfree(c->n_hits);
+  dfree(c->raw_dev); dfree(c->poses); dfree(c->hits); dfree(c->sorted); dfree(c->sorted_n); dfree(c->dbg_tau);
+  dfree(c->n_hits);
   dfree(c->counts); dfree(c->offsets); dfree(c->S); dfree(c->x_hi); dfree(c->x_lo); dfree(c->gain);
   dfree(c->env_stage); dfree(c->keys); dfree(c->pmax); dfree(c->cloud_stage); dfree(c->n_cloud_dev); dfree(c->err_dev);
   delete c;
@@ -793,7 +813,8 @@ int sonar_scene_upload(sonar_ctx* ctx, const float* verts, int64_t n_verts, cons
     CU(cudaMemcpyAsync(dm, mu, sizeof(float) * n_tris, cudaMemcpyHostToDevice, ctx->stream));
     CU(cudaMemcpyAsync(df, flags, n_tris, cudaMemcpyHostToDevice, ctx->stream));
     cudaError_t e = build_bvh(dv, dt, dm, df, (int32_t)n_tris, &ctx->tri32, &ctx->triv, &ctx->tri_prim, &ctx->tri_mu,
-                              &ctx->tri_flags, &ctx->nodes, &ctx->sc.root, ctx->stream);
+                              &ctx->tri_flags, &ctx->tri_plane, &ctx->tri_inv_n, &ctx->nodes, &ctx->sc.root,
+                              ctx->stream);
     cudaFree(dv);
     cudaFree(dt);
     cudaFree(dm);
@@ -815,6 +836,8 @@ int sonar_scene_upload(sonar_ctx* ctx, const float* verts, int64_t n_verts, cons
   ctx->sc.tri_prim = ctx->tri_prim;
   ctx->sc.tri_mu = ctx->tri_mu;
   ctx->sc.tri_flags = ctx->tri_flags;
+  ctx->sc.tri_plane = ctx->tri_plane;
+  ctx->sc.tri_inv_n = ctx->tri_inv_n;
   ctx->sc.nodes = ctx->nodes;
   ctx->sc.n_tris = (int32_t)n_tris;
   ctx->sc.points = ctx->points;

@@ -17,91 +17,17 @@
 #include <math.h>
 
 #include "common.cuh"
+#include "tcgen05.cuh"
 
 namespace sonar {
 namespace {
+using namespace tc;
 
 constexpr int BM = 128;
 constexpr int BK = 64;
 constexpr int STAGES = 4;
 constexpr int kGemmThreads = 192;  // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
 
-// ----------------------------------------------------------------- PTX wrappers
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait: gives up after ~2^31 cycles (about a second), flags the error.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err) {
-  if (mbar_try(bar, parity)) return true;
-  long long t0 = clock64();
-  for (;;) {
-    for (int i = 0; i < 64; ++i)
-      if (mbar_try(bar, parity)) return true;
-    if (clock64() - t0 > (1ll << 31)) {
-      atomicOr(err, kErrTimeout);
-      return false;
-    }
-  }
-}
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
-      : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-      ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
-      : "memory");
-}
-
-// UMMA shared-memory descriptor, K-major, 128-byte swizzle: 8-row core groups 1024 B
-// apart (SBO), leading offset unused (1), descriptor version 1 (bits 46-47).
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
-  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
-         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
-}
-// Instruction descriptor, kind::f16: D F32, A/B F16 (0) or BF16 (1), both K-major.
-__host__ __device__ constexpr uint32_t make_idesc(int ab_format, int M, int N) {
-  return (1u << 4) | ((uint32_t)ab_format << 7) | ((uint32_t)ab_format << 10) | ((uint32_t)(N >> 3) << 17) |
-         ((uint32_t)(M >> 4) << 24);
-}
-
-#define TMEM_LD_32(taddr, r)                                                                                  \
-  asm volatile(                                                                                               \
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17," \
-      "%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"                                        \
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),       \
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), \
-        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),            \
-        "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),            \
-        "=r"(r[30]), "=r"(r[31])                                                                              \
-      : "r"(taddr))
 
 // Tile order: groups of up to 16 row tiles; inside a group the column tiles run in
 // the outer loop, so concurrently running CTAs share one steering block through L2.
@@ -316,49 +242,61 @@ __global__ void k_steer(SteerArgs a) {
 
 // ----------------------------------------------------------------- peaks -> cloud
 // Per ping: decode each beam's packed (value, first index) maximum, apply the absolute
-// or ping-relative threshold, and write points in beam order.
+// or ping-relative threshold, and write points in beam order. Block-wide exclusive scan
+// of the keep flags by warp shuffles; positions in FP32 (a 15 m range keeps them
+// within ~1e-6 m).
 __global__ void __launch_bounds__(1024) k_peaks(PeakArgs a) {
-  __shared__ int s_scan[1024];
+  __shared__ int s_warp[32];
   __shared__ long long s_base;
-  const int p = blockIdx.x, t = threadIdx.x;
+  const int p = blockIdx.x, t = threadIdx.x, lane = t & 31, wid = t >> 5;
   const int Nb = a.n_beam_az * a.n_beam_el;
   const float vmax = __uint_as_float(a.ping_max[p]);
   const float thr = a.thr_mode == 1 ? a.thr * vmax : a.thr;
   const DevPose& P = a.poses[p];
+  float R[9], T[3];
+  for (int k = 0; k < 9; ++k) R[k] = (float)P.R[k];
+  for (int k = 0; k < 3; ++k) T[k] = (float)P.t[k];
+  const float daz = (float)(a.hfov / a.n_beam_az), del = (float)(a.vfov / a.n_beam_el);
   if (t == 0) s_base = 0;
   __syncthreads();
   for (int b0 = 0; b0 < Nb; b0 += 1024) {
     const int b = b0 + t;
-    unsigned long long key = b < Nb ? a.peak_keys[(size_t)p * Nb + b] : 0ull;
+    const unsigned long long key = b < Nb ? a.peak_keys[(size_t)p * Nb + b] : 0ull;
     const float val = __uint_as_float((uint32_t)(key >> 32));
     const bool keep = key != 0ull && val >= thr;
-    s_scan[t] = keep ? 1 : 0;
+    const unsigned ballot = __ballot_sync(0xffffffffu, keep);
+    const int in_warp = __popc(ballot & ((1u << lane) - 1u));
+    if (lane == 0) s_warp[wid] = __popc(ballot);
     __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {
-      int v = t >= off ? s_scan[t - off] : 0;
-      __syncthreads();
-      s_scan[t] += v;
-      __syncthreads();
+    if (wid == 0) {
+      int v = s_warp[lane], x = v;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      s_warp[lane] = x - v;  // exclusive prefix of warp counts
     }
-    const long long pos = s_base + s_scan[t] - (keep ? 1 : 0);
+    __syncthreads();
+    const long long pos = s_base + s_warp[wid] + in_warp;
     if (keep && pos < a.cap) {
       const int n = (int)(0xFFFFFFFFu - (uint32_t)(key & 0xFFFFFFFFull));
       const int bi = b % a.n_beam_az, bj = b / a.n_beam_az;
-      const double az = -a.hfov / 2 + (bi + 0.5) * a.hfov / a.n_beam_az;
-      const double el = -a.vfov / 2 + (bj + 0.5) * a.vfov / a.n_beam_el;
-      const double r = a.r_min + (n + 0.5) * a.dr;
-      const double v[3] = {r * cos(el) * cos(az), r * cos(el) * sin(az), r * sin(el)};
+      float saz, caz, sel, cel;
+      sincosf((float)(-a.hfov / 2) + ((float)bi + 0.5f) * daz, &saz, &caz);
+      sincosf((float)(-a.vfov / 2) + ((float)bj + 0.5f) * del, &sel, &cel);
+      const float r = (float)a.r_min + ((float)n + 0.5f) * (float)a.dr;
+      const float v0 = r * cel * caz, v1 = r * cel * saz, v2 = r * sel;
       sonar_point pt;
-      pt.x = (float)(P.R[0] * v[0] + P.R[1] * v[1] + P.R[2] * v[2] + P.t[0]);
-      pt.y = (float)(P.R[3] * v[0] + P.R[4] * v[1] + P.R[5] * v[2] + P.t[1]);
-      pt.z = (float)(P.R[6] * v[0] + P.R[7] * v[1] + P.R[8] * v[2] + P.t[2]);
+      pt.x = R[0] * v0 + R[1] * v1 + R[2] * v2 + T[0];
+      pt.y = R[3] * v0 + R[4] * v1 + R[5] * v2 + T[1];
+      pt.z = R[6] * v0 + R[7] * v1 + R[8] * v2 + T[2];
       pt.intensity = val;
       pt.beam = b;
       pt.bin = n;
       a.cloud[(size_t)p * a.cap + pos] = pt;
     }
     __syncthreads();
-    if (t == 1023) s_base += s_scan[1023];
+    if (t == 1023) s_base = pos + (keep ? 1 : 0);
     __syncthreads();
   }
   if (t == 0) a.n_cloud[p] = s_base;

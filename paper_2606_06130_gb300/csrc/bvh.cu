@@ -116,7 +116,8 @@ __global__ void k_hierarchy(const unsigned long long* keys, int n, int2* child, 
 
 __global__ void k_leaves(const float* V, const int32_t* T, const float* mu, const uint8_t* fl,
                          const unsigned long long* keys, int n, float4* lbox_lo, float4* lbox_hi,
-                         float4* tri32, float* triv, int32_t* tri_prim, float* tri_mu, uint8_t* tri_flags) {
+                         float4* tri32, float* triv, int32_t* tri_prim, float* tri_mu, uint8_t* tri_flags,
+                         double4* tri_plane, float* tri_inv_n) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   int prim = (int)(keys[k] & 0xffffffffu);
@@ -132,6 +133,16 @@ __global__ void k_leaves(const float* V, const int32_t* T, const float* mu, cons
   tri_prim[k] = prim;
   tri_mu[k] = mu[prim];
   tri_flags[k] = fl[prim];
+  // FP64 plane: float vertex differences are exact in FP64; unrounded product order
+  const double e1x = __dsub_rn(b.x, a.x), e1y = __dsub_rn(b.y, a.y), e1z = __dsub_rn(b.z, a.z);
+  const double e2x = __dsub_rn(c.x, a.x), e2y = __dsub_rn(c.y, a.y), e2z = __dsub_rn(c.z, a.z);
+  const double nx = __dsub_rn(__dmul_rn(e1y, e2z), __dmul_rn(e1z, e2y));
+  const double ny = __dsub_rn(__dmul_rn(e1z, e2x), __dmul_rn(e1x, e2z));
+  const double nz = __dsub_rn(__dmul_rn(e1x, e2y), __dmul_rn(e1y, e2x));
+  const double d0 = __dadd_rn(__dadd_rn(__dmul_rn(nx, (double)a.x), __dmul_rn(ny, (double)a.y)), __dmul_rn(nz, (double)a.z));
+  tri_plane[k] = make_double4(nx, ny, nz, d0);
+  const double nn = __dadd_rn(__dadd_rn(__dmul_rn(nx, nx), __dmul_rn(ny, ny)), __dmul_rn(nz, nz));
+  tri_inv_n[k] = nn > 0.0 ? (float)(1.0 / sqrt(nn)) : 0.f;
 }
 
 __global__ void k_refit(int n, const int2* child, const int* par_int, const int* par_leaf,
@@ -189,7 +200,8 @@ __global__ void k_single(int2* child) { child[0] = make_int2(~0, INT_MIN); }
 
 cudaError_t build_bvh(const float* V, const int32_t* T, const float* mu, const uint8_t* fl, int32_t n,
                       float4** tri32, float** triv, int32_t** tri_prim, float** tri_mu,
-                      uint8_t** tri_flags, BvhNode** nodes, int32_t* root, cudaStream_t st) {
+                      uint8_t** tri_flags, double4** tri_plane, float** tri_inv_n, BvhNode** nodes, int32_t* root,
+                      cudaStream_t st) {
   int n_pow2 = 1;
   while (n_pow2 < n) n_pow2 <<= 1;
   int n_int = n > 1 ? n - 1 : 1;
@@ -198,6 +210,8 @@ cudaError_t build_bvh(const float* V, const int32_t* T, const float* mu, const u
   CK(cudaMalloc(tri_prim, sizeof(int32_t) * n));
   CK(cudaMalloc(tri_mu, sizeof(float) * n));
   CK(cudaMalloc(tri_flags, n));
+  CK(cudaMalloc(tri_plane, sizeof(double4) * n));
+  CK(cudaMalloc(tri_inv_n, sizeof(float) * n));
   CK(cudaMalloc(nodes, sizeof(BvhNode) * n_int));
   float* bb;
   unsigned long long* keys;
@@ -225,7 +239,7 @@ cudaError_t build_bvh(const float* V, const int32_t* T, const float* mu, const u
     for (int j = k >> 1; j > 0; j >>= 1)
       k_bitonic<<<(int)ceil_div(n_pow2, B), B, 0, st>>>(keys, n_pow2, k, j);
   k_leaves<<<(int)ceil_div(n, B), B, 0, st>>>(V, T, mu, fl, keys, n, lbl, lbh, *tri32, *triv, *tri_prim,
-                                               *tri_mu, *tri_flags);
+                                               *tri_mu, *tri_flags, *tri_plane, *tri_inv_n);
   if (n > 1) {
     k_hierarchy<<<(int)ceil_div(n - 1, B), B, 0, st>>>(keys, n, child, par_int, par_leaf);
     k_refit<<<(int)ceil_div(n, B), B, 0, st>>>(n, child, par_int, par_leaf, lbl, lbh, ibl, ibh, flags);

@@ -16,7 +16,8 @@
 namespace sonar {
 
 constexpr int kPad = 16;          // guard rows before/after each ping's samples in S
-constexpr int kRTab = 16384;      // intervals of the pulse-autocorrelation table
+constexpr int kRTab = 16384;      // intervals of the pulse-autocorrelation table (linear)
+constexpr int kRTabS = 512;       // intervals of the small table (cubic, 2 guard entries per side)
 constexpr double kEpsHit = 1e-7;  // minimum hit distance along a segment [m]
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kMaxStack = 64;     // BVH traversal stack depth
@@ -53,6 +54,8 @@ struct DevScene {
   const int32_t* tri_prim; // leaf -> original triangle id
   const float* tri_mu;     // leaf order
   const uint8_t* tri_flags;// leaf order
+  const double4* tri_plane;// leaf order: n = (b - a) x (c - a) in FP64 (unnormalised), n . a
+  const float* tri_inv_n;  // leaf order: 1 / |n|
   const BvhNode* nodes;
   int32_t n_tris;
   int32_t root;            // internal node index, or ~leaf for a one-triangle scene
@@ -79,6 +82,7 @@ struct TraceArgs {
   double surface_z, r_surface, r_seabed, alpha;
   uint32_t seed32;
   double ssp_z0, ssp_c0, ssp_g;  // c(z) = c0 + g (z - z0)
+  double inv_c0;                 // 1 / c0 (isovelocity one-way time per metre)
   double T_stop;                 // one-way time limit
   double t0, inv_dt, hw, f0;     // sample-grid mapping of delays
   int32_t nr_pad;
@@ -113,8 +117,8 @@ namespace sonar {
 struct BvhBuild;
 cudaError_t build_bvh(const float* d_verts, const int32_t* d_tris, const float* d_mu,
                       const uint8_t* d_flags, int32_t n_tris, float4** tri32, float** triv,
-                      int32_t** tri_prim, float** tri_mu, uint8_t** tri_flags, BvhNode** nodes,
-                      int32_t* root, cudaStream_t st);
+                      int32_t** tri_prim, float** tri_mu, uint8_t** tri_flags, double4** tri_plane,
+                      float** tri_inv_n, BvhNode** nodes, int32_t* root, cudaStream_t st);
 cudaError_t launch_ray_table(double* dirs, float* row_domega, int32_t n_ray_az, int32_t n_ray_el,
                              int32_t n_sub, double hfov, double vfov, uint32_t seed32,
                              cudaStream_t st);
@@ -124,21 +128,28 @@ cudaError_t launch_points(const TraceArgs& a, cudaStream_t st);
 
 struct SynthArgs {
   const HitRec* hits_sorted;
+  const int32_t* sorted_n;  // first-tap row of each sorted hit (compact copy of nglob)
   const int32_t* n_valid;   // hits with at least one tap in range (binning total)
   const float2* rtab;       // [kRTab + 1]
   float rtab_scale;         // table index per unit of (u0 + i)
+  const float2* rtab_s;     // [kRTabS + 5], entry i at u = -T_p + (i - 2) 2 T_p / kRTabS
+  float rtab_s_scale;
   int32_t taps;             // W
   int32_t nx, ny;
   float pitch_over_lambda;  // element pitch in carrier wavelengths (at c_ref)
   float2* S;                // [n_pings * nr_pad][M] element echoes
   int64_t total_rows;       // n_pings * nr_pad
+  int32_t n_pass;           // tensor-core synthesis: 3 (BF16 hi/lo split) or 1
   int* err;
 };
 cudaError_t launch_bin(const HitRec* hits, const unsigned long long* n_hits, int32_t n_bins,
-                       int32_t* counts, int32_t* offsets, HitRec* sorted, int sm_count,
-                       cudaStream_t st);
+                       int32_t* counts, int32_t* offsets, HitRec* sorted, int32_t* sorted_n,
+                       int sm_count, cudaStream_t st);
 cudaError_t launch_synth(const SynthArgs& a, int sm_count, cudaStream_t st);
-cudaError_t launch_rtab(float2* rtab, double pulse, double bw, double dt, cudaStream_t st);
+bool synth_tc_supported(int nx, int ny, int taps);
+cudaError_t prepare_synth_tc();
+cudaError_t launch_synth_tc(const SynthArgs& a, int sm_count, cudaStream_t st);
+cudaError_t launch_rtab(float2* rtab, float2* rtab_s, double pulse, double bw, cudaStream_t st);
 
 struct ConvertArgs {
   const float2* S;          // [n_pings][nr_pad][M]

@@ -12,11 +12,18 @@
 namespace sonar {
 namespace {
 
+// Hits arrive in ray order, so neighbouring lanes usually share a bin: one atomic per
+// distinct bin in the warp (__match_any_sync), added by the group's lowest lane.
 __global__ void k_hist(const HitRec* hits, const unsigned long long* n_hits, int32_t n_bins, int32_t* counts) {
-  int64_t n = (int64_t)*n_hits;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    int g = hits[i].nglob;
-    if (g >= 0 && g < n_bins) atomicAdd(&counts[g], 1);
+  const int64_t n = (int64_t)*n_hits;
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); i0 < n; i0 += stride) {
+    const int64_t i = i0 + lane;
+    int g = i < n ? hits[i].nglob : -1;
+    if (g >= n_bins) g = -1;
+    const unsigned grp = __match_any_sync(0xffffffffu, g);
+    if (g >= 0 && lane == __ffs(grp) - 1) atomicAdd(&counts[g], __popc(grp));
   }
 }
 
@@ -47,11 +54,28 @@ __global__ void __launch_bounds__(1024) k_scan(const int32_t* counts, int32_t n_
 }
 
 __global__ void k_scatter(const HitRec* hits, const unsigned long long* n_hits, int32_t n_bins, int32_t* cursor,
-                          HitRec* sorted) {
-  int64_t n = (int64_t)*n_hits;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    HitRec h = hits[i];
-    if (h.nglob >= 0 && h.nglob < n_bins) sorted[atomicAdd(&cursor[h.nglob], 1)] = h;
+                          HitRec* sorted, int32_t* sorted_n) {
+  const int64_t n = (int64_t)*n_hits;
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); i0 < n; i0 += stride) {
+    const int64_t i = i0 + lane;
+    HitRec h;
+    int g = -1;
+    if (i < n) {
+      h = hits[i];
+      g = h.nglob < n_bins ? h.nglob : -1;
+    }
+    const unsigned grp = __match_any_sync(0xffffffffu, g);
+    const int leader = __ffs(grp) - 1;
+    int base = 0;
+    if (g >= 0 && lane == leader) base = atomicAdd(&cursor[g], __popc(grp));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (g >= 0) {
+      const int pos = base + __popc(grp & ((1u << lane) - 1u));
+      sorted[pos] = h;
+      sorted_n[pos] = g;
+    }
   }
 }
 
@@ -203,10 +227,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_synth(SynthArgs a, const int32_
 // FP64 from the closed form: the Hann window as three complex exponentials turns
 // R(u) into nine exponential integrals over the overlap of the two pulse supports.
 __device__ inline double sinc_d(double x) { return fabs(x) < 1e-4 ? 1.0 - x * x / 6.0 : sin(x) / x; }
-__global__ void k_rtab(float2* tab, double T, double B) {
+__global__ void k_rtab(float2* tab, int n_int, int guard, double T, double B) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i > kRTab) return;
-  double u = -T + 2.0 * T * (double)i / (double)kRTab;
+  if (i > n_int + 2 * guard) return;
+  double u = -T + 2.0 * T * (double)(i - guard) / (double)n_int;
   if (!(fabs(u) < T)) { tab[i] = make_float2(0.f, 0.f); return; }
   const double kappa = B / T, Om = 2.0 * kPi / T, E = 3.0 * T / 8.0;
   const double L = fmax(-T / 2, -T / 2 - u), U = fmin(T / 2, T / 2 - u);
@@ -281,13 +305,13 @@ __global__ void k_gain_pow2(float* gain, int n, int mode) {
 }  // namespace
 
 cudaError_t launch_bin(const HitRec* hits, const unsigned long long* n_hits, int32_t n_bins, int32_t* counts,
-                       int32_t* offsets, HitRec* sorted, int sm_count, cudaStream_t st) {
+                       int32_t* offsets, HitRec* sorted, int32_t* sorted_n, int sm_count, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(int32_t) * n_bins, st);
   if (e != cudaSuccess) return e;
   k_hist<<<sm_count * 8, 256, 0, st>>>(hits, n_hits, n_bins, counts);
   k_scan<<<1, 1024, 0, st>>>(counts, n_bins, offsets, counts);
   // counts now doubles as the scatter cursor
-  k_scatter<<<sm_count * 8, 256, 0, st>>>(hits, n_hits, n_bins, counts, sorted);
+  k_scatter<<<sm_count * 8, 256, 0, st>>>(hits, n_hits, n_bins, counts, sorted, sorted_n);
   return cudaGetLastError();
 }
 
@@ -299,8 +323,9 @@ cudaError_t launch_synth(const SynthArgs& a, int sm_count, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_rtab(float2* rtab, double pulse, double bw, double, cudaStream_t st) {
-  k_rtab<<<(kRTab + 1 + 255) / 256, 256, 0, st>>>(rtab, pulse, bw);
+cudaError_t launch_rtab(float2* rtab, float2* rtab_s, double pulse, double bw, cudaStream_t st) {
+  k_rtab<<<(kRTab + 1 + 255) / 256, 256, 0, st>>>(rtab, kRTab, 0, pulse, bw);
+  k_rtab<<<(kRTabS + 5 + 255) / 256, 256, 0, st>>>(rtab_s, kRTabS, 2, pulse, bw);
   return cudaGetLastError();
 }
 

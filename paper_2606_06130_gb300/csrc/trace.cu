@@ -8,9 +8,12 @@
 // sound-speed profile as exact circular arcs intersected chord by chord.
 //
 // Precision: the traversal culls in FP32 with widened boxes and a slack barycentric
-// test; every triangle that survives the slack test is decided by an FP64 ray/triangle
-// test written with explicitly rounded operations (no contraction), so the chosen
-// primitive and its distance are those of an FP64 evaluation of the same test.
+// test. A triangle whose FP32 barycentrics lie inside by more than the slack is a hit
+// in FP64 too; every other survivor (near an edge, nearly parallel, near an interval
+// end) is decided by an FP64 ray/triangle test written with explicitly rounded
+// operations, and competing hits closer than the FP32 distance error are ordered by
+// their FP64 distances. The distance of the chosen hit is always FP64 (from the
+// stored FP64 plane), so delays and carrier phase keep FP64 accuracy.
 #include "common.cuh"
 
 namespace sonar {
@@ -47,26 +50,43 @@ __device__ __forceinline__ D3 tri_vert(const float* v, int k) {
   return d3((double)v[3 * k], (double)v[3 * k + 1], (double)v[3 * k + 2]);
 }
 
-// FP64 two-sided ray/triangle test (Moller-Trumbore), inclusive edges.
+// FP64 two-sided ray/triangle test (Moller-Trumbore), inclusive edges. One reciprocal
+// of the determinant replaces three divisions (FP64 division is a long sequence on this
+// part); u, v, t differ from divided values by at most an ulp.
 __device__ bool tri_test64(const float* tv, D3 o, D3 d, double& t) {
   D3 a = tri_vert(tv, 0), b = tri_vert(tv, 1), c = tri_vert(tv, 2);
   D3 e1 = sub(b, a), e2 = sub(c, a);
   D3 p = cross(d, e2);
   double det = dot(e1, p);
   if (det == 0.0) return false;
+  const double inv = dd(1.0, det);
   D3 s = sub(o, a);
-  double u = dd(dot(s, p), det);
+  double u = dm(dot(s, p), inv);
   if (!(u >= 0.0 && u <= 1.0)) return false;
   D3 q = cross(s, e1);
-  double v = dd(dot(d, q), det);
+  double v = dm(dot(d, q), inv);
   if (!(v >= 0.0 && da(u, v) <= 1.0)) return false;
-  t = dd(dot(e2, q), det);
+  t = dm(dot(e2, q), inv);
   return true;
 }
 
-__device__ D3 tri_normal64(const float* tv) {
-  D3 a = tri_vert(tv, 0), b = tri_vert(tv, 1), c = tri_vert(tv, 2);
-  D3 n = cross(sub(b, a), sub(c, a));
+__device__ __forceinline__ double4 load_plane(const DevScene& sc, int leaf) {
+  const double2* p = reinterpret_cast<const double2*>(sc.tri_plane + leaf);
+  const double2 a = __ldg(p), b = __ldg(p + 1);
+  return make_double4(a.x, a.y, b.x, b.y);
+}
+
+// |cos| of the incidence angle from the stored FP64 plane normal: the dot product in
+// FP64 (grazing incidence keeps its relative accuracy), the scaling in FP32.
+__device__ __forceinline__ float kinc32(const DevScene& sc, int leaf, D3 d) {
+  const double4 P = load_plane(sc, leaf);
+  return fabsf((float)dot(d, d3(P.x, P.y, P.z))) * __ldg(&sc.tri_inv_n[leaf]);
+}
+
+// Unit geometric normal (b - a) x (c - a) / |.| in FP64, for specular reflection.
+__device__ D3 tri_normal64(const DevScene& sc, int leaf) {
+  const double4 P = load_plane(sc, leaf);
+  const D3 n = d3(P.x, P.y, P.z);
   double l = __dsqrt_rn(dot(n, n));
   return d3(dd(n.x, l), dd(n.y, l), dd(n.z, l));
 }
@@ -91,10 +111,19 @@ struct Hit {
   int leaf;
 };
 
-// Nearest triangle with FP64 distance in (kEpsHit, tmax], excluding `exclude`
-// (original id), ties to the lowest id.
+// FP64 distance to the triangle's plane: (n . a - n . o) / (n . d).
+__device__ __forceinline__ double plane_t(const DevScene& sc, int leaf, D3 o, D3 d) {
+  const double4 P = load_plane(sc, leaf);
+  const D3 n = d3(P.x, P.y, P.z);
+  return dd(ds(P.w, dot(n, o)), dot(n, d));
+}
+
+// Nearest triangle with FP64 distance in (tmin, tmax], excluding `exclude` (original
+// id), ties to the lowest id. The distance of the returned hit is FP64.
 __device__ Hit closest_hit(const DevScene& sc, D3 o, D3 d, double tmin, double tmax, int exclude, int* err) {
   Hit best = {INFINITY, -1, -1};
+  bool best_exact = true;
+  float best_t32 = INFINITY;
   if (sc.n_tris == 0) return best;
   Ray32 r;
   r.ox = (float)o.x; r.oy = (float)o.y; r.oz = (float)o.z;
@@ -107,7 +136,7 @@ __device__ Hit closest_hit(const DevScene& sc, D3 o, D3 d, double tmin, double t
   int node = sc.root;
   const int max_visits = 2 * sc.n_tris + 64;  // a tree visits each node at most once
   for (int visits = 0;; ++visits) {
-    if (visits > max_visits) { atomicOr(err, kErrLoop); return best; }
+    if (visits > max_visits) { atomicOr(err, kErrLoop); break; }
     const BvhNode* nd = sc.nodes + node;
     float4 A = __ldg(&nd->a), B = __ldg(&nd->b), Cz = __ldg(&nd->c);
     int4 ch = __ldg(&nd->d);
@@ -127,7 +156,8 @@ __device__ Hit closest_hit(const DevScene& sc, D3 o, D3 d, double tmin, double t
       float px = r.dy * e2.z - r.dz * e2.y, py = r.dz * e2.x - r.dx * e2.z, pz = r.dx * e2.y - r.dy * e2.x;
       float det = e1.x * px + e1.y * py + e1.z * pz;
       float n1 = e1.x * e1.x + e1.y * e1.y + e1.z * e1.z, n2 = e2.x * e2.x + e2.y * e2.y + e2.z * e2.z;
-      bool pass;
+      bool pass, in32 = false;
+      float t32 = 0.f;
       if (det * det <= 1e-12f * n1 * n2) {
         pass = true;  // nearly parallel: let FP64 decide
       } else {
@@ -136,28 +166,52 @@ __device__ Hit closest_hit(const DevScene& sc, D3 o, D3 d, double tmin, double t
         float u = (sx * px + sy * py + sz * pz) * inv;
         float qx = sy * e1.z - sz * e1.y, qy = sz * e1.x - sx * e1.z, qz = sx * e1.y - sy * e1.x;
         float v = (r.dx * qx + r.dy * qy + r.dz * qz) * inv;
-        float t = (e2.x * qx + e2.y * qy + e2.z * qz) * inv;
-        float eps = 1e-3f + 1e-5f * sqrtf(n1 * n2 / (det * det)) * (1.0f + fabsf(t));
-        pass = u >= -eps && v >= -eps && u + v <= 1.0f + eps && t <= tcull && t >= -1e-3f;
+        t32 = (e2.x * qx + e2.y * qy + e2.z * qz) * inv;
+        float eps = 1e-3f + 1e-5f * sqrtf(n1 * n2 / (det * det)) * (1.0f + fabsf(t32));
+        pass = u >= -eps && v >= -eps && u + v <= 1.0f + eps && t32 <= tcull && t32 >= -1e-3f;
+        in32 = u >= eps && v >= eps && u + v <= 1.0f - eps;
       }
       if (!pass) continue;
       int prim = __ldg(&sc.tri_prim[leaf]);
       if (prim == exclude) continue;
-      double t64;
-      if (tri_test64(sc.triv + 9 * leaf, o, d, t64) && t64 > tmin && t64 <= tmax) {
-        if (t64 < best.t || (t64 == best.t && prim < best.prim)) {
-          best.t = t64;
-          best.prim = prim;
-          best.leaf = leaf;
-          tcull = fminf(tcull, (float)t64 * (1.0f + 1e-6f) + 1e-4f);
-        }
+      // A candidate is definite when its FP32 barycentrics are inside by more than the
+      // slack and its distance clears both interval ends: FP64 would accept it too, so
+      // only its distance is needed, and only when it competes with another hit.
+      const float tslack = 1e-4f + 1e-5f * fabsf(t32);
+      const bool definite = in32 && t32 >= (float)tmin + tslack && t32 <= (float)tmax - tslack;
+      double t64 = INFINITY;
+      bool exact = false;
+      if (!definite) {
+        if (!(tri_test64(sc.triv + 9 * leaf, o, d, t64) && t64 > tmin && t64 <= tmax)) continue;
+        exact = true;
+      }
+      bool take;
+      if (best.prim < 0) {
+        take = true;
+      } else if (!exact && t32 < best_t32 - tslack) {
+        take = true;
+      } else if (!exact && t32 > best_t32 + tslack) {
+        take = false;
+      } else {
+        // close or exact: compare FP64 distances, ties to the lowest primitive id
+        if (!exact) { t64 = plane_t(sc, leaf, o, d); exact = true; }
+        if (!best_exact) { best.t = plane_t(sc, best.leaf, o, d); best_exact = true; }
+        take = t64 < best.t || (t64 == best.t && prim < best.prim);
+      }
+      if (take) {
+        best.prim = prim;
+        best.leaf = leaf;
+        best.t = t64;
+        best_exact = exact;
+        best_t32 = exact ? (float)t64 : t32;
+        tcull = fminf(tcull, best_t32 * (1.0f + 1e-5f) + 2e-4f);
       }
     }
     hl = hit2[0];
     hr = hit2[1];
     if (hl && hr) {
       int nearc = ln <= rn ? ch.x : ch.y, farc = ln <= rn ? ch.y : ch.x;
-      if (sp >= kMaxStack) { atomicOr(err, kErrStack); return best; }
+      if (sp >= kMaxStack) { atomicOr(err, kErrStack); break; }
       stack[sp++] = farc;
       node = nearc;
     } else if (hl) {
@@ -169,6 +223,7 @@ __device__ Hit closest_hit(const DevScene& sc, D3 o, D3 d, double tmin, double t
       node = stack[--sp];
     }
   }
+  if (best.prim >= 0 && !best_exact) best.t = plane_t(sc, best.leaf, o, d);
   return best;
 }
 
@@ -220,9 +275,11 @@ __device__ __forceinline__ double speckle(const TraceArgs& A, uint32_t ray, uint
   return dm(2.0 * kPi, u24(x));
 }
 
-// Lambertian amplitude Gamma^2 sqrt(mu cos(k) dOmega) / L exp(-2 alpha L).
-__device__ __forceinline__ double lambert(const TraceArgs& A, double gam, double mu, double kinc, double dOmega, double L) {
-  return gam * gam * sqrt(mu * kinc * dOmega) / L * exp(-2.0 * A.alpha * L);
+// Lambertian amplitude Gamma^2 sqrt(mu cos(k) dOmega) / L exp(-2 alpha L), in FP32: the
+// amplitude needs no more than FP32 precision, unlike the delay and phase.
+__device__ __forceinline__ double lambert(const TraceArgs& A, double gam, float mu, float kinc, float dOmega, double L) {
+  const float Lf = (float)L;
+  return (double)((float)(gam * gam) * sqrtf(mu * kinc * dOmega) / Lf * expf(-2.0f * (float)A.alpha * Lf));
 }
 
 // ----------------------------------------------------------------- curved rays
@@ -308,11 +365,11 @@ __device__ void route_curved(const TraceArgs& A, int ping, D3 o, D3 d0, D3 us, u
       n = d3(0.0, 0.0, 1.0);
       gam *= A.r_surface;
     } else {
-      n = tri_normal64(A.sc.triv + 9 * hq.leaf);
-      double kinc = fabs(dc.x * n.x + dc.y * n.y + dc.z * n.z);
-      double amp = lambert(A, gam, (double)A.sc.tri_mu[hq.leaf], kinc, dOmega, s_hit);
+      const float kinc = kinc32(A.sc, hq.leaf, dc);
+      double amp = lambert(A, gam, A.sc.tri_mu[hq.leaf], kinc, (float)dOmega, s_hit);
       emit(A, ping, 2.0 * T_hit, amp, speckle(A, ray, sub, bounce), us, hq.prim, keybase | (uint32_t)bounce);
       if (!((A.sc.tri_flags[hq.leaf] & 1) && bounce < A.max_bounces)) break;
+      n = tri_normal64(A.sc, hq.leaf);  // FP64 only where the route continues
       gam *= A.r_seabed;
     }
     double thh = th - xi * A.ssp_g * (f * h);
@@ -342,8 +399,12 @@ __device__ void route_straight(const TraceArgs& A, int ping, D3 o, D3 d0, D3 us,
     Hit hq = closest_hit(A.sc, pos, dir, kEpsHit, tlim, prev, A.err);
     double ts = INFINITY;
     if (A.has_surface && prev != -2 && dir.z != 0.0) {
-      double t = dd(ds(A.surface_z, pos.z), dir.z);
-      if (t > kEpsHit && t <= tlim) ts = t;
+      // divide only when the plane lies ahead within reach
+      const double num = ds(A.surface_z, pos.z);
+      if (num * dir.z > 0.0 && fabs(num) <= tlim * fabs(dir.z) * (1.0 + 1e-12)) {
+        double t = dd(num, dir.z);
+        if (t > kEpsHit && t <= tlim) ts = t;
+      }
     }
     if (hq.prim < 0 && ts == INFINITY) break;
     if (ts < hq.t) {
@@ -356,13 +417,13 @@ __device__ void route_straight(const TraceArgs& A, int ping, D3 o, D3 d0, D3 us,
       prev = -2;
       continue;
     }
-    D3 n = tri_normal64(A.sc.triv + 9 * hq.leaf);
     pos = axpy(pos, hq.t, dir);
     L = da(L, hq.t);
-    double kinc = fabs(dot(dir, n));
-    double amp = lambert(A, gam, (double)A.sc.tri_mu[hq.leaf], kinc, dOmega, L);
-    emit(A, ping, 2.0 * dd(L, cw), amp, speckle(A, ray, sub, bounce), us, hq.prim, keybase | (uint32_t)bounce);
+    const float kinc = kinc32(A.sc, hq.leaf, dir);
+    double amp = lambert(A, gam, A.sc.tri_mu[hq.leaf], kinc, (float)dOmega, L);
+    emit(A, ping, 2.0 * dm(L, A.inv_c0), amp, speckle(A, ray, sub, bounce), us, hq.prim, keybase | (uint32_t)bounce);
     if ((A.sc.tri_flags[hq.leaf] & 1) && bounce < A.max_bounces) {
+      const D3 n = tri_normal64(A.sc, hq.leaf);  // FP64 only where the route continues
       double k = dm(2.0, dot(dir, n));
       dir = d3(ds(dir.x, dm(k, n.x)), ds(dir.y, dm(k, n.y)), ds(dir.z, dm(k, n.z)));
       gam *= A.r_seabed;
@@ -374,7 +435,7 @@ __device__ void route_straight(const TraceArgs& A, int ping, D3 o, D3 d0, D3 us,
   }
 }
 
-__global__ void __launch_bounds__(128) k_trace(TraceArgs A) {
+__global__ void __launch_bounds__(128, 4) k_trace(TraceArgs A) {
   const int64_t total = (int64_t)A.n_pings * A.n_subrays;
   for (int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gid < total; gid += (int64_t)gridDim.x * blockDim.x) {
     int ping = (int)(gid / A.n_subrays);

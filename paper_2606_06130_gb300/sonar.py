@@ -32,6 +32,7 @@ SONAR_OPT_DEBUG = 1
 SONAR_OPT_TIMING = 2
 SONAR_OPT_GRAPH = 3
 SONAR_OPT_TILE_N = 4
+SONAR_OPT_SYNTH = 5
 
 PRECISIONS = {"fp32": SONAR_FP32, "bf16": SONAR_BF16, "fp16": SONAR_FP16}
 
