@@ -161,24 +161,35 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant_
         const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + c * 32);
         TMEM_LD_32(taddr, v);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        // envelope of 16 beams, then their per-beam maxima over the warp's 32 samples as
+        // 16 independent butterfly reductions (latency overlapped), one atomic per lane
+        const int beam0 = nb * (BN / 2) + c * 16;
+        unsigned long long key[16];
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-          const int beam = nb * (BN / 2) + c * 16 + j;
+          const int beam = beam0 + j;
           const float re = __uint_as_float(v[2 * j]), im = __uint_as_float(v[2 * j + 1]);
           const float e = sqrtf(re * re + im * im) * scale;
           const bool vb = beam < a.n_beams;
           if (vn && vb) env_p[(size_t)beam * a.nr + n] = e;
-          unsigned long long key = (elig && vb)
+          key[j] = (elig && vb)
               ? (((unsigned long long)__float_as_uint(e) << 32) | (unsigned long long)(0xFFFFFFFFu - (uint32_t)n))
               : 0ull;
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {
-            unsigned long long other = __shfl_xor_sync(0xffffffffu, key, o);
-            key = other > key ? other : key;
-          }
-          if (lane == 0 && key != 0ull) atomicMax(&keys_p[beam], key);
           if (elig && vb) pmax = fmaxf(pmax, e);
         }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const unsigned long long other = __shfl_xor_sync(0xffffffffu, key[j], o);
+            key[j] = other > key[j] ? other : key[j];
+          }
+        }
+        unsigned long long mine = 0ull;
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          if (lane == j) mine = key[j];
+        if (lane < 16 && mine != 0ull) atomicMax(&keys_p[beam0 + lane], mine);
       }
       tc_fence_before();
       __syncwarp();

@@ -8,7 +8,7 @@
 // the real 4-form of ez (row (my, 0) = (Re ez, -Im ez), row (my, 1) = (Im ez, Re ez)).
 //
 // Persistent CTAs take equal contiguous ranges of the delay-sorted hits and walk them
-// in K-blocks of up to 32 hits whose taps fall inside at most TMAX tiles. Eight
+// in K-blocks of up to 32 hits whose taps fall inside at most TMAX tiles. Sixteen
 // generator warps stage each K-block (taps from the pulse table, phasors by sincospi),
 // write the B operand and one A operand per touched tile straight into shared memory
 // in the UMMA 128-byte-swizzle K-major layout (BF16; FP32 form also the residual lo
@@ -30,8 +30,8 @@ constexpr int NA = 3;            // A operand ring slots (hi + lo)
 constexpr int NB = 2;            // B operand ring slots (hi + lo)
 constexpr int RING = 8;          // TMEM accumulator slots of 64 columns
 constexpr int TMAX = 5;          // tiles one K-block may touch
-constexpr int kGenWarps = 8;
-constexpr int kEpiWarp0 = 1;     // warps 1..4: epilogue, warp 0: MMA, warps 5..12: generators
+constexpr int kGenWarps = 16;
+constexpr int kEpiWarp0 = 1;     // warps 1..4: epilogue, warp 0: MMA, warps 5..20: generators
 constexpr int kGenWarp0 = 5;
 constexpr int kThreadsTC = 32 * (kGenWarp0 + kGenWarps);
 constexpr int kGenThreads = 32 * kGenWarps;
