@@ -53,11 +53,11 @@ struct sonar_ctx {
   int32_t* tri_prim = nullptr;
   float* tri_mu = nullptr;
   uint8_t* tri_flags = nullptr;
-  double4* tri_plane = nullptr;
+  double4_32a* tri_plane = nullptr;
   float* tri_inv_n = nullptr;
   BvhNode* nodes = nullptr;
   float4* points = nullptr;
-  double4* planes = nullptr;
+  double4_32a* planes = nullptr;
   uint64_t scene_version = 0;
 
   // parameter-derived tables
@@ -828,8 +828,8 @@ int sonar_scene_upload(sonar_ctx* ctx, const float* verts, int64_t n_verts, cons
     CU(cudaMemcpy(ctx->points, pts.data(), sizeof(float4) * n_points, cudaMemcpyHostToDevice));
   }
   if (n_planes > 0) {
-    CU(cudaMalloc(&ctx->planes, sizeof(double4) * n_planes));
-    CU(cudaMemcpy(ctx->planes, planes, sizeof(double4) * n_planes, cudaMemcpyHostToDevice));
+    CU(cudaMalloc(&ctx->planes, sizeof(double4_32a) * n_planes));
+    CU(cudaMemcpy(ctx->planes, planes, sizeof(double4_32a) * n_planes, cudaMemcpyHostToDevice));
   }
   ctx->sc.tri32 = ctx->tri32;
   ctx->sc.triv = ctx->triv;

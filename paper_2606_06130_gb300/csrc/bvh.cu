@@ -117,7 +117,7 @@ __global__ void k_hierarchy(const unsigned long long* keys, int n, int2* child, 
 __global__ void k_leaves(const float* V, const int32_t* T, const float* mu, const uint8_t* fl,
                          const unsigned long long* keys, int n, float4* lbox_lo, float4* lbox_hi,
                          float4* tri32, float* triv, int32_t* tri_prim, float* tri_mu, uint8_t* tri_flags,
-                         double4* tri_plane, float* tri_inv_n) {
+                         double4_32a* tri_plane, float* tri_inv_n) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   int prim = (int)(keys[k] & 0xffffffffu);
@@ -140,7 +140,7 @@ __global__ void k_leaves(const float* V, const int32_t* T, const float* mu, cons
   const double ny = __dsub_rn(__dmul_rn(e1z, e2x), __dmul_rn(e1x, e2z));
   const double nz = __dsub_rn(__dmul_rn(e1x, e2y), __dmul_rn(e1y, e2x));
   const double d0 = __dadd_rn(__dadd_rn(__dmul_rn(nx, (double)a.x), __dmul_rn(ny, (double)a.y)), __dmul_rn(nz, (double)a.z));
-  tri_plane[k] = make_double4(nx, ny, nz, d0);
+  tri_plane[k] = make_double4_32a(nx, ny, nz, d0);
   const double nn = __dadd_rn(__dadd_rn(__dmul_rn(nx, nx), __dmul_rn(ny, ny)), __dmul_rn(nz, nz));
   tri_inv_n[k] = nn > 0.0 ? (float)(1.0 / sqrt(nn)) : 0.f;
 }
@@ -200,7 +200,7 @@ __global__ void k_single(int2* child) { child[0] = make_int2(~0, INT_MIN); }
 
 cudaError_t build_bvh(const float* V, const int32_t* T, const float* mu, const uint8_t* fl, int32_t n,
                       float4** tri32, float** triv, int32_t** tri_prim, float** tri_mu,
-                      uint8_t** tri_flags, double4** tri_plane, float** tri_inv_n, BvhNode** nodes, int32_t* root,
+                      uint8_t** tri_flags, double4_32a** tri_plane, float** tri_inv_n, BvhNode** nodes, int32_t* root,
                       cudaStream_t st) {
   int n_pow2 = 1;
   while (n_pow2 < n) n_pow2 <<= 1;
@@ -210,7 +210,7 @@ cudaError_t build_bvh(const float* V, const int32_t* T, const float* mu, const u
   CK(cudaMalloc(tri_prim, sizeof(int32_t) * n));
   CK(cudaMalloc(tri_mu, sizeof(float) * n));
   CK(cudaMalloc(tri_flags, n));
-  CK(cudaMalloc(tri_plane, sizeof(double4) * n));
+  CK(cudaMalloc(tri_plane, sizeof(double4_32a) * n));
   CK(cudaMalloc(tri_inv_n, sizeof(float) * n));
   CK(cudaMalloc(nodes, sizeof(BvhNode) * n_int));
   float* bb;

@@ -54,14 +54,14 @@ struct DevScene {
   const int32_t* tri_prim; // leaf -> original triangle id
   const float* tri_mu;     // leaf order
   const uint8_t* tri_flags;// leaf order
-  const double4* tri_plane;// leaf order: n = (b - a) x (c - a) in FP64 (unnormalised), n . a
+  const double4_32a* tri_plane;// leaf order: n = (b - a) x (c - a) in FP64 (unnormalised), n . a
   const float* tri_inv_n;  // leaf order: 1 / |n|
   const BvhNode* nodes;
   int32_t n_tris;
   int32_t root;            // internal node index, or ~leaf for a one-triangle scene
   const float4* points;    // x, y, z, sigma
   int32_t n_points;
-  const double4* planes;   // unit normal, offset
+  const double4_32a* planes;   // unit normal, offset
   int32_t n_planes;
 };
 
@@ -117,7 +117,7 @@ namespace sonar {
 struct BvhBuild;
 cudaError_t build_bvh(const float* d_verts, const int32_t* d_tris, const float* d_mu,
                       const uint8_t* d_flags, int32_t n_tris, float4** tri32, float** triv,
-                      int32_t** tri_prim, float** tri_mu, uint8_t** tri_flags, double4** tri_plane,
+                      int32_t** tri_prim, float** tri_mu, uint8_t** tri_flags, double4_32a** tri_plane,
                       float** tri_inv_n, BvhNode** nodes, int32_t* root, cudaStream_t st);
 cudaError_t launch_ray_table(double* dirs, float* row_domega, int32_t n_ray_az, int32_t n_ray_el,
                              int32_t n_sub, double hfov, double vfov, uint32_t seed32,

@@ -144,7 +144,9 @@ template <int WT, bool SZ>
 __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tc(SynthArgs a, uint32_t idesc) {
   constexpr int NA = Mode<SZ>::NA, TILE_OP = Mode<SZ>::TILE_OP, KB_OP = Mode<SZ>::KB_OP;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
-  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  // align by pointer arithmetic on the shared array, so that the compiler keeps the
+  // shared address space (an integer round trip would turn every access generic)
+  uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   uint8_t* sT = smem;                              // per-tile operands: NA x (hi, lo)
   uint8_t* sK = sT + NA * 2 * TILE_OP;             // per-K-block operands: NB x (hi, lo)
   Stage<WT>* st = reinterpret_cast<Stage<WT>*>(sK + NB * 2 * KB_OP);
@@ -193,8 +195,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tc(SynthArgs a, uint32_
 
   if (warp == 0) {
     // ------------------------------------------------------------- MMA issuer
-    int uses[RING];
-    for (int i = 0; i < RING; ++i) uses[i] = 0;
+    // per TMEM slot: has it held a tile before (used), parity of its use count (par)
+    uint32_t used = 0, par = 0;
     int live_lo = INT_MAX, live_hi = -1, j = 0, a_idx = 0;
     int win = load_window(a.sorted_n, h0, h1, lane);
     for (int64_t h = h0; h < h1;) {
@@ -211,8 +213,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tc(SynthArgs a, uint32_
           const bool fresh = t > live_hi;
           bool ok = b_ok;
           if (fresh) {
-            const int use = uses[slot]++;
-            if (use > 0) ok = ok && wait_or_abort(smem_u32(&tfree[slot]), (use - 1) & 1, abort_flag, a.err);
+            const uint32_t bit = 1u << slot;
+            if (used & bit) ok = ok && wait_or_abort(smem_u32(&tfree[slot]), ((par >> slot) & 1u) ^ 1u, abort_flag, a.err);
+            used |= bit;
+            par ^= bit;
           }
           const int aslot = a_idx % NA;
           ok = ok && wait_or_abort(smem_u32(&a_full[aslot]), (a_idx / NA) & 1, abort_flag, a.err);
@@ -255,12 +259,12 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tc(SynthArgs a, uint32_
     const int q = warp & 3;  // TMEM lane quarter this warp may access
     const int L = q * 32 + lane;
     const int r_hi = L / nx, mx = L - r_hi * nx;  // (my_hi, mx) or (n, mx)
-    int uses[RING], cur[RING];
-    for (int i = 0; i < RING; ++i) { uses[i] = 0; cur[i] = 0; }
+    // per TMEM slot: parity of its use count (par) and of the tile it holds now (cur)
+    uint32_t par = 0, cur = 0;
     int live_lo = INT_MAX, live_hi = -1;
     auto flush = [&](int u) {
       const int slot = u % RING;
-      const bool ok = wait_or_abort(smem_u32(&tdone[slot]), cur[slot] & 1, abort_flag, a.err);
+      const bool ok = wait_or_abort(smem_u32(&tdone[slot]), (cur >> slot) & 1u, abort_flag, a.err);
       if (ok) {
         tc_fence_after();
         for (int c0 = 0; c0 < n_cols; c0 += 16) {
@@ -294,7 +298,11 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tc(SynthArgs a, uint32_
       const int64_t hn = h + kb.cnt;
       win = load_window(a.sorted_n, hn, h1, lane);
       for (int u = live_lo; u <= live_hi && u < kb.t_first; ++u) flush(u);
-      for (int t = (live_hi + 1 > kb.t_first ? live_hi + 1 : kb.t_first); t <= kb.t_last; ++t) cur[t % RING] = uses[t % RING]++;
+      for (int t = (live_hi + 1 > kb.t_first ? live_hi + 1 : kb.t_first); t <= kb.t_last; ++t) {
+        const uint32_t bit = 1u << (t % RING);
+        cur = (cur & ~bit) | (par & bit);
+        par ^= bit;
+      }
       live_lo = kb.t_first;
       if (kb.t_last > live_hi) live_hi = kb.t_last;
       h = hn;

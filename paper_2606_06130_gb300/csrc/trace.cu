@@ -70,22 +70,22 @@ __device__ bool tri_test64(const float* tv, D3 o, D3 d, double& t) {
   return true;
 }
 
-__device__ __forceinline__ double4 load_plane(const DevScene& sc, int leaf) {
+__device__ __forceinline__ double4_32a load_plane(const DevScene& sc, int leaf) {
   const double2* p = reinterpret_cast<const double2*>(sc.tri_plane + leaf);
   const double2 a = __ldg(p), b = __ldg(p + 1);
-  return make_double4(a.x, a.y, b.x, b.y);
+  return make_double4_32a(a.x, a.y, b.x, b.y);
 }
 
 // |cos| of the incidence angle from the stored FP64 plane normal: the dot product in
 // FP64 (grazing incidence keeps its relative accuracy), the scaling in FP32.
 __device__ __forceinline__ float kinc32(const DevScene& sc, int leaf, D3 d) {
-  const double4 P = load_plane(sc, leaf);
+  const double4_32a P = load_plane(sc, leaf);
   return fabsf((float)dot(d, d3(P.x, P.y, P.z))) * __ldg(&sc.tri_inv_n[leaf]);
 }
 
 // Unit geometric normal (b - a) x (c - a) / |.| in FP64, for specular reflection.
 __device__ D3 tri_normal64(const DevScene& sc, int leaf) {
-  const double4 P = load_plane(sc, leaf);
+  const double4_32a P = load_plane(sc, leaf);
   const D3 n = d3(P.x, P.y, P.z);
   double l = __dsqrt_rn(dot(n, n));
   return d3(dd(n.x, l), dd(n.y, l), dd(n.z, l));
@@ -113,7 +113,7 @@ struct Hit {
 
 // FP64 distance to the triangle's plane: (n . a - n . o) / (n . d).
 __device__ __forceinline__ double plane_t(const DevScene& sc, int leaf, D3 o, D3 d) {
-  const double4 P = load_plane(sc, leaf);
+  const double4_32a P = load_plane(sc, leaf);
   const D3 n = d3(P.x, P.y, P.z);
   return dd(ds(P.w, dot(n, o)), dot(n, d));
 }
@@ -463,14 +463,14 @@ __device__ bool leg_clear(const TraceArgs& A, D3 a, D3 b) {
   return h.prim < 0;
 }
 
-__device__ D3 mirror(const double4 pl, D3 x) {
+__device__ D3 mirror(const double4_32a pl, D3 x) {
   double k = 2.0 * (pl.x * x.x + pl.y * x.y + pl.z * x.z - pl.w);
   return d3(x.x - k * pl.x, x.y - k * pl.y, x.z - k * pl.z);
 }
 
-__device__ double4 plane_of(const TraceArgs& A, int idx, double& gam) {
+__device__ double4_32a plane_of(const TraceArgs& A, int idx, double& gam) {
   if (A.has_surface) {
-    if (idx == 0) { gam = A.r_surface; return make_double4(0.0, 0.0, 1.0, A.surface_z); }
+    if (idx == 0) { gam = A.r_surface; return make_double4_32a(0.0, 0.0, 1.0, A.surface_z); }
     idx -= 1;
   }
   gam = A.r_seabed;
@@ -573,7 +573,7 @@ __global__ void k_points(TraceArgs A) {
   D3 a = o, tgt = img;
   for (int k = 0; k < len; ++k) {
     double gk;
-    double4 pl = plane_of(A, seq[k], gk);
+    double4_32a pl = plane_of(A, seq[k], gk);
     double dA = pl.x * a.x + pl.y * a.y + pl.z * a.z - pl.w;
     double dT = pl.x * tgt.x + pl.y * tgt.y + pl.z * tgt.z - pl.w;
     if (!(dA * dT < 0)) return;
