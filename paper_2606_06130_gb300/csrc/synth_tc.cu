@@ -3,29 +3,26 @@
 // Element phasors are separable, exp(j k_a u.p_m) = ey[mx] ez[my], so the echoes of a
 // tile of T consecutive range samples are complex contractions over the hits k of
 //   S[n][my nx + mx] = sum_k g_k(n) ey_k[mx] ez_k[my],   g_k(n) = c_k R(t_n - tau_k).
-// Two operand factorisations (both MMA shapes M = 128, N = 64, two K columns per hit):
-//
-//  per-K-block z split (arrays with nx ny a multiple of 128): with my = my_hi L2 + my_lo
-//  (L2 = nx ny / 128), ez[my] = E1[my_hi] E2[my_lo], E1 = ez shifted by L2 my_hi,
-//  E2[my_lo] = exp(j theta_z my_lo). The M operand A[(my_hi, mx)][k] = ey[mx] E1[my_hi]
-//  does not depend on the tile and is generated once per K-block; only the N operand
-//  B[k][(n, my_lo, re/im)] = g_k(n) E2[my_lo] (T = 32 / L2 samples) is generated per
-//  tile.
-//
-//  per-tile (small arrays): A[(n, mx)][k] = g_k(n) ey[mx] per tile (T = 128 / nx) and
-//  B[k][(my, re/im)] = ez[my] once per K-block.
-//
-// N operands are stored as the real 4-form: row (., 0) = (Re b, -Im b), row (., 1) =
-// (Im b, Re b) over the (re, im) K pair of each hit.
+// Each hit contributes two K columns (re, im); the MMA shape is M = 128, N = 64.
 //
 // Persistent CTAs take equal contiguous ranges of the delay-sorted hits and walk them in
-// K-blocks of up to 32 hits whose taps stay inside TMAX tiles. Sixteen generator warps
-// stage each K-block (taps from a cubic pulse table in shared memory, phasors by
-// sincospi) and write the operands straight into shared memory in the UMMA 128-byte
-// swizzle K-major layout (BF16; the FP32 form also writes the residual lo parts and runs
-// three passes hi*hi, hi*lo, lo*hi). One thread issues tcgen05.mma into a ring of TMEM
-// accumulators (one per tile); four epilogue warps add a tile's accumulator into S
-// (FP32, vector atomics) once the walk has passed it.
+// K-blocks of up to 32 hits whose taps stay inside TMAX tiles. Generator warps form the
+// operands in BF16 (the FP32 form also writes the residual lo parts and runs three
+// passes hi*hi, hi*lo, lo*hi); one thread issues tcgen05.mma into a ring of TMEM
+// accumulators, one per tile; four epilogue warps add a tile's accumulator into S (FP32,
+// vector atomics) once the walk has passed it. N operands are stored as the real
+// 4-form: row (., 0) = (Re b, -Im b), row (., 1) = (Im b, Re b).
+//
+// k_synth_tz (arrays of nx ny = 128 L2 elements): with my = my_hi L2 + my_lo the z
+//   phasor factors as ez[my] = E1[my_hi] E2[my_lo] (E1 = ez at L2 my_hi, E2[my_lo] =
+//   exp(j theta_z my_lo)). The M operand A[(my_hi, mx)][k] = ey[mx] E1[my_hi] does not
+//   depend on the tile: it is written once per K-block into tensor memory (tcgen05.st),
+//   which the MMA reads as A. Only the N operand B[k][(n, my_lo, re/im)] = g_k(n)
+//   E2[my_lo] (T = 32 / L2 samples) is formed per tile, in shared memory. The sixteen
+//   generator warps form four independent groups, one per MMA K step (8 hits), each with
+//   one warp per TMEM lane quarter and its own named barrier.
+// k_synth_tc (small arrays): A[(n, mx)][k] = g_k(n) ey[mx] per tile (T = 128 / nx) and
+//   B[k][(my, re/im)] = ez[my] once per K-block, both in shared memory.
 #include <limits.h>
 
 #include "common.cuh"
@@ -36,37 +33,25 @@ namespace {
 using namespace tc;
 
 constexpr int KH = 32;           // hits per K-block: K = 64 BF16 columns (re, im)
-constexpr int NB = 2;            // per-K-block operand ring slots (hi + lo)
-constexpr int RING = 8;          // TMEM accumulator slots of 64 columns
 constexpr int TMAX = 5;          // tiles one K-block may touch
 constexpr int kGenWarps = 16;
 constexpr int kGenWarp0 = 5;     // warp 0: MMA, warps 1..4: epilogue, warps 5..20: generators
 constexpr int kThreadsTC = 32 * (kGenWarp0 + kGenWarps);
 constexpr int kGenThreads = 32 * kGenWarps;
 constexpr int M_BYTES = 128 * 128;  // 128 rows x 64 BF16
-constexpr int N_BYTES = 64 * 128;   // up to 64 rows x 64 BF16
+constexpr int N_BYTES = 64 * 128;   // 64 rows x 64 BF16
 constexpr int kMaxAx = 64;
 
-template <bool SZ> struct Mode {
-  static constexpr int NA = SZ ? 4 : 3;                 // per-tile operand ring slots
-  static constexpr int TILE_OP = SZ ? N_BYTES : M_BYTES;  // bytes of one per-tile operand (hi)
-  static constexpr int KB_OP = SZ ? M_BYTES : N_BYTES;    // bytes of one per-K-block operand (hi)
-};
-
-template <int WT>
-struct Stage {
-  HitRec rec[KH];
-  int n[KH];
-  float2 g[WT][KH];        // tap-major: staging writes and operand reads are conflict-free
-  float2 ey[KH][kMaxAx];   // per hit, element-major: a warp reads consecutive elements
-  float2 ez[KH][kMaxAx];   // ez[my], or E1 in [0, H1) and E2 in [H1, H1 + L2)
-};
-
-template <int WT, bool SZ>
-constexpr size_t tc_smem_bytes() {
-  return 1024 + (size_t)Mode<SZ>::NA * 2 * Mode<SZ>::TILE_OP + (size_t)NB * 2 * Mode<SZ>::KB_OP +
-         2 * sizeof(Stage<WT>) + 64 * 8 + 64;
-}
+// k_synth_tc rings
+constexpr int NA = 3;            // per-tile A slots (hi + lo)
+constexpr int NB = 2;            // per-K-block B slots (hi + lo)
+constexpr int RING = 8;          // TMEM accumulators of 64 columns
+// k_synth_tz rings
+constexpr int kGroups = 4;
+constexpr int KG = KH / kGroups;   // hits per generator group = one MMA K step
+constexpr int NT = 8;              // per-tile B slots (hi + lo)
+constexpr int ZRING = 6;           // TMEM accumulators of 64 columns
+constexpr int kAcol = ZRING * 64;  // TMEM columns of the two per-K-block A slots (hi 32, lo 32)
 
 struct KBlk {
   int cnt, t_first, t_last;
@@ -109,7 +94,12 @@ __device__ __forceinline__ void sts128(uint32_t addr, uint32_t a, uint32_t b, ui
 __device__ __forceinline__ void red_add2(float* dst, float a, float b) {
   asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(dst), "f"(a), "f"(b) : "memory");
 }
-__device__ __forceinline__ void gen_bar() { asm volatile("bar.sync 1, %0;" ::"n"(kGenThreads) : "memory"); }
+__device__ __forceinline__ void named_bar(uint32_t id, uint32_t n) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ float2 cmul(float2 p, float2 q) {
+  return make_float2(p.x * q.x - p.y * q.y, p.x * q.y + p.y * q.x);
+}
 
 // One 16-byte operand chunk (4 complex values, hits 4c..4c+3) in the 128-byte swizzle.
 __device__ __forceinline__ void store_chunk(uint32_t hi_base, uint32_t lo_base, int row, int c, const float2 (&v)[4],
@@ -123,6 +113,26 @@ __device__ __forceinline__ void store_chunk(uint32_t hi_base, uint32_t lo_base, 
   const uint32_t off = (uint32_t)(row * 128 + ((c ^ (row & 7)) << 4));
   sts128(hi_base + off, hv[0], hv[1], hv[2], hv[3]);
   if (fp32_form) sts128(lo_base + off, lv[0], lv[1], lv[2], lv[3]);
+}
+
+// Tap c_k R(u) from the shared-memory pulse table by 4-point Lagrange interpolation
+// (error ~4e-8); zero outside the pulse support.
+__device__ __forceinline__ float2 tap_value(const float2* tab, float scale, float u, float cr, float ci) {
+  float2 g = make_float2(0.f, 0.f);
+  const float x = u * scale + (float)(kRTabS / 2 + 2);
+  if (x >= 1.0f && x < (float)(kRTabS + 3)) {
+    const int i = (int)x;
+    const float f = x - (float)i;
+    const float wm = -f * (f - 1.f) * (f - 2.f) * (1.f / 6.f);
+    const float w0 = (f + 1.f) * (f - 1.f) * (f - 2.f) * 0.5f;
+    const float w1 = -(f + 1.f) * f * (f - 2.f) * 0.5f;
+    const float w2 = (f + 1.f) * f * (f - 1.f) * (1.f / 6.f);
+    const float2 r0 = tab[i - 1], r1 = tab[i], r2 = tab[i + 1], r3 = tab[i + 2];
+    const float rr = wm * r0.x + w0 * r1.x + w1 * r2.x + w2 * r3.x;
+    const float ri = wm * r0.y + w0 * r1.y + w1 * r2.y + w2 * r3.y;
+    g = make_float2(cr * rr - ci * ri, cr * ri + ci * rr);
+  }
+  return g;
 }
 
 #define TMEM_LD_16(taddr, r)                                                                                  \
@@ -140,20 +150,352 @@ __device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity, vol
   return false;
 }
 
-template <int WT, bool SZ>
-__global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tc(SynthArgs a, uint32_t idesc) {
-  constexpr int NA = Mode<SZ>::NA, TILE_OP = Mode<SZ>::TILE_OP, KB_OP = Mode<SZ>::KB_OP;
+// Epilogue role (warps 1..4): walks the K-blocks like the MMA issuer and, for every tile
+// the walk has passed, adds the accumulator columns of its TMEM slot into S. dst(u, pr)
+// is the S entry of column pair pr of this thread's lane row in tile u.
+template <int R, class Dst>
+__device__ __forceinline__ void epilogue_role(const SynthArgs& a, int64_t h0, int64_t h1, int T, int W, int q,
+                                              int lane, uint32_t tmem_base, uint64_t* tdone, uint64_t* tfree,
+                                              volatile int* abort_flag, int n_cols, Dst dst) {
+  uint32_t par = 0, cur = 0;  // per slot: parity of its use count, parity of the tile it holds
+  int live_lo = INT_MAX, live_hi = -1;
+  auto flush = [&](int u) {
+    const int slot = u % R;
+    const bool ok = wait_or_abort(smem_u32(&tdone[slot]), (cur >> slot) & 1u, abort_flag, a.err);
+    if (ok) {
+      tc_fence_after();
+      for (int c0 = 0; c0 < n_cols; c0 += 16) {
+        uint32_t v[16];
+        TMEM_LD_16(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(slot * 64 + c0), v);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int i = 0; i < 8; ++i) red_add2(dst(u, c0 / 2 + i), __uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1]));
+      }
+    }
+    tc_fence_before();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(smem_u32(&tfree[slot]));
+  };
+  int win = load_window(a.sorted_n, h0, h1, lane);
+  for (int64_t h = h0; h < h1;) {
+    const KBlk kb = kblock_from(win, T, W);
+    const int64_t hn = h + kb.cnt;
+    win = load_window(a.sorted_n, hn, h1, lane);
+    for (int u = live_lo; u <= live_hi && u < kb.t_first; ++u) flush(u);
+    for (int t = (live_hi + 1 > kb.t_first ? live_hi + 1 : kb.t_first); t <= kb.t_last; ++t) {
+      const uint32_t bit = 1u << (t % R);
+      cur = (cur & ~bit) | (par & bit);
+      par ^= bit;
+    }
+    live_lo = kb.t_first;
+    if (kb.t_last > live_hi) live_hi = kb.t_last;
+    h = hn;
+  }
+  for (int u = live_lo; u <= live_hi; ++u) flush(u);
+}
+
+__device__ __forceinline__ void tmem_alloc_512(uint32_t* slot) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)), "r"(512)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_free_512(uint32_t base) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(base), "r"(512) : "memory");
+}
+
+// =====================================================================================
+// k_synth_tz: z-split operands, per-K-block A in tensor memory
+// =====================================================================================
+template <int WT>
+struct ZStage {  // one generator group's 8 hits of one K-block
+  HitRec rec[KG];
+  int n[KG];
+  float2 g[WT][KG];        // taps, tap-major
+  float2 ey[KG][kMaxAx];
+  float2 ez[KG][kMaxAx];   // E1 in [0, H1), E2 in [H1, H1 + L2)
+};
+
+template <int WT>
+constexpr size_t tz_smem_bytes() {
+  return 1024 + (size_t)NT * 2 * N_BYTES + 2 * kGroups * sizeof(ZStage<WT>) + 64 * 8 + 64;
+}
+
+template <int WT>
+__global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_t idesc) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   // align by pointer arithmetic on the shared array, so that the compiler keeps the
   // shared address space (an integer round trip would turn every access generic)
   uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-  uint8_t* sT = smem;                              // per-tile operands: NA x (hi, lo)
-  uint8_t* sK = sT + NA * 2 * TILE_OP;             // per-K-block operands: NB x (hi, lo)
-  Stage<WT>* st = reinterpret_cast<Stage<WT>*>(sK + NB * 2 * KB_OP);
+  uint8_t* sB = smem;  // NT x (hi, lo) per-tile N operands
+  ZStage<WT>(*zst)[kGroups] = reinterpret_cast<ZStage<WT>(*)[kGroups]>(sB + NT * 2 * N_BYTES);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(&zst[2][0]);
+  uint64_t* tb_full = bars;
+  uint64_t* tb_empty = bars + NT;
+  uint64_t* am_full = bars + 2 * NT;
+  uint64_t* am_empty = am_full + 2;
+  uint64_t* tdone = am_empty + 2;
+  uint64_t* tfree = tdone + ZRING;
+  uint64_t* done = tfree + ZRING;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  __shared__ float2 s_rtab[kRTabS + 5];
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nx = a.nx, ny = a.ny, M = nx * ny;
+  const int L2 = M / 128, lL2 = 31 - __clz(L2);  // my_lo count, a power of two
+  const int H1 = ny / L2;                         // my_hi count
+  const int lnx = 31 - __clz(nx);                 // nx is a power of two
+  const int T = 32 / L2;
+  const int W = a.taps;
+  const int64_t Hn = *a.n_valid;
+  const int64_t h0 = Hn * blockIdx.x / gridDim.x, h1 = Hn * (blockIdx.x + 1) / gridDim.x;
+  const bool fp32_form = a.n_pass == 3;
+
+  for (int i = threadIdx.x; i < kRTabS + 5; i += blockDim.x) s_rtab[i] = a.rtab_s[i];
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < NT; ++i) { mbar_init(smem_u32(&tb_full[i]), kGenWarps); mbar_init(smem_u32(&tb_empty[i]), 1); }
+    for (int i = 0; i < 2; ++i) { mbar_init(smem_u32(&am_full[i]), kGenWarps); mbar_init(smem_u32(&am_empty[i]), 1); }
+    for (int i = 0; i < ZRING; ++i) { mbar_init(smem_u32(&tdone[i]), 1); mbar_init(smem_u32(&tfree[i]), 4); }
+    mbar_init(smem_u32(done), 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tmem_alloc_512(tmem_slot);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------- MMA issuer
+    uint32_t used = 0, par = 0;  // per slot: held a tile before, parity of its use count
+    int live_lo = INT_MAX, live_hi = -1, j = 0, tix = 0;
+    int win = load_window(a.sorted_n, h0, h1, lane);
+    for (int64_t h = h0; h < h1;) {
+      const KBlk kb = kblock_from(win, T, W);
+      const int64_t hn = h + kb.cnt;
+      win = load_window(a.sorted_n, hn, h1, lane);
+      if (lane == 0) {
+        // tiles the walk has passed: their accumulators are final once these MMAs land
+        for (int u = live_lo; u <= live_hi && u < kb.t_first; ++u) tc_commit(smem_u32(&tdone[u % ZRING]));
+        const int aslot = j & 1;
+        const bool a_ok = wait_or_abort(smem_u32(&am_full[aslot]), (j >> 1) & 1, abort_flag, a.err);
+        const uint32_t ah = tmem_base + (uint32_t)(kAcol + aslot * 64), al = ah + 32;
+        for (int t = kb.t_first; t <= kb.t_last; ++t) {
+          const int slot = t % ZRING;
+          const bool fresh = t > live_hi;
+          bool ok = a_ok;
+          if (fresh) {
+            const uint32_t bit = 1u << slot;
+            if (used & bit) ok = ok && wait_or_abort(smem_u32(&tfree[slot]), ((par >> slot) & 1u) ^ 1u, abort_flag, a.err);
+            used |= bit;
+            par ^= bit;
+          }
+          const int bslot = tix % NT;
+          ok = ok && wait_or_abort(smem_u32(&tb_full[bslot]), (tix / NT) & 1, abort_flag, a.err);
+          if (ok) {
+            tc_fence_after();
+            const uint32_t d = tmem_base + (uint32_t)(slot * 64);
+            const uint32_t bh = smem_u32(sB + bslot * 2 * N_BYTES), bl = bh + N_BYTES;
+            for (int pass = 0; pass < a.n_pass; ++pass) {
+              const uint32_t aa = pass == 2 ? al : ah, bb = pass == 1 ? bl : bh;
+#pragma unroll
+              for (int kk = 0; kk < 4; ++kk)
+                tc_mma_tmem_a(d, aa + kk * 8, sw128_desc(bb + kk * 32), idesc, (fresh && pass == 0 && kk == 0) ? 0u : 1u);
+            }
+            tc_commit(smem_u32(&tb_empty[bslot]));
+          }
+          ++tix;
+        }
+        if (a_ok) tc_commit(smem_u32(&am_empty[aslot]));
+      }
+      live_lo = kb.t_first;
+      if (kb.t_last > live_hi) live_hi = kb.t_last;
+      ++j;
+      h = hn;
+      __syncwarp();
+    }
+    if (lane == 0) {
+      for (int u = live_lo; u <= live_hi; ++u) tc_commit(smem_u32(&tdone[u % ZRING]));
+      tc_commit(smem_u32(done));
+      mbar_wait(smem_u32(done), 0, a.err);
+    }
+    __syncwarp();
+  } else if (warp < kGenWarp0) {
+    // ------------------------------------------------------------- epilogue
+    const int q = warp & 3;  // TMEM lane quarter this warp may access
+    const int L = q * 32 + lane;
+    const int my_hi = L >> lnx, mx = L & (nx - 1);
+    epilogue_role<ZRING>(a, h0, h1, T, W, q, lane, tmem_base, tdone, tfree, abort_flag, 64, [&](int u, int pr) {
+      const int nl = pr >> lL2, my_lo = pr & (L2 - 1);
+      const int64_t row = (int64_t)u * T + nl;
+      return reinterpret_cast<float*>(a.S + row * M + (my_hi * L2 + my_lo) * nx + mx);
+    });
+  } else {
+    // ------------------------------------------------------------- operand generators
+    const int gw = warp - kGenWarp0;
+    const int grp = gw >> 2;            // hits KG grp .. KG grp + 7 of every K-block
+    const int wi = gw & 3;              // warp in group
+    const int tg = wi * 32 + lane;      // thread in group
+    const int q = warp & 3;             // TMEM lane quarter of this warp
+    const uint32_t bar_id = 1 + grp;
+    const float pl2 = 2.0f * a.pitch_over_lambda;
+    const int nz = H1 + L2;
+    // A operand: this thread's TMEM lane is row (my_hi, mx)
+    const int arow = q * 32 + lane, a_hi = arow >> lnx, a_mx = arow & (nx - 1);
+    // B operand: a warp writes 32 rows of one of the group's two chunks (4 hits each)
+    const int cl = wi & 1, brow = (wi >> 1) * 32 + lane;
+    const int pr = brow >> 1, br = brow & 1, nl = pr >> lL2, my_lo = pr & (L2 - 1);
+    const int bchunk = 2 * grp + cl;
+    auto fetch = [&](int64_t hs) {
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      const int64_t k = hs + KG * grp + (tg >> 1);
+      if (tg < 2 * KG && k < h1) v = __ldg(reinterpret_cast<const uint4*>(a.hits_sorted + k) + (tg & 1));
+      return v;
+    };
+    {
+      const uint4 v = fetch(h0);
+      if (tg < 2 * KG) reinterpret_cast<uint4*>(&zst[0][grp].rec[tg >> 1])[tg & 1] = v;
+      named_bar(bar_id, 128);
+    }
+    int win = load_window(a.sorted_n, h0, h1, lane);
+    int j = 0, tix = 0;
+    for (int64_t h = h0; h < h1;) {
+      const KBlk kb = kblock_from(win, T, W);
+      const int64_t hn = h + kb.cnt;
+      win = load_window(a.sorted_n, hn, h1, lane);
+      const uint4 recv = fetch(hn);
+      ZStage<WT>& S = zst[j & 1][grp];
+      const int kvalid = kb.cnt - KG * grp;  // hits of this group inside the K-block
+      // taps c_k R((u0 + i) dt); padding hits contribute zero
+      for (int item = tg; item < KG * WT; item += 128) {
+        const int kl = item & (KG - 1), qq = item >> 3;
+        float2 g = make_float2(0.f, 0.f);
+        if (kl < kvalid && qq < W) {
+          const HitRec& hr = S.rec[kl];
+          g = tap_value(s_rtab, a.rtab_s_scale, hr.u0 + (float)qq, hr.cr, hr.ci);
+        }
+        S.g[qq][kl] = g;
+        if (qq == 0) S.n[kl] = kl < kvalid ? S.rec[kl].nglob : INT_MIN / 2;
+      }
+      // ey[mx] = exp(j 2 pi (d/lambda) (mx - (nx-1)/2) u_y)
+      for (int item = tg; item < KG * nx; item += 128) {
+        const int mx = item & (nx - 1), kl = item >> lnx;
+        float2 e = make_float2(0.f, 0.f);
+        if (kl < kvalid) {
+          float s, c;
+          sincospif(pl2 * ((float)mx - 0.5f * (float)(nx - 1)) * S.rec[kl].uy, &s, &c);
+          e = make_float2(c, s);
+        }
+        S.ey[kl][mx] = e;
+      }
+      // E1[my_hi] = ez[L2 my_hi], E2[my_lo] = exp(j 2 pi (d/lambda) my_lo u_z)
+      for (int item = tg; item < KG * nz; item += 128) {
+        const int kl = item & (KG - 1), qz = item >> 3;
+        float2 e = make_float2(0.f, 0.f);
+        if (kl < kvalid) {
+          const float arg = qz < H1 ? (float)(L2 * qz) - 0.5f * (float)(ny - 1) : (float)(qz - H1);
+          float s, c;
+          sincospif(pl2 * arg * S.rec[kl].uz, &s, &c);
+          e = make_float2(c, s);
+        }
+        S.ez[kl][qz] = e;
+      }
+      // the next K-block's records go to the other stage buffer, whose records were last
+      // read before the previous barrier
+      if (tg < 2 * KG) reinterpret_cast<uint4*>(&zst[(j + 1) & 1][grp].rec[tg >> 1])[tg & 1] = recv;
+      named_bar(bar_id, 128);
+
+      // per-K-block A operand: row (my_hi, mx) = this thread's TMEM lane, 8 columns
+      const int aslot = j & 1;
+      wait_or_abort(smem_u32(&am_empty[aslot]), ((j >> 1) & 1) ^ 1, abort_flag, a.err);
+      tc_fence_after();
+      {
+        uint32_t hi[KG], lo[KG];
+#pragma unroll
+        for (int kl = 0; kl < KG; ++kl) {
+          const float2 v = cmul(S.ey[kl][a_mx], S.ez[kl][a_hi]);
+          hi[kl] = pack_bf16(v.x, v.y);
+          lo[kl] = pack_lo(v.x, v.y, hi[kl]);
+        }
+        const uint32_t ta = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(kAcol + aslot * 64 + KG * grp);
+        tmem_st8(ta, hi);
+        if (fp32_form) tmem_st8(ta + 32, lo);
+        tmem_st_wait();
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&am_full[aslot]));
+
+      // per-tile B operand: rows (n, my_lo, re/im) of chunk bchunk
+      int nk[4];
+      float2 e2[4];
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        nk[kk] = S.n[4 * cl + kk];
+        e2[kk] = S.ez[4 * cl + kk][H1 + my_lo];
+      }
+      for (int t = kb.t_first; t <= kb.t_last; ++t) {
+        const int bslot = tix % NT;
+        wait_or_abort(smem_u32(&tb_empty[bslot]), ((tix / NT) & 1) ^ 1, abort_flag, a.err);
+        const uint32_t bh = smem_u32(sB + bslot * 2 * N_BYTES), bl = bh + N_BYTES;
+        const int trow = t * T + nl;
+        float2 v[4];
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          const int tap = trow - nk[kk];
+          float2 b = make_float2(0.f, 0.f);
+          if ((unsigned)tap < (unsigned)WT) b = cmul(S.g[tap][4 * cl + kk], e2[kk]);
+          v[kk] = br == 0 ? make_float2(b.x, -b.y) : make_float2(b.y, b.x);
+        }
+        store_chunk(bh, bl, brow, bchunk, v, fp32_form);
+        fence_proxy_async();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&tb_full[bslot]));
+        ++tix;
+      }
+      ++j;
+      h = hn;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_free_512(tmem_base);
+  }
+}
+
+// =====================================================================================
+// k_synth_tc: per-tile A = taps x ey, per-K-block B = ez (small arrays)
+// =====================================================================================
+template <int WT>
+struct Stage {
+  HitRec rec[KH];
+  int n[KH];
+  float2 g[WT][KH];        // tap-major: staging writes and operand reads are conflict-free
+  float2 ey[KH][kMaxAx];   // per hit, element-major: a warp reads consecutive elements
+  float2 ez[KH][kMaxAx];
+};
+
+template <int WT>
+constexpr size_t tc_smem_bytes() {
+  return 1024 + (size_t)NA * 2 * M_BYTES + (size_t)NB * 2 * N_BYTES + 2 * sizeof(Stage<WT>) + 64 * 8 + 64;
+}
+
+__device__ __forceinline__ void gen_bar() { asm volatile("bar.sync 1, %0;" ::"n"(kGenThreads) : "memory"); }
+
+template <int WT>
+__global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tc(SynthArgs a, uint32_t idesc) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  uint8_t* sA = smem;                          // per-tile A: NA x (hi, lo)
+  uint8_t* sB = sA + NA * 2 * M_BYTES;         // per-K-block B: NB x (hi, lo)
+  Stage<WT>* st = reinterpret_cast<Stage<WT>*>(sB + NB * 2 * N_BYTES);
   uint64_t* bars = reinterpret_cast<uint64_t*>(st + 2);
-  uint64_t* a_full = bars;                         // per-tile ring
+  uint64_t* a_full = bars;
   uint64_t* a_empty = bars + NA;
-  uint64_t* b_full = bars + 2 * NA;                // per-K-block ring
+  uint64_t* b_full = bars + 2 * NA;
   uint64_t* b_empty = bars + 2 * NA + NB;
   uint64_t* tdone = bars + 2 * NA + 2 * NB;
   uint64_t* tfree = tdone + RING;
@@ -164,12 +506,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tc(SynthArgs a, uint32_
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nx = a.nx, ny = a.ny, M = nx * ny;
-  const int L2 = SZ ? M / 128 : 1;   // my_lo count (z split), a power of two
-  const int lL2 = 31 - __clz(L2);
-  const int H1 = SZ ? ny / L2 : 1;   // my_hi count (z split)
-  const int T = SZ ? 32 / L2 : 128 / nx;
+  const int lnx = 31 - __clz(nx);
+  const int T = 128 / nx;
   const int W = a.taps;
-  const int n_cols = SZ ? 64 : 2 * ny;  // MMA N
+  const int n_cols = 2 * ny;
   const int64_t Hn = *a.n_valid;
   const int64_t h0 = Hn * blockIdx.x / gridDim.x, h1 = Hn * (blockIdx.x + 1) / gridDim.x;
   const bool fp32_form = a.n_pass == 3;
@@ -183,11 +523,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tc(SynthArgs a, uint32_
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(RING * 64) : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
+  if (warp == 0) tmem_alloc_512(tmem_slot);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -195,7 +531,6 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tc(SynthArgs a, uint32_
 
   if (warp == 0) {
     // ------------------------------------------------------------- MMA issuer
-    // per TMEM slot: has it held a tile before (used), parity of its use count (par)
     uint32_t used = 0, par = 0;
     int live_lo = INT_MAX, live_hi = -1, j = 0, a_idx = 0;
     int win = load_window(a.sorted_n, h0, h1, lane);
@@ -204,7 +539,6 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tc(SynthArgs a, uint32_
       const int64_t hn = h + kb.cnt;
       win = load_window(a.sorted_n, hn, h1, lane);
       if (lane == 0) {
-        // tiles the walk has passed: their accumulators are final once these MMAs land
         for (int u = live_lo; u <= live_hi && u < kb.t_first; ++u) tc_commit(smem_u32(&tdone[u % RING]));
         const int bslot = j % NB;
         const bool b_ok = wait_or_abort(smem_u32(&b_full[bslot]), (j / NB) & 1, abort_flag, a.err);
@@ -223,11 +557,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tc(SynthArgs a, uint32_
           if (ok) {
             tc_fence_after();
             const uint32_t d = tmem_base + (uint32_t)(slot * 64);
-            const uint32_t th = smem_u32(sT + aslot * 2 * TILE_OP), tl = th + TILE_OP;
-            const uint32_t kh = smem_u32(sK + bslot * 2 * KB_OP), kl = kh + KB_OP;
-            // M operand (A) and N operand (B) of this mode
-            const uint32_t ah = SZ ? kh : th, al = SZ ? kl : tl;
-            const uint32_t bh = SZ ? th : kh, bl = SZ ? tl : kl;
+            const uint32_t ah = smem_u32(sA + aslot * 2 * M_BYTES), al = ah + M_BYTES;
+            const uint32_t bh = smem_u32(sB + bslot * 2 * N_BYTES), bl = bh + N_BYTES;
             for (int pass = 0; pass < a.n_pass; ++pass) {
               const uint32_t aa = pass == 2 ? al : ah, bb = pass == 1 ? bl : bh;
 #pragma unroll
@@ -241,7 +572,6 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tc(SynthArgs a, uint32_
         }
         if (b_ok) tc_commit(smem_u32(&b_empty[bslot]));
       }
-      // live tiles: from this K-block's first tile to the furthest tile touched so far
       live_lo = kb.t_first;
       if (kb.t_last > live_hi) live_hi = kb.t_last;
       ++j;
@@ -256,66 +586,19 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tc(SynthArgs a, uint32_
     __syncwarp();
   } else if (warp < kGenWarp0) {
     // ------------------------------------------------------------- epilogue
-    const int q = warp & 3;  // TMEM lane quarter this warp may access
+    const int q = warp & 3;
     const int L = q * 32 + lane;
-    const int r_hi = L / nx, mx = L - r_hi * nx;  // (my_hi, mx) or (n, mx)
-    // per TMEM slot: parity of its use count (par) and of the tile it holds now (cur)
-    uint32_t par = 0, cur = 0;
-    int live_lo = INT_MAX, live_hi = -1;
-    auto flush = [&](int u) {
-      const int slot = u % RING;
-      const bool ok = wait_or_abort(smem_u32(&tdone[slot]), (cur >> slot) & 1u, abort_flag, a.err);
-      if (ok) {
-        tc_fence_after();
-        for (int c0 = 0; c0 < n_cols; c0 += 16) {
-          uint32_t v[16];
-          TMEM_LD_16(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(slot * 64 + c0), v);
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const int pr = c0 / 2 + i;  // (n, my_lo) pair, or my
-            int64_t row, my;
-            if (SZ) {
-              const int nl = pr >> lL2, my_lo = pr & (L2 - 1);
-              row = (int64_t)u * T + nl;
-              my = r_hi * L2 + my_lo;
-            } else {
-              row = (int64_t)u * T + r_hi;
-              my = pr;
-            }
-            float* dst = reinterpret_cast<float*>(a.S + row * M + my * nx + mx);
-            red_add2(dst, __uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1]));
-          }
-        }
-      }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(&tfree[slot]));
-    };
-    int win = load_window(a.sorted_n, h0, h1, lane);
-    for (int64_t h = h0; h < h1;) {
-      const KBlk kb = kblock_from(win, T, W);
-      const int64_t hn = h + kb.cnt;
-      win = load_window(a.sorted_n, hn, h1, lane);
-      for (int u = live_lo; u <= live_hi && u < kb.t_first; ++u) flush(u);
-      for (int t = (live_hi + 1 > kb.t_first ? live_hi + 1 : kb.t_first); t <= kb.t_last; ++t) {
-        const uint32_t bit = 1u << (t % RING);
-        cur = (cur & ~bit) | (par & bit);
-        par ^= bit;
-      }
-      live_lo = kb.t_first;
-      if (kb.t_last > live_hi) live_hi = kb.t_last;
-      h = hn;
-    }
-    for (int u = live_lo; u <= live_hi; ++u) flush(u);
+    const int nl = L >> lnx, mx = L & (nx - 1);
+    epilogue_role<RING>(a, h0, h1, T, W, q, lane, tmem_base, tdone, tfree, abort_flag, n_cols, [&](int u, int my) {
+      const int64_t row = (int64_t)u * T + nl;
+      return reinterpret_cast<float*>(a.S + row * M + my * nx + mx);
+    });
   } else {
     // ------------------------------------------------------------- operand generators
     const int gt = threadIdx.x - kGenWarp0 * 32;
-    const int lnx = 31 - __clz(nx);  // nx is a power of two
     const float pl2 = 2.0f * a.pitch_over_lambda;
     int j = 0, a_idx = 0;
     // hit records are fetched one K-block ahead: 32 records from the K-block's first hit
-    // (one coalesced 16-byte load per thread; records past the K-block are ignored)
     auto fetch_recs = [&](int64_t hs) {
       uint4 v = make_uint4(0u, 0u, 0u, 0u);
       const int64_t k = hs + (gt >> 1);
@@ -332,33 +615,15 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tc(SynthArgs a, uint32_
       if (gt < 2 * KH) reinterpret_cast<uint4*>(&S.rec[gt >> 1])[gt & 1] = recv;
       recv = fetch_recs(hn);
       gen_bar();
-      // taps c_k R((u0 + i) dt) from the pulse table; padding hits contribute zero
       for (int item = gt; item < KH * WT; item += kGenThreads) {
         const int k = item & (KH - 1), qq = item >> 5;
         const bool valid = k < kb.cnt;
         const HitRec& hr = S.rec[k];
         float2 g = make_float2(0.f, 0.f);
-        if (valid && qq < W) {
-          // 4-point Lagrange interpolation in the shared-memory table (error ~4e-8)
-          const float x = (hr.u0 + (float)qq) * a.rtab_s_scale + (float)(kRTabS / 2 + 2);
-          if (x >= 1.0f && x < (float)(kRTabS + 3)) {
-            const int i = (int)x;
-            const float f = x - (float)i;
-            const float wm = -f * (f - 1.f) * (f - 2.f) * (1.f / 6.f);
-            const float w0 = (f + 1.f) * (f - 1.f) * (f - 2.f) * 0.5f;
-            const float w1 = -(f + 1.f) * f * (f - 2.f) * 0.5f;
-            const float w2 = (f + 1.f) * f * (f - 1.f) * (1.f / 6.f);
-            const float2 r0 = s_rtab[i - 1], r1 = s_rtab[i], r2 = s_rtab[i + 1], r3 = s_rtab[i + 2];
-            const float rr = wm * r0.x + w0 * r1.x + w1 * r2.x + w2 * r3.x;
-            const float ri = wm * r0.y + w0 * r1.y + w1 * r2.y + w2 * r3.y;
-            g = make_float2(hr.cr * rr - hr.ci * ri, hr.cr * ri + hr.ci * rr);
-          }
-        }
+        if (valid && qq < W) g = tap_value(s_rtab, a.rtab_s_scale, hr.u0 + (float)qq, hr.cr, hr.ci);
         S.g[qq][k] = g;
         if (qq == 0) S.n[k] = valid ? hr.nglob : INT_MIN / 2;
       }
-      // separable element phasors: ey[mx] = exp(j 2 pi (d/lambda) (mx - (nx-1)/2) u_y);
-      // z: ez[my] (per-tile mode) or E1[my_hi] = ez[L2 my_hi], E2[my_lo] = exp(j theta_z my_lo)
       for (int item = gt; item < KH * nx; item += kGenThreads) {
         const int mx = item & (nx - 1), k = item >> lnx;
         float2 e = make_float2(0.f, 0.f);
@@ -369,106 +634,54 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tc(SynthArgs a, uint32_
         }
         S.ey[k][mx] = e;
       }
-      const int nz = SZ ? H1 + L2 : ny;
-      for (int item = gt; item < KH * nz; item += kGenThreads) {
-        const int k = item / nz, qz = item - k * nz;
+      for (int item = gt; item < KH * ny; item += kGenThreads) {
+        const int k = item / ny, my = item - k * ny;
         float2 e = make_float2(0.f, 0.f);
         if (k < kb.cnt) {
-          float arg;
-          if (!SZ) arg = (float)qz - 0.5f * (float)(ny - 1);
-          else if (qz < H1) arg = (float)(L2 * qz) - 0.5f * (float)(ny - 1);
-          else arg = (float)(qz - H1);
           float s, c;
-          sincospif(pl2 * arg * S.rec[k].uz, &s, &c);
+          sincospif(pl2 * ((float)my - 0.5f * (float)(ny - 1)) * S.rec[k].uz, &s, &c);
           e = make_float2(c, s);
         }
-        S.ez[k][qz] = e;
+        S.ez[k][my] = e;
       }
       gen_bar();
-      // per-K-block operand
+      // per-K-block B[k][(my, re/im)] = 4-form of ez[my]
       const int bslot = j % NB;
       wait_or_abort(smem_u32(&b_empty[bslot]), ((j / NB) & 1) ^ 1, abort_flag, a.err);
       {
-        const uint32_t kh = smem_u32(sK + bslot * 2 * KB_OP), kl = kh + KB_OP;
-        if (SZ) {
-          // A[(my_hi, mx)][k] = ey[mx] E1[my_hi]; a warp covers 32 rows of one chunk
-          for (int idx = gt; idx < 128 * 8; idx += kGenThreads) {
-            const int c = idx >> 7, row = idx & 127;
-            const int my_hi = row >> lnx, mx = row & (nx - 1);
-            float2 v[4];
+        const uint32_t bh = smem_u32(sB + bslot * 2 * N_BYTES), bl = bh + N_BYTES;
+        for (int idx = gt; idx < n_cols * 8; idx += kGenThreads) {
+          const int c = idx / n_cols, row = idx - c * n_cols;
+          const int my = row >> 1, r = row & 1;
+          float2 v[4];
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-              const float2 e = S.ey[4 * c + kk][mx], z = S.ez[4 * c + kk][my_hi];
-              v[kk] = make_float2(e.x * z.x - e.y * z.y, e.x * z.y + e.y * z.x);
-            }
-            store_chunk(kh, kl, row, c, v, fp32_form);
+          for (int kk = 0; kk < 4; ++kk) {
+            const float2 e = S.ez[4 * c + kk][my];
+            v[kk] = r == 0 ? make_float2(e.x, -e.y) : make_float2(e.y, e.x);
           }
-        } else {
-          // B[k][(my, re/im)] = 4-form of ez[my]
-          for (int idx = gt; idx < n_cols * 8; idx += kGenThreads) {
-            const int c = idx / n_cols, row = idx - c * n_cols;
-            const int my = row >> 1, r = row & 1;
-            float2 v[4];
-#pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-              const float2 e = S.ez[4 * c + kk][my];
-              v[kk] = r == 0 ? make_float2(e.x, -e.y) : make_float2(e.y, e.x);
-            }
-            store_chunk(kh, kl, row, c, v, fp32_form);
-          }
+          store_chunk(bh, bl, row, c, v, fp32_form);
         }
       }
       fence_proxy_async();
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&b_full[bslot]));
-      // per-tile operand for every touched tile
+      // per-tile A[(n, mx)][k] = g_k(n) ey[mx]; a warp covers 32 rows of one chunk
       for (int t = kb.t_first; t <= kb.t_last; ++t) {
         const int aslot = a_idx % NA;
         wait_or_abort(smem_u32(&a_empty[aslot]), ((a_idx / NA) & 1) ^ 1, abort_flag, a.err);
-        const uint32_t th = smem_u32(sT + aslot * 2 * TILE_OP), tl = th + TILE_OP;
-        if (SZ) {
-          // B[k][(n, my_lo, re/im)] = 4-form of g_k(n) E2[my_lo]
-          for (int idx = gt; idx < 64 * 8; idx += kGenThreads) {
-            const int c = idx >> 6, row = idx & 63;
-            const int pr = row >> 1, r = row & 1;
-            const int nl = pr >> lL2, my_lo = pr & (L2 - 1);
-            const int trow = t * T + nl;
-            float2 v[4];
+        const uint32_t ah = smem_u32(sA + aslot * 2 * M_BYTES), al = ah + M_BYTES;
+        for (int idx = gt; idx < 128 * 8; idx += kGenThreads) {
+          const int c = idx >> 7, row = idx & 127;
+          const int nl = row >> lnx, mx = row & (nx - 1);
+          const int trow = t * T + nl;
+          float2 v[4];
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-              const int k = 4 * c + kk;
-              const int tap = trow - S.n[k];
-              float x = 0.f, y = 0.f;
-              if (tap >= 0 && tap < WT) {
-                const float2 g = S.g[tap][k], z = S.ez[k][H1 + my_lo];
-                x = g.x * z.x - g.y * z.y;
-                y = g.x * z.y + g.y * z.x;
-              }
-              v[kk] = r == 0 ? make_float2(x, -y) : make_float2(y, x);
-            }
-            store_chunk(th, tl, row, c, v, fp32_form);
+          for (int kk = 0; kk < 4; ++kk) {
+            const int k = 4 * c + kk;
+            const int tap = trow - S.n[k];
+            v[kk] = (tap >= 0 && tap < WT) ? cmul(S.g[tap][k], S.ey[k][mx]) : make_float2(0.f, 0.f);
           }
-        } else {
-          // A[(n, mx)][k] = g_k(n) ey[mx]; a warp covers 32 rows of one chunk
-          for (int idx = gt; idx < 128 * 8; idx += kGenThreads) {
-            const int c = idx >> 7, row = idx & 127;
-            const int nl = row >> lnx, mx = row & (nx - 1);
-            const int trow = t * T + nl;
-            float2 v[4];
-#pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-              const int k = 4 * c + kk;
-              const int tap = trow - S.n[k];
-              float x = 0.f, y = 0.f;
-              if (tap >= 0 && tap < WT) {
-                const float2 g = S.g[tap][k], e = S.ey[k][mx];
-                x = g.x * e.x - g.y * e.y;
-                y = g.x * e.y + g.y * e.x;
-              }
-              v[kk] = make_float2(x, y);
-            }
-            store_chunk(th, tl, row, c, v, fp32_form);
-          }
+          store_chunk(ah, al, row, c, v, fp32_form);
         }
         fence_proxy_async();
         __syncwarp();
@@ -483,7 +696,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tc(SynthArgs a, uint32_
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(RING * 64) : "memory");
+    tmem_free_512(tmem_base);
   }
 }
 
@@ -495,16 +708,20 @@ bool z_split(int nx, int ny) {
          nx * (ny / L2) == 128 && ny / L2 + L2 <= kMaxAx;
 }
 
-template <int WT, bool SZ>
+template <int WT>
 cudaError_t set_attr() {
-  return cudaFuncSetAttribute(k_synth_tc<WT, SZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)tc_smem_bytes<WT, SZ>());
+  cudaError_t e = cudaFuncSetAttribute(k_synth_tc<WT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)tc_smem_bytes<WT>());
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_synth_tz<WT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tz_smem_bytes<WT>());
 }
 
-template <int WT, bool SZ>
-void launch_one(const SynthArgs& a, int sm_count, cudaStream_t st) {
-  const uint32_t idesc = make_idesc(1, 128, SZ ? 64 : 2 * a.ny);
-  k_synth_tc<WT, SZ><<<sm_count, kThreadsTC, tc_smem_bytes<WT, SZ>(), st>>>(a, idesc);
+template <int WT>
+void launch_one(const SynthArgs& a, bool zs, int sm_count, cudaStream_t st) {
+  if (zs)
+    k_synth_tz<WT><<<sm_count, kThreadsTC, tz_smem_bytes<WT>(), st>>>(a, make_idesc(1, 128, 64));
+  else
+    k_synth_tc<WT><<<sm_count, kThreadsTC, tc_smem_bytes<WT>(), st>>>(a, make_idesc(1, 128, 2 * a.ny));
 }
 
 }  // namespace
@@ -518,19 +735,16 @@ bool synth_tc_supported(int nx, int ny, int taps) {
 
 cudaError_t prepare_synth_tc() {
   cudaError_t e;
-  if ((e = set_attr<8, false>()) != cudaSuccess) return e;
-  if ((e = set_attr<12, false>()) != cudaSuccess) return e;
-  if ((e = set_attr<16, false>()) != cudaSuccess) return e;
-  if ((e = set_attr<8, true>()) != cudaSuccess) return e;
-  if ((e = set_attr<12, true>()) != cudaSuccess) return e;
-  return set_attr<16, true>();
+  if ((e = set_attr<8>()) != cudaSuccess) return e;
+  if ((e = set_attr<12>()) != cudaSuccess) return e;
+  return set_attr<16>();
 }
 
 cudaError_t launch_synth_tc(const SynthArgs& a, int sm_count, cudaStream_t st) {
-  const bool sz = z_split(a.nx, a.ny);
-  if (a.taps <= 8) sz ? launch_one<8, true>(a, sm_count, st) : launch_one<8, false>(a, sm_count, st);
-  else if (a.taps <= 12) sz ? launch_one<12, true>(a, sm_count, st) : launch_one<12, false>(a, sm_count, st);
-  else sz ? launch_one<16, true>(a, sm_count, st) : launch_one<16, false>(a, sm_count, st);
+  const bool zs = z_split(a.nx, a.ny);
+  if (a.taps <= 8) launch_one<8>(a, zs, sm_count, st);
+  else if (a.taps <= 12) launch_one<12>(a, zs, sm_count, st);
+  else launch_one<16>(a, zs, sm_count, st);
   return cudaGetLastError();
 }
 
