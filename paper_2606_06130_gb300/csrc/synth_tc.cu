@@ -65,17 +65,18 @@ __device__ __forceinline__ int load_window(const int32_t* ng, int64_t h, int64_t
 }
 
 // K-block starting at the window's first hit: as many hits (<= 32) as keep every tap
-// inside TMAX tiles of T rows. Warp-cooperative (all 32 lanes), identical in every role.
-__device__ __forceinline__ KBlk kblock_from(int v, int T, int W) {
+// inside TMAX tiles of T = 2^lT rows. Warp-cooperative (all 32 lanes), identical in
+// every role. Rows are non-negative, so shifts are floor divisions.
+__device__ __forceinline__ KBlk kblock_from(int v, int lT, int W) {
   const int g0 = __shfl_sync(0xffffffffu, v, 0);
   KBlk k;
-  k.t_first = g0 / T;
-  const int limit = T * (k.t_first + TMAX) - W;
+  k.t_first = g0 >> lT;
+  const int limit = ((k.t_first + TMAX) << lT) - W;
   const unsigned ok = __ballot_sync(0xffffffffu, v <= limit);
   k.cnt = __popc(ok);
   if (k.cnt < 1) k.cnt = 1;  // cannot happen for W <= T (TMAX - 1) + 1
   const int g_last = __shfl_sync(0xffffffffu, v, k.cnt - 1);
-  k.t_last = (g_last + W - 1) / T;
+  k.t_last = (g_last + W - 1) >> lT;
   return k;
 }
 
@@ -154,7 +155,7 @@ __device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity, vol
 // the walk has passed, adds the accumulator columns of its TMEM slot into S. dst(u, pr)
 // is the S entry of column pair pr of this thread's lane row in tile u.
 template <int R, class Dst>
-__device__ __forceinline__ void epilogue_role(const SynthArgs& a, int64_t h0, int64_t h1, int T, int W, int q,
+__device__ __forceinline__ void epilogue_role(const SynthArgs& a, int64_t h0, int64_t h1, int lT, int W, int q,
                                               int lane, uint32_t tmem_base, uint64_t* tdone, uint64_t* tfree,
                                               volatile int* abort_flag, int n_cols, Dst dst) {
   uint32_t par = 0, cur = 0;  // per slot: parity of its use count, parity of the tile it holds
@@ -178,7 +179,7 @@ __device__ __forceinline__ void epilogue_role(const SynthArgs& a, int64_t h0, in
   };
   int win = load_window(a.sorted_n, h0, h1, lane);
   for (int64_t h = h0; h < h1;) {
-    const KBlk kb = kblock_from(win, T, W);
+    const KBlk kb = kblock_from(win, lT, W);
     const int64_t hn = h + kb.cnt;
     win = load_window(a.sorted_n, hn, h1, lane);
     for (int u = live_lo; u <= live_hi && u < kb.t_first; ++u) flush(u);
@@ -245,7 +246,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_
   const int L2 = M / 128, lL2 = 31 - __clz(L2);  // my_lo count, a power of two
   const int H1 = ny / L2;                         // my_hi count
   const int lnx = 31 - __clz(nx);                 // nx is a power of two
-  const int T = 32 / L2;
+  const int T = 32 / L2, lT = 5 - lL2;
   const int W = a.taps;
   const int64_t Hn = *a.n_valid;
   const int64_t h0 = Hn * blockIdx.x / gridDim.x, h1 = Hn * (blockIdx.x + 1) / gridDim.x;
@@ -269,10 +270,11 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_
   if (warp == 0) {
     // ------------------------------------------------------------- MMA issuer
     uint32_t used = 0, par = 0;  // per slot: held a tile before, parity of its use count
-    int live_lo = INT_MAX, live_hi = -1, j = 0, tix = 0;
+    int live_lo = INT_MAX, live_hi = -1, j = 0;
+    unsigned tix = 0;
     int win = load_window(a.sorted_n, h0, h1, lane);
     for (int64_t h = h0; h < h1;) {
-      const KBlk kb = kblock_from(win, T, W);
+      const KBlk kb = kblock_from(win, lT, W);
       const int64_t hn = h + kb.cnt;
       win = load_window(a.sorted_n, hn, h1, lane);
       if (lane == 0) {
@@ -291,17 +293,22 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_
             used |= bit;
             par ^= bit;
           }
-          const int bslot = tix % NT;
+          const int bslot = tix & (NT - 1);
           ok = ok && wait_or_abort(smem_u32(&tb_full[bslot]), (tix / NT) & 1, abort_flag, a.err);
           if (ok) {
             tc_fence_after();
             const uint32_t d = tmem_base + (uint32_t)(slot * 64);
-            const uint32_t bh = smem_u32(sB + bslot * 2 * N_BYTES), bl = bh + N_BYTES;
-            for (int pass = 0; pass < a.n_pass; ++pass) {
-              const uint32_t aa = pass == 2 ? al : ah, bb = pass == 1 ? bl : bh;
+            // K step kk advances B by 32 bytes: +2 in the descriptor's address field
+            const uint64_t bdh = sw128_desc(smem_u32(sB + bslot * 2 * N_BYTES));
+            const uint64_t bdl = bdh + (N_BYTES >> 4);
+            tc_mma_tmem_a(d, ah, bdh, idesc, fresh ? 0u : 1u);
 #pragma unroll
-              for (int kk = 0; kk < 4; ++kk)
-                tc_mma_tmem_a(d, aa + kk * 8, sw128_desc(bb + kk * 32), idesc, (fresh && pass == 0 && kk == 0) ? 0u : 1u);
+            for (int kk = 1; kk < 4; ++kk) tc_mma_tmem_a(d, ah + kk * 8, bdh + 2 * kk, idesc, 1u);
+            if (fp32_form) {
+#pragma unroll
+              for (int kk = 0; kk < 4; ++kk) tc_mma_tmem_a(d, ah + kk * 8, bdl + 2 * kk, idesc, 1u);
+#pragma unroll
+              for (int kk = 0; kk < 4; ++kk) tc_mma_tmem_a(d, al + kk * 8, bdh + 2 * kk, idesc, 1u);
             }
             tc_commit(smem_u32(&tb_empty[bslot]));
           }
@@ -326,7 +333,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_
     const int q = warp & 3;  // TMEM lane quarter this warp may access
     const int L = q * 32 + lane;
     const int my_hi = L >> lnx, mx = L & (nx - 1);
-    epilogue_role<ZRING>(a, h0, h1, T, W, q, lane, tmem_base, tdone, tfree, abort_flag, 64, [&](int u, int pr) {
+    epilogue_role<ZRING>(a, h0, h1, lT, W, q, lane, tmem_base, tdone, tfree, abort_flag, 64, [&](int u, int pr) {
       const int nl = pr >> lL2, my_lo = pr & (L2 - 1);
       const int64_t row = (int64_t)u * T + nl;
       return reinterpret_cast<float*>(a.S + row * M + (my_hi * L2 + my_lo) * nx + mx);
@@ -359,9 +366,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_
       named_bar(bar_id, 128);
     }
     int win = load_window(a.sorted_n, h0, h1, lane);
-    int j = 0, tix = 0;
+    int j = 0;
+    unsigned tix = 0;
     for (int64_t h = h0; h < h1;) {
-      const KBlk kb = kblock_from(win, T, W);
+      const KBlk kb = kblock_from(win, lT, W);
       const int64_t hn = h + kb.cnt;
       win = load_window(a.sorted_n, hn, h1, lane);
       const uint4 recv = fetch(hn);
@@ -436,7 +444,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_
         e2[kk] = S.ez[4 * cl + kk][H1 + my_lo];
       }
       for (int t = kb.t_first; t <= kb.t_last; ++t) {
-        const int bslot = tix % NT;
+        const int bslot = tix & (NT - 1);
         wait_or_abort(smem_u32(&tb_empty[bslot]), ((tix / NT) & 1) ^ 1, abort_flag, a.err);
         const uint32_t bh = smem_u32(sB + bslot * 2 * N_BYTES), bl = bh + N_BYTES;
         const int trow = t * T + nl;
@@ -507,7 +515,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tc(SynthArgs a, uint32_
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nx = a.nx, ny = a.ny, M = nx * ny;
   const int lnx = 31 - __clz(nx);
-  const int T = 128 / nx;
+  const int T = 128 / nx, lT = 7 - lnx;
   const int W = a.taps;
   const int n_cols = 2 * ny;
   const int64_t Hn = *a.n_valid;
@@ -535,7 +543,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tc(SynthArgs a, uint32_
     int live_lo = INT_MAX, live_hi = -1, j = 0, a_idx = 0;
     int win = load_window(a.sorted_n, h0, h1, lane);
     for (int64_t h = h0; h < h1;) {
-      const KBlk kb = kblock_from(win, T, W);
+      const KBlk kb = kblock_from(win, lT, W);
       const int64_t hn = h + kb.cnt;
       win = load_window(a.sorted_n, hn, h1, lane);
       if (lane == 0) {
@@ -589,7 +597,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tc(SynthArgs a, uint32_
     const int q = warp & 3;
     const int L = q * 32 + lane;
     const int nl = L >> lnx, mx = L & (nx - 1);
-    epilogue_role<RING>(a, h0, h1, T, W, q, lane, tmem_base, tdone, tfree, abort_flag, n_cols, [&](int u, int my) {
+    epilogue_role<RING>(a, h0, h1, lT, W, q, lane, tmem_base, tdone, tfree, abort_flag, n_cols, [&](int u, int my) {
       const int64_t row = (int64_t)u * T + nl;
       return reinterpret_cast<float*>(a.S + row * M + my * nx + mx);
     });
@@ -608,7 +616,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tc(SynthArgs a, uint32_
     int win = load_window(a.sorted_n, h0, h1, lane);
     uint4 recv = fetch_recs(h0);
     for (int64_t h = h0; h < h1;) {
-      const KBlk kb = kblock_from(win, T, W);
+      const KBlk kb = kblock_from(win, lT, W);
       const int64_t hn = h + kb.cnt;
       win = load_window(a.sorted_n, hn, h1, lane);
       Stage<WT>& S = st[j & 1];
