@@ -135,8 +135,9 @@ def stage_work(stage, params, stats, n_pings):
         # complex [Nb x M] . [M x Nr] as a real GEMM: 8 Nb M Nr flop per ping
         return 8.0 * nb * M * nr * n_pings, "flop", "tensor"
     if stage == "synth":
-        # per (hit, element): phasor product (6 flop) + W complex MACs (8 flop each)
-        return float(stats["n_hits"]) * M * (8 * stats["taps"] + 6), "flop", "alu"
+        # per (hit, element): phasor product (6 flop) + W complex MACs (8 flop each); the
+        # contraction runs on the tensor cores (BF16 operands, hi/lo split in the FP32 form)
+        return float(stats["n_hits"]) * M * (8 * stats["taps"] + 6), "flop", "tensor"
     if stage == "convert":
         return float(n_pings) * nr * M * (8 + 8), "byte", "hbm"
     return None
@@ -157,7 +158,7 @@ def read_traffic(kernel):
         if src_hash is None:
             return None
         import hashlib
-        unit = {"synth": "synth.cu", "beamform": "beamform.cu", "trace": "trace.cu"}.get(kernel)
+        unit = {"k_synth_tz": "synth_tc.cu", "k_gemm": "beamform.cu", "k_trace": "trace.cu"}.get(kernel)
         cur = hashlib.sha1(open(os.path.join(ROOT, "paper_2606_06130_gb300", "csrc", unit), "rb").read()).hexdigest()[:12]
         return float(nbytes) if cur == src_hash else None
     except (OSError, ValueError):
@@ -278,8 +279,9 @@ def run_ours(args, ws, rank, local):
     else:
         peak, punit, achieved = pk["hbm_gbs"], "GB/s", amount / dt_s / 1e9
         pnote = f"HBM copy, {pk_kind}"
-    traffic = read_traffic(dom)
-    roof = {"kernel": {"synth": "k_synth", "beamform": "k_gemm", "convert": "k_convert"}[dom],
+    kname = {"synth": "k_synth_tz", "beamform": "k_gemm", "convert": "k_convert"}[dom]
+    traffic = read_traffic(kname)
+    roof = {"kernel": kname,
             "bound": bound, "achieved": achieved, "peak": peak, "unit": punit, "frac": achieved / peak,
             "peak_source": pnote, "traffic": traffic,
             "algorithmic_per_launch": amount, "algorithmic_unit": unit, "launch_ms": mean_stage[dom]}

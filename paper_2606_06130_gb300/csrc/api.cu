@@ -446,14 +446,18 @@ int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, cons
   ta.r_surface = p->r_surface;
   ta.r_seabed = p->r_seabed;
   ta.alpha = p->alpha_np_per_m;
+  ta.alpha32 = (float)p->alpha_np_per_m;
   ta.seed32 = seed32(p->seed);
   ta.ssp_z0 = d.ssp_z0;
   ta.ssp_c0 = d.ssp_c0;
   ta.ssp_g = d.ssp_g;
   ta.inv_c0 = 1.0 / d.ssp_c0;
+  ta.two_inv_c0 = 2.0 * ta.inv_c0;
   ta.T_stop = d.T_stop;
+  ta.L_stop = d.T_stop * d.ssp_c0;
   ta.t0 = d.t0;
   ta.inv_dt = 1.0 / d.dt;
+  ta.t0_dt = d.t0 * ta.inv_dt;
   ta.hw = d.hw;
   ta.f0 = p->f0_hz;
   ta.nr_pad = d.nr_pad;

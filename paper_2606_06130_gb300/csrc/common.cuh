@@ -69,6 +69,7 @@ struct DevScene {
 struct DevPose {
   double R[9];
   double t[3];
+  float t32[3];  // the position rounded to FP32, for the FP32 traversal
 };
 
 // Everything the trace kernels need, passed by value.
@@ -80,11 +81,15 @@ struct TraceArgs {
   int32_t n_pings, n_ray_az, n_ray_el, n_sub, n_subrays;
   int32_t max_bounces, has_surface, curved;
   double surface_z, r_surface, r_seabed, alpha;
+  float alpha32;                 // alpha in FP32, for the amplitude
   uint32_t seed32;
   double ssp_z0, ssp_c0, ssp_g;  // c(z) = c0 + g (z - z0)
   double inv_c0;                 // 1 / c0 (isovelocity one-way time per metre)
+  double two_inv_c0;             // 2 / c0 (isovelocity two-way delay per metre of path)
   double T_stop;                 // one-way time limit
+  double L_stop;                 // isovelocity path-length limit T_stop c0
   double t0, inv_dt, hw, f0;     // sample-grid mapping of delays
+  double t0_dt;                  // t0 / dt
   int32_t nr_pad;
   int32_t n_routes;              // point-scatterer routes per point
   HitRec* hits;

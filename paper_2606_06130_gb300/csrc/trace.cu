@@ -13,7 +13,10 @@
 // end) is decided by an FP64 ray/triangle test written with explicitly rounded
 // operations, and competing hits closer than the FP32 distance error are ordered by
 // their FP64 distances. The distance of the chosen hit is always FP64 (from the
-// stored FP64 plane), so delays and carrier phase keep FP64 accuracy.
+// stored FP64 plane), so delays and carrier phase keep FP64 accuracy. FP64 operations
+// are scarce on this part: decisions (the ray/triangle test) use explicitly rounded
+// operations in the oracle's order, while positions, distances and delays contract into
+// FMAs (an ulp or so from the oracle), and amplitudes are FP32.
 #include "common.cuh"
 
 namespace sonar {
@@ -35,15 +38,39 @@ __device__ __forceinline__ D3 cross(D3 a, D3 b) {
 __device__ __forceinline__ D3 axpy(D3 p, double t, D3 d) {  // p + t d, as p[k] += t * d[k]
   return d3(da(p.x, dm(t, d.x)), da(p.y, dm(t, d.y)), da(p.z, dm(t, d.z)));
 }
+// contracted forms for positions and distances
+__device__ __forceinline__ double dotf(D3 a, D3 b) { return fma(a.z, b.z, fma(a.y, b.y, a.x * b.x)); }
+__device__ __forceinline__ D3 axpyf(D3 p, double t, D3 d) {
+  return d3(fma(t, d.x, p.x), fma(t, d.y, p.y), fma(t, d.z, p.z));
+}
 __device__ __forceinline__ D3 rot(const double* R, D3 v) {
-  return d3(da(da(dm(R[0], v.x), dm(R[1], v.y)), dm(R[2], v.z)),
-            da(da(dm(R[3], v.x), dm(R[4], v.y)), dm(R[5], v.z)),
-            da(da(dm(R[6], v.x), dm(R[7], v.y)), dm(R[8], v.z)));
+  return d3(fma(R[2], v.z, fma(R[1], v.y, R[0] * v.x)), fma(R[5], v.z, fma(R[4], v.y, R[3] * v.x)),
+            fma(R[8], v.z, fma(R[7], v.y, R[6] * v.x)));
 }
 __device__ __forceinline__ D3 rot_t(const double* R, D3 v) {
   return d3(da(da(dm(R[0], v.x), dm(R[3], v.y)), dm(R[6], v.z)),
             da(da(dm(R[1], v.x), dm(R[4], v.y)), dm(R[7], v.z)),
             da(da(dm(R[2], v.x), dm(R[5], v.y)), dm(R[8], v.z)));
+}
+
+// a / b for |b| in [1e-30, 1e30]: an FP32 reciprocal seed refined by two Newton-Raphson
+// steps y += y (1 - b y) (2^-23 -> 2^-46 -> full precision) and one residual correction
+// of the quotient q += (a - b q) y. Within an ulp or so of the correctly rounded
+// quotient at a fraction of the cost of FP64 division, which is long on this part.
+__device__ __forceinline__ double ddiv_nr(double a, double b) {
+  double y = (double)__frcp_rn((float)b);
+  y = fma(y, fma(-b, y, 1.0), y);
+  y = fma(y, fma(-b, y, 1.0), y);
+  const double q = a * y;
+  return fma(fma(-b, q, a), y, q);
+}
+// 1 / sqrt(s) for s in [1e-30, 1e30]: FP32 seed, two Newton-Raphson steps
+// y *= (3 - s y^2) / 2.
+__device__ __forceinline__ double drsqrt_nr(double s) {
+  double y = (double)rsqrtf((float)s);
+  y = y * fma(-0.5 * s, y * y, 1.5);
+  y = y * fma(-0.5 * s, y * y, 1.5);
+  return y;
 }
 
 __device__ __forceinline__ D3 tri_vert(const float* v, int k) {
@@ -59,7 +86,8 @@ __device__ bool tri_test64(const float* tv, D3 o, D3 d, double& t) {
   D3 p = cross(d, e2);
   double det = dot(e1, p);
   if (det == 0.0) return false;
-  const double inv = dd(1.0, det);
+  const double ad = fabs(det);
+  const double inv = ad > 1e-30 && ad < 1e30 ? ddiv_nr(1.0, det) : dd(1.0, det);
   D3 s = sub(o, a);
   double u = dm(dot(s, p), inv);
   if (!(u >= 0.0 && u <= 1.0)) return false;
@@ -80,15 +108,15 @@ __device__ __forceinline__ double4_32a load_plane(const DevScene& sc, int leaf) 
 // FP64 (grazing incidence keeps its relative accuracy), the scaling in FP32.
 __device__ __forceinline__ float kinc32(const DevScene& sc, int leaf, D3 d) {
   const double4_32a P = load_plane(sc, leaf);
-  return fabsf((float)dot(d, d3(P.x, P.y, P.z))) * __ldg(&sc.tri_inv_n[leaf]);
+  return fabsf((float)dotf(d, d3(P.x, P.y, P.z))) * __ldg(&sc.tri_inv_n[leaf]);
 }
 
 // Unit geometric normal (b - a) x (c - a) / |.| in FP64, for specular reflection.
 __device__ D3 tri_normal64(const DevScene& sc, int leaf) {
   const double4_32a P = load_plane(sc, leaf);
   const D3 n = d3(P.x, P.y, P.z);
-  double l = __dsqrt_rn(dot(n, n));
-  return d3(dd(n.x, l), dd(n.y, l), dd(n.z, l));
+  const double il = drsqrt_nr(dotf(n, n));
+  return d3(dm(n.x, il), dm(n.y, il), dm(n.z, il));
 }
 
 // ----------------------------------------------------------------- traversal
@@ -115,21 +143,28 @@ struct Hit {
 __device__ __forceinline__ double plane_t(const DevScene& sc, int leaf, D3 o, D3 d) {
   const double4_32a P = load_plane(sc, leaf);
   const D3 n = d3(P.x, P.y, P.z);
-  return dd(ds(P.w, dot(n, o)), dot(n, d));
+  return ddiv_nr(P.w - dotf(n, o), dotf(n, d));
 }
 
 // Nearest triangle with FP64 distance in (tmin, tmax], excluding `exclude` (original
 // id), ties to the lowest id. The distance of the returned hit is FP64.
-__device__ Hit closest_hit(const DevScene& sc, D3 o, D3 d, double tmin, double tmax, int exclude, int* err) {
+// o32: the origin rounded to FP32 when the caller has it (nullptr: converted here).
+__device__ Hit closest_hit(const DevScene& sc, D3 o, D3 d, double tmin, double tmax, int exclude, int* err,
+                           const float* o32 = nullptr) {
   Hit best = {INFINITY, -1, -1};
   bool best_exact = true;
   float best_t32 = INFINITY;
   if (sc.n_tris == 0) return best;
   Ray32 r;
-  r.ox = (float)o.x; r.oy = (float)o.y; r.oz = (float)o.z;
+  if (o32) {
+    r.ox = o32[0]; r.oy = o32[1]; r.oz = o32[2];
+  } else {
+    r.ox = (float)o.x; r.oy = (float)o.y; r.oz = (float)o.z;
+  }
   r.dx = (float)d.x; r.dy = (float)d.y; r.dz = (float)d.z;
-  r.ix = 1.0f / r.dx; r.iy = 1.0f / r.dy; r.iz = 1.0f / r.dz;
+  r.ix = __frcp_rn(r.dx); r.iy = __frcp_rn(r.dy); r.iz = __frcp_rn(r.dz);
   const float tmax_f = (float)tmax * (1.0f + 1e-6f) + 1e-4f;
+  const float tmin32 = (float)tmin, tmax32 = (float)tmax;  // the loop stays in FP32
   float tcull = tmax_f;
   int stack[kMaxStack];
   int sp = 0;
@@ -178,7 +213,7 @@ __device__ Hit closest_hit(const DevScene& sc, D3 o, D3 d, double tmin, double t
       // slack and its distance clears both interval ends: FP64 would accept it too, so
       // only its distance is needed, and only when it competes with another hit.
       const float tslack = 1e-4f + 1e-5f * fabsf(t32);
-      const bool definite = in32 && t32 >= (float)tmin + tslack && t32 <= (float)tmax - tslack;
+      const bool definite = in32 && t32 >= tmin32 + tslack && t32 <= tmax32 - tslack;
       double t64 = INFINITY;
       bool exact = false;
       if (!definite) {
@@ -239,47 +274,48 @@ __device__ __forceinline__ unsigned long long warp_reserve(unsigned long long* c
   return base + rank;
 }
 
-__device__ __forceinline__ double wrap_pi(double a) {
-  return ds(a, dm(2.0 * kPi, floor(dd(da(a, kPi), 2.0 * kPi))));
-}
-
-// tau: FP64 two-way delay; amp: |c_k|; psi: speckle; u: sonar-frame arrival direction.
-__device__ void emit(const TraceArgs& A, int ping, double tau, double amp, double psi, D3 u, int prim, uint32_t key) {
+// tau: FP64 two-way delay; amp: |c_k|; psi_cyc: speckle phase in cycles; (uy, uz):
+// sonar-frame arrival direction.
+__device__ void emit(const TraceArgs& A, int ping, double tau, float amp, double psi_cyc, float uy, float uz,
+                     int prim, uint32_t key) {
   unsigned long long slot = warp_reserve(A.n_hits);
   if ((int64_t)slot >= A.hit_cap) { atomicOr(A.err, kErrCapacity); return; }
-  // carrier phase reduced modulo one cycle in FP64 before forming the phasor
-  double fc = dm(A.f0, tau);
-  double phi = wrap_pi(ds(psi, dm(2.0 * kPi, ds(fc, floor(fc)))));
-  double q = dm(ds(tau, A.t0), A.inv_dt);
-  double nf = floor(ds(q, A.hw)) + 1.0;
+  // phase psi - f0 tau in cycles, reduced modulo one cycle in FP64 to [-1/2, 1/2] before
+  // forming the phasor
+  double cyc = fma(-A.f0, tau, psi_cyc);
+  cyc -= rint(cyc);
+  // fractional sample position q = (tau - t0) / dt; first tap nf = floor(q - hw) + 1
+  const double q = fma(tau, A.inv_dt, -A.t0_dt);
+  const double nf = floor(q - A.hw) + 1.0;
   HitRec h;
   // a hit whose first tap lies outside this ping's padded rows has no tap in range
-  const bool in_rows = nf + kPad >= 0.0 && nf + kPad < (double)A.nr_pad;
-  h.nglob = in_rows ? ping * A.nr_pad + (int)nf + kPad : -1;
+  const int64_t nfi = (int64_t)nf;  // saturating conversion; |nf| is bounded by T_stop anyway
+  const bool in_rows = nfi >= -kPad && nfi < (int64_t)A.nr_pad - kPad;
+  h.nglob = in_rows ? ping * A.nr_pad + (int)nfi + kPad : -1;
   h.u0 = (float)(nf - q);
   float s, c;
-  sincosf((float)phi, &s, &c);
-  h.cr = (float)amp * c;
-  h.ci = (float)amp * s;
-  h.uy = (float)u.y;
-  h.uz = (float)u.z;
+  sincospif(2.0f * (float)cyc, &s, &c);
+  h.cr = amp * c;
+  h.ci = amp * s;
+  h.uy = uy;
+  h.uz = uz;
   h.prim = prim;
   h.key = key;
   A.hits[slot] = h;
   if (A.dbg_tau) A.dbg_tau[slot] = tau;
 }
 
+// Speckle phase of a hit in cycles: a 24-bit uniform fraction from the hash (exact in FP64).
 __device__ __forceinline__ double speckle(const TraceArgs& A, uint32_t ray, uint32_t sub, uint32_t bounce) {
   uint32_t x = ray, y = sub, z = 1u + bounce, w = A.seed32;
   pcg4d(x, y, z, w);
-  return dm(2.0 * kPi, u24(x));
+  return u24(x);
 }
 
 // Lambertian amplitude Gamma^2 sqrt(mu cos(k) dOmega) / L exp(-2 alpha L), in FP32: the
 // amplitude needs no more than FP32 precision, unlike the delay and phase.
-__device__ __forceinline__ double lambert(const TraceArgs& A, double gam, float mu, float kinc, float dOmega, double L) {
-  const float Lf = (float)L;
-  return (double)((float)(gam * gam) * sqrtf(mu * kinc * dOmega) / Lf * expf(-2.0f * (float)A.alpha * Lf));
+__device__ __forceinline__ float lambert(const TraceArgs& A, float gam, float mu, float kinc, float dOmega, float L) {
+  return gam * gam * sqrtf(mu * kinc * dOmega) / L * expf(-2.0f * A.alpha32 * L);
 }
 
 // ----------------------------------------------------------------- curved rays
@@ -366,8 +402,9 @@ __device__ void route_curved(const TraceArgs& A, int ping, D3 o, D3 d0, D3 us, u
       gam *= A.r_surface;
     } else {
       const float kinc = kinc32(A.sc, hq.leaf, dc);
-      double amp = lambert(A, gam, A.sc.tri_mu[hq.leaf], kinc, (float)dOmega, s_hit);
-      emit(A, ping, 2.0 * T_hit, amp, speckle(A, ray, sub, bounce), us, hq.prim, keybase | (uint32_t)bounce);
+      const float amp = lambert(A, (float)gam, A.sc.tri_mu[hq.leaf], kinc, (float)dOmega, (float)s_hit);
+      emit(A, ping, 2.0 * T_hit, amp, speckle(A, ray, sub, bounce), (float)us.y, (float)us.z, hq.prim,
+           keybase | (uint32_t)bounce);
       if (!((A.sc.tri_flags[hq.leaf] & 1) && bounce < A.max_bounces)) break;
       n = tri_normal64(A.sc, hq.leaf);  // FP64 only where the route continues
       gam *= A.r_seabed;
@@ -386,47 +423,46 @@ __device__ void route_curved(const TraceArgs& A, int ping, D3 o, D3 d0, D3 us, u
   }
 }
 
-__device__ void route_straight(const TraceArgs& A, int ping, D3 o, D3 d0, D3 us, uint32_t ray, uint32_t sub,
-                               double dOmega, uint32_t keybase) {
-  const double cw = A.ssp_c0;
-  const double L_stop = dm(A.T_stop, cw);
+__device__ void route_straight(const TraceArgs& A, int ping, D3 o, const float* o32, D3 d0, float uy, float uz,
+                               uint32_t ray, uint32_t sub, float dOmega, uint32_t keybase) {
   D3 pos = o, dir = d0;
-  double L = 0.0, gam = 1.0;
+  double L = 0.0;
+  float gam = 1.0f;
   int bounce = 0, prev = -1;
   for (int iter = 0; iter < 8; ++iter) {
-    double tlim = ds(L_stop, L);
+    const double tlim = A.L_stop - L;
     if (!(tlim > 0)) break;
-    Hit hq = closest_hit(A.sc, pos, dir, kEpsHit, tlim, prev, A.err);
+    Hit hq = closest_hit(A.sc, pos, dir, kEpsHit, tlim, prev, A.err, iter == 0 ? o32 : nullptr);
     double ts = INFINITY;
     if (A.has_surface && prev != -2 && dir.z != 0.0) {
       // divide only when the plane lies ahead within reach
-      const double num = ds(A.surface_z, pos.z);
+      const double num = A.surface_z - pos.z;
       if (num * dir.z > 0.0 && fabs(num) <= tlim * fabs(dir.z) * (1.0 + 1e-12)) {
-        double t = dd(num, dir.z);
+        const double t = fabs(dir.z) > 1e-30 ? ddiv_nr(num, dir.z) : dd(num, dir.z);
         if (t > kEpsHit && t <= tlim) ts = t;
       }
     }
     if (hq.prim < 0 && ts == INFINITY) break;
     if (ts < hq.t) {
       if (bounce >= A.max_bounces) break;
-      pos = axpy(pos, ts, dir);
-      L = da(L, ts);
+      pos = axpyf(pos, ts, dir);
+      L += ts;
       dir.z = -dir.z;
-      gam *= A.r_surface;
+      gam *= (float)A.r_surface;
       bounce++;
       prev = -2;
       continue;
     }
-    pos = axpy(pos, hq.t, dir);
-    L = da(L, hq.t);
+    L += hq.t;
     const float kinc = kinc32(A.sc, hq.leaf, dir);
-    double amp = lambert(A, gam, A.sc.tri_mu[hq.leaf], kinc, (float)dOmega, L);
-    emit(A, ping, 2.0 * dm(L, A.inv_c0), amp, speckle(A, ray, sub, bounce), us, hq.prim, keybase | (uint32_t)bounce);
+    const float amp = lambert(A, gam, A.sc.tri_mu[hq.leaf], kinc, dOmega, (float)L);
+    emit(A, ping, L * A.two_inv_c0, amp, speckle(A, ray, sub, bounce), uy, uz, hq.prim, keybase | (uint32_t)bounce);
     if ((A.sc.tri_flags[hq.leaf] & 1) && bounce < A.max_bounces) {
+      pos = axpyf(pos, hq.t, dir);
       const D3 n = tri_normal64(A.sc, hq.leaf);  // FP64 only where the route continues
-      double k = dm(2.0, dot(dir, n));
-      dir = d3(ds(dir.x, dm(k, n.x)), ds(dir.y, dm(k, n.y)), ds(dir.z, dm(k, n.z)));
-      gam *= A.r_seabed;
+      const double k = 2.0 * dotf(dir, n);
+      dir = d3(fma(-k, n.x, dir.x), fma(-k, n.y, dir.y), fma(-k, n.z, dir.z));
+      gam *= (float)A.r_seabed;
       bounce++;
       prev = hq.prim;
       continue;
@@ -443,13 +479,13 @@ __global__ void __launch_bounds__(128, 4) k_trace(TraceArgs A) {
     uint32_t ray = (uint32_t)(sr / A.n_sub), sub = (uint32_t)(sr % A.n_sub);
     int row = (int)(ray / A.n_ray_az);
     const DevPose& P = A.poses[ping];
-    D3 us = d3(A.ray_dirs[3 * sr], A.ray_dirs[3 * sr + 1], A.ray_dirs[3 * sr + 2]);
-    D3 dw = rot(P.R, us);
-    D3 o = d3(P.t[0], P.t[1], P.t[2]);
-    double dOmega = (double)A.row_domega[row];
-    uint32_t keybase = ((uint32_t)sr) << 2;
+    const D3 us = d3(A.ray_dirs[3 * sr], A.ray_dirs[3 * sr + 1], A.ray_dirs[3 * sr + 2]);
+    const D3 dw = rot(P.R, us);
+    const D3 o = d3(P.t[0], P.t[1], P.t[2]);
+    const float dOmega = A.row_domega[row];
+    const uint32_t keybase = ((uint32_t)sr) << 2;
     if (A.curved) route_curved(A, ping, o, dw, us, ray, sub, dOmega, keybase);
-    else route_straight(A, ping, o, dw, us, ray, sub, dOmega, keybase);
+    else route_straight(A, ping, o, P.t32, dw, (float)us.y, (float)us.z, ray, sub, dOmega, keybase);
   }
 }
 
@@ -537,7 +573,8 @@ __global__ void k_points(TraceArgs A) {
       left -= h;
     }
     double amp = sigma / (sarc * sarc) * exp(-2.0 * A.alpha * sarc);
-    emit(A, ping, 2.0 * T, amp, 0.0, rot_t(P.R, dw), -1, key);
+    const D3 u = rot_t(P.R, dw);
+    emit(A, ping, 2.0 * T, (float)amp, 0.0, (float)u.y, (float)u.z, -1, key);
     return;
   }
   int np = (A.has_surface ? 1 : 0) + A.sc.n_planes;
@@ -586,7 +623,8 @@ __global__ void k_points(TraceArgs A) {
   if (!leg_clear(A, a, x)) return;
   double amp = sigma * gam * gam / (L * L) * exp(-2.0 * A.alpha * L);
   D3 dw = d3(dv.x / L, dv.y / L, dv.z / L);
-  emit(A, ping, 2.0 * L / A.ssp_c0, amp, 0.0, rot_t(P.R, dw), -1, key);
+  const D3 u = rot_t(P.R, dw);
+  emit(A, ping, 2.0 * L / A.ssp_c0, (float)amp, 0.0, (float)u.y, (float)u.z, -1, key);
 }
 
 // Sonar-frame sub-ray directions (Sec. III Eq. 2-3 grid, cell-centred) with hashed
@@ -630,6 +668,7 @@ __global__ void k_poses(const double* raw, DevPose* poses, int n) {
   P.R[3] = 2 * (x * y + w * z);     P.R[4] = 1 - 2 * (x * x + z * z); P.R[5] = 2 * (y * z - w * x);
   P.R[6] = 2 * (x * z - w * y);     P.R[7] = 2 * (y * z + w * x);     P.R[8] = 1 - 2 * (x * x + y * y);
   P.t[0] = p[0]; P.t[1] = p[1]; P.t[2] = p[2];
+  P.t32[0] = (float)p[0]; P.t32[1] = (float)p[1]; P.t32[2] = (float)p[2];
   poses[i] = P;
 }
 
