@@ -50,14 +50,23 @@ def dist_setup():
 
 
 # ------------------------------------------------------------------ oracle sample
-def oracle_sample_params(p):
-    """1/8 of a ping: the central 1/8 of the vertical field of view (ray and beam rows),
-    all range bins, all elements."""
+def oracle_sample_params(p, k=8):
+    """1/k of a ping (k in 8, 16, 32, 64): the central 1/k of the vertical field of view
+    (ray and beam rows), all range bins, all elements."""
     q = dict(p)
-    q["vfov"] = p["vfov"] / 8
-    q["n_ray_el"] = p["n_ray_el"] // 8
-    q["n_beam_el"] = p["n_beam_el"] // 8
-    return q, 1.0 / 8.0
+    q["vfov"] = p["vfov"] / k
+    q["n_ray_el"] = p["n_ray_el"] // k
+    q["n_beam_el"] = p["n_beam_el"] // k
+    return q, 1.0 / k
+
+
+def sample_divisor(steps):
+    """Oracle sample size for a run of `steps` steps: about 0.4 s per 1/8 ping on 16 host
+    cores, so larger K takes smaller samples and the run stays near a minute."""
+    for k in (8, 16, 32):
+        if steps * 0.4 * 8 / k <= 60:
+            return k
+    return 64
 
 
 def oracle_ping(scene, params, pose, ssp):
@@ -68,38 +77,49 @@ def oracle_ping(scene, params, pose, ssp):
     return h["n"]
 
 
-def time_oracle(steps, warmup):
+def time_oracle(steps, warmup, min_seconds=0.0, k=8):
+    """Oracle pings/s on the 1/k-ping sample: `steps` samples, more until min_seconds pass."""
     import oracle
     from paper_2606_06130_gb300 import inputs
     scene, params, poses, ssp = inputs.workload("c2")
-    q, frac = oracle_sample_params(params)
+    q, frac = oracle_sample_params(params, k)
     for _ in range(warmup):
         oracle_ping(scene, q, poses[0], ssp)
     t0 = time.perf_counter()
-    for _ in range(steps):
+    done = 0
+    while done < steps or time.perf_counter() - t0 < min_seconds:
         oracle_ping(scene, q, poses[0], ssp)
+        done += 1
+    steps = done
     dt = time.perf_counter() - t0
     return {"value": steps * frac / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": "1/8 of the ping per step: central 1/8 of the vertical field of view (32 of 256 ray rows, "
-                      "8 of 64 beam rows), all 1024 bins and 1024 elements; FP64 C oracle, OpenMP",
+            "sample": f"1/{k} of the ping per step: central 1/{k} of the vertical field of view "
+                      f"({params['n_ray_el'] // k} of {params['n_ray_el']} ray rows, {params['n_beam_el'] // k} of "
+                      f"{params['n_beam_el']} beam rows), all 1024 bins and 1024 elements; FP64 C oracle, OpenMP",
             "seconds": dt, "steps": steps}
 
 
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
+    """nvidia-smi clock samples every 50 ms; only those taken inside [begin(), end()] count."""
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_id):
+        self.all_rows = []
         self.rows = []
+        self.t_begin = self.t_end = None
         self.proc = None
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_id), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.th = threading.Thread(target=self._read, daemon=True)
             self.th.start()
+            t0 = time.monotonic()
+            while not self.all_rows and time.monotonic() - t0 < 10.0:  # sampler running
+                time.sleep(0.01)
         except OSError:
             self.proc = None
 
@@ -107,7 +127,13 @@ class ClockSampler:
         for line in self.proc.stdout:
             parts = [x.strip() for x in line.split(",")]
             if len(parts) == 7:
-                self.rows.append(parts)
+                self.all_rows.append((time.monotonic(), parts))
+
+    def begin(self):
+        self.t_begin = time.monotonic()
+
+    def end(self):
+        self.t_end = time.monotonic()
 
     def stop(self):
         if self.proc is None:
@@ -117,6 +143,8 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
+        self.rows = [r for t, r in self.all_rows
+                     if self.t_begin is not None and self.t_begin <= t <= (self.t_end or t)]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
         mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
@@ -204,6 +232,7 @@ def run_ours(args, ws, rank, local):
     torch.cuda.synchronize()
     gpu_id = torch.cuda.get_device_properties(local).uuid if hasattr(torch.cuda.get_device_properties(local), "uuid") else local
     clocks = ClockSampler(f"GPU-{gpu_id}" if not isinstance(gpu_id, int) else gpu_id)
+    clocks.begin()
     for i in range(args.steps):
         flush.zero_()  # L2 flush outside the timed events
         ev[i][0].record(stream)
@@ -214,6 +243,7 @@ def run_ours(args, ws, rank, local):
             stages[k].append(st["ms_" + k])
         launches += st["kernels"]
     torch.cuda.synchronize()
+    clocks.end()
     clk = clocks.stop()
     t_ms = sum(a.elapsed_time(b) for a, b in ev)
     if ws > 1:
@@ -289,7 +319,7 @@ def run_ours(args, ws, rank, local):
     err = oracle_error(scene, params, pose, ssp, env, args.precision) if not args.no_oracle else None
     cpu = None
     if ws == 1 and not args.no_oracle:
-        cpu = time_oracle(1, 0)
+        cpu = time_oracle(1, 0, min_seconds=10.0)
     value = ws * args.steps / (t_ms / 1e3)
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": max(args.warmup, 3), "ms_per_step": t_ms / args.steps, "higher_is_better": True,
@@ -367,7 +397,7 @@ def other_forms(torch, s, inputs, dev):
 def run_reference(args, ws, rank):
     if rank != 0:
         return
-    r = time_oracle(args.steps, args.warmup)
+    r = time_oracle(args.steps, args.warmup, k=sample_divisor(args.steps + args.warmup))
     out = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * r["seconds"] / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -381,7 +411,7 @@ def run_reference(args, ws, rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16"])
