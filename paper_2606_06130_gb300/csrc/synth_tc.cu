@@ -11,13 +11,14 @@
 // passes hi*hi, hi*lo, lo*hi); one thread issues tcgen05.mma into a ring of TMEM
 // accumulators, one per tile; four epilogue warps add a tile's accumulator into S (FP32,
 // vector atomics) once the walk has passed it. N operands are stored as the real
-// 4-form: row (., 0) = (Re b, -Im b), row (., 1) = (Im b, Re b).
+// 4-form: a row (Re b, -Im b) gives the real part and a row (Im b, Re b) the imaginary
+// part of each complex output.
 //
 // k_synth_tz (arrays of nx ny = 128 L2 elements): with my = my_hi L2 + my_lo the z
 //   phasor factors as ez[my] = E1[my_hi] E2[my_lo] (E1 = ez at L2 my_hi, E2[my_lo] =
 //   exp(j theta_z my_lo)). The M operand A[(my_hi, mx)][k] = ey[mx] E1[my_hi] does not
 //   depend on the tile: it is written once per K-block into tensor memory (tcgen05.st),
-//   which the MMA reads as A. Only the N operand B[k][(n, my_lo, re/im)] = g_k(n)
+//   which the MMA reads as A. Only the N operand B[k][(re/im, n, my_lo)] = g_k(n)
 //   E2[my_lo] (T = 32 / L2 samples) is formed per tile, in shared memory. The sixteen
 //   generator warps form four independent groups, one per MMA K step (8 hits), each with
 //   one warp per TMEM lane quarter and its own named barrier.
@@ -143,6 +144,11 @@ __device__ __forceinline__ float2 tap_value(const float2* tab, float scale, floa
                  "=r"(r[15])                                                                                   \
                : "r"(taddr))
 
+#define TMEM_LD_8(taddr, r)                                                                       \
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"                 \
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]) \
+               : "r"(taddr))
+
 // Bounded wait that gives up for good once any role of the CTA has timed out.
 __device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* err) {
   if (*abort_flag) return false;
@@ -153,8 +159,10 @@ __device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity, vol
 
 // Epilogue role (warps 1..4): walks the K-blocks like the MMA issuer and, for every tile
 // the walk has passed, adds the accumulator columns of its TMEM slot into S. dst(u, pr)
-// is the S entry of column pair pr of this thread's lane row in tile u.
-template <int R, class Dst>
+// is the S entry of complex column pr of this thread's lane row in tile u; the real and
+// imaginary parts sit in adjacent columns (2 pr, 2 pr + 1), or, with HALVES, in columns
+// pr and 32 + pr of a 64-column accumulator.
+template <int R, bool HALVES, class Dst>
 __device__ __forceinline__ void epilogue_role(const SynthArgs& a, int64_t h0, int64_t h1, int lT, int W, int q,
                                               int lane, uint32_t tmem_base, uint64_t* tdone, uint64_t* tfree,
                                               volatile int* abort_flag, int n_cols, Dst dst) {
@@ -165,12 +173,24 @@ __device__ __forceinline__ void epilogue_role(const SynthArgs& a, int64_t h0, in
     const bool ok = wait_or_abort(smem_u32(&tdone[slot]), (cur >> slot) & 1u, abort_flag, a.err);
     if (ok) {
       tc_fence_after();
-      for (int c0 = 0; c0 < n_cols; c0 += 16) {
-        uint32_t v[16];
-        TMEM_LD_16(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(slot * 64 + c0), v);
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      const uint32_t ta = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(slot * 64);
+      if (HALVES) {
+        for (int c0 = 0; c0 < 32; c0 += 8) {
+          uint32_t re[8], im[8];
+          TMEM_LD_8(ta + c0, re);
+          TMEM_LD_8(ta + 32 + c0, im);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int i = 0; i < 8; ++i) red_add2(dst(u, c0 / 2 + i), __uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1]));
+          for (int i = 0; i < 8; ++i) red_add2(dst(u, c0 + i), __uint_as_float(re[i]), __uint_as_float(im[i]));
+        }
+      } else {
+        for (int c0 = 0; c0 < n_cols; c0 += 16) {
+          uint32_t v[16];
+          TMEM_LD_16(ta + c0, v);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int i = 0; i < 8; ++i) red_add2(dst(u, c0 / 2 + i), __uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1]));
+        }
       }
     }
     tc_fence_before();
@@ -254,7 +274,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_
 
   for (int i = threadIdx.x; i < kRTabS + 5; i += blockDim.x) s_rtab[i] = a.rtab_s[i];
   if (threadIdx.x == 0) {
-    for (int i = 0; i < NT; ++i) { mbar_init(smem_u32(&tb_full[i]), kGenWarps); mbar_init(smem_u32(&tb_empty[i]), 1); }
+    for (int i = 0; i < NT; ++i) { mbar_init(smem_u32(&tb_full[i]), kGenWarps / 2); mbar_init(smem_u32(&tb_empty[i]), 1); }
     for (int i = 0; i < 2; ++i) { mbar_init(smem_u32(&am_full[i]), kGenWarps); mbar_init(smem_u32(&am_empty[i]), 1); }
     for (int i = 0; i < ZRING; ++i) { mbar_init(smem_u32(&tdone[i]), 1); mbar_init(smem_u32(&tfree[i]), 4); }
     mbar_init(smem_u32(done), 1);
@@ -333,7 +353,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_
     const int q = warp & 3;  // TMEM lane quarter this warp may access
     const int L = q * 32 + lane;
     const int my_hi = L >> lnx, mx = L & (nx - 1);
-    epilogue_role<ZRING>(a, h0, h1, lT, W, q, lane, tmem_base, tdone, tfree, abort_flag, 64, [&](int u, int pr) {
+    epilogue_role<ZRING, true>(a, h0, h1, lT, W, q, lane, tmem_base, tdone, tfree, abort_flag, 64, [&](int u, int pr) {
       const int nl = pr >> lL2, my_lo = pr & (L2 - 1);
       const int64_t row = (int64_t)u * T + nl;
       return reinterpret_cast<float*>(a.S + row * M + (my_hi * L2 + my_lo) * nx + mx);
@@ -350,10 +370,13 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_
     const int nz = H1 + L2;
     // A operand: this thread's TMEM lane is row (my_hi, mx)
     const int arow = q * 32 + lane, a_hi = arow >> lnx, a_mx = arow & (nx - 1);
-    // B operand: a warp writes 32 rows of one of the group's two chunks (4 hits each)
-    const int cl = wi & 1, brow = (wi >> 1) * 32 + lane;
-    const int pr = brow >> 1, br = brow & 1, nl = pr >> lL2, my_lo = pr & (L2 - 1);
+    // B operand: lane = complex column pr = (n, my_lo), written as rows pr (re) and 32 + pr
+    // (im) of one of the group's two chunks (4 hits each); warps 0, 1 of the group take the
+    // even tiles of a K-block, warps 2, 3 the odd ones
+    const int cl = wi & 1, half = wi >> 1;
+    const int pr = lane, nl = pr >> lL2, my_lo = pr & (L2 - 1);
     const int bchunk = 2 * grp + cl;
+    const uint32_t boff = (uint32_t)(pr * 128 + ((bchunk ^ (pr & 7)) << 4));
     auto fetch = [&](int64_t hs) {
       uint4 v = make_uint4(0u, 0u, 0u, 0u);
       const int64_t k = hs + KG * grp + (tg >> 1);
@@ -443,25 +466,43 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_
         nk[kk] = S.n[4 * cl + kk];
         e2[kk] = S.ez[4 * cl + kk][H1 + my_lo];
       }
-      for (int t = kb.t_first; t <= kb.t_last; ++t) {
-        const int bslot = tix & (NT - 1);
-        wait_or_abort(smem_u32(&tb_empty[bslot]), ((tix / NT) & 1) ^ 1, abort_flag, a.err);
+      const int ntiles = kb.t_last - kb.t_first + 1;
+      for (int i = half; i < ntiles; i += 2) {
+        const unsigned tq = tix + (unsigned)i;
+        const int bslot = tq & (NT - 1);
+        wait_or_abort(smem_u32(&tb_empty[bslot]), ((tq / NT) & 1) ^ 1, abort_flag, a.err);
         const uint32_t bh = smem_u32(sB + bslot * 2 * N_BYTES), bl = bh + N_BYTES;
-        const int trow = t * T + nl;
-        float2 v[4];
+        const int trow = (kb.t_first + i) * T + nl;
+        // row pr: (Re b, -Im b); row 32 + pr: (Im b, Re b) = the same BF16 pair with its
+        // halves swapped and the new low half negated (rounding is sign-symmetric)
+        uint32_t hv[4], lv[4];
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk) {
           const int tap = trow - nk[kk];
-          float2 b = make_float2(0.f, 0.f);
-          if ((unsigned)tap < (unsigned)WT) b = cmul(S.g[tap][4 * cl + kk], e2[kk]);
-          v[kk] = br == 0 ? make_float2(b.x, -b.y) : make_float2(b.y, b.x);
+          float bx = 0.f, nby = 0.f;
+          if ((unsigned)tap < (unsigned)WT) {
+            const float2 g = S.g[tap][4 * cl + kk];
+            bx = g.x * e2[kk].x - g.y * e2[kk].y;
+            nby = -(g.x * e2[kk].y) - g.y * e2[kk].x;
+          }
+          hv[kk] = pack_bf16(bx, nby);
+          lv[kk] = pack_lo(bx, nby, hv[kk]);
         }
-        store_chunk(bh, bl, brow, bchunk, v, fp32_form);
+        sts128(bh + boff, hv[0], hv[1], hv[2], hv[3]);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) hv[kk] = __byte_perm(hv[kk], 0u, 0x1032) ^ 0x8000u;
+        sts128(bh + boff + 32 * 128, hv[0], hv[1], hv[2], hv[3]);
+        if (fp32_form) {
+          sts128(bl + boff, lv[0], lv[1], lv[2], lv[3]);
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) lv[kk] = __byte_perm(lv[kk], 0u, 0x1032) ^ 0x8000u;
+          sts128(bl + boff + 32 * 128, lv[0], lv[1], lv[2], lv[3]);
+        }
         fence_proxy_async();
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_u32(&tb_full[bslot]));
-        ++tix;
       }
+      tix += (unsigned)ntiles;
       ++j;
       h = hn;
     }
@@ -597,7 +638,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tc(SynthArgs a, uint32_
     const int q = warp & 3;
     const int L = q * 32 + lane;
     const int nl = L >> lnx, mx = L & (nx - 1);
-    epilogue_role<RING>(a, h0, h1, lT, W, q, lane, tmem_base, tdone, tfree, abort_flag, n_cols, [&](int u, int my) {
+    epilogue_role<RING, false>(a, h0, h1, lT, W, q, lane, tmem_base, tdone, tfree, abort_flag, n_cols, [&](int u, int my) {
       const int64_t row = (int64_t)u * T + nl;
       return reinterpret_cast<float*>(a.S + row * M + my * nx + mx);
     });
