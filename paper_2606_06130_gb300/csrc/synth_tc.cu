@@ -54,8 +54,18 @@ constexpr int NT = 8;              // per-tile B slots (hi + lo)
 constexpr int ZRING = 6;           // TMEM accumulators of 64 columns
 constexpr int kAcol = ZRING * 64;  // TMEM columns of the two per-K-block A slots (hi 32, lo 32)
 
+// The walk over tiles that every role repeats identically. Tiles are numbered by a
+// virtual index that only grows; an epoch maps tile base + i to the rows origin + T i ..
+// origin + T i + T - 1. A K-block may open a new epoch at its first row (origin = that row,
+// base past every tile used so far), which retires all live tiles.
+struct TileWalk {
+  int origin = -1, base = 0;           // current epoch (origin < 0: none yet)
+  int live_lo = INT_MAX, live_hi = -1;  // tiles that may still receive MMAs
+  __device__ __forceinline__ int row0(int t, int lT) const { return origin + ((t - base) << lT); }
+};
 struct KBlk {
   int cnt, t_first, t_last;
+  int origin, base;  // the epoch this K-block uses
 };
 
 // First-tap rows of the 32 sorted hits from h (lane i holds hit h + i; INT_MAX past the
@@ -66,19 +76,46 @@ __device__ __forceinline__ int load_window(const int32_t* ng, int64_t h, int64_t
 }
 
 // K-block starting at the window's first hit: as many hits (<= 32) as keep every tap
-// inside TMAX tiles of T = 2^lT rows. Warp-cooperative (all 32 lanes), identical in
-// every role. Rows are non-negative, so shifts are floor divisions.
-__device__ __forceinline__ KBlk kblock_from(int v, int lT, int W) {
-  const int g0 = __shfl_sync(0xffffffffu, v, 0);
+// inside TMAX tiles of T = 2^lT rows from the K-block's first tile. It stays in the
+// current epoch unless a new epoch at its first row n0 covers its hits with fewer tiles
+// per hit (an epoch at n0 needs ceil((span + W) / T) tiles, the fixed grid up to one more).
+// Warp-cooperative (all 32 lanes), identical in every role. Rows are sorted and
+// non-negative, so n0 >= origin and shifts are floor divisions.
+__device__ __forceinline__ KBlk kblock_from(int v, int lT, int W, const TileWalk& w) {
+  const int n0 = __shfl_sync(0xffffffffu, v, 0);
+  int tf = 0, tl = 0, cnt = 0;
+  if (w.origin >= 0) {
+    tf = (n0 - w.origin) >> lT;
+    const int lim = w.origin + ((tf + TMAX) << lT) - W;
+    cnt = __popc(__ballot_sync(0xffffffffu, v <= lim));
+    if (cnt < 1) cnt = 1;  // cannot happen for W <= T (TMAX - 1) + 1
+    tl = (__shfl_sync(0xffffffffu, v, cnt - 1) + W - 1 - w.origin) >> lT;
+  }
+  const int lim_f = n0 + (TMAX << lT) - W;
+  int cnt_f = __popc(__ballot_sync(0xffffffffu, v <= lim_f));
+  if (cnt_f < 1) cnt_f = 1;
+  const int tl_f = (__shfl_sync(0xffffffffu, v, cnt_f - 1) + W - 1 - n0) >> lT;
   KBlk k;
-  k.t_first = g0 >> lT;
-  const int limit = ((k.t_first + TMAX) << lT) - W;
-  const unsigned ok = __ballot_sync(0xffffffffu, v <= limit);
-  k.cnt = __popc(ok);
-  if (k.cnt < 1) k.cnt = 1;  // cannot happen for W <= T (TMAX - 1) + 1
-  const int g_last = __shfl_sync(0xffffffffu, v, k.cnt - 1);
-  k.t_last = (g_last + W - 1) >> lT;
+  if (w.origin < 0 || (tl_f + 1) * cnt < (tl - tf + 1) * cnt_f) {
+    k.origin = n0;
+    k.base = w.live_hi + 1;
+    k.cnt = cnt_f;
+    k.t_first = k.base;
+    k.t_last = k.base + tl_f;
+  } else {
+    k.origin = w.origin;
+    k.base = w.base;
+    k.cnt = cnt;
+    k.t_first = w.base + tf;
+    k.t_last = w.base + tl;
+  }
   return k;
+}
+__device__ __forceinline__ void walk_advance(TileWalk& w, const KBlk& kb) {
+  w.origin = kb.origin;
+  w.base = kb.base;
+  w.live_lo = kb.t_first;
+  if (kb.t_last > w.live_hi) w.live_hi = kb.t_last;
 }
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
@@ -167,8 +204,9 @@ __device__ __forceinline__ void epilogue_role(const SynthArgs& a, int64_t h0, in
                                               int lane, uint32_t tmem_base, uint64_t* tdone, uint64_t* tfree,
                                               volatile int* abort_flag, int n_cols, Dst dst) {
   uint32_t par = 0, cur = 0;  // per slot: parity of its use count, parity of the tile it holds
-  int live_lo = INT_MAX, live_hi = -1;
+  TileWalk w;
   auto flush = [&](int u) {
+    const int64_t r0 = w.row0(u, lT);
     const int slot = u % R;
     const bool ok = wait_or_abort(smem_u32(&tdone[slot]), (cur >> slot) & 1u, abort_flag, a.err);
     if (ok) {
@@ -181,7 +219,7 @@ __device__ __forceinline__ void epilogue_role(const SynthArgs& a, int64_t h0, in
           TMEM_LD_8(ta + 32 + c0, im);
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-          for (int i = 0; i < 8; ++i) red_add2(dst(u, c0 + i), __uint_as_float(re[i]), __uint_as_float(im[i]));
+          for (int i = 0; i < 8; ++i) red_add2(dst(r0, c0 + i), __uint_as_float(re[i]), __uint_as_float(im[i]));
         }
       } else {
         for (int c0 = 0; c0 < n_cols; c0 += 16) {
@@ -189,7 +227,7 @@ __device__ __forceinline__ void epilogue_role(const SynthArgs& a, int64_t h0, in
           TMEM_LD_16(ta + c0, v);
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-          for (int i = 0; i < 8; ++i) red_add2(dst(u, c0 / 2 + i), __uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1]));
+          for (int i = 0; i < 8; ++i) red_add2(dst(r0, c0 / 2 + i), __uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1]));
         }
       }
     }
@@ -199,20 +237,19 @@ __device__ __forceinline__ void epilogue_role(const SynthArgs& a, int64_t h0, in
   };
   int win = load_window(a.sorted_n, h0, h1, lane);
   for (int64_t h = h0; h < h1;) {
-    const KBlk kb = kblock_from(win, lT, W);
+    const KBlk kb = kblock_from(win, lT, W, w);
     const int64_t hn = h + kb.cnt;
     win = load_window(a.sorted_n, hn, h1, lane);
-    for (int u = live_lo; u <= live_hi && u < kb.t_first; ++u) flush(u);
-    for (int t = (live_hi + 1 > kb.t_first ? live_hi + 1 : kb.t_first); t <= kb.t_last; ++t) {
+    for (int u = w.live_lo; u <= w.live_hi && u < kb.t_first; ++u) flush(u);  // in their own epoch
+    for (int t = (w.live_hi + 1 > kb.t_first ? w.live_hi + 1 : kb.t_first); t <= kb.t_last; ++t) {
       const uint32_t bit = 1u << (t % R);
       cur = (cur & ~bit) | (par & bit);
       par ^= bit;
     }
-    live_lo = kb.t_first;
-    if (kb.t_last > live_hi) live_hi = kb.t_last;
+    walk_advance(w, kb);
     h = hn;
   }
-  for (int u = live_lo; u <= live_hi; ++u) flush(u);
+  for (int u = w.live_lo; u <= w.live_hi; ++u) flush(u);
 }
 
 __device__ __forceinline__ void tmem_alloc_512(uint32_t* slot) {
@@ -290,22 +327,23 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_
   if (warp == 0) {
     // ------------------------------------------------------------- MMA issuer
     uint32_t used = 0, par = 0;  // per slot: held a tile before, parity of its use count
-    int live_lo = INT_MAX, live_hi = -1, j = 0;
+    TileWalk w;
+    int j = 0;
     unsigned tix = 0;
     int win = load_window(a.sorted_n, h0, h1, lane);
     for (int64_t h = h0; h < h1;) {
-      const KBlk kb = kblock_from(win, lT, W);
+      const KBlk kb = kblock_from(win, lT, W, w);
       const int64_t hn = h + kb.cnt;
       win = load_window(a.sorted_n, hn, h1, lane);
       if (lane == 0) {
         // tiles the walk has passed: their accumulators are final once these MMAs land
-        for (int u = live_lo; u <= live_hi && u < kb.t_first; ++u) tc_commit(smem_u32(&tdone[u % ZRING]));
+        for (int u = w.live_lo; u <= w.live_hi && u < kb.t_first; ++u) tc_commit(smem_u32(&tdone[u % ZRING]));
         const int aslot = j & 1;
         const bool a_ok = wait_or_abort(smem_u32(&am_full[aslot]), (j >> 1) & 1, abort_flag, a.err);
         const uint32_t ah = tmem_base + (uint32_t)(kAcol + aslot * 64), al = ah + 32;
         for (int t = kb.t_first; t <= kb.t_last; ++t) {
           const int slot = t % ZRING;
-          const bool fresh = t > live_hi;
+          const bool fresh = t > w.live_hi;
           bool ok = a_ok;
           if (fresh) {
             const uint32_t bit = 1u << slot;
@@ -336,14 +374,13 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_
         }
         if (a_ok) tc_commit(smem_u32(&am_empty[aslot]));
       }
-      live_lo = kb.t_first;
-      if (kb.t_last > live_hi) live_hi = kb.t_last;
+      walk_advance(w, kb);
       ++j;
       h = hn;
       __syncwarp();
     }
     if (lane == 0) {
-      for (int u = live_lo; u <= live_hi; ++u) tc_commit(smem_u32(&tdone[u % ZRING]));
+      for (int u = w.live_lo; u <= w.live_hi; ++u) tc_commit(smem_u32(&tdone[u % ZRING]));
       tc_commit(smem_u32(done));
       mbar_wait(smem_u32(done), 0, a.err);
     }
@@ -353,9 +390,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_
     const int q = warp & 3;  // TMEM lane quarter this warp may access
     const int L = q * 32 + lane;
     const int my_hi = L >> lnx, mx = L & (nx - 1);
-    epilogue_role<ZRING, true>(a, h0, h1, lT, W, q, lane, tmem_base, tdone, tfree, abort_flag, 64, [&](int u, int pr) {
+    epilogue_role<ZRING, true>(a, h0, h1, lT, W, q, lane, tmem_base, tdone, tfree, abort_flag, 64, [&](int64_t r0, int pr) {
       const int nl = pr >> lL2, my_lo = pr & (L2 - 1);
-      const int64_t row = (int64_t)u * T + nl;
+      const int64_t row = r0 + nl;
       return reinterpret_cast<float*>(a.S + row * M + (my_hi * L2 + my_lo) * nx + mx);
     });
   } else {
@@ -389,10 +426,12 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_
       named_bar(bar_id, 128);
     }
     int win = load_window(a.sorted_n, h0, h1, lane);
+    TileWalk w;
     int j = 0;
     unsigned tix = 0;
     for (int64_t h = h0; h < h1;) {
-      const KBlk kb = kblock_from(win, lT, W);
+      const KBlk kb = kblock_from(win, lT, W, w);
+      walk_advance(w, kb);
       const int64_t hn = h + kb.cnt;
       win = load_window(a.sorted_n, hn, h1, lane);
       const uint4 recv = fetch(hn);
@@ -467,12 +506,13 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_
         e2[kk] = S.ez[4 * cl + kk][H1 + my_lo];
       }
       const int ntiles = kb.t_last - kb.t_first + 1;
+      const int trow0 = kb.origin + ((kb.t_first - kb.base) << lT) + nl;  // row nl of the first tile
       for (int i = half; i < ntiles; i += 2) {
         const unsigned tq = tix + (unsigned)i;
         const int bslot = tq & (NT - 1);
         wait_or_abort(smem_u32(&tb_empty[bslot]), ((tq / NT) & 1) ^ 1, abort_flag, a.err);
         const uint32_t bh = smem_u32(sB + bslot * 2 * N_BYTES), bl = bh + N_BYTES;
-        const int trow = (kb.t_first + i) * T + nl;
+        const int trow = trow0 + (i << lT);
         // row pr: (Re b, -Im b); row 32 + pr: (Im b, Re b) = the same BF16 pair with its
         // halves swapped and the new low half negated (rounding is sign-symmetric)
         uint32_t hv[4], lv[4];
@@ -581,19 +621,20 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tc(SynthArgs a, uint32_
   if (warp == 0) {
     // ------------------------------------------------------------- MMA issuer
     uint32_t used = 0, par = 0;
-    int live_lo = INT_MAX, live_hi = -1, j = 0, a_idx = 0;
+    TileWalk w;
+    int j = 0, a_idx = 0;
     int win = load_window(a.sorted_n, h0, h1, lane);
     for (int64_t h = h0; h < h1;) {
-      const KBlk kb = kblock_from(win, lT, W);
+      const KBlk kb = kblock_from(win, lT, W, w);
       const int64_t hn = h + kb.cnt;
       win = load_window(a.sorted_n, hn, h1, lane);
       if (lane == 0) {
-        for (int u = live_lo; u <= live_hi && u < kb.t_first; ++u) tc_commit(smem_u32(&tdone[u % RING]));
+        for (int u = w.live_lo; u <= w.live_hi && u < kb.t_first; ++u) tc_commit(smem_u32(&tdone[u % RING]));
         const int bslot = j % NB;
         const bool b_ok = wait_or_abort(smem_u32(&b_full[bslot]), (j / NB) & 1, abort_flag, a.err);
         for (int t = kb.t_first; t <= kb.t_last; ++t) {
           const int slot = t % RING;
-          const bool fresh = t > live_hi;
+          const bool fresh = t > w.live_hi;
           bool ok = b_ok;
           if (fresh) {
             const uint32_t bit = 1u << slot;
@@ -621,14 +662,13 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tc(SynthArgs a, uint32_
         }
         if (b_ok) tc_commit(smem_u32(&b_empty[bslot]));
       }
-      live_lo = kb.t_first;
-      if (kb.t_last > live_hi) live_hi = kb.t_last;
+      walk_advance(w, kb);
       ++j;
       h = hn;
       __syncwarp();
     }
     if (lane == 0) {
-      for (int u = live_lo; u <= live_hi; ++u) tc_commit(smem_u32(&tdone[u % RING]));
+      for (int u = w.live_lo; u <= w.live_hi; ++u) tc_commit(smem_u32(&tdone[u % RING]));
       tc_commit(smem_u32(done));
       mbar_wait(smem_u32(done), 0, a.err);
     }
@@ -638,8 +678,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tc(SynthArgs a, uint32_
     const int q = warp & 3;
     const int L = q * 32 + lane;
     const int nl = L >> lnx, mx = L & (nx - 1);
-    epilogue_role<RING, false>(a, h0, h1, lT, W, q, lane, tmem_base, tdone, tfree, abort_flag, n_cols, [&](int u, int my) {
-      const int64_t row = (int64_t)u * T + nl;
+    epilogue_role<RING, false>(a, h0, h1, lT, W, q, lane, tmem_base, tdone, tfree, abort_flag, n_cols, [&](int64_t r0, int my) {
+      const int64_t row = r0 + nl;
       return reinterpret_cast<float*>(a.S + row * M + my * nx + mx);
     });
   } else {
@@ -656,8 +696,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tc(SynthArgs a, uint32_
     };
     int win = load_window(a.sorted_n, h0, h1, lane);
     uint4 recv = fetch_recs(h0);
+    TileWalk w;
     for (int64_t h = h0; h < h1;) {
-      const KBlk kb = kblock_from(win, lT, W);
+      const KBlk kb = kblock_from(win, lT, W, w);
+      walk_advance(w, kb);
       const int64_t hn = h + kb.cnt;
       win = load_window(a.sorted_n, hn, h1, lane);
       Stage<WT>& S = st[j & 1];
@@ -722,7 +764,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tc(SynthArgs a, uint32_
         for (int idx = gt; idx < 128 * 8; idx += kGenThreads) {
           const int c = idx >> 7, row = idx & 127;
           const int nl = row >> lnx, mx = row & (nx - 1);
-          const int trow = t * T + nl;
+          const int trow = kb.origin + ((t - kb.base) << lT) + nl;
           float2 v[4];
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk) {
