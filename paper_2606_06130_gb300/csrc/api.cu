@@ -463,14 +463,16 @@ int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, cons
   ta.nr_pad = d.nr_pad;
   ta.n_routes = d.n_routes;
   ta.hits = ctx->hits;
+  ta.bin_counts = ctx->counts;
   ta.dbg_tau = ctx->debug ? ctx->dbg_tau : nullptr;
   ta.n_hits = ctx->n_hits;
   ta.hit_cap = ctx->hit_cap;
   ta.err = ctx->err_dev;
+  const int32_t n_bins = P * d.nr_pad;
+  CU(cudaMemsetAsync(ctx->counts, 0, sizeof(int32_t) * n_bins, st));
   CU(launch_trace(ta, ctx->sm_count, st));
   CU(launch_points(ta, st));
   mark(1);
-  const int32_t n_bins = P * d.nr_pad;
   CU(launch_bin(ctx->hits, ctx->n_hits, n_bins, ctx->counts, ctx->offsets, ctx->sorted, ctx->sorted_n, ctx->sm_count,
                 st));
   CU(cudaMemsetAsync(ctx->S, 0, sizeof(float2) * ctx->s_elems, st));
@@ -522,6 +524,8 @@ int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, cons
   ga.tiles_n = 2 * d.nb_pad / d.tile_n;
   ga.k_blocks = d.k_pad / 64;
   ga.n_phase = d.n_phase;
+  ga.xsel = d.n_phase == 3 ? 4 : 0;  // FP32 form: hi*hi, hi*lo (pass 1), lo*hi (pass 2)
+  ga.ysel = d.n_phase == 3 ? 2 : 0;
   ga.tile_n = d.tile_n;
   ga.f16 = f16 ? 1 : 0;
   ga.nr = d.nr;

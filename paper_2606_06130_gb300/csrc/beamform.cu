@@ -90,8 +90,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant_
         tile_coords(t, a.tiles_m, a.tiles_n, mb, nb);
         for (int it = 0; it < k_iters && ok; ++it) {
           const int ph = it / a.k_blocks, kb = it % a.k_blocks;
-          const CUtensorMap* ma = ph == 2 ? &a.map_xl : &a.map_xh;
-          const CUtensorMap* mbm = ph == 1 ? &a.map_yl : &a.map_yh;
+          const CUtensorMap* ma = ((a.xsel >> ph) & 1) ? &a.map_xl : &a.map_xh;
+          const CUtensorMap* mbm = ((a.ysel >> ph) & 1) ? &a.map_yl : &a.map_yh;
           if (!mbar_wait(smem_u32(&empty[stage]), phase ^ 1, a.err)) { ok = false; break; }
           mbar_expect_tx(smem_u32(&full[stage]), A_BYTES + B_BYTES);
           tma_load_2d(smem_u32(sA + stage * A_BYTES), ma, kb * BK, mb * BM, smem_u32(&full[stage]));
@@ -255,64 +255,77 @@ __global__ void k_steer(SteerArgs a) {
 
 // ----------------------------------------------------------------- peaks -> cloud
 // Per ping: decode each beam's packed (value, first index) maximum, apply the absolute
-// or ping-relative threshold, and write points in beam order. Block-wide exclusive scan
-// of the keep flags by warp shuffles; positions in FP32 (a 15 m range keeps them
-// within ~1e-6 m).
+// or ping-relative threshold, and write points in beam order. One CTA per 1024 beams of a
+// ping: it recounts the kept beams of the chunks before its own (a few thousand keys, so
+// no CTA waits on another), then places its own by a block-wide exclusive scan of the
+// keep flags. Positions in FP32 (a 15 m range keeps them within ~1e-6 m).
+__device__ __forceinline__ bool peak_kept(unsigned long long key, float thr) {
+  return key != 0ull && __uint_as_float((uint32_t)(key >> 32)) >= thr;
+}
+
 __global__ void __launch_bounds__(1024) k_peaks(PeakArgs a) {
   __shared__ int s_warp[32];
-  __shared__ long long s_base;
-  const int p = blockIdx.x, t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  __shared__ int s_before;
+  const int p = blockIdx.y, chunk = blockIdx.x, t = threadIdx.x, lane = t & 31, wid = t >> 5;
   const int Nb = a.n_beam_az * a.n_beam_el;
   const float vmax = __uint_as_float(a.ping_max[p]);
   const float thr = a.thr_mode == 1 ? a.thr * vmax : a.thr;
-  const DevPose& P = a.poses[p];
-  float R[9], T[3];
-  for (int k = 0; k < 9; ++k) R[k] = (float)P.R[k];
-  for (int k = 0; k < 3; ++k) T[k] = (float)P.t[k];
-  const float daz = (float)(a.hfov / a.n_beam_az), del = (float)(a.vfov / a.n_beam_el);
-  if (t == 0) s_base = 0;
+  const unsigned long long* keys = a.peak_keys + (size_t)p * Nb;
+  const int b0 = chunk * 1024;
+  // kept beams in the chunks before this one
+  int before = 0;
+  for (int b = t; b < b0; b += 1024) before += peak_kept(__ldg(&keys[b]), thr) ? 1 : 0;
+  for (int o = 16; o > 0; o >>= 1) before += __shfl_xor_sync(0xffffffffu, before, o);
+  if (lane == 0) s_warp[wid] = before;
   __syncthreads();
-  for (int b0 = 0; b0 < Nb; b0 += 1024) {
-    const int b = b0 + t;
-    const unsigned long long key = b < Nb ? a.peak_keys[(size_t)p * Nb + b] : 0ull;
-    const float val = __uint_as_float((uint32_t)(key >> 32));
-    const bool keep = key != 0ull && val >= thr;
-    const unsigned ballot = __ballot_sync(0xffffffffu, keep);
-    const int in_warp = __popc(ballot & ((1u << lane) - 1u));
-    if (lane == 0) s_warp[wid] = __popc(ballot);
-    __syncthreads();
-    if (wid == 0) {
-      int v = s_warp[lane], x = v;
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-      }
-      s_warp[lane] = x - v;  // exclusive prefix of warp counts
-    }
-    __syncthreads();
-    const long long pos = s_base + s_warp[wid] + in_warp;
-    if (keep && pos < a.cap) {
-      const int n = (int)(0xFFFFFFFFu - (uint32_t)(key & 0xFFFFFFFFull));
-      const int bi = b % a.n_beam_az, bj = b / a.n_beam_az;
-      float saz, caz, sel, cel;
-      sincosf((float)(-a.hfov / 2) + ((float)bi + 0.5f) * daz, &saz, &caz);
-      sincosf((float)(-a.vfov / 2) + ((float)bj + 0.5f) * del, &sel, &cel);
-      const float r = (float)a.r_min + ((float)n + 0.5f) * (float)a.dr;
-      const float v0 = r * cel * caz, v1 = r * cel * saz, v2 = r * sel;
-      sonar_point pt;
-      pt.x = R[0] * v0 + R[1] * v1 + R[2] * v2 + T[0];
-      pt.y = R[3] * v0 + R[4] * v1 + R[5] * v2 + T[1];
-      pt.z = R[6] * v0 + R[7] * v1 + R[8] * v2 + T[2];
-      pt.intensity = val;
-      pt.beam = b;
-      pt.bin = n;
-      a.cloud[(size_t)p * a.cap + pos] = pt;
-    }
-    __syncthreads();
-    if (t == 1023) s_base = pos + (keep ? 1 : 0);
-    __syncthreads();
+  if (wid == 0) {
+    int v = s_warp[lane];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) s_before = v;
   }
-  if (t == 0) a.n_cloud[p] = s_base;
+  __syncthreads();
+  const int base = s_before;
+  // this chunk: exclusive scan of the keep flags
+  const int b = b0 + t;
+  const unsigned long long key = b < Nb ? __ldg(&keys[b]) : 0ull;
+  const bool keep = peak_kept(key, thr);
+  const unsigned ballot = __ballot_sync(0xffffffffu, keep);
+  const int in_warp = __popc(ballot & ((1u << lane) - 1u));
+  __syncthreads();  // s_warp is reused
+  if (lane == 0) s_warp[wid] = __popc(ballot);
+  __syncthreads();
+  if (wid == 0) {
+    const int v = s_warp[lane];
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    s_warp[lane] = x - v;  // exclusive prefix of warp counts
+  }
+  __syncthreads();
+  const long long pos = (long long)base + s_warp[wid] + in_warp;
+  if (keep && pos < a.cap) {
+    const DevPose& P = a.poses[p];
+    const float daz = (float)(a.hfov / a.n_beam_az), del = (float)(a.vfov / a.n_beam_el);
+    const int n = (int)(0xFFFFFFFFu - (uint32_t)(key & 0xFFFFFFFFull));
+    const int bi = b % a.n_beam_az, bj = b / a.n_beam_az;
+    float saz, caz, sel, cel;
+    sincosf((float)(-a.hfov / 2) + ((float)bi + 0.5f) * daz, &saz, &caz);
+    sincosf((float)(-a.vfov / 2) + ((float)bj + 0.5f) * del, &sel, &cel);
+    const float r = (float)a.r_min + ((float)n + 0.5f) * (float)a.dr;
+    const float v0 = r * cel * caz, v1 = r * cel * saz, v2 = r * sel;
+    sonar_point pt;
+    pt.x = (float)P.R[0] * v0 + (float)P.R[1] * v1 + (float)P.R[2] * v2 + (float)P.t[0];
+    pt.y = (float)P.R[3] * v0 + (float)P.R[4] * v1 + (float)P.R[5] * v2 + (float)P.t[1];
+    pt.z = (float)P.R[6] * v0 + (float)P.R[7] * v1 + (float)P.R[8] * v2 + (float)P.t[2];
+    pt.intensity = __uint_as_float((uint32_t)(key >> 32));
+    pt.beam = b;
+    pt.bin = n;
+    a.cloud[(size_t)p * a.cap + pos] = pt;
+  }
+  // the last chunk knows the ping's total
+  if (chunk == gridDim.x - 1 && t == 1023) a.n_cloud[p] = pos + (keep ? 1 : 0);
 }
 
 }  // namespace
@@ -345,7 +358,8 @@ cudaError_t launch_gemm(const GemmArgs& a, int sm_count, cudaStream_t st) {
 }
 
 cudaError_t launch_peaks(const PeakArgs& a, cudaStream_t st) {
-  k_peaks<<<a.n_pings, 1024, 0, st>>>(a);
+  const int nb = a.n_beam_az * a.n_beam_el;
+  k_peaks<<<dim3((unsigned)ceil_div(nb, 1024), a.n_pings), 1024, 0, st>>>(a);
   return cudaGetLastError();
 }
 

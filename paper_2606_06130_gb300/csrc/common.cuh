@@ -93,6 +93,7 @@ struct TraceArgs {
   int32_t nr_pad;
   int32_t n_routes;              // point-scatterer routes per point
   HitRec* hits;
+  int32_t* bin_counts;           // [n_pings * nr_pad] hits per first-tap row (zeroed by the caller)
   double* dbg_tau;               // nullable: FP64 delay per hit
   unsigned long long* n_hits;    // device counter
   int64_t hit_cap;
@@ -147,6 +148,8 @@ struct SynthArgs {
   int32_t n_pass;           // tensor-core synthesis: 3 (BF16 hi/lo split) or 1
   int* err;
 };
+// Counting sort of the hits by first-tap row; counts[] holds the per-row histogram (the
+// trace kernels count as they emit) and doubles as the scatter cursor.
 cudaError_t launch_bin(const HitRec* hits, const unsigned long long* n_hits, int32_t n_bins,
                        int32_t* counts, int32_t* offsets, HitRec* sorted, int32_t* sorted_n,
                        int sm_count, cudaStream_t st);
@@ -180,6 +183,7 @@ cudaError_t launch_steer(const SteerArgs& a, cudaStream_t st);
 struct GemmArgs {
   CUtensorMap map_xh, map_xl, map_yh, map_yl;
   int32_t tiles_m, tiles_n, k_blocks, n_phase, tile_n;
+  int32_t xsel, ysel;        // bit p: pass p reads the lo part of X (echoes) / Y (steering)
   int32_t f16;               // operands FP16 (1) or BF16 (0)
   int32_t nr, nr_x, n_beams, n_blank;
   float r_min, dr, alpha2;   // TVG(r) = r exp(alpha2 r)

@@ -12,21 +12,6 @@
 namespace sonar {
 namespace {
 
-// Hits arrive in ray order, so neighbouring lanes usually share a bin: one atomic per
-// distinct bin in the warp (__match_any_sync), added by the group's lowest lane.
-__global__ void k_hist(const HitRec* hits, const unsigned long long* n_hits, int32_t n_bins, int32_t* counts) {
-  const int64_t n = (int64_t)*n_hits;
-  const int lane = threadIdx.x & 31;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); i0 < n; i0 += stride) {
-    const int64_t i = i0 + lane;
-    int g = i < n ? hits[i].nglob : -1;
-    if (g >= n_bins) g = -1;
-    const unsigned grp = __match_any_sync(0xffffffffu, g);
-    if (g >= 0 && lane == __ffs(grp) - 1) atomicAdd(&counts[g], __popc(grp));
-  }
-}
-
 // Exclusive scan of counts (single CTA of 1024 threads); offsets[n_bins] = total.
 __global__ void __launch_bounds__(1024) k_scan(const int32_t* counts, int32_t n_bins, int32_t* offsets, int32_t* cursor) {
   __shared__ int32_t part[1024];
@@ -53,18 +38,25 @@ __global__ void __launch_bounds__(1024) k_scan(const int32_t* counts, int32_t n_
   if (t == 1023) offsets[n_bins] = part[1023];
 }
 
+// Hits arrive in ray order, so neighbouring lanes usually share a row: one atomic per
+// distinct row in the warp (__match_any_sync), taken by the group's lowest lane. Records
+// move as two 16-byte vectors.
 __global__ void k_scatter(const HitRec* hits, const unsigned long long* n_hits, int32_t n_bins, int32_t* cursor,
                           HitRec* sorted, int32_t* sorted_n) {
   const int64_t n = (int64_t)*n_hits;
   const int lane = threadIdx.x & 31;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  static_assert(sizeof(HitRec) == 32, "HitRec is two 16-byte vectors");
   for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); i0 < n; i0 += stride) {
     const int64_t i = i0 + lane;
-    HitRec h;
+    uint4 v0 = make_uint4(0u, 0u, 0u, 0u), v1 = v0;
     int g = -1;
     if (i < n) {
-      h = hits[i];
-      g = h.nglob < n_bins ? h.nglob : -1;
+      const uint4* src = reinterpret_cast<const uint4*>(hits + i);
+      v0 = __ldg(src);
+      v1 = __ldg(src + 1);
+      g = (int)v0.x;  // nglob is the record's first word
+      if (g >= n_bins) g = -1;
     }
     const unsigned grp = __match_any_sync(0xffffffffu, g);
     const int leader = __ffs(grp) - 1;
@@ -73,7 +65,9 @@ __global__ void k_scatter(const HitRec* hits, const unsigned long long* n_hits, 
     base = __shfl_sync(0xffffffffu, base, leader);
     if (g >= 0) {
       const int pos = base + __popc(grp & ((1u << lane) - 1u));
-      sorted[pos] = h;
+      uint4* dst = reinterpret_cast<uint4*>(sorted + pos);
+      dst[0] = v0;
+      dst[1] = v1;
       sorted_n[pos] = g;
     }
   }
@@ -306,9 +300,6 @@ __global__ void k_gain_pow2(float* gain, int n, int mode) {
 
 cudaError_t launch_bin(const HitRec* hits, const unsigned long long* n_hits, int32_t n_bins, int32_t* counts,
                        int32_t* offsets, HitRec* sorted, int32_t* sorted_n, int sm_count, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(int32_t) * n_bins, st);
-  if (e != cudaSuccess) return e;
-  k_hist<<<sm_count * 8, 256, 0, st>>>(hits, n_hits, n_bins, counts);
   k_scan<<<1, 1024, 0, st>>>(counts, n_bins, offsets, counts);
   // counts now doubles as the scatter cursor
   k_scatter<<<sm_count * 8, 256, 0, st>>>(hits, n_hits, n_bins, counts, sorted, sorted_n);

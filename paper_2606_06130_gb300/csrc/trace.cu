@@ -293,6 +293,12 @@ __device__ void emit(const TraceArgs& A, int ping, double tau, float amp, double
   const bool in_rows = nfi >= -kPad && nfi < (int64_t)A.nr_pad - kPad;
   h.nglob = in_rows ? ping * A.nr_pad + (int)nfi + kPad : -1;
   h.u0 = (float)(nf - q);
+  // histogram of first-tap rows for the counting sort: one atomic per distinct row among
+  // the emitting lanes
+  {
+    const unsigned grp = __match_any_sync(__activemask(), h.nglob);
+    if (h.nglob >= 0 && (int)(threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(&A.bin_counts[h.nglob], __popc(grp));
+  }
   float s, c;
   sincospif(2.0f * (float)cyc, &s, &c);
   h.cr = amp * c;
