@@ -25,6 +25,7 @@
 // k_synth_tc (small arrays): A[(n, mx)][k] = g_k(n) ey[mx] per tile (T = 128 / nx) and
 //   B[k][(my, re/im)] = ez[my] once per K-block, both in shared memory.
 #include <limits.h>
+#include <stddef.h>
 
 #include "common.cuh"
 #include "tcgen05.cuh"
@@ -264,14 +265,20 @@ __device__ __forceinline__ void tmem_free_512(uint32_t base) {
 // =====================================================================================
 // k_synth_tz: z-split operands, per-K-block A in tensor memory
 // =====================================================================================
+// Records are stored into the stage as 16-byte vectors: every stage starts on a 16-byte
+// boundary (alignas makes the size a multiple of 16 too).
 template <int WT>
-struct ZStage {  // one generator group's 8 hits of one K-block
+struct alignas(16) ZStage {  // one generator group's 8 hits of one K-block
   HitRec rec[KG];
   int n[KG];
   float2 g[WT][KG];        // taps, tap-major
   float2 ey[KG][kMaxAx];
   float2 ez[KG][kMaxAx];   // E1 in [0, H1), E2 in [H1, H1 + L2)
 };
+
+static_assert(sizeof(ZStage<8>) % 16 == 0 && sizeof(ZStage<12>) % 16 == 0 && sizeof(ZStage<16>) % 16 == 0,
+              "stages hold 16-byte vector stores");
+static_assert(offsetof(ZStage<8>, rec) % 16 == 0, "records are 16-byte aligned in a stage");
 
 template <int WT>
 constexpr size_t tz_smem_bytes() {
@@ -559,13 +566,16 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_
 // k_synth_tc: per-tile A = taps x ey, per-K-block B = ez (small arrays)
 // =====================================================================================
 template <int WT>
-struct Stage {
+struct alignas(16) Stage {
   HitRec rec[KH];
   int n[KH];
   float2 g[WT][KH];        // tap-major: staging writes and operand reads are conflict-free
   float2 ey[KH][kMaxAx];   // per hit, element-major: a warp reads consecutive elements
   float2 ez[KH][kMaxAx];
 };
+
+static_assert(sizeof(Stage<8>) % 16 == 0 && sizeof(Stage<12>) % 16 == 0 && sizeof(Stage<16>) % 16 == 0,
+              "stages hold 16-byte vector stores");
 
 template <int WT>
 constexpr size_t tc_smem_bytes() {
