@@ -366,14 +366,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_
             // K step kk advances B by 32 bytes: +2 in the descriptor's address field
             const uint64_t bdh = sw128_desc(smem_u32(sB + bslot * 2 * N_BYTES));
             const uint64_t bdl = bdh + (N_BYTES >> 4);
-            tc_mma_tmem_a(d, ah, bdh, idesc, fresh ? 0u : 1u);
-#pragma unroll
-            for (int kk = 1; kk < 4; ++kk) tc_mma_tmem_a(d, ah + kk * 8, bdh + 2 * kk, idesc, 1u);
+            tc_mma4_tmem_a(d, ah, bdh, idesc, fresh ? 0u : 1u);
             if (fp32_form) {
-#pragma unroll
-              for (int kk = 0; kk < 4; ++kk) tc_mma_tmem_a(d, ah + kk * 8, bdl + 2 * kk, idesc, 1u);
-#pragma unroll
-              for (int kk = 0; kk < 4; ++kk) tc_mma_tmem_a(d, al + kk * 8, bdh + 2 * kk, idesc, 1u);
+              tc_mma4_tmem_a(d, ah, bdl, idesc, 1u);
+              tc_mma4_tmem_a(d, al, bdh, idesc, 1u);
             }
             tc_commit(smem_u32(&tb_empty[bslot]));
           }

@@ -82,6 +82,23 @@ __device__ __forceinline__ void tc_mma_tmem_a(uint32_t d_tmem, uint32_t a_tmem, 
       ::"r"(d_tmem), "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(acc)
       : "memory");
 }
+// Four MMAs of consecutive K steps with A in tensor memory: A advances 8 columns (16
+// elements) and the B descriptor 2 (32 bytes of a 128-byte swizzled row) per step; the
+// first accumulates into D unless acc0 is 0, the rest always do.
+__device__ __forceinline__ void tc_mma4_tmem_a(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
+                                               uint32_t acc0) {
+  asm volatile(
+      "{\n .reg .pred p, q;\n .reg .b32 a1, a2, a3;\n .reg .b64 b1, b2, b3;\n"
+      " setp.ne.b32 p, %4, 0;\n setp.eq.b32 q, %4, %4;\n"
+      " add.u32 a1, %1, 8;\n add.u32 a2, %1, 16;\n add.u32 a3, %1, 24;\n"
+      " add.u64 b1, %2, 2;\n add.u64 b2, %2, 4;\n add.u64 b3, %2, 6;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], [a1], b1, %3, q;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], [a2], b2, %3, q;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], [a3], b3, %3, q;\n}\n"
+      ::"r"(d_tmem), "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(acc0)
+      : "memory");
+}
 // Eight consecutive 32-bit columns of this thread's TMEM lane.
 __device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&v)[8]) {
   asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
