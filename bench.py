@@ -42,6 +42,25 @@ def peaks_file():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
+def max_over_ranks(x: float, ws: int) -> float:
+    """Maximum of a host value over all ranks (the slowest rank's time); identity at N=1.
+    The tensor lives where the process group's backend wants it (CUDA for NCCL)."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(ws: int, steps_per_rank: int, seconds: float) -> float:
+    """Units per second of the whole job: every rank processes steps_per_rank pings in
+    the (max-over-ranks) time."""
+    return ws * steps_per_rank / seconds
+
+
 def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -245,11 +264,7 @@ def run_ours(args, ws, rank, local):
     torch.cuda.synchronize()
     clocks.end()
     clk = clocks.stop()
-    t_ms = sum(a.elapsed_time(b) for a, b in ev)
-    if ws > 1:
-        t = torch.tensor([t_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_ms = float(t.item())
+    t_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), ws)
     stats = s.stats()
 
     # end to end through the C ABI with host buffers: pinned env, host cloud
@@ -263,11 +278,7 @@ def run_ours(args, ws, rank, local):
     for _ in range(k_e2e):
         s.ping_batch([pose], params, ssp, precision=args.precision, env=env_h[None], cloud=cloud_h[None], cloud_cap=nb)
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - e0
-    if ws > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(time.perf_counter() - e0, ws)
 
     # the same ping replayed as a captured CUDA graph (no stage events)
     s.set_option(SONAR_OPT_TIMING, 0)
@@ -283,6 +294,7 @@ def run_ours(args, ws, rank, local):
         g1.record(stream)
         g1.synchronize()
         g_ms += g0.elapsed_time(g1)
+    g_ms = max_over_ranks(g_ms, ws)
 
     # other forms (same run): BF16 single ping, BF16 64-ping trajectory batch
     forms = {}
@@ -320,7 +332,7 @@ def run_ours(args, ws, rank, local):
     cpu = None
     if ws == 1 and not args.no_oracle:
         cpu = time_oracle(1, 0, min_seconds=10.0)
-    value = ws * args.steps / (t_ms / 1e3)
+    value = whole_job_rate(ws, args.steps, t_ms / 1e3)
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": max(args.warmup, 3), "ms_per_step": t_ms / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else args.precision,
@@ -334,9 +346,9 @@ def run_ours(args, ws, rank, local):
            "stages_ms": mean_stage,
            "hits_per_ping": stats["n_hits"],
            "gpu_launches": launches,
-           "graph_replay": {"value": ws * args.steps / (g_ms / 1e3), "unit": UNIT,
+           "graph_replay": {"value": whole_job_rate(ws, args.steps, g_ms / 1e3), "unit": UNIT,
                             "note": "same steps replayed as one CUDA graph per ping, no stage events"},
-           "e2e": {"value": ws * k_e2e / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 56,
+           "e2e": {"value": whole_job_rate(ws, k_e2e, e2e_s), "unit": UNIT, "h2d_bytes_per_step": 56,
                    "d2h_bytes_per_step": int(env.numel() * 4 + nb * 24 + 8), "steps": k_e2e,
                    "path": "sonar_ping_batch with pinned host env and pageable host cloud"},
            "clocks": clk,
