@@ -145,7 +145,9 @@ SONAR_API const char* sonar_last_error(const sonar_ctx* ctx);
    sonar_stats; calls then launch their kernels directly instead of replaying the
    graph (graph event nodes cannot be timed).
    SONAR_OPT_GRAPH: 1 (default) replays the ping pipeline as a captured CUDA graph.
-   SONAR_OPT_TILE_N: beamforming N tile (128 or 256; 0 = autotuned). */
+   SONAR_OPT_TILE_N: beamforming N tile (128, 192, 224 or 256); 0 (default) picks per
+   call the width that minimises waves x width, waves being the output tiles over the
+   SMs rounded up. */
 #define SONAR_OPT_DEBUG 1
 #define SONAR_OPT_TIMING 2
 #define SONAR_OPT_GRAPH 3

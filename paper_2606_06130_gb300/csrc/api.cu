@@ -16,7 +16,23 @@ using namespace sonar;
 
 namespace {
 
-constexpr int kTileDefault = 256;
+// Beamforming N tiles the GEMM is built for; 0 picks per call the one that minimises
+// waves x width (waves = output tiles / SMs, rounded up): the last wave of a few large
+// tiles can leave most SMs idle.
+constexpr int kTiles[] = {256, 224, 192};
+
+int pick_tile_n(int64_t nr_rows_tiles, int64_t nb, int sm_count) {
+  int best = 256;
+  int64_t best_cost = INT64_MAX;
+  for (int bn : kTiles) {
+    const int64_t nb_pad = (nb + bn / 2 - 1) / (bn / 2) * (bn / 2);
+    const int64_t tiles = nr_rows_tiles * (2 * nb_pad / bn);
+    const int64_t waves = (tiles + sm_count - 1) / sm_count;
+    const int64_t cost = waves * bn;
+    if (cost < best_cost) { best_cost = cost; best = bn; }
+  }
+  return best;
+}
 
 template <typename T>
 void dfree(T*& p) {
@@ -173,7 +189,7 @@ int validate(sonar_ctx* ctx, const sonar_params* p, const sonar_ssp* ssp) {
   return SONAR_OK;
 }
 
-int derive(sonar_ctx* ctx, const sonar_params* p, const sonar_ssp* ssp, double z_sonar, Derived& d) {
+int derive(sonar_ctx* ctx, const sonar_params* p, const sonar_ssp* ssp, double z_sonar, int n_pings, Derived& d) {
   d.ssp_z0 = 0.0;
   d.ssp_g = 0.0;
   int nn = ssp ? ssp->n_nodes : 0;
@@ -205,7 +221,8 @@ int derive(sonar_ctx* ctx, const sonar_params* p, const sonar_ssp* ssp, double z
   d.M = p->nx * p->ny;
   d.k_pad = (int)round_up(2LL * d.M, 64);
   d.nb = p->n_beam_az * p->n_beam_el;
-  d.tile_n = ctx->tile_opt == 128 ? 128 : kTileDefault;
+  d.tile_n = ctx->tile_opt != 0 ? ctx->tile_opt
+                                 : pick_tile_n((int64_t)n_pings * d.nr_x / 128, d.nb, ctx->sm_count);
   d.nb_pad = (int)round_up(d.nb, d.tile_n / 2);
   d.n_phase = p->precision == SONAR_FP32 ? 3 : 1;
   d.n_blank = 0;
@@ -586,7 +603,7 @@ int run(sonar_ctx* ctx, const sonar_pose* poses, int P, const sonar_params* p, c
   CU(cudaEventRecord(ctx->ev_in, ctx->user_stream));
   CU(cudaStreamWaitEvent(ctx->stream, ctx->ev_in, 0));
   Derived d;
-  if ((rc = derive(ctx, p, ssp, poses[0].t[2], d))) return rc;
+  if ((rc = derive(ctx, p, ssp, poses[0].t[2], P, d))) return rc;
   if ((int64_t)P * d.nr_pad + 1 > (1LL << 31) - 1) return fail(ctx, SONAR_E_UNSUPPORTED, "batch too large");
   if ((rc = ensure_tables(ctx, p, d))) return rc;
   if ((rc = ensure_workspace(ctx, P, d))) return rc;
@@ -748,7 +765,8 @@ int sonar_set_option(sonar_ctx* ctx, int32_t option, int64_t value) {
       ctx->synth_opt = (int)value;
       break;
     case SONAR_OPT_TILE_N:
-      if (value != 0 && value != 128 && value != 256) return fail(ctx, SONAR_E_ARG, "tile_n must be 0, 128 or 256");
+      if (value != 0 && value != 128 && value != 192 && value != 224 && value != 256)
+        return fail(ctx, SONAR_E_ARG, "tile_n must be 0, 128, 192, 224 or 256");
       ctx->tile_opt = (int)value;
       break;
     default: return fail(ctx, SONAR_E_ARG, "unknown option %d", option);

@@ -28,6 +28,10 @@ constexpr int BK = 64;
 constexpr int STAGES = 4;
 constexpr int kGemmThreads = 192;  // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
 
+// TMEM columns of the double-buffered accumulator: 2 BN rounded up to a power of two
+// (allocation granularity).
+constexpr uint32_t tmem_cols(int bn) { return 2 * bn <= 256 ? 256u : 512u; }
+
 
 // Tile order: groups of up to 16 row tiles; inside a group the column tiles run in
 // the outer loop, so concurrently running CTAs share one steering block through L2.
@@ -70,7 +74,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant_
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(2 * BN) : "memory");
+                 "r"(tmem_cols(BN)) : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   tc_fence_before();
@@ -205,7 +209,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant_
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(2 * BN) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(tmem_cols(BN)) : "memory");
   }
 }
 
@@ -336,23 +340,32 @@ cudaError_t launch_steer(const SteerArgs& a, cudaStream_t st) {
 }
 
 // Dynamic shared-memory opt-in of the GEMM kernels (once per device, outside capture).
+template <int BN>
+cudaError_t gemm_attr() {
+  return cudaFuncSetAttribute(k_gemm<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem<BN>());
+}
 cudaError_t prepare_gemm() {
-  cudaError_t e = cudaFuncSetAttribute(k_gemm<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem<256>());
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_gemm<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem<128>());
+  cudaError_t e;
+  if ((e = gemm_attr<256>()) != cudaSuccess) return e;
+  if ((e = gemm_attr<224>()) != cudaSuccess) return e;
+  if ((e = gemm_attr<192>()) != cudaSuccess) return e;
+  return gemm_attr<128>();
+}
+
+template <int BN>
+void launch_bn(const GemmArgs& a, int grid, cudaStream_t st) {
+  k_gemm<BN><<<grid, kGemmThreads, gemm_smem<BN>(), st>>>(a, make_idesc(a.f16 ? 0 : 1, BM, BN));
 }
 
 cudaError_t launch_gemm(const GemmArgs& a, int sm_count, cudaStream_t st) {
   const int n_tiles = a.tiles_m * a.tiles_n;
   const int grid = n_tiles < sm_count ? n_tiles : sm_count;
-  const uint32_t idesc_bf16_256 = make_idesc(1, BM, 256), idesc_f16_256 = make_idesc(0, BM, 256);
-  const uint32_t idesc_bf16_128 = make_idesc(1, BM, 128), idesc_f16_128 = make_idesc(0, BM, 128);
-  const bool is_f16 = a.f16 != 0;
-  const int tn = a.tile_n;
-  if (tn == 256) {
-    k_gemm<256><<<grid, kGemmThreads, gemm_smem<256>(), st>>>(a, is_f16 ? idesc_f16_256 : idesc_bf16_256);
-  } else {
-    k_gemm<128><<<grid, kGemmThreads, gemm_smem<128>(), st>>>(a, is_f16 ? idesc_f16_128 : idesc_bf16_128);
+  switch (a.tile_n) {
+    case 256: launch_bn<256>(a, grid, st); break;
+    case 224: launch_bn<224>(a, grid, st); break;
+    case 192: launch_bn<192>(a, grid, st); break;
+    case 128: launch_bn<128>(a, grid, st); break;
+    default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
