@@ -155,6 +155,15 @@ __device__ __forceinline__ void store_chunk(uint32_t hi_base, uint32_t lo_base, 
   if (fp32_form) sts128(lo_base + off, lv[0], lv[1], lv[2], lv[3]);
 }
 
+// sin(pi x), cos(pi x) for the element phasors, which only feed BF16 operands (2^-9
+// rounding, 2^-17 with the hi/lo split): x is reduced exactly to r in [-1, 1]
+// (x - 2 rint(x / 2) has no rounding for |x| < 2^22), then the hardware sine and cosine
+// on [-pi, pi] (absolute error ~5e-7).
+__device__ __forceinline__ void sincospi_operand(float x, float* s, float* c) {
+  const float r = x - 2.0f * rintf(0.5f * x);
+  __sincosf(3.14159265358979f * r, s, c);
+}
+
 // Tap c_k R(u) from the shared-memory pulse table by 4-point Lagrange interpolation
 // (error ~4e-8); zero outside the pulse support.
 __device__ __forceinline__ float2 tap_value(const float2* tab, float scale, float u, float cr, float ci) {
@@ -457,7 +466,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_
         float2 e = make_float2(0.f, 0.f);
         if (kl < kvalid) {
           float s, c;
-          sincospif(pl2 * ((float)mx - 0.5f * (float)(nx - 1)) * S.rec[kl].uy, &s, &c);
+          sincospi_operand(pl2 * ((float)mx - 0.5f * (float)(nx - 1)) * S.rec[kl].uy, &s, &c);
           e = make_float2(c, s);
         }
         S.ey[kl][mx] = e;
@@ -469,7 +478,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_
         if (kl < kvalid) {
           const float arg = qz < H1 ? (float)(L2 * qz) - 0.5f * (float)(ny - 1) : (float)(qz - H1);
           float s, c;
-          sincospif(pl2 * arg * S.rec[kl].uz, &s, &c);
+          sincospi_operand(pl2 * arg * S.rec[kl].uz, &s, &c);
           e = make_float2(c, s);
         }
         S.ez[kl][qz] = e;
@@ -726,7 +735,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tc(SynthArgs a, uint32_
         float2 e = make_float2(0.f, 0.f);
         if (k < kb.cnt) {
           float s, c;
-          sincospif(pl2 * ((float)mx - 0.5f * (float)(nx - 1)) * S.rec[k].uy, &s, &c);
+          sincospi_operand(pl2 * ((float)mx - 0.5f * (float)(nx - 1)) * S.rec[k].uy, &s, &c);
           e = make_float2(c, s);
         }
         S.ey[k][mx] = e;
@@ -736,7 +745,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tc(SynthArgs a, uint32_
         float2 e = make_float2(0.f, 0.f);
         if (k < kb.cnt) {
           float s, c;
-          sincospif(pl2 * ((float)my - 0.5f * (float)(ny - 1)) * S.rec[k].uz, &s, &c);
+          sincospi_operand(pl2 * ((float)my - 0.5f * (float)(ny - 1)) * S.rec[k].uz, &s, &c);
           e = make_float2(c, s);
         }
         S.ez[k][my] = e;
