@@ -89,8 +89,7 @@ struct sonar_ctx {
 
   // workspaces
   int p_cap = 0;
-  double* raw_host = nullptr;  // pinned [p][7]
-  double* raw_dev = nullptr;
+  DevPose* pose_host = nullptr;  // pinned [p]: rotation and position of each ping
   DevPose* poses = nullptr;
   HitRec* hits = nullptr;
   HitRec* sorted = nullptr;
@@ -187,6 +186,23 @@ int validate(sonar_ctx* ctx, const sonar_params* p, const sonar_ssp* ssp) {
       if (!(ssp->c[i] > 0)) return fail(ctx, SONAR_E_ARG, "ssp speeds must be positive");
   }
   return SONAR_OK;
+}
+
+// Rotation matrix of a ping's unit quaternion (w, x, y, z), normalised first, and its
+// position (also rounded to FP32 for the FP32 traversal).
+DevPose dev_pose(const sonar_pose& ps) {
+  const double* q = ps.q;
+  const double qn = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  const double w = q[0] / qn, x = q[1] / qn, y = q[2] / qn, z = q[3] / qn;
+  DevPose P;
+  P.R[0] = 1 - 2 * (y * y + z * z); P.R[1] = 2 * (x * y - w * z);     P.R[2] = 2 * (x * z + w * y);
+  P.R[3] = 2 * (x * y + w * z);     P.R[4] = 1 - 2 * (x * x + z * z); P.R[5] = 2 * (y * z - w * x);
+  P.R[6] = 2 * (x * z - w * y);     P.R[7] = 2 * (y * z + w * x);     P.R[8] = 1 - 2 * (x * x + y * y);
+  for (int k = 0; k < 3; ++k) {
+    P.t[k] = ps.t[k];
+    P.t32[k] = (float)ps.t[k];
+  }
+  return P;
 }
 
 int derive(sonar_ctx* ctx, const sonar_params* p, const sonar_ssp* ssp, double z_sonar, int n_pings, Derived& d) {
@@ -352,14 +368,13 @@ int grow(sonar_ctx* ctx, T*& ptr, int64_t& cap, int64_t need, size_t elem, bool 
 int ensure_workspace(sonar_ctx* ctx, int P, const Derived& d) {
   int rc;
   if (P > ctx->p_cap) {
-    if (ctx->raw_host) cudaFreeHost(ctx->raw_host);
+    if (ctx->pose_host) cudaFreeHost(ctx->pose_host);
     if (ctx->n_cloud_host) cudaFreeHost(ctx->n_cloud_host);
-    ctx->raw_host = nullptr;
+    ctx->pose_host = nullptr;
     ctx->n_cloud_host = nullptr;
-    dfree(ctx->raw_dev); dfree(ctx->poses); dfree(ctx->gain); dfree(ctx->pmax); dfree(ctx->n_cloud_dev);
-    CU(cudaMallocHost(&ctx->raw_host, sizeof(double) * 7 * P));
+    dfree(ctx->poses); dfree(ctx->gain); dfree(ctx->pmax); dfree(ctx->n_cloud_dev);
+    CU(cudaMallocHost(&ctx->pose_host, sizeof(DevPose) * P));
     CU(cudaMallocHost(&ctx->n_cloud_host, sizeof(long long) * P));
-    CU(cudaMalloc(&ctx->raw_dev, sizeof(double) * 7 * P));
     CU(cudaMalloc(&ctx->poses, sizeof(DevPose) * P));
     CU(cudaMalloc(&ctx->gain, sizeof(float) * P));
     CU(cudaMalloc(&ctx->pmax, sizeof(unsigned) * P));
@@ -440,11 +455,17 @@ int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, cons
     if (ctx->timing) cudaEventRecord(ctx->stage_ev[i], st);
   };
   const bool fp16 = p->precision == SONAR_FP16;
-  *kernels = 9 + (ctx->sc.n_points > 0 ? 1 : 0) + (fp16 ? 1 : 0);
+  // trace, scan, scatter, synthesis, convert, GEMM, peaks; points; FP16 absmax and gain
+  *kernels = 7 + (ctx->sc.n_points > 0 ? 1 : 0) + (fp16 ? 2 : 0);
   mark(0);
+  // every buffer that starts at zero is cleared up front, so the kernels run back to back
+  const int32_t n_bins = P * d.nr_pad;
   CU(cudaMemsetAsync(ctx->n_hits, 0, sizeof(unsigned long long), st));
   CU(cudaMemsetAsync(ctx->err_dev, 0, sizeof(int), st));
-  CU(launch_poses(ctx->raw_dev, ctx->poses, P, st));
+  CU(cudaMemsetAsync(ctx->counts, 0, sizeof(int32_t) * n_bins, st));
+  CU(cudaMemsetAsync(ctx->S, 0, sizeof(float2) * ctx->s_elems, st));
+  CU(cudaMemsetAsync(ctx->keys, 0, sizeof(unsigned long long) * (size_t)P * d.nb, st));
+  CU(cudaMemsetAsync(ctx->pmax, 0, sizeof(unsigned) * P, st));
   TraceArgs ta;
   memset(&ta, 0, sizeof(ta));
   ta.sc = ctx->sc;
@@ -485,16 +506,11 @@ int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, cons
   ta.n_hits = ctx->n_hits;
   ta.hit_cap = ctx->hit_cap;
   ta.err = ctx->err_dev;
-  const int32_t n_bins = P * d.nr_pad;
-  CU(cudaMemsetAsync(ctx->counts, 0, sizeof(int32_t) * n_bins, st));
   CU(launch_trace(ta, ctx->sm_count, st));
   CU(launch_points(ta, st));
   mark(1);
   CU(launch_bin(ctx->hits, ctx->n_hits, n_bins, ctx->counts, ctx->offsets, ctx->sorted, ctx->sorted_n, ctx->sm_count,
                 st));
-  CU(cudaMemsetAsync(ctx->S, 0, sizeof(float2) * ctx->s_elems, st));
-  CU(cudaMemsetAsync(ctx->keys, 0, sizeof(unsigned long long) * (size_t)P * d.nb, st));
-  CU(cudaMemsetAsync(ctx->pmax, 0, sizeof(unsigned) * P, st));
   mark(2);
   SynthArgs sa;
   sa.hits_sorted = ctx->sorted;
@@ -552,7 +568,7 @@ int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, cons
   ga.r_min = (float)p->r_min_m;
   ga.dr = (float)d.dr;
   ga.alpha2 = (float)(2.0 * p->alpha_np_per_m);
-  ga.gain = ctx->gain;
+  ga.gain = fp16 ? ctx->gain : nullptr;  // element echoes carry a gain only in the FP16 form
   ga.y_gain_inv = (float)(1.0 / ctx->y_gain);
   ga.env = o.env;
   ga.peak_keys = ctx->keys;
@@ -626,12 +642,8 @@ int run(sonar_ctx* ctx, const sonar_pose* poses, int P, const sonar_params* p, c
     o.cloud = ctx->cloud_stage;
   }
 
-  for (int i = 0; i < P; ++i) {
-    double* r = ctx->raw_host + 7 * i;
-    r[0] = poses[i].t[0]; r[1] = poses[i].t[1]; r[2] = poses[i].t[2];
-    r[3] = poses[i].q[0]; r[4] = poses[i].q[1]; r[5] = poses[i].q[2]; r[6] = poses[i].q[3];
-  }
-  CU(cudaMemcpyAsync(ctx->raw_dev, ctx->raw_host, sizeof(double) * 7 * P, cudaMemcpyHostToDevice, ctx->stream));
+  for (int i = 0; i < P; ++i) ctx->pose_host[i] = dev_pose(poses[i]);
+  CU(cudaMemcpyAsync(ctx->poses, ctx->pose_host, sizeof(DevPose) * P, cudaMemcpyHostToDevice, ctx->stream));
 
   const bool timed = ctx->timing;
   int kernels = 0;
@@ -795,9 +807,9 @@ int sonar_destroy(sonar_ctx* c) {
   if (c->stream) cudaStreamDestroy(c->stream);
   free_scene(c);
   dfree(c->ray_dirs); dfree(c->row_domega); dfree(c->y_hi); dfree(c->y_lo); dfree(c->rtab); dfree(c->taper_dev);
-  if (c->raw_host) cudaFreeHost(c->raw_host);
+  if (c->pose_host) cudaFreeHost(c->pose_host);
   if (c->n_cloud_host) cudaFreeHost(c->n_cloud_host);
-  dfree(c->raw_dev); dfree(c->poses); dfree(c->hits); dfree(c->sorted); dfree(c->sorted_n); dfree(c->dbg_tau);
+  dfree(c->poses); dfree(c->hits); dfree(c->sorted); dfree(c->sorted_n); dfree(c->dbg_tau);
   dfree(c->n_hits);
   dfree(c->counts); dfree(c->offsets); dfree(c->S); dfree(c->x_hi); dfree(c->x_lo); dfree(c->gain);
   dfree(c->env_stage); dfree(c->keys); dfree(c->pmax); dfree(c->cloud_stage); dfree(c->n_cloud_dev); dfree(c->err_dev);

@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant_
       const bool vn = n < a.nr;
       const bool elig = vn && n >= a.n_blank;
       const float r = a.r_min + ((float)n + 0.5f) * a.dr;
-      const float scale = r * __expf(a.alpha2 * r) * a.y_gain_inv / a.gain[p];
+      const float scale = r * __expf(a.alpha2 * r) * a.y_gain_inv / (a.gain ? a.gain[p] : 1.0f);
       float* env_p = a.env + (size_t)p * a.n_beams * a.nr;
       unsigned long long* keys_p = a.peak_keys + (size_t)p * a.n_beams;
       float pmax = 0.f;

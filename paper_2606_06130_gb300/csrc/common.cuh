@@ -128,7 +128,6 @@ cudaError_t build_bvh(const float* d_verts, const int32_t* d_tris, const float* 
 cudaError_t launch_ray_table(double* dirs, float* row_domega, int32_t n_ray_az, int32_t n_ray_el,
                              int32_t n_sub, double hfov, double vfov, uint32_t seed32,
                              cudaStream_t st);
-cudaError_t launch_poses(const double* raw, DevPose* poses, int32_t n, cudaStream_t st);
 cudaError_t launch_trace(const TraceArgs& a, int sm_count, cudaStream_t st);
 cudaError_t launch_points(const TraceArgs& a, cudaStream_t st);
 
@@ -187,7 +186,7 @@ struct GemmArgs {
   int32_t f16;               // operands FP16 (1) or BF16 (0)
   int32_t nr, nr_x, n_beams, n_blank;
   float r_min, dr, alpha2;   // TVG(r) = r exp(alpha2 r)
-  const float* gain;         // [n_pings]: element-echo gain
+  const float* gain;         // [n_pings]: element-echo gain (FP16 form), nullptr: 1
   float y_gain_inv;
   float* env;                // [n_pings][Nb][Nr]
   unsigned long long* peak_keys;  // [n_pings][Nb]

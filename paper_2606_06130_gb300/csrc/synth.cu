@@ -326,7 +326,7 @@ cudaError_t launch_convert(const ConvertArgs& a, int sm_count, cudaStream_t st) 
     if (e != cudaSuccess) return e;
     k_absmax<<<dim3(sm_count, a.n_pings), 256, 0, st>>>(a.S, a.nr, a.nr_pad, a.M, a.gain);
   }
-  k_gain_pow2<<<(a.n_pings + 63) / 64, 64, 0, st>>>(a.gain, a.n_pings, a.mode);
+  if (a.mode == SONAR_FP16) k_gain_pow2<<<(a.n_pings + 63) / 64, 64, 0, st>>>(a.gain, a.n_pings, a.mode);
   k_convert<<<sm_count * 8, 256, 0, st>>>(a);
   return cudaGetLastError();
 }

@@ -662,22 +662,6 @@ __global__ void k_ray_table(double* dirs, float* row_domega, int nra, int nre, i
   dirs[3 * gid + 2] = sin(el);
 }
 
-// Rotation matrix of each ping's unit quaternion (w, x, y, z), normalised first.
-__global__ void k_poses(const double* raw, DevPose* poses, int n) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const double* p = raw + 7 * i;
-  double qn = sqrt(p[3] * p[3] + p[4] * p[4] + p[5] * p[5] + p[6] * p[6]);
-  double w = p[3] / qn, x = p[4] / qn, y = p[5] / qn, z = p[6] / qn;
-  DevPose P;
-  P.R[0] = 1 - 2 * (y * y + z * z); P.R[1] = 2 * (x * y - w * z);     P.R[2] = 2 * (x * z + w * y);
-  P.R[3] = 2 * (x * y + w * z);     P.R[4] = 1 - 2 * (x * x + z * z); P.R[5] = 2 * (y * z - w * x);
-  P.R[6] = 2 * (x * z - w * y);     P.R[7] = 2 * (y * z + w * x);     P.R[8] = 1 - 2 * (x * x + y * y);
-  P.t[0] = p[0]; P.t[1] = p[1]; P.t[2] = p[2];
-  P.t32[0] = (float)p[0]; P.t32[1] = (float)p[1]; P.t32[2] = (float)p[2];
-  poses[i] = P;
-}
-
 }  // namespace
 
 cudaError_t launch_ray_table(double* dirs, float* row_domega, int32_t nra, int32_t nre, int32_t nsub,
@@ -685,11 +669,6 @@ cudaError_t launch_ray_table(double* dirs, float* row_domega, int32_t nra, int32
   int64_t n = (int64_t)nra * nre * nsub;
   if (n < nre) n = nre;
   k_ray_table<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(dirs, row_domega, nra, nre, nsub, hfov, vfov, seed32);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_poses(const double* raw, DevPose* poses, int32_t n, cudaStream_t st) {
-  k_poses<<<(unsigned)ceil_div(n, 64), 64, 0, st>>>(raw, poses, n);
   return cudaGetLastError();
 }
 
