@@ -79,6 +79,7 @@ struct sonar_ctx {
   // parameter-derived tables
   std::vector<uint8_t> ray_key, steer_key, rtab_key;
   double* ray_dirs = nullptr;
+  float* ray_dirs32 = nullptr;
   float* row_domega = nullptr;
   void* y_hi = nullptr;
   void* y_lo = nullptr;
@@ -202,6 +203,7 @@ DevPose dev_pose(const sonar_pose& ps) {
     P.t[k] = ps.t[k];
     P.t32[k] = (float)ps.t[k];
   }
+  for (int k = 0; k < 9; ++k) P.R32[k] = (float)P.R[k];
   return P;
 }
 
@@ -306,11 +308,13 @@ int ensure_tables(sonar_ctx* ctx, const sonar_params* p, const Derived& d) {
   key_add(k, p->hfov_rad); key_add(k, p->vfov_rad); key_add(k, p->seed);
   if (k != ctx->ray_key) {
     dfree(ctx->ray_dirs);
+    dfree(ctx->ray_dirs32);
     dfree(ctx->row_domega);
     CU(cudaMalloc(&ctx->ray_dirs, sizeof(double) * 3 * d.n_subrays));
+    CU(cudaMalloc(&ctx->ray_dirs32, sizeof(float) * 3 * d.n_subrays));
     CU(cudaMalloc(&ctx->row_domega, sizeof(float) * p->n_ray_el));
-    CU(launch_ray_table(ctx->ray_dirs, ctx->row_domega, p->n_ray_az, p->n_ray_el, p->n_sub, p->hfov_rad,
-                        p->vfov_rad, seed32(p->seed), ctx->stream));
+    CU(launch_ray_table(ctx->ray_dirs, ctx->ray_dirs32, ctx->row_domega, p->n_ray_az, p->n_ray_el, p->n_sub,
+                        p->hfov_rad, p->vfov_rad, seed32(p->seed), ctx->stream));
     ctx->ray_key = k;
   }
   k.clear();
@@ -471,6 +475,7 @@ int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, cons
   ta.sc = ctx->sc;
   ta.poses = ctx->poses;
   ta.ray_dirs = ctx->ray_dirs;
+  ta.ray_dirs32 = ctx->ray_dirs32;
   ta.row_domega = ctx->row_domega;
   ta.n_pings = P;
   ta.n_ray_az = p->n_ray_az;
@@ -493,6 +498,8 @@ int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, cons
   ta.two_inv_c0 = 2.0 * ta.inv_c0;
   ta.T_stop = d.T_stop;
   ta.L_stop = d.T_stop * d.ssp_c0;
+  ta.L_stop32 = (float)ta.L_stop;
+  ta.surface_z32 = (float)p->surface_z;
   ta.t0 = d.t0;
   ta.inv_dt = 1.0 / d.dt;
   ta.t0_dt = d.t0 * ta.inv_dt;
@@ -806,7 +813,7 @@ int sonar_destroy(sonar_ctx* c) {
     if (e) cudaEventDestroy(e);
   if (c->stream) cudaStreamDestroy(c->stream);
   free_scene(c);
-  dfree(c->ray_dirs); dfree(c->row_domega); dfree(c->y_hi); dfree(c->y_lo); dfree(c->rtab); dfree(c->taper_dev);
+  dfree(c->ray_dirs); dfree(c->ray_dirs32); dfree(c->row_domega); dfree(c->y_hi); dfree(c->y_lo); dfree(c->rtab); dfree(c->taper_dev);
   if (c->pose_host) cudaFreeHost(c->pose_host);
   if (c->n_cloud_host) cudaFreeHost(c->n_cloud_host);
   dfree(c->poses); dfree(c->hits); dfree(c->sorted); dfree(c->sorted_n); dfree(c->dbg_tau);

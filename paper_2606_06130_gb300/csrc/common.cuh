@@ -70,6 +70,7 @@ struct DevPose {
   double R[9];
   double t[3];
   float t32[3];  // the position rounded to FP32, for the FP32 traversal
+  float R32[9];  // the rotation rounded to FP32, for the FP32 traversal direction
 };
 
 // Everything the trace kernels need, passed by value.
@@ -77,6 +78,7 @@ struct TraceArgs {
   DevScene sc;
   const DevPose* poses;
   const double* ray_dirs;   // [n_subrays][3] sonar-frame sub-ray directions
+  const float* ray_dirs32;  // the same rounded to FP32
   const float* row_domega;  // [n_ray_el] sub-ray solid angle per elevation row
   int32_t n_pings, n_ray_az, n_ray_el, n_sub, n_subrays;
   int32_t max_bounces, has_surface, curved;
@@ -88,6 +90,7 @@ struct TraceArgs {
   double two_inv_c0;             // 2 / c0 (isovelocity two-way delay per metre of path)
   double T_stop;                 // one-way time limit
   double L_stop;                 // isovelocity path-length limit T_stop c0
+  float L_stop32, surface_z32;   // the same rounded to FP32, for FP32 pre-checks
   double t0, inv_dt, hw, f0;     // sample-grid mapping of delays
   double t0_dt;                  // t0 / dt
   int32_t nr_pad;
@@ -125,7 +128,7 @@ cudaError_t build_bvh(const float* d_verts, const int32_t* d_tris, const float* 
                       const uint8_t* d_flags, int32_t n_tris, float4** tri32, float** triv,
                       int32_t** tri_prim, float** tri_mu, uint8_t** tri_flags, double4_32a** tri_plane,
                       float** tri_inv_n, BvhNode** nodes, int32_t* root, cudaStream_t st);
-cudaError_t launch_ray_table(double* dirs, float* row_domega, int32_t n_ray_az, int32_t n_ray_el,
+cudaError_t launch_ray_table(double* dirs, float* dirs32, float* row_domega, int32_t n_ray_az, int32_t n_ray_el,
                              int32_t n_sub, double hfov, double vfov, uint32_t seed32,
                              cudaStream_t st);
 cudaError_t launch_trace(const TraceArgs& a, int sm_count, cudaStream_t st);

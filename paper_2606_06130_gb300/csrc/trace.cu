@@ -35,9 +35,6 @@ __device__ __forceinline__ double dot(D3 a, D3 b) { return da(da(dm(a.x, b.x), d
 __device__ __forceinline__ D3 cross(D3 a, D3 b) {
   return d3(ds(dm(a.y, b.z), dm(a.z, b.y)), ds(dm(a.z, b.x), dm(a.x, b.z)), ds(dm(a.x, b.y), dm(a.y, b.x)));
 }
-__device__ __forceinline__ D3 axpy(D3 p, double t, D3 d) {  // p + t d, as p[k] += t * d[k]
-  return d3(da(p.x, dm(t, d.x)), da(p.y, dm(t, d.y)), da(p.z, dm(t, d.z)));
-}
 // contracted forms for positions and distances
 __device__ __forceinline__ double dotf(D3 a, D3 b) { return fma(a.z, b.z, fma(a.y, b.y, a.x * b.x)); }
 __device__ __forceinline__ D3 axpyf(D3 p, double t, D3 d) {
@@ -53,13 +50,13 @@ __device__ __forceinline__ D3 rot_t(const double* R, D3 v) {
             da(da(dm(R[2], v.x), dm(R[5], v.y)), dm(R[8], v.z)));
 }
 
-// a / b for |b| in [1e-30, 1e30]: an FP32 reciprocal seed refined by two Newton-Raphson
-// steps y += y (1 - b y) (2^-23 -> 2^-46 -> full precision) and one residual correction
-// of the quotient q += (a - b q) y. Within an ulp or so of the correctly rounded
-// quotient at a fraction of the cost of FP64 division, which is long on this part.
+// a / b for |b| in [1e-30, 1e30]: an FP32 reciprocal seed refined by one Newton-Raphson
+// step y += y (1 - b y) (relative error 2^-23 -> 2^-46), then one residual correction of
+// the quotient q += (a - b q) y, which squares the error again (to rounding level).
+// Within an ulp or so of the correctly rounded quotient at a fraction of the cost of
+// FP64 division, which is long on this part.
 __device__ __forceinline__ double ddiv_nr(double a, double b) {
   double y = (double)__frcp_rn((float)b);
-  y = fma(y, fma(-b, y, 1.0), y);
   y = fma(y, fma(-b, y, 1.0), y);
   const double q = a * y;
   return fma(fma(-b, q, a), y, q);
@@ -148,9 +145,11 @@ __device__ __forceinline__ double plane_t(const DevScene& sc, int leaf, D3 o, D3
 
 // Nearest triangle with FP64 distance in (tmin, tmax], excluding `exclude` (original
 // id), ties to the lowest id. The distance of the returned hit is FP64.
-// o32: the origin rounded to FP32 when the caller has it (nullptr: converted here).
+// o32, d32: the origin and the direction in FP32 when the caller has them (nullptr:
+// converted here). An FP32 direction from FP32 operands differs from the FP64 one by
+// ~1e-7, far inside the traversal's slack.
 __device__ Hit closest_hit(const DevScene& sc, D3 o, D3 d, double tmin, double tmax, int exclude, int* err,
-                           const float* o32 = nullptr) {
+                           const float* o32 = nullptr, const float* d32 = nullptr) {
   Hit best = {INFINITY, -1, -1};
   bool best_exact = true;
   float best_t32 = INFINITY;
@@ -161,7 +160,11 @@ __device__ Hit closest_hit(const DevScene& sc, D3 o, D3 d, double tmin, double t
   } else {
     r.ox = (float)o.x; r.oy = (float)o.y; r.oz = (float)o.z;
   }
-  r.dx = (float)d.x; r.dy = (float)d.y; r.dz = (float)d.z;
+  if (d32) {
+    r.dx = d32[0]; r.dy = d32[1]; r.dz = d32[2];
+  } else {
+    r.dx = (float)d.x; r.dy = (float)d.y; r.dz = (float)d.z;
+  }
   r.ix = __frcp_rn(r.dx); r.iy = __frcp_rn(r.dy); r.iz = __frcp_rn(r.dz);
   const float tmax_f = (float)tmax * (1.0f + 1e-6f) + 1e-4f;
   const float tmin32 = (float)tmin, tmax32 = (float)tmax;  // the loop stays in FP32
@@ -429,8 +432,8 @@ __device__ void route_curved(const TraceArgs& A, int ping, D3 o, D3 d0, D3 us, u
   }
 }
 
-__device__ void route_straight(const TraceArgs& A, int ping, D3 o, const float* o32, D3 d0, float uy, float uz,
-                               uint32_t ray, uint32_t sub, float dOmega, uint32_t keybase) {
+__device__ void route_straight(const TraceArgs& A, int ping, D3 o, const float* o32, D3 d0, const float* d32,
+                               float uy, float uz, uint32_t ray, uint32_t sub, float dOmega, uint32_t keybase) {
   D3 pos = o, dir = d0;
   double L = 0.0;
   float gam = 1.0f;
@@ -438,9 +441,18 @@ __device__ void route_straight(const TraceArgs& A, int ping, D3 o, const float* 
   for (int iter = 0; iter < 8; ++iter) {
     const double tlim = A.L_stop - L;
     if (!(tlim > 0)) break;
-    Hit hq = closest_hit(A.sc, pos, dir, kEpsHit, tlim, prev, A.err, iter == 0 ? o32 : nullptr);
+    Hit hq = closest_hit(A.sc, pos, dir, kEpsHit, tlim, prev, A.err, iter == 0 ? o32 : nullptr,
+                         iter == 0 ? d32 : nullptr);
     double ts = INFINITY;
-    if (A.has_surface && prev != -2 && dir.z != 0.0) {
+    // from the origin, an FP32 look first: the plane clearly behind or clearly out of
+    // reach skips the FP64 test
+    bool surf_maybe = A.has_surface && prev != -2 && dir.z != 0.0;
+    if (surf_maybe && iter == 0) {
+      const float num32 = A.surface_z32 - o32[2], dz32 = d32[2];  // tlim = L_stop at the origin
+      const bool clear = fabsf(num32) > 1e-3f && fabsf(dz32) > 1e-5f;
+      if (clear && (num32 * dz32 < 0.f || fabsf(num32) > A.L_stop32 * fabsf(dz32) * 1.001f + 1e-3f)) surf_maybe = false;
+    }
+    if (surf_maybe) {
       // divide only when the plane lies ahead within reach
       const double num = A.surface_z - pos.z;
       if (num * dir.z > 0.0 && fabs(num) <= tlim * fabs(dir.z) * (1.0 + 1e-12)) {
@@ -491,7 +503,14 @@ __global__ void __launch_bounds__(128, 4) k_trace(TraceArgs A) {
     const float dOmega = A.row_domega[row];
     const uint32_t keybase = ((uint32_t)sr) << 2;
     if (A.curved) route_curved(A, ping, o, dw, us, ray, sub, dOmega, keybase);
-    else route_straight(A, ping, o, P.t32, dw, (float)us.y, (float)us.z, ray, sub, dOmega, keybase);
+    else {
+      const float* u32 = A.ray_dirs32 + 3 * sr;
+      const float ux = u32[0], uy = u32[1], uz = u32[2];
+      const float d32[3] = {fmaf(P.R32[2], uz, fmaf(P.R32[1], uy, P.R32[0] * ux)),
+                            fmaf(P.R32[5], uz, fmaf(P.R32[4], uy, P.R32[3] * ux)),
+                            fmaf(P.R32[8], uz, fmaf(P.R32[7], uy, P.R32[6] * ux))};
+      route_straight(A, ping, o, P.t32, dw, d32, uy, uz, ray, sub, dOmega, keybase);
+    }
   }
 }
 
@@ -635,7 +654,7 @@ __global__ void k_points(TraceArgs A) {
 
 // Sonar-frame sub-ray directions (Sec. III Eq. 2-3 grid, cell-centred) with hashed
 // jitter inside 2x2 quarter cells, and the sub-ray solid angle per elevation row.
-__global__ void k_ray_table(double* dirs, float* row_domega, int nra, int nre, int nsub, double hfov,
+__global__ void k_ray_table(double* dirs, float* dirs32, float* row_domega, int nra, int nre, int nsub, double hfov,
                             double vfov, uint32_t seed32) {
   int64_t n = (int64_t)nra * nre * nsub;
   int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -660,15 +679,17 @@ __global__ void k_ray_table(double* dirs, float* row_domega, int nra, int nre, i
   dirs[3 * gid] = cos(el) * cos(az);
   dirs[3 * gid + 1] = cos(el) * sin(az);
   dirs[3 * gid + 2] = sin(el);
+  for (int k = 0; k < 3; ++k) dirs32[3 * gid + k] = (float)dirs[3 * gid + k];
 }
 
 }  // namespace
 
-cudaError_t launch_ray_table(double* dirs, float* row_domega, int32_t nra, int32_t nre, int32_t nsub,
+cudaError_t launch_ray_table(double* dirs, float* dirs32, float* row_domega, int32_t nra, int32_t nre, int32_t nsub,
                              double hfov, double vfov, uint32_t seed32, cudaStream_t st) {
   int64_t n = (int64_t)nra * nre * nsub;
   if (n < nre) n = nre;
-  k_ray_table<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(dirs, row_domega, nra, nre, nsub, hfov, vfov, seed32);
+  k_ray_table<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(dirs, dirs32, row_domega, nra, nre, nsub, hfov, vfov,
+                                                          seed32);
   return cudaGetLastError();
 }
 
