@@ -267,19 +267,6 @@ def run_ours(args, ws, rank, local):
     t_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), ws)
     stats = s.stats()
 
-    # end to end through the C ABI with host buffers: pinned env, host cloud
-    env_h = torch.empty(env.shape, dtype=torch.float32, pin_memory=True)
-    cloud_h = np.zeros((nb, 6), np.int32)
-    for _ in range(2):
-        s.ping_batch([pose], params, ssp, precision=args.precision, env=env_h[None], cloud=cloud_h[None], cloud_cap=nb)
-    k_e2e = max(3, min(args.steps, 20))
-    torch.cuda.synchronize()
-    e0 = time.perf_counter()
-    for _ in range(k_e2e):
-        s.ping_batch([pose], params, ssp, precision=args.precision, env=env_h[None], cloud=cloud_h[None], cloud_cap=nb)
-    torch.cuda.synchronize()
-    e2e_s = max_over_ranks(time.perf_counter() - e0, ws)
-
     # the same ping replayed as a captured CUDA graph (no stage events)
     s.set_option(SONAR_OPT_TIMING, 0)
     for _ in range(3):
@@ -295,6 +282,21 @@ def run_ours(args, ws, rank, local):
         g1.synchronize()
         g_ms += g0.elapsed_time(g1)
     g_ms = max_over_ranks(g_ms, ws)
+
+    # end to end through the C ABI as a user calls it (defaults: graph replay, no stage
+    # events), pose in, envelope and cloud out to pinned host buffers that the kernels
+    # write through the device's mapping of them
+    env_h = torch.empty(env.shape, dtype=torch.float32, pin_memory=True)
+    cloud_h = torch.empty((nb, 6), dtype=torch.int32, pin_memory=True)
+    for _ in range(2):
+        s.ping_batch([pose], params, ssp, precision=args.precision, env=env_h[None], cloud=cloud_h[None], cloud_cap=nb)
+    k_e2e = max(3, min(args.steps, 200))
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    for _ in range(k_e2e):
+        s.ping_batch([pose], params, ssp, precision=args.precision, env=env_h[None], cloud=cloud_h[None], cloud_cap=nb)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - e0, ws)
 
     # other forms (same run): BF16 single ping, BF16 64-ping trajectory batch
     forms = {}
@@ -350,7 +352,7 @@ def run_ours(args, ws, rank, local):
                             "note": "same steps replayed as one CUDA graph per ping, no stage events"},
            "e2e": {"value": whole_job_rate(ws, k_e2e, e2e_s), "unit": UNIT, "h2d_bytes_per_step": 144,
                    "d2h_bytes_per_step": int(env.numel() * 4 + nb * 24 + 8), "steps": k_e2e,
-                   "path": "sonar_ping_batch with pinned host env and pageable host cloud"},
+                   "path": "sonar_ping_batch (default graph replay) with pinned host env and cloud"},
            "clocks": clk,
            "error_vs_oracle": err,
            "forms": forms,

@@ -171,11 +171,14 @@ SONAR_API int sonar_scene_upload(sonar_ctx* ctx, const float* verts, int64_t n_v
                        const float* sigma, int64_t n_points, const double* planes, int64_t n_planes);
 
 /* ---------------------------------------------------------------- pings */
-/* One ping. env: [n_beam_el][n_beam_az][n_range] f32 envelope |B| * TVG (device or
-   host). cloud: up to cloud_cap points ordered by beam (device or host; may be NULL
-   with cloud_cap 0). n_cloud (host, may be NULL): number of points found, even when it
-   exceeds cloud_cap (then SONAR_E_CAPACITY is returned and cloud holds the first
-   cloud_cap points). */
+/* One ping. env: [n_beam_el][n_beam_az][n_range] f32 envelope |B| * TVG. cloud: up to
+   cloud_cap points ordered by beam (may be NULL with cloud_cap 0). Outputs may be device
+   memory, pinned host memory mapped into the device's address space (cudaHostAlloc,
+   cudaHostRegister: the kernels write it in place, so results reach the host while the
+   pipeline runs), or other host memory (staged on the device, copied at the end). The
+   call returns when the outputs are complete. n_cloud (host, may be NULL): number of
+   points found, even when it exceeds cloud_cap (then SONAR_E_CAPACITY is returned and
+   cloud holds the first cloud_cap points). */
 SONAR_API int sonar_ping(sonar_ctx* ctx, const sonar_pose* pose, const sonar_params* params,
                const sonar_ssp* ssp, float* env, sonar_point* cloud, int64_t cloud_cap,
                int64_t* n_cloud);

@@ -434,6 +434,30 @@ int ensure_workspace(sonar_ctx* ctx, int P, const Derived& d) {
   return SONAR_OK;
 }
 
+// Where an output lives: device memory (written in place), pinned host memory mapped
+// into this device's address space (written in place through the mapping, so results
+// cross to the host while the kernels run), or other host memory (staged on the
+// device and copied at the end). *dev is the address the kernels write to.
+enum class Mem { Device, Mapped, Host };
+Mem classify(void* p, void** dev) {
+  *dev = nullptr;
+  if (!p) return Mem::Host;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return Mem::Host;
+  }
+  if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) {
+    *dev = p;
+    return Mem::Device;
+  }
+  if (at.type == cudaMemoryTypeHost && at.devicePointer) {
+    *dev = at.devicePointer;
+    return Mem::Mapped;
+  }
+  return Mem::Host;
+}
+
 bool is_device_ptr(const void* p) {
   if (!p) return false;
   cudaPointerAttributes at;
@@ -631,18 +655,21 @@ int run(sonar_ctx* ctx, const sonar_pose* poses, int P, const sonar_params* p, c
   if ((rc = ensure_tables(ctx, p, d))) return rc;
   if ((rc = ensure_workspace(ctx, P, d))) return rc;
 
-  // outputs: device buffers are written in place, host buffers through staging
-  const bool env_dev = is_device_ptr(env);
-  const bool cloud_dev = cloud_cap == 0 || is_device_ptr(cloud);
+  // outputs: device buffers and mapped pinned host buffers are written in place, other
+  // host buffers through staging
+  void* env_d = nullptr;
+  void* cloud_d = nullptr;
+  const bool env_dev = classify(env, &env_d) != Mem::Host;
+  const bool cloud_dev = cloud_cap == 0 || classify(cloud, &cloud_d) != Mem::Host;
   const int64_t env_elems = (int64_t)P * d.nb * d.nr;
   Outputs o;
-  o.env = env;
+  o.env = static_cast<float*>(env_d);
   if (!env_dev) {
     if ((rc = grow(ctx, ctx->env_stage, ctx->env_cap, env_elems, sizeof(float), false))) return rc;
     o.env = ctx->env_stage;
   }
   o.cap = cloud_cap;
-  o.cloud = cloud;
+  o.cloud = cloud_cap == 0 ? cloud : static_cast<sonar_point*>(cloud_d);
   if (!cloud_dev) {
     if ((rc = grow(ctx, ctx->cloud_stage, ctx->cloud_stage_cap, (int64_t)P * cloud_cap, sizeof(sonar_point), false)))
       return rc;

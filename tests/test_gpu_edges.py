@@ -147,3 +147,27 @@ def test_single_ray_without_bounces(sonar):
     scene, params, pose, ssp = c1(n_ray_az=1, n_ray_el=1, max_bounces=0, hfov=math.radians(10.0),
                                   vfov=math.radians(10.0))
     full_parity(sonar, scene, params, pose, ssp)
+
+
+def test_outputs_in_device_pinned_and_pageable_memory_agree(sonar):
+    """Device outputs are written in place, pinned host outputs through the device's
+    mapping of them, pageable ones through staging: all three give the same ping."""
+    from paper_2606_06130_gb300.sonar import cloud_records
+    scene, params, pose, ssp = c1()
+    sonar.upload(scene)
+    nb = params["n_beam_az"] * params["n_beam_el"]
+    shape = (1, params["n_beam_el"], params["n_beam_az"], params["n_range"])
+    env_d, cloud_d, n_d = sonar.ping_batch([pose], params, ssp)
+    env_p = torch.zeros(shape, dtype=torch.float32, pin_memory=True)
+    cloud_p = torch.zeros((1, nb, 6), dtype=torch.int32, pin_memory=True)
+    _, _, n_p = sonar.ping_batch([pose], params, ssp, env=env_p, cloud=cloud_p, cloud_cap=nb)
+    env_h = np.zeros(shape, np.float32)
+    cloud_h = np.zeros((1, nb, 6), np.int32)
+    _, _, n_h = sonar.ping_batch([pose], params, ssp, env=env_h, cloud=cloud_h, cloud_cap=nb)
+    torch.cuda.synchronize()
+    E_d = env_d.cpu().numpy()
+    assert parity.nl2(env_p.numpy(), E_d) <= 1e-6 and parity.nl2(env_h, E_d) <= 1e-6
+    assert int(n_d[0]) == int(n_p[0]) == int(n_h[0])
+    c_d = cloud_records(cloud_d[0], int(n_d[0]))
+    for c in (cloud_records(cloud_p[0], int(n_p[0])), cloud_records(cloud_h[0], int(n_h[0]))):
+        assert list(c["beam"]) == list(c_d["beam"]) and list(c["bin"]) == list(c_d["bin"])
