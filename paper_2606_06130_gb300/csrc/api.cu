@@ -115,6 +115,7 @@ struct sonar_ctx {
   int64_t cloud_stage_cap = 0;
   long long* n_cloud_dev = nullptr;
   long long* n_cloud_host = nullptr;  // pinned
+  unsigned long long* counters_host = nullptr;  // pinned: hits of the last call, error bits
   int* err_dev = nullptr;
   int64_t ws_hits = 0, ws_bins = 0, ws_s = 0, ws_x = 0;
 
@@ -469,9 +470,12 @@ bool is_device_ptr(const void* p) {
 }
 
 struct Outputs {
-  float* env;
+  float* env;               // where the kernels write
   sonar_point* cloud;
   int64_t cap;
+  float* env_host;          // staged outputs: the caller's host buffers, else nullptr
+  sonar_point* cloud_host;
+  int64_t env_elems;
 };
 
 // Enqueue the whole pipeline for P pings on the context stream (graph-capturable:
@@ -485,6 +489,8 @@ int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, cons
   const bool fp16 = p->precision == SONAR_FP16;
   // trace, scan, scatter, synthesis, convert, GEMM, peaks; points; FP16 absmax and gain
   *kernels = 7 + (ctx->sc.n_points > 0 ? 1 : 0) + (fp16 ? 2 : 0);
+  // the poses the host has just written into the pinned staging record
+  CU(cudaMemcpyAsync(ctx->poses, ctx->pose_host, sizeof(DevPose) * P, cudaMemcpyHostToDevice, st));
   mark(0);
   // every buffer that starts at zero is cleared up front, so the kernels run back to back
   const int32_t n_bins = P * d.nr_pad;
@@ -626,6 +632,14 @@ int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, cons
   pa.n_cloud = ctx->n_cloud_dev;
   CU(launch_peaks(pa, st));
   mark(6);
+  // results back to the host: staged outputs, per-ping point counts, hit count, error bits
+  if (o.env_host)
+    CU(cudaMemcpyAsync(o.env_host, o.env, sizeof(float) * o.env_elems, cudaMemcpyDeviceToHost, st));
+  if (o.cloud_host && o.cap > 0)
+    CU(cudaMemcpyAsync(o.cloud_host, o.cloud, sizeof(sonar_point) * P * o.cap, cudaMemcpyDeviceToHost, st));
+  CU(cudaMemcpyAsync(ctx->n_cloud_host, ctx->n_cloud_dev, sizeof(long long) * P, cudaMemcpyDeviceToHost, st));
+  CU(cudaMemcpyAsync(ctx->counters_host, ctx->n_hits, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+  CU(cudaMemcpyAsync(ctx->counters_host + 1, ctx->err_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
   return SONAR_OK;
 }
 
@@ -664,20 +678,27 @@ int run(sonar_ctx* ctx, const sonar_pose* poses, int P, const sonar_params* p, c
   const int64_t env_elems = (int64_t)P * d.nb * d.nr;
   Outputs o;
   o.env = static_cast<float*>(env_d);
+  o.env_host = nullptr;
+  o.env_elems = env_elems;
   if (!env_dev) {
     if ((rc = grow(ctx, ctx->env_stage, ctx->env_cap, env_elems, sizeof(float), false))) return rc;
     o.env = ctx->env_stage;
+    o.env_host = env;
   }
   o.cap = cloud_cap;
   o.cloud = cloud_cap == 0 ? cloud : static_cast<sonar_point*>(cloud_d);
+  o.cloud_host = nullptr;
   if (!cloud_dev) {
     if ((rc = grow(ctx, ctx->cloud_stage, ctx->cloud_stage_cap, (int64_t)P * cloud_cap, sizeof(sonar_point), false)))
       return rc;
     o.cloud = ctx->cloud_stage;
+    o.cloud_host = cloud;
   }
+  if (!ctx->counters_host) CU(cudaMallocHost(&ctx->counters_host, 2 * sizeof(unsigned long long)));
+  ctx->counters_host[1] = 0;
 
+  // the graph's first node copies these to the device
   for (int i = 0; i < P; ++i) ctx->pose_host[i] = dev_pose(poses[i]);
-  CU(cudaMemcpyAsync(ctx->poses, ctx->pose_host, sizeof(DevPose) * P, cudaMemcpyHostToDevice, ctx->stream));
 
   const bool timed = ctx->timing;
   int kernels = 0;
@@ -685,6 +706,8 @@ int run(sonar_ctx* ctx, const sonar_pose* poses, int P, const sonar_params* p, c
   if (ctx->use_graph && !timed) {
     std::vector<uint8_t> k;
     key_add(k, P); key_add(k, *p); key_add(k, o.env); key_add(k, o.cloud); key_add(k, o.cap);
+    key_add(k, o.env_host); key_add(k, o.cloud_host); key_add(k, ctx->pose_host); key_add(k, ctx->counters_host);
+    key_add(k, ctx->n_cloud_host);
     key_add(k, ctx->debug); key_add(k, ctx->timing); key_add(k, ctx->synth_opt); key_add(k, ctx->scene_version);
     key_add(k, d.c_ref);
     if (ssp) {
@@ -711,18 +734,11 @@ int run(sonar_ctx* ctx, const sonar_pose* poses, int P, const sonar_params* p, c
     rc = enqueue(ctx, P, p, d, o, &kernels);
   }
   if (rc) return rc;
-  if (!env_dev)
-    CU(cudaMemcpyAsync(env, o.env, sizeof(float) * env_elems, cudaMemcpyDeviceToHost, ctx->stream));
-  if (!cloud_dev && cloud_cap > 0)
-    CU(cudaMemcpyAsync(cloud, o.cloud, sizeof(sonar_point) * P * cloud_cap, cudaMemcpyDeviceToHost, ctx->stream));
-  CU(cudaMemcpyAsync(ctx->n_cloud_host, ctx->n_cloud_dev, sizeof(long long) * P, cudaMemcpyDeviceToHost, ctx->stream));
-  unsigned long long nh = 0;
-  int errw = 0;
-  CU(cudaMemcpyAsync(&nh, ctx->n_hits, sizeof(nh), cudaMemcpyDeviceToHost, ctx->stream));
-  CU(cudaMemcpyAsync(&errw, ctx->err_dev, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   CU(cudaEventRecord(ctx->ev_out, ctx->stream));
   CU(cudaStreamWaitEvent(ctx->user_stream, ctx->ev_out, 0));
   CU(cudaStreamSynchronize(ctx->stream));
+  const unsigned long long nh = ctx->counters_host[0];
+  const int errw = (int)ctx->counters_host[1];
   ctx->last_p = P;
   ctx->last_d = d;
   ctx->last_params = *p;
@@ -843,6 +859,7 @@ int sonar_destroy(sonar_ctx* c) {
   dfree(c->ray_dirs); dfree(c->ray_dirs32); dfree(c->row_domega); dfree(c->y_hi); dfree(c->y_lo); dfree(c->rtab); dfree(c->taper_dev);
   if (c->pose_host) cudaFreeHost(c->pose_host);
   if (c->n_cloud_host) cudaFreeHost(c->n_cloud_host);
+  if (c->counters_host) cudaFreeHost(c->counters_host);
   dfree(c->poses); dfree(c->hits); dfree(c->sorted); dfree(c->sorted_n); dfree(c->dbg_tau);
   dfree(c->n_hits);
   dfree(c->counts); dfree(c->offsets); dfree(c->S); dfree(c->x_hi); dfree(c->x_lo); dfree(c->gain);
