@@ -153,8 +153,12 @@ SONAR_API const char* sonar_last_error(const sonar_ctx* ctx);
 #define SONAR_OPT_GRAPH 3
 #define SONAR_OPT_TILE_N 4
 /* SONAR_OPT_SYNTH: 0 (default) synthesises element echoes on the tensor cores where the
-   array allows it (nx a power of two, ny % 8 == 0, ny <= 32), 1 always uses the FP32
-   SIMT synthesis kernel. */
+   array allows it (nx a power of two, and either nx ny a multiple of 128, where the
+   z phasor splits into coarse and fine factors, or ny % 8 == 0 and ny <= 32), 1 always
+   uses the FP32 SIMT synthesis kernel. 2, 3 and 4 are as 0 but ask the z-split
+   tensor-core kernel for tiles of 32, 64 or 96 complex columns; a shape that does not
+   fit the array and pulse falls back to the default choice. Any other value:
+   SONAR_E_ARG. */
 #define SONAR_OPT_SYNTH 5
 SONAR_API int sonar_set_option(sonar_ctx* ctx, int32_t option, int64_t value);
 

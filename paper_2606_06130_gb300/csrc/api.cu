@@ -59,7 +59,8 @@ struct sonar_ctx {
   std::string err;
   bool debug = false, timing = false, use_graph = true;
   int tile_opt = 0;
-  int synth_opt = 0;  // 0: tensor-core synthesis where supported, 1: FP32 SIMT synthesis
+  int synth_opt = 0;  // 0: tensor-core synthesis where supported, 1: FP32 SIMT synthesis,
+                      // 2, 3, 4: tensor-core synthesis asking for 32, 64, 96 columns per tile
 
   // scene
   bool has_scene = false;
@@ -408,8 +409,8 @@ int ensure_workspace(sonar_ctx* ctx, int P, const Derived& d) {
     if ((rc = grow(ctx, ctx->offsets, c1, bins, sizeof(int32_t), false))) return rc;
     ctx->ws_bins = bins;
   }
-  // guard rows: taps past the last ping and whole tensor-core tiles (up to 32 rows)
-  int64_t s_need = ((int64_t)P * d.nr_pad + 2 * kPad + 64) * d.M;
+  // guard rows: taps past the last ping and whole tensor-core tiles (up to 96 rows)
+  int64_t s_need = ((int64_t)P * d.nr_pad + 2 * kPad + 96) * d.M;
   if (s_need > ctx->ws_s || !ctx->S) {
     int64_t c0 = 0;
     dfree(ctx->S);
@@ -457,16 +458,6 @@ Mem classify(void* p, void** dev) {
     return Mem::Mapped;
   }
   return Mem::Host;
-}
-
-bool is_device_ptr(const void* p) {
-  if (!p) return false;
-  cudaPointerAttributes at;
-  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
 struct Outputs {
@@ -565,7 +556,9 @@ int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, cons
   sa.total_rows = (int64_t)P * d.nr_pad;
   sa.n_pass = p->precision == SONAR_FP32 ? 3 : 1;
   sa.err = ctx->err_dev;
-  if (ctx->synth_opt == 0 && synth_tc_supported(p->nx, p->ny, d.taps)) CU(launch_synth_tc(sa, ctx->sm_count, st));
+  static const int kPairs[5] = {0, 0, 32, 64, 96};
+  if (ctx->synth_opt != 1 && synth_tc_supported(p->nx, p->ny, d.taps))
+    CU(launch_synth_tc(sa, kPairs[ctx->synth_opt], ctx->sm_count, st));
   else CU(launch_synth(sa, ctx->sm_count, st));
   mark(3);
   ConvertArgs ca;
@@ -823,7 +816,7 @@ int sonar_set_option(sonar_ctx* ctx, int32_t option, int64_t value) {
     case SONAR_OPT_TIMING: ctx->timing = value != 0; break;
     case SONAR_OPT_GRAPH: ctx->use_graph = value != 0; break;
     case SONAR_OPT_SYNTH:
-      if (value != 0 && value != 1) return fail(ctx, SONAR_E_ARG, "synthesis option must be 0 or 1");
+      if (value < 0 || value > 4) return fail(ctx, SONAR_E_ARG, "synthesis option must be 0 to 4");
       ctx->synth_opt = (int)value;
       break;
     case SONAR_OPT_TILE_N:

@@ -158,7 +158,9 @@ cudaError_t launch_bin(const HitRec* hits, const unsigned long long* n_hits, int
 cudaError_t launch_synth(const SynthArgs& a, int sm_count, cudaStream_t st);
 bool synth_tc_supported(int nx, int ny, int taps);
 cudaError_t prepare_synth_tc();
-cudaError_t launch_synth_tc(const SynthArgs& a, int sm_count, cudaStream_t st);
+// want_pairs: complex columns per z-split tile (32, 64, 96) when that shape fits; 0 (or
+// a shape that does not fit) takes the default choice.
+cudaError_t launch_synth_tc(const SynthArgs& a, int want_pairs, int sm_count, cudaStream_t st);
 cudaError_t launch_rtab(float2* rtab, float2* rtab_s, double pulse, double bw, cudaStream_t st);
 
 struct ConvertArgs {

@@ -3,10 +3,11 @@
 // Element phasors are separable, exp(j k_a u.p_m) = ey[mx] ez[my], so the echoes of a
 // tile of T consecutive range samples are complex contractions over the hits k of
 //   S[n][my nx + mx] = sum_k g_k(n) ey_k[mx] ez_k[my],   g_k(n) = c_k R(t_n - tau_k).
-// Each hit contributes two K columns (re, im); the MMA shape is M = 128, N = 64.
+// Each hit contributes two K columns (re, im); the MMA shape is M = 128 and N = 64, 128
+// or 192 (32, 64 or 96 complex output columns per tile).
 //
 // Persistent CTAs take equal contiguous ranges of the delay-sorted hits and walk them in
-// K-blocks of up to 32 hits whose taps stay inside TMAX tiles. Generator warps form the
+// K-blocks of up to 32 hits whose taps stay inside a few tiles. Generator warps form the
 // operands in BF16 (the FP32 form also writes the residual lo parts and runs three
 // passes hi*hi, hi*lo, lo*hi); one thread issues tcgen05.mma into a ring of TMEM
 // accumulators, one per tile; four epilogue warps add a tile's accumulator into S (FP32,
@@ -19,9 +20,12 @@
 //   exp(j theta_z my_lo)). The M operand A[(my_hi, mx)][k] = ey[mx] E1[my_hi] does not
 //   depend on the tile: it is written once per K-block into tensor memory (tcgen05.st),
 //   which the MMA reads as A. Only the N operand B[k][(re/im, n, my_lo)] = g_k(n)
-//   E2[my_lo] (T = 32 / L2 samples) is formed per tile, in shared memory. The sixteen
-//   generator warps form four independent groups, one per MMA K step (8 hits), each with
-//   one warp per TMEM lane quarter and its own named barrier.
+//   E2[my_lo] (T = NP / L2 samples for NP complex columns) is formed per tile, in shared
+//   memory. Every MMA costs a fixed issue time whatever its N, so wider tiles (NP = 64,
+//   96) need fewer of them; the price is fewer TMEM accumulators (384 / 2 NP) and so
+//   fewer tiles per K-block. The sixteen generator warps form four independent groups,
+//   one per MMA K step (8 hits), each with one warp per TMEM lane quarter and its own
+//   named barrier.
 // k_synth_tc (small arrays): A[(n, mx)][k] = g_k(n) ey[mx] per tile (T = 128 / nx) and
 //   B[k][(my, re/im)] = ez[my] once per K-block, both in shared memory.
 #include <limits.h>
@@ -35,7 +39,7 @@ namespace {
 using namespace tc;
 
 constexpr int KH = 32;           // hits per K-block: K = 64 BF16 columns (re, im)
-constexpr int TMAX = 5;          // tiles one K-block may touch
+constexpr int TMAX = 5;          // tiles one K-block may touch (k_synth_tc)
 constexpr int kGenWarps = 16;
 constexpr int kGenWarp0 = 5;     // warp 0: MMA, warps 1..4: epilogue, warps 5..20: generators
 constexpr int kThreadsTC = 32 * (kGenWarp0 + kGenWarps);
@@ -48,12 +52,21 @@ constexpr int kMaxAx = 64;
 constexpr int NA = 3;            // per-tile A slots (hi + lo)
 constexpr int NB = 2;            // per-K-block B slots (hi + lo)
 constexpr int RING = 8;          // TMEM accumulators of 64 columns
-// k_synth_tz rings
+// k_synth_tz
 constexpr int kGroups = 4;
 constexpr int KG = KH / kGroups;   // hits per generator group = one MMA K step
-constexpr int NT = 8;              // per-tile B slots (hi + lo)
-constexpr int ZRING = 6;           // TMEM accumulators of 64 columns
-constexpr int kAcol = ZRING * 64;  // TMEM columns of the two per-K-block A slots (hi 32, lo 32)
+constexpr int kAcol = 384;         // TMEM columns of the two per-K-block A slots (hi 32, lo 32)
+
+// Tile shape of k_synth_tz for NP complex output columns per tile.
+template <int NP>
+struct ZShape {
+  static constexpr int N_ROWS = 2 * NP;               // B rows = MMA N: NP real, NP imaginary
+  static constexpr int B_BYTES = N_ROWS * 128;        // one 128-byte swizzled row per B row
+  static constexpr int RING = kAcol / N_ROWS;         // TMEM accumulators below the A slots
+  static constexpr int NT = NP == 32 ? 8 : (NP == 64 ? 4 : 3);  // per-tile B slots (hi + lo)
+  static constexpr int TMAXZ = RING < 5 ? RING : 5;   // tiles one K-block may touch
+  static constexpr int UNITS = 2 * (NP / 32);         // warp tasks per tile and group
+};
 
 // The walk over tiles that every role repeats identically. Tiles are numbered by a
 // virtual index that only grows; an epoch maps tile base + i to the rows origin + T i ..
@@ -62,7 +75,16 @@ constexpr int kAcol = ZRING * 64;  // TMEM columns of the two per-K-block A slot
 struct TileWalk {
   int origin = -1, base = 0;           // current epoch (origin < 0: none yet)
   int live_lo = INT_MAX, live_hi = -1;  // tiles that may still receive MMAs
-  __device__ __forceinline__ int row0(int t, int lT) const { return origin + ((t - base) << lT); }
+  __device__ __forceinline__ int row0(int t, int T) const { return origin + (t - base) * T; }
+};
+// Rows per tile T = MUL 2^s. Every quotient the walk takes is of a non-negative row
+// offset, so floor division by T is a shift and a division by the compile-time MUL (a
+// multiply-high), off the MMA issuer's critical path.
+template <int MUL>
+struct TileRows {
+  int s;
+  __device__ __forceinline__ int T() const { return MUL << s; }
+  __device__ __forceinline__ int div(int x) const { return (int)((unsigned)(x >> s) / (unsigned)MUL); }
 };
 struct KBlk {
   int cnt, t_first, t_last;
@@ -77,25 +99,27 @@ __device__ __forceinline__ int load_window(const int32_t* ng, int64_t h, int64_t
 }
 
 // K-block starting at the window's first hit: as many hits (<= 32) as keep every tap
-// inside TMAX tiles of T = 2^lT rows from the K-block's first tile. It stays in the
-// current epoch unless a new epoch at its first row n0 covers its hits with fewer tiles
-// per hit (an epoch at n0 needs ceil((span + W) / T) tiles, the fixed grid up to one more).
+// inside tmax tiles of T rows from the K-block's first tile. It stays in the current
+// epoch unless a new epoch at its first row n0 covers its hits with fewer tiles per hit
+// (an epoch at n0 needs ceil((span + W) / T) tiles, the fixed grid up to one more).
 // Warp-cooperative (all 32 lanes), identical in every role. Rows are sorted and
-// non-negative, so n0 >= origin and shifts are floor divisions.
-__device__ __forceinline__ KBlk kblock_from(int v, int lT, int W, const TileWalk& w) {
+// non-negative, so n0 >= origin and the integer quotients are floor divisions.
+template <int MUL>
+__device__ __forceinline__ KBlk kblock_from(int v, const TileRows<MUL>& tr, int tmax, int W, const TileWalk& w) {
+  const int T = tr.T();
   const int n0 = __shfl_sync(0xffffffffu, v, 0);
   int tf = 0, tl = 0, cnt = 0;
   if (w.origin >= 0) {
-    tf = (n0 - w.origin) >> lT;
-    const int lim = w.origin + ((tf + TMAX) << lT) - W;
+    tf = tr.div(n0 - w.origin);
+    const int lim = w.origin + (tf + tmax) * T - W;
     cnt = __popc(__ballot_sync(0xffffffffu, v <= lim));
-    if (cnt < 1) cnt = 1;  // cannot happen for W <= T (TMAX - 1) + 1
-    tl = (__shfl_sync(0xffffffffu, v, cnt - 1) + W - 1 - w.origin) >> lT;
+    if (cnt < 1) cnt = 1;  // cannot happen for W <= T (tmax - 1) + 1
+    tl = tr.div(__shfl_sync(0xffffffffu, v, cnt - 1) + W - 1 - w.origin);
   }
-  const int lim_f = n0 + (TMAX << lT) - W;
+  const int lim_f = n0 + tmax * T - W;
   int cnt_f = __popc(__ballot_sync(0xffffffffu, v <= lim_f));
   if (cnt_f < 1) cnt_f = 1;
-  const int tl_f = (__shfl_sync(0xffffffffu, v, cnt_f - 1) + W - 1 - n0) >> lT;
+  const int tl_f = tr.div(__shfl_sync(0xffffffffu, v, cnt_f - 1) + W - 1 - n0);
   KBlk k;
   if (w.origin < 0 || (tl_f + 1) * cnt < (tl - tf + 1) * cnt_f) {
     k.origin = n0;
@@ -207,26 +231,28 @@ __device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity, vol
 // Epilogue role (warps 1..4): walks the K-blocks like the MMA issuer and, for every tile
 // the walk has passed, adds the accumulator columns of its TMEM slot into S. dst(u, pr)
 // is the S entry of complex column pr of this thread's lane row in tile u; the real and
-// imaginary parts sit in adjacent columns (2 pr, 2 pr + 1), or, with HALVES, in columns
-// pr and 32 + pr of a 64-column accumulator.
-template <int R, bool HALVES, class Dst>
-__device__ __forceinline__ void epilogue_role(const SynthArgs& a, int64_t h0, int64_t h1, int lT, int W, int q,
-                                              int lane, uint32_t tmem_base, uint64_t* tdone, uint64_t* tfree,
-                                              volatile int* abort_flag, int n_cols, Dst dst) {
+// imaginary parts sit in adjacent columns (2 pr, 2 pr + 1) of a 64-column accumulator,
+// or, with HALVES, in columns pr and NP + pr of a 2 NP-column one. R accumulators, at
+// most tmax tiles per K-block, T rows per tile.
+template <int R, bool HALVES, int NP, class TR, class Dst>
+__device__ __forceinline__ void epilogue_role(const SynthArgs& a, int64_t h0, int64_t h1, TR tr, int tmax, int W,
+                                              int q, int lane, uint32_t tmem_base, uint64_t* tdone,
+                                              uint64_t* tfree, volatile int* abort_flag, int n_cols, Dst dst) {
+  constexpr int SLOT_COLS = HALVES ? 2 * NP : 64;
   uint32_t par = 0, cur = 0;  // per slot: parity of its use count, parity of the tile it holds
   TileWalk w;
   auto flush = [&](int u) {
-    const int64_t r0 = w.row0(u, lT);
+    const int64_t r0 = w.row0(u, tr.T());
     const int slot = u % R;
     const bool ok = wait_or_abort(smem_u32(&tdone[slot]), (cur >> slot) & 1u, abort_flag, a.err);
     if (ok) {
       tc_fence_after();
-      const uint32_t ta = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(slot * 64);
+      const uint32_t ta = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(slot * SLOT_COLS);
       if (HALVES) {
-        for (int c0 = 0; c0 < 32; c0 += 8) {
+        for (int c0 = 0; c0 < NP; c0 += 8) {
           uint32_t re[8], im[8];
           TMEM_LD_8(ta + c0, re);
-          TMEM_LD_8(ta + 32 + c0, im);
+          TMEM_LD_8(ta + NP + c0, im);
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
           for (int i = 0; i < 8; ++i) red_add2(dst(r0, c0 + i), __uint_as_float(re[i]), __uint_as_float(im[i]));
@@ -247,7 +273,7 @@ __device__ __forceinline__ void epilogue_role(const SynthArgs& a, int64_t h0, in
   };
   int win = load_window(a.sorted_n, h0, h1, lane);
   for (int64_t h = h0; h < h1;) {
-    const KBlk kb = kblock_from(win, lT, W, w);
+    const KBlk kb = kblock_from(win, tr, tmax, W, w);
     const int64_t hn = h + kb.cnt;
     win = load_window(a.sorted_n, hn, h1, lane);
     for (int u = w.live_lo; u <= w.live_hi && u < kb.t_first; ++u) flush(u);  // in their own epoch
@@ -289,27 +315,30 @@ static_assert(sizeof(ZStage<8>) % 16 == 0 && sizeof(ZStage<12>) % 16 == 0 && siz
               "stages hold 16-byte vector stores");
 static_assert(offsetof(ZStage<8>, rec) % 16 == 0, "records are 16-byte aligned in a stage");
 
-template <int WT>
+template <int WT, int NP>
 constexpr size_t tz_smem_bytes() {
-  return 1024 + (size_t)NT * 2 * N_BYTES + 2 * kGroups * sizeof(ZStage<WT>) + 64 * 8 + 64;
+  using Z = ZShape<NP>;
+  return 1024 + (size_t)Z::NT * 2 * Z::B_BYTES + 2 * kGroups * sizeof(ZStage<WT>) + 64 * 8 + 64;
 }
 
-template <int WT>
+template <int WT, int NP>
 __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_t idesc) {
+  using Z = ZShape<NP>;
+  constexpr int NT = Z::NT, RING = Z::RING, B_BYTES = Z::B_BYTES;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   // align by pointer arithmetic on the shared array, so that the compiler keeps the
   // shared address space (an integer round trip would turn every access generic)
   uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   uint8_t* sB = smem;  // NT x (hi, lo) per-tile N operands
-  ZStage<WT>(*zst)[kGroups] = reinterpret_cast<ZStage<WT>(*)[kGroups]>(sB + NT * 2 * N_BYTES);
+  ZStage<WT>(*zst)[kGroups] = reinterpret_cast<ZStage<WT>(*)[kGroups]>(sB + NT * 2 * B_BYTES);
   uint64_t* bars = reinterpret_cast<uint64_t*>(&zst[2][0]);
   uint64_t* tb_full = bars;
   uint64_t* tb_empty = bars + NT;
   uint64_t* am_full = bars + 2 * NT;
   uint64_t* am_empty = am_full + 2;
   uint64_t* tdone = am_empty + 2;
-  uint64_t* tfree = tdone + ZRING;
-  uint64_t* done = tfree + ZRING;
+  uint64_t* tfree = tdone + RING;
+  uint64_t* done = tfree + RING;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   __shared__ float2 s_rtab[kRTabS + 5];
@@ -319,7 +348,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_
   const int L2 = M / 128, lL2 = 31 - __clz(L2);  // my_lo count, a power of two
   const int H1 = ny / L2;                         // my_hi count
   const int lnx = 31 - __clz(nx);                 // nx is a power of two
-  const int T = 32 / L2, lT = 5 - lL2;
+  const TileRows<NP / 32> tr{5 - lL2};           // T = NP / L2 rows per tile
+  const int T = tr.T();
   const int W = a.taps;
   const int64_t Hn = *a.n_valid;
   const int64_t h0 = Hn * blockIdx.x / gridDim.x, h1 = Hn * (blockIdx.x + 1) / gridDim.x;
@@ -327,9 +357,12 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_
 
   for (int i = threadIdx.x; i < kRTabS + 5; i += blockDim.x) s_rtab[i] = a.rtab_s[i];
   if (threadIdx.x == 0) {
-    for (int i = 0; i < NT; ++i) { mbar_init(smem_u32(&tb_full[i]), kGenWarps / 2); mbar_init(smem_u32(&tb_empty[i]), 1); }
+    for (int i = 0; i < NT; ++i) {
+      mbar_init(smem_u32(&tb_full[i]), kGroups * Z::UNITS);
+      mbar_init(smem_u32(&tb_empty[i]), 1);
+    }
     for (int i = 0; i < 2; ++i) { mbar_init(smem_u32(&am_full[i]), kGenWarps); mbar_init(smem_u32(&am_empty[i]), 1); }
-    for (int i = 0; i < ZRING; ++i) { mbar_init(smem_u32(&tdone[i]), 1); mbar_init(smem_u32(&tfree[i]), 4); }
+    for (int i = 0; i < RING; ++i) { mbar_init(smem_u32(&tdone[i]), 1); mbar_init(smem_u32(&tfree[i]), 4); }
     mbar_init(smem_u32(done), 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -348,17 +381,17 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_
     unsigned tix = 0;
     int win = load_window(a.sorted_n, h0, h1, lane);
     for (int64_t h = h0; h < h1;) {
-      const KBlk kb = kblock_from(win, lT, W, w);
+      const KBlk kb = kblock_from(win, tr, Z::TMAXZ, W, w);
       const int64_t hn = h + kb.cnt;
       win = load_window(a.sorted_n, hn, h1, lane);
       if (lane == 0) {
         // tiles the walk has passed: their accumulators are final once these MMAs land
-        for (int u = w.live_lo; u <= w.live_hi && u < kb.t_first; ++u) tc_commit(smem_u32(&tdone[u % ZRING]));
+        for (int u = w.live_lo; u <= w.live_hi && u < kb.t_first; ++u) tc_commit(smem_u32(&tdone[u % RING]));
         const int aslot = j & 1;
         const bool a_ok = wait_or_abort(smem_u32(&am_full[aslot]), (j >> 1) & 1, abort_flag, a.err);
         const uint32_t ah = tmem_base + (uint32_t)(kAcol + aslot * 64), al = ah + 32;
         for (int t = kb.t_first; t <= kb.t_last; ++t) {
-          const int slot = t % ZRING;
+          const int slot = t % RING;
           const bool fresh = t > w.live_hi;
           bool ok = a_ok;
           if (fresh) {
@@ -367,14 +400,14 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_
             used |= bit;
             par ^= bit;
           }
-          const int bslot = tix & (NT - 1);
+          const int bslot = (int)(tix % NT);
           ok = ok && wait_or_abort(smem_u32(&tb_full[bslot]), (tix / NT) & 1, abort_flag, a.err);
           if (ok) {
             tc_fence_after();
-            const uint32_t d = tmem_base + (uint32_t)(slot * 64);
+            const uint32_t d = tmem_base + (uint32_t)(slot * Z::N_ROWS);
             // K step kk advances B by 32 bytes: +2 in the descriptor's address field
-            const uint64_t bdh = sw128_desc(smem_u32(sB + bslot * 2 * N_BYTES));
-            const uint64_t bdl = bdh + (N_BYTES >> 4);
+            const uint64_t bdh = sw128_desc(smem_u32(sB + bslot * 2 * B_BYTES));
+            const uint64_t bdl = bdh + (B_BYTES >> 4);
             tc_mma4_tmem_a(d, ah, bdh, idesc, fresh ? 0u : 1u);
             if (fp32_form) {
               tc_mma4_tmem_a(d, ah, bdl, idesc, 1u);
@@ -392,7 +425,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_
       __syncwarp();
     }
     if (lane == 0) {
-      for (int u = w.live_lo; u <= w.live_hi; ++u) tc_commit(smem_u32(&tdone[u % ZRING]));
+      for (int u = w.live_lo; u <= w.live_hi; ++u) tc_commit(smem_u32(&tdone[u % RING]));
       tc_commit(smem_u32(done));
       mbar_wait(smem_u32(done), 0, a.err);
     }
@@ -402,11 +435,12 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_
     const int q = warp & 3;  // TMEM lane quarter this warp may access
     const int L = q * 32 + lane;
     const int my_hi = L >> lnx, mx = L & (nx - 1);
-    epilogue_role<ZRING, true>(a, h0, h1, lT, W, q, lane, tmem_base, tdone, tfree, abort_flag, 64, [&](int64_t r0, int pr) {
-      const int nl = pr >> lL2, my_lo = pr & (L2 - 1);
-      const int64_t row = r0 + nl;
-      return reinterpret_cast<float*>(a.S + row * M + (my_hi * L2 + my_lo) * nx + mx);
-    });
+    epilogue_role<RING, true, NP>(a, h0, h1, tr, Z::TMAXZ, W, q, lane, tmem_base, tdone, tfree, abort_flag, 2 * NP,
+                                  [&](int64_t r0, int pr) {
+                                    const int nl = pr >> lL2, my_lo = pr & (L2 - 1);
+                                    const int64_t row = r0 + nl;
+                                    return reinterpret_cast<float*>(a.S + row * M + (my_hi * L2 + my_lo) * nx + mx);
+                                  });
   } else {
     // ------------------------------------------------------------- operand generators
     const int gw = warp - kGenWarp0;
@@ -419,13 +453,16 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_
     const int nz = H1 + L2;
     // A operand: this thread's TMEM lane is row (my_hi, mx)
     const int arow = q * 32 + lane, a_hi = arow >> lnx, a_mx = arow & (nx - 1);
-    // B operand: lane = complex column pr = (n, my_lo), written as rows pr (re) and 32 + pr
-    // (im) of one of the group's two chunks (4 hits each); warps 0, 1 of the group take the
-    // even tiles of a K-block, warps 2, 3 the odd ones
-    const int cl = wi & 1, half = wi >> 1;
-    const int pr = lane, nl = pr >> lL2, my_lo = pr & (L2 - 1);
+    // B operand: a task is 32 complex columns pr = (n, my_lo) of one tile and one of the
+    // group's two chunks (4 hits each), written as rows pr (re) and NP + pr (im). Tasks
+    // u = wi, wi + 4, ... of a K-block's tiles fall to warp wi; tasks of one tile are
+    // (column block, chunk) pairs with the chunk lowest, so a warp's chunk is fixed and
+    // so are the lane's my_lo and hit phasors.
+    const int cl = wi & 1, my_lo = lane & (L2 - 1);
     const int bchunk = 2 * grp + cl;
-    const uint32_t boff = (uint32_t)(pr * 128 + ((bchunk ^ (pr & 7)) << 4));
+    // column block pb adds 32 B rows (32 / L2 tile rows) to lane's column pr = lane
+    const uint32_t boff0 = (uint32_t)(lane * 128 + ((bchunk ^ (lane & 7)) << 4));
+    const int nl0 = lane >> lL2, nl_pb = 32 >> lL2;
     auto fetch = [&](int64_t hs) {
       uint4 v = make_uint4(0u, 0u, 0u, 0u);
       const int64_t k = hs + KG * grp + (tg >> 1);
@@ -442,7 +479,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_
     int j = 0;
     unsigned tix = 0;
     for (int64_t h = h0; h < h1;) {
-      const KBlk kb = kblock_from(win, lT, W, w);
+      const KBlk kb = kblock_from(win, tr, Z::TMAXZ, W, w);
       walk_advance(w, kb);
       const int64_t hn = h + kb.cnt;
       win = load_window(a.sorted_n, hn, h1, lane);
@@ -518,14 +555,17 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_
         e2[kk] = S.ez[4 * cl + kk][H1 + my_lo];
       }
       const int ntiles = kb.t_last - kb.t_first + 1;
-      const int trow0 = kb.origin + ((kb.t_first - kb.base) << lT) + nl;  // row nl of the first tile
-      for (int i = half; i < ntiles; i += 2) {
+      const int row_first = kb.origin + (kb.t_first - kb.base) * T;  // first row of the first tile
+      for (int u = wi; u < ntiles * Z::UNITS; u += 4) {
+        const int i = (int)((unsigned)u / (unsigned)Z::UNITS);  // tile of the K-block
+        const int pb = Z::UNITS == 2 ? 0 : (u - i * Z::UNITS) >> 1;  // column block
         const unsigned tq = tix + (unsigned)i;
-        const int bslot = tq & (NT - 1);
+        const int bslot = (int)(tq % NT);
         wait_or_abort(smem_u32(&tb_empty[bslot]), ((tq / NT) & 1) ^ 1, abort_flag, a.err);
-        const uint32_t bh = smem_u32(sB + bslot * 2 * N_BYTES), bl = bh + N_BYTES;
-        const int trow = trow0 + (i << lT);
-        // row pr: (Re b, -Im b); row 32 + pr: (Im b, Re b) = the same BF16 pair with its
+        const uint32_t bh = smem_u32(sB + bslot * 2 * B_BYTES), bl = bh + B_BYTES;
+        const uint32_t boff = boff0 + (uint32_t)(pb * 32 * 128);
+        const int trow = row_first + i * T + pb * nl_pb + nl0;
+        // row pr: (Re b, -Im b); row NP + pr: (Im b, Re b) = the same BF16 pair with its
         // halves swapped and the new low half negated (rounding is sign-symmetric)
         uint32_t hv[4], lv[4];
 #pragma unroll
@@ -543,12 +583,12 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_
         sts128(bh + boff, hv[0], hv[1], hv[2], hv[3]);
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk) hv[kk] = __byte_perm(hv[kk], 0u, 0x1032) ^ 0x8000u;
-        sts128(bh + boff + 32 * 128, hv[0], hv[1], hv[2], hv[3]);
+        sts128(bh + boff + NP * 128, hv[0], hv[1], hv[2], hv[3]);
         if (fp32_form) {
           sts128(bl + boff, lv[0], lv[1], lv[2], lv[3]);
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk) lv[kk] = __byte_perm(lv[kk], 0u, 0x1032) ^ 0x8000u;
-          sts128(bl + boff + 32 * 128, lv[0], lv[1], lv[2], lv[3]);
+          sts128(bl + boff + NP * 128, lv[0], lv[1], lv[2], lv[3]);
         }
         fence_proxy_async();
         __syncwarp();
@@ -611,7 +651,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tc(SynthArgs a, uint32_
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nx = a.nx, ny = a.ny, M = nx * ny;
   const int lnx = 31 - __clz(nx);
-  const int T = 128 / nx, lT = 7 - lnx;
+  const TileRows<1> tr{7 - lnx};  // T = 128 / nx rows per tile
+  const int T = tr.T();
   const int W = a.taps;
   const int n_cols = 2 * ny;
   const int64_t Hn = *a.n_valid;
@@ -640,7 +681,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tc(SynthArgs a, uint32_
     int j = 0, a_idx = 0;
     int win = load_window(a.sorted_n, h0, h1, lane);
     for (int64_t h = h0; h < h1;) {
-      const KBlk kb = kblock_from(win, lT, W, w);
+      const KBlk kb = kblock_from(win, tr, TMAX, W, w);
       const int64_t hn = h + kb.cnt;
       win = load_window(a.sorted_n, hn, h1, lane);
       if (lane == 0) {
@@ -693,7 +734,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tc(SynthArgs a, uint32_
     const int q = warp & 3;
     const int L = q * 32 + lane;
     const int nl = L >> lnx, mx = L & (nx - 1);
-    epilogue_role<RING, false>(a, h0, h1, lT, W, q, lane, tmem_base, tdone, tfree, abort_flag, n_cols, [&](int64_t r0, int my) {
+    epilogue_role<RING, false, 32>(a, h0, h1, tr, TMAX, W, q, lane, tmem_base, tdone, tfree, abort_flag, n_cols, [&](int64_t r0, int my) {
       const int64_t row = r0 + nl;
       return reinterpret_cast<float*>(a.S + row * M + my * nx + mx);
     });
@@ -713,7 +754,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tc(SynthArgs a, uint32_
     uint4 recv = fetch_recs(h0);
     TileWalk w;
     for (int64_t h = h0; h < h1;) {
-      const KBlk kb = kblock_from(win, lT, W, w);
+      const KBlk kb = kblock_from(win, tr, TMAX, W, w);
       walk_advance(w, kb);
       const int64_t hn = h + kb.cnt;
       win = load_window(a.sorted_n, hn, h1, lane);
@@ -779,7 +820,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tc(SynthArgs a, uint32_
         for (int idx = gt; idx < 128 * 8; idx += kGenThreads) {
           const int c = idx >> 7, row = idx & 127;
           const int nl = row >> lnx, mx = row & (nx - 1);
-          const int trow = kb.origin + ((t - kb.base) << lT) + nl;
+          const int trow = kb.origin + (t - kb.base) * T + nl;
           float2 v[4];
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk) {
@@ -814,18 +855,55 @@ bool z_split(int nx, int ny) {
          nx * (ny / L2) == 128 && ny / L2 + L2 <= kMaxAx;
 }
 
+// Shared memory per CTA: dynamic bytes plus the static pulse table (4136 bytes, padded
+// to the 1024-byte alignment of the dynamic array), within the 227 KB a CTA may hold.
+static_assert(tz_smem_bytes<16, 96>() + 5 * 1024 <= 227 * 1024, "z-split tile fits");
+static_assert(tc_smem_bytes<16>() + 5 * 1024 <= 227 * 1024, "per-tile kernel fits");
+
+// A z-split tile of NP complex columns holds T = NP / L2 whole rows, and a K-block of
+// tap span W must fit in TMAXZ of them.
+template <int NP>
+bool zs_fits(int nx, int ny, int W) {
+  const int L2 = nx * ny / 128;
+  return NP % L2 == 0 && W <= (NP / L2) * (ZShape<NP>::TMAXZ - 1) + 1;
+}
+
+// Complex columns per z-split tile (0: no z-split shape applies). want (32, 64, 96) is
+// taken when it fits; otherwise 64, then 96, then 32. 64 columns halve the MMAs of 32
+// while keeping three accumulators; 96 save a third more MMAs but leave two, which
+// stalls the issuer on the epilogue. Measured on 32x32 arrays (delay-sorted hits of a
+// 1024-bin ping): 64 columns beat 32 by 23% (FP32 form) and 6% (BF16), and 96 by 4-5%.
+int zs_pairs(int nx, int ny, int W, int want) {
+  if (!z_split(nx, ny)) return 0;
+  const bool f32 = zs_fits<32>(nx, ny, W), f64 = zs_fits<64>(nx, ny, W), f96 = zs_fits<96>(nx, ny, W);
+  if ((want == 32 && f32) || (want == 64 && f64) || (want == 96 && f96)) return want;
+  return f64 ? 64 : (f96 ? 96 : (f32 ? 32 : 0));
+}
+
 template <int WT>
 cudaError_t set_attr() {
   cudaError_t e = cudaFuncSetAttribute(k_synth_tc<WT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)tc_smem_bytes<WT>());
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_synth_tz<WT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tz_smem_bytes<WT>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_synth_tz<WT, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tz_smem_bytes<WT, 32>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_synth_tz<WT, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tz_smem_bytes<WT, 64>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_synth_tz<WT, 96>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tz_smem_bytes<WT, 96>());
+  return e;
 }
 
 template <int WT>
-void launch_one(const SynthArgs& a, bool zs, int sm_count, cudaStream_t st) {
-  if (zs)
-    k_synth_tz<WT><<<sm_count, kThreadsTC, tz_smem_bytes<WT>(), st>>>(a, make_idesc(1, 128, 64));
+void launch_one(const SynthArgs& a, int zs_np, int sm_count, cudaStream_t st) {
+  if (zs_np == 32)
+    k_synth_tz<WT, 32><<<sm_count, kThreadsTC, tz_smem_bytes<WT, 32>(), st>>>(a, make_idesc(1, 128, 64));
+  else if (zs_np == 64)
+    k_synth_tz<WT, 64><<<sm_count, kThreadsTC, tz_smem_bytes<WT, 64>(), st>>>(a, make_idesc(1, 128, 128));
+  else if (zs_np == 96)
+    k_synth_tz<WT, 96><<<sm_count, kThreadsTC, tz_smem_bytes<WT, 96>(), st>>>(a, make_idesc(1, 128, 192));
   else
     k_synth_tc<WT><<<sm_count, kThreadsTC, tc_smem_bytes<WT>(), st>>>(a, make_idesc(1, 128, 2 * a.ny));
 }
@@ -834,7 +912,7 @@ void launch_one(const SynthArgs& a, bool zs, int sm_count, cudaStream_t st) {
 
 bool synth_tc_supported(int nx, int ny, int taps) {
   if (taps > 16) return false;
-  if (z_split(nx, ny)) return taps <= (32 / (nx * ny / 128)) * (TMAX - 1) + 1;
+  if (z_split(nx, ny)) return zs_pairs(nx, ny, taps, 0) != 0;
   const bool pow2 = nx >= 4 && nx <= 64 && (nx & (nx - 1)) == 0;
   return pow2 && ny % 8 == 0 && ny >= 8 && ny <= 32 && taps <= (128 / nx) * (TMAX - 1) + 1;
 }
@@ -846,11 +924,11 @@ cudaError_t prepare_synth_tc() {
   return set_attr<16>();
 }
 
-cudaError_t launch_synth_tc(const SynthArgs& a, int sm_count, cudaStream_t st) {
-  const bool zs = z_split(a.nx, a.ny);
-  if (a.taps <= 8) launch_one<8>(a, zs, sm_count, st);
-  else if (a.taps <= 12) launch_one<12>(a, zs, sm_count, st);
-  else launch_one<16>(a, zs, sm_count, st);
+cudaError_t launch_synth_tc(const SynthArgs& a, int want_pairs, int sm_count, cudaStream_t st) {
+  const int zs_np = zs_pairs(a.nx, a.ny, a.taps, want_pairs);
+  if (a.taps <= 8) launch_one<8>(a, zs_np, sm_count, st);
+  else if (a.taps <= 12) launch_one<12>(a, zs_np, sm_count, st);
+  else launch_one<16>(a, zs_np, sm_count, st);
   return cudaGetLastError();
 }
 

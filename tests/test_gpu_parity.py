@@ -136,3 +136,23 @@ def test_tensor_core_synthesis_matches_simt(sonar, name, precision):
     tol = S_TOL if precision == "fp32" else 1e-2
     assert parity.nl2(out[0][1], out[1][1]) < tol
     assert parity.nl2(out[0][0], out[1][0]) < (1e-4 if precision == "fp32" else 1e-2)
+
+
+@pytest.mark.parametrize("shape", [2, 3, 4])
+@pytest.mark.parametrize("nx,ny,precision", [(32, 32, "fp32"), (16, 16, "fp32"), (8, 16, "fp32"), (32, 32, "bf16")])
+def test_z_split_tile_shapes_match_simt(sonar, shape, nx, ny, precision):
+    """The z-split kernel at each tile width (32, 64, 96 complex columns: synthesis
+    option 2, 3, 4) with L2 = 8, 2 and 1 fine z elements per tile row, against the FP32
+    SIMT kernel: FP32 form to S_TOL, BF16 form to 1e-2."""
+    from paper_2606_06130_gb300.sonar import SONAR_OPT_SYNTH
+    scene, params, poses, ssp = inputs.workload("c1")
+    params = dict(params, nx=nx, ny=ny, n_beam_az=24, n_beam_el=12)
+    out = {}
+    for mode in (1, shape):
+        sonar.set_option(SONAR_OPT_SYNTH, mode)
+        E, _, _ = run(sonar, scene, params, poses[0], ssp, precision)
+        out[mode] = (E, sonar.echoes(params)[0])
+    sonar.set_option(SONAR_OPT_SYNTH, 0)
+    tol = S_TOL if precision == "fp32" else 1e-2
+    assert parity.nl2(out[shape][1], out[1][1]) < tol
+    assert parity.nl2(out[shape][0], out[1][0]) < (1e-4 if precision == "fp32" else 1e-2)
