@@ -65,7 +65,6 @@ struct ZShape {
   static constexpr int RING = kAcol / N_ROWS;         // TMEM accumulators below the A slots
   static constexpr int NT = NP == 32 ? 8 : (NP == 64 ? 4 : 3);  // per-tile B slots (hi + lo)
   static constexpr int TMAXZ = RING < 5 ? RING : 5;   // tiles one K-block may touch
-  static constexpr int UNITS = 2 * (NP / 32);         // warp tasks per tile and group
 };
 
 // The walk over tiles that every role repeats identically. Tiles are numbered by a
@@ -154,6 +153,9 @@ __device__ __forceinline__ uint32_t pack_lo(float a, float b, uint32_t hi) {
 }
 __device__ __forceinline__ void sts128(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
   asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
+}
+__device__ __forceinline__ void sts64(uint32_t addr, uint32_t a, uint32_t b) {
+  asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(addr), "r"(a), "r"(b) : "memory");
 }
 __device__ __forceinline__ void red_add2(float* dst, float a, float b) {
   asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(dst), "f"(a), "f"(b) : "memory");
@@ -358,7 +360,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_
   for (int i = threadIdx.x; i < kRTabS + 5; i += blockDim.x) s_rtab[i] = a.rtab_s[i];
   if (threadIdx.x == 0) {
     for (int i = 0; i < NT; ++i) {
-      mbar_init(smem_u32(&tb_full[i]), kGroups * Z::UNITS);
+      mbar_init(smem_u32(&tb_full[i]), kGenWarps);
       mbar_init(smem_u32(&tb_empty[i]), 1);
     }
     for (int i = 0; i < 2; ++i) { mbar_init(smem_u32(&am_full[i]), kGenWarps); mbar_init(smem_u32(&am_empty[i]), 1); }
@@ -453,16 +455,15 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_
     const int nz = H1 + L2;
     // A operand: this thread's TMEM lane is row (my_hi, mx)
     const int arow = q * 32 + lane, a_hi = arow >> lnx, a_mx = arow & (nx - 1);
-    // B operand: a task is 32 complex columns pr = (n, my_lo) of one tile and one of the
-    // group's two chunks (4 hits each), written as rows pr (re) and NP + pr (im). Tasks
-    // u = wi, wi + 4, ... of a K-block's tiles fall to warp wi; tasks of one tile are
-    // (column block, chunk) pairs with the chunk lowest, so a warp's chunk is fixed and
-    // so are the lane's my_lo and hit phasors.
-    const int cl = wi & 1, my_lo = lane & (L2 - 1);
-    const int bchunk = 2 * grp + cl;
-    // column block pb adds 32 B rows (32 / L2 tile rows) to lane's column pr = lane
-    const uint32_t boff0 = (uint32_t)(lane * 128 + ((bchunk ^ (lane & 7)) << 4));
-    const int nl0 = lane >> lL2, nl_pb = 32 >> lL2;
+    // B operand: the group's share of a tile is NP complex columns pr = (n, my_lo) by its
+    // 8 hits, written as rows pr (re) and NP + pr (im). Item it = tg + 128 r (r < NP / 32)
+    // is column pr = it / 4 and hit pair pp = it % 4 (hits 2 pp, 2 pp + 1: one 8-byte
+    // half of a 16-byte chunk), so every thread has the same number of items per tile and
+    // keeps its hit pair, my_lo and the column's swizzle phase for the whole kernel.
+    const int pp = tg & 3, c0 = tg >> 2;                  // column c0 + 32 r
+    const int my_lo = c0 & (L2 - 1);
+    const int nl0 = c0 >> lL2, nl_r = 32 >> lL2;          // tile row of column c0 + 32 r
+    const uint32_t boff0 = (uint32_t)(c0 * 128 + (((2 * grp + (pp >> 1)) ^ (c0 & 7)) << 4) + ((pp & 1) << 3));
     auto fetch = [&](int64_t hs) {
       uint4 v = make_uint4(0u, 0u, 0u, 0u);
       const int64_t k = hs + KG * grp + (tg >> 1);
@@ -546,49 +547,44 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&am_full[aslot]));
 
-      // per-tile B operand: rows (n, my_lo, re/im) of chunk bchunk
-      int nk[4];
-      float2 e2[4];
-#pragma unroll
-      for (int kk = 0; kk < 4; ++kk) {
-        nk[kk] = S.n[4 * cl + kk];
-        e2[kk] = S.ez[4 * cl + kk][H1 + my_lo];
-      }
+      // per-tile B operand: every generator thread writes NP / 32 items of every tile
+      const int k0 = 2 * pp, k1 = k0 + 1;
+      const int nk0 = S.n[k0], nk1 = S.n[k1];
+      const float2 e20 = S.ez[k0][H1 + my_lo], e21 = S.ez[k1][H1 + my_lo];
       const int ntiles = kb.t_last - kb.t_first + 1;
       const int row_first = kb.origin + (kb.t_first - kb.base) * T;  // first row of the first tile
-      for (int u = wi; u < ntiles * Z::UNITS; u += 4) {
-        const int i = (int)((unsigned)u / (unsigned)Z::UNITS);  // tile of the K-block
-        const int pb = Z::UNITS == 2 ? 0 : (u - i * Z::UNITS) >> 1;  // column block
+      for (int i = 0; i < ntiles; ++i) {
         const unsigned tq = tix + (unsigned)i;
         const int bslot = (int)(tq % NT);
         wait_or_abort(smem_u32(&tb_empty[bslot]), ((tq / NT) & 1) ^ 1, abort_flag, a.err);
         const uint32_t bh = smem_u32(sB + bslot * 2 * B_BYTES), bl = bh + B_BYTES;
-        const uint32_t boff = boff0 + (uint32_t)(pb * 32 * 128);
-        const int trow = row_first + i * T + pb * nl_pb + nl0;
-        // row pr: (Re b, -Im b); row NP + pr: (Im b, Re b) = the same BF16 pair with its
-        // halves swapped and the new low half negated (rounding is sign-symmetric)
-        uint32_t hv[4], lv[4];
+        const int trow0 = row_first + i * T + nl0;
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-          const int tap = trow - nk[kk];
-          float bx = 0.f, nby = 0.f;
-          if ((unsigned)tap < (unsigned)WT) {
-            const float2 g = S.g[tap][4 * cl + kk];
-            bx = g.x * e2[kk].x - g.y * e2[kk].y;
-            nby = -(g.x * e2[kk].y) - g.y * e2[kk].x;
+        for (int r = 0; r < NP / 32; ++r) {
+          const int trow = trow0 + r * nl_r;
+          const uint32_t boff = boff0 + (uint32_t)(r * 32 * 128);
+          // row pr: (Re b, -Im b); row NP + pr: (Im b, Re b) = the same BF16 pair with its
+          // halves swapped and the new low half negated (rounding is sign-symmetric)
+          float bx0 = 0.f, nby0 = 0.f, bx1 = 0.f, nby1 = 0.f;
+          const int tap0 = trow - nk0, tap1 = trow - nk1;
+          if ((unsigned)tap0 < (unsigned)WT) {
+            const float2 g = S.g[tap0][k0];
+            bx0 = g.x * e20.x - g.y * e20.y;
+            nby0 = -(g.x * e20.y) - g.y * e20.x;
           }
-          hv[kk] = pack_bf16(bx, nby);
-          lv[kk] = pack_lo(bx, nby, hv[kk]);
-        }
-        sts128(bh + boff, hv[0], hv[1], hv[2], hv[3]);
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk) hv[kk] = __byte_perm(hv[kk], 0u, 0x1032) ^ 0x8000u;
-        sts128(bh + boff + NP * 128, hv[0], hv[1], hv[2], hv[3]);
-        if (fp32_form) {
-          sts128(bl + boff, lv[0], lv[1], lv[2], lv[3]);
-#pragma unroll
-          for (int kk = 0; kk < 4; ++kk) lv[kk] = __byte_perm(lv[kk], 0u, 0x1032) ^ 0x8000u;
-          sts128(bl + boff + NP * 128, lv[0], lv[1], lv[2], lv[3]);
+          if ((unsigned)tap1 < (unsigned)WT) {
+            const float2 g = S.g[tap1][k1];
+            bx1 = g.x * e21.x - g.y * e21.y;
+            nby1 = -(g.x * e21.y) - g.y * e21.x;
+          }
+          const uint32_t h0 = pack_bf16(bx0, nby0), h1 = pack_bf16(bx1, nby1);
+          sts64(bh + boff, h0, h1);
+          sts64(bh + boff + NP * 128, __byte_perm(h0, 0u, 0x1032) ^ 0x8000u, __byte_perm(h1, 0u, 0x1032) ^ 0x8000u);
+          if (fp32_form) {
+            const uint32_t l0 = pack_lo(bx0, nby0, h0), l1 = pack_lo(bx1, nby1, h1);
+            sts64(bl + boff, l0, l1);
+            sts64(bl + boff + NP * 128, __byte_perm(l0, 0u, 0x1032) ^ 0x8000u, __byte_perm(l1, 0u, 0x1032) ^ 0x8000u);
+          }
         }
         fence_proxy_async();
         __syncwarp();
@@ -869,15 +865,17 @@ bool zs_fits(int nx, int ny, int W) {
 }
 
 // Complex columns per z-split tile (0: no z-split shape applies). want (32, 64, 96) is
-// taken when it fits; otherwise 64, then 96, then 32. 64 columns halve the MMAs of 32
-// while keeping three accumulators; 96 save a third more MMAs but leave two, which
-// stalls the issuer on the epilogue. Measured on 32x32 arrays (delay-sorted hits of a
-// 1024-bin ping): 64 columns beat 32 by 23% (FP32 form) and 6% (BF16), and 96 by 4-5%.
+// taken when it fits; otherwise 96, then 64, then 32. An MMA costs about the same issue
+// time whatever its N, so 96 columns need a third of the MMAs of 32; and with T = 12
+// rows an 11-tap K-block of one row fits one tile, which also halves the B operand rows
+// formed per K-block against 64 columns. Measured on 32x32 arrays (1024-bin ping, 534k
+// hits), 32 / 64 / 96 columns: FP32 form 0.346 / 0.262 / 0.252 ms, BF16 0.264 / 0.240 /
+// 0.225 ms.
 int zs_pairs(int nx, int ny, int W, int want) {
   if (!z_split(nx, ny)) return 0;
   const bool f32 = zs_fits<32>(nx, ny, W), f64 = zs_fits<64>(nx, ny, W), f96 = zs_fits<96>(nx, ny, W);
   if ((want == 32 && f32) || (want == 64 && f64) || (want == 96 && f96)) return want;
-  return f64 ? 64 : (f96 ? 96 : (f32 ? 32 : 0));
+  return f96 ? 96 : (f64 ? 64 : (f32 ? 32 : 0));
 }
 
 template <int WT>
