@@ -17,15 +17,15 @@
 //
 // k_synth_tz (arrays of nx ny = 128 L2 elements): with my = my_hi L2 + my_lo the z
 //   phasor factors as ez[my] = E1[my_hi] E2[my_lo] (E1 = ez at L2 my_hi, E2[my_lo] =
-//   exp(j theta_z my_lo)). The M operand A[(my_hi, mx)][k] = ey[mx] E1[my_hi] does not
-//   depend on the tile: it is written once per K-block into tensor memory (tcgen05.st),
-//   which the MMA reads as A. Only the N operand B[k][(re/im, n, my_lo)] = g_k(n)
-//   E2[my_lo] (T = NP / L2 samples for NP complex columns) is formed per tile, in shared
-//   memory. Every MMA costs a fixed issue time whatever its N, so wider tiles (NP = 64,
-//   96) need fewer of them; the price is fewer TMEM accumulators (384 / 2 NP) and so
-//   fewer tiles per K-block. The sixteen generator warps form four independent groups,
-//   one per MMA K step (8 hits), each with one warp per TMEM lane quarter and its own
-//   named barrier.
+//   exp(j theta_z my_lo)). The M operand A[(my_hi, mx)][k] = ey[mx] E1[my_hi], one phase
+//   per entry, does not depend on the tile: it is written once per K-block into tensor
+//   memory (tcgen05.st), which the MMA reads as A. Only the N operand B[k][(re/im, n,
+//   my_lo)] = g_k(n) E2[my_lo] (T = NP / L2 samples for NP complex columns) is formed per
+//   tile, in shared memory. Every MMA costs a fixed issue time whatever its N, so wider
+//   tiles (NP = 64, 96) need fewer of them; the price is fewer TMEM accumulators
+//   (384 / 2 NP) and so fewer tiles per K-block. The sixteen generator warps form four
+//   independent groups, one per MMA K step (8 hits), each with one warp per TMEM lane
+//   quarter and its own named barrier.
 // k_synth_tc (small arrays): A[(n, mx)][k] = g_k(n) ey[mx] per tile (T = 128 / nx) and
 //   B[k][(my, re/im)] = ez[my] once per K-block, both in shared memory.
 #include <limits.h>
@@ -309,8 +309,7 @@ struct alignas(16) ZStage {  // one generator group's 8 hits of one K-block
   HitRec rec[KG];
   int n[KG];
   float2 g[WT][KG];        // taps, tap-major
-  float2 ey[KG][kMaxAx];
-  float2 ez[KG][kMaxAx];   // E1 in [0, H1), E2 in [H1, H1 + L2)
+  float2 e2[KG][32];       // E2[my_lo], my_lo < L2 <= 32
 };
 
 static_assert(sizeof(ZStage<8>) % 16 == 0 && sizeof(ZStage<12>) % 16 == 0 && sizeof(ZStage<16>) % 16 == 0,
@@ -348,7 +347,6 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nx = a.nx, ny = a.ny, M = nx * ny;
   const int L2 = M / 128, lL2 = 31 - __clz(L2);  // my_lo count, a power of two
-  const int H1 = ny / L2;                         // my_hi count
   const int lnx = 31 - __clz(nx);                 // nx is a power of two
   const TileRows<NP / 32> tr{5 - lL2};           // T = NP / L2 rows per tile
   const int T = tr.T();
@@ -452,9 +450,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_
     const int q = warp & 3;             // TMEM lane quarter of this warp
     const uint32_t bar_id = 1 + grp;
     const float pl2 = 2.0f * a.pitch_over_lambda;
-    const int nz = H1 + L2;
-    // A operand: this thread's TMEM lane is row (my_hi, mx)
+    // A operand: this thread's TMEM lane is row (my_hi, mx), element (mx, L2 my_hi)
     const int arow = q * 32 + lane, a_hi = arow >> lnx, a_mx = arow & (nx - 1);
+    const float ax = pl2 * ((float)a_mx - 0.5f * (float)(nx - 1));
+    const float az = pl2 * ((float)(L2 * a_hi) - 0.5f * (float)(ny - 1));
     // B operand: the group's share of a tile is NP complex columns pr = (n, my_lo) by its
     // 8 hits, written as rows pr (re) and NP + pr (im). Item it = tg + 128 r (r < NP / 32)
     // is column pr = it / 4 and hit pair pp = it % 4 (hits 2 pp, 2 pp + 1: one 8-byte
@@ -498,28 +497,17 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_
         S.g[qq][kl] = g;
         if (qq == 0) S.n[kl] = kl < kvalid ? S.rec[kl].nglob : INT_MIN / 2;
       }
-      // ey[mx] = exp(j 2 pi (d/lambda) (mx - (nx-1)/2) u_y)
-      for (int item = tg; item < KG * nx; item += 128) {
-        const int mx = item & (nx - 1), kl = item >> lnx;
+      // E2[my_lo] = exp(j 2 pi (d/lambda) my_lo u_z), on the group's last threads (the
+      // first KG WT ones form the taps)
+      for (int item = 127 - tg; item < KG * L2; item += 128) {
+        const int kl = item & (KG - 1), ql = item >> 3;
         float2 e = make_float2(0.f, 0.f);
         if (kl < kvalid) {
           float s, c;
-          sincospi_operand(pl2 * ((float)mx - 0.5f * (float)(nx - 1)) * S.rec[kl].uy, &s, &c);
+          sincospi_operand(pl2 * (float)ql * S.rec[kl].uz, &s, &c);
           e = make_float2(c, s);
         }
-        S.ey[kl][mx] = e;
-      }
-      // E1[my_hi] = ez[L2 my_hi], E2[my_lo] = exp(j 2 pi (d/lambda) my_lo u_z)
-      for (int item = tg; item < KG * nz; item += 128) {
-        const int kl = item & (KG - 1), qz = item >> 3;
-        float2 e = make_float2(0.f, 0.f);
-        if (kl < kvalid) {
-          const float arg = qz < H1 ? (float)(L2 * qz) - 0.5f * (float)(ny - 1) : (float)(qz - H1);
-          float s, c;
-          sincospi_operand(pl2 * arg * S.rec[kl].uz, &s, &c);
-          e = make_float2(c, s);
-        }
-        S.ez[kl][qz] = e;
+        S.e2[kl][ql] = e;
       }
       // the next K-block's records go to the other stage buffer, whose records were last
       // read before the previous barrier
@@ -531,12 +519,17 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_
       wait_or_abort(smem_u32(&am_empty[aslot]), ((j >> 1) & 1) ^ 1, abort_flag, a.err);
       tc_fence_after();
       {
+        // ey[mx] E1[my_hi] = exp(j 2 pi (d/lambda) ((mx - (nx-1)/2) u_y + (L2 my_hi -
+        // (ny-1)/2) u_z)), one phase per hit (padding hits: 0)
         uint32_t hi[KG], lo[KG];
 #pragma unroll
         for (int kl = 0; kl < KG; ++kl) {
-          const float2 v = cmul(S.ey[kl][a_mx], S.ez[kl][a_hi]);
-          hi[kl] = pack_bf16(v.x, v.y);
-          lo[kl] = pack_lo(v.x, v.y, hi[kl]);
+          const float2 u = *reinterpret_cast<const float2*>(&S.rec[kl].uy);
+          float sn, cs;
+          sincospi_operand(fmaf(ax, u.x, az * u.y), &sn, &cs);
+          if (kl >= kvalid) sn = cs = 0.f;
+          hi[kl] = pack_bf16(cs, sn);
+          lo[kl] = pack_lo(cs, sn, hi[kl]);
         }
         const uint32_t ta = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(kAcol + aslot * 64 + KG * grp);
         tmem_st8(ta, hi);
@@ -550,7 +543,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_
       // per-tile B operand: every generator thread writes NP / 32 items of every tile
       const int k0 = 2 * pp, k1 = k0 + 1;
       const int nk0 = S.n[k0], nk1 = S.n[k1];
-      const float2 e20 = S.ez[k0][H1 + my_lo], e21 = S.ez[k1][H1 + my_lo];
+      const float2 e20 = S.e2[k0][my_lo], e21 = S.e2[k1][my_lo];
       const int ntiles = kb.t_last - kb.t_first + 1;
       const int row_first = kb.origin + (kb.t_first - kb.base) * T;  // first row of the first tile
       for (int i = 0; i < ntiles; ++i) {
@@ -869,8 +862,8 @@ bool zs_fits(int nx, int ny, int W) {
 // time whatever its N, so 96 columns need a third of the MMAs of 32; and with T = 12
 // rows an 11-tap K-block of one row fits one tile, which also halves the B operand rows
 // formed per K-block against 64 columns. Measured on 32x32 arrays (1024-bin ping, 534k
-// hits), 32 / 64 / 96 columns: FP32 form 0.346 / 0.262 / 0.252 ms, BF16 0.264 / 0.240 /
-// 0.225 ms.
+// hits), 64 / 96 columns: FP32 form 0.248 / 0.225 ms, BF16 0.215 / 0.205 ms; 32 columns
+// took 30% longer than 64 (FP32 form).
 int zs_pairs(int nx, int ny, int W, int want) {
   if (!z_split(nx, ny)) return 0;
   const bool f32 = zs_fits<32>(nx, ny, W), f64 = zs_fits<64>(nx, ny, W), f96 = zs_fits<96>(nx, ny, W);
