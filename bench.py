@@ -92,12 +92,13 @@ def oracle_ping(scene, params, pose, ssp):
     import oracle
     h = oracle.trace(scene, params, pose, ssp)
     E, _, _ = oracle.volume(params, h)
-    oracle.peaks(params, pose, E)
-    return h["n"]
+    pk = oracle.peaks(params, pose, E)
+    return h, E, pk
 
 
-def time_oracle(steps, warmup, min_seconds=0.0, k=8):
-    """Oracle pings/s on the 1/k-ping sample: `steps` samples, more until min_seconds pass."""
+def time_oracle(steps, warmup, min_seconds=0.0, k=8, keep=None):
+    """Oracle pings/s on the 1/k-ping sample: `steps` samples, more until min_seconds pass.
+    keep (a dict), if given, receives the sample's parameters and the last oracle outputs."""
     import oracle
     from paper_2606_06130_gb300 import inputs
     scene, params, poses, ssp = inputs.workload("c2")
@@ -107,10 +108,12 @@ def time_oracle(steps, warmup, min_seconds=0.0, k=8):
     t0 = time.perf_counter()
     done = 0
     while done < steps or time.perf_counter() - t0 < min_seconds:
-        oracle_ping(scene, q, poses[0], ssp)
+        out = oracle_ping(scene, q, poses[0], ssp)
         done += 1
     steps = done
     dt = time.perf_counter() - t0
+    if keep is not None:
+        keep.update(params=q, pose=poses[0], ssp=ssp, h=out[0], E=out[1], peaks=out[2])
     return {"value": steps * frac / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"1/{k} of the ping per step: central 1/{k} of the vertical field of view "
                       f"({params['n_ray_el'] // k} of {params['n_ray_el']} ray rows, {params['n_beam_el'] // k} of "
@@ -228,6 +231,16 @@ def run_ours(args, ws, rank, local):
     scene, params, poses, ssp = inputs.workload("c2")
     s = Sonar(local)
     s.upload(scene)
+    torch.cuda.synchronize()
+    # scene upload and BVH build, timed apart from the pings (median of 3 rebuilds)
+    up = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        s.upload(scene)
+        torch.cuda.synchronize()
+        up.append((time.perf_counter() - t0) * 1e3)
+    upload_ms = {"value": float(np.median(up)), "unit": "ms", "triangles": int(len(scene.tris)),
+                 "what": "host-to-device copy, LBVH build and packing (wall clock)"}
     nb = params["n_beam_az"] * params["n_beam_el"]
     env = torch.empty((params["n_beam_el"], params["n_beam_az"], params["n_range"]), dtype=torch.float32, device=dev)
     cloud = torch.empty((nb, 6), dtype=torch.int32, device=dev)
@@ -330,10 +343,13 @@ def run_ours(args, ws, rank, local):
             "peak_source": pnote, "traffic": traffic,
             "algorithmic_per_launch": amount, "algorithmic_unit": unit, "launch_ms": mean_stage[dom]}
 
-    err = oracle_error(scene, params, pose, ssp, env, args.precision) if not args.no_oracle else None
-    cpu = None
+    # CPU baseline leg: the oracle timed on a sample of the workload; the same sample's
+    # oracle outputs give the GPU path's errors
+    cpu = err = None
     if ws == 1 and not args.no_oracle:
-        cpu = time_oracle(1, 0, min_seconds=10.0)
+        ref = {}
+        cpu = time_oracle(1, 0, min_seconds=10.0, keep=ref)
+        err = sample_errors(torch, s, ref)
     value = whole_job_rate(ws, args.steps, t_ms / 1e3)
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": max(args.warmup, 3), "ms_per_step": t_ms / args.steps, "higher_is_better": True,
@@ -346,6 +362,8 @@ def run_ours(args, ws, rank, local):
                       "parallelism": f"replicas x{ws}"},
            "roofline": roof,
            "stages_ms": mean_stage,
+           "stage_rooflines": stage_rooflines(mean_stage, params, stats, args.precision, pk),
+           "scene_upload_ms": upload_ms,
            "hits_per_ping": stats["n_hits"],
            "gpu_launches": launches,
            "graph_replay": {"value": whole_job_rate(ws, args.steps, g_ms / 1e3), "unit": UNIT,
@@ -363,18 +381,81 @@ def run_ours(args, ws, rank, local):
         torch.distributed.destroy_process_group()
 
 
-def oracle_error(scene, params, pose, ssp, env, precision):
-    """Envelope normalised L2 against the FP64 oracle on sampled range bins (all beams)."""
-    import oracle
-    h = oracle.trace(scene, params, pose, ssp)
-    dr = params["r_max"] / params["n_range"]
-    n_hit = np.floor(h["tau"] * h["c_ref"] / 2 / dr).astype(int)
-    dense = np.argsort(np.bincount(n_hit, minlength=params["n_range"]))[-8:]
-    ns = np.unique(np.concatenate([dense, np.arange(0, params["n_range"], 128)])).astype(np.int32)
-    E_ref, _, _ = oracle.volume(params, h, ns=ns)
-    E = env.reshape(-1, params["n_range"]).double().cpu().numpy()[:, ns]
-    return {"env_nl2": float(np.linalg.norm(E - E_ref) / np.linalg.norm(E_ref)), "sampled_bins": len(ns),
-            "beams": int(E.shape[0]), "precision": precision}
+def sample_errors(torch, s, ref):
+    """Errors of the GPU path on the CPU-baseline sample, against the oracle outputs of
+    that sample (all its bins and beams): envelope normalised L2 per precision form;
+    prim ids and peak (beam, bin) mismatches outside the near-tie margins, with the
+    excluded counts (FP32 form)."""
+    from paper_2606_06130_gb300.sonar import SONAR_OPT_DEBUG, cloud_records
+    from tests import parity
+    q, pose, ssp, h, E_ref, pk = ref["params"], ref["pose"], ref["ssp"], ref["h"], ref["E"], ref["peaks"]
+    out = {"sample": "the CPU baseline's sample (central 1/8 of the vertical field of view)",
+           "beams": int(E_ref.shape[0]), "bins": int(E_ref.shape[1]), "hits_oracle": int(h["n"])}
+    s.set_option(SONAR_OPT_DEBUG, 1)
+    env_nl2 = {}
+    for prec in ("fp32", "bf16", "fp16"):
+        env, cloud, n = s.ping(pose, q, ssp, precision=prec)
+        torch.cuda.synchronize()
+        E = env.reshape(-1, q["n_range"]).double().cpu().numpy()
+        env_nl2[prec] = parity.nl2(E, E_ref)
+        rel = 1e-3 if prec == "fp32" else 2e-2
+        nb0 = parity.n_blank(q)
+        vmax = E_ref[:, nb0:].max()
+        thr = q["thr"] * vmax if q["thr_mode"] == 1 else q["thr"]
+        ok = parity.peak_margin_mask(E_ref, nb0, thr, rel)
+        pts = cloud_records(cloud, n)
+        gpu = {int(b): int(k) for b, k in zip(pts["beam"], pts["bin"])}
+        want = {int(b): int(k) for b, k in zip(pk["beam"], pk["bin"])}
+        bad = sum(1 for b in np.nonzero(ok)[0] if gpu.get(int(b)) != want.get(int(b)))
+        out[f"peaks_{prec}"] = {"mismatch": bad, "excluded": int(np.count_nonzero(~ok)), "margin_rel": rel}
+        if prec == "fp32":
+            g = s.hits()
+            ig, ir, only_g, only_r = parity.match_hits(g, h, q["n_sub"])
+            clear = (h["margin"][ir] > 1e-5) & (h["gap"][ir] > 1e-6)
+            out["prims"] = {"matched": int(len(ig)), "mismatch": int(np.count_nonzero((g["prim"][ig] != h["prim"][ir]) & clear)),
+                            "excluded": int(np.count_nonzero(~clear)), "unmatched": int(len(only_g) + len(only_r))}
+    s.set_option(SONAR_OPT_DEBUG, 0)
+    out["env_nl2"] = env_nl2
+    return out
+
+
+def stage_rooflines(mean_stage, params, stats, precision, pk):
+    """Achieved rate of every stage against its bound: tensor stages in TFLOP/s of the
+    measured BF16 peaks (burst and sustained), memory stages in GB/s of the measured HBM
+    copy rate, the traversal in sub-rays/s (FP64- and latency-bound: no single peak)."""
+    M = params["nx"] * params["ny"]
+    nb = params["n_beam_az"] * params["n_beam_el"]
+    nr = params["n_range"]
+    H = float(stats["n_hits"])
+    sub_rays = params["n_ray_az"] * params["n_ray_el"] * params["n_sub"]
+    hbm = pk["hbm_gbs"]
+
+    def mem(stage, nbytes, what):
+        gbs = nbytes / (mean_stage[stage] / 1e3) / 1e9
+        return {"bound": "hbm", "bytes": nbytes, "bytes_are": what, "achieved": gbs, "unit": "GB/s",
+                "peak": hbm, "frac": gbs / hbm}
+
+    def tensor(stage, flop, executed):
+        tf = flop / (mean_stage[stage] / 1e3) / 1e12
+        return {"bound": "tensor", "flop": flop, "executed_flop": executed, "achieved": tf, "unit": "TFLOP/s",
+                "peak": pk["bf16_tflops"], "frac": tf / pk["bf16_tflops"],
+                "frac_sustained": tf / pk["bf16_tflops_sustained"],
+                "executed_frac": executed / flop * tf / pk["bf16_tflops"]}
+
+    n_pass = 3 if precision == "fp32" else 1
+    synth_flop = H * M * (8 * stats["taps"] + 6)
+    gemm_flop = 8.0 * nb * M * nr
+    out = {
+        "trace": {"bound": "fp64 pipe and latency", "achieved": sub_rays / (mean_stage["trace"] / 1e3) / 1e6,
+                  "unit": "M sub-rays/s", "hits_per_s": H / (mean_stage["trace"] / 1e3), "peak": None, "frac": None},
+        "bin": mem("bin", 2 * 32 * H, "32-byte hit records read and written once"),
+        "synth": tensor("synth", synth_flop, synth_flop),
+        "convert": mem("convert", nr * M * (8 + (8 if precision == "fp32" else 4)),
+                       "FP32 complex echoes read, 16-bit operand(s) written"),
+        "beamform": tensor("beamform", gemm_flop, gemm_flop * n_pass),
+        "peaks": mem("peaks", nb * (8 + 24), "per-beam keys read, point records written"),
+    }
+    return out
 
 
 def other_forms(torch, s, inputs, dev):
