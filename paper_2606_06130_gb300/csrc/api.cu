@@ -614,10 +614,12 @@ int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, cons
   pa.n_beam_az = p->n_beam_az;
   pa.n_beam_el = p->n_beam_el;
   pa.nr = d.nr;
-  pa.hfov = p->hfov_rad;
-  pa.vfov = p->vfov_rad;
-  pa.r_min = p->r_min_m;
-  pa.dr = d.dr;
+  pa.az0 = (float)(-p->hfov_rad / 2);
+  pa.daz = (float)(p->hfov_rad / p->n_beam_az);
+  pa.el0 = (float)(-p->vfov_rad / 2);
+  pa.del = (float)(p->vfov_rad / p->n_beam_el);
+  pa.r_min = (float)p->r_min_m;
+  pa.dr = (float)d.dr;
   pa.thr_mode = p->thr_mode;
   pa.thr = (float)p->thr;
   pa.cloud = o.cloud;

@@ -262,7 +262,8 @@ __global__ void k_steer(SteerArgs a) {
 // or ping-relative threshold, and write points in beam order. One CTA per 1024 beams of a
 // ping: it recounts the kept beams of the chunks before its own (a few thousand keys, so
 // no CTA waits on another), then places its own by a block-wide exclusive scan of the
-// keep flags. Positions in FP32 (a 15 m range keeps them within ~1e-6 m).
+// keep flags. Positions in FP32 (a 15 m range keeps them within ~1e-6 m), from the
+// beam grid and pose rounded to FP32 once (FP64 work per thread is slow on this part).
 __device__ __forceinline__ bool peak_kept(unsigned long long key, float thr) {
   return key != 0ull && __uint_as_float((uint32_t)(key >> 32)) >= thr;
 }
@@ -276,9 +277,16 @@ __global__ void __launch_bounds__(1024) k_peaks(PeakArgs a) {
   const float thr = a.thr_mode == 1 ? a.thr * vmax : a.thr;
   const unsigned long long* keys = a.peak_keys + (size_t)p * Nb;
   const int b0 = chunk * 1024;
-  // kept beams in the chunks before this one
+  // kept beams in the chunks before this one (independent loads, four at a time)
   int before = 0;
-  for (int b = t; b < b0; b += 1024) before += peak_kept(__ldg(&keys[b]), thr) ? 1 : 0;
+  int bb = t;
+  for (; bb + 3 * 1024 < b0; bb += 4 * 1024) {
+    const unsigned long long k0 = __ldg(&keys[bb]), k1 = __ldg(&keys[bb + 1024]);
+    const unsigned long long k2 = __ldg(&keys[bb + 2048]), k3 = __ldg(&keys[bb + 3072]);
+    before += (peak_kept(k0, thr) ? 1 : 0) + (peak_kept(k1, thr) ? 1 : 0) + (peak_kept(k2, thr) ? 1 : 0) +
+              (peak_kept(k3, thr) ? 1 : 0);
+  }
+  for (; bb < b0; bb += 1024) before += peak_kept(__ldg(&keys[bb]), thr) ? 1 : 0;
   for (int o = 16; o > 0; o >>= 1) before += __shfl_xor_sync(0xffffffffu, before, o);
   if (lane == 0) s_warp[wid] = before;
   __syncthreads();
@@ -310,19 +318,19 @@ __global__ void __launch_bounds__(1024) k_peaks(PeakArgs a) {
   __syncthreads();
   const long long pos = (long long)base + s_warp[wid] + in_warp;
   if (keep && pos < a.cap) {
-    const DevPose& P = a.poses[p];
-    const float daz = (float)(a.hfov / a.n_beam_az), del = (float)(a.vfov / a.n_beam_el);
+    const float* R = a.poses[p].R32;
+    const float* T = a.poses[p].t32;
     const int n = (int)(0xFFFFFFFFu - (uint32_t)(key & 0xFFFFFFFFull));
     const int bi = b % a.n_beam_az, bj = b / a.n_beam_az;
     float saz, caz, sel, cel;
-    sincosf((float)(-a.hfov / 2) + ((float)bi + 0.5f) * daz, &saz, &caz);
-    sincosf((float)(-a.vfov / 2) + ((float)bj + 0.5f) * del, &sel, &cel);
-    const float r = (float)a.r_min + ((float)n + 0.5f) * (float)a.dr;
+    sincosf(a.az0 + ((float)bi + 0.5f) * a.daz, &saz, &caz);
+    sincosf(a.el0 + ((float)bj + 0.5f) * a.del, &sel, &cel);
+    const float r = a.r_min + ((float)n + 0.5f) * a.dr;
     const float v0 = r * cel * caz, v1 = r * cel * saz, v2 = r * sel;
     sonar_point pt;
-    pt.x = (float)P.R[0] * v0 + (float)P.R[1] * v1 + (float)P.R[2] * v2 + (float)P.t[0];
-    pt.y = (float)P.R[3] * v0 + (float)P.R[4] * v1 + (float)P.R[5] * v2 + (float)P.t[1];
-    pt.z = (float)P.R[6] * v0 + (float)P.R[7] * v1 + (float)P.R[8] * v2 + (float)P.t[2];
+    pt.x = R[0] * v0 + R[1] * v1 + R[2] * v2 + T[0];
+    pt.y = R[3] * v0 + R[4] * v1 + R[5] * v2 + T[1];
+    pt.z = R[6] * v0 + R[7] * v1 + R[8] * v2 + T[2];
     pt.intensity = __uint_as_float((uint32_t)(key >> 32));
     pt.beam = b;
     pt.bin = n;

@@ -206,7 +206,9 @@ struct PeakArgs {
   const unsigned int* ping_max;
   const DevPose* poses;
   int32_t n_pings, n_beam_az, n_beam_el, nr;
-  double hfov, vfov, r_min, dr;
+  // beam and bin grid in FP32, rounded on the host: az0 = -hfov/2, daz = hfov/n_beam_az,
+  // el0, del likewise, r_min and dr
+  float az0, daz, el0, del, r_min, dr;
   int32_t thr_mode;
   float thr;
   sonar_point* cloud;       // [n_pings][cap]

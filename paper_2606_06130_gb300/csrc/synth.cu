@@ -259,28 +259,51 @@ __global__ void k_absmax(const float2* S, int32_t nr, int32_t nr_pad, int32_t M,
   if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<int*>(gain + p), __float_as_int(mx));
 }
 
-__global__ void k_convert(ConvertArgs a) {
-  const int64_t rows = (int64_t)a.n_pings * a.nr;
+// One CTA per range row (ping p, sample n): the row's M complex echoes become the GEMM's
+// 16-bit operand row(s), four elements (two 16-byte loads, one 16-byte store per part)
+// per thread step; rows whose M is not a multiple of 4 take the scalar path.
+__device__ __forceinline__ uint32_t cvt_pair(float x, float y, int mode, float gn, uint32_t* lo) {
+  if (mode == SONAR_FP16) {
+    __half2 h = __floats2half2_rn(x * gn, y * gn);
+    return *reinterpret_cast<uint32_t*>(&h);
+  }
+  __nv_bfloat162 hi = __floats2bfloat162_rn(x, y);
+  if (mode == SONAR_FP32) {
+    const float2 hf = __bfloat1622float2(hi);
+    __nv_bfloat162 l = __floats2bfloat162_rn(x - hf.x, y - hf.y);
+    *lo = *reinterpret_cast<uint32_t*>(&l);
+  }
+  return *reinterpret_cast<uint32_t*>(&hi);
+}
+
+__global__ void __launch_bounds__(256) k_convert(ConvertArgs a) {
+  const int r = blockIdx.x;
+  const int p = r / a.nr, n = r - p * a.nr;
   const int M = a.M;
-  const int64_t total = rows * M;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = i / M;
-    const int m = (int)(i % M);
-    const int p = (int)(r / a.nr), n = (int)(r % a.nr);
-    float2 v = a.S[((int64_t)p * a.nr_pad + kPad + n) * M + m];
-    const int64_t dst = ((int64_t)p * a.nr_x + n) * a.k_pad + 2 * m;
-    if (a.mode == SONAR_FP16) {
-      float gn = a.gain[p];
-      __half2 h = __floats2half2_rn(v.x * gn, v.y * gn);
-      *reinterpret_cast<__half2*>(reinterpret_cast<__half*>(a.x_hi) + dst) = h;
-    } else {
-      __nv_bfloat162 hi = __floats2bfloat162_rn(v.x, v.y);
-      *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(a.x_hi) + dst) = hi;
-      if (a.mode == SONAR_FP32) {
-        float2 hf = __bfloat1622float2(hi);
-        __nv_bfloat162 lo = __floats2bfloat162_rn(v.x - hf.x, v.y - hf.y);
-        *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(a.x_lo) + dst) = lo;
-      }
+  const float2* src = a.S + ((int64_t)p * a.nr_pad + kPad + n) * M;
+  const int64_t dst0 = ((int64_t)p * a.nr_x + n) * a.k_pad;  // 16-bit units
+  uint16_t* xh = reinterpret_cast<uint16_t*>(a.x_hi) + dst0;
+  uint16_t* xl = reinterpret_cast<uint16_t*>(a.x_lo) + dst0;
+  const float gn = a.mode == SONAR_FP16 ? a.gain[p] : 1.0f;
+  if ((M & 3) == 0) {
+    for (int m = threadIdx.x * 4; m < M; m += blockDim.x * 4) {
+      const float4 v0 = __ldg(reinterpret_cast<const float4*>(src + m));
+      const float4 v1 = __ldg(reinterpret_cast<const float4*>(src + m + 2));
+      uint4 h, l = make_uint4(0u, 0u, 0u, 0u);
+      h.x = cvt_pair(v0.x, v0.y, a.mode, gn, &l.x);
+      h.y = cvt_pair(v0.z, v0.w, a.mode, gn, &l.y);
+      h.z = cvt_pair(v1.x, v1.y, a.mode, gn, &l.z);
+      h.w = cvt_pair(v1.z, v1.w, a.mode, gn, &l.w);
+      *reinterpret_cast<uint4*>(xh + 2 * m) = h;
+      if (a.mode == SONAR_FP32) *reinterpret_cast<uint4*>(xl + 2 * m) = l;
+    }
+  } else {
+    for (int m = threadIdx.x; m < M; m += blockDim.x) {
+      const float2 v = src[m];
+      uint32_t l = 0u;
+      const uint32_t h = cvt_pair(v.x, v.y, a.mode, gn, &l);
+      *reinterpret_cast<uint32_t*>(xh + 2 * m) = h;
+      if (a.mode == SONAR_FP32) *reinterpret_cast<uint32_t*>(xl + 2 * m) = l;
     }
   }
 }
@@ -327,7 +350,7 @@ cudaError_t launch_convert(const ConvertArgs& a, int sm_count, cudaStream_t st) 
     k_absmax<<<dim3(sm_count, a.n_pings), 256, 0, st>>>(a.S, a.nr, a.nr_pad, a.M, a.gain);
   }
   if (a.mode == SONAR_FP16) k_gain_pow2<<<(a.n_pings + 63) / 64, 64, 0, st>>>(a.gain, a.n_pings, a.mode);
-  k_convert<<<sm_count * 8, 256, 0, st>>>(a);
+  k_convert<<<a.n_pings * a.nr, 256, 0, st>>>(a);
   return cudaGetLastError();
 }
 
