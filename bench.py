@@ -368,7 +368,7 @@ def run_ours(args, ws, rank, local):
            "gpu_launches": launches,
            "graph_replay": {"value": whole_job_rate(ws, args.steps, g_ms / 1e3), "unit": UNIT,
                             "note": "same steps replayed as one CUDA graph per ping, no stage events"},
-           "e2e": {"value": whole_job_rate(ws, k_e2e, e2e_s), "unit": UNIT, "h2d_bytes_per_step": 144,
+           "e2e": {"value": whole_job_rate(ws, k_e2e, e2e_s), "unit": UNIT, "h2d_bytes_per_step": 192,
                    "d2h_bytes_per_step": int(env.numel() * 4 + nb * 24 + 8), "steps": k_e2e,
                    "path": "sonar_ping_batch (default graph replay) with pinned host env and cloud"},
            "clocks": clk,

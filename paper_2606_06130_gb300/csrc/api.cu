@@ -193,6 +193,12 @@ int validate(sonar_ctx* ctx, const sonar_params* p, const sonar_ssp* ssp) {
 
 // Rotation matrix of a ping's unit quaternion (w, x, y, z), normalised first, and its
 // position (also rounded to FP32 for the FP32 traversal).
+// x as an FP32 pair: hi = RN(x), lo = RN(x - hi).
+float2 df_pair(double x) {
+  const float hi = (float)x;
+  return make_float2(hi, (float)(x - (double)hi));
+}
+
 DevPose dev_pose(const sonar_pose& ps) {
   const double* q = ps.q;
   const double qn = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
@@ -206,6 +212,8 @@ DevPose dev_pose(const sonar_pose& ps) {
     P.t32[k] = (float)ps.t[k];
   }
   for (int k = 0; k < 9; ++k) P.R32[k] = (float)P.R[k];
+  for (int k = 0; k < 3; ++k) P.t_lo[k] = (float)(P.t[k] - (double)P.t32[k]);
+  for (int k = 0; k < 9; ++k) P.R_lo[k] = (float)(P.R[k] - (double)P.R32[k]);
   return P;
 }
 
@@ -313,7 +321,7 @@ int ensure_tables(sonar_ctx* ctx, const sonar_params* p, const Derived& d) {
     dfree(ctx->ray_dirs32);
     dfree(ctx->row_domega);
     CU(cudaMalloc(&ctx->ray_dirs, sizeof(double) * 3 * d.n_subrays));
-    CU(cudaMalloc(&ctx->ray_dirs32, sizeof(float) * 3 * d.n_subrays));
+    CU(cudaMalloc(&ctx->ray_dirs32, sizeof(float) * 6 * d.n_subrays));
     CU(cudaMalloc(&ctx->row_domega, sizeof(float) * p->n_ray_el));
     CU(launch_ray_table(ctx->ray_dirs, ctx->ray_dirs32, ctx->row_domega, p->n_ray_az, p->n_ray_el, p->n_sub,
                         p->hfov_rad, p->vfov_rad, seed32(p->seed), ctx->stream));
@@ -497,6 +505,7 @@ int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, cons
   ta.poses = ctx->poses;
   ta.ray_dirs = ctx->ray_dirs;
   ta.ray_dirs32 = ctx->ray_dirs32;
+  ta.ray_dirs_lo = ctx->ray_dirs32 + 3 * d.n_subrays;
   ta.row_domega = ctx->row_domega;
   ta.n_pings = P;
   ta.n_ray_az = p->n_ray_az;
@@ -526,6 +535,13 @@ int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, cons
   ta.t0_dt = d.t0 * ta.inv_dt;
   ta.hw = d.hw;
   ta.f0 = p->f0_hz;
+  ta.L_stop_df = df_pair(ta.L_stop);
+  ta.surface_z_df = df_pair(isnan(p->surface_z) ? 0.0 : p->surface_z);
+  ta.two_inv_c0_df = df_pair(ta.two_inv_c0);
+  ta.f0_df = df_pair(ta.f0);
+  ta.inv_dt_df = df_pair(ta.inv_dt);
+  ta.t0_dt_df = df_pair(ta.t0_dt);
+  ta.hw_df = df_pair(ta.hw);
   ta.nr_pad = d.nr_pad;
   ta.n_routes = d.n_routes;
   ta.hits = ctx->hits;
@@ -921,6 +937,7 @@ int sonar_scene_upload(sonar_ctx* ctx, const float* verts, int64_t n_verts, cons
   ctx->sc.tri_mu = ctx->tri_mu;
   ctx->sc.tri_flags = ctx->tri_flags;
   ctx->sc.tri_plane = ctx->tri_plane;
+  ctx->sc.tri_plane_df = reinterpret_cast<const float4*>(ctx->tri_plane + n_tris);
   ctx->sc.tri_inv_n = ctx->tri_inv_n;
   ctx->sc.nodes = ctx->nodes;
   ctx->sc.n_tris = (int32_t)n_tris;

@@ -141,6 +141,12 @@ __global__ void k_leaves(const float* V, const int32_t* T, const float* mu, cons
   const double nz = __dsub_rn(__dmul_rn(e1x, e2y), __dmul_rn(e1y, e2x));
   const double d0 = __dadd_rn(__dadd_rn(__dmul_rn(nx, (double)a.x), __dmul_rn(ny, (double)a.y)), __dmul_rn(nz, (double)a.z));
   tri_plane[k] = make_double4_32a(nx, ny, nz, d0);
+  // FP32 pairs of the plane after the n FP64 planes: hi = RN(x), lo = RN(x - hi)
+  float4* df = reinterpret_cast<float4*>(tri_plane + n);
+  const float hx = (float)nx, hy = (float)ny, hz = (float)nz, hw = (float)d0;
+  df[2 * k] = make_float4(hx, hy, hz, hw);
+  df[2 * k + 1] = make_float4((float)(nx - (double)hx), (float)(ny - (double)hy), (float)(nz - (double)hz),
+                              (float)(d0 - (double)hw));
   const double nn = __dadd_rn(__dadd_rn(__dmul_rn(nx, nx), __dmul_rn(ny, ny)), __dmul_rn(nz, nz));
   tri_inv_n[k] = nn > 0.0 ? (float)(1.0 / sqrt(nn)) : 0.f;
 }
@@ -210,7 +216,7 @@ cudaError_t build_bvh(const float* V, const int32_t* T, const float* mu, const u
   CK(cudaMalloc(tri_prim, sizeof(int32_t) * n));
   CK(cudaMalloc(tri_mu, sizeof(float) * n));
   CK(cudaMalloc(tri_flags, n));
-  CK(cudaMalloc(tri_plane, sizeof(double4_32a) * n));
+  CK(cudaMalloc(tri_plane, (sizeof(double4_32a) + 2 * sizeof(float4)) * n));  // FP64 planes, then FP32 pairs
   CK(cudaMalloc(tri_inv_n, sizeof(float) * n));
   CK(cudaMalloc(nodes, sizeof(BvhNode) * n_int));
   float* bb;

@@ -55,6 +55,7 @@ struct DevScene {
   const float* tri_mu;     // leaf order
   const uint8_t* tri_flags;// leaf order
   const double4_32a* tri_plane;// leaf order: n = (b - a) x (c - a) in FP64 (unnormalised), n . a
+  const float4* tri_plane_df;  // leaf order, [2 n_tris]: the same as FP32 pairs, hi then lo per leaf
   const float* tri_inv_n;  // leaf order: 1 / |n|
   const BvhNode* nodes;
   int32_t n_tris;
@@ -71,6 +72,8 @@ struct DevPose {
   double t[3];
   float t32[3];  // the position rounded to FP32, for the FP32 traversal
   float R32[9];  // the rotation rounded to FP32, for the FP32 traversal direction
+  float t_lo[3]; // t - t32 and R - R32 rounded to FP32: (t32, t_lo) and (R32, R_lo) are
+  float R_lo[9]; // the FP32 pairs (hi + lo) of the straight-ray path
 };
 
 // Everything the trace kernels need, passed by value.
@@ -79,6 +82,7 @@ struct TraceArgs {
   const DevPose* poses;
   const double* ray_dirs;   // [n_subrays][3] sonar-frame sub-ray directions
   const float* ray_dirs32;  // the same rounded to FP32
+  const float* ray_dirs_lo; // dirs - dirs32 rounded to FP32 (the FP32 pair's low part)
   const float* row_domega;  // [n_ray_el] sub-ray solid angle per elevation row
   int32_t n_pings, n_ray_az, n_ray_el, n_sub, n_subrays;
   int32_t max_bounces, has_surface, curved;
@@ -93,6 +97,8 @@ struct TraceArgs {
   float L_stop32, surface_z32;   // the same rounded to FP32, for FP32 pre-checks
   double t0, inv_dt, hw, f0;     // sample-grid mapping of delays
   double t0_dt;                  // t0 / dt
+  // the same constants as FP32 pairs (hi, lo) for the straight-ray path
+  float2 L_stop_df, surface_z_df, two_inv_c0_df, f0_df, inv_dt_df, t0_dt_df, hw_df;
   int32_t nr_pad;
   int32_t n_routes;              // point-scatterer routes per point
   HitRec* hits;
@@ -128,6 +134,7 @@ cudaError_t build_bvh(const float* d_verts, const int32_t* d_tris, const float* 
                       const uint8_t* d_flags, int32_t n_tris, float4** tri32, float** triv,
                       int32_t** tri_prim, float** tri_mu, uint8_t** tri_flags, double4_32a** tri_plane,
                       float** tri_inv_n, BvhNode** nodes, int32_t* root, cudaStream_t st);
+// dirs32 holds 6 n floats: the directions rounded to FP32, then their FP32 residuals.
 cudaError_t launch_ray_table(double* dirs, float* dirs32, float* row_domega, int32_t n_ray_az, int32_t n_ray_el,
                              int32_t n_sub, double hfov, double vfov, uint32_t seed32,
                              cudaStream_t st);

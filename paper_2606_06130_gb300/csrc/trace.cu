@@ -37,9 +37,6 @@ __device__ __forceinline__ D3 cross(D3 a, D3 b) {
 }
 // contracted forms for positions and distances
 __device__ __forceinline__ double dotf(D3 a, D3 b) { return fma(a.z, b.z, fma(a.y, b.y, a.x * b.x)); }
-__device__ __forceinline__ D3 axpyf(D3 p, double t, D3 d) {
-  return d3(fma(t, d.x, p.x), fma(t, d.y, p.y), fma(t, d.z, p.z));
-}
 __device__ __forceinline__ D3 rot(const double* R, D3 v) {
   return d3(fma(R[2], v.z, fma(R[1], v.y, R[0] * v.x)), fma(R[5], v.z, fma(R[4], v.y, R[3] * v.x)),
             fma(R[8], v.z, fma(R[7], v.y, R[6] * v.x)));
@@ -72,6 +69,70 @@ __device__ __forceinline__ double drsqrt_nr(double s) {
 
 __device__ __forceinline__ D3 tri_vert(const float* v, int k) {
   return d3((double)v[3 * k], (double)v[3 * k + 1], (double)v[3 * k + 2]);
+}
+
+// ----------------------------------------------------------------- FP32 pairs
+// A value as the unevaluated sum hi + lo of two FP32 numbers, |lo| <= ulp(hi) / 2, about
+// 48 significant bits: Dekker's double-length arithmetic (Dekker 1971), with Knuth's
+// error-free sum and the FMA product error. FP32 issues at many times the FP64 rate on
+// this part, so the straight-ray path carries its geometry, delays and phases in pairs:
+// ~2^-46 relative per operation against the 1e-12 the delays need. The explicitly rounded
+// operations keep the compiler from contracting the error terms away.
+struct F2 {
+  float hi, lo;
+};
+struct DF3 {
+  F2 x, y, z;
+};
+__device__ __forceinline__ F2 f2(float a) { return F2{a, 0.f}; }
+__device__ __forceinline__ F2 f2(float2 v) { return F2{v.x, v.y}; }
+__device__ __forceinline__ F2 quick_two_sum(float a, float b) {  // |a| >= |b| or a == 0
+  const float s = __fadd_rn(a, b);
+  return F2{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ F2 two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
+  return F2{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ F2 operator+(F2 x, F2 y) {
+  F2 s = two_sum(x.hi, y.hi);
+  const F2 t = two_sum(x.lo, y.lo);
+  s = quick_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
+  return quick_two_sum(s.hi, __fadd_rn(s.lo, t.lo));
+}
+__device__ __forceinline__ F2 operator-(F2 x) { return F2{-x.hi, -x.lo}; }
+__device__ __forceinline__ F2 operator-(F2 x, F2 y) { return x + (-y); }
+__device__ __forceinline__ F2 operator*(F2 x, F2 y) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  float e = __fmaf_rn(x.hi, y.hi, -p);
+  e = __fmaf_rn(x.hi, y.lo, e);
+  e = __fmaf_rn(x.lo, y.hi, e);
+  return quick_two_sum(p, e);
+}
+// x / y by long division: three quotient digits from one FP32 reciprocal of y.hi, each
+// taken from the remainder the previous ones leave.
+__device__ __forceinline__ F2 operator/(F2 x, F2 y) {
+  const float r = __frcp_rn(y.hi);
+  const float q1 = __fmul_rn(x.hi, r);
+  F2 rem = x - f2(q1) * y;
+  const float q2 = __fmul_rn(rem.hi, r);
+  rem = rem - f2(q2) * y;
+  const float q3 = __fmul_rn(rem.hi, r);
+  return quick_two_sum(q1, q2) + f2(q3);
+}
+// pairs are normalised (hi = RN(hi + lo)), so these compare values
+__device__ __forceinline__ bool operator<(F2 a, F2 b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+__device__ __forceinline__ bool operator==(F2 a, F2 b) { return a.hi == b.hi && a.lo == b.lo; }
+__device__ __forceinline__ F2 dot(const DF3& a, const DF3& b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ DF3 axpy(const DF3& p, F2 t, const DF3& d) {
+  return DF3{p.x + t * d.x, p.y + t * d.y, p.z + t * d.z};
+}
+// FP64 views, for the rare exact triangle tests and the debug delays
+__device__ __forceinline__ double to_d(F2 v) { return (double)v.hi + (double)v.lo; }
+__device__ __forceinline__ D3 to_d3(const DF3& v) { return d3(to_d(v.x), to_d(v.y), to_d(v.z)); }
+__device__ __forceinline__ F2 f2_of(double x) {
+  const float hi = (float)x;
+  return F2{hi, (float)(x - (double)hi)};
 }
 
 // FP64 two-sided ray/triangle test (Moller-Trumbore), inclusive edges. One reciprocal
@@ -116,6 +177,17 @@ __device__ D3 tri_normal64(const DevScene& sc, int leaf) {
   return d3(dm(n.x, il), dm(n.y, il), dm(n.z, il));
 }
 
+__device__ __forceinline__ DF3 plane_n_df(const DevScene& sc, int leaf, F2& w) {
+  const float4 h = __ldg(&sc.tri_plane_df[2 * leaf]), l = __ldg(&sc.tri_plane_df[2 * leaf + 1]);
+  w = F2{h.w, l.w};
+  return DF3{F2{h.x, l.x}, F2{h.y, l.y}, F2{h.z, l.z}};
+}
+__device__ __forceinline__ float kinc32(const DevScene& sc, int leaf, const DF3& d) {
+  F2 w;
+  const DF3 n = plane_n_df(sc, leaf, w);
+  return fabsf(dot(d, n).hi) * __ldg(&sc.tri_inv_n[leaf]);
+}
+
 // ----------------------------------------------------------------- traversal
 struct Ray32 {
   float ox, oy, oz, ix, iy, iz, dx, dy, dz;
@@ -130,11 +202,13 @@ __device__ __forceinline__ void slab(float lox, float hix, float loy, float hiy,
   tf = fminf(fminf(fmaxf(x0, x1), fmaxf(y0, y1)), fminf(fmaxf(z0, z1), thi));
 }
 
-struct Hit {
-  double t;
+template <class R>
+struct HitT {
+  R t;
   int prim;  // original id, -1 none
   int leaf;
 };
+using Hit = HitT<double>;
 
 // FP64 distance to the triangle's plane: (n . a - n . o) / (n . d).
 __device__ __forceinline__ double plane_t(const DevScene& sc, int leaf, D3 o, D3 d) {
@@ -142,32 +216,65 @@ __device__ __forceinline__ double plane_t(const DevScene& sc, int leaf, D3 o, D3
   const D3 n = d3(P.x, P.y, P.z);
   return ddiv_nr(P.w - dotf(n, o), dotf(n, d));
 }
+// The same from the plane's FP32 pairs.
+__device__ __forceinline__ F2 plane_t(const DevScene& sc, int leaf, const DF3& o, const DF3& d) {
+  F2 w;
+  const DF3 n = plane_n_df(sc, leaf, w);
+  return (w - dot(n, o)) / dot(n, d);
+}
+
+// Generic pieces of the traversal over the two precisions of its exact parts.
+__device__ __forceinline__ float to_f(double x) { return (float)x; }
+__device__ __forceinline__ float to_f(F2 x) { return x.hi; }
+__device__ __forceinline__ void lead32(const D3& v, float* f) { f[0] = (float)v.x; f[1] = (float)v.y; f[2] = (float)v.z; }
+__device__ __forceinline__ void lead32(const DF3& v, float* f) { f[0] = v.x.hi; f[1] = v.y.hi; f[2] = v.z.hi; }
+__device__ __forceinline__ void r_inf(double& x) { x = INFINITY; }
+__device__ __forceinline__ void r_inf(F2& x) { x = F2{INFINITY, 0.f}; }
+// FP64 ray/triangle decision with its distance inside (tmin, tmax]
+__device__ bool tri_test64(const float* tv, D3 o, D3 d, double& t);
+__device__ __forceinline__ bool tri_exact(const float* tv, const D3& o, const D3& d, double tmin, double tmax,
+                                          double& t) {
+  return tri_test64(tv, o, d, t) && t > tmin && t <= tmax;
+}
+__device__ __forceinline__ bool tri_exact(const float* tv, const DF3& o, const DF3& d, F2 tmin, F2 tmax, F2& t) {
+  double t64;
+  if (!tri_test64(tv, to_d3(o), to_d3(d), t64)) return false;
+  t = f2_of(t64);
+  return tmin < t && !(tmax < t);
+}
 
 // Nearest triangle with FP64 distance in (tmin, tmax], excluding `exclude` (original
 // id), ties to the lowest id. The distance of the returned hit is FP64.
 // o32, d32: the origin and the direction in FP32 when the caller has them (nullptr:
 // converted here). An FP32 direction from FP32 operands differs from the FP64 one by
 // ~1e-7, far inside the traversal's slack.
-__device__ Hit closest_hit(const DevScene& sc, D3 o, D3 d, double tmin, double tmax, int exclude, int* err,
-                           const float* o32 = nullptr, const float* d32 = nullptr) {
-  Hit best = {INFINITY, -1, -1};
+template <class V, class R>
+__device__ HitT<R> closest_hit(const DevScene& sc, const V& o, const V& d, R tmin, R tmax, int exclude, int* err,
+                               const float* o32 = nullptr, const float* d32 = nullptr) {
+  HitT<R> best;
+  r_inf(best.t);
+  best.prim = -1;
+  best.leaf = -1;
   bool best_exact = true;
   float best_t32 = INFINITY;
   if (sc.n_tris == 0) return best;
   Ray32 r;
+  float f[3];
   if (o32) {
     r.ox = o32[0]; r.oy = o32[1]; r.oz = o32[2];
   } else {
-    r.ox = (float)o.x; r.oy = (float)o.y; r.oz = (float)o.z;
+    lead32(o, f);
+    r.ox = f[0]; r.oy = f[1]; r.oz = f[2];
   }
   if (d32) {
     r.dx = d32[0]; r.dy = d32[1]; r.dz = d32[2];
   } else {
-    r.dx = (float)d.x; r.dy = (float)d.y; r.dz = (float)d.z;
+    lead32(d, f);
+    r.dx = f[0]; r.dy = f[1]; r.dz = f[2];
   }
   r.ix = __frcp_rn(r.dx); r.iy = __frcp_rn(r.dy); r.iz = __frcp_rn(r.dz);
-  const float tmax_f = (float)tmax * (1.0f + 1e-6f) + 1e-4f;
-  const float tmin32 = (float)tmin, tmax32 = (float)tmax;  // the loop stays in FP32
+  const float tmax_f = to_f(tmax) * (1.0f + 1e-6f) + 1e-4f;
+  const float tmin32 = to_f(tmin), tmax32 = to_f(tmax);  // the loop stays in FP32
   float tcull = tmax_f;
   int stack[kMaxStack];
   int sp = 0;
@@ -217,10 +324,11 @@ __device__ Hit closest_hit(const DevScene& sc, D3 o, D3 d, double tmin, double t
       // only its distance is needed, and only when it competes with another hit.
       const float tslack = 1e-4f + 1e-5f * fabsf(t32);
       const bool definite = in32 && t32 >= tmin32 + tslack && t32 <= tmax32 - tslack;
-      double t64 = INFINITY;
+      R t64;
+      r_inf(t64);
       bool exact = false;
       if (!definite) {
-        if (!(tri_test64(sc.triv + 9 * leaf, o, d, t64) && t64 > tmin && t64 <= tmax)) continue;
+        if (!tri_exact(sc.triv + 9 * leaf, o, d, tmin, tmax, t64)) continue;
         exact = true;
       }
       bool take;
@@ -241,7 +349,7 @@ __device__ Hit closest_hit(const DevScene& sc, D3 o, D3 d, double tmin, double t
         best.leaf = leaf;
         best.t = t64;
         best_exact = exact;
-        best_t32 = exact ? (float)t64 : t32;
+        best_t32 = exact ? to_f(t64) : t32;
         tcull = fminf(tcull, best_t32 * (1.0f + 1e-5f) + 2e-4f);
       }
     }
@@ -315,10 +423,52 @@ __device__ void emit(const TraceArgs& A, int ping, double tau, float amp, double
 }
 
 // Speckle phase of a hit in cycles: a 24-bit uniform fraction from the hash (exact in FP64).
+// emit() for the straight-ray path, from a two-way delay held as an FP32 pair: the
+// phase psi - f0 tau with f0 tau's integer part removed exactly, the sample position
+// q = tau / dt - t0 / dt and its first tap floor(q - hw) + 1, all in pairs.
+__device__ void emit_df(const TraceArgs& A, int ping, F2 tau, float amp, float psi_cyc, float uy, float uz,
+                        int prim, uint32_t key) {
+  unsigned long long slot = warp_reserve(A.n_hits);
+  if ((int64_t)slot >= A.hit_cap) { atomicOr(A.err, kErrCapacity); return; }
+  const F2 y = f2(psi_cyc) - f2(A.f0_df) * tau;
+  const float k = rintf(y.hi);
+  const float cyc = __fadd_rn(__fsub_rn(y.hi, k), y.lo);  // y.hi - k is exact
+  const F2 q = tau * f2(A.inv_dt_df) - f2(A.t0_dt_df);
+  const F2 z = q - f2(A.hw_df);
+  float fl = floorf(z.hi);
+  if (fl == z.hi && z.lo < 0.f) fl -= 1.f;  // an integral hi with a negative lo
+  const float nf = fminf(fmaxf(fl + 1.f, -1e9f), 1e9f);
+  HitRec h;
+  const int nfi = (int)nf;
+  const bool in_rows = nfi >= -kPad && nfi < A.nr_pad - kPad;
+  h.nglob = in_rows ? ping * A.nr_pad + nfi + kPad : -1;
+  h.u0 = __fsub_rn(__fsub_rn(nf, q.hi), q.lo);  // nf - q.hi is exact (Sterbenz)
+  {
+    const unsigned grp = __match_any_sync(__activemask(), h.nglob);
+    if (h.nglob >= 0 && (int)(threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(&A.bin_counts[h.nglob], __popc(grp));
+  }
+  float s, c;
+  sincospif(2.0f * cyc, &s, &c);
+  h.cr = amp * c;
+  h.ci = amp * s;
+  h.uy = uy;
+  h.uz = uz;
+  h.prim = prim;
+  h.key = key;
+  A.hits[slot] = h;
+  if (A.dbg_tau) A.dbg_tau[slot] = to_d(tau);
+}
+
 __device__ __forceinline__ double speckle(const TraceArgs& A, uint32_t ray, uint32_t sub, uint32_t bounce) {
   uint32_t x = ray, y = sub, z = 1u + bounce, w = A.seed32;
   pcg4d(x, y, z, w);
   return u24(x);
+}
+// the same in FP32 (a 24-bit fraction, exact in FP32)
+__device__ __forceinline__ float speckle32(const TraceArgs& A, uint32_t ray, uint32_t sub, uint32_t bounce) {
+  uint32_t x = ray, y = sub, z = 1u + bounce, w = A.seed32;
+  pcg4d(x, y, z, w);
+  return (float)(x >> 8) * (1.0f / 16777216.0f);
 }
 
 // Lambertian amplitude Gamma^2 sqrt(mu cos(k) dOmega) / L exp(-2 alpha L), in FP32: the
@@ -432,54 +582,59 @@ __device__ void route_curved(const TraceArgs& A, int ping, D3 o, D3 d0, D3 us, u
   }
 }
 
-__device__ void route_straight(const TraceArgs& A, int ping, D3 o, const float* o32, D3 d0, const float* d32,
-                               float uy, float uz, uint32_t ray, uint32_t sub, float dOmega, uint32_t keybase) {
-  D3 pos = o, dir = d0;
-  double L = 0.0;
+__device__ void route_straight(const TraceArgs& A, int ping, DF3 o, const float* o32, DF3 d0, float uy, float uz,
+                               uint32_t ray, uint32_t sub, float dOmega, uint32_t keybase) {
+  // kEpsHit as an FP32 pair (folded at compile time)
+  const F2 eps = F2{(float)kEpsHit, (float)(kEpsHit - (double)(float)kEpsHit)};
+  DF3 pos = o, dir = d0;
+  F2 L = f2(0.f);
   float gam = 1.0f;
   int bounce = 0, prev = -1;
   for (int iter = 0; iter < 8; ++iter) {
-    const double tlim = A.L_stop - L;
-    if (!(tlim > 0)) break;
-    Hit hq = closest_hit(A.sc, pos, dir, kEpsHit, tlim, prev, A.err, iter == 0 ? o32 : nullptr,
-                         iter == 0 ? d32 : nullptr);
-    double ts = INFINITY;
+    const F2 tlim = f2(A.L_stop_df) - L;
+    if (!(tlim.hi > 0.f)) break;
+    HitT<F2> hq = closest_hit(A.sc, pos, dir, eps, tlim, prev, A.err, iter == 0 ? o32 : nullptr);
+    F2 ts = F2{INFINITY, 0.f};
     // from the origin, an FP32 look first: the plane clearly behind or clearly out of
-    // reach skips the FP64 test
-    bool surf_maybe = A.has_surface && prev != -2 && dir.z != 0.0;
+    // reach skips the exact test
+    bool surf_maybe = A.has_surface && prev != -2 && dir.z.hi != 0.f;
     if (surf_maybe && iter == 0) {
-      const float num32 = A.surface_z32 - o32[2], dz32 = d32[2];  // tlim = L_stop at the origin
+      const float num32 = A.surface_z32 - o32[2], dz32 = dir.z.hi;  // tlim = L_stop at the origin
       const bool clear = fabsf(num32) > 1e-3f && fabsf(dz32) > 1e-5f;
       if (clear && (num32 * dz32 < 0.f || fabsf(num32) > A.L_stop32 * fabsf(dz32) * 1.001f + 1e-3f)) surf_maybe = false;
     }
     if (surf_maybe) {
-      // divide only when the plane lies ahead within reach
-      const double num = A.surface_z - pos.z;
-      if (num * dir.z > 0.0 && fabs(num) <= tlim * fabs(dir.z) * (1.0 + 1e-12)) {
-        const double t = fabs(dir.z) > 1e-30 ? ddiv_nr(num, dir.z) : dd(num, dir.z);
-        if (t > kEpsHit && t <= tlim) ts = t;
+      // divide only when the plane lies ahead within reach (a loose FP32 bound; the
+      // exact test follows)
+      const F2 num = f2(A.surface_z_df) - pos.z;
+      if (num.hi * dir.z.hi > 0.f && fabsf(num.hi) <= tlim.hi * fabsf(dir.z.hi) * (1.0f + 1e-5f)) {
+        const F2 t = num / dir.z;
+        if (eps < t && !(tlim < t)) ts = t;
       }
     }
-    if (hq.prim < 0 && ts == INFINITY) break;
+    if (hq.prim < 0 && ts.hi == INFINITY) break;
     if (ts < hq.t) {
       if (bounce >= A.max_bounces) break;
-      pos = axpyf(pos, ts, dir);
-      L += ts;
+      pos = axpy(pos, ts, dir);
+      L = L + ts;
       dir.z = -dir.z;
       gam *= (float)A.r_surface;
       bounce++;
       prev = -2;
       continue;
     }
-    L += hq.t;
+    L = L + hq.t;
     const float kinc = kinc32(A.sc, hq.leaf, dir);
-    const float amp = lambert(A, gam, A.sc.tri_mu[hq.leaf], kinc, dOmega, (float)L);
-    emit(A, ping, L * A.two_inv_c0, amp, speckle(A, ray, sub, bounce), uy, uz, hq.prim, keybase | (uint32_t)bounce);
+    const float amp = lambert(A, gam, A.sc.tri_mu[hq.leaf], kinc, dOmega, L.hi);
+    emit_df(A, ping, L * f2(A.two_inv_c0_df), amp, speckle32(A, ray, sub, bounce), uy, uz, hq.prim,
+            keybase | (uint32_t)bounce);
     if ((A.sc.tri_flags[hq.leaf] & 1) && bounce < A.max_bounces) {
-      pos = axpyf(pos, hq.t, dir);
-      const D3 n = tri_normal64(A.sc, hq.leaf);  // FP64 only where the route continues
-      const double k = 2.0 * dotf(dir, n);
-      dir = d3(fma(-k, n.x, dir.x), fma(-k, n.y, dir.y), fma(-k, n.z, dir.z));
+      pos = axpy(pos, hq.t, dir);
+      // specular reflection off the triangle's plane: d - 2 (d . n) / (n . n) n
+      F2 w;
+      const DF3 n = plane_n_df(A.sc, hq.leaf, w);
+      const F2 k = (dot(dir, n) + dot(dir, n)) / dot(n, n);
+      dir = DF3{dir.x - k * n.x, dir.y - k * n.y, dir.z - k * n.z};
       gam *= (float)A.r_seabed;
       bounce++;
       prev = hq.prim;
@@ -489,6 +644,7 @@ __device__ void route_straight(const TraceArgs& A, int ping, D3 o, const float* 
   }
 }
 
+template <bool CURVED>
 __global__ void __launch_bounds__(128, 4) k_trace(TraceArgs A) {
   const int64_t total = (int64_t)A.n_pings * A.n_subrays;
   for (int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gid < total; gid += (int64_t)gridDim.x * blockDim.x) {
@@ -497,19 +653,25 @@ __global__ void __launch_bounds__(128, 4) k_trace(TraceArgs A) {
     uint32_t ray = (uint32_t)(sr / A.n_sub), sub = (uint32_t)(sr % A.n_sub);
     int row = (int)(ray / A.n_ray_az);
     const DevPose& P = A.poses[ping];
-    const D3 us = d3(A.ray_dirs[3 * sr], A.ray_dirs[3 * sr + 1], A.ray_dirs[3 * sr + 2]);
-    const D3 dw = rot(P.R, us);
-    const D3 o = d3(P.t[0], P.t[1], P.t[2]);
     const float dOmega = A.row_domega[row];
     const uint32_t keybase = ((uint32_t)sr) << 2;
-    if (A.curved) route_curved(A, ping, o, dw, us, ray, sub, dOmega, keybase);
-    else {
-      const float* u32 = A.ray_dirs32 + 3 * sr;
-      const float ux = u32[0], uy = u32[1], uz = u32[2];
-      const float d32[3] = {fmaf(P.R32[2], uz, fmaf(P.R32[1], uy, P.R32[0] * ux)),
-                            fmaf(P.R32[5], uz, fmaf(P.R32[4], uy, P.R32[3] * ux)),
-                            fmaf(P.R32[8], uz, fmaf(P.R32[7], uy, P.R32[6] * ux))};
-      route_straight(A, ping, o, P.t32, dw, d32, uy, uz, ray, sub, dOmega, keybase);
+    if (CURVED) {
+      const D3 us = d3(A.ray_dirs[3 * sr], A.ray_dirs[3 * sr + 1], A.ray_dirs[3 * sr + 2]);
+      const D3 dw = rot(P.R, us);
+      const D3 o = d3(P.t[0], P.t[1], P.t[2]);
+      route_curved(A, ping, o, dw, us, ray, sub, dOmega, keybase);
+    } else {
+      // world direction R us and origin t as FP32 pairs
+      const float* uh = A.ray_dirs32 + 3 * sr;
+      const float* ul = A.ray_dirs_lo + 3 * sr;
+      const F2 u[3] = {F2{uh[0], ul[0]}, F2{uh[1], ul[1]}, F2{uh[2], ul[2]}};
+      F2 dw[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+        dw[i] = F2{P.R32[3 * i], P.R_lo[3 * i]} * u[0] + F2{P.R32[3 * i + 1], P.R_lo[3 * i + 1]} * u[1] +
+                F2{P.R32[3 * i + 2], P.R_lo[3 * i + 2]} * u[2];
+      const DF3 o = DF3{F2{P.t32[0], P.t_lo[0]}, F2{P.t32[1], P.t_lo[1]}, F2{P.t32[2], P.t_lo[2]}};
+      route_straight(A, ping, o, P.t32, DF3{dw[0], dw[1], dw[2]}, uh[1], uh[2], ray, sub, dOmega, keybase);
     }
   }
 }
@@ -679,7 +841,11 @@ __global__ void k_ray_table(double* dirs, float* dirs32, float* row_domega, int 
   dirs[3 * gid] = cos(el) * cos(az);
   dirs[3 * gid + 1] = cos(el) * sin(az);
   dirs[3 * gid + 2] = sin(el);
-  for (int k = 0; k < 3; ++k) dirs32[3 * gid + k] = (float)dirs[3 * gid + k];
+  for (int k = 0; k < 3; ++k) {
+    const float hi = (float)dirs[3 * gid + k];
+    dirs32[3 * gid + k] = hi;
+    dirs32[3 * n + 3 * gid + k] = (float)(dirs[3 * gid + k] - (double)hi);
+  }
 }
 
 }  // namespace
@@ -699,7 +865,8 @@ cudaError_t launch_trace(const TraceArgs& a, int sm_count, cudaStream_t st) {
   int64_t cap = (int64_t)sm_count * 16;
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
-  k_trace<<<(unsigned)blocks, 128, 0, st>>>(a);
+  if (a.curved) k_trace<true><<<(unsigned)blocks, 128, 0, st>>>(a);
+  else k_trace<false><<<(unsigned)blocks, 128, 0, st>>>(a);
   return cudaGetLastError();
 }
 
