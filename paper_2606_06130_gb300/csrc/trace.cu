@@ -644,8 +644,10 @@ __device__ void route_straight(const TraceArgs& A, int ping, DF3 o, const float*
   }
 }
 
+// Traversal is latency-bound (dependent node loads), so residency pays: the straight-ray
+// kernel fits five CTAs of 128 threads per SM (96 registers), the curved one four.
 template <bool CURVED>
-__global__ void __launch_bounds__(128, 4) k_trace(TraceArgs A) {
+__global__ void __launch_bounds__(128, CURVED ? 4 : 5) k_trace(TraceArgs A) {
   const int64_t total = (int64_t)A.n_pings * A.n_subrays;
   for (int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gid < total; gid += (int64_t)gridDim.x * blockDim.x) {
     int ping = (int)(gid / A.n_subrays);
