@@ -422,7 +422,7 @@ def sample_errors(torch, s, ref):
 def stage_rooflines(mean_stage, params, stats, precision, pk):
     """Achieved rate of every stage against its bound: tensor stages in TFLOP/s of the
     measured BF16 peaks (burst and sustained), memory stages in GB/s of the measured HBM
-    copy rate, the traversal in sub-rays/s (FP64- and latency-bound: no single peak)."""
+    copy rate, the traversal in sub-rays/s (latency-bound: no single peak)."""
     M = params["nx"] * params["ny"]
     nb = params["n_beam_az"] * params["n_beam_el"]
     nr = params["n_range"]
@@ -446,7 +446,7 @@ def stage_rooflines(mean_stage, params, stats, precision, pk):
     synth_flop = H * M * (8 * stats["taps"] + 6)
     gemm_flop = 8.0 * nb * M * nr
     out = {
-        "trace": {"bound": "fp64 pipe and latency", "achieved": sub_rays / (mean_stage["trace"] / 1e3) / 1e6,
+        "trace": {"bound": "latency (dependent BVH node loads)", "achieved": sub_rays / (mean_stage["trace"] / 1e3) / 1e6,
                   "unit": "M sub-rays/s", "hits_per_s": H / (mean_stage["trace"] / 1e3), "peak": None, "frac": None},
         "bin": mem("bin", 2 * 32 * H, "32-byte hit records read and written once"),
         "synth": tensor("synth", synth_flop, synth_flop),
