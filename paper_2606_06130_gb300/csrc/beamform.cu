@@ -167,8 +167,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant_
         const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + c * 32);
         TMEM_LD_32(taddr, v);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        // envelope of 16 beams, then their per-beam maxima over the warp's 32 samples as
-        // 16 independent butterfly reductions (latency overlapped), one atomic per lane
+        // envelope of 16 beams, then their per-beam maxima over the warp's 32 samples by a
+        // reduce-scatter: each round a lane keeps half of its beams and trades the other
+        // half with its partner (8 + 4 + 2 + 1 exchanges), until lanes 2j and 2j + 1 hold
+        // beam j; one atomic per beam
         const int beam0 = nb * (BN / 2) + c * 16;
         unsigned long long key[16];
 #pragma unroll
@@ -184,18 +186,19 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant_
           if (elig && vb) pmax = fmaxf(pmax, e);
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
+        for (int h = 8; h >= 1; h >>= 1) {  // h beams kept; partner lane differs in bit 2h
+          const bool up = (lane & (2 * h)) != 0;
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const unsigned long long other = __shfl_xor_sync(0xffffffffu, key[j], o);
-            key[j] = other > key[j] ? other : key[j];
+          for (int i = 0; i < h; ++i) {
+            const unsigned long long give = up ? key[i] : key[h + i];
+            const unsigned long long keep = up ? key[h + i] : key[i];
+            const unsigned long long got = __shfl_xor_sync(0xffffffffu, give, 2 * h);
+            key[i] = got > keep ? got : keep;
           }
         }
-        unsigned long long mine = 0ull;
-#pragma unroll
-        for (int j = 0; j < 16; ++j)
-          if (lane == j) mine = key[j];
-        if (lane < 16 && mine != 0ull) atomicMax(&keys_p[beam0 + lane], mine);
+        const unsigned long long other = __shfl_xor_sync(0xffffffffu, key[0], 1);
+        const unsigned long long mine = other > key[0] ? other : key[0];
+        if ((lane & 1) == 0 && mine != 0ull) atomicMax(&keys_p[beam0 + (lane >> 1)], mine);
       }
       tc_fence_before();
       __syncwarp();
