@@ -81,6 +81,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant_
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
+  // the operands come from the conversion kernel
+  pdl_wait();
 
   if (warp == 0) {
     // ------------------------------------------------------------- TMA producer
@@ -273,6 +275,7 @@ __device__ __forceinline__ bool peak_kept(unsigned long long key, float thr) {
 
 __global__ void __launch_bounds__(1024) k_peaks(PeakArgs a) {
   __shared__ int s_warp[32];
+  pdl_wait();
   __shared__ int s_before;
   const int p = blockIdx.y, chunk = blockIdx.x, t = threadIdx.x, lane = t & 31, wid = t >> 5;
   const int Nb = a.n_beam_az * a.n_beam_el;
@@ -364,26 +367,28 @@ cudaError_t prepare_gemm() {
 }
 
 template <int BN>
-void launch_bn(const GemmArgs& a, int grid, cudaStream_t st) {
-  k_gemm<BN><<<grid, kGemmThreads, gemm_smem<BN>(), st>>>(a, make_idesc(a.f16 ? 0 : 1, BM, BN));
+cudaError_t launch_bn(const GemmArgs& a, int grid, cudaStream_t st) {
+  return launch_pdl(k_gemm<BN>, dim3(grid), dim3(kGemmThreads), gemm_smem<BN>(), st, a, make_idesc(a.f16 ? 0 : 1, BM, BN));
 }
 
 cudaError_t launch_gemm(const GemmArgs& a, int sm_count, cudaStream_t st) {
   const int n_tiles = a.tiles_m * a.tiles_n;
   const int grid = n_tiles < sm_count ? n_tiles : sm_count;
+  cudaError_t e;
   switch (a.tile_n) {
-    case 256: launch_bn<256>(a, grid, st); break;
-    case 224: launch_bn<224>(a, grid, st); break;
-    case 192: launch_bn<192>(a, grid, st); break;
-    case 128: launch_bn<128>(a, grid, st); break;
+    case 256: e = launch_bn<256>(a, grid, st); break;
+    case 224: e = launch_bn<224>(a, grid, st); break;
+    case 192: e = launch_bn<192>(a, grid, st); break;
+    case 128: e = launch_bn<128>(a, grid, st); break;
     default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_peaks(const PeakArgs& a, cudaStream_t st) {
   const int nb = a.n_beam_az * a.n_beam_el;
-  k_peaks<<<dim3((unsigned)ceil_div(nb, 1024), a.n_pings), 1024, 0, st>>>(a);
+  cudaError_t e = launch_pdl(k_peaks, dim3((unsigned)ceil_div(nb, 1024), a.n_pings), dim3(1024), 0, st, a);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

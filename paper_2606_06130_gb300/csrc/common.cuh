@@ -9,6 +9,8 @@
 
 #include "sonar.h"
 
+#include <utility>
+
 #if defined(__CUDA_ARCH__) && (__CUDA_ARCH__ != 1030)
 #error "this library is written for sm_103a only"
 #endif
@@ -111,6 +113,30 @@ struct TraceArgs {
 
 // ------------------------------------------------------------------ small helpers
 __host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Programmatic dependent launch: the per-ping kernels are launched so that one may start
+// (its prologue: barrier set-up, tensor-memory allocation, table loads) while the
+// previous one drains its last CTAs. Every such kernel calls pdl_wait() with all its
+// threads before it reads anything an earlier kernel of the ping wrote; the wait returns
+// once the previous kernel has completed and its writes are visible, and because every
+// kernel waits before it can finish, completion is ordered along the whole chain.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // pcg4d (Jarzynski & Olano, JCGT 2020), 32-bit.
 __host__ __device__ inline void pcg4d(uint32_t& x, uint32_t& y, uint32_t& z, uint32_t& w) {

@@ -15,6 +15,7 @@ namespace {
 // Exclusive scan of counts (single CTA of 1024 threads); offsets[n_bins] = total.
 __global__ void __launch_bounds__(1024) k_scan(const int32_t* counts, int32_t n_bins, int32_t* offsets, int32_t* cursor) {
   __shared__ int32_t part[1024];
+  pdl_wait();
   const int t = threadIdx.x;
   const int per = (n_bins + 1023) / 1024;
   const int b0 = t * per, b1 = min(b0 + per, n_bins);
@@ -43,6 +44,7 @@ __global__ void __launch_bounds__(1024) k_scan(const int32_t* counts, int32_t n_
 // move as two 16-byte vectors.
 __global__ void k_scatter(const HitRec* hits, const unsigned long long* n_hits, int32_t n_bins, int32_t* cursor,
                           HitRec* sorted, int32_t* sorted_n) {
+  pdl_wait();
   const int64_t n = (int64_t)*n_hits;
   const int lane = threadIdx.x & 31;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -87,6 +89,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_synth(SynthArgs a, const int32_
   __shared__ float2 s_g[kSub][WT];
   __shared__ float2 s_ey[kSub][kMaxAxis];
   __shared__ float2 s_ez[kSub][kMaxAxis];
+  pdl_wait();
 
   const int nx = a.nx, ny = a.ny, M = nx * ny;
   const int64_t H = *total_ptr;
@@ -277,6 +280,7 @@ __device__ __forceinline__ uint32_t cvt_pair(float x, float y, int mode, float g
 }
 
 __global__ void __launch_bounds__(256) k_convert(ConvertArgs a) {
+  pdl_wait();
   const int r = blockIdx.x;
   const int p = r / a.nr, n = r - p * a.nr;
   const int M = a.M;
@@ -323,17 +327,21 @@ __global__ void k_gain_pow2(float* gain, int n, int mode) {
 
 cudaError_t launch_bin(const HitRec* hits, const unsigned long long* n_hits, int32_t n_bins, int32_t* counts,
                        int32_t* offsets, HitRec* sorted, int32_t* sorted_n, int sm_count, cudaStream_t st) {
-  k_scan<<<1, 1024, 0, st>>>(counts, n_bins, offsets, counts);
+  cudaError_t e = launch_pdl(k_scan, dim3(1), dim3(1024), 0, st, (const int32_t*)counts, n_bins, offsets, counts);
+  if (e != cudaSuccess) return e;
   // counts now doubles as the scatter cursor
-  k_scatter<<<sm_count * 8, 256, 0, st>>>(hits, n_hits, n_bins, counts, sorted, sorted_n);
+  e = launch_pdl(k_scatter, dim3(sm_count * 8), dim3(256), 0, st, hits, n_hits, n_bins, counts, sorted, sorted_n);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
 cudaError_t launch_synth(const SynthArgs& a, int sm_count, cudaStream_t st) {
   const int32_t* total = a.n_valid;  // offsets[n_bins] of the binning step
-  if (a.taps <= 8) k_synth<8><<<sm_count, kThreads, 0, st>>>(a, total);
-  else if (a.taps <= 12) k_synth<12><<<sm_count, kThreads, 0, st>>>(a, total);
-  else k_synth<16><<<sm_count, kThreads, 0, st>>>(a, total);
+  cudaError_t e;
+  if (a.taps <= 8) e = launch_pdl(k_synth<8>, dim3(sm_count), dim3(kThreads), 0, st, a, total);
+  else if (a.taps <= 12) e = launch_pdl(k_synth<12>, dim3(sm_count), dim3(kThreads), 0, st, a, total);
+  else e = launch_pdl(k_synth<16>, dim3(sm_count), dim3(kThreads), 0, st, a, total);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
@@ -350,7 +358,8 @@ cudaError_t launch_convert(const ConvertArgs& a, int sm_count, cudaStream_t st) 
     k_absmax<<<dim3(sm_count, a.n_pings), 256, 0, st>>>(a.S, a.nr, a.nr_pad, a.M, a.gain);
   }
   if (a.mode == SONAR_FP16) k_gain_pow2<<<(a.n_pings + 63) / 64, 64, 0, st>>>(a.gain, a.n_pings, a.mode);
-  k_convert<<<a.n_pings * a.nr, 256, 0, st>>>(a);
+  cudaError_t ce = launch_pdl(k_convert, dim3(a.n_pings * a.nr), dim3(256), 0, st, a);
+  if (ce != cudaSuccess) return ce;
   return cudaGetLastError();
 }
 

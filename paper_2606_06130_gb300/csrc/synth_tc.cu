@@ -351,8 +351,6 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_
   const TileRows<NP / 32> tr{5 - lL2};           // T = NP / L2 rows per tile
   const int T = tr.T();
   const int W = a.taps;
-  const int64_t Hn = *a.n_valid;
-  const int64_t h0 = Hn * blockIdx.x / gridDim.x, h1 = Hn * (blockIdx.x + 1) / gridDim.x;
   const bool fp32_form = a.n_pass == 3;
 
   for (int i = threadIdx.x; i < kRTabS + 5; i += blockDim.x) s_rtab[i] = a.rtab_s[i];
@@ -372,6 +370,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
+  // the hits come from the binning kernels
+  pdl_wait();
+  const int64_t Hn = *a.n_valid;
+  const int64_t h0 = Hn * blockIdx.x / gridDim.x, h1 = Hn * (blockIdx.x + 1) / gridDim.x;
 
   if (warp == 0) {
     // ------------------------------------------------------------- MMA issuer
@@ -644,8 +646,6 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tc(SynthArgs a, uint32_
   const int T = tr.T();
   const int W = a.taps;
   const int n_cols = 2 * ny;
-  const int64_t Hn = *a.n_valid;
-  const int64_t h0 = Hn * blockIdx.x / gridDim.x, h1 = Hn * (blockIdx.x + 1) / gridDim.x;
   const bool fp32_form = a.n_pass == 3;
 
   for (int i = threadIdx.x; i < kRTabS + 5; i += blockDim.x) s_rtab[i] = a.rtab_s[i];
@@ -662,6 +662,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tc(SynthArgs a, uint32_
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
+  pdl_wait();
+  const int64_t Hn = *a.n_valid;
+  const int64_t h0 = Hn * blockIdx.x / gridDim.x, h1 = Hn * (blockIdx.x + 1) / gridDim.x;
 
   if (warp == 0) {
     // ------------------------------------------------------------- MMA issuer
@@ -888,15 +891,18 @@ cudaError_t set_attr() {
 }
 
 template <int WT>
-void launch_one(const SynthArgs& a, int zs_np, int sm_count, cudaStream_t st) {
+cudaError_t launch_one(const SynthArgs& a, int zs_np, int sm_count, cudaStream_t st) {
   if (zs_np == 32)
-    k_synth_tz<WT, 32><<<sm_count, kThreadsTC, tz_smem_bytes<WT, 32>(), st>>>(a, make_idesc(1, 128, 64));
+    return launch_pdl(k_synth_tz<WT, 32>, dim3(sm_count), dim3(kThreadsTC), tz_smem_bytes<WT, 32>(), st, a,
+               make_idesc(1, 128, 64));
   else if (zs_np == 64)
-    k_synth_tz<WT, 64><<<sm_count, kThreadsTC, tz_smem_bytes<WT, 64>(), st>>>(a, make_idesc(1, 128, 128));
+    return launch_pdl(k_synth_tz<WT, 64>, dim3(sm_count), dim3(kThreadsTC), tz_smem_bytes<WT, 64>(), st, a,
+               make_idesc(1, 128, 128));
   else if (zs_np == 96)
-    k_synth_tz<WT, 96><<<sm_count, kThreadsTC, tz_smem_bytes<WT, 96>(), st>>>(a, make_idesc(1, 128, 192));
-  else
-    k_synth_tc<WT><<<sm_count, kThreadsTC, tc_smem_bytes<WT>(), st>>>(a, make_idesc(1, 128, 2 * a.ny));
+    return launch_pdl(k_synth_tz<WT, 96>, dim3(sm_count), dim3(kThreadsTC), tz_smem_bytes<WT, 96>(), st, a,
+               make_idesc(1, 128, 192));
+  return launch_pdl(k_synth_tc<WT>, dim3(sm_count), dim3(kThreadsTC), tc_smem_bytes<WT>(), st, a,
+               make_idesc(1, 128, 2 * a.ny));
 }
 
 }  // namespace
@@ -917,10 +923,11 @@ cudaError_t prepare_synth_tc() {
 
 cudaError_t launch_synth_tc(const SynthArgs& a, int want_pairs, int sm_count, cudaStream_t st) {
   const int zs_np = zs_pairs(a.nx, a.ny, a.taps, want_pairs);
-  if (a.taps <= 8) launch_one<8>(a, zs_np, sm_count, st);
-  else if (a.taps <= 12) launch_one<12>(a, zs_np, sm_count, st);
-  else launch_one<16>(a, zs_np, sm_count, st);
-  return cudaGetLastError();
+  cudaError_t e;
+  if (a.taps <= 8) e = launch_one<8>(a, zs_np, sm_count, st);
+  else if (a.taps <= 12) e = launch_one<12>(a, zs_np, sm_count, st);
+  else e = launch_one<16>(a, zs_np, sm_count, st);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace sonar

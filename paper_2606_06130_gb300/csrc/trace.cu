@@ -648,6 +648,7 @@ __device__ void route_straight(const TraceArgs& A, int ping, DF3 o, const float*
 // kernel fits five CTAs of 128 threads per SM (96 registers), the curved one four.
 template <bool CURVED>
 __global__ void __launch_bounds__(128, CURVED ? 4 : 5) k_trace(TraceArgs A) {
+  pdl_wait();
   const int64_t total = (int64_t)A.n_pings * A.n_subrays;
   for (int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gid < total; gid += (int64_t)gridDim.x * blockDim.x) {
     int ping = (int)(gid / A.n_subrays);
@@ -706,6 +707,7 @@ __device__ double4_32a plane_of(const TraceArgs& A, int idx, double& gam) {
 // direct eigen-arc in a linear profile. Routes are plane sequences without immediate
 // repeats, enumerated by length then lexicographically.
 __global__ void k_points(TraceArgs A) {
+  pdl_wait();
   int64_t total = (int64_t)A.n_pings * A.sc.n_points * A.n_routes;
   int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (gid >= total) return;
@@ -867,15 +869,17 @@ cudaError_t launch_trace(const TraceArgs& a, int sm_count, cudaStream_t st) {
   int64_t cap = (int64_t)sm_count * 16;
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
-  if (a.curved) k_trace<true><<<(unsigned)blocks, 128, 0, st>>>(a);
-  else k_trace<false><<<(unsigned)blocks, 128, 0, st>>>(a);
+  cudaError_t e = a.curved ? launch_pdl(k_trace<true>, dim3((unsigned)blocks), dim3(128), 0, st, a)
+                           : launch_pdl(k_trace<false>, dim3((unsigned)blocks), dim3(128), 0, st, a);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
 cudaError_t launch_points(const TraceArgs& a, cudaStream_t st) {
   int64_t total = (int64_t)a.n_pings * a.sc.n_points * a.n_routes;
   if (total == 0) return cudaSuccess;
-  k_points<<<(unsigned)ceil_div(total, 64), 64, 0, st>>>(a);
+  cudaError_t e = launch_pdl(k_points, dim3((unsigned)ceil_div(total, 64)), dim3(64), 0, st, a);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
