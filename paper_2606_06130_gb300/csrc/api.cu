@@ -16,6 +16,25 @@ using namespace sonar;
 
 namespace {
 
+// Zeroes, in one launch, every buffer a call accumulates into: the element echoes S
+// (16-byte stores), the per-row hit histogram, the per-beam peak keys and ping maxima,
+// the hit counter and the error bits.
+__global__ void k_clear(float2* S, int64_t n_s, int32_t* counts, int32_t n_bins, unsigned long long* keys,
+                        int64_t n_keys, unsigned* pmax, int n_p, unsigned long long* n_hits, int* err) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  float4* S4 = reinterpret_cast<float4*>(S);  // cudaMalloc alignment
+  for (int64_t i = t; i < n_s / 2; i += stride) S4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  if ((n_s & 1) && t == 0) S[n_s - 1] = make_float2(0.f, 0.f);
+  for (int64_t i = t; i < n_bins; i += stride) counts[i] = 0;
+  for (int64_t i = t; i < n_keys; i += stride) keys[i] = 0ull;
+  for (int64_t i = t; i < n_p; i += stride) pmax[i] = 0u;
+  if (t == 0) {
+    *n_hits = 0ull;
+    *err = 0;
+  }
+}
+
 // Beamforming N tiles the GEMM is built for; 0 picks per call the one that minimises
 // waves x width (waves = output tiles / SMs, rounded up): the last wave of a few large
 // tiles can leave most SMs idle.
@@ -117,6 +136,8 @@ struct sonar_ctx {
   long long* n_cloud_dev = nullptr;
   long long* n_cloud_host = nullptr;  // pinned
   unsigned long long* counters_host = nullptr;  // pinned: hits of the last call, error bits
+  long long* n_cloud_map = nullptr;             // device mappings of the two above
+  unsigned long long* counters_map = nullptr;
   int* err_dev = nullptr;
   int64_t ws_hits = 0, ws_bins = 0, ws_s = 0, ws_x = 0;
 
@@ -389,6 +410,7 @@ int ensure_workspace(sonar_ctx* ctx, int P, const Derived& d) {
     dfree(ctx->poses); dfree(ctx->gain); dfree(ctx->pmax); dfree(ctx->n_cloud_dev);
     CU(cudaMallocHost(&ctx->pose_host, sizeof(DevPose) * P));
     CU(cudaMallocHost(&ctx->n_cloud_host, sizeof(long long) * P));
+    CU(cudaHostGetDevicePointer((void**)&ctx->n_cloud_map, ctx->n_cloud_host, 0));
     CU(cudaMalloc(&ctx->poses, sizeof(DevPose) * P));
     CU(cudaMalloc(&ctx->gain, sizeof(float) * P));
     CU(cudaMalloc(&ctx->pmax, sizeof(unsigned) * P));
@@ -491,14 +513,12 @@ int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, cons
   // the poses the host has just written into the pinned staging record
   CU(cudaMemcpyAsync(ctx->poses, ctx->pose_host, sizeof(DevPose) * P, cudaMemcpyHostToDevice, st));
   mark(0);
-  // every buffer that starts at zero is cleared up front, so the kernels run back to back
+  // every buffer that starts at zero is cleared up front, in one launch, so the kernels
+  // run back to back
   const int32_t n_bins = P * d.nr_pad;
-  CU(cudaMemsetAsync(ctx->n_hits, 0, sizeof(unsigned long long), st));
-  CU(cudaMemsetAsync(ctx->err_dev, 0, sizeof(int), st));
-  CU(cudaMemsetAsync(ctx->counts, 0, sizeof(int32_t) * n_bins, st));
-  CU(cudaMemsetAsync(ctx->S, 0, sizeof(float2) * ctx->s_elems, st));
-  CU(cudaMemsetAsync(ctx->keys, 0, sizeof(unsigned long long) * (size_t)P * d.nb, st));
-  CU(cudaMemsetAsync(ctx->pmax, 0, sizeof(unsigned) * P, st));
+  k_clear<<<4 * ctx->sm_count, 256, 0, st>>>(ctx->S, ctx->s_elems, ctx->counts, n_bins, ctx->keys,
+                                             (int64_t)P * d.nb, ctx->pmax, P, ctx->n_hits, ctx->err_dev);
+  CU(cudaGetLastError());
   TraceArgs ta;
   memset(&ta, 0, sizeof(ta));
   ta.sc = ctx->sc;
@@ -641,6 +661,10 @@ int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, cons
   pa.cloud = o.cloud;
   pa.cap = o.cap;
   pa.n_cloud = ctx->n_cloud_dev;
+  pa.n_cloud_host = ctx->n_cloud_map;
+  pa.counters_host = ctx->counters_map;
+  pa.n_hits = ctx->n_hits;
+  pa.err = ctx->err_dev;
   CU(launch_peaks(pa, st));
   mark(6);
   // results back to the host: staged outputs, per-ping point counts, hit count, error bits
@@ -648,9 +672,7 @@ int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, cons
     CU(cudaMemcpyAsync(o.env_host, o.env, sizeof(float) * o.env_elems, cudaMemcpyDeviceToHost, st));
   if (o.cloud_host && o.cap > 0)
     CU(cudaMemcpyAsync(o.cloud_host, o.cloud, sizeof(sonar_point) * P * o.cap, cudaMemcpyDeviceToHost, st));
-  CU(cudaMemcpyAsync(ctx->n_cloud_host, ctx->n_cloud_dev, sizeof(long long) * P, cudaMemcpyDeviceToHost, st));
-  CU(cudaMemcpyAsync(ctx->counters_host, ctx->n_hits, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
-  CU(cudaMemcpyAsync(ctx->counters_host + 1, ctx->err_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
+  // (point counts, hit count and error bits reach the host through k_peaks' mapped writes)
   return SONAR_OK;
 }
 
@@ -705,7 +727,10 @@ int run(sonar_ctx* ctx, const sonar_pose* poses, int P, const sonar_params* p, c
     o.cloud = ctx->cloud_stage;
     o.cloud_host = cloud;
   }
-  if (!ctx->counters_host) CU(cudaMallocHost(&ctx->counters_host, 2 * sizeof(unsigned long long)));
+  if (!ctx->counters_host) {
+    CU(cudaMallocHost(&ctx->counters_host, 2 * sizeof(unsigned long long)));
+    CU(cudaHostGetDevicePointer((void**)&ctx->counters_map, ctx->counters_host, 0));
+  }
   ctx->counters_host[1] = 0;
 
   // the graph's first node copies these to the device

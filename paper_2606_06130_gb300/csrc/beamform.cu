@@ -343,7 +343,15 @@ __global__ void __launch_bounds__(1024) k_peaks(PeakArgs a) {
     a.cloud[(size_t)p * a.cap + pos] = pt;
   }
   // the last chunk knows the ping's total
-  if (chunk == gridDim.x - 1 && t == 1023) a.n_cloud[p] = pos + (keep ? 1 : 0);
+  if (chunk == gridDim.x - 1 && t == 1023) {
+    a.n_cloud[p] = pos + (keep ? 1 : 0);
+    a.n_cloud_host[p] = pos + (keep ? 1 : 0);
+  }
+  // every earlier kernel of the call has completed (the dependent-launch chain)
+  if (p == 0 && chunk == 0 && t == 0) {
+    a.counters_host[0] = *a.n_hits;
+    a.counters_host[1] = (unsigned long long)(unsigned)*a.err;
+  }
 }
 
 }  // namespace

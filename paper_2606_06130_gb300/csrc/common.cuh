@@ -247,6 +247,12 @@ struct PeakArgs {
   sonar_point* cloud;       // [n_pings][cap]
   int64_t cap;
   long long* n_cloud;       // [n_pings]
+  // the call's results for the host, written through the device mapping of pinned host
+  // words (no copy after the kernel): points per ping, then hit count and error bits
+  long long* n_cloud_host;
+  unsigned long long* counters_host;   // [2]
+  const unsigned long long* n_hits;
+  const int* err;
 };
 cudaError_t launch_peaks(const PeakArgs& a, cudaStream_t st);
 }  // namespace sonar
