@@ -54,6 +54,8 @@ def lib():
         vp, i64, i32, d = C.c_void_p, C.c_int64, C.c_int32, C.c_double
         _lib.orc_trace.argtypes = [vp, vp, vp, vp, vp, vp, i32, C.c_int, vp]
         _lib.orc_synth.argtypes = [vp, vp, vp, i64, vp]
+        _lib.orc_raw.argtypes = [vp, vp, i32, i32, vp, i64, vp]
+        _lib.orc_pulse.argtypes = [d, d, d, vp, vp]
         _lib.orc_beamform.argtypes = [vp, d, vp, vp, i64, vp, i64, vp]
         _lib.orc_envelope.argtypes = [vp, vp, vp, i64, i64, vp]
         _lib.orc_peaks.argtypes = [vp, vp, vp, vp, vp, vp, vp]
@@ -190,6 +192,54 @@ def peaks(params: dict, pose: dict, E: np.ndarray) -> dict:
     q = np.ascontiguousarray(pose["q"], np.float64)
     n = lib().orc_peaks(C.byref(make_params(params)), _ptr(t), _ptr(q), _ptr(E), _ptr(pts), _ptr(pb), _ptr(pn))
     return {"xyzi": pts[:n], "beam": pb[:n], "bin": pn[:n]}
+
+
+def raw_echoes(params: dict, hits: dict, U: int, ns) -> np.ndarray:
+    """Raw element series r_m(t_n + s dt / U), s = 0..U-1, for the requested samples n (any
+    integers, also outside [0, n_range)): complex128 [U, len(ns), M]. The echo before
+    pulse compression (Sec. II.B time series)."""
+    ns = np.ascontiguousarray(ns, np.int32)
+    M = params["nx"] * params["ny"]
+    hs, keep = _hits_struct(hits)
+    out = np.zeros((U, len(ns), M, 2), np.float64)
+    for s in range(U):
+        lib().orc_raw(C.byref(make_params(params)), C.byref(hs), U, s, _ptr(ns), len(ns), _ptr(out[s]))
+    return out[..., 0] + 1j * out[..., 1]
+
+
+def matched_filter(params: dict, hits: dict, U: int, ns) -> np.ndarray:
+    """Matched filter of the raw series (Sec. II.B): y_m(t_n) = (dt / (U E)) sum over the raw
+    samples t_i = t_j + s dt / U of r_m(t_i) conj(p(t_i - t_n)), E = 3T/8 the pulse energy.
+    A rectangle-rule quadrature of the correlation integral that defines R, so y tends to
+    the compressed echoes s_m[n] as U grows. complex128 [len(ns), M]."""
+    ns = np.asarray(ns, np.int64)
+    T, B = params["pulse"], params["bw"]
+    dt = 2.0 * (params["r_max"] - params["r_min"]) / params["n_range"] / hits["c_ref"]
+    D = int(math.ceil(T / 2 / dt)) + 1
+    d = np.arange(-D, D + 1)
+    rows = np.unique((ns[:, None] + d[None, :]).ravel())
+    raw = raw_echoes(params, hits, U, rows)
+    idx = {int(r): i for i, r in enumerate(rows)}
+    E = 3.0 * T / 8.0
+    y = np.zeros((len(ns), params["nx"] * params["ny"]), np.complex128)
+    for s in range(U):
+        h = np.conj(pulse(d * dt + s * dt / U, T, B))
+        for a, n in enumerate(ns):
+            for k, dd in enumerate(d):
+                if h[k] != 0:
+                    y[a] += raw[s, idx[int(n + dd)]] * h[k]
+    return y * (dt / (U * E))
+
+
+def pulse(t, T: float, B: float) -> np.ndarray:
+    """The transmitted pulse p(t) (Hann-windowed linear chirp, |t| <= T/2)."""
+    t = np.atleast_1d(np.asarray(t, np.float64))
+    out = np.zeros(t.shape, np.complex128)
+    re, im = C.c_double(), C.c_double()
+    for i, x in enumerate(t.ravel()):
+        lib().orc_pulse(float(x), T, B, C.byref(re), C.byref(im))
+        out.ravel()[i] = re.value + 1j * im.value
+    return out
 
 
 def pulse_acf(u, T: float, B: float) -> np.ndarray:

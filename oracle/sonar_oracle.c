@@ -104,6 +104,15 @@ void orc_pulse_acf(double u, double T, double B, double* re, double* im) {
   *im = cimag(r);
 }
 
+/* The transmitted pulse itself (its raw, uncompressed echo): p(t) = w(t) exp(j pi (B/T)
+   t^2) for |t| <= T/2, zero outside, w the Hann window above. */
+void orc_pulse(double t, double T, double B, double* re, double* im) {
+  if (!(fabs(t) <= T / 2)) { *re = 0; *im = 0; return; }
+  const double w = 0.5 * (1.0 + cos(TWO_PI * t / T)), ph = PI * (B / T) * t * t;
+  *re = w * cos(ph);
+  *im = w * sin(ph);
+}
+
 /* ------------------------------------------------------------------ geometry */
 static void tri_verts(const orc_scene* sc, int32_t prim, double a[3], double b[3], double c[3]) {
   const int32_t* t = sc->tris + 3 * (int64_t)prim;
@@ -837,10 +846,14 @@ int orc_trace(const orc_scene* sc, const orc_params* p, const double pose_t[3], 
    s_m[n] = sum_k c_k R(t_n - tau_k) exp(j k_a u_k . p_m), k_a = 2 pi f0 / c_ref,
    t_n = 2 (r_min + (n + 1/2) dr) / c_ref, elements p_m = (0, y_m, z_m) on a centred
    nx x ny grid of the given pitch, m = my * nx + mx. */
-void orc_synth(const orc_params* p, const orc_hits* h, const int32_t* ns, int64_t n_ns, double* s_out) {
+/* raw != 0: the raw (uncompressed) element series instead, r_m(t) = sum_k c_k p(t - tau_k)
+   exp(j k_a u_k . p_m), sampled at t_n + shift. */
+static void synth_core(const orc_params* p, const orc_hits* h, const int32_t* ns, int64_t n_ns, int raw,
+                       double shift, double* s_out) {
   const int32_t nx = p->nx, ny = p->ny, M = nx * ny;
   const double c_ref = h->c_ref, dr = (p->r_max - p->r_min) / p->n_range;
   const double ka = TWO_PI * p->f0 / c_ref;
+  const double support = raw ? p->pulse / 2 : p->pulse;  /* |u| inside: p on [-T/2, T/2], R on (-T, T) */
   memset(s_out, 0, sizeof(double) * 2 * (size_t)M * (size_t)n_ns);
   /* per hit, the requested samples inside its pulse window and c_k R(t_n - tau_k) */
   int64_t* cnt = (int64_t*)calloc((size_t)h->n + 1, sizeof(int64_t));
@@ -848,8 +861,8 @@ void orc_synth(const orc_params* p, const orc_hits* h, const int32_t* ns, int64_
   for (int64_t k = 0; k < h->n; ++k) {
     int64_t c = 0;
     for (int64_t i = 0; i < n_ns; ++i) {
-      double tn = 2.0 * (p->r_min + (ns[i] + 0.5) * dr) / c_ref;
-      if (fabs(tn - h->tau[k]) < p->pulse) ++c;
+      double tn = 2.0 * (p->r_min + (ns[i] + 0.5) * dr) / c_ref + shift;
+      if (raw ? fabs(tn - h->tau[k]) <= support : fabs(tn - h->tau[k]) < support) ++c;
     }
     cnt[k + 1] = c;
   }
@@ -862,11 +875,14 @@ void orc_synth(const orc_params* p, const orc_hits* h, const int32_t* ns, int64_
     int64_t w = cnt[k];
     cplx ck = h->cr[k] + I * h->ci[k];
     for (int64_t i = 0; i < n_ns; ++i) {
-      double tn = 2.0 * (p->r_min + (ns[i] + 0.5) * dr) / c_ref;
+      double tn = 2.0 * (p->r_min + (ns[i] + 0.5) * dr) / c_ref + shift;
       double u = tn - h->tau[k];
-      if (fabs(u) < p->pulse) {
+      if (raw ? fabs(u) <= support : fabs(u) < support) {
         double re, im;
-        orc_pulse_acf(u, p->pulse, p->bw, &re, &im);
+        if (raw)
+          orc_pulse(u, p->pulse, p->bw, &re, &im);
+        else
+          orc_pulse_acf(u, p->pulse, p->bw, &re, &im);
         pi[w] = i;
         pg[w] = ck * (re + I * im);
         ++w;
@@ -890,6 +906,18 @@ void orc_synth(const orc_params* p, const orc_hits* h, const int32_t* ns, int64_
   free(cnt);
   free(pi);
   free(pg);
+}
+
+void orc_synth(const orc_params* p, const orc_hits* h, const int32_t* ns, int64_t n_ns, double* s_out) {
+  synth_core(p, h, ns, n_ns, 0, 0.0, s_out);
+}
+
+/* Raw element series (the uncompressed echo before a matched filter): r_m at
+   t_n + s dt / U, dt = 2 dr / c_ref, for the requested samples n. */
+void orc_raw(const orc_params* p, const orc_hits* h, int32_t U, int32_t s, const int32_t* ns, int64_t n_ns,
+             double* s_out) {
+  const double dt = 2.0 * (p->r_max - p->r_min) / p->n_range / h->c_ref;
+  synth_core(p, h, ns, n_ns, 1, s * dt / U, s_out);
 }
 
 /* Beam directions (Sec. III Eq. 2-3, cell-centred): az_i = -HFOV/2 + (i+1/2) HFOV/N_az,

@@ -62,6 +62,8 @@ typedef struct {
 
 /* Normalised autocorrelation R(u) of the Hann-windowed LFM pulse. */
 void orc_pulse_acf(double u, double pulse, double bw, double* re, double* im);
+/* The transmitted pulse p(t): Hann-windowed linear chirp over |t| <= T/2. */
+void orc_pulse(double t, double pulse, double bw, double* re, double* im);
 
 /* 32-bit pcg4d hash (Jarzynski & Olano 2020); v is updated in place. */
 void orc_pcg4d(uint32_t v[4]);
@@ -78,6 +80,9 @@ int orc_trace(const orc_scene* sc, const orc_params* p, const double pose_t[3],
               int32_t n_ssp, int use_bvh, orc_hits* out);
 
 /* Element echoes s_m[n] for samples ns[0..n_ns): out[n_ns][M][2]. */
+/* Raw element series at t_n + s dt / U (the echo before pulse compression). */
+void orc_raw(const orc_params* p, const orc_hits* h, int32_t U, int32_t s, const int32_t* ns, int64_t n_ns,
+             double* s_out);
 void orc_synth(const orc_params* p, const orc_hits* h, const int32_t* ns, int64_t n_ns,
                double* s_out);
 
