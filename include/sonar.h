@@ -160,6 +160,15 @@ SONAR_API const char* sonar_last_error(const sonar_ctx* ctx);
    fit the array and pulse falls back to the default choice. Any other value:
    SONAR_E_ARG. */
 #define SONAR_OPT_SYNTH 5
+/* SONAR_OPT_RAW: 0 (default) synthesises the element echoes already pulse-compressed,
+   through the pulse autocorrelation R (Sec. II.B). U = 1..8 instead synthesises the raw
+   element time series, the echo of the transmitted chirp p itself, at U samples per
+   range cell (t_n + s dt / U, s < U: a sampling rate of U / dt >= B), and compresses it
+   with an explicit matched filter (correlation with p) before beamforming. The result
+   equals the compressed echoes to the quadrature error of the correlation sum (about
+   2e-4 relative at U = 4, 4e-5 at U = 6). Costs U synthesis passes. Needs a pulse longer
+   than two range samples (SONAR_E_UNSUPPORTED otherwise); any other value: SONAR_E_ARG. */
+#define SONAR_OPT_RAW 6
 SONAR_API int sonar_set_option(sonar_ctx* ctx, int32_t option, int64_t value);
 
 /* ---------------------------------------------------------------- scene */
@@ -201,6 +210,10 @@ SONAR_API int sonar_get_hits(sonar_ctx* ctx, sonar_hit* host_out, int64_t cap, i
 /* Element echoes s_m[n] of the last call (requires SONAR_OPT_DEBUG), host
    [n_pings][n_range][ny*nx][2] f32 (m = my * nx + mx). */
 SONAR_API int sonar_get_echoes(sonar_ctx* ctx, float* host_out, int64_t cap_floats);
+/* Raw element series of the last call, phase s of SONAR_OPT_RAW = U (requires
+   SONAR_OPT_DEBUG and a ping with U > 0): r_m(t_n + s dt / U), host
+   [n_pings][n_range][ny*nx][2] f32. SONAR_E_ARG for a phase outside [0, U). */
+SONAR_API int sonar_get_raw(sonar_ctx* ctx, int32_t phase, float* host_out, int64_t cap_floats);
 SONAR_API int sonar_get_stats(const sonar_ctx* ctx, sonar_stats* out);
 
 /* ---------------------------------------------------------------- allocation-free cloud */

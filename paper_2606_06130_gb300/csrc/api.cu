@@ -19,13 +19,17 @@ namespace {
 // Zeroes, in one launch, every buffer a call accumulates into: the element echoes S
 // (16-byte stores), the per-row hit histogram, the per-beam peak keys and ping maxima,
 // the hit counter and the error bits.
-__global__ void k_clear(float2* S, int64_t n_s, int32_t* counts, int32_t n_bins, unsigned long long* keys,
-                        int64_t n_keys, unsigned* pmax, int n_p, unsigned long long* n_hits, int* err) {
+__global__ void k_clear(float2* S, int64_t n_s, float2* S2, int64_t n_s2, int32_t* counts, int32_t n_bins,
+                        unsigned long long* keys, int64_t n_keys, unsigned* pmax, int n_p, unsigned long long* n_hits,
+                        int* err) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   float4* S4 = reinterpret_cast<float4*>(S);  // cudaMalloc alignment
   for (int64_t i = t; i < n_s / 2; i += stride) S4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
   if ((n_s & 1) && t == 0) S[n_s - 1] = make_float2(0.f, 0.f);
+  float4* R4 = reinterpret_cast<float4*>(S2);  // the raw series' phases (S2 may be null: n_s2 = 0)
+  for (int64_t i = t; i < n_s2 / 2; i += stride) R4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  if ((n_s2 & 1) && t == 0) S2[n_s2 - 1] = make_float2(0.f, 0.f);
   for (int64_t i = t; i < n_bins; i += stride) counts[i] = 0;
   for (int64_t i = t; i < n_keys; i += stride) keys[i] = 0ull;
   for (int64_t i = t; i < n_p; i += stride) pmax[i] = 0u;
@@ -78,6 +82,10 @@ struct sonar_ctx {
   std::string err;
   bool debug = false, timing = false, use_graph = true;
   int tile_opt = 0;
+  int raw_u = 0;      // 0: compressed synthesis; U > 0: raw series at U samples per cell + matched filter
+  int last_raw_u = 0;
+  float2* S_raw = nullptr;  // raw series: U phases of s_elems
+  int64_t ws_raw = 0;
   int synth_opt = 0;  // 0: tensor-core synthesis where supported, 1: FP32 SIMT synthesis,
                       // 2, 3, 4: tensor-core synthesis asking for 32, 64, 96 columns per tile
 
@@ -97,7 +105,7 @@ struct sonar_ctx {
   uint64_t scene_version = 0;
 
   // parameter-derived tables
-  std::vector<uint8_t> ray_key, steer_key, rtab_key;
+  std::vector<uint8_t> ray_key, steer_key, rtab_key, ptab_key;
   double* ray_dirs = nullptr;
   float* ray_dirs32 = nullptr;
   float* row_domega = nullptr;
@@ -105,6 +113,8 @@ struct sonar_ctx {
   void* y_lo = nullptr;
   size_t y_elems = 0;
   float2* rtab = nullptr;
+  float2* ptab = nullptr;   // raw series: U shifted pulse tables (both grids), then the matched-filter taps
+  int ptab_u = 0, ptab_d = 0;
   float* taper_dev = nullptr;
   double y_gain = 1.0;
 
@@ -261,6 +271,8 @@ int derive(sonar_ctx* ctx, const sonar_params* p, const sonar_ssp* ssp, double z
   d.t0 = 2.0 * (p->r_min_m + 0.5 * d.dr) / d.c_ref;
   d.hw = p->pulse_s / d.dt;
   d.taps = (int)floor(2.0 * d.hw) + 1;
+  if (ctx->raw_u > 0 && !(d.hw > 2.0))
+    return fail(ctx, SONAR_E_UNSUPPORTED, "raw series need a pulse longer than two range samples");
   if (d.taps > 16)
     return fail(ctx, SONAR_E_UNSUPPORTED, "pulse spans %d range samples; at most 16 are supported", d.taps);
   d.T_stop = p->r_max_m / d.c_ref + p->pulse_s / 2.0;
@@ -355,6 +367,25 @@ int ensure_tables(sonar_ctx* ctx, const sonar_params* p, const Derived& d) {
     CU(launch_rtab(ctx->rtab, ctx->rtab + kRTab + 1, p->pulse_s, p->bw_hz, ctx->stream));
     ctx->rtab_key = k;
   }
+  if (ctx->raw_u > 0) {
+    // raw series: the pulse shifted by s dt / U on both table grids, and the matched
+    // filter's taps over |d| <= D range samples
+    const int D = (int)ceil(p->pulse_s / (2.0 * d.dt)) + 1;
+    k.clear();
+    key_add(k, p->pulse_s); key_add(k, p->bw_hz); key_add(k, d.dt); key_add(k, ctx->raw_u);
+    if (k != ctx->ptab_key) {
+      dfree(ctx->ptab);
+      const int64_t n = (int64_t)ctx->raw_u * (kRTab + 1 + kRTabS + 5 + 2 * D + 1);
+      CU(cudaMalloc(&ctx->ptab, sizeof(float2) * n));
+      float2* big = ctx->ptab;
+      float2* small = big + (int64_t)ctx->raw_u * (kRTab + 1);
+      float2* taps = small + (int64_t)ctx->raw_u * (kRTabS + 5);
+      CU(launch_ptab(big, small, taps, ctx->raw_u, D, p->pulse_s, p->bw_hz, d.dt, ctx->stream));
+      ctx->ptab_u = ctx->raw_u;
+      ctx->ptab_d = D;
+      ctx->ptab_key = k;
+    }
+  }
   k.clear();
   key_add(k, p->nx); key_add(k, p->ny); key_add(k, d.pitch_over_lambda); key_add(k, p->hfov_rad);
   key_add(k, p->vfov_rad); key_add(k, p->n_beam_az); key_add(k, p->n_beam_el); key_add(k, p->precision);
@@ -448,6 +479,12 @@ int ensure_workspace(sonar_ctx* ctx, int P, const Derived& d) {
     ctx->ws_s = s_need;
   }
   ctx->s_elems = s_need;
+  if (ctx->raw_u > 0 && (s_need * ctx->raw_u > ctx->ws_raw || !ctx->S_raw)) {
+    int64_t c0 = 0;
+    dfree(ctx->S_raw);
+    if ((rc = grow(ctx, ctx->S_raw, c0, s_need * ctx->raw_u, sizeof(float2), false))) return rc;
+    ctx->ws_raw = s_need * ctx->raw_u;
+  }
   int64_t x_need = (int64_t)P * d.nr_x * d.k_pad;
   if (x_need != ctx->ws_x || !ctx->x_hi) {
     int64_t c0 = 0, c1 = 0;
@@ -509,14 +546,15 @@ int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, cons
   };
   const bool fp16 = p->precision == SONAR_FP16;
   // trace, scan, scatter, synthesis, convert, GEMM, peaks; points; FP16 absmax and gain
-  *kernels = 7 + (ctx->sc.n_points > 0 ? 1 : 0) + (fp16 ? 2 : 0);
+  *kernels = 7 + (ctx->sc.n_points > 0 ? 1 : 0) + (fp16 ? 2 : 0) + (ctx->raw_u > 0 ? ctx->raw_u : 0);
   // the poses the host has just written into the pinned staging record
   CU(cudaMemcpyAsync(ctx->poses, ctx->pose_host, sizeof(DevPose) * P, cudaMemcpyHostToDevice, st));
   mark(0);
   // every buffer that starts at zero is cleared up front, in one launch, so the kernels
   // run back to back
   const int32_t n_bins = P * d.nr_pad;
-  k_clear<<<4 * ctx->sm_count, 256, 0, st>>>(ctx->S, ctx->s_elems, ctx->counts, n_bins, ctx->keys,
+  k_clear<<<4 * ctx->sm_count, 256, 0, st>>>(ctx->S, ctx->s_elems, ctx->raw_u > 0 ? ctx->S_raw : nullptr,
+                                             ctx->s_elems * ctx->raw_u, ctx->counts, n_bins, ctx->keys,
                                              (int64_t)P * d.nb, ctx->pmax, P, ctx->n_hits, ctx->err_dev);
   CU(cudaGetLastError());
   TraceArgs ta;
@@ -593,9 +631,36 @@ int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, cons
   sa.n_pass = p->precision == SONAR_FP32 ? 3 : 1;
   sa.err = ctx->err_dev;
   static const int kPairs[5] = {0, 0, 32, 64, 96};
-  if (ctx->synth_opt != 1 && synth_tc_supported(p->nx, p->ny, d.taps))
-    CU(launch_synth_tc(sa, kPairs[ctx->synth_opt], ctx->sm_count, st));
-  else CU(launch_synth(sa, ctx->sm_count, st));
+  const bool tc = ctx->synth_opt != 1 && synth_tc_supported(p->nx, p->ny, d.taps);
+  if (ctx->raw_u == 0) {
+    if (tc) CU(launch_synth_tc(sa, kPairs[ctx->synth_opt], ctx->sm_count, st));
+    else CU(launch_synth(sa, ctx->sm_count, st));
+  } else {
+    // raw series: one synthesis pass per phase s with the pulse shifted by s dt / U in
+    // place of its autocorrelation (the same hits, sorted by the same rows), then the
+    // matched filter into S
+    const int U = ctx->raw_u;
+    for (int s = 0; s < U; ++s) {
+      SynthArgs sr = sa;
+      sr.rtab = ctx->ptab + (int64_t)s * (kRTab + 1);
+      sr.rtab_s = ctx->ptab + (int64_t)U * (kRTab + 1) + (int64_t)s * (kRTabS + 5);
+      sr.S = ctx->S_raw + (int64_t)s * ctx->s_elems;
+      if (tc) CU(launch_synth_tc(sr, kPairs[ctx->synth_opt], ctx->sm_count, st));
+      else CU(launch_synth(sr, ctx->sm_count, st));
+    }
+    MfArgs ma;
+    ma.raw = ctx->S_raw;
+    ma.phase_stride = ctx->s_elems;
+    ma.S = ctx->S;
+    ma.taps = ctx->ptab + (int64_t)U * (kRTab + 1 + kRTabS + 5);
+    ma.U = U;
+    ma.D = ctx->ptab_d;
+    ma.nr = d.nr;
+    ma.nr_pad = d.nr_pad;
+    ma.M = d.M;
+    ma.n_pings = P;
+    CU(launch_mfilter(ma, st));
+  }
   mark(3);
   ConvertArgs ca;
   ca.S = ctx->S;
@@ -745,6 +810,7 @@ int run(sonar_ctx* ctx, const sonar_pose* poses, int P, const sonar_params* p, c
     key_add(k, o.env_host); key_add(k, o.cloud_host); key_add(k, ctx->pose_host); key_add(k, ctx->counters_host);
     key_add(k, ctx->n_cloud_host);
     key_add(k, ctx->debug); key_add(k, ctx->timing); key_add(k, ctx->synth_opt); key_add(k, ctx->scene_version);
+    key_add(k, ctx->raw_u);
     key_add(k, d.c_ref);
     if (ssp) {
       key_add(k, ssp->n_nodes);
@@ -777,6 +843,7 @@ int run(sonar_ctx* ctx, const sonar_pose* poses, int P, const sonar_params* p, c
   const int errw = (int)ctx->counters_host[1];
   ctx->last_p = P;
   ctx->last_d = d;
+  ctx->last_raw_u = ctx->raw_u;
   ctx->last_params = *p;
   ctx->stats.n_hits = (int64_t)nh;
   ctx->stats.hit_capacity = ctx->hit_cap;
@@ -862,6 +929,10 @@ int sonar_set_option(sonar_ctx* ctx, int32_t option, int64_t value) {
       if (value < 0 || value > 4) return fail(ctx, SONAR_E_ARG, "synthesis option must be 0 to 4");
       ctx->synth_opt = (int)value;
       break;
+    case SONAR_OPT_RAW:
+      if (value < 0 || value > 8) return fail(ctx, SONAR_E_ARG, "raw series: 0 (off) or 1 to 8 samples per cell");
+      ctx->raw_u = (int)value;
+      break;
     case SONAR_OPT_TILE_N:
       if (value != 0 && value != 128 && value != 192 && value != 224 && value != 256)
         return fail(ctx, SONAR_E_ARG, "tile_n must be 0, 128, 192, 224 or 256");
@@ -898,7 +969,7 @@ int sonar_destroy(sonar_ctx* c) {
   if (c->counters_host) cudaFreeHost(c->counters_host);
   dfree(c->poses); dfree(c->hits); dfree(c->sorted); dfree(c->sorted_n); dfree(c->dbg_tau);
   dfree(c->n_hits);
-  dfree(c->counts); dfree(c->offsets); dfree(c->S); dfree(c->x_hi); dfree(c->x_lo); dfree(c->gain);
+  dfree(c->counts); dfree(c->offsets); dfree(c->S); dfree(c->S_raw); dfree(c->ptab); dfree(c->x_hi); dfree(c->x_lo); dfree(c->gain);
   dfree(c->env_stage); dfree(c->keys); dfree(c->pmax); dfree(c->cloud_stage); dfree(c->n_cloud_dev); dfree(c->err_dev);
   delete c;
   return SONAR_OK;
@@ -1023,6 +1094,23 @@ int sonar_get_echoes(sonar_ctx* ctx, float* out, int64_t cap_floats) {
   CU(cudaSetDevice(ctx->device));
   for (int p = 0; p < ctx->last_p; ++p) {
     const float2* src = ctx->S + ((int64_t)p * d.nr_pad + kPad) * d.M;
+    CU(cudaMemcpyAsync(out + p * per_ping, src, sizeof(float) * per_ping, cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  CU(cudaStreamSynchronize(ctx->stream));
+  return SONAR_OK;
+}
+
+int sonar_get_raw(sonar_ctx* ctx, int32_t phase, float* out, int64_t cap_floats) {
+  if (!ctx || !out) return SONAR_E_ARG;
+  if (ctx->last_p == 0 || ctx->last_raw_u == 0) return fail(ctx, SONAR_E_ARG, "no raw-series ping yet");
+  if (!ctx->debug) return fail(ctx, SONAR_E_ARG, "enable SONAR_OPT_DEBUG before the ping");
+  if (phase < 0 || phase >= ctx->last_raw_u) return fail(ctx, SONAR_E_ARG, "phase %d outside [0, %d)", phase, ctx->last_raw_u);
+  const Derived& d = ctx->last_d;
+  const int64_t per_ping = (int64_t)d.nr * d.M * 2;
+  if (cap_floats < per_ping * ctx->last_p) return fail(ctx, SONAR_E_CAPACITY, "need %lld floats", (long long)(per_ping * ctx->last_p));
+  CU(cudaSetDevice(ctx->device));
+  for (int p = 0; p < ctx->last_p; ++p) {
+    const float2* src = ctx->S_raw + (int64_t)phase * ctx->s_elems + ((int64_t)p * d.nr_pad + kPad) * d.M;
     CU(cudaMemcpyAsync(out + p * per_ping, src, sizeof(float) * per_ping, cudaMemcpyDeviceToHost, ctx->stream));
   }
   CU(cudaStreamSynchronize(ctx->stream));

@@ -196,6 +196,22 @@ cudaError_t prepare_synth_tc();
 cudaError_t launch_synth_tc(const SynthArgs& a, int want_pairs, int sm_count, cudaStream_t st);
 cudaError_t launch_rtab(float2* rtab, float2* rtab_s, double pulse, double bw, cudaStream_t st);
 
+// Raw element series (echo before pulse compression) and its matched filter.
+// launch_ptab: for each phase s < U, the transmitted pulse shifted by s dt / U, p(u + s dt
+// / U), on the grids of the two synthesis tables (ptab [U][kRTab + 1], ptab_s [U][kRTabS
+// + 5]), so that a synthesis pass with them writes r_m(t_n + s dt / U); and the matched
+// filter's taps taps[s][D + d] = (dt / (U E)) conj(p(d dt + s dt / U)), |d| <= D.
+cudaError_t launch_ptab(float2* ptab, float2* ptab_s, float2* taps, int32_t U, int32_t D, double pulse, double bw,
+                        double dt, cudaStream_t st);
+struct MfArgs {
+  const float2* raw;        // [U] phases of [n_pings * nr_pad + guard][M], phase_stride apart
+  int64_t phase_stride;
+  float2* S;                // output: compressed echoes, rows kPad .. kPad + nr of each ping
+  const float2* taps;       // [U][2 D + 1]
+  int32_t U, D, nr, nr_pad, M, n_pings;
+};
+cudaError_t launch_mfilter(const MfArgs& a, cudaStream_t st);
+
 struct ConvertArgs {
   const float2* S;          // [n_pings][nr_pad][M]
   int32_t n_pings, nr, nr_pad, nr_x, M, k_pad;

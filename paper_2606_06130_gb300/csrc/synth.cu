@@ -323,6 +323,62 @@ __global__ void k_gain_pow2(float* gain, int n, int mode) {
   gain[p] = ldexpf(1.0f, 14 - e);
 }
 
+
+// ----------------------------------------------------------------- raw series, matched filter
+// The transmitted pulse p(t) = w(t) exp(j pi (B/T) t^2) on |t| <= T/2, Hann w = (1 + cos(2 pi
+// t / T)) / 2 (Sec. II.B), evaluated in FP64 once per parameter set.
+__device__ double2 pulse_p(double t, double T, double B) {
+  if (!(fabs(t) <= T / 2)) return make_double2(0.0, 0.0);
+  const double w = 0.5 * (1.0 + cos(2.0 * kPi * t / T)), ph = kPi * (B / T) * t * t;
+  return make_double2(w * cos(ph), w * sin(ph));
+}
+
+// Pulse tables of phase blockIdx.y on the grid of the autocorrelation tables (entry i at
+// u = -T + 2 T (i - guard) / n_int), shifted by s dt / U.
+__global__ void k_ptab(float2* tab, int n_int, int guard, double T, double B, double dt, int U) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, s = blockIdx.y;
+  if (i > n_int + 2 * guard) return;
+  const double u = -T + 2.0 * T * (double)(i - guard) / (double)n_int;
+  const double2 v = pulse_p(u + s * dt / U, T, B);
+  tab[(int64_t)s * (n_int + 2 * guard + 1) + i] = make_float2((float)v.x, (float)v.y);
+}
+
+__global__ void k_mftaps(float2* taps, int U, int D, double T, double B, double dt) {
+  const int d = (int)threadIdx.x - D, s = blockIdx.x;
+  if (d > D) return;
+  const double2 v = pulse_p(d * dt + s * dt / U, T, B);
+  const double g = dt / (U * (3.0 * T / 8.0));
+  taps[s * (2 * D + 1) + D + d] = make_float2((float)(g * v.x), (float)(-g * v.y));
+}
+
+// y_m(t_n) = sum over the U phases s and the offsets |d| <= D of r_m(t_{n+d} + s dt / U)
+// taps[s][D + d]: the rectangle rule of (1/E) int r(t) conj(p(t - t_n)) dt on the raw
+// samples. A thread owns one element and kMfRows consecutive samples of a ping; the raw
+// rows it reads repeat across its samples and stay in L1.
+constexpr int kMfRows = 16;
+__global__ void __launch_bounds__(128) k_mfilter(MfArgs a) {
+  pdl_wait();
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= a.M) return;
+  const int nblk = (a.nr + kMfRows - 1) / kMfRows;
+  const int p = blockIdx.y / nblk, n0 = (blockIdx.y % nblk) * kMfRows;
+  const int64_t base = ((int64_t)p * a.nr_pad + kPad) * a.M + m;
+  const int n1 = min(n0 + kMfRows, a.nr);
+  for (int n = n0; n < n1; ++n) {
+    float yr = 0.f, yi = 0.f;
+    for (int s = 0; s < a.U; ++s) {
+      const float2* src = a.raw + s * a.phase_stride + base + (int64_t)n * a.M;
+      const float2* h = a.taps + s * (2 * a.D + 1) + a.D;
+      for (int d = -a.D; d <= a.D; ++d) {
+        const float2 r = __ldg(src + (int64_t)d * a.M), t = __ldg(h + d);
+        yr = fmaf(r.x, t.x, fmaf(-r.y, t.y, yr));
+        yi = fmaf(r.x, t.y, fmaf(r.y, t.x, yi));
+      }
+    }
+    a.S[base + (int64_t)n * a.M] = make_float2(yr, yi);
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_bin(const HitRec* hits, const unsigned long long* n_hits, int32_t n_bins, int32_t* counts,
@@ -343,6 +399,20 @@ cudaError_t launch_synth(const SynthArgs& a, int sm_count, cudaStream_t st) {
   else e = launch_pdl(k_synth<16>, dim3(sm_count), dim3(kThreads), 0, st, a, total);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
+}
+
+cudaError_t launch_ptab(float2* ptab, float2* ptab_s, float2* taps, int32_t U, int32_t D, double pulse, double bw,
+                        double dt, cudaStream_t st) {
+  k_ptab<<<dim3((kRTab + 1 + 255) / 256, U), 256, 0, st>>>(ptab, kRTab, 0, pulse, bw, dt, U);
+  k_ptab<<<dim3((kRTabS + 5 + 255) / 256, U), 256, 0, st>>>(ptab_s, kRTabS, 2, pulse, bw, dt, U);
+  k_mftaps<<<U, 2 * D + 1, 0, st>>>(taps, U, D, pulse, bw, dt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mfilter(const MfArgs& a, cudaStream_t st) {
+  const int nblk = (a.nr + kMfRows - 1) / kMfRows;
+  return launch_pdl(k_mfilter, dim3((unsigned)ceil_div(a.M, 128), (unsigned)(a.n_pings * nblk)), dim3(128), 0, st,
+                    a);
 }
 
 cudaError_t launch_rtab(float2* rtab, float2* rtab_s, double pulse, double bw, cudaStream_t st) {

@@ -33,6 +33,7 @@ SONAR_OPT_TIMING = 2
 SONAR_OPT_GRAPH = 3
 SONAR_OPT_TILE_N = 4
 SONAR_OPT_SYNTH = 5
+SONAR_OPT_RAW = 6
 
 PRECISIONS = {"fp32": SONAR_FP32, "bf16": SONAR_BF16, "fp16": SONAR_FP16}
 
@@ -96,6 +97,7 @@ _SIGS = {
                                    C.POINTER(sonar_ssp), C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]),
     "sonar_get_hits": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]),
     "sonar_get_echoes": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
+    "sonar_get_raw": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int64]),
     "sonar_get_stats": (C.c_int, [C.c_void_p, C.POINTER(sonar_stats)]),
     "sonar_cloud_noalloc": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(sonar_params), C.POINTER(sonar_pose),
                                       C.c_void_p, C.c_int64, C.POINTER(C.c_int64), C.c_void_p]),
@@ -258,6 +260,13 @@ class Sonar:
         M = params["nx"] * params["ny"]
         out = np.zeros((n_pings, params["n_range"], M, 2), np.float32)
         self._check(lib().sonar_get_echoes(self.h, out.ctypes.data, out.size))
+        return out[..., 0] + 1j * out[..., 1]
+
+    def raw(self, params: dict, phase: int, n_pings: int = 1) -> np.ndarray:
+        """Raw element series of the last call at phase s (samples t_n + s dt / U)."""
+        M = params["nx"] * params["ny"]
+        out = np.zeros((n_pings, params["n_range"], M, 2), np.float32)
+        self._check(lib().sonar_get_raw(self.h, phase, out.ctypes.data, out.size))
         return out[..., 0] + 1j * out[..., 1]
 
     def stats(self) -> dict:
