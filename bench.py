@@ -477,6 +477,19 @@ def other_forms(torch, s, inputs, dev):
             s.ping(poses[0], params, ssp, precision=prec)
         torch.cuda.synchronize()
         out[f"c2_single_{prec}"] = {"value": 10 / (time.perf_counter() - t0), "unit": UNIT}
+    # the raw element series at 4 samples per range cell and the explicit matched filter
+    from paper_2606_06130_gb300.sonar import SONAR_OPT_RAW
+    s.set_option(SONAR_OPT_RAW, 4)
+    for _ in range(3):
+        s.ping(poses[0], params, ssp, precision="fp32")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(10):
+        s.ping(poses[0], params, ssp, precision="fp32")
+    torch.cuda.synchronize()
+    out["c2_raw_u4_fp32"] = {"value": 10 / (time.perf_counter() - t0), "unit": UNIT,
+                             "note": "raw chirp echoes at 4 samples per range cell + matched filter"}
+    s.set_option(SONAR_OPT_RAW, 0)
     sc4, p4, poses4, ssp4 = inputs.workload("c4")
     s.upload(sc4)
     for prec in ("fp32", "bf16"):

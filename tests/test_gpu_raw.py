@@ -111,3 +111,13 @@ def test_raw_option_arguments(sonar):
     run(sonar, scene, params, pose, ssp, 2)
     with pytest.raises(SonarError):
         sonar.raw(params, 2)  # phases 0 and 1 only
+
+
+def test_c2_raw_path_equals_compressed_to_quadrature_error(sonar):
+    """Full-size harbour ping (534k hits, 32x32 array): the raw path at U = 4 against the
+    compressed path, envelope and element echoes, all beams and bins."""
+    scene, params, poses, ssp = inputs.workload("c2")
+    E4, y4, _ = run(sonar, scene, params, poses[0], ssp, 4)
+    E0, s0, _ = run(sonar, scene, params, poses[0], ssp, 0)
+    assert parity.nl2(y4, s0) < 4e-4
+    assert parity.nl2(E4, E0) < 4e-4
