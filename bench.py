@@ -240,7 +240,7 @@ def run_ours(args, ws, rank, local):
         torch.cuda.synchronize()
         up.append((time.perf_counter() - t0) * 1e3)
     upload_ms = {"value": float(np.median(up)), "unit": "ms", "triangles": int(len(scene.tris)),
-                 "what": "host-to-device copy, LBVH build and packing (wall clock)"}
+                 "what": "host-to-device copy, binned-SAH hierarchy on the host, device refit and packing (wall clock)"}
     nb = params["n_beam_az"] * params["n_beam_el"]
     env = torch.empty((params["n_beam_el"], params["n_beam_az"], params["n_range"]), dtype=torch.float32, device=dev)
     cloud = torch.empty((nb, 6), dtype=torch.int32, device=dev)

@@ -169,6 +169,11 @@ SONAR_API const char* sonar_last_error(const sonar_ctx* ctx);
    2e-4 relative at U = 4, 4e-5 at U = 6). Costs U synthesis passes. Needs a pulse longer
    than two range samples (SONAR_E_UNSUPPORTED otherwise); any other value: SONAR_E_ARG. */
 #define SONAR_OPT_RAW 6
+/* SONAR_OPT_BVH: how sonar_scene_upload builds the triangle hierarchy. 0 (default): a
+   top-down binned surface-area-heuristic build on the host (fewer node visits per ray;
+   sequential host work, once per scene); 1: Morton-order LBVH built on the device (the
+   fastest build). Both give the same hits; takes effect at the next upload. */
+#define SONAR_OPT_BVH 7
 SONAR_API int sonar_set_option(sonar_ctx* ctx, int32_t option, int64_t value);
 
 /* ---------------------------------------------------------------- scene */

@@ -83,6 +83,7 @@ struct sonar_ctx {
   bool debug = false, timing = false, use_graph = true;
   int tile_opt = 0;
   int raw_u = 0;      // 0: compressed synthesis; U > 0: raw series at U samples per cell + matched filter
+  int bvh_opt = 0;    // 0: binned-SAH hierarchy (host build), 1: Morton-order LBVH (device build)
   int last_raw_u = 0;
   float2* S_raw = nullptr;  // raw series: U phases of s_elems
   int64_t ws_raw = 0;
@@ -933,6 +934,10 @@ int sonar_set_option(sonar_ctx* ctx, int32_t option, int64_t value) {
       if (value < 0 || value > 8) return fail(ctx, SONAR_E_ARG, "raw series: 0 (off) or 1 to 8 samples per cell");
       ctx->raw_u = (int)value;
       break;
+    case SONAR_OPT_BVH:
+      if (value != 0 && value != 1) return fail(ctx, SONAR_E_ARG, "BVH build: 0 (SAH) or 1 (Morton order)");
+      ctx->bvh_opt = (int)value;
+      break;
     case SONAR_OPT_TILE_N:
       if (value != 0 && value != 128 && value != 192 && value != 224 && value != 256)
         return fail(ctx, SONAR_E_ARG, "tile_n must be 0, 128, 192, 224 or 256");
@@ -1008,7 +1013,8 @@ int sonar_scene_upload(sonar_ctx* ctx, const float* verts, int64_t n_verts, cons
     CU(cudaMemcpyAsync(dt, tris, sizeof(int32_t) * 3 * n_tris, cudaMemcpyHostToDevice, ctx->stream));
     CU(cudaMemcpyAsync(dm, mu, sizeof(float) * n_tris, cudaMemcpyHostToDevice, ctx->stream));
     CU(cudaMemcpyAsync(df, flags, n_tris, cudaMemcpyHostToDevice, ctx->stream));
-    cudaError_t e = build_bvh(dv, dt, dm, df, (int32_t)n_tris, &ctx->tri32, &ctx->triv, &ctx->tri_prim, &ctx->tri_mu,
+    cudaError_t e = build_bvh(dv, dt, verts, tris, ctx->bvh_opt == 0, dm, df, (int32_t)n_tris, &ctx->tri32, &ctx->triv,
+                              &ctx->tri_prim, &ctx->tri_mu,
                               &ctx->tri_flags, &ctx->tri_plane, &ctx->tri_inv_n, &ctx->nodes, &ctx->sc.root,
                               ctx->stream);
     cudaFree(dv);

@@ -156,8 +156,10 @@ __host__ __device__ inline double u24(uint32_t h) { return (double)(h >> 8) * (1
 // Host-side launchers implemented in the .cu files.
 namespace sonar {
 struct BvhBuild;
-cudaError_t build_bvh(const float* d_verts, const int32_t* d_tris, const float* d_mu,
-                      const uint8_t* d_flags, int32_t n_tris, float4** tri32, float** triv,
+// sah != 0: the hierarchy comes from a binned-SAH build on the host copies h_verts,
+// h_tris; 0: Morton order and the Karras hierarchy on the device.
+cudaError_t build_bvh(const float* d_verts, const int32_t* d_tris, const float* h_verts, const int32_t* h_tris,
+                      int sah, const float* d_mu, const uint8_t* d_flags, int32_t n_tris, float4** tri32, float** triv,
                       int32_t** tri_prim, float** tri_mu, uint8_t** tri_flags, double4_32a** tri_plane,
                       float** tri_inv_n, BvhNode** nodes, int32_t* root, cudaStream_t st);
 // dirs32 holds 6 n floats: the directions rounded to FP32, then their FP32 residuals.
