@@ -16,6 +16,7 @@ import argparse
 import json
 import math
 import os
+import platform
 import subprocess
 import sys
 import threading
@@ -509,8 +510,52 @@ def other_forms(torch, s, inputs, dev):
     return out
 
 
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return platform.processor() or platform.machine()
+
+
+def oracle_timing():
+    """The reference arm with --oracle-timing (not part of the default runs): the FP64
+    oracle as it stands on this host, whole C1 and C2 pings single-threaded and on all
+    cores, and the C4 64-ping trajectory on all cores from 8 pings, extrapolated."""
+    import oracle
+    from paper_2606_06130_gb300 import inputs
+    n_all = oracle.num_threads()
+    rows = []
+    for threads in (1, n_all):
+        oracle.set_threads(threads)
+        for name in ("c1", "c2"):
+            scene, params, poses, ssp = inputs.workload(name)
+            t0 = time.perf_counter()
+            h, _, _ = oracle_ping(scene, params, poses[0], ssp)
+            dt = time.perf_counter() - t0
+            rows.append({"config": name, "threads": threads, "seconds_per_ping": dt, "pings_per_s": 1.0 / dt,
+                         "hits": int(h["n"])})
+    oracle.set_threads(n_all)
+    scene, params, poses, ssp = inputs.workload("c4")
+    t0 = time.perf_counter()
+    hits = 0
+    for k in range(8):
+        h, _, _ = oracle_ping(scene, params, poses[k], ssp)
+        hits += int(h["n"])
+    dt = time.perf_counter() - t0
+    rows.append({"config": "c4", "threads": n_all, "pings": 8, "seconds": dt, "pings_per_s": 8 / dt,
+                 "hits": hits, "note": f"64 pings extrapolated: {64 * dt / 8:.1f} s"})
+    print(json.dumps({"oracle_timing": rows, "cpu": cpu_model(), "nproc": os.cpu_count()}), flush=True)
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
+        return
+    if args.oracle_timing:
+        oracle_timing()
         return
     r = time_oracle(args.steps, args.warmup, k=sample_divisor(args.steps + args.warmup))
     out = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -532,6 +577,9 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16"])
     ap.add_argument("--no-oracle", action="store_true", help="skip the oracle error and CPU baseline")
     ap.add_argument("--no-forms", action="store_true", help="skip the BF16/FP16/batch side measurements")
+    ap.add_argument("--oracle-timing", action="store_true",
+                    help="with --impl reference: time the FP64 oracle in full instead (C1, C2 whole pings at 1 "
+                         "and all threads; C4 8 pings)")
     args = ap.parse_args()
     ws, rank, local = dist_setup()
     if args.impl == "reference":

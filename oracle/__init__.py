@@ -68,6 +68,7 @@ def lib():
         _lib.orc_eigen_arc.argtypes = [vp, vp, i32, vp, vp, vp, vp, vp]
         _lib.orc_eigen_arc.restype = C.c_int
         _lib.orc_num_threads.restype = C.c_int
+        _lib.orc_set_threads.argtypes = [C.c_int]
     return _lib
 
 
@@ -77,6 +78,10 @@ def _ptr(a):
 
 def num_threads() -> int:
     return lib().orc_num_threads()
+
+
+def set_threads(n: int) -> None:
+    lib().orc_set_threads(int(n))
 
 
 def make_params(p: dict) -> OrcParams:

@@ -62,6 +62,8 @@ typedef struct {
 
 /* Normalised autocorrelation R(u) of the Hann-windowed LFM pulse. */
 void orc_pulse_acf(double u, double pulse, double bw, double* re, double* im);
+/* OpenMP threads of the parallel loops (n > 0). */
+void orc_set_threads(int n);
 /* The transmitted pulse p(t): Hann-windowed linear chirp over |t| <= T/2. */
 void orc_pulse(double t, double pulse, double bw, double* re, double* im);
 
