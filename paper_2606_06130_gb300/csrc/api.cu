@@ -331,15 +331,18 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-int make_map(sonar_ctx* ctx, CUtensorMap* m, void* base, int64_t rows, int64_t cols, int box_rows, bool f16) {
+// box_k: K elements per box row, 64 (128-byte swizzle) or 32 (64-byte swizzle).
+int make_map(sonar_ctx* ctx, CUtensorMap* m, void* base, int64_t rows, int64_t cols, int box_rows, bool f16,
+             int box_k = 64) {
   auto fn = encode_fn();
   if (!fn) return fail(ctx, SONAR_E_CUDA, "cuTensorMapEncodeTiled unavailable");
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
-  cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
+  cuuint32_t box[2] = {(cuuint32_t)box_k, (cuuint32_t)box_rows};
   cuuint32_t es[2] = {1, 1};
   CUresult r = fn(m, f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides,
-                  box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  box_k == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(ctx, SONAR_E_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
   return SONAR_OK;
@@ -681,16 +684,15 @@ int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, cons
   memset(&ga, 0, sizeof(ga));
   const bool f16 = fp16;
   int rc;
-  if ((rc = make_map(ctx, &ga.map_xh, ctx->x_hi, (int64_t)P * d.nr_x, d.k_pad, 128, f16))) return rc;
-  if ((rc = make_map(ctx, &ga.map_xl, ctx->x_lo, (int64_t)P * d.nr_x, d.k_pad, 128, f16))) return rc;
-  if ((rc = make_map(ctx, &ga.map_yh, ctx->y_hi, 2LL * d.nb_pad, d.k_pad, d.tile_n, f16))) return rc;
-  if ((rc = make_map(ctx, &ga.map_yl, ctx->y_lo, 2LL * d.nb_pad, d.k_pad, d.tile_n, f16))) return rc;
+  const int box_k = d.n_phase == 3 ? 32 : 64;
+  if ((rc = make_map(ctx, &ga.map_xh, ctx->x_hi, (int64_t)P * d.nr_x, d.k_pad, 128, f16, box_k))) return rc;
+  if ((rc = make_map(ctx, &ga.map_xl, ctx->x_lo, (int64_t)P * d.nr_x, d.k_pad, 128, f16, box_k))) return rc;
+  if ((rc = make_map(ctx, &ga.map_yh, ctx->y_hi, 2LL * d.nb_pad, d.k_pad, d.tile_n, f16, box_k))) return rc;
+  if ((rc = make_map(ctx, &ga.map_yl, ctx->y_lo, 2LL * d.nb_pad, d.k_pad, d.tile_n, f16, box_k))) return rc;
   ga.tiles_m = P * d.nr_x / 128;
   ga.tiles_n = 2 * d.nb_pad / d.tile_n;
   ga.k_blocks = d.k_pad / 64;
   ga.n_phase = d.n_phase;
-  ga.xsel = d.n_phase == 3 ? 4 : 0;  // FP32 form: hi*hi, hi*lo (pass 1), lo*hi (pass 2)
-  ga.ysel = d.n_phase == 3 ? 2 : 0;
   ga.tile_n = d.tile_n;
   ga.f16 = f16 ? 1 : 0;
   ga.nr = d.nr;

@@ -12,8 +12,12 @@
 // into a double-buffered TMEM accumulator (2 x tile_n columns) so the epilogue of one
 // tile overlaps the MMAs of the next. Persistent CTAs, one per SM.
 //
-// FP32 form: X = Xh + Xl, Y = Yh + Yl in BF16; three passes hi*hi, hi*lo, lo*hi
-// accumulate into the same FP32 accumulator.
+// FP32 form: X = Xh + Xl, Y = Yh + Yl in BF16; the three products hi*hi, hi*lo, lo*hi
+// accumulate into the same FP32 accumulator. Its stages hold all four operand tiles of a
+// 32-deep K slice (64-byte swizzle) and issue the three products from them: each tile
+// crosses shared memory once instead of twice, which matters because an M = 128 MMA on
+// one SM is bound by shared-memory bandwidth (operand reads plus TMA writes), while four
+// stages keep the pipeline as deep as the one-product forms' 64-deep, two-tile stages.
 #include <math.h>
 
 #include "common.cuh"
@@ -24,9 +28,22 @@ namespace {
 using namespace tc;
 
 constexpr int BM = 128;
-constexpr int BK = 64;
 constexpr int STAGES = 4;
 constexpr int kGemmThreads = 192;  // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+
+// NPASS products per K slice (1: BF16/FP16, 3: FP32 form); PARTS tiles per operand (hi,
+// lo) in a stage; BK the K slice (64: 128-byte swizzle, 32: 64-byte swizzle).
+template <int NPASS>
+struct GemmShape {
+  static constexpr int PARTS = NPASS == 3 ? 2 : 1;
+  static constexpr int BK = NPASS == 3 ? 32 : 64;
+};
+
+// UMMA shared-memory descriptor, K-major, 64-byte swizzle: 8-row groups 512 B apart.
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t addr) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(512 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
+}
 
 // TMEM columns of the double-buffered accumulator: 2 BN rounded up to a power of two
 // (allocation granularity).
@@ -45,16 +62,17 @@ __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int
   mb = gm0 + r % gsz;
 }
 
-template <int BN>
+template <int BN, int NPASS>
 __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant__ GemmArgs a, uint32_t idesc) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   // align by pointer arithmetic on the shared array, so that the compiler keeps the
   // shared address space (an integer round trip would turn every access generic)
   uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  constexpr int PARTS = GemmShape<NPASS>::PARTS, BK = GemmShape<NPASS>::BK;
   constexpr uint32_t A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
-  uint8_t* sA = smem;
-  uint8_t* sB = smem + STAGES * A_BYTES;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sB + STAGES * B_BYTES);
+  uint8_t* sA = smem;                                 // [stage][part] A tiles (X: echoes)
+  uint8_t* sB = smem + STAGES * PARTS * A_BYTES;      // [stage][part] B tiles (Y: steering)
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sB + STAGES * PARTS * B_BYTES);
   uint64_t* full = bars;
   uint64_t* empty = bars + STAGES;
   uint64_t* tfull = bars + 2 * STAGES;
@@ -64,7 +82,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant_
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n_tiles = a.tiles_m * a.tiles_n;
-  const int k_iters = a.n_phase * a.k_blocks;
+  const int k_iters = a.k_blocks * (64 / BK);  // K slices per tile
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) { mbar_init(smem_u32(&full[s]), 1); mbar_init(smem_u32(&empty[s]), 1); }
@@ -94,14 +112,18 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant_
       for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
         int mb, nb;
         tile_coords(t, a.tiles_m, a.tiles_n, mb, nb);
-        for (int it = 0; it < k_iters && ok; ++it) {
-          const int ph = it / a.k_blocks, kb = it % a.k_blocks;
-          const CUtensorMap* ma = ((a.xsel >> ph) & 1) ? &a.map_xl : &a.map_xh;
-          const CUtensorMap* mbm = ((a.ysel >> ph) & 1) ? &a.map_yl : &a.map_yh;
+        for (int kb = 0; kb < k_iters && ok; ++kb) {
           if (!mbar_wait(smem_u32(&empty[stage]), phase ^ 1, a.err)) { ok = false; break; }
-          mbar_expect_tx(smem_u32(&full[stage]), A_BYTES + B_BYTES);
-          tma_load_2d(smem_u32(sA + stage * A_BYTES), ma, kb * BK, mb * BM, smem_u32(&full[stage]));
-          tma_load_2d(smem_u32(sB + stage * B_BYTES), mbm, kb * BK, nb * BN, smem_u32(&full[stage]));
+          const uint32_t fb = smem_u32(&full[stage]);
+          mbar_expect_tx(fb, PARTS * (A_BYTES + B_BYTES));
+          uint8_t* const a_st = sA + stage * PARTS * A_BYTES;
+          uint8_t* const b_st = sB + stage * PARTS * B_BYTES;
+          tma_load_2d(smem_u32(a_st), &a.map_xh, kb * BK, mb * BM, fb);
+          tma_load_2d(smem_u32(b_st), &a.map_yh, kb * BK, nb * BN, fb);
+          if (PARTS == 2) {
+            tma_load_2d(smem_u32(a_st + A_BYTES), &a.map_xl, kb * BK, mb * BM, fb);
+            tma_load_2d(smem_u32(b_st + B_BYTES), &a.map_yl, kb * BK, nb * BN, fb);
+          }
           ++issued;
           if (++stage == STAGES) { stage = 0; phase ^= 1; }
         }
@@ -129,10 +151,18 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant_
         for (int it = 0; it < k_iters; ++it) {
           if (!mbar_wait(smem_u32(&full[stage]), phase, a.err)) { ok = false; break; }
           tc_fence_after();
-          const uint32_t a0 = smem_u32(sA + stage * A_BYTES), b0 = smem_u32(sB + stage * B_BYTES);
+          const uint32_t ah = smem_u32(sA + stage * PARTS * A_BYTES), bh = smem_u32(sB + stage * PARTS * B_BYTES);
 #pragma unroll
-          for (int kk = 0; kk < BK / 16; ++kk)
-            tc_mma(d_tmem, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32), idesc, (it | kk) != 0);
+          for (int pass = 0; pass < NPASS; ++pass) {
+            // hi*hi, then hi*lo, then lo*hi; a K step of 16 advances 32 bytes in the row
+            const uint32_t a0 = pass == 2 ? ah + A_BYTES : ah, b0 = pass == 1 ? bh + B_BYTES : bh;
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk) {
+              const uint64_t da = BK == 64 ? sw128_desc(a0 + kk * 32) : sw64_desc(a0 + kk * 32);
+              const uint64_t db = BK == 64 ? sw128_desc(b0 + kk * 32) : sw64_desc(b0 + kk * 32);
+              tc_mma(d_tmem, da, db, idesc, (it | pass | kk) != 0);
+            }
+          }
           tc_commit(smem_u32(&empty[stage]));
           if (++stage == STAGES) { stage = 0; phase ^= 1; }
         }
@@ -218,10 +248,11 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant_
   }
 }
 
-template <int BN>
+template <int BN, int NPASS>
 constexpr size_t gemm_smem() {
-  return 1024 + (size_t)STAGES * (BM * BK * 2 + BN * BK * 2) + 256;
+  return 1024 + (size_t)STAGES * GemmShape<NPASS>::PARTS * (BM + BN) * GemmShape<NPASS>::BK * 2 + 256;
 }
+static_assert(gemm_smem<256, 3>() <= 227 * 1024 && gemm_smem<256, 1>() <= 227 * 1024, "GEMM stages fit");
 
 // ----------------------------------------------------------------- steering matrix
 // W[b][m] = w_m exp(-j k_a u_b . p_m) / sum w, beams cell-centred (Sec. III Eq. 2-3),
@@ -364,7 +395,10 @@ cudaError_t launch_steer(const SteerArgs& a, cudaStream_t st) {
 // Dynamic shared-memory opt-in of the GEMM kernels (once per device, outside capture).
 template <int BN>
 cudaError_t gemm_attr() {
-  return cudaFuncSetAttribute(k_gemm<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem<BN>());
+  cudaError_t e = cudaFuncSetAttribute(k_gemm<BN, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)gemm_smem<BN, 1>());
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_gemm<BN, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem<BN, 3>());
 }
 cudaError_t prepare_gemm() {
   cudaError_t e;
@@ -376,7 +410,10 @@ cudaError_t prepare_gemm() {
 
 template <int BN>
 cudaError_t launch_bn(const GemmArgs& a, int grid, cudaStream_t st) {
-  return launch_pdl(k_gemm<BN>, dim3(grid), dim3(kGemmThreads), gemm_smem<BN>(), st, a, make_idesc(a.f16 ? 0 : 1, BM, BN));
+  const uint32_t idesc = make_idesc(a.f16 ? 0 : 1, BM, BN);
+  if (a.n_phase == 3)
+    return launch_pdl(k_gemm<BN, 3>, dim3(grid), dim3(kGemmThreads), gemm_smem<BN, 3>(), st, a, idesc);
+  return launch_pdl(k_gemm<BN, 1>, dim3(grid), dim3(kGemmThreads), gemm_smem<BN, 1>(), st, a, idesc);
 }
 
 cudaError_t launch_gemm(const GemmArgs& a, int sm_count, cudaStream_t st) {

@@ -237,8 +237,9 @@ cudaError_t launch_steer(const SteerArgs& a, cudaStream_t st);
 
 struct GemmArgs {
   CUtensorMap map_xh, map_xl, map_yh, map_yl;
-  int32_t tiles_m, tiles_n, k_blocks, n_phase, tile_n;
-  int32_t xsel, ysel;        // bit p: pass p reads the lo part of X (echoes) / Y (steering)
+  int32_t tiles_m, tiles_n, k_blocks, tile_n;  // k_blocks: K / 64
+  int32_t n_phase;           // products per K slice: 3 (FP32 form: hi*hi, hi*lo, lo*hi) or 1;
+                             // the FP32 form's maps have 32-element K boxes, 64-byte swizzle
   int32_t f16;               // operands FP16 (1) or BF16 (0)
   int32_t nr, nr_x, n_beams, n_blank;
   float r_min, dr, alpha2;   // TVG(r) = r exp(alpha2 r)
