@@ -28,15 +28,17 @@ namespace {
 using namespace tc;
 
 constexpr int BM = 128;
-constexpr int STAGES = 4;
 constexpr int kGemmThreads = 192;  // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
 
 // NPASS products per K slice (1: BF16/FP16, 3: FP32 form); PARTS tiles per operand (hi,
 // lo) in a stage; BK the K slice (64: 128-byte swizzle, 32: 64-byte swizzle).
-template <int NPASS>
+template <int NPASS, int BN = 224>
 struct GemmShape {
   static constexpr int PARTS = NPASS == 3 ? 2 : 1;
   static constexpr int BK = NPASS == 3 ? 32 : 64;
+  // as many stages as 224 KB of shared memory hold, up to five
+  static constexpr int STAGE_BYTES = PARTS * (BM + BN) * BK * 2;
+  static constexpr int STAGES = (224 * 1024) / STAGE_BYTES < 5 ? (224 * 1024) / STAGE_BYTES : 5;
 };
 
 // UMMA shared-memory descriptor, K-major, 64-byte swizzle: 8-row groups 512 B apart.
@@ -68,7 +70,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant_
   // align by pointer arithmetic on the shared array, so that the compiler keeps the
   // shared address space (an integer round trip would turn every access generic)
   uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-  constexpr int PARTS = GemmShape<NPASS>::PARTS, BK = GemmShape<NPASS>::BK;
+  constexpr int PARTS = GemmShape<NPASS, BN>::PARTS, BK = GemmShape<NPASS, BN>::BK;
+  constexpr int STAGES = GemmShape<NPASS, BN>::STAGES;
   constexpr uint32_t A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
   uint8_t* sA = smem;                                 // [stage][part] A tiles (X: echoes)
   uint8_t* sB = smem + STAGES * PARTS * A_BYTES;      // [stage][part] B tiles (Y: steering)
@@ -250,7 +253,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant_
 
 template <int BN, int NPASS>
 constexpr size_t gemm_smem() {
-  return 1024 + (size_t)STAGES * GemmShape<NPASS>::PARTS * (BM + BN) * GemmShape<NPASS>::BK * 2 + 256;
+  return 1024 + (size_t)GemmShape<NPASS, BN>::STAGES * GemmShape<NPASS, BN>::STAGE_BYTES + 256;
 }
 static_assert(gemm_smem<256, 3>() <= 227 * 1024 && gemm_smem<256, 1>() <= 227 * 1024, "GEMM stages fit");
 
