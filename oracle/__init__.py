@@ -27,7 +27,7 @@ class OrcParams(C.Structure):
                 ("n_ray_el", C.c_int32), ("n_sub", C.c_int32), ("max_bounces", C.c_int32),
                 ("surface_z", C.c_double), ("r_surface", C.c_double), ("r_seabed", C.c_double),
                 ("alpha", C.c_double), ("seed", C.c_uint64), ("thr_mode", C.c_int32),
-                ("thr", C.c_double)]
+                ("thr", C.c_double), ("cross", C.c_int32)]
 
 
 class OrcScene(C.Structure):
@@ -87,7 +87,7 @@ def set_threads(n: int) -> None:
 def make_params(p: dict) -> OrcParams:
     o = OrcParams()
     for name, _ in OrcParams._fields_:
-        v = p[name]
+        v = p.get(name, 0) if name == "cross" else p[name]
         if name == "surface_z" and v is None:
             v = math.nan
         setattr(o, name, v)

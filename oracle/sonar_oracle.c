@@ -512,6 +512,54 @@ static void reflect(double d[3], const double n[3]) {
   d[0] -= k * n[0]; d[1] -= k * n[1]; d[2] -= k * n[2];
 }
 
+/* Cross-term multipath of a mesh hit reached after one or more reflections (Sec. II.B
+   multi-bounce paths, extended to routes whose outgoing and returning legs differ):
+   out along the route and back on the straight line to the array, and the reciprocal
+   path (out straight, back along the route). The route's ray tube samples the surface
+   with footprint L^2 dOmega / cos(k_route); bistatic Lambertian scattering
+   mu cos(k_in) cos(k_out) over it, spread over L^2 on the route and L_d^2 on the straight
+   leg, leaves the amplitude Gamma sqrt(mu cos(k_d) dOmega) / L_d exp(-alpha (L + L_d))
+   for either path, with Gamma the route's one-way reflection product and delay
+   (L + L_d) / c. The straight leg must reach the facet from the side the route arrives
+   on and pass no other triangle closer than L_d - CROSS_CLEAR. Both paths share one
+   speckle phase (reciprocity), keyed apart from the route's own. seg carries the
+   bounce count plus 16 (returns straight, arrives from the hit's direction) or 32
+   (returns along the route, arrives along the launch direction). */
+#define CROSS_CLEAR 1e-4
+static void cross_mesh(const tctx* c, hbuf* hb, int32_t ray, int32_t sub, int32_t seg, int32_t prim,
+                       const double x[3], double L, double gam, const double dir[3], const double n[3],
+                       double dOmega, const double us[3], double margin, double gap) {
+  const orc_params* p = c->p;
+  double v[3];
+  sub3(x, c->t, v);
+  double Ld = norm3(v);
+  if (!(Ld > CROSS_CLEAR)) return;
+  double tau = (L + Ld) / c->ssp.c0;
+  if (!(tau <= 2.0 * c->T_stop)) return;
+  double vn = dot3(v, n);
+  if (!(dot3(dir, n) * vn > 0)) return;
+  double ud[3] = {v[0] / Ld, v[1] / Ld, v[2] / Ld};
+  hitq sh = closest(c->sc, c->bv, c->t, ud, EPS_HIT, Ld - CROSS_CLEAR, prim);
+  if (sh.prim >= 0) return;
+  ohit h;
+  h.ray = ray; h.sub = sub; h.prim = prim;
+  h.tau = tau;
+  h.len = 0.5 * (L + Ld);
+  h.amp = gam * sqrt(c->sc->mu[prim] * (fabs(vn) / Ld) * dOmega) / Ld * exp(-p->alpha * (L + Ld));
+  uint32_t k[4] = {(uint32_t)ray, (uint32_t)sub, (uint32_t)(9 + seg), c->s32};
+  orc_pcg4d(k);
+  h.psi = TWO_PI * u24(k[0]);
+  h.phi = wrap_pi(h.psi - TWO_PI * frac(p->f0 * h.tau));
+  h.margin = margin;
+  h.gap = gap;
+  h.seg = seg | 16;
+  mat_t_vec(c->R, ud, h.u);
+  hb_push(hb, &h);
+  h.seg = seg | 32;
+  h.u[0] = us[0]; h.u[1] = us[1]; h.u[2] = us[2];
+  hb_push(hb, &h);
+}
+
 /* Isovelocity route (Sec. II.A ray casting, Sec. II.B limited secondary reflections):
    straight segments; a triangle hit scatters and, when the triangle is a specular
    mirror and bounces remain, the ray reflects about the geometric normal; the sea
@@ -551,6 +599,8 @@ static void route_straight(const tctx* c, const double o[3], const double d0[3],
     double kinc = fabs(dot3(dir, n));
     emit_mesh_hit(c, hb, ray, sub, bounce, hq.prim, L / cw, L, gam, kinc, dOmega, us, hq.margin,
                   hq.t2 - hq.t);
+    if (p->cross && bounce > 0)
+      cross_mesh(c, hb, ray, sub, bounce, hq.prim, pos, L, gam, dir, n, dOmega, us, hq.margin, hq.t2 - hq.t);
     if ((c->sc->flags[hq.prim] & 1) && bounce < p->max_bounces) {
       reflect(dir, n);
       gam *= p->r_seabed;
@@ -652,7 +702,10 @@ static void mirror_point(const double pl[4], const double x[3], double r[3]) {
    reflections). Mirror planes: the sea surface (reflection r_surface) then the scene's
    planes (reflection r_seabed). Routes are plane sequences without immediate repeats,
    enumerated by length then lexicographically; each leg is shadow-tested. Amplitude
-   sigma Gamma^2 / L^2, no speckle. */
+   sigma Gamma^2 / L^2, no speckle. With cross terms every ordered pair (i, j) of distinct
+   valid routes adds the path out along i and back along j: delay (L_i + L_j) / c,
+   amplitude sigma Gamma_i Gamma_j / (L_i L_j) exp(-alpha (L_i + L_j)), arriving along
+   route j; sub = 0x10000 | i << 8 | j (route indices), seg = the total reflections. */
 static void point_routes(const tctx* c, hbuf* hb) {
   const orc_scene* sc = c->sc;
   const orc_params* p = c->p;
@@ -710,6 +763,8 @@ static void point_routes(const tctx* c, hbuf* hb) {
       continue;
     }
     int32_t route = 0;
+    struct { int32_t idx, len; double L, gam, u[3]; } pr[256];
+    int npr = 0;
     for (int len = 0; len <= maxb; ++len) {
       int64_t count = len == 0 ? 1 : np;
       for (int k = 1; k < len; ++k) count *= (np - 1);
@@ -762,8 +817,30 @@ static void point_routes(const tctx* c, hbuf* hb) {
         h.margin = INFINITY;
         h.gap = INFINITY;
         hb_push(hb, &h);
+        if (p->cross && npr < 256) {
+          pr[npr].idx = route; pr[npr].len = len; pr[npr].L = L; pr[npr].gam = gam;
+          for (int k = 0; k < 3; ++k) pr[npr].u[k] = h.u[k];
+          ++npr;
+        }
       }
     }
+    for (int i = 0; i < npr; ++i)
+      for (int j = 0; j < npr; ++j) {
+        if (i == j) continue;
+        ohit h;
+        h.ray = (int32_t)ip; h.sub = 0x10000 | (pr[i].idx << 8) | pr[j].idx;
+        h.seg = pr[i].len + pr[j].len; h.prim = -1;
+        double Ls = pr[i].L + pr[j].L;
+        h.tau = Ls / c->ssp.c0;
+        h.len = 0.5 * Ls;
+        h.amp = sigma * pr[i].gam * pr[j].gam / (pr[i].L * pr[j].L) * exp(-p->alpha * Ls);
+        h.psi = 0.0;
+        h.phi = wrap_pi(-TWO_PI * frac(p->f0 * h.tau));
+        for (int k = 0; k < 3; ++k) h.u[k] = pr[j].u[k];
+        h.margin = INFINITY;
+        h.gap = INFINITY;
+        hb_push(hb, &h);
+      }
   }
 }
 
@@ -775,6 +852,7 @@ int orc_trace(const orc_scene* sc, const orc_params* p, const double pose_t[3], 
   c.p = p;
   if (p->n_sub != 1 && p->n_sub != 4) return 3;
   if (ssp_make(ssp_z, ssp_cc, n_ssp, p->c_ref, &c.ssp) != 0) return 2;
+  if (p->cross && c.ssp.curved) return 4; /* cross terms are formed for isovelocity routes only */
   c.c_ref = p->c_ref > 0 ? p->c_ref : ssp_c(&c.ssp, pose_t[2]);
   /* one-way time after which no echo reaches the last range sample */
   c.T_stop = p->r_max / c.c_ref + p->pulse / 2.0;

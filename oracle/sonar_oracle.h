@@ -38,6 +38,7 @@ typedef struct {
   uint64_t seed;
   int32_t thr_mode;        /* 0 absolute, 1 relative to the ping maximum */
   double thr;
+  int32_t cross;           /* 1: add out/back cross-term multipath (isovelocity only) */
 } orc_params;
 
 typedef struct {

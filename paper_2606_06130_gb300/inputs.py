@@ -307,8 +307,41 @@ def trajectory_c4(n: int = 64, seed: int = TRAJ_SEED) -> list:
     return out
 
 
+def scene_wall_mirror(seed: int = SCENE_SEED) -> tuple:
+    """Scene for out/back cross-term multipath: a flat mirror seabed (z = -4, two
+    triangles, reflectivity 0.3); a vertical wall 6 m ahead (x = 6, 16 x 8 quads over
+    y in [-5, 5], z in [-4, 0], reflectivity U(0.2, 0.6)) that seabed-reflected rays
+    reach from below; a plate at x = 3 (y in [-0.8, 0.8], z in [-2.5, -2.2]) that hides
+    part of that wall band from the sonar but not from the reflected routes; three unit
+    point scatterers between the sonar and the plate. Sonar at (0, 0, -2) tilted 15
+    degrees down. Returns (scene, pose)."""
+    rng = np.random.default_rng(seed)
+    sea = np.array([[-2.0, -8.0, -4.0], [12.0, -8.0, -4.0], [12.0, 8.0, -4.0], [-2.0, 8.0, -4.0]])
+    ys, zs = np.linspace(-5.0, 5.0, 17), np.linspace(-4.0, 0.0, 9)
+    wv = np.array([[6.0, y, z] for z in zs for y in ys])
+    wt = []
+    for j in range(len(zs) - 1):
+        for i in range(len(ys) - 1):
+            a = j * len(ys) + i
+            wt += [(a, a + 1, a + len(ys) + 1), (a, a + len(ys) + 1, a + len(ys))]
+    plate = np.array([[3.0, -0.8, -2.5], [3.0, 0.8, -2.5], [3.0, 0.8, -2.2], [3.0, -0.8, -2.2]])
+    verts, tris, mu, flags = _assemble([(sea, [(0, 1, 2), (0, 2, 3)], 0.3, 1), (wv, wt, 0.0, 0),
+                                        (plate, [(0, 1, 2), (0, 2, 3)], 0.5, 0)])
+    mu[2:2 + len(wt)] = rng.uniform(0.2, 0.6, len(wt)).astype(np.float32)
+    pts = np.stack([rng.uniform(1.0, 2.0, 3), rng.uniform(-1.5, 1.5, 3), rng.uniform(-3.5, -1.5, 3)], 1)
+    sc = Scene(verts, tris, mu, flags, pts.astype(np.float32), np.ones(3, np.float32),
+               np.array([[0.0, 0.0, 1.0, -4.0]]))
+    return sc, pose((0.0, 0.0, -2.0), tilt_down_deg=15.0)
+
+
 def workload(name: str):
-    """(scene, params, poses, ssp) of a named workload; poses is a list."""
+    """(scene, params, poses, ssp) of a named workload; poses is a list.
+
+    wall_mirror: the c1 sensor to 10 m (512 bins) without a sea surface, over
+    scene_wall_mirror, for cross-term multipath."""
+    if name == "wall_mirror":
+        sc, ps = scene_wall_mirror()
+        return sc, dict(sensor_params("c1"), r_max=10.0, n_range=512, surface_z=None), [ps], ssp("c1")
     if name in ("c1", "c3"):
         sc, ps = scene_c1()
         return sc, sensor_params(name), [ps], ssp(name)
