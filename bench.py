@@ -491,6 +491,19 @@ def other_forms(torch, s, inputs, dev):
     out["c2_raw_u4_fp32"] = {"value": 10 / (time.perf_counter() - t0), "unit": UNIT,
                              "note": "raw chirp echoes at 4 samples per range cell + matched filter"}
     s.set_option(SONAR_OPT_RAW, 0)
+    # out/back cross-term multipath (every reflected route also returns straight)
+    from paper_2606_06130_gb300.sonar import SONAR_OPT_CROSS
+    s.set_option(SONAR_OPT_CROSS, 1)
+    for _ in range(3):
+        s.ping(poses[0], params, ssp, precision="fp32")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(10):
+        s.ping(poses[0], params, ssp, precision="fp32")
+    torch.cuda.synchronize()
+    out["c2_cross_fp32"] = {"value": 10 / (time.perf_counter() - t0), "unit": UNIT,
+                            "hits": s.stats()["n_hits"], "note": "out/back cross-term multipath on"}
+    s.set_option(SONAR_OPT_CROSS, 0)
     sc4, p4, poses4, ssp4 = inputs.workload("c4")
     s.upload(sc4)
     for prec in ("fp32", "bf16"):

@@ -106,7 +106,10 @@ typedef struct {
 } sonar_point;
 
 /* Debug/parity export of one hit (32 bytes). key: mesh hits ((ray * n_sub + sub) << 2
-   | bounce); point scatterers 0x80000000 | (point << 8) | route. */
+   | bounce), plus 0x40000000 for the cross term that returns straight (arriving from the
+   hit) or 0x20000000 for its reciprocal (arriving along the route); point scatterers
+   0x80000000 | (point << 8) | route, cross pairs 0xC0000000 | (point << 16) |
+   (out route << 8) | back route (SONAR_OPT_CROSS). */
 typedef struct {
   uint32_t key;
   int32_t prim;   /* triangle id, or -1 for a point scatterer */
@@ -174,6 +177,22 @@ SONAR_API const char* sonar_last_error(const sonar_ctx* ctx);
    sequential host work, once per scene); 1: Morton-order LBVH built on the device (the
    fastest build). Both give the same hits; takes effect at the next upload. */
 #define SONAR_OPT_BVH 7
+/* SONAR_OPT_CROSS: 1 adds out/back cross-term multipath (Sec. II.B multi-bounce and
+   secondary paths, with the outgoing and returning legs allowed to differ); 0 (default)
+   keeps every route monostatic (the same legs out and back).
+   Mesh: every hit reached after k >= 1 reflections adds two echoes, out along the route
+   and straight back to the array and the reciprocal, when the straight leg reaches the
+   facet from the side the route arrives on and passes no other triangle closer than
+   0.1 mm to the hit. Delay (L + L_d) / c for route length L and straight distance L_d;
+   amplitude Gamma sqrt(mu cos(k_d) dOmega) / L_d exp(-alpha (L + L_d)) (bistatic
+   Lambertian scattering over the route's footprint, Gamma the route's one-way
+   reflection product, k_d the straight leg's incidence angle); one speckle phase for the
+   pair. Point scatterers: every ordered pair (i, j) of distinct valid image-source
+   routes adds out along i and back along j, delay (L_i + L_j) / c, amplitude
+   sigma Gamma_i Gamma_j / (L_i L_j) exp(-alpha (L_i + L_j)), arriving along j.
+   Isovelocity profiles only (SONAR_E_UNSUPPORTED at the ping with a gradient);
+   at most 2^27 sub-rays and 16384 point scatterers. Any other value: SONAR_E_ARG. */
+#define SONAR_OPT_CROSS 8
 SONAR_API int sonar_set_option(sonar_ctx* ctx, int32_t option, int64_t value);
 
 /* ---------------------------------------------------------------- scene */

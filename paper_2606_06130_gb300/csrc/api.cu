@@ -84,6 +84,9 @@ struct sonar_ctx {
   int tile_opt = 0;
   int raw_u = 0;      // 0: compressed synthesis; U > 0: raw series at U samples per cell + matched filter
   int bvh_opt = 0;    // 0: binned-SAH hierarchy (host build), 1: Morton-order LBVH (device build)
+  int cross = 0;      // 1: out/back cross-term multipath
+  PtRoute* pt_route = nullptr;  // point-route records for cross pairing
+  int64_t ws_pt_route = 0;
   int last_raw_u = 0;
   float2* S_raw = nullptr;  // raw series: U phases of s_elems
   int64_t ws_raw = 0;
@@ -302,6 +305,8 @@ int derive(sonar_ctx* ctx, const sonar_params* p, const sonar_ssp* ssp, double z
     d.n_routes = (int)total;
   }
   if (d.n_routes > 256) return fail(ctx, SONAR_E_UNSUPPORTED, "too many point-scatterer routes");
+  if (ctx->cross && d.curved)
+    return fail(ctx, SONAR_E_UNSUPPORTED, "cross-term multipath needs an isovelocity profile");
   d.wsum = 0.0;
   d.wmax = 0.0;
   for (int m = 0; m < d.M; ++m) {
@@ -313,7 +318,12 @@ int derive(sonar_ctx* ctx, const sonar_params* p, const sonar_ssp* ssp, double z
   if (!(d.wsum > 0)) return fail(ctx, SONAR_E_ARG, "taper weights sum to zero");
   d.n_subrays = (int64_t)p->n_ray_az * p->n_ray_el * p->n_sub;
   int64_t npts = ctx->has_scene ? ctx->sc.n_points : 0;
-  d.hit_cap_per_ping = d.n_subrays * (1 + p->max_bounces) + npts * d.n_routes;
+  if (ctx->cross && (d.n_subrays > (1LL << 27) || npts > 16384))
+    return fail(ctx, SONAR_E_UNSUPPORTED, "cross-term keys hold at most 2^27 sub-rays and 16384 points");
+  // a route emits one hit per segment; with cross terms every segment after a
+  // reflection adds two, and a point's routes pair up in every ordered combination
+  d.hit_cap_per_ping = ctx->cross ? d.n_subrays * (1 + 3 * (int64_t)p->max_bounces) + npts * d.n_routes * d.n_routes
+                                  : d.n_subrays * (1 + p->max_bounces) + npts * d.n_routes;
   return SONAR_OK;
 }
 
@@ -466,6 +476,13 @@ int ensure_workspace(sonar_ctx* ctx, int P, const Derived& d) {
     ctx->ws_hits = hit_need;
   }
   ctx->hit_cap = hit_need;
+  const int64_t pt_need = ctx->cross ? (int64_t)P * (ctx->has_scene ? ctx->sc.n_points : 0) * d.n_routes : 0;
+  if (pt_need > ctx->ws_pt_route) {
+    int64_t c0 = 0;
+    dfree(ctx->pt_route);
+    if ((rc = grow(ctx, ctx->pt_route, c0, pt_need, sizeof(PtRoute), false))) return rc;
+    ctx->ws_pt_route = pt_need;
+  }
   int64_t bins = (int64_t)P * d.nr_pad + 1;
   if (bins > ctx->ws_bins || !ctx->counts) {
     int64_t c0 = 0, c1 = 0;
@@ -549,8 +566,10 @@ int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, cons
     if (ctx->timing) cudaEventRecord(ctx->stage_ev[i], st);
   };
   const bool fp16 = p->precision == SONAR_FP16;
-  // trace, scan, scatter, synthesis, convert, GEMM, peaks; points; FP16 absmax and gain
-  *kernels = 7 + (ctx->sc.n_points > 0 ? 1 : 0) + (fp16 ? 2 : 0) + (ctx->raw_u > 0 ? ctx->raw_u : 0);
+  // clear, trace, scan, scatter, synthesis, convert, GEMM, peaks; points (and their cross
+  // pairs); FP16 absmax and gain; raw phases
+  const bool pairs = ctx->cross && ctx->sc.n_points > 0;
+  *kernels = 8 + (ctx->sc.n_points > 0 ? 1 : 0) + (pairs ? 1 : 0) + (fp16 ? 2 : 0) + (ctx->raw_u > 0 ? ctx->raw_u : 0);
   // the poses the host has just written into the pinned staging record
   CU(cudaMemcpyAsync(ctx->poses, ctx->pose_host, sizeof(DevPose) * P, cudaMemcpyHostToDevice, st));
   mark(0);
@@ -606,6 +625,8 @@ int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, cons
   ta.hw_df = df_pair(ta.hw);
   ta.nr_pad = d.nr_pad;
   ta.n_routes = d.n_routes;
+  ta.cross = ctx->cross;
+  ta.pt_route = pairs ? ctx->pt_route : nullptr;
   ta.hits = ctx->hits;
   ta.bin_counts = ctx->counts;
   ta.dbg_tau = ctx->debug ? ctx->dbg_tau : nullptr;
@@ -614,6 +635,7 @@ int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, cons
   ta.err = ctx->err_dev;
   CU(launch_trace(ta, ctx->sm_count, st));
   CU(launch_points(ta, st));
+  if (pairs) CU(launch_point_pairs(ta, st));
   mark(1);
   CU(launch_bin(ctx->hits, ctx->n_hits, n_bins, ctx->counts, ctx->offsets, ctx->sorted, ctx->sorted_n, ctx->sm_count,
                 st));
@@ -940,6 +962,10 @@ int sonar_set_option(sonar_ctx* ctx, int32_t option, int64_t value) {
       if (value != 0 && value != 1) return fail(ctx, SONAR_E_ARG, "BVH build: 0 (SAH) or 1 (Morton order)");
       ctx->bvh_opt = (int)value;
       break;
+    case SONAR_OPT_CROSS:
+      if (value != 0 && value != 1) return fail(ctx, SONAR_E_ARG, "cross terms: 0 (off) or 1 (on)");
+      ctx->cross = (int)value;
+      break;
     case SONAR_OPT_TILE_N:
       if (value != 0 && value != 128 && value != 192 && value != 224 && value != 256)
         return fail(ctx, SONAR_E_ARG, "tile_n must be 0, 128, 192, 224 or 256");
@@ -974,6 +1000,7 @@ int sonar_destroy(sonar_ctx* c) {
   if (c->pose_host) cudaFreeHost(c->pose_host);
   if (c->n_cloud_host) cudaFreeHost(c->n_cloud_host);
   if (c->counters_host) cudaFreeHost(c->counters_host);
+  dfree(c->pt_route);
   dfree(c->poses); dfree(c->hits); dfree(c->sorted); dfree(c->sorted_n); dfree(c->dbg_tau);
   dfree(c->n_hits);
   dfree(c->counts); dfree(c->offsets); dfree(c->S); dfree(c->S_raw); dfree(c->ptab); dfree(c->x_hi); dfree(c->x_lo); dfree(c->gain);

@@ -79,6 +79,14 @@ struct DevPose {
 };
 
 // Everything the trace kernels need, passed by value.
+// One point-scatterer image-source route, kept for cross-term pairing: one-way length L
+// (0: the route is not valid), reflection product gam, sonar-frame arrival (uy, uz).
+struct PtRoute {
+  double L, gam;
+  float uy, uz;
+  int32_t len, pad;
+};
+
 struct TraceArgs {
   DevScene sc;
   const DevPose* poses;
@@ -103,6 +111,8 @@ struct TraceArgs {
   float2 L_stop_df, surface_z_df, two_inv_c0_df, f0_df, inv_dt_df, t0_dt_df, hw_df;
   int32_t nr_pad;
   int32_t n_routes;              // point-scatterer routes per point
+  int32_t cross;                 // 1: out/back cross-term multipath
+  PtRoute* pt_route;             // [n_pings][n_points][n_routes] with cross terms, else null
   HitRec* hits;
   int32_t* bin_counts;           // [n_pings * nr_pad] hits per first-tap row (zeroed by the caller)
   double* dbg_tau;               // nullable: FP64 delay per hit
@@ -168,6 +178,7 @@ cudaError_t launch_ray_table(double* dirs, float* dirs32, float* row_domega, int
                              cudaStream_t st);
 cudaError_t launch_trace(const TraceArgs& a, int sm_count, cudaStream_t st);
 cudaError_t launch_points(const TraceArgs& a, cudaStream_t st);
+cudaError_t launch_point_pairs(const TraceArgs& a, cudaStream_t st);
 
 struct SynthArgs {
   const HitRec* hits_sorted;

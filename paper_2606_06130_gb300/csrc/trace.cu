@@ -582,8 +582,46 @@ __device__ void route_curved(const TraceArgs& A, int ping, D3 o, D3 d0, D3 us, u
   }
 }
 
-__device__ void route_straight(const TraceArgs& A, int ping, DF3 o, const float* o32, DF3 d0, float uy, float uz,
-                               uint32_t ray, uint32_t sub, float dOmega, uint32_t keybase) {
+// Cross-term multipath of a mesh hit reached after one or more reflections (Sec. II.B
+// multi-bounce paths with differing outgoing and returning legs): out along the route
+// and straight back to the array, and the reciprocal path, both with delay
+// (L + L_d) / c and amplitude Gamma sqrt(mu cos(k_d) dOmega) / L_d exp(-alpha (L + L_d))
+// (bistatic Lambertian scattering over the route's footprint; Gamma the route's one-way
+// reflection product). The straight leg must reach the facet from the side the route
+// arrives on and pass no other triangle closer than L_d - kCrossClear. Its geometry and
+// shadow test run in FP64 from the pose; the delay adds L_d to the route's FP32-pair
+// length. One speckle phase serves both paths (reciprocity), keyed apart from the
+// route's own (third hash word 9 + bounce).
+constexpr double kCrossClear = 1e-4;
+__device__ void emit_cross(const TraceArgs& A, int ping, const DevPose& P, const DF3& xh, F2 L, const DF3& dir,
+                           float gam, int leaf, int prim, float dOmega, float uy, float uz, uint32_t ray,
+                           uint32_t sub_i, int bounce, uint32_t keybase) {
+  const D3 X = to_d3(xh);
+  const D3 v = d3(X.x - P.t[0], X.y - P.t[1], X.z - P.t[2]);
+  const double Ld = sqrt(dot(v, v));
+  if (!(Ld > kCrossClear)) return;
+  const F2 tau = (L + f2_of(Ld)) * (f2(A.two_inv_c0_df) * f2(0.5f));
+  if (!(to_d(tau) <= 2.0 * A.T_stop)) return;
+  const double4_32a pl = load_plane(A.sc, leaf);
+  const D3 n = d3(pl.x, pl.y, pl.z);
+  const double vn = dot(v, n);
+  if (!(dot(to_d3(dir), n) * vn > 0.0)) return;
+  const D3 ud = d3(v.x / Ld, v.y / Ld, v.z / Ld);
+  const D3 o = d3(P.t[0], P.t[1], P.t[2]);
+  const Hit sh = closest_hit(A.sc, o, ud, kEpsHit, Ld - kCrossClear, prim, A.err);
+  if (sh.prim >= 0) return;
+  const float kd = (float)(fabs(vn) / Ld) * __ldg(&A.sc.tri_inv_n[leaf]);
+  const float amp = gam * sqrtf(A.sc.tri_mu[leaf] * kd * dOmega) / (float)Ld * expf(-A.alpha32 * (L.hi + (float)Ld));
+  const float psi = speckle32(A, ray, sub_i, 8u + (uint32_t)bounce);
+  const D3 u = rot_t(P.R, ud);
+  const uint32_t key = keybase | (uint32_t)bounce;
+  emit_df(A, ping, tau, amp, psi, (float)u.y, (float)u.z, prim, key | 0x40000000u);
+  emit_df(A, ping, tau, amp, psi, uy, uz, prim, key | 0x20000000u);
+}
+
+template <bool CROSS>
+__device__ void route_straight(const TraceArgs& A, int ping, const DevPose& P, DF3 o, const float* o32, DF3 d0,
+                               float uy, float uz, uint32_t ray, uint32_t sub, float dOmega, uint32_t keybase) {
   // kEpsHit as an FP32 pair (folded at compile time)
   const F2 eps = F2{(float)kEpsHit, (float)(kEpsHit - (double)(float)kEpsHit)};
   DF3 pos = o, dir = d0;
@@ -628,6 +666,9 @@ __device__ void route_straight(const TraceArgs& A, int ping, DF3 o, const float*
     const float amp = lambert(A, gam, A.sc.tri_mu[hq.leaf], kinc, dOmega, L.hi);
     emit_df(A, ping, L * f2(A.two_inv_c0_df), amp, speckle32(A, ray, sub, bounce), uy, uz, hq.prim,
             keybase | (uint32_t)bounce);
+    if (CROSS && bounce > 0)
+      emit_cross(A, ping, P, axpy(pos, hq.t, dir), L, dir, gam, hq.leaf, hq.prim, dOmega, uy, uz, ray, sub, bounce,
+                 keybase);
     if ((A.sc.tri_flags[hq.leaf] & 1) && bounce < A.max_bounces) {
       pos = axpy(pos, hq.t, dir);
       // specular reflection off the triangle's plane: d - 2 (d . n) / (n . n) n
@@ -645,8 +686,10 @@ __device__ void route_straight(const TraceArgs& A, int ping, DF3 o, const float*
 }
 
 // Traversal is latency-bound (dependent node loads), so residency pays: the straight-ray
-// kernel fits five CTAs of 128 threads per SM (96 registers), the curved one four.
-template <bool CURVED>
+// kernel fits five CTAs of 128 threads per SM (96 registers), the curved one four. The
+// cross-term variant is a separate instantiation, so that its extra live state does not
+// cost the default kernel registers.
+template <bool CURVED, bool CROSS>
 __global__ void __launch_bounds__(128, CURVED ? 4 : 5) k_trace(TraceArgs A) {
   pdl_wait();
   const int64_t total = (int64_t)A.n_pings * A.n_subrays;
@@ -674,7 +717,7 @@ __global__ void __launch_bounds__(128, CURVED ? 4 : 5) k_trace(TraceArgs A) {
         dw[i] = F2{P.R32[3 * i], P.R_lo[3 * i]} * u[0] + F2{P.R32[3 * i + 1], P.R_lo[3 * i + 1]} * u[1] +
                 F2{P.R32[3 * i + 2], P.R_lo[3 * i + 2]} * u[2];
       const DF3 o = DF3{F2{P.t32[0], P.t_lo[0]}, F2{P.t32[1], P.t_lo[1]}, F2{P.t32[2], P.t_lo[2]}};
-      route_straight(A, ping, o, P.t32, DF3{dw[0], dw[1], dw[2]}, uh[1], uh[2], ray, sub, dOmega, keybase);
+      route_straight<CROSS>(A, ping, P, o, P.t32, DF3{dw[0], dw[1], dw[2]}, uh[1], uh[2], ray, sub, dOmega, keybase);
     }
   }
 }
@@ -720,6 +763,7 @@ __global__ void k_points(TraceArgs A) {
   D3 o = d3(P.t[0], P.t[1], P.t[2]);
   double sigma = xp.w;
   uint32_t key = 0x80000000u | ((uint32_t)ip << 8) | (uint32_t)route;
+  if (A.cross) A.pt_route[gid] = PtRoute{0.0, 0.0, 0.f, 0.f, 0, 0};  // invalid until it passes
   if (A.curved) {
     if (route != 0) return;
     double dx = x.x - o.x, dy = x.y - o.y;
@@ -816,6 +860,28 @@ __global__ void k_points(TraceArgs A) {
   D3 dw = d3(dv.x / L, dv.y / L, dv.z / L);
   const D3 u = rot_t(P.R, dw);
   emit(A, ping, 2.0 * L / A.ssp_c0, (float)amp, 0.0, (float)u.y, (float)u.z, -1, key);
+  if (A.cross) A.pt_route[gid] = PtRoute{L, gam, (float)u.y, (float)u.z, len, 0};
+}
+
+// Cross pairs of a point scatterer's routes: out along route i, back along route j != i,
+// delay (L_i + L_j) / c, amplitude sigma Gamma_i Gamma_j / (L_i L_j) exp(-alpha
+// (L_i + L_j)), arriving along route j; no speckle. Reads the routes k_points recorded.
+__global__ void k_point_pairs(TraceArgs A) {
+  pdl_wait();
+  const int nr = A.n_routes;
+  const int64_t total = (int64_t)A.n_pings * A.sc.n_points * nr * nr;
+  const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gid >= total) return;
+  const int j = (int)(gid % nr), i = (int)((gid / nr) % nr);
+  const int64_t pt = gid / ((int64_t)nr * nr);  // ping * n_points + point
+  if (i == j) return;
+  const PtRoute a = A.pt_route[pt * nr + i], b = A.pt_route[pt * nr + j];
+  if (!(a.L > 0.0) || !(b.L > 0.0)) return;
+  const int ip = (int)(pt % A.sc.n_points), ping = (int)(pt / A.sc.n_points);
+  const double Ls = a.L + b.L;
+  const double amp = (double)A.sc.points[ip].w * a.gam * b.gam / (a.L * b.L) * exp(-A.alpha * Ls);
+  const uint32_t key = 0xC0000000u | ((uint32_t)ip << 16) | ((uint32_t)i << 8) | (uint32_t)j;
+  emit(A, ping, Ls / A.ssp_c0, (float)amp, 0.0, b.uy, b.uz, -1, key);
 }
 
 // Sonar-frame sub-ray directions (Sec. III Eq. 2-3 grid, cell-centred) with hashed
@@ -854,6 +920,14 @@ __global__ void k_ray_table(double* dirs, float* dirs32, float* row_domega, int 
 
 }  // namespace
 
+cudaError_t launch_point_pairs(const TraceArgs& a, cudaStream_t st) {
+  const int64_t total = (int64_t)a.n_pings * a.sc.n_points * a.n_routes * a.n_routes;
+  if (total == 0) return cudaSuccess;
+  cudaError_t e = launch_pdl(k_point_pairs, dim3((unsigned)ceil_div(total, 128)), dim3(128), 0, st, a);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_ray_table(double* dirs, float* dirs32, float* row_domega, int32_t nra, int32_t nre, int32_t nsub,
                              double hfov, double vfov, uint32_t seed32, cudaStream_t st) {
   int64_t n = (int64_t)nra * nre * nsub;
@@ -869,8 +943,9 @@ cudaError_t launch_trace(const TraceArgs& a, int sm_count, cudaStream_t st) {
   int64_t cap = (int64_t)sm_count * 16;
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
-  cudaError_t e = a.curved ? launch_pdl(k_trace<true>, dim3((unsigned)blocks), dim3(128), 0, st, a)
-                           : launch_pdl(k_trace<false>, dim3((unsigned)blocks), dim3(128), 0, st, a);
+  cudaError_t e = a.curved  ? launch_pdl(k_trace<true, false>, dim3((unsigned)blocks), dim3(128), 0, st, a)
+                  : a.cross ? launch_pdl(k_trace<false, true>, dim3((unsigned)blocks), dim3(128), 0, st, a)
+                            : launch_pdl(k_trace<false, false>, dim3((unsigned)blocks), dim3(128), 0, st, a);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }

@@ -35,6 +35,7 @@ SONAR_OPT_TILE_N = 4
 SONAR_OPT_SYNTH = 5
 SONAR_OPT_RAW = 6
 SONAR_OPT_BVH = 7
+SONAR_OPT_CROSS = 8
 
 PRECISIONS = {"fp32": SONAR_FP32, "bf16": SONAR_BF16, "fp16": SONAR_FP16}
 

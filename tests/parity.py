@@ -6,11 +6,17 @@ import oracle
 
 
 def oracle_keys(h: dict, n_sub: int) -> np.ndarray:
+    """The C ABI's hit keys of the oracle's hits. Mesh: seg = bounce, plus 16 for the
+    cross term that returns straight (key bit 30) or 32 for its reciprocal (bit 29).
+    Points: sub = route, or 0x10000 | out route << 8 | back route for a cross pair."""
     ray = h["ray"].astype(np.uint64)
     sub = h["sub"].astype(np.uint64)
     seg = h["seg"].astype(np.uint64)
-    mesh = ((ray * np.uint64(n_sub) + sub) << np.uint64(2)) | seg
-    pts = np.uint64(0x80000000) | (ray << np.uint64(8)) | sub
+    u = np.uint64
+    mesh = ((ray * u(n_sub) + sub) << u(2)) | (seg & u(3))
+    mesh |= np.where(seg & u(16), u(0x40000000), u(0)) | np.where(seg & u(32), u(0x20000000), u(0))
+    pts = np.where(sub & u(0x10000), u(0xC0000000) | (ray << u(16)) | (sub & u(0xFFFF)),
+                   u(0x80000000) | (ray << u(8)) | sub)
     return np.where(h["prim"] >= 0, mesh, pts).astype(np.uint64)
 
 
@@ -35,14 +41,15 @@ def nl2(a, b) -> float:
     return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
 
 
-def check_hits(gpu: np.ndarray, ref: dict, n_sub: int, margin=1e-5, gap=1e-6):
+def check_hits(gpu: np.ndarray, ref: dict, n_sub: int, margin=1e-5, gap=1e-6, per_tie=2):
     """Hit-level parity. Prim ids must match bit-exactly wherever the oracle's
     barycentric margin and runner-up distance gap exceed the near-tie margins; the
-    number of excluded hits is returned. Delays agree to FP64 rounding."""
+    number of excluded hits is returned. Delays agree to FP64 rounding. per_tie: hits
+    one near-tie may add or drop (later segments of its route, and their cross terms)."""
     ig, ir, only_g, only_r = match_hits(gpu, ref, n_sub)
     clear = (ref["margin"][ir] > margin) & (ref["gap"][ir] > gap)
     # a route that ends differently near a tie may add or drop later segments
-    assert len(only_g) + len(only_r) <= 2 * (np.count_nonzero(~clear) + 1), (len(only_g), len(only_r))
+    assert len(only_g) + len(only_r) <= per_tie * (np.count_nonzero(~clear) + 1), (len(only_g), len(only_r))
     prim_ok = gpu["prim"][ig] == ref["prim"][ir]
     assert np.all(prim_ok[clear]), f"{np.count_nonzero(~prim_ok[clear])} prim mismatches outside margins"
     same = prim_ok
