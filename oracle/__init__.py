@@ -27,7 +27,11 @@ class OrcParams(C.Structure):
                 ("n_ray_el", C.c_int32), ("n_sub", C.c_int32), ("max_bounces", C.c_int32),
                 ("surface_z", C.c_double), ("r_surface", C.c_double), ("r_seabed", C.c_double),
                 ("alpha", C.c_double), ("seed", C.c_uint64), ("thr_mode", C.c_int32),
-                ("thr", C.c_double), ("cross", C.c_int32)]
+                ("thr", C.c_double), ("cross", C.c_int32), ("vol_n", C.c_int64),
+                ("vol_lo", C.c_double * 3), ("vol_hi", C.c_double * 3), ("vol_sv", C.c_double)]
+
+
+_PARAM_DEFAULTS = {"cross": 0, "vol_n": 0, "vol_lo": (0.0, 0.0, 0.0), "vol_hi": (0.0, 0.0, 0.0), "vol_sv": 0.0}
 
 
 class OrcScene(C.Structure):
@@ -87,7 +91,9 @@ def set_threads(n: int) -> None:
 def make_params(p: dict) -> OrcParams:
     o = OrcParams()
     for name, _ in OrcParams._fields_:
-        v = p.get(name, 0) if name == "cross" else p[name]
+        v = p.get(name, _PARAM_DEFAULTS[name]) if name in _PARAM_DEFAULTS else p[name]
+        if name in ("vol_lo", "vol_hi"):
+            v = (C.c_double * 3)(*[float(x) for x in v])
         if name == "surface_z" and v is None:
             v = math.nan
         setattr(o, name, v)

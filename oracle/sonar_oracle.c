@@ -844,6 +844,45 @@ static void point_routes(const tctx* c, hbuf* hb) {
   }
 }
 
+/* Water-column (volume) reverberation (Sec. II.B volumetric backscatter paths, Sec. V
+   clutter): vol_n point scatterers frozen in the world frame, uniform in the box
+   [vol_lo, vol_hi]; the i-th sits at lo + (hi - lo) u, u the first three 24-bit
+   fractions of pcg4d(i mod 2^32, i div 2^32, 0x564F4C, seed). Each has the amplitude
+   coefficient sigma = sqrt(s_v V / n), V the box volume, so that the backscattering
+   cross-section per unit volume is s_v, and echoes on its direct route when the leg is
+   clear: amplitude sigma / L^2 exp(-2 alpha L), delay 2 L / c, no speckle phase (the
+   random positions make the speckle). ray = i, sub = 0x20000. */
+static void volume_scatter(const tctx* c, int64_t i0, int64_t i1, hbuf* hb) {
+  const orc_params* p = c->p;
+  double V = 1.0;
+  for (int k = 0; k < 3; ++k) V *= p->vol_hi[k] - p->vol_lo[k];
+  const double sigma = sqrt(p->vol_sv * V / (double)p->vol_n);
+  const double L_stop = c->T_stop * c->ssp.c0;
+  for (int64_t i = i0; i < i1; ++i) {
+    uint32_t v[4] = {(uint32_t)i, (uint32_t)((uint64_t)i >> 32), 0x564F4Cu, c->s32};
+    orc_pcg4d(v);
+    double x[3];
+    for (int k = 0; k < 3; ++k) x[k] = p->vol_lo[k] + (p->vol_hi[k] - p->vol_lo[k]) * u24(v[k]);
+    double dv[3];
+    sub3(x, c->t, dv);
+    double L = norm3(dv);
+    if (!(L > 0) || !(L <= L_stop)) continue;
+    if (!leg_clear(c, c->t, x)) continue;
+    ohit h;
+    h.ray = (int32_t)i; h.sub = 0x20000; h.seg = 0; h.prim = -1;
+    h.tau = 2.0 * L / c->ssp.c0;
+    h.len = L;
+    h.amp = sigma / (L * L) * exp(-2.0 * p->alpha * L);
+    h.psi = 0.0;
+    h.phi = wrap_pi(-TWO_PI * frac(p->f0 * h.tau));
+    double dw[3] = {dv[0] / L, dv[1] / L, dv[2] / L};
+    mat_t_vec(c->R, dw, h.u);
+    h.margin = INFINITY;
+    h.gap = INFINITY;
+    hb_push(hb, &h);
+  }
+}
+
 int orc_trace(const orc_scene* sc, const orc_params* p, const double pose_t[3], const double pose_q[4],
               const double* ssp_z, const double* ssp_cc, int32_t n_ssp, int use_bvh, orc_hits* out) {
   tctx c;
@@ -853,6 +892,12 @@ int orc_trace(const orc_scene* sc, const orc_params* p, const double pose_t[3], 
   if (p->n_sub != 1 && p->n_sub != 4) return 3;
   if (ssp_make(ssp_z, ssp_cc, n_ssp, p->c_ref, &c.ssp) != 0) return 2;
   if (p->cross && c.ssp.curved) return 4; /* cross terms are formed for isovelocity routes only */
+  if (p->vol_n < 0 || p->vol_n > (1LL << 28)) return 5;
+  if (p->vol_n > 0) {
+    if (c.ssp.curved) return 4; /* volume scatterers: isovelocity direct routes only */
+    for (int k = 0; k < 3; ++k)
+      if (!(p->vol_hi[k] > p->vol_lo[k]) || !(p->vol_sv >= 0)) return 5;
+  }
   c.c_ref = p->c_ref > 0 ? p->c_ref : ssp_c(&c.ssp, pose_t[2]);
   /* one-way time after which no echo reaches the last range sample */
   c.T_stop = p->r_max / c.c_ref + p->pulse / 2.0;
@@ -874,7 +919,11 @@ int orc_trace(const orc_scene* sc, const orc_params* p, const double pose_t[3], 
      hash-jittered point. */
   const int32_t nra = p->n_ray_az, nre = p->n_ray_el;
   const double daz = p->hfov / nra, del = p->vfov / nre;
-  hbuf* rows = (hbuf*)calloc((size_t)nre + 1, sizeof(hbuf));
+  /* rows: one per elevation row of rays, the point scatterers, then the volume
+     scatterers in chunks (kept in index order) */
+  const int32_t nvc = p->vol_n > 0 ? 64 : 0;
+  const int32_t nrows = nre + 1 + nvc;
+  hbuf* rows = (hbuf*)calloc((size_t)nrows, sizeof(hbuf));
 #pragma omp parallel for schedule(dynamic, 1)
   for (int32_t j = 0; j < nre; ++j) {
     double el_lo = -p->vfov / 2 + j * del, el_hi = el_lo + del;
@@ -900,17 +949,20 @@ int orc_trace(const orc_scene* sc, const orc_params* p, const double pose_t[3], 
     }
   }
   point_routes(&c, &rows[nre]);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int32_t q = 0; q < nvc; ++q)
+    volume_scatter(&c, p->vol_n * q / nvc, p->vol_n * (q + 1) / nvc, &rows[nre + 1 + q]);
   if (use_bvh) bvh_free(&bv);
 
   int64_t total = 0;
-  for (int32_t j = 0; j <= nre; ++j) total += rows[j].n;
+  for (int32_t j = 0; j < nrows; ++j) total += rows[j].n;
   out->n = total;
   int rc = 0;
   if (total > out->cap) {
     rc = (int)(-total > -2147483647 ? -total : -2147483647);
   } else {
     int64_t w = 0;
-    for (int32_t j = 0; j <= nre; ++j) {
+    for (int32_t j = 0; j < nrows; ++j) {
       for (int64_t k = 0; k < rows[j].n; ++k, ++w) {
         const ohit* h = &rows[j].v[k];
         out->ray[w] = h->ray; out->sub[w] = h->sub; out->seg[w] = h->seg; out->prim[w] = h->prim;
@@ -922,7 +974,7 @@ int orc_trace(const orc_scene* sc, const orc_params* p, const double pose_t[3], 
       }
     }
   }
-  for (int32_t j = 0; j <= nre; ++j) free(rows[j].v);
+  for (int32_t j = 0; j < nrows; ++j) free(rows[j].v);
   free(rows);
   return rc;
 }

@@ -39,6 +39,9 @@ typedef struct {
   int32_t thr_mode;        /* 0 absolute, 1 relative to the ping maximum */
   double thr;
   int32_t cross;           /* 1: add out/back cross-term multipath (isovelocity only) */
+  int64_t vol_n;           /* water-column scatterers (0: none; isovelocity only) */
+  double vol_lo[3], vol_hi[3];  /* their world-frame box [m] */
+  double vol_sv;           /* volume backscattering coefficient s_v [1/m] */
 } orc_params;
 
 typedef struct {
