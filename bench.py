@@ -504,6 +504,19 @@ def other_forms(torch, s, inputs, dev):
     out["c2_cross_fp32"] = {"value": 10 / (time.perf_counter() - t0), "unit": UNIT,
                             "hits": s.stats()["n_hits"], "note": "out/back cross-term multipath on"}
     s.set_option(SONAR_OPT_CROSS, 0)
+    # water-column reverberation: 10^6 scatterers in a box over the wall and the seabed
+    s.set_volume(1_000_000, (-2.0, -12.0, -10.5), (14.0, 12.0, -4.0), 1e-4)
+    for _ in range(3):
+        s.ping(poses[0], params, ssp, precision="fp32")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(10):
+        s.ping(poses[0], params, ssp, precision="fp32")
+    torch.cuda.synchronize()
+    out["c2_volume1m_fp32"] = {"value": 10 / (time.perf_counter() - t0), "unit": UNIT,
+                               "hits": s.stats()["n_hits"],
+                               "note": "10^6 water-column scatterers (s_v 1e-4 /m) on top of the mesh"}
+    s.set_volume(0)
     sc4, p4, poses4, ssp4 = inputs.workload("c4")
     s.upload(sc4)
     for prec in ("fp32", "bf16"):

@@ -109,7 +109,8 @@ typedef struct {
    | bounce), plus 0x40000000 for the cross term that returns straight (arriving from the
    hit) or 0x20000000 for its reciprocal (arriving along the route); point scatterers
    0x80000000 | (point << 8) | route, cross pairs 0xC0000000 | (point << 16) |
-   (out route << 8) | back route (SONAR_OPT_CROSS). */
+   (out route << 8) | back route (SONAR_OPT_CROSS); water-column scatterers
+   0xA0000000 | index (sonar_set_volume). */
 typedef struct {
   uint32_t key;
   int32_t prim;   /* triangle id, or -1 for a point scatterer */
@@ -206,6 +207,25 @@ SONAR_API int sonar_set_option(sonar_ctx* ctx, int32_t option, int64_t value);
 SONAR_API int sonar_scene_upload(sonar_ctx* ctx, const float* verts, int64_t n_verts, const int32_t* tris,
                        int64_t n_tris, const float* mu, const uint8_t* flags, const float* points,
                        const float* sigma, int64_t n_points, const double* planes, int64_t n_planes);
+
+/* Water-column (volume) reverberation (Sec. II.B volumetric backscatter paths): n point
+   scatterers frozen in the world frame, uniform in the box [lo, hi]. Scatterer i sits at
+   lo + (hi - lo) u, u the first three 24-bit fractions (word >> 8) / 2^24 of the 32-bit
+   pcg4d hash (Jarzynski & Olano 2020) of (i mod 2^32, i div 2^32, 0x564F4C,
+   seed ^ seed >> 32), seed the ping's params.seed. Each has the amplitude coefficient
+   sigma = sqrt(s_v V / n), V the box volume, so that the backscattering cross-section per
+   unit volume is s_v [1/m]; it echoes on its direct route when the straight leg to the
+   array is clear: amplitude sigma / L^2 exp(-2 alpha L), delay 2 L / c, no speckle phase
+   (the random positions make the reverberation speckle). Hit keys 0xA0000000 | i. */
+typedef struct {
+  int64_t n;          /* scatterers; 0 turns volume reverberation off; at most 2^28 */
+  double lo[3], hi[3];/* world-frame box [m], hi > lo on every axis */
+  double s_v;         /* volume backscattering coefficient [1/m], >= 0 */
+} sonar_volume;
+/* Sets the volume scatterers of the following pings (v NULL: none). SONAR_E_ARG for an
+   empty box, a negative s_v or n outside [0, 2^28]; a ping with a sound-speed gradient,
+   or with more than 2^21 point scatterers, returns SONAR_E_UNSUPPORTED while n > 0. */
+SONAR_API int sonar_set_volume(sonar_ctx* ctx, const sonar_volume* v);
 
 /* ---------------------------------------------------------------- pings */
 /* One ping. env: [n_beam_el][n_beam_az][n_range] f32 envelope |B| * TVG. cloud: up to

@@ -85,6 +85,8 @@ struct sonar_ctx {
   int raw_u = 0;      // 0: compressed synthesis; U > 0: raw series at U samples per cell + matched filter
   int bvh_opt = 0;    // 0: binned-SAH hierarchy (host build), 1: Morton-order LBVH (device build)
   int cross = 0;      // 1: out/back cross-term multipath
+  int64_t vol_n = 0;  // water-column scatterers per ping
+  double vol_lo[3] = {0, 0, 0}, vol_hi[3] = {0, 0, 0}, vol_sigma = 0.0;
   PtRoute* pt_route = nullptr;  // point-route records for cross pairing
   int64_t ws_pt_route = 0;
   int last_raw_u = 0;
@@ -307,6 +309,10 @@ int derive(sonar_ctx* ctx, const sonar_params* p, const sonar_ssp* ssp, double z
   if (d.n_routes > 256) return fail(ctx, SONAR_E_UNSUPPORTED, "too many point-scatterer routes");
   if (ctx->cross && d.curved)
     return fail(ctx, SONAR_E_UNSUPPORTED, "cross-term multipath needs an isovelocity profile");
+  if (ctx->vol_n > 0 && d.curved)
+    return fail(ctx, SONAR_E_UNSUPPORTED, "volume reverberation needs an isovelocity profile");
+  if (ctx->vol_n > 0 && ctx->has_scene && ctx->sc.n_points >= (1 << 21))
+    return fail(ctx, SONAR_E_UNSUPPORTED, "volume reverberation keys allow at most 2^21 point scatterers");
   d.wsum = 0.0;
   d.wmax = 0.0;
   for (int m = 0; m < d.M; ++m) {
@@ -324,6 +330,7 @@ int derive(sonar_ctx* ctx, const sonar_params* p, const sonar_ssp* ssp, double z
   // reflection adds two, and a point's routes pair up in every ordered combination
   d.hit_cap_per_ping = ctx->cross ? d.n_subrays * (1 + 3 * (int64_t)p->max_bounces) + npts * d.n_routes * d.n_routes
                                   : d.n_subrays * (1 + p->max_bounces) + npts * d.n_routes;
+  d.hit_cap_per_ping += ctx->vol_n;
   return SONAR_OK;
 }
 
@@ -569,7 +576,8 @@ int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, cons
   // clear, trace, scan, scatter, synthesis, convert, GEMM, peaks; points (and their cross
   // pairs); FP16 absmax and gain; raw phases
   const bool pairs = ctx->cross && ctx->sc.n_points > 0;
-  *kernels = 8 + (ctx->sc.n_points > 0 ? 1 : 0) + (pairs ? 1 : 0) + (fp16 ? 2 : 0) + (ctx->raw_u > 0 ? ctx->raw_u : 0);
+  *kernels = 8 + (ctx->sc.n_points > 0 ? 1 : 0) + (pairs ? 1 : 0) + (ctx->vol_n > 0 ? 1 : 0) + (fp16 ? 2 : 0) +
+             (ctx->raw_u > 0 ? ctx->raw_u : 0);
   // the poses the host has just written into the pinned staging record
   CU(cudaMemcpyAsync(ctx->poses, ctx->pose_host, sizeof(DevPose) * P, cudaMemcpyHostToDevice, st));
   mark(0);
@@ -627,6 +635,9 @@ int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, cons
   ta.n_routes = d.n_routes;
   ta.cross = ctx->cross;
   ta.pt_route = pairs ? ctx->pt_route : nullptr;
+  ta.vol_n = ctx->vol_n;
+  for (int k = 0; k < 3; ++k) { ta.vol_lo[k] = ctx->vol_lo[k]; ta.vol_hi[k] = ctx->vol_hi[k]; }
+  ta.vol_sigma = ctx->vol_sigma;
   ta.hits = ctx->hits;
   ta.bin_counts = ctx->counts;
   ta.dbg_tau = ctx->debug ? ctx->dbg_tau : nullptr;
@@ -636,6 +647,7 @@ int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, cons
   CU(launch_trace(ta, ctx->sm_count, st));
   CU(launch_points(ta, st));
   if (pairs) CU(launch_point_pairs(ta, st));
+  CU(launch_volume(ta, st));
   mark(1);
   CU(launch_bin(ctx->hits, ctx->n_hits, n_bins, ctx->counts, ctx->offsets, ctx->sorted, ctx->sorted_n, ctx->sm_count,
                 st));
@@ -972,6 +984,26 @@ int sonar_set_option(sonar_ctx* ctx, int32_t option, int64_t value) {
       ctx->tile_opt = (int)value;
       break;
     default: return fail(ctx, SONAR_E_ARG, "unknown option %d", option);
+  }
+  if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; ctx->gkey.clear(); }
+  return SONAR_OK;
+}
+
+int sonar_set_volume(sonar_ctx* ctx, const sonar_volume* v) {
+  if (!ctx) return SONAR_E_ARG;
+  if (!v || v->n == 0) {
+    ctx->vol_n = 0;
+  } else {
+    if (v->n < 0 || v->n > (1LL << 28)) return fail(ctx, SONAR_E_ARG, "volume scatterers: 0 to 2^28");
+    double V = 1.0;
+    for (int k = 0; k < 3; ++k) {
+      if (!(v->hi[k] > v->lo[k])) return fail(ctx, SONAR_E_ARG, "volume box must have hi > lo on every axis");
+      V *= v->hi[k] - v->lo[k];
+    }
+    if (!(v->s_v >= 0)) return fail(ctx, SONAR_E_ARG, "volume backscattering coefficient must be >= 0");
+    ctx->vol_n = v->n;
+    for (int k = 0; k < 3; ++k) { ctx->vol_lo[k] = v->lo[k]; ctx->vol_hi[k] = v->hi[k]; }
+    ctx->vol_sigma = sqrt(v->s_v * V / (double)v->n);
   }
   if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; ctx->gkey.clear(); }
   return SONAR_OK;

@@ -113,6 +113,9 @@ struct TraceArgs {
   int32_t n_routes;              // point-scatterer routes per point
   int32_t cross;                 // 1: out/back cross-term multipath
   PtRoute* pt_route;             // [n_pings][n_points][n_routes] with cross terms, else null
+  int64_t vol_n;                 // water-column scatterers per ping (0: none)
+  double vol_lo[3], vol_hi[3];   // their world-frame box
+  double vol_sigma;              // amplitude coefficient of each, sqrt(s_v V / n)
   HitRec* hits;
   int32_t* bin_counts;           // [n_pings * nr_pad] hits per first-tap row (zeroed by the caller)
   double* dbg_tau;               // nullable: FP64 delay per hit
@@ -179,6 +182,7 @@ cudaError_t launch_ray_table(double* dirs, float* dirs32, float* row_domega, int
 cudaError_t launch_trace(const TraceArgs& a, int sm_count, cudaStream_t st);
 cudaError_t launch_points(const TraceArgs& a, cudaStream_t st);
 cudaError_t launch_point_pairs(const TraceArgs& a, cudaStream_t st);
+cudaError_t launch_volume(const TraceArgs& a, cudaStream_t st);
 
 struct SynthArgs {
   const HitRec* hits_sorted;

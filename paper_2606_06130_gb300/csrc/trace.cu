@@ -248,7 +248,9 @@ __device__ __forceinline__ bool tri_exact(const float* tv, const DF3& o, const D
 // o32, d32: the origin and the direction in FP32 when the caller has them (nullptr:
 // converted here). An FP32 direction from FP32 operands differs from the FP64 one by
 // ~1e-7, far inside the traversal's slack.
-template <class V, class R>
+// ANY: an existence query (shadow legs): it returns the first triangle confirmed inside
+// the interval, whose distance it leaves unset.
+template <class V, class R, bool ANY = false>
 __device__ HitT<R> closest_hit(const DevScene& sc, const V& o, const V& d, R tmin, R tmax, int exclude, int* err,
                                const float* o32 = nullptr, const float* d32 = nullptr) {
   HitT<R> best;
@@ -330,6 +332,11 @@ __device__ HitT<R> closest_hit(const DevScene& sc, const V& o, const V& d, R tmi
       if (!definite) {
         if (!tri_exact(sc.triv + 9 * leaf, o, d, tmin, tmax, t64)) continue;
         exact = true;
+      }
+      if (ANY) {
+        best.prim = prim;
+        best.leaf = leaf;
+        return best;
       }
       bool take;
       if (best.prim < 0) {
@@ -608,7 +615,7 @@ __device__ void emit_cross(const TraceArgs& A, int ping, const DevPose& P, const
   if (!(dot(to_d3(dir), n) * vn > 0.0)) return;
   const D3 ud = d3(v.x / Ld, v.y / Ld, v.z / Ld);
   const D3 o = d3(P.t[0], P.t[1], P.t[2]);
-  const Hit sh = closest_hit(A.sc, o, ud, kEpsHit, Ld - kCrossClear, prim, A.err);
+  const Hit sh = closest_hit<D3, double, true>(A.sc, o, ud, kEpsHit, Ld - kCrossClear, prim, A.err);
   if (sh.prim >= 0) return;
   const float kd = (float)(fabs(vn) / Ld) * __ldg(&A.sc.tri_inv_n[leaf]);
   const float amp = gam * sqrtf(A.sc.tri_mu[leaf] * kd * dOmega) / (float)Ld * expf(-A.alpha32 * (L.hi + (float)Ld));
@@ -728,7 +735,7 @@ __device__ bool leg_clear(const TraceArgs& A, D3 a, D3 b) {
   double len = sqrt(dot(d, d));
   if (len <= 2e-6) return true;
   d = d3(d.x / len, d.y / len, d.z / len);
-  Hit h = closest_hit(A.sc, a, d, 1e-6, len - 1e-6, -1, A.err);
+  Hit h = closest_hit<D3, double, true>(A.sc, a, d, 1e-6, len - 1e-6, -1, A.err);
   return h.prim < 0;
 }
 
@@ -884,6 +891,35 @@ __global__ void k_point_pairs(TraceArgs A) {
   emit(A, ping, Ls / A.ssp_c0, (float)amp, 0.0, b.uy, b.uz, -1, key);
 }
 
+// Water-column reverberation (Sec. II.B volumetric backscatter paths): scatterer i of
+// the world-frame box sits at lo + (hi - lo) u, u the first three 24-bit fractions of
+// pcg4d(i mod 2^32, i div 2^32, 0x564F4C, seed) (products and sums rounded separately);
+// it echoes on its direct route when the leg is clear: amplitude sigma / L^2
+// exp(-2 alpha L), delay 2 L / c, no speckle phase. One thread per (ping, scatterer).
+__global__ void k_volume(TraceArgs A) {
+  pdl_wait();
+  const int64_t total = (int64_t)A.n_pings * A.vol_n;
+  const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gid >= total) return;
+  const int64_t i = gid % A.vol_n;
+  const int ping = (int)(gid / A.vol_n);
+  uint32_t h[4] = {(uint32_t)i, (uint32_t)((uint64_t)i >> 32), 0x564F4Cu, A.seed32};
+  pcg4d(h[0], h[1], h[2], h[3]);
+  double x[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+    x[k] = __dadd_rn(A.vol_lo[k], __dmul_rn(__dsub_rn(A.vol_hi[k], A.vol_lo[k]), u24(h[k])));
+  const DevPose& P = A.poses[ping];
+  const D3 o = d3(P.t[0], P.t[1], P.t[2]), xp = d3(x[0], x[1], x[2]);
+  const D3 dv = sub(xp, o);
+  const double L = sqrt(dot(dv, dv));
+  if (!(L > 0.0) || !(L <= A.L_stop)) return;
+  if (!leg_clear(A, o, xp)) return;
+  const double amp = A.vol_sigma / (L * L) * exp(-2.0 * A.alpha * L);
+  const D3 u = rot_t(P.R, d3(dv.x / L, dv.y / L, dv.z / L));
+  emit(A, ping, 2.0 * L / A.ssp_c0, (float)amp, 0.0, (float)u.y, (float)u.z, -1, 0xA0000000u | (uint32_t)i);
+}
+
 // Sonar-frame sub-ray directions (Sec. III Eq. 2-3 grid, cell-centred) with hashed
 // jitter inside 2x2 quarter cells, and the sub-ray solid angle per elevation row.
 __global__ void k_ray_table(double* dirs, float* dirs32, float* row_domega, int nra, int nre, int nsub, double hfov,
@@ -924,6 +960,14 @@ cudaError_t launch_point_pairs(const TraceArgs& a, cudaStream_t st) {
   const int64_t total = (int64_t)a.n_pings * a.sc.n_points * a.n_routes * a.n_routes;
   if (total == 0) return cudaSuccess;
   cudaError_t e = launch_pdl(k_point_pairs, dim3((unsigned)ceil_div(total, 128)), dim3(128), 0, st, a);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_volume(const TraceArgs& a, cudaStream_t st) {
+  const int64_t total = (int64_t)a.n_pings * a.vol_n;
+  if (total == 0) return cudaSuccess;
+  cudaError_t e = launch_pdl(k_volume, dim3((unsigned)ceil_div(total, 128)), dim3(128), 0, st, a);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }

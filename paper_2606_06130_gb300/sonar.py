@@ -60,6 +60,10 @@ class sonar_params(C.Structure):
                 ("thr_mode", C.c_int32), ("thr", C.c_double), ("taper", C.POINTER(C.c_float))]
 
 
+class sonar_volume(C.Structure):
+    _fields_ = [("n", C.c_int64), ("lo", C.c_double * 3), ("hi", C.c_double * 3), ("s_v", C.c_double)]
+
+
 class sonar_point(C.Structure):
     _fields_ = [("x", C.c_float), ("y", C.c_float), ("z", C.c_float), ("intensity", C.c_float),
                 ("beam", C.c_int32), ("bin", C.c_int32)]
@@ -91,6 +95,7 @@ _SIGS = {
     "sonar_destroy": (C.c_int, [C.c_void_p]),
     "sonar_last_error": (C.c_char_p, [C.c_void_p]),
     "sonar_set_option": (C.c_int, [C.c_void_p, C.c_int32, C.c_int64]),
+    "sonar_set_volume": (C.c_int, [C.c_void_p, C.POINTER(sonar_volume)]),
     "sonar_scene_upload": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p,
                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64]),
     "sonar_ping": (C.c_int, [C.c_void_p, C.POINTER(sonar_pose), C.POINTER(sonar_params), C.POINTER(sonar_ssp),
@@ -212,6 +217,11 @@ class Sonar:
 
     def set_option(self, option: int, value: int):
         self._check(lib().sonar_set_option(self.h, option, int(value)))
+
+    def set_volume(self, n: int, lo=(0.0, 0.0, 0.0), hi=(0.0, 0.0, 0.0), s_v: float = 0.0):
+        """Water-column scatterers of the following pings (n = 0: none)."""
+        v = sonar_volume(int(n), (C.c_double * 3)(*map(float, lo)), (C.c_double * 3)(*map(float, hi)), float(s_v))
+        self._check(lib().sonar_set_volume(self.h, C.byref(v)))
 
     def upload(self, scene):
         v = np.ascontiguousarray(scene.verts, np.float32)

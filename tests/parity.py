@@ -8,7 +8,8 @@ import oracle
 def oracle_keys(h: dict, n_sub: int) -> np.ndarray:
     """The C ABI's hit keys of the oracle's hits. Mesh: seg = bounce, plus 16 for the
     cross term that returns straight (key bit 30) or 32 for its reciprocal (bit 29).
-    Points: sub = route, or 0x10000 | out route << 8 | back route for a cross pair."""
+    Points: sub = route, or 0x10000 | out route << 8 | back route for a cross pair;
+    water-column scatterers: sub = 0x20000, ray = index."""
     ray = h["ray"].astype(np.uint64)
     sub = h["sub"].astype(np.uint64)
     seg = h["seg"].astype(np.uint64)
@@ -17,6 +18,7 @@ def oracle_keys(h: dict, n_sub: int) -> np.ndarray:
     mesh |= np.where(seg & u(16), u(0x40000000), u(0)) | np.where(seg & u(32), u(0x20000000), u(0))
     pts = np.where(sub & u(0x10000), u(0xC0000000) | (ray << u(16)) | (sub & u(0xFFFF)),
                    u(0x80000000) | (ray << u(8)) | sub)
+    pts = np.where(sub == u(0x20000), u(0xA0000000) | ray, pts)
     return np.where(h["prim"] >= 0, mesh, pts).astype(np.uint64)
 
 
