@@ -7,6 +7,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -87,6 +88,9 @@ struct sonar_ctx {
   int cross = 0;      // 1: out/back cross-term multipath
   int64_t vol_n = 0;  // water-column scatterers per ping
   double vol_lo[3] = {0, 0, 0}, vol_hi[3] = {0, 0, 0}, vol_sigma = 0.0;
+  int32_t* vol_order = nullptr;  // Morton order of the scatterers (null: index order)
+  int64_t vol_order_cap = 0;
+  std::vector<uint8_t> vol_key;  // (n, seed) the order was computed for
   PtRoute* pt_route = nullptr;  // point-route records for cross pairing
   int64_t ws_pt_route = 0;
   int last_raw_u = 0;
@@ -366,7 +370,48 @@ int make_map(sonar_ctx* ctx, CUtensorMap* m, void* base, int64_t rows, int64_t c
 }
 
 // (Re)build ray table, pulse table and steering matrix when their parameters change.
+template <typename T>
+int grow(sonar_ctx* ctx, T*& ptr, int64_t& cap, int64_t need, size_t elem, bool zero);
+
+// Water-column scatterers up to this count are processed in the Morton order of their
+// positions (a host sort at the first ping with a new count or seed); beyond it, in index
+// order.
+constexpr int64_t kVolSortMax = 1LL << 24;
+
+// 10-bit value spread to every third bit (Morton interleave).
+uint64_t spread3(uint32_t v) {
+  uint64_t x = v & 0x3FFu;
+  x = (x | x << 16) & 0x30000FFull;
+  x = (x | x << 8) & 0x300F00Full;
+  x = (x | x << 4) & 0x30C30C3ull;
+  x = (x | x << 2) & 0x9249249ull;
+  return x;
+}
+
 int ensure_tables(sonar_ctx* ctx, const sonar_params* p, const Derived& d) {
+  if (ctx->vol_n > 0 && ctx->vol_n <= kVolSortMax) {
+    // the scatterer positions are lo + (hi - lo) u with u from the hash words: their top
+    // 10 bits per axis give the Morton key, whatever the box
+    const uint32_t s32 = seed32(p->seed);
+    std::vector<uint8_t> kv;
+    key_add(kv, ctx->vol_n); key_add(kv, s32);
+    if (kv != ctx->vol_key || !ctx->vol_order) {
+      const int64_t n = ctx->vol_n;
+      std::vector<uint64_t> key((size_t)n);
+      for (int64_t i = 0; i < n; ++i) {
+        uint32_t x = (uint32_t)i, y = (uint32_t)((uint64_t)i >> 32), z = 0x564F4Cu, w = s32;
+        pcg4d(x, y, z, w);
+        key[(size_t)i] = ((spread3(x >> 22) | spread3(y >> 22) << 1 | spread3(z >> 22) << 2) << 32) | (uint64_t)i;
+      }
+      std::sort(key.begin(), key.end());
+      std::vector<int32_t> ord((size_t)n);
+      for (int64_t j = 0; j < n; ++j) ord[(size_t)j] = (int32_t)(key[(size_t)j] & 0xFFFFFFFFull);
+      int rc;
+      if ((rc = grow(ctx, ctx->vol_order, ctx->vol_order_cap, n, sizeof(int32_t), false))) return rc;
+      CU(cudaMemcpy(ctx->vol_order, ord.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice));
+      ctx->vol_key = kv;
+    }
+  }
   std::vector<uint8_t> k;
   key_add(k, p->n_ray_az); key_add(k, p->n_ray_el); key_add(k, p->n_sub);
   key_add(k, p->hfov_rad); key_add(k, p->vfov_rad); key_add(k, p->seed);
@@ -638,6 +683,7 @@ int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, cons
   ta.vol_n = ctx->vol_n;
   for (int k = 0; k < 3; ++k) { ta.vol_lo[k] = ctx->vol_lo[k]; ta.vol_hi[k] = ctx->vol_hi[k]; }
   ta.vol_sigma = ctx->vol_sigma;
+  ta.vol_order = ctx->vol_n > 0 && ctx->vol_n <= kVolSortMax ? ctx->vol_order : nullptr;
   ta.hits = ctx->hits;
   ta.bin_counts = ctx->counts;
   ta.dbg_tau = ctx->debug ? ctx->dbg_tau : nullptr;
@@ -853,6 +899,7 @@ int run(sonar_ctx* ctx, const sonar_pose* poses, int P, const sonar_params* p, c
       key_add(k, ssp->n_nodes);
       for (int i = 0; i < ssp->n_nodes; ++i) { key_add(k, ssp->c[i]); if (ssp->z) key_add(k, ssp->z[i]); }
     }
+    key_add(k, ctx->vol_order);
     key_add(k, ctx->hits); key_add(k, ctx->S); key_add(k, ctx->x_hi); key_add(k, ctx->y_hi); key_add(k, ctx->keys);
     if (!ctx->gexec || k != ctx->gkey) {
       if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; }
@@ -1032,7 +1079,7 @@ int sonar_destroy(sonar_ctx* c) {
   if (c->pose_host) cudaFreeHost(c->pose_host);
   if (c->n_cloud_host) cudaFreeHost(c->n_cloud_host);
   if (c->counters_host) cudaFreeHost(c->counters_host);
-  dfree(c->pt_route);
+  dfree(c->pt_route); dfree(c->vol_order);
   dfree(c->poses); dfree(c->hits); dfree(c->sorted); dfree(c->sorted_n); dfree(c->dbg_tau);
   dfree(c->n_hits);
   dfree(c->counts); dfree(c->offsets); dfree(c->S); dfree(c->S_raw); dfree(c->ptab); dfree(c->x_hi); dfree(c->x_lo); dfree(c->gain);

@@ -116,6 +116,7 @@ struct TraceArgs {
   int64_t vol_n;                 // water-column scatterers per ping (0: none)
   double vol_lo[3], vol_hi[3];   // their world-frame box
   double vol_sigma;              // amplitude coefficient of each, sqrt(s_v V / n)
+  const int32_t* vol_order;      // [vol_n] processing order (Morton order of the positions), or null
   HitRec* hits;
   int32_t* bin_counts;           // [n_pings * nr_pad] hits per first-tap row (zeroed by the caller)
   double* dbg_tau;               // nullable: FP64 delay per hit

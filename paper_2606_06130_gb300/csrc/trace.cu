@@ -895,13 +895,15 @@ __global__ void k_point_pairs(TraceArgs A) {
 // the world-frame box sits at lo + (hi - lo) u, u the first three 24-bit fractions of
 // pcg4d(i mod 2^32, i div 2^32, 0x564F4C, seed) (products and sums rounded separately);
 // it echoes on its direct route when the leg is clear: amplitude sigma / L^2
-// exp(-2 alpha L), delay 2 L / c, no speckle phase. One thread per (ping, scatterer).
+// exp(-2 alpha L), delay 2 L / c, no speckle phase. One thread per (ping, scatterer),
+// taken in the Morton order of the positions when the host has sorted them, so that the
+// shadow legs of a warp run to neighbouring points and traverse the same nodes.
 __global__ void k_volume(TraceArgs A) {
   pdl_wait();
   const int64_t total = (int64_t)A.n_pings * A.vol_n;
   const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (gid >= total) return;
-  const int64_t i = gid % A.vol_n;
+  const int64_t i = A.vol_order ? (int64_t)A.vol_order[gid % A.vol_n] : gid % A.vol_n;
   const int ping = (int)(gid / A.vol_n);
   uint32_t h[4] = {(uint32_t)i, (uint32_t)((uint64_t)i >> 32), 0x564F4Cu, A.seed32};
   pcg4d(h[0], h[1], h[2], h[3]);
@@ -910,14 +912,22 @@ __global__ void k_volume(TraceArgs A) {
   for (int k = 0; k < 3; ++k)
     x[k] = __dadd_rn(A.vol_lo[k], __dmul_rn(__dsub_rn(A.vol_hi[k], A.vol_lo[k]), u24(h[k])));
   const DevPose& P = A.poses[ping];
-  const D3 o = d3(P.t[0], P.t[1], P.t[2]), xp = d3(x[0], x[1], x[2]);
-  const D3 dv = sub(xp, o);
+  const D3 o = d3(P.t[0], P.t[1], P.t[2]);
+  const D3 dv = d3(x[0] - o.x, x[1] - o.y, x[2] - o.z);
   const double L = sqrt(dot(dv, dv));
   if (!(L > 0.0) || !(L <= A.L_stop)) return;
-  if (!leg_clear(A, o, xp)) return;
-  const double amp = A.vol_sigma / (L * L) * exp(-2.0 * A.alpha * L);
-  const D3 u = rot_t(P.R, d3(dv.x / L, dv.y / L, dv.z / L));
-  emit(A, ping, 2.0 * L / A.ssp_c0, (float)amp, 0.0, (float)u.y, (float)u.z, -1, 0xA0000000u | (uint32_t)i);
+  // FP64 issues at ~2 operations per clock per SM on this part: only the leg direction
+  // (for the exact triangle tests) and the delay stay in FP64, with one reciprocal in
+  // place of three divisions; the amplitude and the arrival direction need only FP32
+  const double il = 1.0 / L;
+  const D3 d = d3(dv.x * il, dv.y * il, dv.z * il);
+  if (L > 2e-6 && closest_hit<D3, double, true>(A.sc, o, d, 1e-6, L - 1e-6, -1, A.err).prim >= 0) return;
+  const float Lf = (float)L;
+  const float amp = (float)A.vol_sigma / (Lf * Lf) * expf(-2.0f * A.alpha32 * Lf);
+  const float dx = (float)d.x, dy = (float)d.y, dz = (float)d.z;
+  const float uy = P.R32[1] * dx + P.R32[4] * dy + P.R32[7] * dz;  // (R^T d).y
+  const float uz = P.R32[2] * dx + P.R32[5] * dy + P.R32[8] * dz;  // (R^T d).z
+  emit(A, ping, L * A.two_inv_c0, amp, 0.0, uy, uz, -1, 0xA0000000u | (uint32_t)i);
 }
 
 // Sonar-frame sub-ray directions (Sec. III Eq. 2-3 grid, cell-centred) with hashed
