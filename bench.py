@@ -315,6 +315,24 @@ def run_ours(args, ws, rank, local):
     for _ in range(k_e2e):
         s.ping_batch([pose], params, ssp, precision=args.precision, env=env_h[None], cloud=cloud_h[None], cloud_cap=nb)
     torch.cuda.synchronize()
+    e2e_sync_s = max_over_ranks(time.perf_counter() - e0, ws)
+    # the streaming call: sonar_ping_async with two calls in flight, each into its own
+    # pinned host buffers; the envelope goes to the host by copy engine while the next
+    # ping computes. Every step's pose upload and envelope/cloud/count read-back is inside
+    # the timed region (the final wait retires the last two).
+    env_a = [torch.empty(env.shape, dtype=torch.float32, pin_memory=True) for _ in range(2)]
+    cloud_a = [torch.empty((nb, 6), dtype=torch.int32, pin_memory=True) for _ in range(2)]
+    for i in range(4):
+        s.ping_async([pose], params, ssp, precision=args.precision, env=env_a[i & 1][None], cloud=cloud_a[i & 1][None],
+                     cloud_cap=nb)
+    s.wait()
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    for i in range(k_e2e):
+        s.ping_async([pose], params, ssp, precision=args.precision, env=env_a[i & 1][None], cloud=cloud_a[i & 1][None],
+                     cloud_cap=nb)
+    s.wait()
+    torch.cuda.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - e0, ws)
 
     # other forms (same run): BF16 single ping, BF16 64-ping trajectory batch
@@ -376,9 +394,13 @@ def run_ours(args, ws, rank, local):
                      "around each step, L2 flushed between steps outside the events",
            "eager_stage_timed": {"value": whole_job_rate(ws, args.steps, eager_ms / 1e3), "unit": UNIT,
                                  "note": "same steps with per-stage events, kernels launched one by one"},
+           "e2e_sync": {"value": whole_job_rate(ws, k_e2e, e2e_sync_s), "unit": UNIT,
+                        "path": "sonar_ping_batch per step (returns when the outputs are complete), envelope "
+                                "written through the device mapping of pinned host memory"},
            "e2e": {"value": whole_job_rate(ws, k_e2e, e2e_s), "unit": UNIT, "h2d_bytes_per_step": 192,
                    "d2h_bytes_per_step": int(env.numel() * 4 + nb * 24 + 8), "steps": k_e2e,
-                   "path": "sonar_ping_batch (default graph replay) with pinned host env and cloud"},
+                   "path": "sonar_ping_async (two calls in flight, graph replay) into pinned host env and "
+                           "cloud buffers; the envelope leaves by copy engine while the next ping computes"},
            "clocks": clk,
            "error_vs_oracle": err,
            "forms": forms,

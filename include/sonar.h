@@ -248,6 +248,25 @@ SONAR_API int sonar_ping_batch(sonar_ctx* ctx, const sonar_pose* poses, int32_t 
                      const sonar_params* params, const sonar_ssp* ssp, float* env,
                      sonar_point* cloud, int64_t cloud_cap_per_ping, int64_t* n_cloud);
 
+/* Asynchronous pings for a stream of poses known one step at a time: enqueues what
+   sonar_ping_batch computes and returns without waiting for it. env and cloud must be
+   device memory or pinned host memory (cudaHostAlloc / cudaHostRegister; other host
+   memory: SONAR_E_ARG). An envelope bound for pinned host memory is written to a device
+   staging buffer and copied by a copy engine, overlapping the next ping's ray casting
+   and synthesis. At most two calls are in flight: a call first waits for the one made two
+   calls earlier and retires it (fills its n_cloud, host [n_pings], and returns that
+   call's error, if any, in place of its own SONAR_OK). The outputs of a call are complete,
+   and must not be touched before, once it is retired: by the second following
+   sonar_ping_async, by sonar_wait, or by any other call on the context (all of which
+   retire every call in flight first). The context's cuda_stream is ordered after a
+   call's outputs once the call is retired (earlier, it would chain the next call's work
+   behind this call's copy). */
+SONAR_API int sonar_ping_async(sonar_ctx* ctx, const sonar_pose* poses, int32_t n_pings,
+                     const sonar_params* params, const sonar_ssp* ssp, float* env,
+                     sonar_point* cloud, int64_t cloud_cap_per_ping, int64_t* n_cloud);
+/* Retires every asynchronous call in flight, oldest first; returns the first error. */
+SONAR_API int sonar_wait(sonar_ctx* ctx);
+
 /* ---------------------------------------------------------------- debug / parity */
 /* Hits of the last call (requires SONAR_OPT_DEBUG). host_out [cap]; *n = total. */
 SONAR_API int sonar_get_hits(sonar_ctx* ctx, sonar_hit* host_out, int64_t cap, int64_t* n);

@@ -20,11 +20,15 @@ namespace {
 // Zeroes, in one launch, every buffer a call accumulates into: the element echoes S
 // (16-byte stores), the per-row hit histogram, the per-beam peak keys and ping maxima,
 // the hit counter and the error bits.
+// Also brings the poses in: it reads the pinned pose record through its device mapping
+// (pose_src, 16-byte words), so the pipeline has no copy-engine node that could queue
+// behind an earlier ping's envelope copy.
 __global__ void k_clear(float2* S, int64_t n_s, float2* S2, int64_t n_s2, int32_t* counts, int32_t n_bins,
                         unsigned long long* keys, int64_t n_keys, unsigned* pmax, int n_p, unsigned long long* n_hits,
-                        int* err) {
+                        int* err, const uint4* pose_src, uint4* pose_dst, int n_pose16) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (int64_t i = t; i < n_pose16; i += stride) pose_dst[i] = pose_src[i];
   float4* S4 = reinterpret_cast<float4*>(S);  // cudaMalloc alignment
   for (int64_t i = t; i < n_s / 2; i += stride) S4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
   if ((n_s & 1) && t == 0) S[n_s - 1] = make_float2(0.f, 0.f);
@@ -68,6 +72,31 @@ struct Derived {
   double c_ref, dr, dt, t0, hw, T_stop, pitch_over_lambda, ssp_z0, ssp_c0, ssp_g, wsum, wmax;
   int taps, nr, nr_pad, nr_x, M, k_pad, nb, nb_pad, tile_n, n_phase, n_blank, n_routes, curved;
   int64_t n_subrays, hit_cap_per_ping;
+};
+
+// One of the two in-flight slots of asynchronous pings: its own pinned pose record,
+// point counts and counter words, device envelope staging and captured graph, reused
+// only after the slot's previous ping has finished.
+struct AsyncSlot {
+  bool busy = false;
+  DevPose* pose_host = nullptr;               // pinned [p_cap], mapped
+  DevPose* pose_map = nullptr;
+  long long* n_cloud_host = nullptr;          // pinned [p_cap], mapped
+  long long* n_cloud_map = nullptr;
+  unsigned long long* counters_host = nullptr;  // pinned [2]: hit count, error bits; mapped
+  unsigned long long* counters_map = nullptr;
+  int p_cap = 0;
+  float* env_stage = nullptr;
+  int64_t env_cap = 0;
+  cudaEvent_t ev_gemm = nullptr, ev_done = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<uint8_t> gkey;
+  int graph_kernels = 0;
+  // what retiring the ping hands back
+  int64_t* n_cloud_user = nullptr;
+  int P = 0;
+  int64_t cloud_cap = 0;
+  bool cloud_given = false;
 };
 
 }  // namespace
@@ -131,6 +160,7 @@ struct sonar_ctx {
   // workspaces
   int p_cap = 0;
   DevPose* pose_host = nullptr;  // pinned [p]: rotation and position of each ping
+  DevPose* pose_map = nullptr;   // its device mapping
   DevPose* poses = nullptr;
   HitRec* hits = nullptr;
   HitRec* sorted = nullptr;
@@ -164,6 +194,11 @@ struct sonar_ctx {
   // graph
   cudaGraphExec_t gexec = nullptr;
   std::vector<uint8_t> gkey;
+
+  // asynchronous pings: two slots and the copy-engine stream of their envelopes
+  AsyncSlot aslot[2];
+  int next_slot = 0;
+  cudaStream_t copy_stream = nullptr;
 
   // last call
   int last_p = 0;
@@ -506,6 +541,7 @@ int ensure_workspace(sonar_ctx* ctx, int P, const Derived& d) {
     ctx->n_cloud_host = nullptr;
     dfree(ctx->poses); dfree(ctx->gain); dfree(ctx->pmax); dfree(ctx->n_cloud_dev);
     CU(cudaMallocHost(&ctx->pose_host, sizeof(DevPose) * P));
+    CU(cudaHostGetDevicePointer((void**)&ctx->pose_map, ctx->pose_host, 0));
     CU(cudaMallocHost(&ctx->n_cloud_host, sizeof(long long) * P));
     CU(cudaHostGetDevicePointer((void**)&ctx->n_cloud_map, ctx->n_cloud_host, 0));
     CU(cudaMalloc(&ctx->poses, sizeof(DevPose) * P));
@@ -604,9 +640,12 @@ struct Outputs {
   float* env;               // where the kernels write
   sonar_point* cloud;
   int64_t cap;
-  float* env_host;          // staged outputs: the caller's host buffers, else nullptr
-  sonar_point* cloud_host;
+  float* env_host;          // staged outputs copied back in the pipeline: the caller's host
+  sonar_point* cloud_host;  // buffers, else nullptr
   int64_t env_elems;
+  const DevPose* pose_src;              // device mapping of the pinned poses the first kernel reads
+  long long* n_cloud_map;               // device mappings of the pinned per-ping point
+  unsigned long long* counters_map;     // counts and of the hit count / error words
 };
 
 // Enqueue the whole pipeline for P pings on the context stream (graph-capturable:
@@ -624,14 +663,15 @@ int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, cons
   *kernels = 8 + (ctx->sc.n_points > 0 ? 1 : 0) + (pairs ? 1 : 0) + (ctx->vol_n > 0 ? 1 : 0) + (fp16 ? 2 : 0) +
              (ctx->raw_u > 0 ? ctx->raw_u : 0);
   // the poses the host has just written into the pinned staging record
-  CU(cudaMemcpyAsync(ctx->poses, ctx->pose_host, sizeof(DevPose) * P, cudaMemcpyHostToDevice, st));
   mark(0);
   // every buffer that starts at zero is cleared up front, in one launch, so the kernels
   // run back to back
   const int32_t n_bins = P * d.nr_pad;
   k_clear<<<4 * ctx->sm_count, 256, 0, st>>>(ctx->S, ctx->s_elems, ctx->raw_u > 0 ? ctx->S_raw : nullptr,
                                              ctx->s_elems * ctx->raw_u, ctx->counts, n_bins, ctx->keys,
-                                             (int64_t)P * d.nb, ctx->pmax, P, ctx->n_hits, ctx->err_dev);
+                                             (int64_t)P * d.nb, ctx->pmax, P, ctx->n_hits, ctx->err_dev,
+                                             reinterpret_cast<const uint4*>(o.pose_src),
+                                             reinterpret_cast<uint4*>(ctx->poses), (int)(sizeof(DevPose) / 16) * P);
   CU(cudaGetLastError());
   TraceArgs ta;
   memset(&ta, 0, sizeof(ta));
@@ -809,8 +849,8 @@ int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, cons
   pa.cloud = o.cloud;
   pa.cap = o.cap;
   pa.n_cloud = ctx->n_cloud_dev;
-  pa.n_cloud_host = ctx->n_cloud_map;
-  pa.counters_host = ctx->counters_map;
+  pa.n_cloud_host = o.n_cloud_map;
+  pa.counters_host = o.counters_map;
   pa.n_hits = ctx->n_hits;
   pa.err = ctx->err_dev;
   CU(launch_peaks(pa, st));
@@ -824,10 +864,8 @@ int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, cons
   return SONAR_OK;
 }
 
-int run(sonar_ctx* ctx, const sonar_pose* poses, int P, const sonar_params* p, const sonar_ssp* ssp, float* env,
-        sonar_point* cloud, int64_t cloud_cap, int64_t* n_cloud) {
-  if (!ctx) return SONAR_E_ARG;
-  ctx->err.clear();
+int check_call(sonar_ctx* ctx, const sonar_pose* poses, int P, const sonar_params* p, const sonar_ssp* ssp,
+               const float* env, const sonar_point* cloud, int64_t cloud_cap) {
   if (!poses || P < 1) return fail(ctx, SONAR_E_ARG, "need at least one pose");
   if (!env) return fail(ctx, SONAR_E_ARG, "env is NULL");
   if (cloud_cap < 0 || (cloud_cap > 0 && !cloud)) return fail(ctx, SONAR_E_ARG, "bad cloud buffer");
@@ -840,7 +878,63 @@ int run(sonar_ctx* ctx, const sonar_pose* poses, int P, const sonar_params* p, c
     if (!(n2 > 1e-12) || !isfinite(poses[i].t[0] + poses[i].t[1] + poses[i].t[2]))
       return fail(ctx, SONAR_E_ARG, "pose %d is not finite or has a zero quaternion", i);
   }
+  return SONAR_OK;
+}
+
+// Error bits and point counts of a finished call, as the caller sees them.
+int report(sonar_ctx* ctx, int errw, const long long* n_cloud_host, int P, int64_t* n_cloud, int64_t cloud_cap,
+           bool cloud_given) {
+  if (errw & kErrTimeout) return fail(ctx, SONAR_E_TIMEOUT, "a device-side wait exceeded its limit");
+  if (errw & kErrLoop) return fail(ctx, SONAR_E_TIMEOUT, "a ray-marching loop exceeded its step limit");
+  if (errw & kErrStack) return fail(ctx, SONAR_E_TIMEOUT, "BVH traversal stack overflow");
+  if (errw & kErrCapacity) return fail(ctx, SONAR_E_CAPACITY, "hit capacity %lld exceeded", (long long)ctx->hit_cap);
+  int over = 0;
+  for (int i = 0; i < P; ++i) {
+    if (n_cloud) n_cloud[i] = n_cloud_host[i];
+    if (n_cloud_host[i] > cloud_cap) over = 1;
+  }
+  if (over && cloud_given)
+    return fail(ctx, SONAR_E_CAPACITY, "cloud needs more than %lld points per ping", (long long)cloud_cap);
+  return SONAR_OK;
+}
+
+// Captured graphs bake in options and buffers: they are rebuilt after an option, the
+// volume scatterers or the scene change.
+void drop_graphs(sonar_ctx* ctx) {
+  if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; ctx->gkey.clear(); }
+  for (AsyncSlot& sl : ctx->aslot)
+    if (sl.gexec) { cudaGraphExecDestroy(sl.gexec); sl.gexec = nullptr; sl.gkey.clear(); }
+}
+
+// Waits for an asynchronous slot's ping and hands its counts and errors back.
+int retire(sonar_ctx* ctx, AsyncSlot& sl) {
+  if (!sl.busy) return SONAR_OK;
+  sl.busy = false;
+  CU(cudaEventSynchronize(sl.ev_done));
+  CU(cudaStreamWaitEvent(ctx->user_stream, sl.ev_done, 0));
+  ctx->stats.n_hits = (int64_t)sl.counters_host[0];
+  return report(ctx, (int)sl.counters_host[1], sl.n_cloud_host, sl.P, sl.n_cloud_user, sl.cloud_cap, sl.cloud_given);
+}
+
+// Retires every asynchronous ping in flight, oldest first; returns the first error.
+int drain(sonar_ctx* ctx) {
+  int first = SONAR_OK;
+  for (int k = 0; k < 2; ++k) {
+    const int rc = retire(ctx, ctx->aslot[(ctx->next_slot + k) & 1]);
+    if (rc && first == SONAR_OK) first = rc;
+  }
+  return first;
+}
+
+int run(sonar_ctx* ctx, const sonar_pose* poses, int P, const sonar_params* p, const sonar_ssp* ssp, float* env,
+        sonar_point* cloud, int64_t cloud_cap, int64_t* n_cloud) {
+  if (!ctx) return SONAR_E_ARG;
+  ctx->err.clear();
+  int rc = check_call(ctx, poses, P, p, ssp, env, cloud, cloud_cap);
+  if (rc) return rc;
   CU(cudaSetDevice(ctx->device));
+  // asynchronous pings still in flight finish first (and report their errors here)
+  if ((rc = drain(ctx))) return rc;
   // the work stream starts after everything already queued on the caller's stream
   CU(cudaEventRecord(ctx->ev_in, ctx->user_stream));
   CU(cudaStreamWaitEvent(ctx->stream, ctx->ev_in, 0));
@@ -880,6 +974,9 @@ int run(sonar_ctx* ctx, const sonar_pose* poses, int P, const sonar_params* p, c
     CU(cudaHostGetDevicePointer((void**)&ctx->counters_map, ctx->counters_host, 0));
   }
   ctx->counters_host[1] = 0;
+  o.pose_src = ctx->pose_map;
+  o.n_cloud_map = ctx->n_cloud_map;
+  o.counters_map = ctx->counters_map;
 
   // the graph's first node copies these to the device
   for (int i = 0; i < P; ++i) ctx->pose_host[i] = dev_pose(poses[i]);
@@ -944,18 +1041,136 @@ int run(sonar_ctx* ctx, const sonar_pose* poses, int P, const sonar_params* p, c
     ctx->stats.ms_beamform = t[4];
     ctx->stats.ms_peaks = t[5];
   }
-  if (errw & kErrTimeout) return fail(ctx, SONAR_E_TIMEOUT, "a device-side wait exceeded its limit");
-  if (errw & kErrLoop) return fail(ctx, SONAR_E_TIMEOUT, "a ray-marching loop exceeded its step limit");
-  if (errw & kErrStack) return fail(ctx, SONAR_E_TIMEOUT, "BVH traversal stack overflow");
-  if (errw & kErrCapacity) return fail(ctx, SONAR_E_CAPACITY, "hit capacity %lld exceeded", (long long)ctx->hit_cap);
-  int over = 0;
-  for (int i = 0; i < P; ++i) {
-    if (n_cloud) n_cloud[i] = ctx->n_cloud_host[i];
-    if (ctx->n_cloud_host[i] > cloud_cap) over = 1;
+  return report(ctx, errw, ctx->n_cloud_host, P, n_cloud, cloud_cap, cloud_cap > 0 || cloud);
+}
+
+// Asynchronous pings (sonar_ping_async): the pipeline of `run` on one of two slots. The
+// slot's previous ping (two submissions back) is retired first, so at most two pings
+// are in flight. An envelope bound for pinned host memory is written to the slot's
+// device staging and copied by a copy engine on the copy stream, overlapping the next
+// ping's ray casting and synthesis instead of slowing the GEMM epilogue with writes
+// across the host link.
+int run_async(sonar_ctx* ctx, const sonar_pose* poses, int P, const sonar_params* p, const sonar_ssp* ssp,
+              float* env, sonar_point* cloud, int64_t cloud_cap, int64_t* n_cloud) {
+  if (!ctx) return SONAR_E_ARG;
+  ctx->err.clear();
+  int rc = check_call(ctx, poses, P, p, ssp, env, cloud, cloud_cap);
+  if (rc) return rc;
+  CU(cudaSetDevice(ctx->device));
+  void* env_d = nullptr;
+  void* cloud_d = nullptr;
+  const Mem env_kind = classify(env, &env_d);
+  const Mem cloud_kind = cloud_cap == 0 ? Mem::Device : classify(cloud, &cloud_d);
+  if (env_kind == Mem::Host || cloud_kind == Mem::Host)
+    return fail(ctx, SONAR_E_ARG, "asynchronous pings need device or pinned host outputs");
+  const int s = ctx->next_slot;
+  AsyncSlot& sl = ctx->aslot[s];
+  const int rc_prev = retire(ctx, sl);
+  ctx->next_slot ^= 1;
+  CU(cudaEventRecord(ctx->ev_in, ctx->user_stream));
+  CU(cudaStreamWaitEvent(ctx->stream, ctx->ev_in, 0));
+  Derived d;
+  if ((rc = derive(ctx, p, ssp, poses[0].t[2], P, d))) return rc;
+  if ((int64_t)P * d.nr_pad + 1 > (1LL << 31) - 1) return fail(ctx, SONAR_E_UNSUPPORTED, "batch too large");
+  if ((rc = ensure_tables(ctx, p, d))) return rc;
+  if ((rc = ensure_workspace(ctx, P, d))) return rc;
+  if (P > sl.p_cap) {
+    if (sl.pose_host) cudaFreeHost(sl.pose_host);
+    if (sl.n_cloud_host) cudaFreeHost(sl.n_cloud_host);
+    sl.pose_host = nullptr;
+    sl.n_cloud_host = nullptr;
+    sl.p_cap = 0;
+    CU(cudaMallocHost(&sl.pose_host, sizeof(DevPose) * P));
+    CU(cudaHostGetDevicePointer((void**)&sl.pose_map, sl.pose_host, 0));
+    CU(cudaMallocHost(&sl.n_cloud_host, sizeof(long long) * P));
+    CU(cudaHostGetDevicePointer((void**)&sl.n_cloud_map, sl.n_cloud_host, 0));
+    sl.p_cap = P;
   }
-  if (over && (cloud_cap > 0 || cloud))
-    return fail(ctx, SONAR_E_CAPACITY, "cloud needs more than %lld points per ping", (long long)cloud_cap);
-  return SONAR_OK;
+  if (!sl.counters_host) {
+    CU(cudaMallocHost(&sl.counters_host, 2 * sizeof(unsigned long long)));
+    CU(cudaHostGetDevicePointer((void**)&sl.counters_map, sl.counters_host, 0));
+  }
+  if (!sl.ev_done) {
+    CU(cudaEventCreateWithFlags(&sl.ev_done, cudaEventDisableTiming));
+    CU(cudaEventCreateWithFlags(&sl.ev_gemm, cudaEventDisableTiming));
+  }
+  if (!ctx->copy_stream) CU(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+  const int64_t env_elems = (int64_t)P * d.nb * d.nr;
+  const bool staged = env_kind == Mem::Mapped;
+  Outputs o;
+  o.env = static_cast<float*>(env_d);
+  if (staged) {
+    if ((rc = grow(ctx, sl.env_stage, sl.env_cap, env_elems, sizeof(float), false))) return rc;
+    o.env = sl.env_stage;
+  }
+  o.env_host = nullptr;
+  o.env_elems = env_elems;
+  o.cap = cloud_cap;
+  o.cloud = cloud_cap == 0 ? cloud : static_cast<sonar_point*>(cloud_d);
+  o.cloud_host = nullptr;
+  o.pose_src = sl.pose_map;
+  o.n_cloud_map = sl.n_cloud_map;
+  o.counters_map = sl.counters_map;
+  sl.counters_host[0] = 0;
+  sl.counters_host[1] = 0;
+  for (int i = 0; i < P; ++i) sl.pose_host[i] = dev_pose(poses[i]);
+
+  int kernels = 0;
+  if (ctx->use_graph && !ctx->timing) {
+    std::vector<uint8_t> k;
+    key_add(k, P); key_add(k, *p); key_add(k, o.env); key_add(k, o.cloud); key_add(k, o.cap);
+    key_add(k, sl.pose_host); key_add(k, sl.counters_host); key_add(k, sl.n_cloud_host);
+    key_add(k, ctx->debug); key_add(k, ctx->synth_opt); key_add(k, ctx->scene_version);
+    key_add(k, ctx->raw_u);
+    key_add(k, d.c_ref);
+    if (ssp) {
+      key_add(k, ssp->n_nodes);
+      for (int i = 0; i < ssp->n_nodes; ++i) { key_add(k, ssp->c[i]); if (ssp->z) key_add(k, ssp->z[i]); }
+    }
+    key_add(k, ctx->vol_order);
+    key_add(k, ctx->hits); key_add(k, ctx->S); key_add(k, ctx->x_hi); key_add(k, ctx->y_hi); key_add(k, ctx->keys);
+    if (!sl.gexec || k != sl.gkey) {
+      if (sl.gexec) { cudaGraphExecDestroy(sl.gexec); sl.gexec = nullptr; }
+      cudaGraph_t g;
+      CU(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+      rc = enqueue(ctx, P, p, d, o, &sl.graph_kernels);
+      cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
+      if (rc) { if (ce == cudaSuccess) cudaGraphDestroy(g); return rc; }
+      CU(ce);
+      cudaError_t ie = cudaGraphInstantiate(&sl.gexec, g, 0);
+      cudaGraphDestroy(g);
+      CU(ie);
+      sl.gkey = k;
+    }
+    CU(cudaGraphLaunch(sl.gexec, ctx->stream));
+    kernels = sl.graph_kernels;
+  } else {
+    if ((rc = enqueue(ctx, P, p, d, o, &kernels))) return rc;
+  }
+  if (staged) {
+    CU(cudaEventRecord(sl.ev_gemm, ctx->stream));
+    CU(cudaStreamWaitEvent(ctx->copy_stream, sl.ev_gemm, 0));
+    CU(cudaMemcpyAsync(env, sl.env_stage, sizeof(float) * env_elems, cudaMemcpyDeviceToHost, ctx->copy_stream));
+    CU(cudaEventRecord(sl.ev_done, ctx->copy_stream));
+  } else {
+    CU(cudaEventRecord(sl.ev_done, ctx->stream));
+  }
+  // (the caller's stream is ordered after this call's outputs when the call is retired:
+  // ordering it now would chain the next call's work behind this call's envelope copy)
+  sl.busy = true;
+  sl.P = P;
+  sl.n_cloud_user = n_cloud;
+  sl.cloud_cap = cloud_cap;
+  sl.cloud_given = cloud_cap > 0 || cloud;
+  ctx->last_p = P;
+  ctx->last_d = d;
+  ctx->last_raw_u = ctx->raw_u;
+  ctx->last_params = *p;
+  ctx->stats.hit_capacity = ctx->hit_cap;
+  ctx->stats.n_pings = P;
+  ctx->stats.taps = d.taps;
+  ctx->stats.kernels = kernels;
+  return rc_prev;
 }
 
 }  // namespace
@@ -1032,7 +1247,7 @@ int sonar_set_option(sonar_ctx* ctx, int32_t option, int64_t value) {
       break;
     default: return fail(ctx, SONAR_E_ARG, "unknown option %d", option);
   }
-  if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; ctx->gkey.clear(); }
+  drop_graphs(ctx);
   return SONAR_OK;
 }
 
@@ -1052,7 +1267,7 @@ int sonar_set_volume(sonar_ctx* ctx, const sonar_volume* v) {
     for (int k = 0; k < 3; ++k) { ctx->vol_lo[k] = v->lo[k]; ctx->vol_hi[k] = v->hi[k]; }
     ctx->vol_sigma = sqrt(v->s_v * V / (double)v->n);
   }
-  if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; ctx->gkey.clear(); }
+  drop_graphs(ctx);
   return SONAR_OK;
 }
 
@@ -1067,8 +1282,19 @@ static void free_scene(sonar_ctx* c) {
 int sonar_destroy(sonar_ctx* c) {
   if (!c) return SONAR_OK;
   cudaSetDevice(c->device);
+  drain(c);
   cudaStreamSynchronize(c->stream);
-  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
+  drop_graphs(c);
+  for (AsyncSlot& sl : c->aslot) {
+    if (sl.pose_host) cudaFreeHost(sl.pose_host);
+    if (sl.n_cloud_host) cudaFreeHost(sl.n_cloud_host);
+    if (sl.counters_host) cudaFreeHost(sl.counters_host);
+    if (sl.ev_done) cudaEventDestroy(sl.ev_done);
+    if (sl.ev_gemm) cudaEventDestroy(sl.ev_gemm);
+    dfree(sl.env_stage);
+  }
+  if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
   if (c->ev_in) cudaEventDestroy(c->ev_in);
   if (c->ev_out) cudaEventDestroy(c->ev_out);
   for (auto& e : c->stage_ev)
@@ -1104,10 +1330,12 @@ int sonar_scene_upload(sonar_ctx* ctx, const float* verts, int64_t n_verts, cons
   for (int64_t i = 0; i < 3 * n_verts; ++i)
     if (!isfinite(verts[i])) return fail(ctx, SONAR_E_ARG, "vertex %lld is not finite", (long long)(i / 3));
   CU(cudaSetDevice(ctx->device));
+  int rc0 = drain(ctx);
+  if (rc0) return rc0;
   CU(cudaStreamSynchronize(ctx->user_stream));
   CU(cudaStreamSynchronize(ctx->stream));
   free_scene(ctx);
-  if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; ctx->gkey.clear(); }
+  drop_graphs(ctx);
   if (n_tris > 0) {
     float* dv = nullptr;
     int32_t* dt = nullptr;
@@ -1171,8 +1399,25 @@ int sonar_ping_batch(sonar_ctx* ctx, const sonar_pose* poses, int32_t n_pings, c
   return run(ctx, poses, n_pings, params, ssp, env, cloud, cloud_cap_per_ping, n_cloud);
 }
 
+int sonar_ping_async(sonar_ctx* ctx, const sonar_pose* poses, int32_t n_pings, const sonar_params* params,
+                     const sonar_ssp* ssp, float* env, sonar_point* cloud, int64_t cloud_cap_per_ping,
+                     int64_t* n_cloud) {
+  return run_async(ctx, poses, n_pings, params, ssp, env, cloud, cloud_cap_per_ping, n_cloud);
+}
+
+int sonar_wait(sonar_ctx* ctx) {
+  if (!ctx) return SONAR_E_ARG;
+  ctx->err.clear();
+  CU(cudaSetDevice(ctx->device));
+  return drain(ctx);
+}
+
 int sonar_get_hits(sonar_ctx* ctx, sonar_hit* out, int64_t cap, int64_t* n) {
   if (!ctx) return SONAR_E_ARG;
+  {
+    const int rc = drain(ctx);
+    if (rc) return rc;
+  }
   if (!ctx->debug) return fail(ctx, SONAR_E_ARG, "enable SONAR_OPT_DEBUG before the ping");
   if (ctx->last_p == 0) return fail(ctx, SONAR_E_ARG, "no ping yet");
   CU(cudaSetDevice(ctx->device));
@@ -1201,6 +1446,10 @@ int sonar_get_hits(sonar_ctx* ctx, sonar_hit* out, int64_t cap, int64_t* n) {
 
 int sonar_get_echoes(sonar_ctx* ctx, float* out, int64_t cap_floats) {
   if (!ctx || !out) return SONAR_E_ARG;
+  {
+    const int rc = drain(ctx);
+    if (rc) return rc;
+  }
   if (ctx->last_p == 0) return fail(ctx, SONAR_E_ARG, "no ping yet");
   const Derived& d = ctx->last_d;
   const int64_t per_ping = (int64_t)d.nr * d.M * 2;
@@ -1216,6 +1465,10 @@ int sonar_get_echoes(sonar_ctx* ctx, float* out, int64_t cap_floats) {
 
 int sonar_get_raw(sonar_ctx* ctx, int32_t phase, float* out, int64_t cap_floats) {
   if (!ctx || !out) return SONAR_E_ARG;
+  {
+    const int rc = drain(ctx);
+    if (rc) return rc;
+  }
   if (ctx->last_p == 0 || ctx->last_raw_u == 0) return fail(ctx, SONAR_E_ARG, "no raw-series ping yet");
   if (!ctx->debug) return fail(ctx, SONAR_E_ARG, "enable SONAR_OPT_DEBUG before the ping");
   if (phase < 0 || phase >= ctx->last_raw_u) return fail(ctx, SONAR_E_ARG, "phase %d outside [0, %d)", phase, ctx->last_raw_u);

@@ -78,6 +78,8 @@ struct DevPose {
   float R_lo[9]; // the FP32 pairs (hi + lo) of the straight-ray path
 };
 
+static_assert(sizeof(DevPose) % 16 == 0, "poses are copied in 16-byte words");
+
 // Everything the trace kernels need, passed by value.
 // One point-scatterer image-source route, kept for cross-term pairing: one-way length L
 // (0: the route is not valid), reflection product gam, sonar-frame arrival (uy, uz).

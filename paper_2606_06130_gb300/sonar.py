@@ -102,6 +102,9 @@ _SIGS = {
                              C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]),
     "sonar_ping_batch": (C.c_int, [C.c_void_p, C.POINTER(sonar_pose), C.c_int32, C.POINTER(sonar_params),
                                    C.POINTER(sonar_ssp), C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]),
+    "sonar_ping_async": (C.c_int, [C.c_void_p, C.POINTER(sonar_pose), C.c_int32, C.POINTER(sonar_params),
+                                   C.POINTER(sonar_ssp), C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]),
+    "sonar_wait": (C.c_int, [C.c_void_p]),
     "sonar_get_hits": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]),
     "sonar_get_echoes": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
     "sonar_get_raw": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int64]),
@@ -199,6 +202,7 @@ class Sonar:
         rc = lib().sonar_create(C.byref(self.h), device, C.c_void_p(stream.cuda_stream))
         if rc != SONAR_OK:
             raise SonarError(rc, "sonar_create failed (an sm_103 GPU is required)")
+        self._pending = []  # point-count arrays of asynchronous calls not yet retired
 
     def close(self):
         if self.h:
@@ -256,6 +260,42 @@ class Sonar:
         self._check(lib().sonar_ping_batch(self.h, arr, P, C.byref(sp), C.byref(ss), _ptr(env), _ptr(cloud),
                                            cloud_cap, n))
         return env, cloud, np.array(n[:], np.int64)
+
+    def ping_async(self, poses, params: dict, ssp: dict, precision="fp32", taper=None, env=None, cloud=None,
+                   cloud_cap: int | None = None):
+        """Enqueues the pings without waiting (sonar_ping_async). env/cloud: device tensors
+        or pinned host tensors (default: new device tensors). Returns (env, cloud, n_cloud);
+        they are complete once the call is retired: by the second following ping_async,
+        by wait(), or by any other call on this context."""
+        torch = self.torch
+        P = len(poses)
+        nb = params["n_beam_az"] * params["n_beam_el"]
+        if cloud_cap is None:
+            cloud_cap = nb
+        if env is None:
+            env = torch.empty((P, params["n_beam_el"], params["n_beam_az"], params["n_range"]),
+                              dtype=torch.float32, device=f"cuda:{self.device}")
+        if cloud is None:
+            cloud = torch.empty((P, cloud_cap, 6), dtype=torch.int32, device=f"cuda:{self.device}")
+        arr = (sonar_pose * P)(*[make_pose(p) for p in poses])
+        sp = make_params(params, precision, taper)
+        ss = make_ssp(ssp)
+        n = np.zeros(P, np.int64)
+        self._pending.append(n)
+        try:
+            self._check(lib().sonar_ping_async(self.h, arr, P, C.byref(sp), C.byref(ss), _ptr(env), _ptr(cloud),
+                                               cloud_cap, n.ctypes.data_as(C.POINTER(C.c_int64))))
+        finally:
+            # the call retired the one made two calls earlier; its count array is final
+            del self._pending[:-2]
+        return env, cloud, n
+
+    def wait(self):
+        """Retires every asynchronous call in flight (sonar_wait)."""
+        try:
+            self._check(lib().sonar_wait(self.h))
+        finally:
+            self._pending.clear()
 
     def ping(self, pose, params: dict, ssp: dict, **kw):
         env, cloud, n = self.ping_batch([pose], params, ssp, **kw)
