@@ -107,7 +107,6 @@ struct sonar_ctx {
   cudaStream_t user_stream = nullptr;  // caller's stream, ordered with events
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   cudaEvent_t stage_ev[7] = {};
-  int graph_kernels = 0;
   int sm_count = 0;
   std::string err;
   bool debug = false, timing = false, use_graph = true;
@@ -191,9 +190,16 @@ struct sonar_ctx {
   int* err_dev = nullptr;
   int64_t ws_hits = 0, ws_bins = 0, ws_s = 0, ws_x = 0;
 
-  // graph
-  cudaGraphExec_t gexec = nullptr;
-  std::vector<uint8_t> gkey;
+  // captured graphs of the synchronous calls, keyed by everything they bake in (a few,
+  // so that a caller alternating output buffers does not re-capture on every call)
+  struct GraphEntry {
+    std::vector<uint8_t> key;
+    cudaGraphExec_t exec = nullptr;
+    int kernels = 0;
+    uint64_t used = 0;
+  };
+  std::vector<GraphEntry> graphs;
+  uint64_t graph_tick = 0;
 
   // asynchronous pings: two slots and the copy-engine stream of their envelopes
   AsyncSlot aslot[2];
@@ -901,7 +907,8 @@ int report(sonar_ctx* ctx, int errw, const long long* n_cloud_host, int P, int64
 // Captured graphs bake in options and buffers: they are rebuilt after an option, the
 // volume scatterers or the scene change.
 void drop_graphs(sonar_ctx* ctx) {
-  if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; ctx->gkey.clear(); }
+  for (auto& e : ctx->graphs) cudaGraphExecDestroy(e.exec);
+  ctx->graphs.clear();
   for (AsyncSlot& sl : ctx->aslot)
     if (sl.gexec) { cudaGraphExecDestroy(sl.gexec); sl.gexec = nullptr; sl.gkey.clear(); }
 }
@@ -998,21 +1005,35 @@ int run(sonar_ctx* ctx, const sonar_pose* poses, int P, const sonar_params* p, c
     }
     key_add(k, ctx->vol_order);
     key_add(k, ctx->hits); key_add(k, ctx->S); key_add(k, ctx->x_hi); key_add(k, ctx->y_hi); key_add(k, ctx->keys);
-    if (!ctx->gexec || k != ctx->gkey) {
-      if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; }
+    sonar_ctx::GraphEntry* ge = nullptr;
+    for (auto& e : ctx->graphs)
+      if (e.key == k) ge = &e;
+    if (!ge) {
+      constexpr size_t kMaxGraphs = 4;
+      if (ctx->graphs.size() == kMaxGraphs) {  // evict the least recently used
+        auto lru = ctx->graphs.begin();
+        for (auto it = ctx->graphs.begin(); it != ctx->graphs.end(); ++it)
+          if (it->used < lru->used) lru = it;
+        cudaGraphExecDestroy(lru->exec);
+        ctx->graphs.erase(lru);
+      }
+      sonar_ctx::GraphEntry e;
       cudaGraph_t g;
       CU(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-      rc = enqueue(ctx, P, p, d, o, &ctx->graph_kernels);
+      rc = enqueue(ctx, P, p, d, o, &e.kernels);
       cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
       if (rc) { if (ce == cudaSuccess) cudaGraphDestroy(g); return rc; }
       CU(ce);
-      cudaError_t ie = cudaGraphInstantiate(&ctx->gexec, g, 0);
+      cudaError_t ie = cudaGraphInstantiate(&e.exec, g, 0);
       cudaGraphDestroy(g);
       CU(ie);
-      ctx->gkey = k;
+      e.key = k;
+      ctx->graphs.push_back(std::move(e));
+      ge = &ctx->graphs.back();
     }
-    CU(cudaGraphLaunch(ctx->gexec, ctx->stream));
-    kernels = ctx->graph_kernels;
+    ge->used = ++ctx->graph_tick;
+    CU(cudaGraphLaunch(ge->exec, ctx->stream));
+    kernels = ge->kernels;
   } else {
     rc = enqueue(ctx, P, p, d, o, &kernels);
   }
