@@ -217,6 +217,12 @@ def read_traffic(kernel):
 
 
 # ------------------------------------------------------------------ our arm
+# water-column scatterers of --volume (and of the volume form): a box over the wall and
+# the seabed in front of the sonar, s_v = 1e-4 /m
+VOLUME_BOX = ((-2.0, -12.0, -10.5), (14.0, 12.0, -4.0))
+VOLUME_SV = 1e-4
+
+
 def run_ours(args, ws, rank, local):
     import torch
     import __graft_entry__
@@ -231,6 +237,11 @@ def run_ours(args, ws, rank, local):
         dist.init_process_group("nccl", device_id=dev)
     scene, params, poses, ssp = inputs.workload("c2")
     s = Sonar(local)
+    if args.cross:
+        from paper_2606_06130_gb300.sonar import SONAR_OPT_CROSS
+        s.set_option(SONAR_OPT_CROSS, 1)
+    if args.volume > 0:
+        s.set_volume(args.volume, VOLUME_BOX[0], VOLUME_BOX[1], VOLUME_SV)
     s.upload(scene)
     torch.cuda.synchronize()
     # scene upload and BVH build, timed apart from the pings (median of 3 rebuilds)
@@ -383,6 +394,8 @@ def run_ours(args, ws, rank, local):
                       "beamform_operands": {"fp32": "bf16 hi/lo split, 3 tensor products, fp32 accumulate",
                                             "bf16": "bf16, fp32 accumulate", "fp16": "fp16, fp32 accumulate"}[args.precision],
                       "l2": "flushed before every timed step (256 MB write, outside the events)",
+                      "cross_terms": bool(args.cross),
+                      "volume_scatterers": int(args.volume),
                       "parallelism": f"replicas x{ws}"},
            "roofline": roof,
            "stages_ms": mean_stage,
@@ -527,7 +540,7 @@ def other_forms(torch, s, inputs, dev):
                             "hits": s.stats()["n_hits"], "note": "out/back cross-term multipath on"}
     s.set_option(SONAR_OPT_CROSS, 0)
     # water-column reverberation: 10^6 scatterers in a box over the wall and the seabed
-    s.set_volume(1_000_000, (-2.0, -12.0, -10.5), (14.0, 12.0, -4.0), 1e-4)
+    s.set_volume(1_000_000, VOLUME_BOX[0], VOLUME_BOX[1], VOLUME_SV)
     for _ in range(3):
         s.ping(poses[0], params, ssp, precision="fp32")
     torch.cuda.synchronize()
@@ -625,10 +638,16 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16"])
     ap.add_argument("--no-oracle", action="store_true", help="skip the oracle error and CPU baseline")
     ap.add_argument("--no-forms", action="store_true", help="skip the BF16/FP16/batch side measurements")
+    ap.add_argument("--cross", action="store_true",
+                    help="headline workload with out/back cross-term multipath (implies --no-oracle)")
+    ap.add_argument("--volume", type=int, default=0,
+                    help="headline workload plus this many water-column scatterers (implies --no-oracle)")
     ap.add_argument("--oracle-timing", action="store_true",
                     help="with --impl reference: time the FP64 oracle in full instead (C1, C2 whole pings at 1 "
                          "and all threads; C4 8 pings)")
     args = ap.parse_args()
+    if args.cross or args.volume > 0:
+        args.no_oracle = True  # the oracle legs sample the default workload
     ws, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, ws, rank)

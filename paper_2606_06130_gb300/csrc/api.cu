@@ -727,7 +727,12 @@ int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, cons
   ta.cross = ctx->cross;
   ta.pt_route = pairs ? ctx->pt_route : nullptr;
   ta.vol_n = ctx->vol_n;
-  for (int k = 0; k < 3; ++k) { ta.vol_lo[k] = ctx->vol_lo[k]; ta.vol_hi[k] = ctx->vol_hi[k]; }
+  for (int k = 0; k < 3; ++k) {
+    ta.vol_lo[k] = ctx->vol_lo[k];
+    ta.vol_hi[k] = ctx->vol_hi[k];
+    ta.vol_lo_df[k] = df_pair(ctx->vol_lo[k]);
+    ta.vol_span_df[k] = df_pair(ctx->vol_hi[k] - ctx->vol_lo[k]);
+  }
   ta.vol_sigma = ctx->vol_sigma;
   ta.vol_order = ctx->vol_n > 0 && ctx->vol_n <= kVolSortMax ? ctx->vol_order : nullptr;
   ta.hits = ctx->hits;

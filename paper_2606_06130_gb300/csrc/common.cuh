@@ -118,6 +118,7 @@ struct TraceArgs {
   int64_t vol_n;                 // water-column scatterers per ping (0: none)
   double vol_lo[3], vol_hi[3];   // their world-frame box
   double vol_sigma;              // amplitude coefficient of each, sqrt(s_v V / n)
+  float2 vol_lo_df[3], vol_span_df[3];  // lo and hi - lo as FP32 pairs
   const int32_t* vol_order;      // [vol_n] processing order (Morton order of the positions), or null
   HitRec* hits;
   int32_t* bin_counts;           // [n_pings * nr_pad] hits per first-tap row (zeroed by the caller)

@@ -127,6 +127,15 @@ __device__ __forceinline__ F2 dot(const DF3& a, const DF3& b) { return a.x * b.x
 __device__ __forceinline__ DF3 axpy(const DF3& p, F2 t, const DF3& d) {
   return DF3{p.x + t * d.x, p.y + t * d.y, p.z + t * d.z};
 }
+// sqrt of a pair: the FP32 root s of hi, then one Newton correction from the exact
+// residual v - s^2 (s^2 as an error-free product)
+__device__ __forceinline__ F2 sqrt_df(F2 v) {
+  const float s = __fsqrt_rn(v.hi);
+  if (!(s > 0.f)) return F2{s, 0.f};
+  const float p = __fmul_rn(s, s);
+  const F2 r = v - F2{p, __fmaf_rn(s, s, -p)};
+  return quick_two_sum(s, __fdiv_rn(r.hi, __fmul_rn(2.f, s)));
+}
 // FP64 views, for the rare exact triangle tests and the debug delays
 __device__ __forceinline__ double to_d(F2 v) { return (double)v.hi + (double)v.lo; }
 __device__ __forceinline__ D3 to_d3(const DF3& v) { return d3(to_d(v.x), to_d(v.y), to_d(v.z)); }
@@ -907,27 +916,31 @@ __global__ void k_volume(TraceArgs A) {
   const int ping = (int)(gid / A.vol_n);
   uint32_t h[4] = {(uint32_t)i, (uint32_t)((uint64_t)i >> 32), 0x564F4Cu, A.seed32};
   pcg4d(h[0], h[1], h[2], h[3]);
-  double x[3];
-#pragma unroll
-  for (int k = 0; k < 3; ++k)
-    x[k] = __dadd_rn(A.vol_lo[k], __dmul_rn(__dsub_rn(A.vol_hi[k], A.vol_lo[k]), u24(h[k])));
+  // geometry and delay in FP32 pairs, as on the straight-ray path (FP64 issues at ~2
+  // operations per clock per SM on this part): the position lo + (hi - lo) u (u, a
+  // 24-bit fraction, is exact in FP32), the leg, its length and direction; FP64 only in
+  // the rare exact triangle tests of the shadow query
   const DevPose& P = A.poses[ping];
-  const D3 o = d3(P.t[0], P.t[1], P.t[2]);
-  const D3 dv = d3(x[0] - o.x, x[1] - o.y, x[2] - o.z);
-  const double L = sqrt(dot(dv, dv));
-  if (!(L > 0.0) || !(L <= A.L_stop)) return;
-  // FP64 issues at ~2 operations per clock per SM on this part: only the leg direction
-  // (for the exact triangle tests) and the delay stay in FP64, with one reciprocal in
-  // place of three divisions; the amplitude and the arrival direction need only FP32
-  const double il = 1.0 / L;
-  const D3 d = d3(dv.x * il, dv.y * il, dv.z * il);
-  if (L > 2e-6 && closest_hit<D3, double, true>(A.sc, o, d, 1e-6, L - 1e-6, -1, A.err).prim >= 0) return;
-  const float Lf = (float)L;
-  const float amp = (float)A.vol_sigma / (Lf * Lf) * expf(-2.0f * A.alpha32 * Lf);
-  const float dx = (float)d.x, dy = (float)d.y, dz = (float)d.z;
-  const float uy = P.R32[1] * dx + P.R32[4] * dy + P.R32[7] * dz;  // (R^T d).y
-  const float uz = P.R32[2] * dx + P.R32[5] * dy + P.R32[8] * dz;  // (R^T d).z
-  emit(A, ping, L * A.two_inv_c0, amp, 0.0, uy, uz, -1, 0xA0000000u | (uint32_t)i);
+  const DF3 o = DF3{F2{P.t32[0], P.t_lo[0]}, F2{P.t32[1], P.t_lo[1]}, F2{P.t32[2], P.t_lo[2]}};
+  F2 dvk[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const F2 u = f2((float)(h[k] >> 8) * (1.0f / 16777216.0f));
+    dvk[k] = f2(A.vol_lo_df[k]) + f2(A.vol_span_df[k]) * u;
+  }
+  const DF3 dv = DF3{dvk[0] - o.x, dvk[1] - o.y, dvk[2] - o.z};
+  const F2 L = sqrt_df(dot(dv, dv));
+  if (!(L.hi > 0.f) || f2(A.L_stop_df) < L) return;
+  const F2 il = f2(1.f) / L;
+  const DF3 d = DF3{dv.x * il, dv.y * il, dv.z * il};
+  if (L.hi > 2e-6f) {
+    const F2 eps = F2{1e-6f, (float)(1e-6 - (double)1e-6f)};
+    if (closest_hit<DF3, F2, true>(A.sc, o, d, eps, L - eps, -1, A.err, P.t32).prim >= 0) return;
+  }
+  const float amp = (float)A.vol_sigma / (L.hi * L.hi) * expf(-2.0f * A.alpha32 * L.hi);
+  const float uy = P.R32[1] * d.x.hi + P.R32[4] * d.y.hi + P.R32[7] * d.z.hi;  // (R^T d).y
+  const float uz = P.R32[2] * d.x.hi + P.R32[5] * d.y.hi + P.R32[8] * d.z.hi;  // (R^T d).z
+  emit_df(A, ping, L * f2(A.two_inv_c0_df), amp, 0.f, uy, uz, -1, 0xA0000000u | (uint32_t)i);
 }
 
 // Sonar-frame sub-ray directions (Sec. III Eq. 2-3 grid, cell-centred) with hashed
