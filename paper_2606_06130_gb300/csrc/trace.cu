@@ -245,10 +245,33 @@ __device__ __forceinline__ bool tri_exact(const float* tv, const D3& o, const D3
                                           double& t) {
   return tri_test64(tv, o, d, t) && t > tmin && t <= tmax;
 }
+// The same two-sided test in FP32 pairs (edges exact from the FP32 vertices; ~2^-46
+// relative after that). Its decision differs from the FP64 test's only where u, v or
+// 1 - u - v lies within ~1e-13 of zero, far inside the barycentric margin (1e-5) outside
+// which hits must agree; it keeps the straight-ray and volume paths off the FP64 pipe,
+// which issues at a small fraction of the FP32 rate on this part and was a third busy
+// with these tests alone.
+__device__ __forceinline__ DF3 cross_df(const DF3& a, const DF3& b) {
+  return DF3{a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+__device__ bool tri_test_df(const float* tv, const DF3& o, const DF3& d, F2& t) {
+  const DF3 e1 = DF3{two_sum(tv[3], -tv[0]), two_sum(tv[4], -tv[1]), two_sum(tv[5], -tv[2])};
+  const DF3 e2 = DF3{two_sum(tv[6], -tv[0]), two_sum(tv[7], -tv[1]), two_sum(tv[8], -tv[2])};
+  const DF3 p = cross_df(d, e2);
+  const F2 det = dot(e1, p);
+  if (!(fabsf(det.hi) > 1e-30f)) return false;
+  const F2 inv = f2(1.f) / det;
+  const DF3 s = DF3{o.x - f2(tv[0]), o.y - f2(tv[1]), o.z - f2(tv[2])};
+  const F2 u = dot(s, p) * inv;
+  if (u < f2(0.f) || f2(1.f) < u) return false;
+  const DF3 q = cross_df(s, e1);
+  const F2 v = dot(d, q) * inv;
+  if (v < f2(0.f) || f2(1.f) < u + v) return false;
+  t = dot(e2, q) * inv;
+  return true;
+}
 __device__ __forceinline__ bool tri_exact(const float* tv, const DF3& o, const DF3& d, F2 tmin, F2 tmax, F2& t) {
-  double t64;
-  if (!tri_test64(tv, to_d3(o), to_d3(d), t64)) return false;
-  t = f2_of(t64);
+  if (!tri_test_df(tv, o, d, t)) return false;
   return tmin < t && !(tmax < t);
 }
 
