@@ -725,11 +725,15 @@ __device__ void route_straight(const TraceArgs& A, int ping, const DevPose& P, D
 }
 
 // Traversal is latency-bound (dependent node loads), so residency pays: the straight-ray
-// kernel fits five CTAs of 128 threads per SM (96 registers), the curved one four. The
+// kernel runs six CTAs of 128 threads per SM (80 registers, a 36-byte spill; measured on
+// C2: 5 CTAs 0.129 ms, 6 0.123, 7 and 8 within noise of 6), the curved one four. The
 // cross-term variant is a separate instantiation, so that its extra live state does not
 // cost the default kernel registers.
+#ifndef SONAR_TRACE_CTAS
+#define SONAR_TRACE_CTAS 6  // resident CTAs per SM of the straight-ray kernel
+#endif
 template <bool CURVED, bool CROSS>
-__global__ void __launch_bounds__(128, CURVED ? 4 : 5) k_trace(TraceArgs A) {
+__global__ void __launch_bounds__(128, CURVED ? 4 : SONAR_TRACE_CTAS) k_trace(TraceArgs A) {
   pdl_wait();
   const int64_t total = (int64_t)A.n_pings * A.n_subrays;
   for (int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gid < total; gid += (int64_t)gridDim.x * blockDim.x) {
@@ -1030,7 +1034,11 @@ cudaError_t launch_ray_table(double* dirs, float* dirs32, float* row_domega, int
 cudaError_t launch_trace(const TraceArgs& a, int sm_count, cudaStream_t st) {
   int64_t total = (int64_t)a.n_pings * a.n_subrays;
   int64_t blocks = ceil_div(total, 128);
-  int64_t cap = (int64_t)sm_count * 16;
+  // one sub-ray per thread: the block scheduler balances the uneven route lengths. A
+  // cap of 16 blocks per SM (two grid-stride passes for 40% of the blocks on C2) left an
+  // uneven tail: 0.123 ms against 0.106 ms uncapped.
+  const int64_t cap = 0x7fffffffLL;  // the grid limit
+  (void)sm_count;
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
   cudaError_t e = a.curved  ? launch_pdl(k_trace<true, false>, dim3((unsigned)blocks), dim3(128), 0, st, a)
