@@ -188,6 +188,7 @@ struct sonar_ctx {
   long long* n_cloud_map = nullptr;             // device mappings of the two above
   unsigned long long* counters_map = nullptr;
   int* err_dev = nullptr;
+  int32_t* synth_bounds = nullptr;  // [sm_count + 1] cost-balanced synthesis hit ranges
   int64_t ws_hits = 0, ws_bins = 0, ws_s = 0, ws_x = 0;
 
   // captured graphs of the synchronous calls, keyed by everything they bake in (a few,
@@ -414,6 +415,13 @@ int make_map(sonar_ctx* ctx, CUtensorMap* m, void* base, int64_t rows, int64_t c
 template <typename T>
 int grow(sonar_ctx* ctx, T*& ptr, int64_t& cap, int64_t need, size_t elem, bool zero);
 
+// Extra synthesis cost of a non-empty range row, in units of one hit, for the
+// cost-balanced split of the sorted hits over the persistent synthesis CTAs.
+#ifndef SONAR_SYNTH_ROW_COST
+#define SONAR_SYNTH_ROW_COST 16
+#endif
+constexpr int kSynthRowCost = SONAR_SYNTH_ROW_COST;
+
 // Water-column scatterers up to this count are processed in the Morton order of their
 // positions (a host sort at the first ping with a new count or seed); beyond it, in index
 // order.
@@ -558,6 +566,7 @@ int ensure_workspace(sonar_ctx* ctx, int P, const Derived& d) {
   }
   if (!ctx->n_hits) CU(cudaMalloc(&ctx->n_hits, sizeof(unsigned long long)));
   if (!ctx->err_dev) CU(cudaMalloc(&ctx->err_dev, sizeof(int)));
+  if (!ctx->synth_bounds) CU(cudaMalloc(&ctx->synth_bounds, sizeof(int32_t) * (ctx->sm_count + 1)));
   int64_t hit_need = (int64_t)P * d.hit_cap_per_ping;
   if (hit_need < 1) hit_need = 1;
   if (hit_need > ctx->ws_hits || !ctx->hits) {
@@ -747,12 +756,13 @@ int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, cons
   CU(launch_volume(ta, st));
   mark(1);
   CU(launch_bin(ctx->hits, ctx->n_hits, n_bins, ctx->counts, ctx->offsets, ctx->sorted, ctx->sorted_n, ctx->sm_count,
-                st));
+                ctx->synth_bounds, ctx->sm_count, kSynthRowCost, st));
   mark(2);
   SynthArgs sa;
   sa.hits_sorted = ctx->sorted;
   sa.sorted_n = ctx->sorted_n;
   sa.n_valid = ctx->offsets + n_bins;
+  sa.bounds = ctx->synth_bounds;  // persistent synthesis kernels run one CTA per SM
   sa.rtab = ctx->rtab;
   sa.rtab_scale = (float)(d.dt * kRTab / (2.0 * p->pulse_s));
   sa.rtab_s = ctx->rtab + kRTab + 1;
@@ -1335,7 +1345,7 @@ int sonar_destroy(sonar_ctx* c) {
   dfree(c->poses); dfree(c->hits); dfree(c->sorted); dfree(c->sorted_n); dfree(c->dbg_tau);
   dfree(c->n_hits);
   dfree(c->counts); dfree(c->offsets); dfree(c->S); dfree(c->S_raw); dfree(c->ptab); dfree(c->x_hi); dfree(c->x_lo); dfree(c->gain);
-  dfree(c->env_stage); dfree(c->keys); dfree(c->pmax); dfree(c->cloud_stage); dfree(c->n_cloud_dev); dfree(c->err_dev);
+  dfree(c->env_stage); dfree(c->keys); dfree(c->pmax); dfree(c->cloud_stage); dfree(c->n_cloud_dev); dfree(c->err_dev); dfree(c->synth_bounds);
   delete c;
   return SONAR_OK;
 }

@@ -192,6 +192,7 @@ struct SynthArgs {
   const HitRec* hits_sorted;
   const int32_t* sorted_n;  // first-tap row of each sorted hit (compact copy of nglob)
   const int32_t* n_valid;   // hits with at least one tap in range (binning total)
+  const int32_t* bounds;    // [gridDim + 1] cost-balanced hit ranges of the z-split kernel, or null
   const float2* rtab;       // [kRTab + 1]
   float rtab_scale;         // table index per unit of (u0 + i)
   const float2* rtab_s;     // [kRTabS + 5], entry i at u = -T_p + (i - 2) 2 T_p / kRTabS
@@ -206,9 +207,9 @@ struct SynthArgs {
 };
 // Counting sort of the hits by first-tap row; counts[] holds the per-row histogram (the
 // trace kernels count as they emit) and doubles as the scatter cursor.
-cudaError_t launch_bin(const HitRec* hits, const unsigned long long* n_hits, int32_t n_bins,
-                       int32_t* counts, int32_t* offsets, HitRec* sorted, int32_t* sorted_n,
-                       int sm_count, cudaStream_t st);
+cudaError_t launch_bin(const HitRec* hits, const unsigned long long* n_hits, int32_t n_bins, int32_t* counts,
+                       int32_t* offsets, HitRec* sorted, int32_t* sorted_n, int sm_count, int32_t* bounds,
+                       int bounds_g, int row_cost, cudaStream_t st);
 cudaError_t launch_synth(const SynthArgs& a, int sm_count, cudaStream_t st);
 bool synth_tc_supported(int nx, int ny, int taps);
 cudaError_t prepare_synth_tc();

@@ -13,30 +13,63 @@ namespace sonar {
 namespace {
 
 // Exclusive scan of counts (single CTA of 1024 threads); offsets[n_bins] = total.
-__global__ void __launch_bounds__(1024) k_scan(const int32_t* counts, int32_t n_bins, int32_t* offsets, int32_t* cursor) {
-  __shared__ int32_t part[1024];
+// With `bounds`, it also splits the sorted hits into G ranges of equal estimated
+// synthesis cost, one per persistent synthesis CTA: a hit costs 1 and every non-empty
+// row `beta` more (sparse rows cut K-blocks short and spread them over more tiles, so a
+// hit costs more there than in a dense row). bounds[0] = 0, bounds[G] = total; within a
+// row the row's extra cost comes first.
+__global__ void __launch_bounds__(1024) k_scan(const int32_t* counts, int32_t n_bins, int32_t* offsets, int32_t* cursor,
+                                               int32_t* bounds, int G, int beta) {
+  __shared__ int32_t part[1024], pne[1024];
   pdl_wait();
   const int t = threadIdx.x;
   const int per = (n_bins + 1023) / 1024;
   const int b0 = t * per, b1 = min(b0 + per, n_bins);
-  int32_t s = 0;
-  for (int b = b0; b < b1; ++b) s += counts[b];
+  int32_t s = 0, ne = 0;
+  for (int b = b0; b < b1; ++b) {
+    const int32_t c = counts[b];
+    s += c;
+    ne += c > 0;
+  }
   part[t] = s;
+  pne[t] = ne;
   __syncthreads();
   for (int off = 1; off < 1024; off <<= 1) {
-    int32_t v = t >= off ? part[t - off] : 0;
+    const int32_t v = t >= off ? part[t - off] : 0, w = t >= off ? pne[t - off] : 0;
     __syncthreads();
     part[t] += v;
+    pne[t] += w;
     __syncthreads();
   }
-  int32_t run = part[t] - s;
+  int32_t run = part[t] - s, nrun = pne[t] - ne;
+  const int64_t C = (int64_t)part[1023] + (int64_t)beta * pne[1023];  // total cost
+  if (bounds && C == 0)
+    for (int k = t; k <= G; k += 1024) bounds[k] = 0;
   for (int b = b0; b < b1; ++b) {
     const int32_t cnt = counts[b];  // counts and cursor may alias
     offsets[b] = run;
     cursor[b] = run;
+    if (bounds && cnt > 0 && C > 0) {
+      // boundaries k with lo <= k C / G < hi fall in this row's cost interval [lo, hi)
+      const int64_t lo = (int64_t)run + (int64_t)beta * nrun, hi = lo + cnt + beta;
+      for (int64_t k = (lo * G + C - 1) / C; k < G && k * C < hi * G; ++k) {
+        if (k < 1) continue;
+        const int64_t num = k * C - (lo + beta) * G;  // cost past the row's extra, times G
+        int64_t j = num <= 0 ? 0 : (num + G - 1) / G;
+        if (j > cnt) j = cnt;
+        bounds[k] = run + (int32_t)j;
+      }
+    }
     run += cnt;
+    nrun += cnt > 0;
   }
-  if (t == 1023) offsets[n_bins] = part[1023];
+  if (t == 1023) {
+    offsets[n_bins] = part[1023];
+    if (bounds) {
+      bounds[0] = 0;
+      bounds[G] = part[1023];
+    }
+  }
 }
 
 // Hits arrive in ray order, so neighbouring lanes usually share a row: one atomic per
@@ -382,8 +415,10 @@ __global__ void __launch_bounds__(128) k_mfilter(MfArgs a) {
 }  // namespace
 
 cudaError_t launch_bin(const HitRec* hits, const unsigned long long* n_hits, int32_t n_bins, int32_t* counts,
-                       int32_t* offsets, HitRec* sorted, int32_t* sorted_n, int sm_count, cudaStream_t st) {
-  cudaError_t e = launch_pdl(k_scan, dim3(1), dim3(1024), 0, st, (const int32_t*)counts, n_bins, offsets, counts);
+                       int32_t* offsets, HitRec* sorted, int32_t* sorted_n, int sm_count, int32_t* bounds,
+                       int bounds_g, int row_cost, cudaStream_t st) {
+  cudaError_t e = launch_pdl(k_scan, dim3(1), dim3(1024), 0, st, (const int32_t*)counts, n_bins, offsets, counts,
+                             bounds, bounds_g, row_cost);
   if (e != cudaSuccess) return e;
   // counts now doubles as the scatter cursor
   e = launch_pdl(k_scatter, dim3(sm_count * 8), dim3(256), 0, st, hits, n_hits, n_bins, counts, sorted, sorted_n);

@@ -372,8 +372,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_
   const uint32_t tmem_base = *tmem_slot;
   // the hits come from the binning kernels
   pdl_wait();
+  // this CTA's range of the sorted hits: cost-balanced by the binning scan, else equal
   const int64_t Hn = *a.n_valid;
-  const int64_t h0 = Hn * blockIdx.x / gridDim.x, h1 = Hn * (blockIdx.x + 1) / gridDim.x;
+  const int64_t h0 = a.bounds ? (int64_t)a.bounds[blockIdx.x] : Hn * blockIdx.x / gridDim.x;
+  const int64_t h1 = a.bounds ? (int64_t)a.bounds[blockIdx.x + 1] : Hn * (blockIdx.x + 1) / gridDim.x;
 
   if (warp == 0) {
     // ------------------------------------------------------------- MMA issuer
@@ -663,8 +665,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tc(SynthArgs a, uint32_
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
   pdl_wait();
+  // this CTA's range of the sorted hits: cost-balanced by the binning scan, else equal
   const int64_t Hn = *a.n_valid;
-  const int64_t h0 = Hn * blockIdx.x / gridDim.x, h1 = Hn * (blockIdx.x + 1) / gridDim.x;
+  const int64_t h0 = a.bounds ? (int64_t)a.bounds[blockIdx.x] : Hn * blockIdx.x / gridDim.x;
+  const int64_t h1 = a.bounds ? (int64_t)a.bounds[blockIdx.x + 1] : Hn * (blockIdx.x + 1) / gridDim.x;
 
   if (warp == 0) {
     // ------------------------------------------------------------- MMA issuer
