@@ -28,7 +28,9 @@ class OrcParams(C.Structure):
                 ("surface_z", C.c_double), ("r_surface", C.c_double), ("r_seabed", C.c_double),
                 ("alpha", C.c_double), ("seed", C.c_uint64), ("thr_mode", C.c_int32),
                 ("thr", C.c_double), ("cross", C.c_int32), ("vol_n", C.c_int64),
-                ("vol_lo", C.c_double * 3), ("vol_hi", C.c_double * 3), ("vol_sv", C.c_double)]
+                ("vol_lo", C.c_double * 3), ("vol_hi", C.c_double * 3), ("vol_sv", C.c_double),
+                ("fld_nx", C.c_int32), ("fld_nz", C.c_int32), ("fld_x0", C.c_double), ("fld_dx", C.c_double),
+                ("fld_z0", C.c_double), ("fld_dz", C.c_double), ("fld_c", C.c_void_p), ("fld_h", C.c_double)]
 
 
 _PARAM_DEFAULTS = {"cross": 0, "vol_n": 0, "vol_lo": (0.0, 0.0, 0.0), "vol_hi": (0.0, 0.0, 0.0), "vol_sv": 0.0}
@@ -67,6 +69,7 @@ def lib():
         _lib.orc_pulse_acf.argtypes = [d, d, d, vp, vp]
         _lib.orc_pcg4d.argtypes = [vp]
         _lib.orc_closest_hit.argtypes = [vp, vp, vp, d, d, i32, C.c_int, vp, vp, vp]
+        _lib.orc_field_ray.argtypes = [vp, vp, vp, d, i32, vp]
         _lib.orc_closest_hit.restype = i32
         _lib.orc_arc_nodes.argtypes = [vp, vp, i32, vp, vp, d, i32, vp, vp, vp]
         _lib.orc_eigen_arc.argtypes = [vp, vp, i32, vp, vp, vp, vp, vp]
@@ -89,14 +92,26 @@ def set_threads(n: int) -> None:
 
 
 def make_params(p: dict) -> OrcParams:
+    """OrcParams from a parameter dict. A range-dependent sound speed comes as
+    p["field"] = {"x0", "dx", "z0", "dz", "c": [nz][nx] m/s, "h": RK4 step in m}."""
     o = OrcParams()
+    fld = p.get("field")
     for name, _ in OrcParams._fields_:
+        if name.startswith("fld_"):
+            continue
         v = p.get(name, _PARAM_DEFAULTS[name]) if name in _PARAM_DEFAULTS else p[name]
         if name in ("vol_lo", "vol_hi"):
             v = (C.c_double * 3)(*[float(x) for x in v])
         if name == "surface_z" and v is None:
             v = math.nan
         setattr(o, name, v)
+    if fld is not None:
+        cf = np.ascontiguousarray(fld["c"], np.float64)
+        o.fld_nz, o.fld_nx = cf.shape
+        o.fld_x0, o.fld_dx, o.fld_z0, o.fld_dz = (float(fld[k]) for k in ("x0", "dx", "z0", "dz"))
+        o.fld_h = float(fld["h"])
+        o.fld_c = cf.ctypes.data
+        o._keep = cf  # the grid must outlive the call
     return o
 
 
@@ -114,6 +129,20 @@ class _SceneHold:
         self.s = OrcScene(len(self.verts), _ptr(self.verts), len(self.tris), _ptr(self.tris),
                           _ptr(self.mu), _ptr(self.flags), len(self.points), _ptr(self.points),
                           _ptr(self.sigma), len(self.planes), _ptr(self.planes))
+
+
+def field_ray(params: dict, o, d, h: float, n: int) -> np.ndarray:
+    """n RK4 steps of the field-route integrator (Sec. II.A refraction in a 2-D field):
+    (x, y, z, tx, ty, tz, T) after an arc length n h from o along d."""
+    L = lib()
+    op = make_params(params)
+    o = np.ascontiguousarray(o, np.float64)
+    d = np.ascontiguousarray(d, np.float64)
+    out = np.zeros(7, np.float64)
+    rc = L.orc_field_ray(C.byref(op), _ptr(o), _ptr(d), C.c_double(h), C.c_int32(n), _ptr(out))
+    if rc != 0:
+        raise RuntimeError(f"orc_field_ray failed with code {rc}")
+    return out
 
 
 def trace(scene, params: dict, pose: dict, ssp: dict, use_bvh: bool = True) -> dict:

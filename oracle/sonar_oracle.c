@@ -698,6 +698,139 @@ static void mirror_point(const double pl[4], const double x[3], double r[3]) {
   r[0] = x[0] - k * pl[0]; r[1] = x[1] - k * pl[1]; r[2] = x[2] - k * pl[2];
 }
 
+/* ------------------------------------------------------------------ 2-D sound-speed field */
+/* Sec. II.A rays bent by a range- and depth-dependent sound speed (Snell's law in its
+   continuous form). c(x, z) comes from a regular grid, bilinear in each cell; positions
+   outside the grid are clamped to it, so c is constant outward and the gradient
+   component across a clamped axis is zero. Returns c and (dc/dx, dc/dz). */
+static void field_eval(const orc_params* p, double x, double z, double* c, double* cx, double* cz) {
+  const int32_t nx = p->fld_nx, nz = p->fld_nz;
+  double fx = (x - p->fld_x0) / p->fld_dx, fz = (z - p->fld_z0) / p->fld_dz;
+  int inx = 1, inz = 1;
+  if (fx < 0.0) { fx = 0.0; inx = 0; } else if (fx > nx - 1) { fx = nx - 1; inx = 0; }
+  if (fz < 0.0) { fz = 0.0; inz = 0; } else if (fz > nz - 1) { fz = nz - 1; inz = 0; }
+  int32_t i = (int32_t)floor(fx), j = (int32_t)floor(fz);
+  if (i > nx - 2) i = nx - 2;
+  if (j > nz - 2) j = nz - 2;
+  const double u = fx - i, v = fz - j;
+  const double* C = p->fld_c;
+  const double c00 = C[j * nx + i], c10 = C[j * nx + i + 1];
+  const double c01 = C[(j + 1) * nx + i], c11 = C[(j + 1) * nx + i + 1];
+  *c = (1.0 - u) * (1.0 - v) * c00 + u * (1.0 - v) * c10 + (1.0 - u) * v * c01 + u * v * c11;
+  *cx = inx ? ((1.0 - v) * (c10 - c00) + v * (c11 - c01)) / p->fld_dx : 0.0;
+  *cz = inz ? ((1.0 - u) * (c01 - c00) + u * (c11 - c10)) / p->fld_dz : 0.0;
+}
+
+/* Ray equations in arc length s for the state (r, t, T), t the unit tangent:
+   dr/ds = t, dt/ds = ((grad c . t) t - grad c) / c, dT/ds = 1 / c. */
+static void field_deriv(const orc_params* p, const double y[7], double f[7]) {
+  double c, cx, cz;
+  field_eval(p, y[0], y[2], &c, &cx, &cz);
+  const double gt = cx * y[3] + cz * y[5];
+  f[0] = y[3];
+  f[1] = y[4];
+  f[2] = y[5];
+  f[3] = (gt * y[3] - cx) / c;
+  f[4] = gt * y[4] / c;
+  f[5] = (gt * y[5] - cz) / c;
+  f[6] = 1.0 / c;
+}
+
+/* One classical Runge-Kutta step of length h, the tangent renormalised after it. */
+static void rk4_step(const orc_params* p, const double y[7], double h, double out[7]) {
+  double k1[7], k2[7], k3[7], k4[7], tmp[7];
+  field_deriv(p, y, k1);
+  for (int i = 0; i < 7; ++i) tmp[i] = y[i] + 0.5 * h * k1[i];
+  field_deriv(p, tmp, k2);
+  for (int i = 0; i < 7; ++i) tmp[i] = y[i] + 0.5 * h * k2[i];
+  field_deriv(p, tmp, k3);
+  for (int i = 0; i < 7; ++i) tmp[i] = y[i] + h * k3[i];
+  field_deriv(p, tmp, k4);
+  for (int i = 0; i < 7; ++i) out[i] = y[i] + h / 6.0 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
+  const double n = sqrt(out[3] * out[3] + out[4] * out[4] + out[5] * out[5]);
+  out[3] /= n;
+  out[4] /= n;
+  out[5] /= n;
+}
+
+int orc_field_ray(const orc_params* p, const double o[3], const double d[3], double h, int32_t n, double out[7]) {
+  if (p->fld_nx < 2 || p->fld_nz < 2 || !(p->fld_dx > 0) || !(p->fld_dz > 0) || !p->fld_c || n < 0) return 5;
+  double y[7] = {o[0], o[1], o[2], d[0], d[1], d[2], 0.0};
+  for (int32_t k = 0; k < n; ++k) {
+    double yn[7];
+    rk4_step(p, y, h, yn);
+    for (int i = 0; i < 7; ++i) y[i] = yn[i];
+  }
+  for (int i = 0; i < 7; ++i) out[i] = y[i];
+  return 0;
+}
+
+/* Route in a 2-D field: RK4 steps of fld_h; the chord of each step is intersected with
+   the scene and the sea surface like the chords of a circular arc. A hit's time and arc
+   length interpolate the step's end values linearly in the chord fraction f; at a
+   reflection the tangent is (1 - f) t_i + f t_i+1, normalised, reflected about the
+   normal. */
+static void route_field(const tctx* c, const double o[3], const double d0[3], const double us[3],
+                        int32_t ray, int32_t sub, double dOmega, hbuf* hb) {
+  const orc_params* p = c->p;
+  double y[7] = {o[0], o[1], o[2], d0[0], d0[1], d0[2], 0.0};
+  double sarc = 0.0, gam = 1.0;
+  int32_t bounce = 0, prev = -1;
+  for (int iter = 0; iter < 1000000; ++iter) {
+    if (!(y[6] < c->T_stop)) break;
+    double yn[7];
+    rk4_step(p, y, p->fld_h, yn);
+    double ch[3] = {yn[0] - y[0], yn[1] - y[1], yn[2] - y[2]};
+    const double len = norm3(ch);
+    if (!(len > 0)) break;
+    const double dc[3] = {ch[0] / len, ch[1] / len, ch[2] / len};
+    hitq hq = closest(c->sc, c->bv, y, dc, EPS_HIT, len, prev >= 0 ? prev : -1);
+    double ts = INFINITY;
+    if (c->has_surface && prev != -2 && dc[2] != 0.0) {
+      const double t = (p->surface_z - y[2]) / dc[2];
+      if (t > EPS_HIT && t <= len) ts = t;
+    }
+    if (hq.prim < 0 && ts == INFINITY) {
+      for (int i = 0; i < 7; ++i) y[i] = yn[i];
+      sarc += p->fld_h;
+      prev = -1;
+      continue;
+    }
+    const int surf = ts < hq.t;
+    const double thit = surf ? ts : hq.t;
+    const double f = thit / len;
+    const double T_hit = y[6] + f * (yn[6] - y[6]), s_hit = sarc + f * p->fld_h;
+    if (!(T_hit <= c->T_stop)) break;
+    const double hp[3] = {y[0] + thit * dc[0], y[1] + thit * dc[1], y[2] + thit * dc[2]};
+    double n[3];
+    if (surf) {
+      if (bounce >= p->max_bounces) break;
+      n[0] = 0; n[1] = 0; n[2] = 1;
+      gam *= p->r_surface;
+    } else {
+      tri_normal(c->sc, hq.prim, n);
+      const double kinc = fabs(dot3(dc, n));
+      emit_mesh_hit(c, hb, ray, sub, bounce, hq.prim, T_hit, s_hit, gam, kinc, dOmega, us, hq.margin,
+                    hq.t2 - hq.t);
+      if (!((c->sc->flags[hq.prim] & 1) && bounce < p->max_bounces)) break;
+      gam *= p->r_seabed;
+    }
+    double tg[3];
+    for (int k = 0; k < 3; ++k) tg[k] = (1.0 - f) * y[3 + k] + f * yn[3 + k];
+    const double tn = norm3(tg);
+    for (int k = 0; k < 3; ++k) tg[k] /= tn;
+    reflect(tg, n);
+    for (int k = 0; k < 3; ++k) {
+      y[k] = hp[k];
+      y[3 + k] = tg[k];
+    }
+    y[6] = T_hit;
+    sarc = s_hit;
+    bounce++;
+    prev = surf ? -2 : hq.prim;
+  }
+}
+
 /* Point scatterers: monostatic image-source eigen-routes (Sec. II.B limited secondary
    reflections). Mirror planes: the sea surface (reflection r_surface) then the scene's
    planes (reflection r_seabed). Routes are plane sequences without immediate repeats,
@@ -891,6 +1024,14 @@ int orc_trace(const orc_scene* sc, const orc_params* p, const double pose_t[3], 
   c.p = p;
   if (p->n_sub != 1 && p->n_sub != 4) return 3;
   if (ssp_make(ssp_z, ssp_cc, n_ssp, p->c_ref, &c.ssp) != 0) return 2;
+  const int field = p->fld_nx > 0;
+  if (field) {
+    if (p->fld_nx < 2 || p->fld_nz < 2 || !(p->fld_dx > 0) || !(p->fld_dz > 0) || !(p->fld_h > 0) || !p->fld_c)
+      return 5;
+    for (int64_t k = 0; k < (int64_t)p->fld_nx * p->fld_nz; ++k)
+      if (!(p->fld_c[k] > 0)) return 5;
+    if (p->cross || p->vol_n > 0) return 4; /* field routes carry no cross terms or volume */
+  }
   if (p->cross && c.ssp.curved) return 4; /* cross terms are formed for isovelocity routes only */
   if (p->vol_n < 0 || p->vol_n > (1LL << 28)) return 5;
   if (p->vol_n > 0) {
@@ -899,6 +1040,10 @@ int orc_trace(const orc_scene* sc, const orc_params* p, const double pose_t[3], 
       if (!(p->vol_hi[k] > p->vol_lo[k]) || !(p->vol_sv >= 0)) return 5;
   }
   c.c_ref = p->c_ref > 0 ? p->c_ref : ssp_c(&c.ssp, pose_t[2]);
+  if (field && !(p->c_ref > 0)) {
+    double gx, gz;
+    field_eval(p, pose_t[0], pose_t[2], &c.c_ref, &gx, &gz);
+  }
   /* one-way time after which no echo reaches the last range sample */
   c.T_stop = p->r_max / c.c_ref + p->pulse / 2.0;
   double qn = sqrt(pose_q[0] * pose_q[0] + pose_q[1] * pose_q[1] + pose_q[2] * pose_q[2] + pose_q[3] * pose_q[3]);
@@ -943,12 +1088,13 @@ int orc_trace(const orc_scene* sc, const orc_params* p, const double pose_t[3], 
         double us[3] = {cos(el) * cos(az), cos(el) * sin(az), sin(el)};
         double dw[3];
         mat_vec(c.R, us, dw);
-        if (c.ssp.curved) route_curved(&c, c.t, dw, us, ray, s, dOmega, &rows[j]);
+        if (p->fld_nx > 0) route_field(&c, c.t, dw, us, ray, s, dOmega, &rows[j]);
+        else if (c.ssp.curved) route_curved(&c, c.t, dw, us, ray, s, dOmega, &rows[j]);
         else route_straight(&c, c.t, dw, us, ray, s, dOmega, &rows[j]);
       }
     }
   }
-  point_routes(&c, &rows[nre]);
+  if (!field) point_routes(&c, &rows[nre]); /* no eigen-ray search in a 2-D field */
 #pragma omp parallel for schedule(dynamic, 1)
   for (int32_t q = 0; q < nvc; ++q)
     volume_scatter(&c, p->vol_n * q / nvc, p->vol_n * (q + 1) / nvc, &rows[nre + 1 + q]);

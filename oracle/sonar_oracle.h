@@ -42,6 +42,10 @@ typedef struct {
   int64_t vol_n;           /* water-column scatterers (0: none; isovelocity only) */
   double vol_lo[3], vol_hi[3];  /* their world-frame box [m] */
   double vol_sv;           /* volume backscattering coefficient s_v [1/m] */
+  int32_t fld_nx, fld_nz;  /* range-dependent sound speed c(x, z) on a grid (0: none) */
+  double fld_x0, fld_dx, fld_z0, fld_dz;  /* grid origin and spacing [m] */
+  const double* fld_c;     /* [fld_nz][fld_nx] sound speed [m/s] */
+  double fld_h;            /* ray integration step in arc length [m] */
 } orc_params;
 
 typedef struct {
@@ -78,6 +82,11 @@ void orc_pcg4d(uint32_t v[4]);
 int32_t orc_closest_hit(const orc_scene* sc, const double o[3], const double d[3],
                         double tmin, double tmax, int32_t exclude, int use_bvh,
                         double* t, double* margin, double* t_second);
+
+/* Test access to the field-route integrator: n RK4 steps of arc length h from the point
+   o along the unit direction d in the sound-speed field of p; out = (r[3], t[3], T), the
+   position, unit tangent and one-way time. Returns 0, or 5 for an invalid field. */
+int orc_field_ray(const orc_params* p, const double o[3], const double d[3], double h, int32_t n, double out[7]);
 
 /* Trace one ping: fills the hit list. Returns 0, or -needed when capacity is short,
    or a positive error code. */
