@@ -227,6 +227,28 @@ typedef struct {
    or with more than 2^21 point scatterers, returns SONAR_E_UNSUPPORTED while n > 0. */
 SONAR_API int sonar_set_volume(sonar_ctx* ctx, const sonar_volume* v);
 
+/* Range-dependent sound speed (Sec. II.A: rays bent by Snell's law through a range- and
+   depth-dependent sound speed). c(x, z) on a regular grid of world x (range) and z
+   (depth), bilinear in each cell; positions outside the grid are clamped to it (c
+   constant outward). Rays are integrated by classical Runge-Kutta steps of step_m in
+   arc length on (r, t, T): dr/ds = t, dt/ds = ((grad c . t) t - grad c) / c,
+   dT/ds = 1 / c, the tangent renormalised after each step; the chord of each step is
+   intersected with the scene and the sea surface, a hit's time and arc length
+   interpolated linearly along its chord, and a reflection reflects the interpolated
+   tangent. While a field is set it replaces the sonar_ssp of the pings; the reference
+   speed is params.c_ref, or c at the sonar when that is <= 0. Point scatterers do not
+   echo in a field (no eigen-ray search), and cross terms and volume scatterers are not
+   formed (SONAR_E_UNSUPPORTED at the ping). */
+typedef struct {
+  int32_t nx, nz;         /* grid nodes along x and z, >= 2 each; nx = 0 removes the field */
+  double x0, dx, z0, dz;  /* first node and spacing [m], dx, dz > 0 */
+  const double* c;        /* host [nz][nx] sound speed [m/s], > 0; copied by the call */
+  double step_m;          /* integration step in arc length [m], > 0 */
+} sonar_field;
+/* Sets (or, with f NULL or f->nx 0, removes) the field of the following pings.
+   SONAR_E_ARG for a bad grid, speed or step. */
+SONAR_API int sonar_set_field(sonar_ctx* ctx, const sonar_field* f);
+
 /* ---------------------------------------------------------------- pings */
 /* One ping. env: [n_beam_el][n_beam_az][n_range] f32 envelope |B| * TVG. cloud: up to
    cloud_cap points ordered by beam (may be NULL with cloud_cap 0). Outputs may be device

@@ -115,6 +115,9 @@ struct sonar_ctx {
   int bvh_opt = 0;    // 0: binned-SAH hierarchy (host build), 1: Morton-order LBVH (device build)
   int cross = 0;      // 1: out/back cross-term multipath
   int64_t vol_n = 0;  // water-column scatterers per ping
+  sonar_field fld{};  // range-dependent sound speed (fld.nx = 0: none); c points to fld_c
+  double* fld_c = nullptr;  // device copy of the grid
+  std::vector<double> fld_host;
   double vol_lo[3] = {0, 0, 0}, vol_hi[3] = {0, 0, 0}, vol_sigma = 0.0;
   int32_t* vol_order = nullptr;  // Morton order of the scatterers (null: index order)
   int64_t vol_order_cap = 0;
@@ -300,7 +303,22 @@ DevPose dev_pose(const sonar_pose& ps) {
   return P;
 }
 
-int derive(sonar_ctx* ctx, const sonar_params* p, const sonar_ssp* ssp, double z_sonar, int n_pings, Derived& d) {
+// c(x, z) of a field, bilinear with positions clamped to the grid (the reference speed
+// at the sonar)
+double field_c_host(const sonar_field& f, const double* c, double x, double z) {
+  double fx = (x - f.x0) / f.dx, fz = (z - f.z0) / f.dz;
+  fx = fx < 0.0 ? 0.0 : (fx > f.nx - 1 ? f.nx - 1 : fx);
+  fz = fz < 0.0 ? 0.0 : (fz > f.nz - 1 ? f.nz - 1 : fz);
+  int i = (int)floor(fx), j = (int)floor(fz);
+  if (i > f.nx - 2) i = f.nx - 2;
+  if (j > f.nz - 2) j = f.nz - 2;
+  const double u = fx - i, v = fz - j;
+  return (1.0 - u) * (1.0 - v) * c[j * f.nx + i] + u * (1.0 - v) * c[j * f.nx + i + 1] +
+         (1.0 - u) * v * c[(j + 1) * f.nx + i] + u * v * c[(j + 1) * f.nx + i + 1];
+}
+
+int derive(sonar_ctx* ctx, const sonar_params* p, const sonar_ssp* ssp, double x_sonar, double z_sonar, int n_pings,
+           Derived& d) {
   d.ssp_z0 = 0.0;
   d.ssp_g = 0.0;
   int nn = ssp ? ssp->n_nodes : 0;
@@ -316,6 +334,14 @@ int derive(sonar_ctx* ctx, const sonar_params* p, const sonar_ssp* ssp, double z
   }
   d.curved = d.ssp_g != 0.0;
   d.c_ref = p->c_ref > 0 ? p->c_ref : d.ssp_c0 + d.ssp_g * (z_sonar - d.ssp_z0);
+  if (ctx->fld.nx > 0) {
+    // the field replaces the profile: rays take the curved-path kernel, the reference
+    // speed is c at the sonar unless given
+    if (ctx->cross || ctx->vol_n > 0)
+      return fail(ctx, SONAR_E_UNSUPPORTED, "a sound-speed field carries no cross terms or volume scatterers");
+    d.curved = 1;
+    if (!(p->c_ref > 0)) d.c_ref = field_c_host(ctx->fld, ctx->fld_host.data(), x_sonar, z_sonar);
+  }
   if (!(d.c_ref > 0)) return fail(ctx, SONAR_E_ARG, "non-positive reference sound speed");
   d.nr = p->n_range;
   d.dr = (p->r_max_m - p->r_min_m) / p->n_range;
@@ -342,7 +368,9 @@ int derive(sonar_ctx* ctx, const sonar_params* p, const sonar_ssp* ssp, double z
   while (d.n_blank < d.nr && p->r_min_m + (d.n_blank + 0.5) * d.dr < p->r_blank_m) ++d.n_blank;
   int np = (isnan(p->surface_z) ? 0 : 1) + (ctx->has_scene ? ctx->sc.n_planes : 0);
   int mb = p->max_bounces > 3 ? 3 : p->max_bounces;
-  if (d.curved) {
+  if (ctx->fld.nx > 0) {
+    d.n_routes = 0;  // no eigen-ray search in a field: point scatterers do not echo
+  } else if (d.curved) {
     d.n_routes = 1;
   } else {
     int64_t total = 1, cnt = 1;
@@ -743,6 +771,14 @@ int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, cons
     ta.vol_span_df[k] = df_pair(ctx->vol_hi[k] - ctx->vol_lo[k]);
   }
   ta.vol_sigma = ctx->vol_sigma;
+  ta.fld_nx = ctx->fld.nx;
+  ta.fld_nz = ctx->fld.nz;
+  ta.fld_x0 = ctx->fld.x0;
+  ta.fld_dx = ctx->fld.dx;
+  ta.fld_z0 = ctx->fld.z0;
+  ta.fld_dz = ctx->fld.dz;
+  ta.fld_h = ctx->fld.step_m;
+  ta.fld_c = ctx->fld_c;
   ta.vol_order = ctx->vol_n > 0 && ctx->vol_n <= kVolSortMax ? ctx->vol_order : nullptr;
   ta.hits = ctx->hits;
   ta.bin_counts = ctx->counts;
@@ -961,7 +997,7 @@ int run(sonar_ctx* ctx, const sonar_pose* poses, int P, const sonar_params* p, c
   CU(cudaEventRecord(ctx->ev_in, ctx->user_stream));
   CU(cudaStreamWaitEvent(ctx->stream, ctx->ev_in, 0));
   Derived d;
-  if ((rc = derive(ctx, p, ssp, poses[0].t[2], P, d))) return rc;
+  if ((rc = derive(ctx, p, ssp, poses[0].t[0], poses[0].t[2], P, d))) return rc;
   if ((int64_t)P * d.nr_pad + 1 > (1LL << 31) - 1) return fail(ctx, SONAR_E_UNSUPPORTED, "batch too large");
   if ((rc = ensure_tables(ctx, p, d))) return rc;
   if ((rc = ensure_workspace(ctx, P, d))) return rc;
@@ -1106,7 +1142,7 @@ int run_async(sonar_ctx* ctx, const sonar_pose* poses, int P, const sonar_params
   CU(cudaEventRecord(ctx->ev_in, ctx->user_stream));
   CU(cudaStreamWaitEvent(ctx->stream, ctx->ev_in, 0));
   Derived d;
-  if ((rc = derive(ctx, p, ssp, poses[0].t[2], P, d))) return rc;
+  if ((rc = derive(ctx, p, ssp, poses[0].t[0], poses[0].t[2], P, d))) return rc;
   if ((int64_t)P * d.nr_pad + 1 > (1LL << 31) - 1) return fail(ctx, SONAR_E_UNSUPPORTED, "batch too large");
   if ((rc = ensure_tables(ctx, p, d))) return rc;
   if ((rc = ensure_workspace(ctx, P, d))) return rc;
@@ -1287,6 +1323,34 @@ int sonar_set_option(sonar_ctx* ctx, int32_t option, int64_t value) {
   return SONAR_OK;
 }
 
+int sonar_set_field(sonar_ctx* ctx, const sonar_field* f) {
+  if (!ctx) return SONAR_E_ARG;
+  CU(cudaSetDevice(ctx->device));
+  {
+    const int rc = drain(ctx);
+    if (rc) return rc;
+  }
+  if (!f || f->nx == 0) {
+    ctx->fld = sonar_field{};
+  } else {
+    if (f->nx < 2 || f->nz < 2 || !(f->dx > 0) || !(f->dz > 0) || !(f->step_m > 0) || !f->c ||
+        !isfinite(f->x0) || !isfinite(f->z0))
+      return fail(ctx, SONAR_E_ARG, "field: nx, nz >= 2, dx, dz, step > 0 and a grid are required");
+    const int64_t n = (int64_t)f->nx * f->nz;
+    for (int64_t k = 0; k < n; ++k)
+      if (!(f->c[k] > 0) || !isfinite(f->c[k])) return fail(ctx, SONAR_E_ARG, "field speeds must be positive");
+    CU(cudaStreamSynchronize(ctx->stream));
+    dfree(ctx->fld_c);
+    CU(cudaMalloc(&ctx->fld_c, sizeof(double) * n));
+    CU(cudaMemcpy(ctx->fld_c, f->c, sizeof(double) * n, cudaMemcpyHostToDevice));
+    ctx->fld_host.assign(f->c, f->c + n);
+    ctx->fld = *f;
+    ctx->fld.c = ctx->fld_host.data();
+  }
+  drop_graphs(ctx);
+  return SONAR_OK;
+}
+
 int sonar_set_volume(sonar_ctx* ctx, const sonar_volume* v) {
   if (!ctx) return SONAR_E_ARG;
   if (!v || v->n == 0) {
@@ -1341,7 +1405,7 @@ int sonar_destroy(sonar_ctx* c) {
   if (c->pose_host) cudaFreeHost(c->pose_host);
   if (c->n_cloud_host) cudaFreeHost(c->n_cloud_host);
   if (c->counters_host) cudaFreeHost(c->counters_host);
-  dfree(c->pt_route); dfree(c->vol_order);
+  dfree(c->pt_route); dfree(c->vol_order); dfree(c->fld_c);
   dfree(c->poses); dfree(c->hits); dfree(c->sorted); dfree(c->sorted_n); dfree(c->dbg_tau);
   dfree(c->n_hits);
   dfree(c->counts); dfree(c->offsets); dfree(c->S); dfree(c->S_raw); dfree(c->ptab); dfree(c->x_hi); dfree(c->x_lo); dfree(c->gain);

@@ -119,6 +119,11 @@ struct TraceArgs {
   double vol_lo[3], vol_hi[3];   // their world-frame box
   double vol_sigma;              // amplitude coefficient of each, sqrt(s_v V / n)
   float2 vol_lo_df[3], vol_span_df[3];  // lo and hi - lo as FP32 pairs
+  // range-dependent sound speed c(x, z) on a grid (fld_nx = 0: none; then `curved` selects
+  // the linear profile)
+  int32_t fld_nx, fld_nz;
+  double fld_x0, fld_dx, fld_z0, fld_dz, fld_h;
+  const double* fld_c;           // [fld_nz][fld_nx]
   const int32_t* vol_order;      // [vol_n] processing order (Morton order of the positions), or null
   HitRec* hits;
   int32_t* bin_counts;           // [n_pings * nr_pad] hits per first-tap row (zeroed by the caller)

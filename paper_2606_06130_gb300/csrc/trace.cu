@@ -556,6 +556,135 @@ __device__ __forceinline__ void dir_split(D3 d, double& ex, double& ey, double& 
 }
 __device__ __forceinline__ double ssp_c(const TraceArgs& A, double z) { return A.ssp_c0 + A.ssp_g * (z - A.ssp_z0); }
 
+// ----------------------------------------------------------------- 2-D sound-speed field
+// Sec. II.A rays bent by a range- and depth-dependent sound speed. c(x, z) is bilinear
+// on the grid, positions clamped to it (c constant outward, the gradient across a clamped
+// axis zero); returns c and (dc/dx, dc/dz).
+__device__ void field_eval(const TraceArgs& A, double x, double z, double& c, double& cx, double& cz) {
+  const int nx = A.fld_nx, nz = A.fld_nz;
+  double fx = (x - A.fld_x0) / A.fld_dx, fz = (z - A.fld_z0) / A.fld_dz;
+  bool inx = true, inz = true;
+  if (fx < 0.0) { fx = 0.0; inx = false; } else if (fx > nx - 1) { fx = nx - 1; inx = false; }
+  if (fz < 0.0) { fz = 0.0; inz = false; } else if (fz > nz - 1) { fz = nz - 1; inz = false; }
+  int i = (int)floor(fx), j = (int)floor(fz);
+  if (i > nx - 2) i = nx - 2;
+  if (j > nz - 2) j = nz - 2;
+  const double u = fx - i, v = fz - j;
+  const double* C = A.fld_c;
+  const double c00 = __ldg(&C[j * nx + i]), c10 = __ldg(&C[j * nx + i + 1]);
+  const double c01 = __ldg(&C[(j + 1) * nx + i]), c11 = __ldg(&C[(j + 1) * nx + i + 1]);
+  c = (1.0 - u) * (1.0 - v) * c00 + u * (1.0 - v) * c10 + (1.0 - u) * v * c01 + u * v * c11;
+  cx = inx ? ((1.0 - v) * (c10 - c00) + v * (c11 - c01)) / A.fld_dx : 0.0;
+  cz = inz ? ((1.0 - u) * (c01 - c00) + u * (c11 - c10)) / A.fld_dz : 0.0;
+}
+
+// Ray equations in arc length for (r, t, T), t the unit tangent:
+// dr/ds = t, dt/ds = ((grad c . t) t - grad c) / c, dT/ds = 1 / c.
+__device__ __forceinline__ void field_deriv(const TraceArgs& A, const double (&y)[7], double (&f)[7]) {
+  double c, cx, cz;
+  field_eval(A, y[0], y[2], c, cx, cz);
+  const double ic = 1.0 / c;  // one division; the three components differ from divided ones by an ulp
+  const double gt = cx * y[3] + cz * y[5];
+  f[0] = y[3];
+  f[1] = y[4];
+  f[2] = y[5];
+  f[3] = (gt * y[3] - cx) * ic;
+  f[4] = gt * y[4] * ic;
+  f[5] = (gt * y[5] - cz) * ic;
+  f[6] = ic;
+}
+
+// One classical Runge-Kutta step of length h, the tangent renormalised after it.
+__device__ void rk4_field(const TraceArgs& A, const double (&y)[7], double h, double (&out)[7]) {
+  double k1[7], k2[7], k3[7], k4[7], tmp[7];
+  field_deriv(A, y, k1);
+#pragma unroll
+  for (int i = 0; i < 7; ++i) tmp[i] = y[i] + 0.5 * h * k1[i];
+  field_deriv(A, tmp, k2);
+#pragma unroll
+  for (int i = 0; i < 7; ++i) tmp[i] = y[i] + 0.5 * h * k2[i];
+  field_deriv(A, tmp, k3);
+#pragma unroll
+  for (int i = 0; i < 7; ++i) tmp[i] = y[i] + h * k3[i];
+  field_deriv(A, tmp, k4);
+#pragma unroll
+  for (int i = 0; i < 7; ++i) out[i] = y[i] + h / 6.0 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
+  const double in = 1.0 / sqrt(out[3] * out[3] + out[4] * out[4] + out[5] * out[5]);
+  out[3] *= in;
+  out[4] *= in;
+  out[5] *= in;
+}
+
+// Route in the field: RK4 steps of fld_h, the chord of each step intersected with the
+// scene and the sea surface; a hit's time and arc length interpolate the step's end values
+// in the chord fraction f; a reflection reflects the normalised (1 - f) t_i + f t_i+1.
+__device__ void route_field(const TraceArgs& A, int ping, D3 o, D3 d0, D3 us, uint32_t ray, uint32_t sub,
+                            double dOmega, uint32_t keybase) {
+  double y[7] = {o.x, o.y, o.z, d0.x, d0.y, d0.z, 0.0};
+  double sarc = 0.0, gam = 1.0;
+  int bounce = 0, prev = -1;
+  for (int iter = 0;; ++iter) {
+    if (iter >= 200000) { atomicOr(A.err, kErrLoop); return; }
+    if (!(y[6] < A.T_stop)) break;
+    double yn[7];
+    rk4_field(A, y, A.fld_h, yn);
+    const D3 pos = d3(y[0], y[1], y[2]);
+    const D3 chv = d3(yn[0] - y[0], yn[1] - y[1], yn[2] - y[2]);
+    const double len = sqrt(chv.x * chv.x + chv.y * chv.y + chv.z * chv.z);
+    if (!(len > 0.0)) break;
+    const D3 dc = d3(chv.x / len, chv.y / len, chv.z / len);
+    Hit hq = closest_hit(A.sc, pos, dc, kEpsHit, len, prev >= 0 ? prev : -1, A.err);
+    double ts = INFINITY;
+    if (A.has_surface && prev != -2 && dc.z != 0.0) {
+      const double t = (A.surface_z - pos.z) / dc.z;
+      if (t > kEpsHit && t <= len) ts = t;
+    }
+    if (hq.prim < 0 && ts == INFINITY) {
+#pragma unroll
+      for (int i = 0; i < 7; ++i) y[i] = yn[i];
+      sarc += A.fld_h;
+      prev = -1;
+      continue;
+    }
+    const bool surf = ts < hq.t;
+    const double thit = surf ? ts : hq.t;
+    const double f = thit / len;
+    const double T_hit = y[6] + f * (yn[6] - y[6]), s_hit = sarc + f * A.fld_h;
+    if (!(T_hit <= A.T_stop)) break;
+    D3 n;
+    if (surf) {
+      if (bounce >= A.max_bounces) break;
+      n = d3(0.0, 0.0, 1.0);
+      gam *= A.r_surface;
+    } else {
+      const float kinc = kinc32(A.sc, hq.leaf, dc);
+      const float amp = lambert(A, (float)gam, A.sc.tri_mu[hq.leaf], kinc, (float)dOmega, (float)s_hit);
+      emit(A, ping, 2.0 * T_hit, amp, speckle(A, ray, sub, bounce), (float)us.y, (float)us.z, hq.prim,
+           keybase | (uint32_t)bounce);
+      if (!((A.sc.tri_flags[hq.leaf] & 1) && bounce < A.max_bounces)) break;
+      n = tri_normal64(A.sc, hq.leaf);
+      gam *= A.r_seabed;
+    }
+    double tg[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) tg[k] = (1.0 - f) * y[3 + k] + f * yn[3 + k];
+    const double tn = sqrt(tg[0] * tg[0] + tg[1] * tg[1] + tg[2] * tg[2]);
+    D3 t = d3(tg[0] / tn, tg[1] / tn, tg[2] / tn);
+    const double k = 2.0 * (t.x * n.x + t.y * n.y + t.z * n.z);
+    t = d3(t.x - k * n.x, t.y - k * n.y, t.z - k * n.z);
+    y[0] = pos.x + thit * dc.x;
+    y[1] = pos.y + thit * dc.y;
+    y[2] = pos.z + thit * dc.z;
+    y[3] = t.x;
+    y[4] = t.y;
+    y[5] = t.z;
+    y[6] = T_hit;
+    sarc = s_hit;
+    bounce++;
+    prev = surf ? -2 : hq.prim;
+  }
+}
+
 __device__ void route_curved(const TraceArgs& A, int ping, D3 o, D3 d0, D3 us, uint32_t ray, uint32_t sub,
                              double dOmega, uint32_t keybase) {
   D3 pos = o;
@@ -748,7 +877,8 @@ __global__ void __launch_bounds__(128, CURVED ? 4 : SONAR_TRACE_CTAS) k_trace(Tr
       const D3 us = d3(A.ray_dirs[3 * sr], A.ray_dirs[3 * sr + 1], A.ray_dirs[3 * sr + 2]);
       const D3 dw = rot(P.R, us);
       const D3 o = d3(P.t[0], P.t[1], P.t[2]);
-      route_curved(A, ping, o, dw, us, ray, sub, dOmega, keybase);
+      if (A.fld_nx > 0) route_field(A, ping, o, dw, us, ray, sub, dOmega, keybase);
+      else route_curved(A, ping, o, dw, us, ray, sub, dOmega, keybase);
     } else {
       // world direction R us and origin t as FP32 pairs
       const float* uh = A.ray_dirs32 + 3 * sr;

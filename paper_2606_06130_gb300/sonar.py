@@ -64,6 +64,11 @@ class sonar_volume(C.Structure):
     _fields_ = [("n", C.c_int64), ("lo", C.c_double * 3), ("hi", C.c_double * 3), ("s_v", C.c_double)]
 
 
+class sonar_field(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("nz", C.c_int32), ("x0", C.c_double), ("dx", C.c_double), ("z0", C.c_double),
+                ("dz", C.c_double), ("c", C.POINTER(C.c_double)), ("step_m", C.c_double)]
+
+
 class sonar_point(C.Structure):
     _fields_ = [("x", C.c_float), ("y", C.c_float), ("z", C.c_float), ("intensity", C.c_float),
                 ("beam", C.c_int32), ("bin", C.c_int32)]
@@ -96,6 +101,7 @@ _SIGS = {
     "sonar_last_error": (C.c_char_p, [C.c_void_p]),
     "sonar_set_option": (C.c_int, [C.c_void_p, C.c_int32, C.c_int64]),
     "sonar_set_volume": (C.c_int, [C.c_void_p, C.POINTER(sonar_volume)]),
+    "sonar_set_field": (C.c_int, [C.c_void_p, C.POINTER(sonar_field)]),
     "sonar_scene_upload": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p,
                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64]),
     "sonar_ping": (C.c_int, [C.c_void_p, C.POINTER(sonar_pose), C.POINTER(sonar_params), C.POINTER(sonar_ssp),
@@ -226,6 +232,17 @@ class Sonar:
         """Water-column scatterers of the following pings (n = 0: none)."""
         v = sonar_volume(int(n), (C.c_double * 3)(*map(float, lo)), (C.c_double * 3)(*map(float, hi)), float(s_v))
         self._check(lib().sonar_set_volume(self.h, C.byref(v)))
+
+    def set_field(self, field: dict | None):
+        """Range-dependent sound speed of the following pings: {"x0", "dx", "z0", "dz",
+        "c": [nz][nx] m/s, "h": integration step in m}, or None to remove it."""
+        if field is None:
+            self._check(lib().sonar_set_field(self.h, None))
+            return
+        c = np.ascontiguousarray(field["c"], np.float64)
+        f = sonar_field(c.shape[1], c.shape[0], float(field["x0"]), float(field["dx"]), float(field["z0"]),
+                        float(field["dz"]), c.ctypes.data_as(C.POINTER(C.c_double)), float(field["h"]))
+        self._check(lib().sonar_set_field(self.h, C.byref(f)))
 
     def upload(self, scene):
         v = np.ascontiguousarray(scene.verts, np.float32)
