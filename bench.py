@@ -552,6 +552,21 @@ def other_forms(torch, s, inputs, dev):
                                "hits": s.stats()["n_hits"],
                                "note": "10^6 water-column scatterers (s_v 1e-4 /m) on top of the mesh"}
     s.set_volume(0)
+    # rays through a range-dependent thermocline (RK4 steps of 0.5 m, chords per step)
+    xs, zs = np.linspace(-4.0, 16.0, 21), np.linspace(-12.0, 1.0, 27)
+    thermo = np.array([[1500.0 - 6.0 * math.tanh((z + 6.0 + 0.15 * x) / 1.5) for x in xs] for z in zs])
+    s.set_field({"x0": -4.0, "dx": 1.0, "z0": -12.0, "dz": 0.5, "c": thermo, "h": 0.5})
+    pf = dict(params, c_ref=1500.0)
+    for _ in range(2):
+        s.ping(poses[0], pf, ssp, precision="fp32")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(5):
+        s.ping(poses[0], pf, ssp, precision="fp32")
+    torch.cuda.synchronize()
+    out["c2_field_h0.5_fp32"] = {"value": 5 / (time.perf_counter() - t0), "unit": UNIT,
+                                 "note": "range-dependent thermocline, RK4 rays at 0.5 m steps"}
+    s.set_field(None)
     sc4, p4, poses4, ssp4 = inputs.workload("c4")
     s.upload(sc4)
     for prec in ("fp32", "bf16"):
