@@ -984,6 +984,28 @@ int drain(sonar_ctx* ctx) {
   return first;
 }
 
+// Everything a captured pipeline bakes in: shapes and parameters, output and host-word
+// pointers, options, the scene version, the profile and the workspace buffers (a
+// workspace regrow moves them). Options, volume scatterers, fields and scene uploads also
+// drop every graph outright.
+std::vector<uint8_t> pipeline_key(const sonar_ctx* ctx, int P, const sonar_params* p, const sonar_ssp* ssp,
+                                  const Derived& d, const Outputs& o) {
+  std::vector<uint8_t> k;
+  key_add(k, P); key_add(k, *p); key_add(k, o.env); key_add(k, o.cloud); key_add(k, o.cap);
+  key_add(k, o.env_host); key_add(k, o.cloud_host); key_add(k, o.pose_src); key_add(k, o.counters_map);
+  key_add(k, o.n_cloud_map);
+  key_add(k, ctx->debug); key_add(k, ctx->timing); key_add(k, ctx->synth_opt); key_add(k, ctx->scene_version);
+  key_add(k, ctx->raw_u);
+  key_add(k, d.c_ref);
+  if (ssp) {
+    key_add(k, ssp->n_nodes);
+    for (int i = 0; i < ssp->n_nodes; ++i) { key_add(k, ssp->c[i]); if (ssp->z) key_add(k, ssp->z[i]); }
+  }
+  key_add(k, ctx->vol_order);
+  key_add(k, ctx->hits); key_add(k, ctx->S); key_add(k, ctx->x_hi); key_add(k, ctx->y_hi); key_add(k, ctx->keys);
+  return k;
+}
+
 int run(sonar_ctx* ctx, const sonar_pose* poses, int P, const sonar_params* p, const sonar_ssp* ssp, float* env,
         sonar_point* cloud, int64_t cloud_cap, int64_t* n_cloud) {
   if (!ctx) return SONAR_E_ARG;
@@ -1043,19 +1065,7 @@ int run(sonar_ctx* ctx, const sonar_pose* poses, int P, const sonar_params* p, c
   int kernels = 0;
   // stage events cannot be timed when recorded by graph nodes: timing runs eagerly
   if (ctx->use_graph && !timed) {
-    std::vector<uint8_t> k;
-    key_add(k, P); key_add(k, *p); key_add(k, o.env); key_add(k, o.cloud); key_add(k, o.cap);
-    key_add(k, o.env_host); key_add(k, o.cloud_host); key_add(k, ctx->pose_host); key_add(k, ctx->counters_host);
-    key_add(k, ctx->n_cloud_host);
-    key_add(k, ctx->debug); key_add(k, ctx->timing); key_add(k, ctx->synth_opt); key_add(k, ctx->scene_version);
-    key_add(k, ctx->raw_u);
-    key_add(k, d.c_ref);
-    if (ssp) {
-      key_add(k, ssp->n_nodes);
-      for (int i = 0; i < ssp->n_nodes; ++i) { key_add(k, ssp->c[i]); if (ssp->z) key_add(k, ssp->z[i]); }
-    }
-    key_add(k, ctx->vol_order);
-    key_add(k, ctx->hits); key_add(k, ctx->S); key_add(k, ctx->x_hi); key_add(k, ctx->y_hi); key_add(k, ctx->keys);
+    const std::vector<uint8_t> k = pipeline_key(ctx, P, p, ssp, d, o);
     sonar_ctx::GraphEntry* ge = nullptr;
     for (auto& e : ctx->graphs)
       if (e.key == k) ge = &e;
@@ -1189,18 +1199,7 @@ int run_async(sonar_ctx* ctx, const sonar_pose* poses, int P, const sonar_params
 
   int kernels = 0;
   if (ctx->use_graph && !ctx->timing) {
-    std::vector<uint8_t> k;
-    key_add(k, P); key_add(k, *p); key_add(k, o.env); key_add(k, o.cloud); key_add(k, o.cap);
-    key_add(k, sl.pose_host); key_add(k, sl.counters_host); key_add(k, sl.n_cloud_host);
-    key_add(k, ctx->debug); key_add(k, ctx->synth_opt); key_add(k, ctx->scene_version);
-    key_add(k, ctx->raw_u);
-    key_add(k, d.c_ref);
-    if (ssp) {
-      key_add(k, ssp->n_nodes);
-      for (int i = 0; i < ssp->n_nodes; ++i) { key_add(k, ssp->c[i]); if (ssp->z) key_add(k, ssp->z[i]); }
-    }
-    key_add(k, ctx->vol_order);
-    key_add(k, ctx->hits); key_add(k, ctx->S); key_add(k, ctx->x_hi); key_add(k, ctx->y_hi); key_add(k, ctx->keys);
+    const std::vector<uint8_t> k = pipeline_key(ctx, P, p, ssp, d, o);
     if (!sl.gexec || k != sl.gkey) {
       if (sl.gexec) { cudaGraphExecDestroy(sl.gexec); sl.gexec = nullptr; }
       cudaGraph_t g;

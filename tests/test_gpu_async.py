@@ -115,3 +115,25 @@ def test_async_rejects_pageable_outputs(sonar):
         sonar.ping_async([poses[0]], params, ssp, env=env)
     assert e.value.code == SONAR_E_ARG
     sonar.wait()
+
+
+def test_async_batches(sonar):
+    """Asynchronous calls of three pings each, alternating between two pinned buffers:
+    every ping within the FP32 bar of the oracle."""
+    scene, params, poses, ssp = inputs.workload("c1")
+    sonar.upload(scene)
+    ps = _poses(poses[0], 9, 4)
+    nb = params["n_beam_az"] * params["n_beam_el"]
+    shape = (3, params["n_beam_el"], params["n_beam_az"], params["n_range"])
+    bufs = [torch.empty(shape, dtype=torch.float32, pin_memory=True) for _ in range(3)]
+    counts = []
+    for c in range(3):
+        _, _, n = sonar.ping_async(ps[3 * c:3 * c + 3], params, ssp, env=bufs[c], cloud_cap=nb)
+        counts.append(n)
+    sonar.wait()
+    for c in range(3):
+        assert np.all(counts[c] > 0)
+        for i in range(3):
+            E_ref, _, _ = oracle.volume(params, oracle.trace(scene, params, ps[3 * c + i], ssp))
+            E = bufs[c][i].reshape(-1, params["n_range"]).double().numpy()
+            assert parity.nl2(E, E_ref) <= 1e-4, (c, i)

@@ -122,3 +122,17 @@ def test_cross_rejects_refraction_and_bad_values(sonar):
     with pytest.raises(SonarError) as e:
         sonar.set_option(SONAR_OPT_CROSS, 2)
     assert e.value.code == SONAR_E_ARG
+
+
+def test_cross_without_reflections_is_monostatic(sonar):
+    """max_bounces 0 leaves no reflected route, so cross terms add nothing but the point
+    scatterers' pairs of image routes (none either: only the direct route remains)."""
+    scene, params, poses, ssp = inputs.workload("wall_mirror")
+    params = dict(params, max_bounces=0)
+    E = _ping(sonar, scene, params, poses[0], ssp)
+    hits = sonar.hits()
+    assert _cross_counts(hits["key"]) == (0, 0, 0)
+    ref = oracle.trace(scene, dict(params, cross=1), poses[0], ssp)
+    parity.check_hits(hits, ref, params["n_sub"])
+    E_ref, _, _ = oracle.volume(params, ref)
+    assert parity.nl2(E, E_ref) <= 1e-4

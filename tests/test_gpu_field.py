@@ -115,3 +115,18 @@ def test_field_arguments_and_combinations(sonar):
     env, _, _ = sonar.ping(pose, dict(params, c_ref=1500.0), ISO)
     torch.cuda.synchronize()
     assert parity.nl2(E_f, env.reshape(-1, params["n_range"]).double().cpu().numpy()) < 1e-5
+
+
+def test_smallest_field_grid(sonar):
+    """A 2 x 2 grid (one bilinear cell covering nothing: every position is clamped onto
+    it) with a depth gradient: against the oracle."""
+    scene, params, pose = _wall()
+    zs = pose["t"][2]
+    fld = {"x0": 0.0, "dx": 1.0, "z0": zs - 0.5, "dz": 1.0,
+           "c": np.array([[1495.0, 1496.0], [1505.0, 1504.0]]), "h": 0.1}
+    E, hits, _ = _run(sonar, scene, params, pose, fld)
+    ref = oracle.trace(scene, dict(params, field=fld), pose, ISO)
+    excluded, matched = parity.check_hits(hits, ref, params["n_sub"])
+    assert matched >= ref["n"] - 2 * (excluded + 1) and ref["n"] > 1000
+    E_ref, _, _ = oracle.volume(params, ref)
+    assert parity.nl2(E, E_ref) <= 1e-4

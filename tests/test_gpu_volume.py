@@ -125,3 +125,33 @@ def test_set_volume_rejects_bad_arguments(sonar):
         assert e.value.code == SONAR_E_UNSUPPORTED
     finally:
         sonar.set_volume(0)
+
+
+def test_volume_degenerate_cases(sonar):
+    """One scatterer; a box beyond the range (no echoes); a zero s_v (echoes of zero
+    amplitude): each against the oracle."""
+    scene = inputs.Scene(np.zeros((0, 3), np.float32), np.zeros((0, 3), np.int32), np.zeros(0, np.float32),
+                         np.zeros(0, np.uint8))
+    params = dict(inputs.sensor_params("c1"), surface_z=None, max_bounces=0, n_ray_az=4, n_ray_el=2, r_max=4.0)
+    pose = inputs.pose((0.0, 0.0, -10.0))
+    sonar.upload(scene)
+    for n, lo, hi, sv in [(1, (1.0, -0.5, -10.5), (2.0, 0.5, -9.5), 1e-2),
+                          (500, (50.0, 50.0, 0.0), (60.0, 60.0, 10.0), 1e-3),
+                          (200, (-2.0, -2.0, -12.0), (2.0, 2.0, -8.0), 0.0)]:
+        sonar.set_volume(n, lo, hi, sv)
+        try:
+            env, _, _ = sonar.ping(pose, params, inputs.ssp("c1"))
+            torch.cuda.synchronize()
+            hits = sonar.hits()
+        finally:
+            sonar.set_volume(0)
+        ref = oracle.trace(scene, _vol(params, n, lo, hi, sv), pose, inputs.ssp("c1"))
+        assert _volume_keys(hits["key"]) == ref["n"]
+        if ref["n"] and sv > 0:  # zero amplitudes have no relative error to compare
+            parity.check_hits(hits, ref, params["n_sub"], per_tie=0)
+        E = env.reshape(-1, params["n_range"]).double().cpu().numpy()
+        E_ref, _, _ = oracle.volume(params, ref)
+        if np.linalg.norm(E_ref) > 0:
+            assert parity.nl2(E, E_ref) <= 1e-4
+        else:
+            assert np.all(E == 0.0)
