@@ -778,6 +778,8 @@ int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, cons
   ta.fld_z0 = ctx->fld.z0;
   ta.fld_dz = ctx->fld.dz;
   ta.fld_h = ctx->fld.step_m;
+  ta.fld_idx = ctx->fld.nx > 0 ? 1.0 / ctx->fld.dx : 0.0;
+  ta.fld_idz = ctx->fld.nx > 0 ? 1.0 / ctx->fld.dz : 0.0;
   ta.fld_c = ctx->fld_c;
   ta.vol_order = ctx->vol_n > 0 && ctx->vol_n <= kVolSortMax ? ctx->vol_order : nullptr;
   ta.hits = ctx->hits;

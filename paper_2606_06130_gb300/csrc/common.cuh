@@ -123,6 +123,7 @@ struct TraceArgs {
   // the linear profile)
   int32_t fld_nx, fld_nz;
   double fld_x0, fld_dx, fld_z0, fld_dz, fld_h;
+  double fld_idx, fld_idz;       // 1 / dx, 1 / dz
   const double* fld_c;           // [fld_nz][fld_nx]
   const int32_t* vol_order;      // [vol_n] processing order (Morton order of the positions), or null
   HitRec* hits;

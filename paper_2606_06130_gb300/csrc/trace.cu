@@ -26,15 +26,11 @@ namespace {
 __device__ __forceinline__ double dm(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ double da(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ double ds(double a, double b) { return __dsub_rn(a, b); }
-__device__ __forceinline__ double dd(double a, double b) { return __ddiv_rn(a, b); }
 
 struct D3 { double x, y, z; };
 __device__ __forceinline__ D3 d3(double x, double y, double z) { D3 r = {x, y, z}; return r; }
 __device__ __forceinline__ D3 sub(D3 a, D3 b) { return d3(ds(a.x, b.x), ds(a.y, b.y), ds(a.z, b.z)); }
 __device__ __forceinline__ double dot(D3 a, D3 b) { return da(da(dm(a.x, b.x), dm(a.y, b.y)), dm(a.z, b.z)); }
-__device__ __forceinline__ D3 cross(D3 a, D3 b) {
-  return d3(ds(dm(a.y, b.z), dm(a.z, b.y)), ds(dm(a.z, b.x), dm(a.x, b.z)), ds(dm(a.x, b.y), dm(a.y, b.x)));
-}
 // contracted forms for positions and distances
 __device__ __forceinline__ double dotf(D3 a, D3 b) { return fma(a.z, b.z, fma(a.y, b.y, a.x * b.x)); }
 __device__ __forceinline__ D3 rot(const double* R, D3 v) {
@@ -65,10 +61,6 @@ __device__ __forceinline__ double drsqrt_nr(double s) {
   y = y * fma(-0.5 * s, y * y, 1.5);
   y = y * fma(-0.5 * s, y * y, 1.5);
   return y;
-}
-
-__device__ __forceinline__ D3 tri_vert(const float* v, int k) {
-  return d3((double)v[3 * k], (double)v[3 * k + 1], (double)v[3 * k + 2]);
 }
 
 // ----------------------------------------------------------------- FP32 pairs
@@ -144,26 +136,6 @@ __device__ __forceinline__ F2 f2_of(double x) {
   return F2{hi, (float)(x - (double)hi)};
 }
 
-// FP64 two-sided ray/triangle test (Moller-Trumbore), inclusive edges. One reciprocal
-// of the determinant replaces three divisions (FP64 division is a long sequence on this
-// part); u, v, t differ from divided values by at most an ulp.
-__device__ bool tri_test64(const float* tv, D3 o, D3 d, double& t) {
-  D3 a = tri_vert(tv, 0), b = tri_vert(tv, 1), c = tri_vert(tv, 2);
-  D3 e1 = sub(b, a), e2 = sub(c, a);
-  D3 p = cross(d, e2);
-  double det = dot(e1, p);
-  if (det == 0.0) return false;
-  const double ad = fabs(det);
-  const double inv = ad > 1e-30 && ad < 1e30 ? ddiv_nr(1.0, det) : dd(1.0, det);
-  D3 s = sub(o, a);
-  double u = dm(dot(s, p), inv);
-  if (!(u >= 0.0 && u <= 1.0)) return false;
-  D3 q = cross(s, e1);
-  double v = dm(dot(d, q), inv);
-  if (!(v >= 0.0 && da(u, v) <= 1.0)) return false;
-  t = dm(dot(e2, q), inv);
-  return true;
-}
 
 __device__ __forceinline__ double4_32a load_plane(const DevScene& sc, int leaf) {
   const double2* p = reinterpret_cast<const double2*>(sc.tri_plane + leaf);
@@ -239,11 +211,17 @@ __device__ __forceinline__ void lead32(const D3& v, float* f) { f[0] = (float)v.
 __device__ __forceinline__ void lead32(const DF3& v, float* f) { f[0] = v.x.hi; f[1] = v.y.hi; f[2] = v.z.hi; }
 __device__ __forceinline__ void r_inf(double& x) { x = INFINITY; }
 __device__ __forceinline__ void r_inf(F2& x) { x = F2{INFINITY, 0.f}; }
-// FP64 ray/triangle decision with its distance inside (tmin, tmax]
-__device__ bool tri_test64(const float* tv, D3 o, D3 d, double& t);
+// Near-tie ray/triangle decision with its distance inside (tmin, tmax], for the FP64
+// legs (curved rays, field routes, point, cross-term and volume legs): the FP32-pair test
+// below, whose decision differs from an FP64 one only for margins below ~1e-13.
+__device__ bool tri_test_df(const float* tv, const struct DF3& o, const struct DF3& d, F2& t);
 __device__ __forceinline__ bool tri_exact(const float* tv, const D3& o, const D3& d, double tmin, double tmax,
                                           double& t) {
-  return tri_test64(tv, o, d, t) && t > tmin && t <= tmax;
+  F2 tp;
+  if (!tri_test_df(tv, DF3{f2_of(o.x), f2_of(o.y), f2_of(o.z)}, DF3{f2_of(d.x), f2_of(d.y), f2_of(d.z)}, tp))
+    return false;
+  t = to_d(tp);
+  return t > tmin && t <= tmax;
 }
 // The same two-sided test in FP32 pairs (edges exact from the FP32 vertices; ~2^-46
 // relative after that). Its decision differs from the FP64 test's only where u, v or
@@ -559,10 +537,12 @@ __device__ __forceinline__ double ssp_c(const TraceArgs& A, double z) { return A
 // ----------------------------------------------------------------- 2-D sound-speed field
 // Sec. II.A rays bent by a range- and depth-dependent sound speed. c(x, z) is bilinear
 // on the grid, positions clamped to it (c constant outward, the gradient across a clamped
-// axis zero); returns c and (dc/dx, dc/dz).
+// axis zero); returns c and (dc/dx, dc/dz). FP64 division is a long instruction sequence
+// on this part, so the grid spacings enter as host-computed reciprocals (results differ
+// from divided ones by an ulp).
 __device__ void field_eval(const TraceArgs& A, double x, double z, double& c, double& cx, double& cz) {
   const int nx = A.fld_nx, nz = A.fld_nz;
-  double fx = (x - A.fld_x0) / A.fld_dx, fz = (z - A.fld_z0) / A.fld_dz;
+  double fx = (x - A.fld_x0) * A.fld_idx, fz = (z - A.fld_z0) * A.fld_idz;
   bool inx = true, inz = true;
   if (fx < 0.0) { fx = 0.0; inx = false; } else if (fx > nx - 1) { fx = nx - 1; inx = false; }
   if (fz < 0.0) { fz = 0.0; inz = false; } else if (fz > nz - 1) { fz = nz - 1; inz = false; }
@@ -574,8 +554,8 @@ __device__ void field_eval(const TraceArgs& A, double x, double z, double& c, do
   const double c00 = __ldg(&C[j * nx + i]), c10 = __ldg(&C[j * nx + i + 1]);
   const double c01 = __ldg(&C[(j + 1) * nx + i]), c11 = __ldg(&C[(j + 1) * nx + i + 1]);
   c = (1.0 - u) * (1.0 - v) * c00 + u * (1.0 - v) * c10 + (1.0 - u) * v * c01 + u * v * c11;
-  cx = inx ? ((1.0 - v) * (c10 - c00) + v * (c11 - c01)) / A.fld_dx : 0.0;
-  cz = inz ? ((1.0 - u) * (c01 - c00) + u * (c11 - c10)) / A.fld_dz : 0.0;
+  cx = inx ? ((1.0 - v) * (c10 - c00) + v * (c11 - c01)) * A.fld_idx : 0.0;
+  cz = inz ? ((1.0 - u) * (c01 - c00) + u * (c11 - c10)) * A.fld_idz : 0.0;
 }
 
 // Ray equations in arc length for (r, t, T), t the unit tangent:
@@ -583,7 +563,7 @@ __device__ void field_eval(const TraceArgs& A, double x, double z, double& c, do
 __device__ __forceinline__ void field_deriv(const TraceArgs& A, const double (&y)[7], double (&f)[7]) {
   double c, cx, cz;
   field_eval(A, y[0], y[2], c, cx, cz);
-  const double ic = 1.0 / c;  // one division; the three components differ from divided ones by an ulp
+  const double ic = ddiv_nr(1.0, c);  // one reciprocal (within an ulp of 1 / c)
   const double gt = cx * y[3] + cz * y[5];
   f[0] = y[3];
   f[1] = y[4];
@@ -609,7 +589,7 @@ __device__ void rk4_field(const TraceArgs& A, const double (&y)[7], double h, do
   field_deriv(A, tmp, k4);
 #pragma unroll
   for (int i = 0; i < 7; ++i) out[i] = y[i] + h / 6.0 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
-  const double in = 1.0 / sqrt(out[3] * out[3] + out[4] * out[4] + out[5] * out[5]);
+  const double in = drsqrt_nr(out[3] * out[3] + out[4] * out[4] + out[5] * out[5]);
   out[3] *= in;
   out[4] *= in;
   out[5] *= in;
@@ -630,9 +610,10 @@ __device__ void route_field(const TraceArgs& A, int ping, D3 o, D3 d0, D3 us, ui
     rk4_field(A, y, A.fld_h, yn);
     const D3 pos = d3(y[0], y[1], y[2]);
     const D3 chv = d3(yn[0] - y[0], yn[1] - y[1], yn[2] - y[2]);
-    const double len = sqrt(chv.x * chv.x + chv.y * chv.y + chv.z * chv.z);
-    if (!(len > 0.0)) break;
-    const D3 dc = d3(chv.x / len, chv.y / len, chv.z / len);
+    const double len2 = chv.x * chv.x + chv.y * chv.y + chv.z * chv.z;
+    if (!(len2 > 0.0)) break;
+    const double il = drsqrt_nr(len2), len = len2 * il;
+    const D3 dc = d3(chv.x * il, chv.y * il, chv.z * il);
     Hit hq = closest_hit(A.sc, pos, dc, kEpsHit, len, prev >= 0 ? prev : -1, A.err);
     double ts = INFINITY;
     if (A.has_surface && prev != -2 && dc.z != 0.0) {
@@ -648,7 +629,7 @@ __device__ void route_field(const TraceArgs& A, int ping, D3 o, D3 d0, D3 us, ui
     }
     const bool surf = ts < hq.t;
     const double thit = surf ? ts : hq.t;
-    const double f = thit / len;
+    const double f = thit * il;
     const double T_hit = y[6] + f * (yn[6] - y[6]), s_hit = sarc + f * A.fld_h;
     if (!(T_hit <= A.T_stop)) break;
     D3 n;
