@@ -2,13 +2,17 @@
  * FP64 CPU oracle for per-ping coherent echo formation in a volumetric 3D sonar
  * ("Towards Realistic 3D Sonar Simulation", Sec. II.A-II.B, Sec. III Eq. 1-3).
  *
- * TEST INFRASTRUCTURE ONLY: loaded by tests/, __graft_entry__.smoke() and the
- * cpu_baseline leg of bench.py. The product path never loads it. It is written
+ * TEST INFRASTRUCTURE ONLY: loaded by tests/, __graft_entry__.smoke(), and bench.py's
+ * cpu_baseline leg and reference arm. The product path never loads it. It is written
  * plainly (no blocking, no fusion, FP64 everywhere, closed forms evaluated directly)
  * so that each step can be checked against the reading of the paper stated beside it.
  *
- * Parity unpinned: Lambertian amplitudes on meshes, speckle statistics, multi-bounce
- * mesh routes and curved-ray mesh hits have no closed form or brute-force check.
+ * Parity unpinned: Lambertian amplitudes on general meshes, speckle statistics and
+ * multi-bounce mesh routes beyond one mirror have no closed form or brute-force check.
+ * Curved-ray mesh hits are cross-checked, not pinned: the exact-arc route and the
+ * independent Runge-Kutta field route agree to the arcs' chord error. Cross terms,
+ * volume scatterers and field rays have their own pins (tests/test_oracle_cross.py,
+ * test_oracle_volume.py, test_oracle_field.py).
  */
 #include "sonar_oracle.h"
 
