@@ -194,26 +194,31 @@ def stage_work(stage, params, stats, n_pings):
     return None
 
 
-def read_traffic(kernel):
-    """DRAM bytes per launch from the committed ncu summary, or None."""
+def read_profile(kernel):
+    """(DRAM bytes, executed warp instructions) per launch from the committed ncu
+    summary (profiles/dram_traffic.txt), each None when absent or when the kernel's
+    source has changed since the capture."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     try:
-        src_hash = None
+        row = None
         for line in open(path):
             if line.startswith("#") or not line.strip():
                 continue
-            k, nbytes, h = line.split()[:3]
-            if k == kernel:
-                src_hash = h
+            f = line.split()
+            if f[0] == kernel:
+                row = f
                 break
-        if src_hash is None:
-            return None
+        if row is None:
+            return None, None
         import hashlib
-        unit = {"k_synth_tz": "synth_tc.cu", "k_gemm": "beamform.cu", "k_trace": "trace.cu"}.get(kernel)
+        unit = {"k_synth_tz": "synth_tc.cu", "k_gemm": "beamform.cu", "k_trace": "trace.cu",
+                "k_volume": "trace.cu"}.get(kernel)
         cur = hashlib.sha1(open(os.path.join(ROOT, "paper_2606_06130_gb300", "csrc", unit), "rb").read()).hexdigest()[:12]
-        return float(nbytes) if cur == src_hash else None
-    except (OSError, ValueError):
-        return None
+        if cur != row[2]:
+            return None, None
+        return float(row[1]), (float(row[3]) if len(row) > 3 else None)
+    except (OSError, ValueError, IndexError):
+        return None, None
 
 
 # ------------------------------------------------------------------ our arm
@@ -372,11 +377,19 @@ def run_ours(args, ws, rank, local):
         peak, punit, achieved = pk["hbm_gbs"], "GB/s", amount / dt_s / 1e9
         pnote = f"HBM copy, {pk_kind}"
     kname = {"synth": "k_synth_tz", "beamform": "k_gemm", "convert": "k_convert"}[dom]
-    traffic = read_traffic(kname)
+    traffic, winst = read_profile(kname)
     roof = {"kernel": kname,
             "bound": bound, "achieved": achieved, "peak": peak, "unit": punit, "frac": achieved / peak,
             "peak_source": pnote, "traffic": traffic,
             "algorithmic_per_launch": amount, "algorithmic_unit": unit, "launch_ms": mean_stage[dom]}
+    if winst is not None:
+        # what bounds the synthesis in practice: instruction issue, 4 warp instructions per
+        # clock per SM at most (152 SMs at the sampled clock, else 2070 MHz)
+        mhz = (clk or {}).get("sm_mhz") or 2070.0
+        ipeak = 4 * 152 * mhz * 1e6
+        roof["issue"] = {"warp_instructions_per_launch": winst, "source": "ncu smsp__inst_executed.sum",
+                         "achieved": winst / dt_s, "peak": ipeak, "unit": "warp instructions/s",
+                         "frac": winst / dt_s / ipeak}
 
     # CPU baseline leg: the oracle timed on a sample of the workload; the same sample's
     # oracle outputs give the GPU path's errors
