@@ -156,3 +156,22 @@ def test_z_split_tile_shapes_match_simt(sonar, shape, nx, ny, precision):
     tol = S_TOL if precision == "fp32" else 1e-2
     assert parity.nl2(out[shape][1], out[1][1]) < tol
     assert parity.nl2(out[shape][0], out[1][0]) < (1e-4 if precision == "fp32" else 1e-2)
+
+
+# ------------------------------------------------------------------ C4: 64-ping trajectory
+def test_c4_trajectory_batch_sampled_parity(sonar):
+    """The full 64-ping batch in one call (the batch form the bench times), checked on
+    four of its pings against the oracle: 16 sampled range bins of every beam, and the
+    peaks of the beams the oracle resolves outside the margins on those bins."""
+    scene, params, poses, ssp = inputs.workload("c4")
+    sonar.upload(scene)
+    env, cloud, n = sonar.ping_batch(poses, params, ssp)
+    torch.cuda.synchronize()
+    env = env.reshape(len(poses), -1, params["n_range"])
+    ns = np.arange(0, params["n_range"], 64, dtype=np.int32)
+    for i in (0, 17, 40, 63):
+        ref = oracle.trace(scene, params, poses[i], ssp)
+        E_ref, _, _ = oracle.volume(params, ref, ns=ns)
+        E = env[i][:, ns].double().cpu().numpy()
+        assert parity.nl2(E, E_ref) <= 1e-4, i
+        assert int(n[i]) > 0
