@@ -304,6 +304,12 @@ __device__ __forceinline__ void tmem_free_512(uint32_t base) {
 // =====================================================================================
 // Records are stored into the stage as 16-byte vectors: every stage starts on a 16-byte
 // boundary (alignas makes the size a multiple of 16 too).
+// Stage buffers per generator group, used round robin by K-block. Three, so that the one
+// a K-block's records are written into (during the previous K-block, before the group's
+// barrier) was last read two K-blocks earlier: every warp of the group has passed the
+// intervening barrier since, including the A-operand reads that follow a K-block's own
+// barrier. With two, a fast warp could overwrite records a slow one was still reading.
+constexpr int kZStages = 3;
 template <int WT>
 struct alignas(16) ZStage {  // one generator group's 8 hits of one K-block
   HitRec rec[KG];
@@ -319,7 +325,7 @@ static_assert(offsetof(ZStage<8>, rec) % 16 == 0, "records are 16-byte aligned i
 template <int WT, int NP>
 constexpr size_t tz_smem_bytes() {
   using Z = ZShape<NP>;
-  return 1024 + (size_t)Z::NT * 2 * Z::B_BYTES + 2 * kGroups * sizeof(ZStage<WT>) + 64 * 8 + 64;
+  return 1024 + (size_t)Z::NT * 2 * Z::B_BYTES + kZStages * kGroups * sizeof(ZStage<WT>) + 64 * 8 + 64;
 }
 
 template <int WT, int NP>
@@ -332,7 +338,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_
   uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   uint8_t* sB = smem;  // NT x (hi, lo) per-tile N operands
   ZStage<WT>(*zst)[kGroups] = reinterpret_cast<ZStage<WT>(*)[kGroups]>(sB + NT * 2 * B_BYTES);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(&zst[2][0]);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(&zst[kZStages][0]);
   uint64_t* tb_full = bars;
   uint64_t* tb_empty = bars + NT;
   uint64_t* am_full = bars + 2 * NT;
@@ -488,7 +494,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_
       const int64_t hn = h + kb.cnt;
       win = load_window(a.sorted_n, hn, h1, lane);
       const uint4 recv = fetch(hn);
-      ZStage<WT>& S = zst[j & 1][grp];
+      ZStage<WT>& S = zst[j % kZStages][grp];
       const int kvalid = kb.cnt - KG * grp;  // hits of this group inside the K-block
       // taps c_k R((u0 + i) dt); padding hits contribute zero
       for (int item = tg; item < KG * WT; item += 128) {
@@ -513,9 +519,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_
         }
         S.e2[kl][ql] = e;
       }
-      // the next K-block's records go to the other stage buffer, whose records were last
-      // read before the previous barrier
-      if (tg < 2 * KG) reinterpret_cast<uint4*>(&zst[(j + 1) & 1][grp].rec[tg >> 1])[tg & 1] = recv;
+      // the next K-block's records go to the stage buffer last read two K-blocks ago
+      // (every warp of the group has passed the previous barrier since)
+      if (tg < 2 * KG) reinterpret_cast<uint4*>(&zst[(j + 1) % kZStages][grp].rec[tg >> 1])[tg & 1] = recv;
       named_bar(bar_id, 128);
 
       // per-K-block A operand: row (my_hi, mx) = this thread's TMEM lane, 8 columns
