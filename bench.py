@@ -309,6 +309,7 @@ def run_ours(args, ws, rank, local):
         e0.record(stream)
         ping()
         e1.record(stream)
+        e1.synchronize()  # the call waits for its own stream, not for the caller's
         st = s.stats()
         eager_ms += e0.elapsed_time(e1)
         for k in stages:
