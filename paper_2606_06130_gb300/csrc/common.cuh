@@ -52,7 +52,7 @@ struct BvhNode {
 
 struct DevScene {
   const float4* tri32;     // [n_tris][3]: v0, e1, e2 (leaf order), FP32 filter
-  const float* triv;       // [n_tris][9]: original vertices a, b, c (leaf order), FP64 test
+  const float* triv;       // [n_tris][9]: original vertices a, b, c (leaf order), exact (pair) test
   const int32_t* tri_prim; // leaf -> original triangle id
   const float* tri_mu;     // leaf order
   const uint8_t* tri_flags;// leaf order

@@ -128,7 +128,7 @@ __device__ __forceinline__ F2 sqrt_df(F2 v) {
   const F2 r = v - F2{p, __fmaf_rn(s, s, -p)};
   return quick_two_sum(s, __fdiv_rn(r.hi, __fmul_rn(2.f, s)));
 }
-// FP64 views, for the rare exact triangle tests and the debug delays
+// FP64 views, for the FP64 legs' geometry and the debug delays
 __device__ __forceinline__ double to_d(F2 v) { return (double)v.hi + (double)v.lo; }
 __device__ __forceinline__ D3 to_d3(const DF3& v) { return d3(to_d(v.x), to_d(v.y), to_d(v.z)); }
 __device__ __forceinline__ F2 f2_of(double x) {
@@ -224,7 +224,7 @@ __device__ __forceinline__ bool tri_exact(const float* tv, const D3& o, const D3
   return t > tmin && t <= tmax;
 }
 // The same two-sided test in FP32 pairs (edges exact from the FP32 vertices; ~2^-46
-// relative after that). Its decision differs from the FP64 test's only where u, v or
+// relative after that). Its decision differs from an FP64 test's only where u, v or
 // 1 - u - v lies within ~1e-13 of zero, far inside the barycentric margin (1e-5) outside
 // which hits must agree; it keeps the straight-ray and volume paths off the FP64 pipe,
 // which issues at a small fraction of the FP32 rate on this part and was a third busy
@@ -1056,8 +1056,8 @@ __global__ void k_volume(TraceArgs A) {
   pcg4d(h[0], h[1], h[2], h[3]);
   // geometry and delay in FP32 pairs, as on the straight-ray path (FP64 issues at ~2
   // operations per clock per SM on this part): the position lo + (hi - lo) u (u, a
-  // 24-bit fraction, is exact in FP32), the leg, its length and direction; FP64 only in
-  // the rare exact triangle tests of the shadow query
+  // 24-bit fraction, is exact in FP32), the leg, its length and direction, and the
+  // shadow query's near-tie triangle tests
   const DevPose& P = A.poses[ping];
   const DF3 o = DF3{F2{P.t32[0], P.t_lo[0]}, F2{P.t32[1], P.t_lo[1]}, F2{P.t32[2], P.t_lo[2]}};
   F2 dvk[3];
