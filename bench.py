@@ -226,6 +226,10 @@ def read_profile(kernel):
 # the seabed in front of the sonar, s_v = 1e-4 /m
 VOLUME_BOX = ((-2.0, -12.0, -10.5), (14.0, 12.0, -4.0))
 VOLUME_SV = 1e-4
+# --field and the field form: a thermocline that deepens with range, 6 m/s either side
+XS_F, ZS_F = np.linspace(-4.0, 16.0, 21), np.linspace(-12.0, 1.0, 27)
+THERMOCLINE = {"x0": -4.0, "dx": 1.0, "z0": -12.0, "dz": 0.5,
+               "c": np.array([[1500.0 - 6.0 * math.tanh((z + 6.0 + 0.15 * x) / 1.5) for x in XS_F] for z in ZS_F])}
 
 
 def run_ours(args, ws, rank, local):
@@ -247,6 +251,9 @@ def run_ours(args, ws, rank, local):
         s.set_option(SONAR_OPT_CROSS, 1)
     if args.volume > 0:
         s.set_volume(args.volume, VOLUME_BOX[0], VOLUME_BOX[1], VOLUME_SV)
+    if args.field > 0:
+        s.set_field(dict(THERMOCLINE, h=args.field))
+        params = dict(params, c_ref=1500.0)
     s.upload(scene)
     torch.cuda.synchronize()
     # scene upload and BVH build, timed apart from the pings (median of 3 rebuilds)
@@ -410,6 +417,7 @@ def run_ours(args, ws, rank, local):
                       "l2": "flushed before every timed step (256 MB write, outside the events)",
                       "cross_terms": bool(args.cross),
                       "volume_scatterers": int(args.volume),
+                      "field_step_m": float(args.field) if args.field > 0 else None,
                       "parallelism": f"replicas x{ws}"},
            "roofline": roof,
            "stages_ms": mean_stage,
@@ -567,9 +575,7 @@ def other_forms(torch, s, inputs, dev):
                                "note": "10^6 water-column scatterers (s_v 1e-4 /m) on top of the mesh"}
     s.set_volume(0)
     # rays through a range-dependent thermocline (RK4 steps of 0.5 m, chords per step)
-    xs, zs = np.linspace(-4.0, 16.0, 21), np.linspace(-12.0, 1.0, 27)
-    thermo = np.array([[1500.0 - 6.0 * math.tanh((z + 6.0 + 0.15 * x) / 1.5) for x in xs] for z in zs])
-    s.set_field({"x0": -4.0, "dx": 1.0, "z0": -12.0, "dz": 0.5, "c": thermo, "h": 0.5})
+    s.set_field(dict(THERMOCLINE, h=0.5))
     pf = dict(params, c_ref=1500.0)
     for _ in range(2):
         s.ping(poses[0], pf, ssp, precision="fp32")
@@ -671,11 +677,14 @@ def main():
                     help="headline workload with out/back cross-term multipath (implies --no-oracle)")
     ap.add_argument("--volume", type=int, default=0,
                     help="headline workload plus this many water-column scatterers (implies --no-oracle)")
+    ap.add_argument("--field", type=float, default=0.0,
+                    help="headline workload through the range-dependent thermocline, rays integrated at this "
+                         "step in m (implies --no-oracle)")
     ap.add_argument("--oracle-timing", action="store_true",
                     help="with --impl reference: time the FP64 oracle in full instead (C1, C2 whole pings at 1 "
                          "and all threads; C4 8 pings)")
     args = ap.parse_args()
-    if args.cross or args.volume > 0:
+    if args.cross or args.volume > 0 or args.field > 0:
         args.no_oracle = True  # the oracle legs sample the default workload
     ws, rank, local = dist_setup()
     if args.impl == "reference":
