@@ -740,9 +740,11 @@ __device__ void route_curved(const TraceArgs& A, int ping, D3 o, D3 d0, D3 us, u
 // arrives on and pass no other triangle closer than L_d - kCrossClear. Its geometry and
 // shadow test run in FP64 from the pose; the delay adds L_d to the route's FP32-pair
 // length. One speckle phase serves both paths (reciprocity), keyed apart from the
-// route's own (third hash word 9 + bounce).
+// route's own (third hash word 9 + bounce). Kept out of line: it runs for a few percent
+// of hits, and inlined its FP64 leg and second traversal crowd the instruction cache of
+// the route loop (ray casting with cross terms 0.139-0.142 -> 0.137 ms on C2).
 constexpr double kCrossClear = 1e-4;
-__device__ void emit_cross(const TraceArgs& A, int ping, const DevPose& P, const DF3& xh, F2 L, const DF3& dir,
+__device__ __noinline__ void emit_cross(const TraceArgs& A, int ping, const DevPose& P, const DF3& xh, F2 L, const DF3& dir,
                            float gam, int leaf, int prim, float dOmega, float uy, float uz, uint32_t ray,
                            uint32_t sub_i, int bounce, uint32_t keybase) {
   const D3 X = to_d3(xh);
