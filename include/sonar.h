@@ -49,7 +49,10 @@ extern "C" {
 
 /* ---------------------------------------------------------------- precision forms */
 /* Beamforming contraction precision. Every form accumulates in FP32 on the tensor
-   cores; geometry, delays and carrier phase are FP64, echoes are synthesised in FP32.
+   cores. Route geometry, delays and carrier phase carry FP64-grade precision: FP64 on
+   the curved-ray and field routes, FP32 pairs (hi + lo, about 48 significant bits) on
+   the straight-ray route, delays within 1e-12 relative of FP64 either way; hit
+   amplitudes are FP32 and echoes are synthesised with FP32 accumulation.
    SONAR_FP32: each operand split into BF16 hi + lo, three products hi*hi + hi*lo +
                lo*hi (relative operand error ~2^-17).
    SONAR_BF16 / SONAR_FP16: one product of BF16 / FP16 operands. */
@@ -197,9 +200,11 @@ SONAR_API const char* sonar_last_error(const sonar_ctx* ctx);
 SONAR_API int sonar_set_option(sonar_ctx* ctx, int32_t option, int64_t value);
 
 /* ---------------------------------------------------------------- scene */
-/* Uploads a static scene (Sec. II.A ray casting target) and builds its BVH on the
-   device. verts [n_verts][3] f32 (metres); tris [n_tris][3] i32 vertex indices;
-   mu [n_tris] backscatter coefficient; flags [n_tris] bit0 = specular mirror
+/* Uploads a static scene (Sec. II.A ray casting target) and builds its BVH: by
+   default a binned-SAH hierarchy built on the host and refitted and packed on the
+   device; with SONAR_OPT_BVH 1 a Morton-order LBVH built entirely on the device.
+   verts [n_verts][3] f32 (metres); tris [n_tris][3] i32 vertex indices; mu [n_tris]
+   backscatter coefficient; flags [n_tris] bit0 = specular mirror
    (reflects with r_seabed); points [n_points][3] f32 point scatterers with amplitude
    coefficients sigma [n_points]; planes [n_planes][4] f64 unit normal and offset
    (n.x = d) of mirror planes used for point-scatterer image routes. Any count may be
@@ -312,8 +317,9 @@ SONAR_API int sonar_get_stats(const sonar_ctx* ctx, sonar_stats* out);
    used; poses: host [n_pings]; cloud: device [n_pings][cloud_cap]; n_cloud: host
    [n_pings] (may be NULL), the number of points found per ping; cuda_stream: the
    stream to enqueue on (NULL = legacy default stream). The call synchronises that
-   stream before returning. Produces the same points, in the same beam order, as the
-   cloud of the sonar_ping call that wrote env.
+   stream before returning. Gives the points of the sonar_ping call that wrote env, in
+   the same beam order, with the same beams, bins and intensities; positions are formed
+   in FP64 here and in FP32 by sonar_ping, so they agree to FP32 rounding.
    Scratch (per-beam peak keys, per-ping maxima and counts) lives in one file-scope
    device array of about 4 MiB that every GPU loading the library holds until the
    process exits; the call makes no cudaMalloc/cudaFree or allocating library call.
@@ -322,9 +328,11 @@ SONAR_API int sonar_get_stats(const sonar_ctx* ctx, sonar_stats* out);
    the array's device address (cudaGetSymbolAddress, with that device current); make
    that first call before any stream capture. All calls share the array: calls whose
    GPU work overlaps (other streams, other threads) race and must be serialised by the
-   caller. Returns SONAR_E_ARG on bad arguments, SONAR_E_CAPACITY also when a ping has
-   more than cloud_cap points (cloud then holds the first cloud_cap), SONAR_E_CUDA on a
-   CUDA error. */
+   caller. Returns SONAR_E_ARG on bad arguments, including an env or cloud that is not
+   device (or managed) memory, checked before any work; SONAR_E_CAPACITY also when a
+   ping has more than cloud_cap points and a cloud buffer was given (cloud then holds the
+   first cloud_cap; with cloud NULL and cloud_cap 0 the call only counts, as sonar_ping
+   does); SONAR_E_CUDA on a CUDA error. */
 SONAR_API int sonar_cloud_noalloc(const float* env, int32_t n_pings, const sonar_params* params,
                                   const sonar_pose* poses, sonar_point* cloud, int64_t cloud_cap,
                                   int64_t* n_cloud, void* cuda_stream);

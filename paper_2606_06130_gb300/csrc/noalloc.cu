@@ -114,6 +114,18 @@ __global__ void __launch_bounds__(1024) k_na_compact(NoAllocScratch* s, const __
 std::mutex g_na_mutex;
 NoAllocScratch* g_na_addr[kNoAllocMaxDevices] = {};
 
+// True when the kernels of this device may dereference p: device or managed memory.
+// Host memory (pageable, pinned or unregistered) is refused, so a wrong pointer is an
+// argument error instead of a faulting kernel. cudaPointerGetAttributes allocates nothing.
+bool device_accessible(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
 }  // namespace
 }  // namespace sonar
 
@@ -130,6 +142,7 @@ extern "C" SONAR_API int sonar_cloud_noalloc(const float* env, int32_t n_pings, 
   if (n_pings > kNoAllocMaxPings || nb * n_pings > kNoAllocMaxKeys) return SONAR_E_CAPACITY;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) return SONAR_E_CUDA;
+  if (!device_accessible(env) || (cloud_cap > 0 && !device_accessible(cloud))) return SONAR_E_ARG;
   NoAllocScratch* s = nullptr;
   {
     // first call on a device: resolve the device address of the scratch array
@@ -171,10 +184,11 @@ extern "C" SONAR_API int sonar_cloud_noalloc(const float* env, int32_t n_pings, 
                       cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
     return SONAR_E_CUDA;
+  // as sonar_ping: a count-only call (no cloud buffer) is not a capacity failure
   int rc = SONAR_OK;
   for (int i = 0; i < n_pings; ++i) {
     if (n_cloud) n_cloud[i] = counts[i];
-    if (counts[i] > cloud_cap) rc = SONAR_E_CAPACITY;
+    if (counts[i] > cloud_cap && (cloud_cap > 0 || cloud)) rc = SONAR_E_CAPACITY;
   }
   return rc;
 }

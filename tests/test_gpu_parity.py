@@ -161,17 +161,58 @@ def test_z_split_tile_shapes_match_simt(sonar, shape, nx, ny, precision):
 # ------------------------------------------------------------------ C4: 64-ping trajectory
 def test_c4_trajectory_batch_sampled_parity(sonar):
     """The full 64-ping batch in one call (the batch form the bench times), checked on
-    four of its pings against the oracle: 16 sampled range bins of every beam, and the
-    peaks of the beams the oracle resolves outside the margins on those bins."""
+    four of its pings against the oracle's full volumes (every beam and range bin): the
+    envelope to 1e-4, and the peak (beam, bin) of every beam whose oracle peak beats its
+    runner-up and the threshold by the FP32 margin."""
+    from paper_2606_06130_gb300.sonar import cloud_records
     scene, params, poses, ssp = inputs.workload("c4")
     sonar.upload(scene)
     env, cloud, n = sonar.ping_batch(poses, params, ssp)
     torch.cuda.synchronize()
     env = env.reshape(len(poses), -1, params["n_range"])
-    ns = np.arange(0, params["n_range"], 64, dtype=np.int32)
+    total = 0
     for i in (0, 17, 40, 63):
         ref = oracle.trace(scene, params, poses[i], ssp)
-        E_ref, _, _ = oracle.volume(params, ref, ns=ns)
-        E = env[i][:, ns].double().cpu().numpy()
+        E_ref, _, _ = oracle.volume(params, ref)
+        E = env[i].double().cpu().numpy()
         assert parity.nl2(E, E_ref) <= 1e-4, i
         assert int(n[i]) > 0
+        checked, _ = cloud_check(cloud[i], int(n[i]), params, poses[i], E_ref, 1e-3)
+        assert checked > 0.5 * len(cloud_records(cloud[i], int(n[i]))), i
+        total += checked
+    assert total > 1000
+
+
+def test_c2_fp32_full_volume_peaks(sonar):
+    """The headline ping at full size against the oracle's full volume (8192 beams x 1024
+    bins): envelope normalised L2 <= 1e-4 and every peak (beam, bin) outside the FP32
+    margin bit-exact."""
+    scene, params, poses, ssp = inputs.workload("c2")
+    E, cloud, n = run(sonar, scene, params, poses[0], ssp)
+    ref = oracle.trace(scene, params, poses[0], ssp)
+    E_ref, _, _ = oracle.volume(params, ref)
+    assert parity.nl2(E, E_ref) <= 1e-4
+    checked, excluded = cloud_check(cloud, n, params, poses[0], E_ref, 1e-3)
+    assert checked > 0.9 * params["n_beam_az"] * params["n_beam_el"] - excluded
+    assert checked > 4000
+
+
+@pytest.mark.parametrize("name", ["c1", "c2", "c4"])
+def test_device_lbvh_hit_parity(sonar, name):
+    """The Morton-order LBVH built on the device (SONAR_OPT_BVH 1) gives the oracle's hits:
+    prim ids bit-exact outside the near-tie margins, delays to 1e-12; and the envelope on
+    sampled range bins to 1e-4 (c4: its first pose)."""
+    from paper_2606_06130_gb300.sonar import SONAR_OPT_BVH
+    scene, params, poses, ssp = inputs.workload(name)
+    sonar.set_option(SONAR_OPT_BVH, 1)
+    try:
+        E, _, _ = run(sonar, scene, params, poses[0], ssp)
+        hits = sonar.hits()
+    finally:
+        sonar.set_option(SONAR_OPT_BVH, 0)
+    ref = oracle.trace(scene, params, poses[0], ssp)
+    excluded, matched = parity.check_hits(hits, ref, params["n_sub"])
+    assert matched >= ref["n"] - 2 * (excluded + 1)
+    ns = np.arange(7, params["n_range"], max(1, params["n_range"] // 24), dtype=np.int32)
+    E_ref, _, _ = oracle.volume(params, ref, ns=ns)
+    assert parity.nl2(E[:, ns], E_ref) <= 1e-4

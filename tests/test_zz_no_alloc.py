@@ -28,16 +28,21 @@ def sonar_mod():
     return sonar
 
 
-def _noalloc(sonar, env, params, poses, cap):
+def _call(sonar, env_ptr, params, poses, cloud_ptr, cap):
     P = len(poses)
-    cloud = torch.zeros((P, cap, 6), dtype=torch.int32, device="cuda:0")
     n = (C.c_int64 * P)()
     arr = (sonar.sonar_pose * P)(*[sonar.make_pose(p) for p in poses])
     sp = sonar.make_params(params)
-    rc = sonar.lib().sonar_cloud_noalloc(env.data_ptr(), P, C.byref(sp), arr, cloud.data_ptr(), cap, n,
+    rc = sonar.lib().sonar_cloud_noalloc(env_ptr, P, C.byref(sp), arr, cloud_ptr, cap, n,
                                          C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    return rc, list(n)
+
+
+def _noalloc(sonar, env, params, poses, cap):
+    cloud = torch.zeros((len(poses), cap, 6), dtype=torch.int32, device="cuda:0")
+    rc, n = _call(sonar, env.data_ptr(), params, poses, cloud.data_ptr(), cap)
     assert rc == sonar.SONAR_OK, rc
-    return cloud, list(n)
+    return cloud, n
 
 
 def _same_cloud(sonar, a, na, b, nb):
@@ -85,3 +90,54 @@ def test_noalloc_rejects_sizes_beyond_its_maximum(sonar_mod):
     n = (C.c_int64 * 65)()
     rc = sonar.lib().sonar_cloud_noalloc(env.data_ptr(), 65, C.byref(sp), arr, None, 0, n, None)
     assert rc == sonar.SONAR_E_CAPACITY
+
+
+def test_noalloc_warm_call_allocates_nothing_and_truncates(sonar_mod):
+    """A warm call leaves the device's free memory unchanged; a cloud buffer smaller
+    than a ping's points gives SONAR_E_CAPACITY, the full count, and the first cap
+    points of sonar_ping's cloud; a count-only call (no cloud) succeeds."""
+    sonar = sonar_mod
+    scene, params, poses, ssp = inputs.workload("c1")
+    s = sonar.Sonar(0)
+    s.upload(scene)
+    nb = params["n_beam_az"] * params["n_beam_el"]
+    env, cloud, n = s.ping(poses[0], params, ssp)
+    torch.cuda.synchronize()
+    assert n > 8
+    out = torch.zeros((1, nb, 6), dtype=torch.int32, device="cuda:0")
+    rc, _ = _call(sonar, env.data_ptr(), params, poses[:1], out.data_ptr(), nb)  # warm
+    assert rc == sonar.SONAR_OK
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info(0)[0]
+    rc, n1 = _call(sonar, env.data_ptr(), params, poses[:1], out.data_ptr(), nb)
+    torch.cuda.synchronize()
+    assert rc == sonar.SONAR_OK and n1[0] == n
+    assert torch.cuda.mem_get_info(0)[0] == free0
+
+    cap = n // 2
+    small = torch.zeros((1, cap, 6), dtype=torch.int32, device="cuda:0")
+    rc, n2 = _call(sonar, env.data_ptr(), params, poses[:1], small.data_ptr(), cap)
+    assert rc == sonar.SONAR_E_CAPACITY and n2[0] == n
+    _same_cloud(sonar, cloud[:cap], cap, small[0], cap)
+
+    rc, n3 = _call(sonar, env.data_ptr(), params, poses[:1], None, 0)
+    assert rc == sonar.SONAR_OK and n3[0] == n
+    s.close()
+
+
+def test_noalloc_rejects_host_buffers(sonar_mod):
+    """Host buffers are refused with SONAR_E_ARG before any kernel runs."""
+    sonar = sonar_mod
+    params = inputs.sensor_params("c1")
+    nb = params["n_beam_az"] * params["n_beam_el"]
+    poses = [inputs.pose((0.0, 0.0, -2.0))]
+    env_host = np.zeros((nb, params["n_range"]), np.float32)
+    env_dev = torch.zeros((nb, params["n_range"]), dtype=torch.float32, device="cuda:0")
+    cloud_host = np.zeros((nb, 6), np.int32)
+    cloud_dev = torch.zeros((nb, 6), dtype=torch.int32, device="cuda:0")
+    rc, _ = _call(sonar, env_host.ctypes.data, params, poses, cloud_dev.data_ptr(), nb)
+    assert rc == sonar.SONAR_E_ARG
+    rc, _ = _call(sonar, env_dev.data_ptr(), params, poses, cloud_host.ctypes.data, nb)
+    assert rc == sonar.SONAR_E_ARG
+    rc, _ = _call(sonar, env_dev.data_ptr(), params, poses, cloud_dev.data_ptr(), nb)
+    assert rc == sonar.SONAR_OK
