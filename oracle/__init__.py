@@ -44,7 +44,7 @@ class OrcScene(C.Structure):
 
 
 _HIT_I32 = ("ray", "sub", "seg", "prim")
-_HIT_F64 = ("tau", "len", "amp", "psi", "phi", "ux", "uy", "uz", "cr", "ci", "margin", "gap")
+_HIT_F64 = ("tau", "len", "amp", "psi", "phi", "ux", "uy", "uz", "cr", "ci", "margin", "gap", "kinc", "gam")
 
 
 class OrcHits(C.Structure):
@@ -175,7 +175,9 @@ def trace(scene, params: dict, pose: dict, ssp: dict, use_bvh: bool = True) -> d
 
 def _hits_struct(h: dict):
     keep = {k: np.ascontiguousarray(h[k], np.int32) for k in _HIT_I32}
-    keep.update({k: np.ascontiguousarray(h[k], np.float64) for k in _HIT_F64})
+    # kinc and gam are trace outputs only (nothing downstream reads them): hand-made
+    # hit lists may leave them out
+    keep.update({k: np.ascontiguousarray(h[k] if k in h else np.zeros(h["n"]), np.float64) for k in _HIT_F64})
     s = OrcHits(h["n"], h["n"], *[_ptr(keep[k]) for k in _HIT_I32],
                 *[_ptr(keep[k]) for k in _HIT_F64], h["c_ref"])
     return s, keep

@@ -468,6 +468,7 @@ int orc_eigen_arc(const double* ssp_z, const double* ssp_cc, int32_t n_ssp, cons
 typedef struct {
   int32_t ray, sub, seg, prim;
   double tau, len, amp, psi, phi, u[3], margin, gap;
+  double kinc, gam;  /* incidence cosine at a mesh facet, one-way reflection product */
 } ohit;
 typedef struct { ohit* v; int64_t n, cap; } hbuf;
 static void hb_push(hbuf* b, const ohit* h) {
@@ -495,12 +496,14 @@ typedef struct {
 static void emit_mesh_hit(const tctx* c, hbuf* hb, int32_t ray, int32_t sub, int32_t seg,
                           int32_t prim, double T_oneway, double L, double gam, double kinc,
                           double dOmega, const double us[3], double margin, double gap) {
-  ohit h;
+  ohit h = {0};
   h.ray = ray; h.sub = sub; h.seg = seg; h.prim = prim;
   h.tau = 2.0 * T_oneway;
   h.len = L;
   double mu = c->sc->mu[prim];
   h.amp = gam * gam * sqrt(mu * kinc * dOmega) / L * exp(-2.0 * c->p->alpha * L);
+  h.kinc = kinc;
+  h.gam = gam;
   uint32_t v[4] = {(uint32_t)ray, (uint32_t)sub, (uint32_t)(1 + seg), c->s32};
   orc_pcg4d(v);
   h.psi = TWO_PI * u24(v[0]);
@@ -545,7 +548,7 @@ static void cross_mesh(const tctx* c, hbuf* hb, int32_t ray, int32_t sub, int32_
   double ud[3] = {v[0] / Ld, v[1] / Ld, v[2] / Ld};
   hitq sh = closest(c->sc, c->bv, c->t, ud, EPS_HIT, Ld - CROSS_CLEAR, prim);
   if (sh.prim >= 0) return;
-  ohit h;
+  ohit h = {0};
   h.ray = ray; h.sub = sub; h.prim = prim;
   h.tau = tau;
   h.len = 0.5 * (L + Ld);
@@ -886,7 +889,7 @@ static void point_routes(const tctx* c, hbuf* hb) {
         left -= h;
       }
       if (!clear) continue;
-      ohit h;
+      ohit h = {0};
       h.ray = (int32_t)ip; h.sub = 0; h.seg = 0; h.prim = -1;
       h.tau = 2.0 * T;
       h.len = sarc;
@@ -942,7 +945,7 @@ static void point_routes(const tctx* c, hbuf* hb) {
           a[0] = sp[0]; a[1] = sp[1]; a[2] = sp[2];
         }
         if (!ok || !leg_clear(c, a, x)) continue;
-        ohit h;
+        ohit h = {0};
         h.ray = (int32_t)ip; h.sub = route; h.seg = len; h.prim = -1;
         h.tau = 2.0 * L / c->ssp.c0;
         h.len = L;
@@ -964,7 +967,7 @@ static void point_routes(const tctx* c, hbuf* hb) {
     for (int i = 0; i < npr; ++i)
       for (int j = 0; j < npr; ++j) {
         if (i == j) continue;
-        ohit h;
+        ohit h = {0};
         h.ray = (int32_t)ip; h.sub = 0x10000 | (pr[i].idx << 8) | pr[j].idx;
         h.seg = pr[i].len + pr[j].len; h.prim = -1;
         double Ls = pr[i].L + pr[j].L;
@@ -1005,7 +1008,7 @@ static void volume_scatter(const tctx* c, int64_t i0, int64_t i1, hbuf* hb) {
     double L = norm3(dv);
     if (!(L > 0) || !(L <= L_stop)) continue;
     if (!leg_clear(c, c->t, x)) continue;
-    ohit h;
+    ohit h = {0};
     h.ray = (int32_t)i; h.sub = 0x20000; h.seg = 0; h.prim = -1;
     h.tau = 2.0 * L / c->ssp.c0;
     h.len = L;
@@ -1121,6 +1124,7 @@ int orc_trace(const orc_scene* sc, const orc_params* p, const double pose_t[3], 
         out->ux[w] = h->u[0]; out->uy[w] = h->u[1]; out->uz[w] = h->u[2];
         out->cr[w] = h->amp * cos(h->phi); out->ci[w] = h->amp * sin(h->phi);
         out->margin[w] = h->margin; out->gap[w] = h->gap;
+        out->kinc[w] = h->kinc; out->gam[w] = h->gam;
       }
     }
   }

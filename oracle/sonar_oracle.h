@@ -65,6 +65,8 @@ typedef struct {
   double *ux, *uy, *uz;              /* sensor-frame arrival direction */
   double *cr, *ci;                   /* complex coefficient c_k */
   double *margin, *gap;              /* barycentric margin and distance gap to the runner-up */
+  double *kinc, *gam;                /* mesh hits: incidence cosine |d . n| at the facet and the
+                                        route's one-way reflection product; 0 for other hits */
   double c_ref;                      /* resolved reference sound speed (output) */
 } orc_hits;
 
