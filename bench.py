@@ -587,6 +587,7 @@ def other_forms(torch, s, inputs, dev):
     out["c2_field_h0.5_fp32"] = {"value": 5 / (time.perf_counter() - t0), "unit": UNIT,
                                  "note": "range-dependent thermocline, RK4 rays at 0.5 m steps"}
     s.set_field(None)
+    out.update(surrogate_forms(torch, s, inputs, dev, scene, params, poses, ssp))
     sc4, p4, poses4, ssp4 = inputs.workload("c4")
     s.upload(sc4)
     for prec in ("fp32", "bf16"):
@@ -603,6 +604,46 @@ def other_forms(torch, s, inputs, dev):
                                      "hits_total": st["n_hits"]}
         del env
     s.upload(scene)
+    return out
+
+
+def surrogate_forms(torch, s, inputs, dev, scene, params, poses, ssp):
+    """Throughput of the learned surrogate on the headline ping (its rendering plus the
+    six-layer network over all 8192 beams x 1024 bins), of the geometric envelope it
+    starts from, and of its training step (1024 beams, forward, backward, Adam). The
+    network's weights do not change the work: the seeded initialisation is used."""
+    out = {}
+    nb = params["n_beam_az"] * params["n_beam_el"]
+    s.sur_set_weights(inputs.surrogate_init(1), 0.05)
+    env = torch.empty((1, params["n_beam_el"], params["n_beam_az"], params["n_range"]), dtype=torch.float32, device=dev)
+    for name, call in (("c2_surrogate_bf16", lambda: s.sur_ping(poses, params, ssp, env=env)),
+                       ("c2_geometric", lambda: s.sur_geometric(poses, params, ssp, env=env))):
+        for _ in range(3):
+            call()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        reps = 10
+        for _ in range(reps):
+            call()
+        torch.cuda.synchronize()
+        out[name] = {"value": reps / (time.perf_counter() - t0), "unit": UNIT}
+    out["c2_surrogate_bf16"]["note"] = ("beam-centre rendering + 6-layer conv net (4 hidden layers on tcgen05), "
+                                        "8192 beams x 1024 bins, BF16 weights and activations, FP32 accumulation")
+    target, _, _ = s.ping_batch(poses, params, ssp, cloud_cap=0)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(3)
+    beams = torch.randint(0, nb, (1024,), generator=gen, device=dev, dtype=torch.int32)
+    for _ in range(3):
+        s.sur_train_step(poses, params, ssp, target, beams, lr=1e-4)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    reps = 20
+    for _ in range(reps):
+        s.sur_train_step(poses, params, ssp, target, beams, lr=1e-4)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / reps
+    out["c2_surrogate_train_step"] = {"value": 1.0 / dt, "unit": "steps/s", "beams_per_step": 1024,
+                                      "positions_per_s": 1024 * params["n_range"] / dt}
     return out
 
 
@@ -647,6 +688,36 @@ def oracle_timing():
     print(json.dumps({"oracle_timing": rows, "cpu": cpu_model(), "nproc": os.cpu_count()}), flush=True)
 
 
+def run_surrogate_training(args):
+    """--surrogate-train N: the learned surrogate trained from its seeded initialisation on
+    N pings that the plain method renders over randomised harbour scenes (one training
+    step of 1024 beams per ping), then judged on 64 held-out pings (4 unseen scenes x 16
+    poses, 8192 beams x 1024 bins each) against the plain method, beside the geometric
+    envelope without the network. Prints one JSON line."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2606_06130_gb300 import inputs, surrogate
+    from paper_2606_06130_gb300.sonar import Sonar
+    torch.cuda.set_device(0)
+    s = Sonar(0)
+    params, ssp = inputs.sensor_params("c2"), inputs.ssp("c2")
+    t0 = time.perf_counter()
+    tr = surrogate.train(s, params, ssp, n_pings=args.surrogate_train, seed=1000, batch=8, pings_per_scene=64)
+    t_train = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    ev = surrogate.evaluate(s, params, ssp, scene_seeds=[900001, 900003, 900005, 900007], pings_per_scene=16)
+    L = tr["losses"]
+    out = {"surrogate_training": {
+        "pings": tr["pings"], "steps": tr["steps"], "beams_per_step": tr["beams_per_step"], "e_scale": tr["e_scale"],
+        "loss_first_8": float(L[:8].mean()), "loss_last_1000": float(L[-1000:].mean()),
+        "loss_curve": [float(L[i:i + max(1, len(L) // 20)].mean()) for i in range(0, len(L), max(1, len(L) // 20))],
+        "wall_s": t_train, "plain_render_s": tr["plain_s"], "train_steps_s": tr["train_s"]},
+        "held_out": {"pings": 64, "scenes": 4, "metrics_vs_plain": ev, "eval_s": time.perf_counter() - t0,
+                     "rel_thr": 0.1}}
+    print(json.dumps(out), flush=True)
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return
@@ -683,7 +754,13 @@ def main():
     ap.add_argument("--oracle-timing", action="store_true",
                     help="with --impl reference: time the FP64 oracle in full instead (C1, C2 whole pings at 1 "
                          "and all threads; C4 8 pings)")
+    ap.add_argument("--surrogate-train", type=int, default=0,
+                    help="train the learned surrogate on this many plain-method pings and evaluate it on 64 "
+                         "held-out pings (one JSON line; not part of the default run)")
     args = ap.parse_args()
+    if args.surrogate_train > 0:
+        run_surrogate_training(args)
+        return
     if args.cross or args.volume > 0 or args.field > 0:
         args.no_oracle = True  # the oracle legs sample the default workload
     ws, rank, local = dist_setup()

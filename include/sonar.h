@@ -306,6 +306,83 @@ SONAR_API int sonar_get_echoes(sonar_ctx* ctx, float* host_out, int64_t cap_floa
 SONAR_API int sonar_get_raw(sonar_ctx* ctx, int32_t phase, float* host_out, int64_t cap_floats);
 SONAR_API int sonar_get_stats(const sonar_ctx* ctx, sonar_stats* out);
 
+/* ---------------------------------------------------------------- learned surrogate */
+/* The paper proposes learned scattering functions in place of costly echo physics
+   (Sec. II.B). The surrogate is a per-beam 1-D convolutional network that maps a cheap
+   geometric rendering of each beam to the coherent envelope profile the plain method
+   forms; the plain method generates its training data, judges its error
+   (sonar_sur_compare) and remains the fallback (the surrogate covers isovelocity
+   scenes only and returns SONAR_E_UNSUPPORTED otherwise).
+   Rendering: one ray per beam along the beam centre, routed by the plain method's
+   straight-ray rules (mirror facets and the sea surface reflect, at most max_bounces);
+   per beam the first two scatter (triangle) hits as (L, kappa, mu, Gamma): one-way
+   route length [m], incidence cosine, facet reflectivity, one-way reflection product;
+   zeros where absent.
+   Network: a hit at one-way length L is splatted linearly onto range bins at bin
+   coordinate (L - r_min) / dr - 1/2; four input channels (first-hit splat, second-hit
+   splat, incidence cosines, reflectivities); six convolutions along range, kernel 9,
+   zero padding at the beam's ends, channels 4 -> 64 -> 64 -> 64 -> 64 -> 64 -> 1, ReLU
+   after the first five; output E / e_scale. BF16 weights (rounded from FP32 master
+   parameters), FP32 accumulation, BF16 activations between layers, FP32 biases.
+   Parameters: one FP32 vector of SONAR_SUR_N_PARAMS, layer by layer W_l [cout][cin][9]
+   then b_l [cout].
+   Training: mean squared error between the output and E_target / e_scale over every
+   (beam, bin) of the selected beams, Adam (beta1 0.9, beta2 0.999, eps 1e-8, bias
+   correction). Needs n_range a multiple of 256. */
+#define SONAR_SUR_N_PARAMS 150657
+
+/* Sets the network parameters (host [n], n = SONAR_SUR_N_PARAMS, finite) and the output
+   scale e_scale > 0; resets the Adam moments and step count. */
+SONAR_API int sonar_sur_set_weights(sonar_ctx* ctx, const float* params, int64_t n, double e_scale);
+/* Copies the current parameters to host [n]. SONAR_E_ARG before any set_weights. */
+SONAR_API int sonar_sur_get_weights(sonar_ctx* ctx, float* params, int64_t n);
+/* Geometric rendering of n_pings poses: feat [n_pings][n_beam_el * n_beam_az][8]
+   (L1, kappa1, mu1, Gamma1, L2, kappa2, mu2, Gamma2), device or host memory. Needs a
+   scene; SONAR_E_UNSUPPORTED for a sound-speed gradient or field. */
+SONAR_API int sonar_sur_render(sonar_ctx* ctx, const sonar_pose* poses, int32_t n_pings, const sonar_params* params,
+                               const sonar_ssp* ssp, float* feat);
+/* The surrogate's envelope of n_pings poses: env [n_pings][n_beam_el][n_beam_az][n_range]
+   f32, e_scale times the network output (device memory, or host memory staged through
+   the device). Returns when env is complete. */
+SONAR_API int sonar_sur_ping(sonar_ctx* ctx, const sonar_pose* poses, int32_t n_pings, const sonar_params* params,
+                             const sonar_ssp* ssp, float* env);
+/* The rendering turned into an envelope without the network (the geometric form the
+   surrogate starts from, a cheap LiDAR-like sonar): env [n_pings][n_beam_el][n_beam_az]
+   [n_range] f32, E[n] = TVG(r_n) sum_h a_h |R(t_n - 2 L_h / c_ref)| over the beam's two
+   rendered hits, a_h = Gamma_h^2 sqrt(mu_h kappa_h dOmega_b) / L_h exp(-2 alpha L_h)
+   (the plain method's Lambertian amplitude of a ray tube of the beam cell's solid angle
+   dOmega_b), R the pulse autocorrelation. Device or host memory. Needs no weights. */
+SONAR_API int sonar_sur_geometric(sonar_ctx* ctx, const sonar_pose* poses, int32_t n_pings,
+                                  const sonar_params* params, const sonar_ssp* ssp, float* env);
+/* One training step on n_pings poses whose plain envelopes are env_target (device
+   [n_pings][n_beam_el][n_beam_az][n_range], e.g. from sonar_ping_batch): renders the
+   poses, runs the network over the n_sel selected beams (beams: device int32 indices
+   into the n_pings * nb rendered beams; NULL selects all of them and ignores n_sel),
+   back-propagates the mean squared error and, when update != 0, takes one Adam step of
+   learning rate lr. loss (host, may be NULL): the batch's mean squared error before the
+   step; grad (host [SONAR_SUR_N_PARAMS], may be NULL): its gradient. SONAR_E_ARG for an
+   index outside [0, n_pings * nb) (detected on the device; the step then runs with that
+   beam's input and target taken as zero) or host target/index buffers. */
+SONAR_API int sonar_sur_train_step(sonar_ctx* ctx, const sonar_pose* poses, int32_t n_pings,
+                                   const sonar_params* params, const sonar_ssp* ssp, const float* env_target,
+                                   const int32_t* beams, int64_t n_sel, double lr, int32_t update, double* loss,
+                                   float* grad);
+/* Error of an envelope volume against the plain method's (Sec. II.B: the plain method is
+   the judge of the surrogate). */
+typedef struct {
+  double nl2;            /* ||E - E_ref|| / ||E_ref|| over all pings */
+  int64_t lit_beams;     /* beams whose reference peak reaches rel_thr of its ping maximum */
+  double peak_bin_mean;  /* mean |peak bin - reference peak bin| over lit beams (bins >= r_blank) */
+  double peak_within_1;  /* fraction of lit beams whose peak bin is within 1 bin */
+  double peak_within_4;  /* ... within 4 bins */
+  int64_t cells;         /* (beam, bin) cells whose reference reaches rel_thr of its ping maximum */
+  double si, si_ref;     /* scintillation index var(I) / mean(I)^2 of I = E^2 over those cells */
+} sonar_sur_metrics;
+/* env, env_ref: device [n_pings][n_beam_el * n_beam_az][n_range]; the beam and range grid
+   and r_blank come from params. */
+SONAR_API int sonar_sur_compare(sonar_ctx* ctx, const float* env, const float* env_ref, int32_t n_pings,
+                                const sonar_params* params, double rel_thr, sonar_sur_metrics* out);
+
 /* ---------------------------------------------------------------- allocation-free cloud */
 /* Point cloud of n_pings envelope volumes that are already on the device, computed
    without allocating anything. The paper has no counterpart: this exists for callers

@@ -51,10 +51,12 @@ CHANNELS = (4, 64, 64, 64, 64, 64, 1)
 
 
 # ------------------------------------------------------------------ rendering
-def render(scene, params: dict, pose: dict, ssp: dict, use_bvh: bool = True) -> np.ndarray:
+def render(scene, params: dict, pose: dict, ssp: dict, use_bvh: bool = True, with_ties: bool = False):
     """Per-beam geometric rendering [n_beam_el * n_beam_az, 8] float64: (L, kappa, mu,
     Gamma) of the first and of the second scatter hit of the beam-centre route; zeros
-    where a hit is absent. Isovelocity profiles only."""
+    where a hit is absent. Isovelocity profiles only. with_ties: also return a [beams]
+    bool array, True where every recorded hit of the beam clears the near-tie margins
+    (barycentric margin > 1e-5 and distance gap to the runner-up > 1e-6 m)."""
     nb = params["n_beam_az"] * params["n_beam_el"]
     q = dict(params, n_ray_az=params["n_beam_az"], n_ray_el=params["n_beam_el"], n_sub=1, cross=0,
              vol_n=0)
@@ -66,6 +68,8 @@ def render(scene, params: dict, pose: dict, ssp: dict, use_bvh: bool = True) -> 
     ray, seg, L = h["ray"][mesh], h["seg"][mesh], h["len"][mesh]
     mu = np.asarray(scene.mu, np.float64)[h["prim"][mesh]]
     kinc, gam = h["kinc"][mesh], h["gam"][mesh]
+    tie_free = (h["margin"][mesh] > 1e-5) & (h["gap"][mesh] > 1e-6)
+    clear = np.ones(nb, bool)
     # a route's scatter hits in route order: by one-way length
     order = np.lexsort((L, ray))
     seen = {}
@@ -75,7 +79,8 @@ def render(scene, params: dict, pose: dict, ssp: dict, use_bvh: bool = True) -> 
         if k < 2:
             out[b, 4 * k:4 * k + 4] = (L[i], kinc[i], mu[i], gam[i])
             seen[b] = k + 1
-    return out
+            clear[b] &= bool(tie_free[i])
+    return (out, clear) if with_ties else out
 
 
 def rasterize(feat: np.ndarray, params: dict) -> np.ndarray:
@@ -222,19 +227,22 @@ def adam(theta, g, m, v, t: int, lr: float, b1=0.9, b2=0.999, eps=1e-8):
 # ------------------------------------------------------------------ evaluation
 def beam_metrics(E: np.ndarray, E_ref: np.ndarray, n_blank: int, rel_thr: float):
     """Per-ping evaluation of an envelope volume E [beams, n_range] against the plain
-    method's E_ref: normalised L2 error; per-beam peak-bin error |argmax E - argmax E_ref|
-    (bins at or beyond n_blank, first index on ties) over the beams whose E_ref peak
-    reaches rel_thr of the ping maximum; and the speckle statistic of both, the
-    scintillation index var(I) / mean(I)^2 of the intensity I = E^2 over the (beam, bin)
-    cells where E_ref reaches rel_thr of its maximum. Returns a dict."""
+    method's E_ref. The ping maximum vmax is E_ref's largest value at or beyond bin
+    n_blank. Returns a dict: normalised L2 error; the per-beam peak-bin error
+    |argmax E - argmax E_ref| (bins at or beyond n_blank, first index on ties, negative
+    values of E counted as zero) over the lit beams, whose E_ref peak is positive and
+    reaches rel_thr vmax; and the speckle statistic of both volumes, the scintillation
+    index var(I) / mean(I)^2 of the intensity I = E^2 over the (beam, bin) cells where
+    E_ref is positive and reaches rel_thr vmax."""
     E = np.asarray(E, np.float64)
     E_ref = np.asarray(E_ref, np.float64)
     nl2 = float(np.linalg.norm(E - E_ref) / np.linalg.norm(E_ref))
-    sub, sub_ref = E[:, n_blank:], E_ref[:, n_blank:]
+    sub, sub_ref = np.maximum(E[:, n_blank:], 0.0), E_ref[:, n_blank:]
     vmax = sub_ref.max()
-    lit = sub_ref.max(axis=1) >= rel_thr * vmax
+    bmax = sub_ref.max(axis=1)
+    lit = (bmax >= rel_thr * vmax) & (bmax > 0)
     dpk = np.abs(np.argmax(sub, axis=1) - np.argmax(sub_ref, axis=1))[lit]
-    cells = E_ref >= rel_thr * E_ref.max()
+    cells = (E_ref >= rel_thr * vmax) & (E_ref > 0)
 
     def si(A):
         I = A[cells] ** 2

@@ -15,7 +15,7 @@ SRC = os.path.join(HERE, "csrc")
 INC = os.path.join(ROOT, "include")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libsonar.so")
-UNITS = ["api.cu", "bvh.cu", "trace.cu", "synth.cu", "synth_tc.cu", "beamform.cu", "noalloc.cu"]
+UNITS = ["api.cu", "bvh.cu", "trace.cu", "synth.cu", "synth_tc.cu", "beamform.cu", "surrogate.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr", "-I", INC, "-I", SRC]

@@ -210,6 +210,32 @@ struct sonar_ctx {
   int next_slot = 0;
   cudaStream_t copy_stream = nullptr;
 
+  // learned surrogate
+  struct Sur {
+    float* params = nullptr;       // theta | m | v | grad, kSurParams each
+    __nv_bfloat16* wbf = nullptr;  // forward | backward-data B operands
+    float* wsmall = nullptr;       // first-layer | last-layer weights
+    SurNet net{};
+    bool has_weights = false;
+    double e_scale = 1.0;
+    int64_t step = 0;              // Adam steps taken
+    float* feat = nullptr;         // rendering [P][nb][8]
+    int64_t feat_cap = 0;
+    DevPose* poses = nullptr;
+    int64_t poses_cap = 0;
+    __nv_bfloat16* buf = nullptr;  // kSurBufs activation / gradient buffers of beams_cap beams
+    int64_t beams_cap = 0;
+    int rb = 0;
+    float* g = nullptr;            // loss gradient [n_sel][nr]
+    int64_t g_cap = 0;
+    double* loss = nullptr;
+    double* cmp_tot = nullptr;
+    unsigned* cmp_pmax = nullptr;
+    int32_t* cmp_pk = nullptr;
+    float* cmp_bmax = nullptr;
+    int64_t cmp_cap = 0, cmp_pk_cap = 0, cmp_bmax_cap = 0;
+  } sur;
+
   // last call
   int last_p = 0;
   Derived last_d{};
@@ -691,31 +717,8 @@ struct Outputs {
   unsigned long long* counters_map;     // counts and of the hit count / error words
 };
 
-// Enqueue the whole pipeline for P pings on the context stream (graph-capturable:
-// no host synchronisation, fixed grids that read device-side counts).
-int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, const Outputs& o, int* kernels) {
-  cudaStream_t st = ctx->stream;
-  // stage boundaries: 0 trace 1 bin 2 synth 3 convert 4 beamform 5 peaks 6
-  auto mark = [&](int i) {
-    if (ctx->timing) cudaEventRecord(ctx->stage_ev[i], st);
-  };
-  const bool fp16 = p->precision == SONAR_FP16;
-  // clear, trace, scan, scatter, synthesis, convert, GEMM, peaks; points (and their cross
-  // pairs); FP16 absmax and gain; raw phases
-  const bool pairs = ctx->cross && ctx->sc.n_points > 0;
-  *kernels = 8 + (ctx->sc.n_points > 0 ? 1 : 0) + (pairs ? 1 : 0) + (ctx->vol_n > 0 ? 1 : 0) + (fp16 ? 2 : 0) +
-             (ctx->raw_u > 0 ? ctx->raw_u : 0);
-  // the poses the host has just written into the pinned staging record
-  mark(0);
-  // every buffer that starts at zero is cleared up front, in one launch, so the kernels
-  // run back to back
-  const int32_t n_bins = P * d.nr_pad;
-  k_clear<<<4 * ctx->sm_count, 256, 0, st>>>(ctx->S, ctx->s_elems, ctx->raw_u > 0 ? ctx->S_raw : nullptr,
-                                             ctx->s_elems * ctx->raw_u, ctx->counts, n_bins, ctx->keys,
-                                             (int64_t)P * d.nb, ctx->pmax, P, ctx->n_hits, ctx->err_dev,
-                                             reinterpret_cast<const uint4*>(o.pose_src),
-                                             reinterpret_cast<uint4*>(ctx->poses), (int)(sizeof(DevPose) / 16) * P);
-  CU(cudaGetLastError());
+// Arguments of the ray-casting kernels for P pings with parameters p (derived values d).
+TraceArgs trace_args(const sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, bool pairs) {
   TraceArgs ta;
   memset(&ta, 0, sizeof(ta));
   ta.sc = ctx->sc;
@@ -788,6 +791,35 @@ int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, cons
   ta.n_hits = ctx->n_hits;
   ta.hit_cap = ctx->hit_cap;
   ta.err = ctx->err_dev;
+  return ta;
+}
+
+// Enqueue the whole pipeline for P pings on the context stream (graph-capturable:
+// no host synchronisation, fixed grids that read device-side counts).
+int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, const Outputs& o, int* kernels) {
+  cudaStream_t st = ctx->stream;
+  // stage boundaries: 0 trace 1 bin 2 synth 3 convert 4 beamform 5 peaks 6
+  auto mark = [&](int i) {
+    if (ctx->timing) cudaEventRecord(ctx->stage_ev[i], st);
+  };
+  const bool fp16 = p->precision == SONAR_FP16;
+  // clear, trace, scan, scatter, synthesis, convert, GEMM, peaks; points (and their cross
+  // pairs); FP16 absmax and gain; raw phases
+  const bool pairs = ctx->cross && ctx->sc.n_points > 0;
+  *kernels = 8 + (ctx->sc.n_points > 0 ? 1 : 0) + (pairs ? 1 : 0) + (ctx->vol_n > 0 ? 1 : 0) + (fp16 ? 2 : 0) +
+             (ctx->raw_u > 0 ? ctx->raw_u : 0);
+  // the poses the host has just written into the pinned staging record
+  mark(0);
+  // every buffer that starts at zero is cleared up front, in one launch, so the kernels
+  // run back to back
+  const int32_t n_bins = P * d.nr_pad;
+  k_clear<<<4 * ctx->sm_count, 256, 0, st>>>(ctx->S, ctx->s_elems, ctx->raw_u > 0 ? ctx->S_raw : nullptr,
+                                             ctx->s_elems * ctx->raw_u, ctx->counts, n_bins, ctx->keys,
+                                             (int64_t)P * d.nb, ctx->pmax, P, ctx->n_hits, ctx->err_dev,
+                                             reinterpret_cast<const uint4*>(o.pose_src),
+                                             reinterpret_cast<uint4*>(ctx->poses), (int)(sizeof(DevPose) / 16) * P);
+  CU(cudaGetLastError());
+  TraceArgs ta = trace_args(ctx, P, p, d, pairs);
   CU(launch_trace(ta, ctx->sm_count, st));
   CU(launch_points(ta, st));
   if (pairs) CU(launch_point_pairs(ta, st));
@@ -1246,6 +1278,176 @@ int run_async(sonar_ctx* ctx, const sonar_pose* poses, int P, const sonar_params
   return rc_prev;
 }
 
+
+// ------------------------------------------------------------------ learned surrogate
+constexpr int kSurBufs = 7;          // a1..a5 and two back-propagated gradients
+constexpr int64_t kSurChunk = 8192;  // beams per inference pass
+
+int sur_alloc_params(sonar_ctx* ctx) {
+  auto& S = ctx->sur;
+  if (S.params) return SONAR_OK;
+  CU(cudaMalloc(&S.params, sizeof(float) * 4 * kSurParams));
+  CU(cudaMemset(S.params, 0, sizeof(float) * 4 * kSurParams));
+  const int64_t wn = 4LL * kSurK * kSurC * kSurC;
+  CU(cudaMalloc(&S.wbf, sizeof(__nv_bfloat16) * 2 * wn));
+  CU(cudaMalloc(&S.wsmall, sizeof(float) * (kSurC * 4 * kSurK + kSurC * kSurK)));
+  CU(cudaMalloc(&S.loss, sizeof(double)));
+  S.net.theta = S.params;
+  S.net.m = S.params + kSurParams;
+  S.net.v = S.params + 2 * kSurParams;
+  S.net.grad = S.params + 3 * kSurParams;
+  S.net.wf = S.wbf;
+  S.net.wb = S.wbf + wn;
+  S.net.w_in = S.wsmall;
+  S.net.w_out = S.wsmall + kSurC * 4 * kSurK;
+  return SONAR_OK;
+}
+
+// Common checks and set-up of a surrogate call over P pings: parameters, the scene, the
+// isovelocity restriction, the range grid, the poses on the device and the rendering
+// of every beam of every ping into sur.feat.
+int sur_begin(sonar_ctx* ctx, const sonar_pose* poses, int P, const sonar_params* p, const sonar_ssp* ssp,
+              Derived& d) {
+  int rc;
+  if (!ctx->has_scene) return fail(ctx, SONAR_E_NOSCENE, "no scene uploaded");
+  if (!poses || P < 1) return fail(ctx, SONAR_E_ARG, "need at least one pose");
+  if ((rc = validate(ctx, p, ssp))) return rc;
+  for (int i = 0; i < P; ++i) {
+    const double* q = poses[i].q;
+    double n2 = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
+    if (!(n2 > 1e-12) || !isfinite(poses[i].t[0] + poses[i].t[1] + poses[i].t[2]))
+      return fail(ctx, SONAR_E_ARG, "pose %d is not finite or has a zero quaternion", i);
+  }
+  if (!ctx->sur.has_weights) return fail(ctx, SONAR_E_ARG, "the surrogate has no weights (sonar_sur_set_weights)");
+  CU(cudaSetDevice(ctx->device));
+  if ((rc = drain(ctx))) return rc;
+  if ((rc = derive(ctx, p, ssp, poses[0].t[0], poses[0].t[2], P, d))) return rc;
+  if (d.curved || ctx->fld.nx > 0)
+    return fail(ctx, SONAR_E_UNSUPPORTED, "the surrogate renders isovelocity routes only");
+  if (d.nr % 256 != 0) return fail(ctx, SONAR_E_UNSUPPORTED, "the surrogate needs n_range a multiple of 256");
+  auto& S = ctx->sur;
+  if ((rc = grow(ctx, S.poses, S.poses_cap, P, sizeof(DevPose), false))) return rc;
+  std::vector<DevPose> hp(P);
+  for (int i = 0; i < P; ++i) hp[i] = dev_pose(poses[i]);
+  CU(cudaEventRecord(ctx->ev_in, ctx->user_stream));
+  CU(cudaStreamWaitEvent(ctx->stream, ctx->ev_in, 0));
+  CU(cudaMemcpyAsync(S.poses, hp.data(), sizeof(DevPose) * P, cudaMemcpyHostToDevice, ctx->stream));
+  if ((rc = grow(ctx, S.feat, S.feat_cap, (int64_t)P * d.nb * 8, sizeof(float), false))) return rc;
+  if (!ctx->err_dev) CU(cudaMalloc(&ctx->err_dev, sizeof(int)));
+  CU(cudaMemsetAsync(ctx->err_dev, 0, sizeof(int), ctx->stream));
+  TraceArgs ta = trace_args(ctx, P, p, d, false);
+  ta.poses = S.poses;
+  CU(launch_render(ta, p->n_beam_az, p->n_beam_el, p->hfov_rad, p->vfov_rad, S.feat, ctx->stream));
+  return SONAR_OK;
+}
+
+// Activation and gradient buffers for `beams` beams of rb rows (zero padding rows
+// included; they are zeroed here once and never written afterwards).
+int sur_buffers(sonar_ctx* ctx, int64_t beams, int rb) {
+  auto& S = ctx->sur;
+  if (S.buf && beams <= S.beams_cap && rb == S.rb) return SONAR_OK;
+  dfree(S.buf);
+  S.beams_cap = 0;
+  const int64_t rows = beams * rb;
+  CU(cudaMalloc(&S.buf, sizeof(__nv_bfloat16) * kSurC * rows * kSurBufs));
+  CU(cudaMemsetAsync(S.buf, 0, sizeof(__nv_bfloat16) * kSurC * rows * kSurBufs, ctx->stream));
+  S.beams_cap = beams;
+  S.rb = rb;
+  return SONAR_OK;
+}
+
+__nv_bfloat16* sur_buf(sonar_ctx* ctx, int i) {
+  return ctx->sur.buf + (int64_t)i * ctx->sur.beams_cap * ctx->sur.rb * kSurC;
+}
+
+// Forward pass of n_sel beams (rendering rows `beams`, or the n_feat rows of feat in
+// order): layer 0, the four hidden layers on the tensor cores, the output layer.
+// Training (target != null) leaves the loss gradient in sur.g; inference writes env.
+int sur_forward(sonar_ctx* ctx, const float* feat, const int32_t* beams, int64_t n_sel, int64_t n_feat,
+                const sonar_params* p, const Derived& d, const float* target, float* env) {
+  auto& S = ctx->sur;
+  int rc;
+  const int rb = d.nr + 2 * kSurHalo;
+  cudaStream_t st = ctx->stream;
+  const double inv_dr = 1.0 / d.dr;
+  CU(sur_input(feat, beams, n_sel, n_feat, d.nr, p->r_min_m, inv_dr, S.net, sur_buf(ctx, 0), rb, ctx->err_dev, st));
+  for (int L = 1; L <= 4; ++L) {
+    SurConvArgs ca;
+    memset(&ca, 0, sizeof(ca));
+    if ((rc = make_map(ctx, &ca.map_x, sur_buf(ctx, L - 1), n_sel * rb, kSurC, 128 + kSurK - 1, false))) return rc;
+    if ((rc = make_map(ctx, &ca.map_w, S.net.wf + (int64_t)(L - 1) * kSurK * kSurC * kSurC, kSurK * kSurC, kSurC,
+                       kSurC, false)))
+      return rc;
+    ca.bias = S.net.theta + sur_boff(L);
+    ca.out = sur_buf(ctx, L);
+    ca.n_tiles = n_sel * (d.nr / 128);
+    ca.tiles_per_beam = d.nr / 128;
+    ca.rb = rb;
+    ca.err = ctx->err_dev;
+    CU(sur_conv(ca, false, ctx->sm_count, st));
+  }
+  const float inv_scale = (float)(1.0 / S.e_scale);
+  const float g_scale = (float)(2.0 / ((double)n_sel * d.nr));
+  CU(sur_head(sur_buf(ctx, 4), S.net, n_sel, d.nr, rb, target, beams, n_feat, inv_scale, g_scale, S.g, S.loss, env,
+              (float)S.e_scale, ctx->err_dev, st));
+  return SONAR_OK;
+}
+
+// Backward pass after a training forward pass: gradients of every parameter into sur.grad.
+int sur_backward(sonar_ctx* ctx, const float* feat, const int32_t* beams, int64_t n_sel, int64_t n_feat,
+                 const sonar_params* p, const Derived& d) {
+  auto& S = ctx->sur;
+  int rc;
+  const int rb = d.nr + 2 * kSurHalo;
+  cudaStream_t st = ctx->stream;
+  CU(sur_head_bwd(sur_buf(ctx, 4), S.g, S.net, n_sel, d.nr, rb, sur_buf(ctx, 5), st));
+  int dz = 5;  // buffer of dz_{L+1}
+  for (int L = 4; L >= 1; --L) {
+    SurDwArgs wa;
+    memset(&wa, 0, sizeof(wa));
+    if ((rc = make_map(ctx, &wa.map_x, sur_buf(ctx, L - 1), n_sel * rb, kSurC, 80, false))) return rc;
+    if ((rc = make_map(ctx, &wa.map_dz, sur_buf(ctx, dz), n_sel * rb, kSurC, 80, false))) return rc;
+    wa.grad_w = S.net.grad + sur_woff(L);
+    wa.grad_b = S.net.grad + sur_boff(L);
+    wa.kb_per_beam = d.nr / 64 + 1;
+    wa.n_kb = n_sel * wa.kb_per_beam;
+    wa.nr = d.nr;
+    wa.rb = rb;
+    wa.err = ctx->err_dev;
+    CU(sur_dw(wa, ctx->sm_count, st));
+    SurConvArgs ca;
+    memset(&ca, 0, sizeof(ca));
+    if ((rc = make_map(ctx, &ca.map_x, sur_buf(ctx, dz), n_sel * rb, kSurC, 128 + kSurK - 1, false))) return rc;
+    if ((rc = make_map(ctx, &ca.map_w, S.net.wb + (int64_t)(L - 1) * kSurK * kSurC * kSurC, kSurK * kSurC, kSurC,
+                       kSurC, false)))
+      return rc;
+    ca.mask = sur_buf(ctx, L - 1);
+    ca.out = sur_buf(ctx, 11 - dz);  // the other gradient buffer
+    ca.n_tiles = n_sel * (d.nr / 128);
+    ca.tiles_per_beam = d.nr / 128;
+    ca.rb = rb;
+    ca.err = ctx->err_dev;
+    CU(sur_conv(ca, true, ctx->sm_count, st));
+    dz = 11 - dz;
+  }
+  CU(sur_l1_dw(feat, beams, n_sel, n_feat, d.nr, p->r_min_m, 1.0 / d.dr, sur_buf(ctx, dz), rb, S.net, st));
+  return SONAR_OK;
+}
+
+// Waits for the work stream, orders the caller's stream after it and turns the device
+// error word into a return code.
+int sur_finish(sonar_ctx* ctx) {
+  CU(cudaEventRecord(ctx->ev_out, ctx->stream));
+  CU(cudaStreamWaitEvent(ctx->user_stream, ctx->ev_out, 0));
+  CU(cudaStreamSynchronize(ctx->stream));
+  int errw = 0;
+  CU(cudaMemcpy(&errw, ctx->err_dev, sizeof(int), cudaMemcpyDeviceToHost));
+  if (errw & kErrIndex) return fail(ctx, SONAR_E_ARG, "a beam index lies outside the rendered beams");
+  if (errw & kErrTimeout) return fail(ctx, SONAR_E_TIMEOUT, "a device-side wait exceeded its limit");
+  if (errw & (kErrLoop | kErrStack)) return fail(ctx, SONAR_E_TIMEOUT, "ray casting exceeded a loop or stack limit");
+  return SONAR_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1262,7 +1464,8 @@ int sonar_create(sonar_ctx** out, int device, void* cuda_stream) {
   if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return SONAR_E_CUDA;
   if (!(prop.major == 10 && prop.minor == 3)) return SONAR_E_UNSUPPORTED;
   if (cudaSetDevice(device) != cudaSuccess) return SONAR_E_CUDA;
-  if (prepare_gemm() != cudaSuccess || prepare_synth_tc() != cudaSuccess) return SONAR_E_CUDA;
+  if (prepare_gemm() != cudaSuccess || prepare_synth_tc() != cudaSuccess || sur_conv_prepare() != cudaSuccess)
+    return SONAR_E_CUDA;
   sonar_ctx* c = new (std::nothrow) sonar_ctx();
   if (!c) return SONAR_E_NOMEM;
   c->device = device;
@@ -1411,6 +1614,9 @@ int sonar_destroy(sonar_ctx* c) {
   dfree(c->n_hits);
   dfree(c->counts); dfree(c->offsets); dfree(c->S); dfree(c->S_raw); dfree(c->ptab); dfree(c->x_hi); dfree(c->x_lo); dfree(c->gain);
   dfree(c->env_stage); dfree(c->keys); dfree(c->pmax); dfree(c->cloud_stage); dfree(c->n_cloud_dev); dfree(c->err_dev); dfree(c->synth_bounds);
+  auto& S = c->sur;
+  dfree(S.params); dfree(S.wbf); dfree(S.wsmall); dfree(S.loss); dfree(S.feat); dfree(S.poses); dfree(S.buf); dfree(S.g);
+  dfree(S.cmp_tot); dfree(S.cmp_pmax); dfree(S.cmp_pk); dfree(S.cmp_bmax);
   delete c;
   return SONAR_OK;
 }
@@ -1591,4 +1797,208 @@ int sonar_get_stats(const sonar_ctx* ctx, sonar_stats* out) {
   return SONAR_OK;
 }
 
+
+int sonar_sur_set_weights(sonar_ctx* ctx, const float* params, int64_t n, double e_scale) {
+  if (!ctx) return SONAR_E_ARG;
+  ctx->err.clear();
+  if (!params || n != kSurParams) return fail(ctx, SONAR_E_ARG, "need %lld parameters", (long long)kSurParams);
+  if (!(e_scale > 0) || !isfinite(e_scale)) return fail(ctx, SONAR_E_ARG, "e_scale must be positive");
+  for (int64_t i = 0; i < n; ++i)
+    if (!isfinite(params[i])) return fail(ctx, SONAR_E_ARG, "parameter %lld is not finite", (long long)i);
+  CU(cudaSetDevice(ctx->device));
+  int rc;
+  if ((rc = drain(ctx))) return rc;
+  if ((rc = sur_alloc_params(ctx))) return rc;
+  auto& S = ctx->sur;
+  CU(cudaMemcpyAsync(S.net.theta, params, sizeof(float) * kSurParams, cudaMemcpyHostToDevice, ctx->stream));
+  CU(cudaMemsetAsync(S.net.m, 0, sizeof(float) * 2 * kSurParams, ctx->stream));
+  CU(sur_pack(S.net, 0, 0.f, 0.f, 0.f, 0.f, 1.f, 1.f, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  S.e_scale = e_scale;
+  S.step = 0;
+  S.has_weights = true;
+  return SONAR_OK;
+}
+
+int sonar_sur_get_weights(sonar_ctx* ctx, float* params, int64_t n) {
+  if (!ctx) return SONAR_E_ARG;
+  ctx->err.clear();
+  if (!params || n != kSurParams) return fail(ctx, SONAR_E_ARG, "need room for %lld parameters", (long long)kSurParams);
+  if (!ctx->sur.has_weights) return fail(ctx, SONAR_E_ARG, "the surrogate has no weights");
+  CU(cudaSetDevice(ctx->device));
+  CU(cudaStreamSynchronize(ctx->stream));
+  CU(cudaMemcpy(params, ctx->sur.net.theta, sizeof(float) * kSurParams, cudaMemcpyDeviceToHost));
+  return SONAR_OK;
+}
+
+int sonar_sur_render(sonar_ctx* ctx, const sonar_pose* poses, int32_t n_pings, const sonar_params* params,
+                     const sonar_ssp* ssp, float* feat) {
+  if (!ctx) return SONAR_E_ARG;
+  ctx->err.clear();
+  if (!feat) return fail(ctx, SONAR_E_ARG, "feat is NULL");
+  Derived d;
+  const bool had = ctx->sur.has_weights;
+  ctx->sur.has_weights = true;  // the rendering needs no network
+  int rc = sur_begin(ctx, poses, n_pings, params, ssp, d);
+  ctx->sur.has_weights = had;
+  if (rc) return rc;
+  const int64_t n = (int64_t)n_pings * d.nb * 8;
+  void* fd = nullptr;
+  if (classify(feat, &fd) != Mem::Host) {
+    CU(cudaMemcpyAsync(fd, ctx->sur.feat, sizeof(float) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+    return sur_finish(ctx);
+  }
+  if ((rc = sur_finish(ctx))) return rc;
+  CU(cudaMemcpy(feat, ctx->sur.feat, sizeof(float) * n, cudaMemcpyDeviceToHost));
+  return SONAR_OK;
+}
+
+int sonar_sur_ping(sonar_ctx* ctx, const sonar_pose* poses, int32_t n_pings, const sonar_params* params,
+                   const sonar_ssp* ssp, float* env) {
+  if (!ctx) return SONAR_E_ARG;
+  ctx->err.clear();
+  if (!env) return fail(ctx, SONAR_E_ARG, "env is NULL");
+  Derived d;
+  int rc = sur_begin(ctx, poses, n_pings, params, ssp, d);
+  if (rc) return rc;
+  const int64_t beams = (int64_t)n_pings * d.nb;
+  const int64_t chunk = beams < kSurChunk ? beams : kSurChunk;
+  if ((rc = sur_buffers(ctx, chunk, d.nr + 2 * kSurHalo))) return rc;
+  void* ed = nullptr;
+  const bool dev = classify(env, &ed) != Mem::Host;
+  float* out = static_cast<float*>(ed);
+  if (!dev) {
+    if ((rc = grow(ctx, ctx->env_stage, ctx->env_cap, beams * d.nr, sizeof(float), false))) return rc;
+    out = ctx->env_stage;
+  }
+  for (int64_t b0 = 0; b0 < beams; b0 += chunk) {
+    const int64_t nb = beams - b0 < chunk ? beams - b0 : chunk;
+    if ((rc = sur_forward(ctx, ctx->sur.feat + b0 * 8, nullptr, nb, nb, params, d, nullptr, out + b0 * d.nr)))
+      return rc;
+  }
+  if ((rc = sur_finish(ctx))) return rc;
+  if (!dev) CU(cudaMemcpy(env, ctx->env_stage, sizeof(float) * beams * d.nr, cudaMemcpyDeviceToHost));
+  return SONAR_OK;
+}
+
+int sonar_sur_geometric(sonar_ctx* ctx, const sonar_pose* poses, int32_t n_pings, const sonar_params* params,
+                        const sonar_ssp* ssp, float* env) {
+  if (!ctx) return SONAR_E_ARG;
+  ctx->err.clear();
+  if (!env) return fail(ctx, SONAR_E_ARG, "env is NULL");
+  Derived d;
+  const bool had = ctx->sur.has_weights;
+  ctx->sur.has_weights = true;  // no network involved
+  int rc = sur_begin(ctx, poses, n_pings, params, ssp, d);
+  ctx->sur.has_weights = had;
+  if (rc) return rc;
+  if ((rc = ensure_tables(ctx, params, d))) return rc;
+  const int64_t beams = (int64_t)n_pings * d.nb;
+  void* ed = nullptr;
+  const bool dev = classify(env, &ed) != Mem::Host;
+  float* out = static_cast<float*>(ed);
+  if (!dev) {
+    if ((rc = grow(ctx, ctx->env_stage, ctx->env_cap, beams * d.nr, sizeof(float), false))) return rc;
+    out = ctx->env_stage;
+  }
+  CU(sur_geometric(ctx->sur.feat, beams, params->n_beam_az, params->n_beam_el, params->hfov_rad, params->vfov_rad, d.nr,
+                   params->r_min_m, d.dr, d.c_ref, params->alpha_np_per_m, params->pulse_s, ctx->rtab, kRTab, out,
+                   ctx->stream));
+  if ((rc = sur_finish(ctx))) return rc;
+  if (!dev) CU(cudaMemcpy(env, ctx->env_stage, sizeof(float) * beams * d.nr, cudaMemcpyDeviceToHost));
+  return SONAR_OK;
+}
+
+int sonar_sur_train_step(sonar_ctx* ctx, const sonar_pose* poses, int32_t n_pings, const sonar_params* params,
+                         const sonar_ssp* ssp, const float* env_target, const int32_t* beams, int64_t n_sel,
+                         double lr, int32_t update, double* loss, float* grad) {
+  if (!ctx) return SONAR_E_ARG;
+  ctx->err.clear();
+  if (!env_target) return fail(ctx, SONAR_E_ARG, "env_target is NULL");
+  if (update && !(lr > 0 && isfinite(lr))) return fail(ctx, SONAR_E_ARG, "lr must be positive");
+  Derived d;
+  int rc = sur_begin(ctx, poses, n_pings, params, ssp, d);
+  if (rc) return rc;
+  const int64_t n_feat = (int64_t)n_pings * d.nb;
+  if (!beams) n_sel = n_feat;
+  if (n_sel < 1 || n_sel > (1LL << 24)) return fail(ctx, SONAR_E_ARG, "n_sel must lie in [1, 2^24]");
+  void* td = nullptr;
+  void* bd = nullptr;
+  if (classify(const_cast<float*>(env_target), &td) == Mem::Host)
+    return fail(ctx, SONAR_E_ARG, "env_target must be device memory");
+  if (beams && classify(const_cast<int32_t*>(beams), &bd) == Mem::Host)
+    return fail(ctx, SONAR_E_ARG, "beams must be device memory");
+  auto& S = ctx->sur;
+  if ((rc = sur_buffers(ctx, n_sel, d.nr + 2 * kSurHalo))) return rc;
+  if ((rc = grow(ctx, S.g, S.g_cap, n_sel * d.nr, sizeof(float), false))) return rc;
+  CU(cudaMemsetAsync(S.net.grad, 0, sizeof(float) * kSurParams, ctx->stream));
+  CU(cudaMemsetAsync(S.loss, 0, sizeof(double), ctx->stream));
+  const int32_t* bsel = static_cast<const int32_t*>(bd);
+  if ((rc = sur_forward(ctx, S.feat, bsel, n_sel, n_feat, params, d, static_cast<const float*>(td), nullptr))) return rc;
+  if ((rc = sur_backward(ctx, S.feat, bsel, n_sel, n_feat, params, d))) return rc;
+  if (update) {
+    const double b1 = 0.9, b2 = 0.999;
+    const int64_t t = S.step + 1;
+    CU(sur_pack(S.net, 1, (float)lr, (float)b1, (float)b2, 1e-8f, (float)(1.0 - pow(b1, (double)t)),
+                (float)(1.0 - pow(b2, (double)t)), ctx->stream));
+  }
+  if ((rc = sur_finish(ctx))) return rc;
+  if (update) S.step++;
+  if (loss) {
+    double sq = 0.0;
+    CU(cudaMemcpy(&sq, S.loss, sizeof(double), cudaMemcpyDeviceToHost));
+    *loss = sq / ((double)n_sel * d.nr);
+  }
+  if (grad) CU(cudaMemcpy(grad, S.net.grad, sizeof(float) * kSurParams, cudaMemcpyDeviceToHost));
+  return SONAR_OK;
+}
+
+int sonar_sur_compare(sonar_ctx* ctx, const float* env, const float* env_ref, int32_t n_pings,
+                      const sonar_params* params, double rel_thr, sonar_sur_metrics* out) {
+  if (!ctx) return SONAR_E_ARG;
+  ctx->err.clear();
+  if (!env || !env_ref || !out || n_pings < 1 || !params) return fail(ctx, SONAR_E_ARG, "bad arguments");
+  if (!(rel_thr >= 0 && rel_thr <= 1)) return fail(ctx, SONAR_E_ARG, "rel_thr must lie in [0, 1]");
+  if (params->n_beam_az < 1 || params->n_beam_el < 1 || params->n_range < 1 || !(params->r_max_m > params->r_min_m))
+    return fail(ctx, SONAR_E_ARG, "bad beam or range grid");
+  void* ed = nullptr;
+  void* rd = nullptr;
+  if (classify(const_cast<float*>(env), &ed) == Mem::Host || classify(const_cast<float*>(env_ref), &rd) == Mem::Host)
+    return fail(ctx, SONAR_E_ARG, "both volumes must be device memory");
+  CU(cudaSetDevice(ctx->device));
+  int rc;
+  if ((rc = drain(ctx))) return rc;
+  auto& S = ctx->sur;
+  const int nb = params->n_beam_az * params->n_beam_el, nr = params->n_range;
+  const int64_t beams = (int64_t)n_pings * nb;
+  if (!S.cmp_tot) CU(cudaMalloc(&S.cmp_tot, sizeof(double) * 12));
+  if ((rc = grow(ctx, S.cmp_pmax, S.cmp_cap, n_pings, sizeof(unsigned), false))) return rc;
+  if ((rc = grow(ctx, S.cmp_pk, S.cmp_pk_cap, 2 * beams, sizeof(int32_t), false))) return rc;
+  if ((rc = grow(ctx, S.cmp_bmax, S.cmp_bmax_cap, beams, sizeof(float), false))) return rc;
+  const double dr = (params->r_max_m - params->r_min_m) / nr;
+  int n_blank = 0;
+  while (n_blank < nr && params->r_min_m + (n_blank + 0.5) * dr < params->r_blank_m) ++n_blank;
+  CU(cudaEventRecord(ctx->ev_in, ctx->user_stream));
+  CU(cudaStreamWaitEvent(ctx->stream, ctx->ev_in, 0));
+  CU(cudaMemsetAsync(S.cmp_tot, 0, sizeof(double) * 12, ctx->stream));
+  CU(cudaMemsetAsync(S.cmp_pmax, 0, sizeof(unsigned) * n_pings, ctx->stream));
+  CU(sur_compare(static_cast<const float*>(ed), static_cast<const float*>(rd), n_pings, nb, nr, n_blank, (float)rel_thr,
+                 S.cmp_pmax, S.cmp_pk, S.cmp_bmax, S.cmp_tot, ctx->stream));
+  CU(cudaEventRecord(ctx->ev_out, ctx->stream));
+  CU(cudaStreamWaitEvent(ctx->user_stream, ctx->ev_out, 0));
+  CU(cudaStreamSynchronize(ctx->stream));
+  double t[12];
+  CU(cudaMemcpy(t, S.cmp_tot, sizeof(t), cudaMemcpyDeviceToHost));
+  out->nl2 = t[1] > 0 ? sqrt(t[0] / t[1]) : 0.0;
+  out->lit_beams = (int64_t)t[3];
+  out->peak_bin_mean = t[3] > 0 ? t[2] / t[3] : 0.0;
+  out->peak_within_1 = t[3] > 0 ? t[4] / t[3] : 0.0;
+  out->peak_within_4 = t[3] > 0 ? t[5] / t[3] : 0.0;
+  out->cells = (int64_t)t[6];
+  const double m1 = t[6] > 0 ? t[7] / t[6] : 0.0, m2 = t[6] > 0 ? t[8] / t[6] : 0.0;
+  const double r1 = t[6] > 0 ? t[9] / t[6] : 0.0, r2 = t[6] > 0 ? t[10] / t[6] : 0.0;
+  out->si = m1 > 0 ? m2 / (m1 * m1) - 1.0 : 0.0;
+  out->si_ref = r1 > 0 ? r2 / (r1 * r1) - 1.0 : 0.0;
+  return SONAR_OK;
+}
 }  // extern "C"

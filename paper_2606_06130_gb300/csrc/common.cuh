@@ -29,6 +29,7 @@ constexpr int kErrTimeout = 1;
 constexpr int kErrStack = 2;
 constexpr int kErrCapacity = 4;
 constexpr int kErrLoop = 8;
+constexpr int kErrIndex = 16;  // an index array named an element outside its buffer
 
 // One hit as consumed by echo synthesis (32 bytes).
 struct HitRec {
@@ -193,6 +194,9 @@ cudaError_t launch_trace(const TraceArgs& a, int sm_count, cudaStream_t st);
 cudaError_t launch_points(const TraceArgs& a, cudaStream_t st);
 cudaError_t launch_point_pairs(const TraceArgs& a, cudaStream_t st);
 cudaError_t launch_volume(const TraceArgs& a, cudaStream_t st);
+// Beam-centre geometric rendering of the learned surrogate: feat [n_pings][nbe * nba][8].
+cudaError_t launch_render(const TraceArgs& a, int32_t nba, int32_t nbe, double hfov, double vfov, float* feat,
+                          cudaStream_t st);
 
 struct SynthArgs {
   const HitRec* hits_sorted;
@@ -223,6 +227,83 @@ cudaError_t prepare_synth_tc();
 // a shape that does not fit) takes the default choice.
 cudaError_t launch_synth_tc(const SynthArgs& a, int want_pairs, int sm_count, cudaStream_t st);
 cudaError_t launch_rtab(float2* rtab, float2* rtab_s, double pulse, double bw, cudaStream_t st);
+
+// ------------------------------------------------------------------ learned surrogate
+// Six 1-D convolutions along range (kernel 9, channels 4 -> 64 x 5 -> 1), packed into one
+// FP32 parameter vector layer by layer: W_l [cout][cin][9] then b_l [cout].
+constexpr int kSurC = 64;     // hidden channels
+constexpr int kSurK = 9;      // kernel taps
+constexpr int kSurHalo = 8;   // zero rows before and after each beam's bins in activation buffers
+__host__ __device__ constexpr int sur_cin(int l) { return l == 0 ? 4 : kSurC; }
+__host__ __device__ constexpr int sur_cout(int l) { return l == 5 ? 1 : kSurC; }
+__host__ __device__ constexpr int64_t sur_woff(int l) {
+  return l == 0 ? 0 : sur_woff(l - 1) + (int64_t)sur_cout(l - 1) * sur_cin(l - 1) * kSurK + sur_cout(l - 1);
+}
+__host__ __device__ constexpr int64_t sur_boff(int l) { return sur_woff(l) + (int64_t)sur_cout(l) * sur_cin(l) * kSurK; }
+constexpr int64_t kSurParams = sur_woff(6);
+static_assert(kSurParams == 150657, "parameter count of the surrogate network");
+
+// Device state of the network: FP32 master parameters, Adam moments, gradients, and the
+// BF16 weights in the layouts the kernels read (the first and last layers' as FP32
+// values of their BF16 rounding).
+struct SurNet {
+  float* theta;         // [kSurParams]
+  float* m;             // Adam first moment
+  float* v;             // Adam second moment
+  float* grad;          // [kSurParams]
+  __nv_bfloat16* wf;    // hidden layers 1..4: [4][9][64 cout][64 cin], forward B operands
+  __nv_bfloat16* wb;    // [4][9][64 cin][64 cout], taps reversed: backward-data B operands
+  float* w_in;          // layer 0: [64][4][9]
+  float* w_out;         // layer 5: [64][9]
+};
+// Adam step (update != 0; bias corrections bc1 = 1 - beta1^t, bc2 = 1 - beta2^t) and the
+// repacking of the BF16 weight copies from the master parameters.
+cudaError_t sur_pack(const SurNet& n, int update, float lr, float b1, float b2, float eps, float bc1, float bc2,
+                     cudaStream_t st);
+// Layer 0 from the rendering: act1 rows of the selected beams (beams: indices into the
+// rendering's rows, or null for all). Sparse input: the splats of two hits per beam.
+cudaError_t sur_input(const float* feat, const int32_t* beams, int64_t n_sel, int64_t n_feat, int nr, double r_min,
+                      double inv_dr, const SurNet& n, __nv_bfloat16* act1, int rb, int* err, cudaStream_t st);
+struct SurConvArgs {
+  CUtensorMap map_x;              // input rows [n_sel * rb][64] BF16, box 64 x 136
+  CUtensorMap map_w;              // B operands [9 * 64][64] BF16, box 64 x 64
+  const float* bias;              // forward: [64]
+  const __nv_bfloat16* mask;      // backward-data: the gradient passes where these are > 0
+  __nv_bfloat16* out;
+  int64_t n_tiles;
+  int tiles_per_beam, rb;
+  int* err;
+};
+// Hidden 64 -> 64 layer on the tensor cores: forward (bias, ReLU) or backward-data.
+cudaError_t sur_conv(const SurConvArgs& a, bool backward, int sm_count, cudaStream_t st);
+cudaError_t sur_conv_prepare();
+// Output layer 5: envelope out (inference) or the loss gradient (training).
+cudaError_t sur_head(const __nv_bfloat16* act5, const SurNet& n, int64_t n_sel, int nr, int rb, const float* target,
+                     const int32_t* beams, int64_t n_feat, float inv_scale, float g_scale, float* g, double* loss,
+                     float* env_out, float e_scale, int* err, cudaStream_t st);
+cudaError_t sur_head_bwd(const __nv_bfloat16* act5, const float* g, const SurNet& n, int64_t n_sel, int nr, int rb,
+                         __nv_bfloat16* dz5, cudaStream_t st);
+struct SurDwArgs {
+  CUtensorMap map_x;   // the layer's input rows, box 64 x 80
+  CUtensorMap map_dz;  // its output gradient rows, box 64 x 80
+  float* grad_w;       // [64][64][9] in the parameter packing
+  float* grad_b;       // [64]
+  int64_t n_kb;        // K-blocks of 64 positions: n_sel * (nr / 64 + 1)
+  int kb_per_beam, nr, rb;
+  int* err;
+};
+// Weight and bias gradients of a hidden layer on the tensor cores.
+cudaError_t sur_dw(const SurDwArgs& a, int sm_count, cudaStream_t st);
+// Layer-0 weight and bias gradients from the sparse input.
+cudaError_t sur_l1_dw(const float* feat, const int32_t* beams, int64_t n_sel, int64_t n_feat, int nr, double r_min,
+                      double inv_dr, const __nv_bfloat16* dz1, int rb, const SurNet& n, cudaStream_t st);
+// Envelope of the rendering without the network: [n_beams][nr].
+cudaError_t sur_geometric(const float* feat, int64_t n_beams, int nba, int nbe, double hfov, double vfov, int nr,
+                          double r_min, double dr, double c_ref, double alpha, double T, const float2* rtab, int n_tab,
+                          float* env, cudaStream_t st);
+// Comparison of two envelope volumes [P][nb][nr]: totals[12] (doubles, zeroed by the caller).
+cudaError_t sur_compare(const float* env, const float* ref, int P, int nb, int nr, int n_blank, float rel_thr,
+                        unsigned* ping_max, int32_t* beam_pk, float* beam_max, double* totals, cudaStream_t st);
 
 // Raw element series (echo before pulse compression) and its matched filter.
 // launch_ptab: for each phase s < U, the transmitted pulse shifted by s dt / U, p(u + s dt

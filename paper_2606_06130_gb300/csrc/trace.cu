@@ -1085,6 +1085,86 @@ __global__ void k_volume(TraceArgs A) {
 
 // Sonar-frame sub-ray directions (Sec. III Eq. 2-3 grid, cell-centred) with hashed
 // jitter inside 2x2 quarter cells, and the sub-ray solid angle per elevation row.
+// Geometric rendering of the learned surrogate: one ray per beam along the beam centre,
+// routed by the same straight-ray rules as route_straight (mirror facets and the sea
+// surface reflect, at most max_bounces, up to the one-way length limit). Records the
+// first two scatter (triangle) hits of the route: one-way length L, incidence cosine,
+// facet reflectivity and the route's one-way reflection product, zeros where absent.
+// feat: [n_pings][n_beam_el * n_beam_az][8].
+__global__ void __launch_bounds__(128) k_render(TraceArgs A, int nba, int nbe, double hfov, double vfov, float* feat) {
+  pdl_wait();
+  const int nb = nba * nbe;
+  const int64_t total = (int64_t)A.n_pings * nb;
+  const F2 eps = F2{(float)kEpsHit, (float)(kEpsHit - (double)(float)kEpsHit)};
+  for (int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gid < total; gid += (int64_t)gridDim.x * blockDim.x) {
+    const int ping = (int)(gid / nb), b = (int)(gid % nb);
+    const int i = b % nba, j = b / nba;
+    const double az = -hfov / 2 + (i + 0.5) * hfov / nba;
+    const double el = -vfov / 2 + (j + 0.5) * vfov / nbe;
+    const double us[3] = {cos(el) * cos(az), cos(el) * sin(az), sin(el)};
+    F2 u[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) u[k] = f2_of(us[k]);
+    const DevPose& P = A.poses[ping];
+    F2 dw[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      dw[k] = F2{P.R32[3 * k], P.R_lo[3 * k]} * u[0] + F2{P.R32[3 * k + 1], P.R_lo[3 * k + 1]} * u[1] +
+              F2{P.R32[3 * k + 2], P.R_lo[3 * k + 2]} * u[2];
+    DF3 pos = DF3{F2{P.t32[0], P.t_lo[0]}, F2{P.t32[1], P.t_lo[1]}, F2{P.t32[2], P.t_lo[2]}};
+    DF3 dir = DF3{dw[0], dw[1], dw[2]};
+    float out[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    F2 L = f2(0.f);
+    float gam = 1.0f;
+    int bounce = 0, prev = -1, n_hit = 0;
+    for (int iter = 0; iter < 8 && n_hit < 2; ++iter) {
+      const F2 tlim = f2(A.L_stop_df) - L;
+      if (!(tlim.hi > 0.f)) break;
+      HitT<F2> hq = closest_hit(A.sc, pos, dir, eps, tlim, prev, A.err, iter == 0 ? P.t32 : nullptr);
+      F2 ts = F2{INFINITY, 0.f};
+      if (A.has_surface && prev != -2 && dir.z.hi != 0.f) {
+        const F2 num = f2(A.surface_z_df) - pos.z;
+        if (num.hi * dir.z.hi > 0.f && fabsf(num.hi) <= tlim.hi * fabsf(dir.z.hi) * (1.0f + 1e-5f)) {
+          const F2 t = num / dir.z;
+          if (eps < t && !(tlim < t)) ts = t;
+        }
+      }
+      if (hq.prim < 0 && ts.hi == INFINITY) break;
+      if (ts < hq.t) {
+        if (bounce >= A.max_bounces) break;
+        pos = axpy(pos, ts, dir);
+        L = L + ts;
+        dir.z = -dir.z;
+        gam *= (float)A.r_surface;
+        bounce++;
+        prev = -2;
+        continue;
+      }
+      L = L + hq.t;
+      out[4 * n_hit] = L.hi + L.lo;
+      out[4 * n_hit + 1] = kinc32(A.sc, hq.leaf, dir);
+      out[4 * n_hit + 2] = A.sc.tri_mu[hq.leaf];
+      out[4 * n_hit + 3] = gam;
+      ++n_hit;
+      if ((A.sc.tri_flags[hq.leaf] & 1) && bounce < A.max_bounces) {
+        pos = axpy(pos, hq.t, dir);
+        F2 w;
+        const DF3 n = plane_n_df(A.sc, hq.leaf, w);
+        const F2 k = (dot(dir, n) + dot(dir, n)) / dot(n, n);
+        dir = DF3{dir.x - k * n.x, dir.y - k * n.y, dir.z - k * n.z};
+        gam *= (float)A.r_seabed;
+        bounce++;
+        prev = hq.prim;
+        continue;
+      }
+      break;
+    }
+    float4* o4 = reinterpret_cast<float4*>(feat + gid * 8);
+    o4[0] = make_float4(out[0], out[1], out[2], out[3]);
+    o4[1] = make_float4(out[4], out[5], out[6], out[7]);
+  }
+}
+
 __global__ void k_ray_table(double* dirs, float* dirs32, float* row_domega, int nra, int nre, int nsub, double hfov,
                             double vfov, uint32_t seed32) {
   int64_t n = (int64_t)nra * nre * nsub;
@@ -1158,6 +1238,14 @@ cudaError_t launch_trace(const TraceArgs& a, int sm_count, cudaStream_t st) {
                   : a.cross ? launch_pdl(k_trace<false, true>, dim3((unsigned)blocks), dim3(128), 0, st, a)
                             : launch_pdl(k_trace<false, false>, dim3((unsigned)blocks), dim3(128), 0, st, a);
   if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_render(const TraceArgs& a, int32_t nba, int32_t nbe, double hfov, double vfov, float* feat,
+                          cudaStream_t st) {
+  const int64_t total = (int64_t)a.n_pings * nba * nbe;
+  if (total == 0) return cudaSuccess;
+  k_render<<<(unsigned)ceil_div(total, 128), 128, 0, st>>>(a, nba, nbe, hfov, vfov, feat);
   return cudaGetLastError();
 }
 

@@ -34,6 +34,7 @@ class Scene:
     points: np.ndarray = field(default_factory=lambda: np.zeros((0, 3), np.float32))
     sigma: np.ndarray = field(default_factory=lambda: np.zeros((0,), np.float32))
     planes: np.ndarray = field(default_factory=lambda: np.zeros((0, 4), np.float64))
+    meta: dict = field(default_factory=dict)  # generator facts (e.g. the wall's standoff)
 
     @property
     def n_tris(self) -> int:
@@ -351,3 +352,83 @@ def workload(name: str):
     if name == "c4":
         return scene_c4(), sensor_params(name), trajectory_c4(), ssp(name)
     raise ValueError(name)
+
+
+# ------------------------------------------------------------------------ surrogate
+SUR_CHANNELS = (4, 64, 64, 64, 64, 64, 1)
+SUR_KERNEL = 9
+
+
+def surrogate_init(seed: int = 11) -> np.ndarray:
+    """Initial parameters of the surrogate network, packed layer by layer as
+    W_l [cout][cin][9] then b_l [cout] (FP32): He-normal weights for the ReLU layers
+    (std sqrt(2 / (cin 9))), std sqrt(1 / (cin 9)) for the linear output layer, zero
+    biases."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for l in range(len(SUR_CHANNELS) - 1):
+        cin, cout = SUR_CHANNELS[l], SUR_CHANNELS[l + 1]
+        gain = 2.0 if l < len(SUR_CHANNELS) - 2 else 1.0
+        parts.append(rng.normal(0.0, math.sqrt(gain / (cin * SUR_KERNEL)), cout * cin * SUR_KERNEL))
+        parts.append(np.zeros(cout))
+    return np.concatenate(parts).astype(np.float32)
+
+
+def surrogate_unpack(theta: np.ndarray) -> dict:
+    """{"W": [l][cout][cin][9], "b": [l][cout]} (float64) from the packed vector."""
+    W, b, off = [], [], 0
+    for l in range(len(SUR_CHANNELS) - 1):
+        cin, cout = SUR_CHANNELS[l], SUR_CHANNELS[l + 1]
+        n = cout * cin * SUR_KERNEL
+        W.append(np.asarray(theta[off:off + n], np.float64).reshape(cout, cin, SUR_KERNEL))
+        off += n
+        b.append(np.asarray(theta[off:off + cout], np.float64))
+        off += cout
+    return {"W": W, "b": b}
+
+
+def training_scene(seed: int) -> Scene:
+    """A randomised harbour scene for surrogate training: a corrugated sheet-pile wall
+    (standoff, pitch, flange, web and depth drawn per scene) over a mirror fBm seabed
+    (mean depth 9..12 m, std 0.05..0.3 m, 128 x 128 vertices over 30 x 30 m) with 0..60
+    boxes and cylinders; reflectivity U(0.1, 0.6) per triangle."""
+    rng = np.random.default_rng(seed)
+    x0 = rng.uniform(2.5, 9.0)
+    pitch = rng.uniform(0.35, 0.7)
+    flange = pitch * rng.uniform(0.2, 0.35)
+    web = pitch * rng.uniform(0.1, 0.25)
+    wv, wt = corrugated_wall(x0=x0, pitch=pitch, flange=flange, web=web, depth=rng.uniform(0.05, 0.2))
+    depth = rng.uniform(9.0, 12.0)
+    hf = fbm_heightfield(128, rng, sigma=rng.uniform(0.05, 0.3))
+    xs = np.linspace(-15.0, 15.0, 128)
+    sv, st = _grid_mesh(xs, xs, lambda X, Y: -depth + hf)
+    parts = [(wv, wt, 0.0, 0), (sv, st, 0.0, 1)]
+    for _ in range(int(rng.integers(0, 31))):
+        size = rng.uniform(0.1, 0.8, 3)
+        c = np.array([rng.uniform(-2.0, x0 - 0.5), rng.uniform(-10.0, 10.0), -depth + size[2] / 2])
+        v, t = _box(c, size, rng.uniform(0, math.pi))
+        parts.append((v, t, 0.0, 0))
+    for _ in range(int(rng.integers(0, 31))):
+        r, h = rng.uniform(0.05, 0.4), rng.uniform(0.2, 1.5)
+        c = np.array([rng.uniform(-2.0, x0 - 0.5), rng.uniform(-10.0, 10.0), -depth + h / 2])
+        v, t = _cylinder(c, r, h)
+        parts.append((v, t, 0.0, 0))
+    verts, tris, _, flags = _assemble(parts)
+    mu = rng.uniform(0.1, 0.6, size=len(tris)).astype(np.float32)
+    return Scene(verts, tris, mu, flags, planes=np.array([[0.0, 0.0, 1.0, -depth]]),
+                 meta={"wall_x": x0, "depth": depth})
+
+
+def training_poses(seed: int, n: int, scene: Scene) -> list:
+    """n seeded sonar poses in a training scene: 1.5..7 m in front of the wall's front
+    face, 1..6 m above the seabed's mean plane, heading within 30 degrees of the wall
+    normal, tilted 0..20 degrees down, rolled within 3 degrees."""
+    rng = np.random.default_rng(seed)
+    x_wall, depth = scene.meta["wall_x"], scene.meta["depth"]
+    out = []
+    for _ in range(n):
+        x = x_wall - rng.uniform(1.5, 7.0)
+        z = -depth + rng.uniform(1.0, 6.0)
+        out.append(pose((x, rng.uniform(-6.0, 6.0), z), yaw_deg=rng.uniform(-30.0, 30.0),
+                        tilt_down_deg=rng.uniform(0.0, 20.0), roll_deg=rng.uniform(-3.0, 3.0)))
+    return out

@@ -37,6 +37,8 @@ SONAR_OPT_RAW = 6
 SONAR_OPT_BVH = 7
 SONAR_OPT_CROSS = 8
 
+SONAR_SUR_N_PARAMS = 150657
+
 PRECISIONS = {"fp32": SONAR_FP32, "bf16": SONAR_BF16, "fp16": SONAR_FP16}
 
 
@@ -86,6 +88,12 @@ class sonar_stats(C.Structure):
                 ("ms_peaks", C.c_float)]
 
 
+class sonar_sur_metrics(C.Structure):
+    _fields_ = [("nl2", C.c_double), ("lit_beams", C.c_int64), ("peak_bin_mean", C.c_double),
+                ("peak_within_1", C.c_double), ("peak_within_4", C.c_double), ("cells", C.c_int64),
+                ("si", C.c_double), ("si_ref", C.c_double)]
+
+
 POINT_DTYPE = np.dtype([("x", "<f4"), ("y", "<f4"), ("z", "<f4"), ("intensity", "<f4"),
                         ("beam", "<i4"), ("bin", "<i4")])
 HIT_DTYPE = np.dtype([("key", "<u4"), ("prim", "<i4"), ("tau", "<f8"), ("amp", "<f4"), ("phi", "<f4"),
@@ -115,6 +123,19 @@ _SIGS = {
     "sonar_get_echoes": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
     "sonar_get_raw": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int64]),
     "sonar_get_stats": (C.c_int, [C.c_void_p, C.POINTER(sonar_stats)]),
+    "sonar_sur_set_weights": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_double]),
+    "sonar_sur_get_weights": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
+    "sonar_sur_render": (C.c_int, [C.c_void_p, C.POINTER(sonar_pose), C.c_int32, C.POINTER(sonar_params),
+                                   C.POINTER(sonar_ssp), C.c_void_p]),
+    "sonar_sur_ping": (C.c_int, [C.c_void_p, C.POINTER(sonar_pose), C.c_int32, C.POINTER(sonar_params),
+                                 C.POINTER(sonar_ssp), C.c_void_p]),
+    "sonar_sur_geometric": (C.c_int, [C.c_void_p, C.POINTER(sonar_pose), C.c_int32, C.POINTER(sonar_params),
+                                      C.POINTER(sonar_ssp), C.c_void_p]),
+    "sonar_sur_train_step": (C.c_int, [C.c_void_p, C.POINTER(sonar_pose), C.c_int32, C.POINTER(sonar_params),
+                                       C.POINTER(sonar_ssp), C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.c_int32,
+                                       C.POINTER(C.c_double), C.c_void_p]),
+    "sonar_sur_compare": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(sonar_params),
+                                    C.c_double, C.POINTER(sonar_sur_metrics)]),
     "sonar_cloud_noalloc": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(sonar_params), C.POINTER(sonar_pose),
                                       C.c_void_p, C.c_int64, C.POINTER(C.c_int64), C.c_void_p]),
 }
@@ -337,6 +358,74 @@ class Sonar:
         out = np.zeros((n_pings, params["n_range"], M, 2), np.float32)
         self._check(lib().sonar_get_raw(self.h, phase, out.ctypes.data, out.size))
         return out[..., 0] + 1j * out[..., 1]
+
+    # ------------------------------------------------------------ learned surrogate
+    def sur_set_weights(self, params, e_scale: float):
+        """Network parameters (SONAR_SUR_N_PARAMS floats) and output scale; resets Adam."""
+        a = np.ascontiguousarray(params, np.float32)
+        self._check(lib().sonar_sur_set_weights(self.h, a.ctypes.data, a.size, float(e_scale)))
+
+    def sur_get_weights(self) -> np.ndarray:
+        out = np.zeros(SONAR_SUR_N_PARAMS, np.float32)
+        self._check(lib().sonar_sur_get_weights(self.h, out.ctypes.data, out.size))
+        return out
+
+    def sur_render(self, poses, params: dict, ssp: dict) -> np.ndarray:
+        """Beam-centre geometric rendering: [P, beams, 8] (L, kappa, mu, Gamma of two hits)."""
+        P = len(poses)
+        nb = params["n_beam_az"] * params["n_beam_el"]
+        out = np.zeros((P, nb, 8), np.float32)
+        arr = (sonar_pose * P)(*[make_pose(p) for p in poses])
+        sp, ss = make_params(params), make_ssp(ssp)
+        self._check(lib().sonar_sur_render(self.h, arr, P, C.byref(sp), C.byref(ss), out.ctypes.data))
+        return out
+
+    def sur_ping(self, poses, params: dict, ssp: dict, env=None):
+        """The surrogate's envelope volumes [P, n_beam_el, n_beam_az, n_range] (device tensor)."""
+        torch = self.torch
+        P = len(poses)
+        if env is None:
+            env = torch.empty((P, params["n_beam_el"], params["n_beam_az"], params["n_range"]), dtype=torch.float32,
+                              device=f"cuda:{self.device}")
+        arr = (sonar_pose * P)(*[make_pose(p) for p in poses])
+        sp, ss = make_params(params), make_ssp(ssp)
+        self._check(lib().sonar_sur_ping(self.h, arr, P, C.byref(sp), C.byref(ss), _ptr(env)))
+        return env
+
+    def sur_geometric(self, poses, params: dict, ssp: dict, env=None):
+        """Envelope of the geometric rendering without the network (device tensor)."""
+        torch = self.torch
+        P = len(poses)
+        if env is None:
+            env = torch.empty((P, params["n_beam_el"], params["n_beam_az"], params["n_range"]), dtype=torch.float32,
+                              device=f"cuda:{self.device}")
+        arr = (sonar_pose * P)(*[make_pose(p) for p in poses])
+        sp, ss = make_params(params), make_ssp(ssp)
+        self._check(lib().sonar_sur_geometric(self.h, arr, P, C.byref(sp), C.byref(ss), _ptr(env)))
+        return env
+
+    def sur_train_step(self, poses, params: dict, ssp: dict, target, beams=None, lr: float = 1e-3,
+                       update: bool = True, want_grad: bool = False):
+        """One training step against device envelopes `target` of the same poses; beams: a
+        device int32 tensor of selected beam indices (None: all). Returns (loss, grad)."""
+        P = len(poses)
+        arr = (sonar_pose * P)(*[make_pose(p) for p in poses])
+        sp, ss = make_params(params), make_ssp(ssp)
+        loss = C.c_double()
+        grad = np.zeros(SONAR_SUR_N_PARAMS, np.float32) if want_grad else None
+        n_sel = 0 if beams is None else int(beams.numel())
+        self._check(lib().sonar_sur_train_step(self.h, arr, P, C.byref(sp), C.byref(ss), _ptr(target), _ptr(beams),
+                                               n_sel, float(lr), 1 if update else 0, C.byref(loss),
+                                               grad.ctypes.data if want_grad else None))
+        return loss.value, grad
+
+    def sur_compare(self, env, ref, params: dict, rel_thr: float = 0.1) -> dict:
+        """Metrics of envelope volumes env against ref (device tensors of the same shape)."""
+        m = sonar_sur_metrics()
+        P = int(env.shape[0]) if env.dim() == 4 else 1
+        sp = make_params(params)
+        self._check(lib().sonar_sur_compare(self.h, _ptr(env), _ptr(ref), P, C.byref(sp), float(rel_thr), C.byref(m)))
+        return {k: getattr(m, k) for k, _ in sonar_sur_metrics._fields_}
 
     def stats(self) -> dict:
         s = sonar_stats()
