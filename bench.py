@@ -514,7 +514,7 @@ def stage_rooflines(mean_stage, params, stats, precision, pk):
         "trace": {"bound": "latency (dependent BVH node loads)", "achieved": sub_rays / (mean_stage["trace"] / 1e3) / 1e6,
                   "unit": "M sub-rays/s", "hits_per_s": H / (mean_stage["trace"] / 1e3), "peak": None, "frac": None},
         "bin": mem("bin", 2 * 32 * H, "32-byte hit records read and written once"),
-        "synth": tensor("synth", synth_flop, synth_flop),
+        "synth": tensor("synth", synth_flop, stats.get("synth_mma_flop") or synth_flop),
         "convert": mem("convert", nr * M * (8 + (8 if precision == "fp32" else 4)),
                        "FP32 complex echoes read, 16-bit operand(s) written"),
         "beamform": tensor("beamform", gemm_flop, gemm_flop * n_pass),
@@ -587,6 +587,21 @@ def other_forms(torch, s, inputs, dev):
     out["c2_field_h0.5_fp32"] = {"value": 5 / (time.perf_counter() - t0), "unit": UNIT,
                                  "note": "range-dependent thermocline, RK4 rays at 0.5 m steps"}
     s.set_field(None)
+    # the two straight-ray traversals: per-stage events, ray casting time
+    from paper_2606_06130_gb300.sonar import SONAR_OPT_TIMING, SONAR_OPT_TRAVERSAL
+    trav = {}
+    s.set_option(SONAR_OPT_TIMING, 1)
+    for mode, name in ((0, "per_thread"), (1, "warp_cooperative")):
+        s.set_option(SONAR_OPT_TRAVERSAL, mode)
+        ms = []
+        for i in range(13):
+            s.ping(poses[0], params, ssp, precision="fp32")
+            if i >= 3:
+                ms.append(s.stats()["ms_trace"])
+        trav[name] = {"ms_trace_median": float(np.median(ms)), "ms_trace_min": float(np.min(ms))}
+    s.set_option(SONAR_OPT_TRAVERSAL, 0)
+    s.set_option(SONAR_OPT_TIMING, 0)
+    out["c2_traversal"] = dict(trav, note="straight-ray casting of the headline ping (524k sub-rays), stage events")
     out.update(surrogate_forms(torch, s, inputs, dev, scene, params, poses, ssp))
     sc4, p4, poses4, ssp4 = inputs.workload("c4")
     s.upload(sc4)
@@ -607,44 +622,60 @@ def other_forms(torch, s, inputs, dev):
     return out
 
 
-def surrogate_forms(torch, s, inputs, dev, scene, params, poses, ssp):
-    """Throughput of the learned surrogate on the headline ping (its rendering plus the
-    six-layer network over all 8192 beams x 1024 bins), of the geometric envelope it
-    starts from, and of its training step (1024 beams, forward, backward, Adam). The
-    network's weights do not change the work: the seeded initialisation is used."""
+def surrogate_forms(torch, s, inputs, dev, scene, params, poses, ssp, warmup=3, reps=10):
+    """Throughput of the learned surrogate's training step on the headline ping (1024
+    beams: rendering, forward, backward, Adam), of its inference (the rendering plus the
+    six-layer network over all 8192 beams x 1024 bins), and of the geometric envelope it
+    starts from. The network's weights do not change the work: the seeded initialisation
+    is used."""
     out = {}
     nb = params["n_beam_az"] * params["n_beam_el"]
     s.sur_set_weights(inputs.surrogate_init(1), 0.05)
+    target, _, _ = s.ping_batch(poses, params, ssp, cloud_cap=0)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(3)
+    beams = torch.randint(0, nb, (1024,), generator=gen, device=dev, dtype=torch.int32)
+    for _ in range(warmup):
+        s.sur_train_step(poses, params, ssp, target, beams, lr=1e-4)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(2 * reps):
+        s.sur_train_step(poses, params, ssp, target, beams, lr=1e-4)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / (2 * reps)
+    out["c2_surrogate_train_step"] = {"value": 1.0 / dt, "unit": "steps/s", "beams_per_step": 1024,
+                                      "positions_per_s": 1024 * params["n_range"] / dt}
     env = torch.empty((1, params["n_beam_el"], params["n_beam_az"], params["n_range"]), dtype=torch.float32, device=dev)
     for name, call in (("c2_surrogate_bf16", lambda: s.sur_ping(poses, params, ssp, env=env)),
                        ("c2_geometric", lambda: s.sur_geometric(poses, params, ssp, env=env))):
-        for _ in range(3):
+        for _ in range(warmup):
             call()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        reps = 10
         for _ in range(reps):
             call()
         torch.cuda.synchronize()
         out[name] = {"value": reps / (time.perf_counter() - t0), "unit": UNIT}
     out["c2_surrogate_bf16"]["note"] = ("beam-centre rendering + 6-layer conv net (4 hidden layers on tcgen05), "
                                         "8192 beams x 1024 bins, BF16 weights and activations, FP32 accumulation")
-    target, _, _ = s.ping_batch(poses, params, ssp, cloud_cap=0)
-    gen = torch.Generator(device=dev)
-    gen.manual_seed(3)
-    beams = torch.randint(0, nb, (1024,), generator=gen, device=dev, dtype=torch.int32)
-    for _ in range(3):
-        s.sur_train_step(poses, params, ssp, target, beams, lr=1e-4)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    reps = 20
-    for _ in range(reps):
-        s.sur_train_step(poses, params, ssp, target, beams, lr=1e-4)
-    torch.cuda.synchronize()
-    dt = (time.perf_counter() - t0) / reps
-    out["c2_surrogate_train_step"] = {"value": 1.0 / dt, "unit": "steps/s", "beams_per_step": 1024,
-                                      "positions_per_s": 1024 * params["n_range"] / dt}
     return out
+
+
+def run_surrogate_forms(args):
+    """--surrogate-forms: only the learned surrogate's forms on the headline ping (the
+    profiling command of its kernels); --steps sets the timed repetitions."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2606_06130_gb300 import inputs
+    from paper_2606_06130_gb300.sonar import Sonar
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    scene, params, poses, ssp = inputs.workload("c2")
+    s = Sonar(0)
+    s.upload(scene)
+    out = surrogate_forms(torch, s, inputs, dev, scene, params, poses, ssp, warmup=args.warmup, reps=args.steps)
+    print(json.dumps({"surrogate_forms": out}), flush=True)
 
 
 def cpu_model() -> str:
@@ -757,9 +788,14 @@ def main():
     ap.add_argument("--surrogate-train", type=int, default=0,
                     help="train the learned surrogate on this many plain-method pings and evaluate it on 64 "
                          "held-out pings (one JSON line; not part of the default run)")
+    ap.add_argument("--surrogate-forms", action="store_true",
+                    help="time only the learned surrogate's forms (training step, inference, geometric envelope)")
     args = ap.parse_args()
     if args.surrogate_train > 0:
         run_surrogate_training(args)
+        return
+    if args.surrogate_forms:
+        run_surrogate_forms(args)
         return
     if args.cross or args.volume > 0 or args.field > 0:
         args.no_oracle = True  # the oracle legs sample the default workload

@@ -133,6 +133,14 @@ typedef struct {
      only with SONAR_OPT_TIMING): ray casting, binning, synthesis, operand conversion,
      beamforming GEMM, peak extraction */
   float ms_trace, ms_bin, ms_synth, ms_convert, ms_beamform, ms_peaks;
+  /* tiles of the last synchronous call: beamforming N tile, synthesis tile width in
+     complex columns (0: the kernel's default or a kernel without tile widths), and 1
+     when the autotuner chose them */
+  int32_t tile_n, synth_cols, autotuned;
+  /* tensor flops the z-split synthesis kernel's MMAs executed in the last synchronous
+     call (2 M N K per MMA, every product of the FP32 form counted; 0 for the other
+     synthesis kernels) */
+  double synth_mma_flop;
 } sonar_stats;
 
 /* ---------------------------------------------------------------- context */
@@ -197,6 +205,21 @@ SONAR_API const char* sonar_last_error(const sonar_ctx* ctx);
    Isovelocity profiles only (SONAR_E_UNSUPPORTED at the ping with a gradient);
    at most 2^27 sub-rays and 16384 point scatterers. Any other value: SONAR_E_ARG. */
 #define SONAR_OPT_CROSS 8
+/* SONAR_OPT_AUTOTUNE: 1 (default) lets the first synchronous call of each shape (ping
+   count, range and beam grids, array, precision, raw phases, pulse and range extent) time
+   the beamforming N tiles 256, 224, 192 and 128 and, for arrays the z-split synthesis
+   serves, its tile widths 96, 64 and 32 complex columns on this device (per-stage events,
+   the best of three runs of the call's own pings), and keeps the fastest of each for
+   every later call of that shape (an asynchronous call of a new shape first makes one
+   synchronous call). Only choices left to the library are tuned: SONAR_OPT_TILE_N and
+   SONAR_OPT_SYNTH, when set, win. 0: the closed-form tile heuristic. */
+#define SONAR_OPT_AUTOTUNE 9
+/* SONAR_OPT_TRAVERSAL: how straight rays (isovelocity, no cross terms) traverse the
+   hierarchy. 0 (default): one sub-ray per thread, each with its own stack. 1:
+   warp-cooperative: the 32 sub-rays of a warp walk one shared stack in lockstep, a node
+   visited when any lane's ray overlaps it. Both give the same hits. Any other value:
+   SONAR_E_ARG. */
+#define SONAR_OPT_TRAVERSAL 10
 SONAR_API int sonar_set_option(sonar_ctx* ctx, int32_t option, int64_t value);
 
 /* ---------------------------------------------------------------- scene */

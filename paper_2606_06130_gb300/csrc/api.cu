@@ -39,7 +39,8 @@ __global__ void k_clear(float2* S, int64_t n_s, float2* S2, int64_t n_s2, int32_
   for (int64_t i = t; i < n_keys; i += stride) keys[i] = 0ull;
   for (int64_t i = t; i < n_p; i += stride) pmax[i] = 0u;
   if (t == 0) {
-    *n_hits = 0ull;
+    n_hits[0] = 0ull;  // hit count
+    n_hits[1] = 0ull;  // synthesis tensor flops
     *err = 0;
   }
 }
@@ -83,7 +84,7 @@ struct AsyncSlot {
   DevPose* pose_map = nullptr;
   long long* n_cloud_host = nullptr;          // pinned [p_cap], mapped
   long long* n_cloud_map = nullptr;
-  unsigned long long* counters_host = nullptr;  // pinned [2]: hit count, error bits; mapped
+  unsigned long long* counters_host = nullptr;  // pinned [3]: hit count, error bits, synthesis flops; mapped
   unsigned long long* counters_map = nullptr;
   int p_cap = 0;
   float* env_stage = nullptr;
@@ -111,9 +112,21 @@ struct sonar_ctx {
   std::string err;
   bool debug = false, timing = false, use_graph = true;
   int tile_opt = 0;
+  // autotuner: per (pings, grid, array, precision, raw phases, pulse) the beamforming N
+  // tile and the synthesis tile width measured fastest on this device at the first call
+  int autotune = 1;
+  struct TuneEntry {
+    std::vector<uint8_t> key;
+    int tile_n = 0, pairs = 0;
+    float ms_gemm = 0.f, ms_synth = 0.f;
+  };
+  std::vector<TuneEntry> tuned;
+  int cur_tile_n = 0, cur_pairs = 0;  // the choice in force for the current call (0: heuristic)
+  bool cur_tuned = false;
   int raw_u = 0;      // 0: compressed synthesis; U > 0: raw series at U samples per cell + matched filter
   int bvh_opt = 0;    // 0: binned-SAH hierarchy (host build), 1: Morton-order LBVH (device build)
   int cross = 0;      // 1: out/back cross-term multipath
+  int traversal = 0;  // straight rays: 0 one sub-ray per thread, 1 warp-cooperative
   int64_t vol_n = 0;  // water-column scatterers per ping
   sonar_field fld{};  // range-dependent sound speed (fld.nx = 0: none); c points to fld_c
   double* fld_c = nullptr;  // device copy of the grid
@@ -386,8 +399,9 @@ int derive(sonar_ctx* ctx, const sonar_params* p, const sonar_ssp* ssp, double x
   d.M = p->nx * p->ny;
   d.k_pad = (int)round_up(2LL * d.M, 64);
   d.nb = p->n_beam_az * p->n_beam_el;
-  d.tile_n = ctx->tile_opt != 0 ? ctx->tile_opt
-                                 : pick_tile_n((int64_t)n_pings * d.nr_x / 128, d.nb, ctx->sm_count);
+  d.tile_n = ctx->tile_opt != 0   ? ctx->tile_opt
+             : ctx->cur_tile_n != 0 ? ctx->cur_tile_n
+                                    : pick_tile_n((int64_t)n_pings * d.nr_x / 128, d.nb, ctx->sm_count);
   d.nb_pad = (int)round_up(d.nb, d.tile_n / 2);
   d.n_phase = p->precision == SONAR_FP32 ? 3 : 1;
   d.n_blank = 0;
@@ -618,7 +632,7 @@ int ensure_workspace(sonar_ctx* ctx, int P, const Derived& d) {
     CU(cudaMalloc(&ctx->n_cloud_dev, sizeof(long long) * P));
     ctx->p_cap = P;
   }
-  if (!ctx->n_hits) CU(cudaMalloc(&ctx->n_hits, sizeof(unsigned long long)));
+  if (!ctx->n_hits) CU(cudaMalloc(&ctx->n_hits, 2 * sizeof(unsigned long long)));
   if (!ctx->err_dev) CU(cudaMalloc(&ctx->err_dev, sizeof(int)));
   if (!ctx->synth_bounds) CU(cudaMalloc(&ctx->synth_bounds, sizeof(int32_t) * (ctx->sm_count + 1)));
   int64_t hit_need = (int64_t)P * d.hit_cap_per_ping;
@@ -765,6 +779,7 @@ TraceArgs trace_args(const sonar_ctx* ctx, int P, const sonar_params* p, const D
   ta.nr_pad = d.nr_pad;
   ta.n_routes = d.n_routes;
   ta.cross = ctx->cross;
+  ta.warp_walk = ctx->traversal;
   ta.pt_route = pairs ? ctx->pt_route : nullptr;
   ta.vol_n = ctx->vol_n;
   for (int k = 0; k < 3; ++k) {
@@ -844,11 +859,13 @@ int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, cons
   sa.S = ctx->S;
   sa.total_rows = (int64_t)P * d.nr_pad;
   sa.n_pass = p->precision == SONAR_FP32 ? 3 : 1;
+  sa.mma_flop = ctx->n_hits + 1;
   sa.err = ctx->err_dev;
   static const int kPairs[5] = {0, 0, 32, 64, 96};
   const bool tc = ctx->synth_opt != 1 && synth_tc_supported(p->nx, p->ny, d.taps);
+  const int want_pairs = ctx->synth_opt >= 2 ? kPairs[ctx->synth_opt] : ctx->cur_pairs;
   if (ctx->raw_u == 0) {
-    if (tc) CU(launch_synth_tc(sa, kPairs[ctx->synth_opt], ctx->sm_count, st));
+    if (tc) CU(launch_synth_tc(sa, want_pairs, ctx->sm_count, st));
     else CU(launch_synth(sa, ctx->sm_count, st));
   } else {
     // raw series: one synthesis pass per phase s with the pulse shifted by s dt / U in
@@ -860,7 +877,7 @@ int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, cons
       sr.rtab = ctx->ptab + (int64_t)s * (kRTab + 1);
       sr.rtab_s = ctx->ptab + (int64_t)U * (kRTab + 1) + (int64_t)s * (kRTabS + 5);
       sr.S = ctx->S_raw + (int64_t)s * ctx->s_elems;
-      if (tc) CU(launch_synth_tc(sr, kPairs[ctx->synth_opt], ctx->sm_count, st));
+      if (tc) CU(launch_synth_tc(sr, want_pairs, ctx->sm_count, st));
       else CU(launch_synth(sr, ctx->sm_count, st));
     }
     MfArgs ma;
@@ -1031,6 +1048,7 @@ std::vector<uint8_t> pipeline_key(const sonar_ctx* ctx, int P, const sonar_param
   key_add(k, ctx->debug); key_add(k, ctx->timing); key_add(k, ctx->synth_opt); key_add(k, ctx->scene_version);
   key_add(k, ctx->raw_u);
   key_add(k, d.c_ref);
+  key_add(k, d.tile_n); key_add(k, ctx->cur_pairs);
   if (ssp) {
     key_add(k, ssp->n_nodes);
     for (int i = 0; i < ssp->n_nodes; ++i) { key_add(k, ssp->c[i]); if (ssp->z) key_add(k, ssp->z[i]); }
@@ -1038,6 +1056,103 @@ std::vector<uint8_t> pipeline_key(const sonar_ctx* ctx, int P, const sonar_param
   key_add(k, ctx->vol_order);
   key_add(k, ctx->hits); key_add(k, ctx->S); key_add(k, ctx->x_hi); key_add(k, ctx->y_hi); key_add(k, ctx->keys);
   return k;
+}
+
+// ------------------------------------------------------------------ autotuner
+// The choices the tuner owns are those the caller left to the library (SONAR_OPT_TILE_N
+// and SONAR_OPT_SYNTH at 0); they are keyed by what changes the best tile: the ping
+// count, the range and beam grids, the array, the precision, the raw phases and the
+// pulse and range extent (taps per hit).
+std::vector<uint8_t> tune_key(const sonar_ctx* ctx, int P, const sonar_params* p) {
+  std::vector<uint8_t> k;
+  key_add(k, P); key_add(k, p->n_range); key_add(k, p->n_beam_az); key_add(k, p->n_beam_el);
+  key_add(k, p->nx); key_add(k, p->ny); key_add(k, p->precision); key_add(k, ctx->raw_u);
+  key_add(k, p->pulse_s); key_add(k, p->r_max_m - p->r_min_m); key_add(k, ctx->tile_opt); key_add(k, ctx->synth_opt);
+  return k;
+}
+
+// Sets the current call's tile choices from the cache; false when the key was not tuned.
+bool tune_lookup(sonar_ctx* ctx, const std::vector<uint8_t>& key) {
+  ctx->cur_tile_n = 0;
+  ctx->cur_pairs = 0;
+  ctx->cur_tuned = false;
+  if (!ctx->autotune) return true;
+  for (const auto& e : ctx->tuned)
+    if (e.key == key) {
+      ctx->cur_tile_n = e.tile_n;
+      ctx->cur_pairs = e.pairs;
+      ctx->cur_tuned = true;
+      return true;
+    }
+  return false;
+}
+
+// Times the pipeline eagerly with per-stage events, min of three after one warm-up:
+// the beamforming GEMM at each N tile, then the synthesis at each tile width (with the
+// best N), and keeps the fastest of each. The runs compute the call's own pings into
+// its own outputs, so they leave valid results behind.
+int autotune(sonar_ctx* ctx, int P, const sonar_params* p, const sonar_ssp* ssp, double xs, double zs,
+             const Outputs& o, const std::vector<uint8_t>& key) {
+  const bool saved_timing = ctx->timing;
+  ctx->timing = true;
+  int rc = SONAR_OK;
+  auto measure = [&](float* ms_synth, float* ms_gemm) -> int {
+    Derived d;
+    int r;
+    if ((r = derive(ctx, p, ssp, xs, zs, P, d))) return r;
+    if ((r = ensure_tables(ctx, p, d))) return r;
+    if ((r = ensure_workspace(ctx, P, d))) return r;
+    float bs = 1e30f, bg = 1e30f;
+    for (int rep = 0; rep < 4; ++rep) {
+      int kernels = 0;
+      if ((r = enqueue(ctx, P, p, d, o, &kernels))) return r;
+      CU(cudaStreamSynchronize(ctx->stream));
+      if (rep == 0) continue;
+      float ts = 0.f, tg = 0.f;
+      CU(cudaEventElapsedTime(&ts, ctx->stage_ev[2], ctx->stage_ev[3]));
+      CU(cudaEventElapsedTime(&tg, ctx->stage_ev[4], ctx->stage_ev[5]));
+      bs = fminf(bs, ts);
+      bg = fminf(bg, tg);
+    }
+    *ms_synth = bs;
+    *ms_gemm = bg;
+    return SONAR_OK;
+  };
+  sonar_ctx::TuneEntry e;
+  e.key = key;
+  float best_g = 1e30f, best_s = 1e30f, ms_s = 0.f, ms_g = 0.f;
+  int best_n = 0, best_p = 0;
+  if (ctx->tile_opt == 0) {
+    for (int bn : {256, 224, 192, 128}) {
+      ctx->cur_tile_n = bn;
+      if ((rc = measure(&ms_s, &ms_g))) break;
+      if (ms_g < best_g) { best_g = ms_g; best_n = bn; }
+    }
+  }
+  ctx->cur_tile_n = best_n;
+  Derived d0;
+  if (!rc && (rc = derive(ctx, p, ssp, xs, zs, P, d0)) == SONAR_OK && ctx->synth_opt == 0 &&
+      synth_tz_applies(p->nx, p->ny, d0.taps)) {
+    for (int np : {96, 64, 32}) {
+      ctx->cur_pairs = np;
+      if ((rc = measure(&ms_s, &ms_g))) break;
+      if (ms_s < best_s) { best_s = ms_s; best_p = np; }
+    }
+  }
+  ctx->timing = saved_timing;
+  if (rc) {
+    ctx->cur_tile_n = ctx->cur_pairs = 0;
+    return rc;
+  }
+  e.tile_n = best_n;
+  e.pairs = best_p;
+  e.ms_gemm = best_g;
+  e.ms_synth = best_s;
+  ctx->tuned.push_back(e);
+  ctx->cur_tile_n = best_n;
+  ctx->cur_pairs = best_p;
+  ctx->cur_tuned = true;
+  return SONAR_OK;
 }
 
 int run(sonar_ctx* ctx, const sonar_pose* poses, int P, const sonar_params* p, const sonar_ssp* ssp, float* env,
@@ -1052,6 +1167,8 @@ int run(sonar_ctx* ctx, const sonar_pose* poses, int P, const sonar_params* p, c
   // the work stream starts after everything already queued on the caller's stream
   CU(cudaEventRecord(ctx->ev_in, ctx->user_stream));
   CU(cudaStreamWaitEvent(ctx->stream, ctx->ev_in, 0));
+  const std::vector<uint8_t> tkey = tune_key(ctx, P, p);
+  const bool tuned = tune_lookup(ctx, tkey);
   Derived d;
   if ((rc = derive(ctx, p, ssp, poses[0].t[0], poses[0].t[2], P, d))) return rc;
   if ((int64_t)P * d.nr_pad + 1 > (1LL << 31) - 1) return fail(ctx, SONAR_E_UNSUPPORTED, "batch too large");
@@ -1084,7 +1201,7 @@ int run(sonar_ctx* ctx, const sonar_pose* poses, int P, const sonar_params* p, c
     o.cloud_host = cloud;
   }
   if (!ctx->counters_host) {
-    CU(cudaMallocHost(&ctx->counters_host, 2 * sizeof(unsigned long long)));
+    CU(cudaMallocHost(&ctx->counters_host, 3 * sizeof(unsigned long long)));
     CU(cudaHostGetDevicePointer((void**)&ctx->counters_map, ctx->counters_host, 0));
   }
   ctx->counters_host[1] = 0;
@@ -1094,6 +1211,15 @@ int run(sonar_ctx* ctx, const sonar_pose* poses, int P, const sonar_params* p, c
 
   // the graph's first node copies these to the device
   for (int i = 0; i < P; ++i) ctx->pose_host[i] = dev_pose(poses[i]);
+
+  // first call of this shape: the autotuner times the candidate tiles, then the call
+  // proceeds with the winners
+  if (!tuned) {
+    if ((rc = autotune(ctx, P, p, ssp, poses[0].t[0], poses[0].t[2], o, tkey))) return rc;
+    if ((rc = derive(ctx, p, ssp, poses[0].t[0], poses[0].t[2], P, d))) return rc;
+    if ((rc = ensure_tables(ctx, p, d))) return rc;
+    if ((rc = ensure_workspace(ctx, P, d))) return rc;
+  }
 
   const bool timed = ctx->timing;
   int kernels = 0;
@@ -1147,6 +1273,11 @@ int run(sonar_ctx* ctx, const sonar_pose* poses, int P, const sonar_params* p, c
   ctx->stats.n_pings = P;
   ctx->stats.taps = d.taps;
   ctx->stats.kernels = kernels;
+  ctx->stats.synth_mma_flop = (double)ctx->counters_host[2];
+  ctx->stats.tile_n = d.tile_n;
+  static const int32_t kCols[5] = {0, 0, 32, 64, 96};
+  ctx->stats.synth_cols = ctx->synth_opt >= 2 ? kCols[ctx->synth_opt] : ctx->cur_pairs;
+  ctx->stats.autotuned = ctx->cur_tuned ? 1 : 0;
   if (timed) {
     float t[6];
     for (int i = 0; i < 6; ++i) CU(cudaEventElapsedTime(&t[i], ctx->stage_ev[i], ctx->stage_ev[i + 1]));
@@ -1179,6 +1310,11 @@ int run_async(sonar_ctx* ctx, const sonar_pose* poses, int P, const sonar_params
   const Mem cloud_kind = cloud_cap == 0 ? Mem::Device : classify(cloud, &cloud_d);
   if (env_kind == Mem::Host || cloud_kind == Mem::Host)
     return fail(ctx, SONAR_E_ARG, "asynchronous pings need device or pinned host outputs");
+  // first call of this shape: tuned by one synchronous call (into these outputs)
+  if (!tune_lookup(ctx, tune_key(ctx, P, p))) {
+    if ((rc = run(ctx, poses, P, p, ssp, env, cloud, cloud_cap, nullptr))) return rc;
+    if (!tune_lookup(ctx, tune_key(ctx, P, p))) return fail(ctx, SONAR_E_CUDA, "autotuner left no entry");
+  }
   const int s = ctx->next_slot;
   AsyncSlot& sl = ctx->aslot[s];
   const int rc_prev = retire(ctx, sl);
@@ -1203,7 +1339,7 @@ int run_async(sonar_ctx* ctx, const sonar_pose* poses, int P, const sonar_params
     sl.p_cap = P;
   }
   if (!sl.counters_host) {
-    CU(cudaMallocHost(&sl.counters_host, 2 * sizeof(unsigned long long)));
+    CU(cudaMallocHost(&sl.counters_host, 3 * sizeof(unsigned long long)));
     CU(cudaHostGetDevicePointer((void**)&sl.counters_map, sl.counters_host, 0));
   }
   if (!sl.ev_done) {
@@ -1288,8 +1424,9 @@ int sur_alloc_params(sonar_ctx* ctx) {
   if (S.params) return SONAR_OK;
   CU(cudaMalloc(&S.params, sizeof(float) * 4 * kSurParams));
   CU(cudaMemset(S.params, 0, sizeof(float) * 4 * kSurParams));
-  const int64_t wn = 4LL * kSurK * kSurC * kSurC;
+  const int64_t wn = 4LL * (kSurK + 1) * kSurC * kSurC;  // tap 9 of every layer stays zero
   CU(cudaMalloc(&S.wbf, sizeof(__nv_bfloat16) * 2 * wn));
+  CU(cudaMemset(S.wbf, 0, sizeof(__nv_bfloat16) * 2 * wn));
   CU(cudaMalloc(&S.wsmall, sizeof(float) * (kSurC * 4 * kSurK + kSurC * kSurK)));
   CU(cudaMalloc(&S.loss, sizeof(double)));
   S.net.theta = S.params;
@@ -1375,13 +1512,13 @@ int sur_forward(sonar_ctx* ctx, const float* feat, const int32_t* beams, int64_t
     SurConvArgs ca;
     memset(&ca, 0, sizeof(ca));
     if ((rc = make_map(ctx, &ca.map_x, sur_buf(ctx, L - 1), n_sel * rb, kSurC, 128 + kSurK - 1, false))) return rc;
-    if ((rc = make_map(ctx, &ca.map_w, S.net.wf + (int64_t)(L - 1) * kSurK * kSurC * kSurC, kSurK * kSurC, kSurC,
-                       kSurC, false)))
+    if ((rc = make_map(ctx, &ca.map_w, S.net.wf + (int64_t)(L - 1) * (kSurK + 1) * kSurC * kSurC,
+                       (kSurK + 1) * kSurC, kSurC, kSurC, false)))
       return rc;
     ca.bias = S.net.theta + sur_boff(L);
     ca.out = sur_buf(ctx, L);
-    ca.n_tiles = n_sel * (d.nr / 128);
-    ca.tiles_per_beam = d.nr / 128;
+    ca.n_rows = n_sel * rb;
+    ca.n_tiles = (ca.n_rows + 126) / 127;
     ca.rb = rb;
     ca.err = ctx->err_dev;
     CU(sur_conv(ca, false, ctx->sm_count, st));
@@ -1418,13 +1555,13 @@ int sur_backward(sonar_ctx* ctx, const float* feat, const int32_t* beams, int64_
     SurConvArgs ca;
     memset(&ca, 0, sizeof(ca));
     if ((rc = make_map(ctx, &ca.map_x, sur_buf(ctx, dz), n_sel * rb, kSurC, 128 + kSurK - 1, false))) return rc;
-    if ((rc = make_map(ctx, &ca.map_w, S.net.wb + (int64_t)(L - 1) * kSurK * kSurC * kSurC, kSurK * kSurC, kSurC,
-                       kSurC, false)))
+    if ((rc = make_map(ctx, &ca.map_w, S.net.wb + (int64_t)(L - 1) * (kSurK + 1) * kSurC * kSurC,
+                       (kSurK + 1) * kSurC, kSurC, kSurC, false)))
       return rc;
     ca.mask = sur_buf(ctx, L - 1);
     ca.out = sur_buf(ctx, 11 - dz);  // the other gradient buffer
-    ca.n_tiles = n_sel * (d.nr / 128);
-    ca.tiles_per_beam = d.nr / 128;
+    ca.n_rows = n_sel * rb;
+    ca.n_tiles = (ca.n_rows + 126) / 127;
     ca.rb = rb;
     ca.err = ctx->err_dev;
     CU(sur_conv(ca, true, ctx->sm_count, st));
@@ -1511,6 +1648,15 @@ int sonar_set_option(sonar_ctx* ctx, int32_t option, int64_t value) {
     case SONAR_OPT_BVH:
       if (value != 0 && value != 1) return fail(ctx, SONAR_E_ARG, "BVH build: 0 (SAH) or 1 (Morton order)");
       ctx->bvh_opt = (int)value;
+      break;
+    case SONAR_OPT_TRAVERSAL:
+      if (value != 0 && value != 1) return fail(ctx, SONAR_E_ARG, "traversal: 0 (per thread) or 1 (per warp)");
+      ctx->traversal = (int)value;
+      drop_graphs(ctx);
+      break;
+    case SONAR_OPT_AUTOTUNE:
+      if (value != 0 && value != 1) return fail(ctx, SONAR_E_ARG, "autotune: 0 (off) or 1 (on)");
+      ctx->autotune = (int)value;
       break;
     case SONAR_OPT_CROSS:
       if (value != 0 && value != 1) return fail(ctx, SONAR_E_ARG, "cross terms: 0 (off) or 1 (on)");

@@ -388,8 +388,9 @@ __global__ void __launch_bounds__(1024) k_peaks(PeakArgs a) {
   }
   // every earlier kernel of the call has completed (the dependent-launch chain)
   if (p == 0 && chunk == 0 && t == 0) {
-    a.counters_host[0] = *a.n_hits;
+    a.counters_host[0] = a.n_hits[0];
     a.counters_host[1] = (unsigned long long)(unsigned)*a.err;
+    a.counters_host[2] = a.n_hits[1];
   }
 }
 

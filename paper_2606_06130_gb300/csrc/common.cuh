@@ -115,6 +115,7 @@ struct TraceArgs {
   int32_t nr_pad;
   int32_t n_routes;              // point-scatterer routes per point
   int32_t cross;                 // 1: out/back cross-term multipath
+  int32_t warp_walk;             // 1: straight rays traverse warp-cooperatively (k_trace_warp)
   PtRoute* pt_route;             // [n_pings][n_points][n_routes] with cross terms, else null
   int64_t vol_n;                 // water-column scatterers per ping (0: none)
   double vol_lo[3], vol_hi[3];   // their world-frame box
@@ -213,6 +214,7 @@ struct SynthArgs {
   float2* S;                // [n_pings * nr_pad][M] element echoes
   int64_t total_rows;       // n_pings * nr_pad
   int32_t n_pass;           // tensor-core synthesis: 3 (BF16 hi/lo split) or 1
+  unsigned long long* mma_flop;  // z-split kernel: tensor flops its MMAs execute (added per CTA), or null
   int* err;
 };
 // Counting sort of the hits by first-tap row; counts[] holds the per-row histogram (the
@@ -222,6 +224,8 @@ cudaError_t launch_bin(const HitRec* hits, const unsigned long long* n_hits, int
                        int bounds_g, int row_cost, cudaStream_t st);
 cudaError_t launch_synth(const SynthArgs& a, int sm_count, cudaStream_t st);
 bool synth_tc_supported(int nx, int ny, int taps);
+// True when the z-split tensor-core kernel (tile widths 32, 64, 96) serves the array.
+bool synth_tz_applies(int nx, int ny, int taps);
 cudaError_t prepare_synth_tc();
 // want_pairs: complex columns per z-split tile (32, 64, 96) when that shape fits; 0 (or
 // a shape that does not fit) takes the default choice.
@@ -251,8 +255,8 @@ struct SurNet {
   float* m;             // Adam first moment
   float* v;             // Adam second moment
   float* grad;          // [kSurParams]
-  __nv_bfloat16* wf;    // hidden layers 1..4: [4][9][64 cout][64 cin], forward B operands
-  __nv_bfloat16* wb;    // [4][9][64 cin][64 cout], taps reversed: backward-data B operands
+  __nv_bfloat16* wf;    // hidden layers 1..4: [4][10][64 cout][64 cin], forward B operands (tap 9 zero)
+  __nv_bfloat16* wb;    // [4][10][64 cin][64 cout], taps reversed: backward-data B operands (tap 9 zero)
   float* w_in;          // layer 0: [64][4][9]
   float* w_out;         // layer 5: [64][9]
 };
@@ -265,13 +269,14 @@ cudaError_t sur_pack(const SurNet& n, int update, float lr, float b1, float b2, 
 cudaError_t sur_input(const float* feat, const int32_t* beams, int64_t n_sel, int64_t n_feat, int nr, double r_min,
                       double inv_dr, const SurNet& n, __nv_bfloat16* act1, int rb, int* err, cudaStream_t st);
 struct SurConvArgs {
-  CUtensorMap map_x;              // input rows [n_sel * rb][64] BF16, box 64 x 136
-  CUtensorMap map_w;              // B operands [9 * 64][64] BF16, box 64 x 64
+  CUtensorMap map_x;              // input rows [n_rows][64] BF16, box 64 x 136
+  CUtensorMap map_w;              // B operands [10 * 64][64] BF16, box 64 x 64
   const float* bias;              // forward: [64]
   const __nv_bfloat16* mask;      // backward-data: the gradient passes where these are > 0
   __nv_bfloat16* out;
-  int64_t n_tiles;
-  int tiles_per_beam, rb;
+  int64_t n_tiles;                // ceil(n_rows / 127)
+  int64_t n_rows;                 // n_sel * rb
+  int rb;
   int* err;
 };
 // Hidden 64 -> 64 layer on the tensor cores: forward (bias, ReLU) or backward-data.
@@ -376,8 +381,8 @@ struct PeakArgs {
   // the call's results for the host, written through the device mapping of pinned host
   // words (no copy after the kernel): points per ping, then hit count and error bits
   long long* n_cloud_host;
-  unsigned long long* counters_host;   // [2]
-  const unsigned long long* n_hits;
+  unsigned long long* counters_host;   // [3]: hit count, error bits, synthesis tensor flops
+  const unsigned long long* n_hits;    // [2]: hit count, synthesis tensor flops
   const int* err;
 };
 cudaError_t launch_peaks(const PeakArgs& a, cudaStream_t st);

@@ -15,12 +15,12 @@
 //  - k_sur_input: layer 0 from the rendering. The input is sparse (two hits per beam,
 //    each splatted onto two bins), so each position sums the few taps that touch it.
 //  - k_conv<MODE>: a hidden 64 -> 64 layer as an implicit GEMM on tcgen05. M = 128
-//    positions, N = 64 output channels, K = 9 taps x 64 input channels. The 136 input
-//    rows a tile needs are staged once by TMA (128-byte swizzle); tap k reads them
-//    through a matrix descriptor that starts k rows later (36 MMAs of K = 16 per tile).
-//    The weights of all taps stay in shared memory. MODE 0 is the forward layer (bias,
-//    ReLU); MODE 1 the backward-data pass (the transposed, tap-reversed weights, and the
-//    previous layer's ReLU mask).
+//    rows, N = 128 = two taps x 64 output channels, K = 64 input channels per tap pair.
+//    The 136 input rows a tile needs are staged once by TMA (128-byte swizzle); tap pair
+//    j reads them through a matrix descriptor that starts 2j rows later (20 MMAs of
+//    K = 16 per tile of 127 output rows). The weights of all taps stay in shared memory.
+//    MODE 0 is the forward layer (bias, ReLU); MODE 1 the backward-data pass (the
+//    transposed, tap-reversed weights, and the previous layer's ReLU mask).
 //  - k_dw: a hidden layer's weight gradient dW_k[o][c] = sum_p dz[p][o] x[p + k - 4][c]
 //    on tcgen05. M = 128 = (tap parity, output channel): tensor memory holds the dz
 //    window as the A operand, rows 64..127 shifted one position, so one MMA makes two
@@ -115,42 +115,41 @@ __global__ void k_sur_pack(SurNet n, int update, float lr, float b1, float b2, f
     n.w_out[ci * KT + k] = __bfloat162float(h);
   } else {
     const int L = l - 1;
-    n.wf[((int64_t)(L * KT + k) * C + co) * C + ci] = h;
-    n.wb[((int64_t)(L * KT + (KT - 1 - k)) * C + ci) * C + co] = h;
+    n.wf[((int64_t)(L * (KT + 1) + k) * C + co) * C + ci] = h;
+    n.wb[((int64_t)(L * (KT + 1) + (KT - 1 - k)) * C + ci) * C + co] = h;
   }
 }
 
 // ----------------------------------------------------------------- layer 0
-// One thread per (selected beam, bin). A hit at one-way length L sits at bin coordinate
+// One thread per (selected beam, bin, group of 8 channels): a warp writes four whole
+// 128-byte rows per store. A hit at one-way length L sits at bin coordinate
 // x = (L - r_min) / dr - 1/2 and splats 1 - f, f onto bins floor(x), floor(x) + 1.
 // Channels: 0 first-hit splat, 1 second-hit splat, 2 incidence cosine, 3 reflectivity
-// (both hits, as their splats' amplitudes).
-__global__ void __launch_bounds__(128) k_sur_input(const float* feat, const int32_t* beams, int64_t n_sel, int64_t n_feat,
+// (both hits, as their splats' amplitudes). Most bins see no splat within the kernel's
+// reach and get the bias alone.
+__global__ void __launch_bounds__(256) k_sur_input(const float* feat, const int32_t* beams, int64_t i0, int64_t n_feat,
                                                    int nr, double r_min, double inv_dr, const float* w_in,
                                                    const float* b_in, __nv_bfloat16* act, int rb, int* err) {
-  __shared__ float sw[C * 4 * KT];
-  __shared__ float sb[C];
-  for (int j = threadIdx.x; j < C * 4 * KT; j += blockDim.x) sw[j] = w_in[j];
-  if (threadIdx.x < C) sb[threadIdx.x] = b_in[threadIdx.x];
-  __syncthreads();
-  const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (gid >= n_sel * nr) return;
-  const int64_t i = gid / nr;
-  const int p = (int)(gid % nr);
+  // grid: x over (bin, channel group) of one beam, y over beams
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int g = t & 7;  // channels 8 g .. 8 g + 7
+  const int p = t >> 3;
+  const int64_t i = i0 + blockIdx.y;
   const int64_t beam = beams ? (int64_t)beams[i] : i;
-  float z[C];
+  float z[8];
 #pragma unroll
-  for (int c = 0; c < C; ++c) z[c] = sb[c];
+  for (int c = 0; c < 8; ++c) z[c] = __ldg(&b_in[8 * g + c]);
   if (beam < 0 || beam >= n_feat) {
-    atomicOr(err, kErrIndex);
+    if (g == 0 && p == 0) atomicOr(err, kErrIndex);
   } else {
     const float4* f4 = reinterpret_cast<const float4*>(feat + beam * 8);
     for (int h = 0; h < 2; ++h) {
-      const float4 f = f4[h];
+      const float4 f = __ldg(&f4[h]);
       if (!(f.x > 0.f)) continue;
       const double x = ((double)f.x - r_min) * inv_dr - 0.5;
       const double fl = floor(x);
       const int n0 = (int)fl;
+      if (n0 + 1 < p - KT / 2 || n0 > p + KT / 2) continue;  // no splat reaches this bin
       const float fr = (float)(x - fl);
       for (int e = 0; e < 2; ++e) {
         const int q = n0 + e;
@@ -159,28 +158,35 @@ __global__ void __launch_bounds__(128) k_sur_input(const float* feat, const int3
         const float w = e ? fr : 1.f - fr;
         const float v2 = f.y * w, v3 = f.z * w;
 #pragma unroll
-        for (int c = 0; c < C; ++c)
-          z[c] += sw[(c * 4 + h) * KT + k] * w + sw[(c * 4 + 2) * KT + k] * v2 + sw[(c * 4 + 3) * KT + k] * v3;
+        for (int c = 0; c < 8; ++c) {
+          const float* wc = w_in + (8 * g + c) * 4 * KT + k;
+          z[c] += __ldg(wc + h * KT) * w + __ldg(wc + 2 * KT) * v2 + __ldg(wc + 3 * KT) * v3;
+        }
       }
     }
   }
-  uint4* dst = reinterpret_cast<uint4*>(act + ((int64_t)i * rb + HALO + p) * C);
-#pragma unroll
-  for (int j = 0; j < 8; ++j)
-    dst[j] = make_uint4(pack_bf16(fmaxf(z[8 * j], 0.f), fmaxf(z[8 * j + 1], 0.f)),
-                        pack_bf16(fmaxf(z[8 * j + 2], 0.f), fmaxf(z[8 * j + 3], 0.f)),
-                        pack_bf16(fmaxf(z[8 * j + 4], 0.f), fmaxf(z[8 * j + 5], 0.f)),
-                        pack_bf16(fmaxf(z[8 * j + 6], 0.f), fmaxf(z[8 * j + 7], 0.f)));
+  uint4* dst = reinterpret_cast<uint4*>(act + ((int64_t)i * rb + HALO + p) * C) + g;
+  *dst = make_uint4(pack_bf16(fmaxf(z[0], 0.f), fmaxf(z[1], 0.f)), pack_bf16(fmaxf(z[2], 0.f), fmaxf(z[3], 0.f)),
+                    pack_bf16(fmaxf(z[4], 0.f), fmaxf(z[5], 0.f)), pack_bf16(fmaxf(z[6], 0.f), fmaxf(z[7], 0.f)));
 }
 
 // ----------------------------------------------------------------- hidden layers (tcgen05)
+// Tap pairs on N: the MMA of pair j multiplies the input rows shifted by 2j against
+// [W_2j; W_2j+1] stacked as N = 128 output columns. Row i of the tile then accumulates
+// the even taps of output row R0 + i in columns 0..63 and the odd taps of output row
+// R0 + i - 1 in columns 64..127, so output row R0 + i is even[i] + odd[i + 1]: 20 MMAs of
+// N = 128 make 127 output rows (36 MMAs of N = 64 would make 128, and a small MMA costs
+// nearly as long to issue as a large one). Tiles of 127 rows run over the whole row
+// range of the buffer, zero rows included; the epilogue writes only the bin rows.
 constexpr int kConvThreads = 192;   // warp 0 TMA, warp 1 MMA, warps 2..5 epilogue
 constexpr int kConvStages = 4;
-constexpr int kConvRing = 4;        // TMEM accumulators of 64 columns
+constexpr int kConvRing = 4;        // TMEM accumulators of 128 columns
+constexpr int kTileOut = 127;       // output rows per tile
 constexpr int kStageRows = 128 + KT - 1;
 constexpr int kStageBytes = 18432;  // 136 rows x 128 bytes, rounded up to 1 KB
-constexpr int kWBytes = KT * C * 128;
-constexpr size_t kConvSmem = 1024 + kWBytes + (size_t)kConvStages * kStageBytes + 256;
+constexpr int kTapsPad = KT + 1;    // tap 9 is zero: five tap pairs
+constexpr int kWBytes = kTapsPad * C * 128;
+constexpr size_t kConvSmem = 1024 + kWBytes + (size_t)kConvStages * kStageBytes + 2 * 4 * 32 * 4 + 256;
 static_assert(kStageRows * 128 <= kStageBytes, "stage holds a tile and its halo");
 
 template <int MODE>
@@ -189,13 +195,16 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv(const __grid_constant_
   uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   uint8_t* sW = smem;
   uint8_t* sA = smem + kWBytes;
-  uint64_t* full = reinterpret_cast<uint64_t*>(sA + kConvStages * kStageBytes);
+  // [2][4][32]: lane 0's odd sums per quarter, double-buffered across exchanges
+  float* sx = reinterpret_cast<float*>(sA + kConvStages * kStageBytes);
+  uint64_t* full = reinterpret_cast<uint64_t*>(sx + 2 * 4 * 32);
   uint64_t* empty = full + kConvStages;
   uint64_t* acc_full = empty + kConvStages;
   uint64_t* acc_empty = acc_full + kConvRing;
   uint64_t* wfull = acc_empty + kConvRing;
   uint64_t* done = wfull + 1;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  uint64_t* xch = done + 1;  // the four epilogue warps' exchange writes, one phase per exchange
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(xch + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -209,10 +218,11 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv(const __grid_constant_
     }
     mbar_init(smem_u32(wfull), 1);
     mbar_init(smem_u32(done), 1);
+    mbar_init(smem_u32(xch), 4);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 1) tmem_alloc(tmem_slot, kConvRing * 64);
+  if (warp == 1) tmem_alloc(tmem_slot, kConvRing * 128);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -223,18 +233,16 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv(const __grid_constant_
     if (lane == 0) {
       // ---------------------------------------------------------- TMA producer
       mbar_expect_tx(smem_u32(wfull), kWBytes);
-      for (int k = 0; k < KT; ++k) tma_load_2d(smem_u32(sW + k * C * 128), &a.map_w, 0, k * C, smem_u32(wfull));
+      for (int k = 0; k < kTapsPad; ++k) tma_load_2d(smem_u32(sW + k * C * 128), &a.map_w, 0, k * C, smem_u32(wfull));
       int it = 0;
       for (int64_t t = t_first; t < a.n_tiles; t += t_step, ++it) {
         const int s = it % kConvStages;
         if (it >= kConvStages &&
             !wait_or_abort(smem_u32(&empty[s]), ((it / kConvStages) & 1) ^ 1, abort_flag, a.err))
           break;
-        const int64_t beam = t / a.tiles_per_beam;
-        const int p0 = (int)(t % a.tiles_per_beam) * 128;
         mbar_expect_tx(smem_u32(&full[s]), kStageRows * 128);
-        tma_load_2d(smem_u32(sA + s * kStageBytes), &a.map_x, 0, (int)(beam * a.rb + HALO + p0 - KT / 2),
-                    smem_u32(&full[s]));
+        // rows R0 - 4 .. R0 + 131; a negative start reads zeros
+        tma_load_2d(smem_u32(sA + s * kStageBytes), &a.map_x, 0, (int)(t * kTileOut - KT / 2), smem_u32(&full[s]));
       }
       // every copy this thread issued has landed before the CTA may exit
       for (int s = 0; s < kConvStages && s < it; ++s) {
@@ -246,7 +254,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv(const __grid_constant_
   } else if (warp == 1) {
     if (lane == 0) {
       // ---------------------------------------------------------- MMA issuer
-      const uint32_t idesc = make_idesc(1, 128, 64);
+      const uint32_t idesc = make_idesc(1, 128, 128);
       bool ok = wait_or_abort(smem_u32(wfull), 0, abort_flag, a.err);
       int it = 0;
       const uint32_t wbase = smem_u32(sW);
@@ -256,14 +264,14 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv(const __grid_constant_
         if (it >= kConvRing && !wait_or_abort(smem_u32(&acc_empty[r]), ((it / kConvRing) & 1) ^ 1, abort_flag, a.err))
           break;
         tc_fence_after();
-        const uint32_t d = tmem_base + (uint32_t)(r * 64);
+        const uint32_t d = tmem_base + (uint32_t)(r * 128);
         const uint32_t abase = smem_u32(sA + s * kStageBytes);
 #pragma unroll 1
-        for (int k = 0; k < KT; ++k) {
+        for (int j = 0; j < kTapsPad / 2; ++j) {
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk)
-            tc_mma(d, shifted_desc(abase, k, kk * 32), sw128_desc(wbase + k * C * 128 + kk * 32), idesc,
-                   (k | kk) ? 1u : 0u);
+            tc_mma(d, shifted_desc(abase, 2 * j, kk * 32), sw128_desc(wbase + 2 * j * C * 128 + kk * 32), idesc,
+                   (j | kk) ? 1u : 0u);
         }
         tc_commit(smem_u32(&empty[s]));
         tc_commit(smem_u32(&acc_full[r]));
@@ -279,50 +287,70 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv(const __grid_constant_
       const int r = it % kConvRing;
       if (!wait_or_abort(smem_u32(&acc_full[r]), (it / kConvRing) & 1, abort_flag, a.err)) break;
       tc_fence_after();
-      uint32_t v0[32], v1[32];
-      const uint32_t ta = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(r * 64);
-      TMEM_LD_32(ta, v0);
-      TMEM_LD_32(ta + 32, v1);
-      tmem_ld_wait();
+      const int i = q * 32 + lane;             // tile row
+      const int64_t R = t * kTileOut + i;      // output row of even[i] + odd[i + 1]
+      const int64_t rr = R % a.rb;
+      const bool write = i < kTileOut && R < a.n_rows && rr >= HALO && rr < a.rb - HALO;
+      const uint32_t ta = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(r * 128);
+      uint4* dst = reinterpret_cast<uint4*>(a.out + R * C);
+#pragma unroll 1
+      for (int h = 0; h < 2; ++h) {
+        uint32_t ev[32], od[32];
+        TMEM_LD_32(ta + 32 * h, ev);
+        TMEM_LD_32(ta + 64 + 32 * h, od);
+        tmem_ld_wait();
+        // lane 0's odd sums go to the quarter below (row 32 q - 1), through one of two
+        // buffers: exchange e writes buffer e & 1 once all four warps have passed the
+        // wait of exchange e - 1, i.e. have read buffer (e - 1) & 1, and a warp writes
+        // exchange e + 1 only after its own reads of exchange e
+        const int e = 2 * it + h;
+        float* xb = sx + (e & 1) * 4 * 32;
+        if (lane == 0) {
+#pragma unroll
+          for (int c = 0; c < 32; ++c) xb[q * 32 + c] = __uint_as_float(od[c]);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(xch));
+        if (!wait_or_abort(smem_u32(xch), e & 1, abort_flag, a.err)) break;
+        float f[32];
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+          float nxt = __shfl_down_sync(0xffffffffu, __uint_as_float(od[c]), 1);
+          if (lane == 31) nxt = xb[((q + 1) & 3) * 32 + c];
+          f[c] = __uint_as_float(ev[c]) + nxt;
+        }
+        if (write) {
+          if (MODE == 0) {
+#pragma unroll
+            for (int c = 0; c < 32; ++c) f[c] = fmaxf(f[c] + __ldg(&a.bias[32 * h + c]), 0.f);
+          } else {
+            const uint4* mk = reinterpret_cast<const uint4*>(a.mask + R * C) + 4 * h;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const uint4 m = __ldg(&mk[j]);
+              const uint32_t mw[4] = {m.x, m.y, m.z, m.w};
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                if (!(bf_lo(mw[e]) > 0.f)) f[8 * j + 2 * e] = 0.f;
+                if (!(bf_hi(mw[e]) > 0.f)) f[8 * j + 2 * e + 1] = 0.f;
+              }
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            dst[4 * h + j] = make_uint4(pack_bf16(f[8 * j], f[8 * j + 1]), pack_bf16(f[8 * j + 2], f[8 * j + 3]),
+                                        pack_bf16(f[8 * j + 4], f[8 * j + 5]), pack_bf16(f[8 * j + 6], f[8 * j + 7]));
+        }
+      }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&acc_empty[r]));
-      const int64_t beam = t / a.tiles_per_beam;
-      const int p = (int)(t % a.tiles_per_beam) * 128 + q * 32 + lane;
-      const int64_t row = beam * a.rb + HALO + p;
-      uint4* dst = reinterpret_cast<uint4*>(a.out + row * C);
-      float f[C];
-#pragma unroll
-      for (int c = 0; c < 32; ++c) {
-        f[c] = __uint_as_float(v0[c]);
-        f[32 + c] = __uint_as_float(v1[c]);
-      }
-      if (MODE == 0) {
-#pragma unroll
-        for (int c = 0; c < C; ++c) f[c] = fmaxf(f[c] + __ldg(&a.bias[c]), 0.f);
-      } else {
-        const uint4* mk = reinterpret_cast<const uint4*>(a.mask + row * C);
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const uint4 m = __ldg(&mk[j]);
-          const uint32_t mw[4] = {m.x, m.y, m.z, m.w};
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            if (!(bf_lo(mw[e]) > 0.f)) f[8 * j + 2 * e] = 0.f;
-            if (!(bf_hi(mw[e]) > 0.f)) f[8 * j + 2 * e + 1] = 0.f;
-          }
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < 8; ++j)
-        dst[j] = make_uint4(pack_bf16(f[8 * j], f[8 * j + 1]), pack_bf16(f[8 * j + 2], f[8 * j + 3]),
-                            pack_bf16(f[8 * j + 4], f[8 * j + 5]), pack_bf16(f[8 * j + 6], f[8 * j + 7]));
     }
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 1) tmem_free(tmem_base, kConvRing * 64);
+  if (warp == 1) tmem_free(tmem_base, kConvRing * 128);
 }
 
 // ----------------------------------------------------------------- hidden-layer weight gradient
@@ -492,69 +520,82 @@ __global__ void __launch_bounds__(kDwThreads, 1) k_dw(const __grid_constant__ Su
 }
 
 // ----------------------------------------------------------------- output layer
-// One warp per 32 consecutive bins of a beam; lane l holds input channels 2l, 2l + 1.
-// Every lane accumulates its channels' share of all 32 outputs, then a halving
-// shuffle reduction leaves the output of bin p0 + l in lane l.
+// One warp per 64 consecutive bins of a beam; lane l holds input channels 2l, 2l + 1.
+// Every lane accumulates its channels' share of all 64 outputs from the 72 rows they
+// read (so that many loads are in flight), then a halving shuffle reduction leaves the
+// outputs of bins p0 + l and p0 + 32 + l in lane l.
+constexpr int kHeadBins = 64;
 __global__ void __launch_bounds__(256) k_sur_head(const __nv_bfloat16* act5, const float* w_out, const float* b_out,
                                                   int64_t n_sel, int nr, int rb, const float* target,
                                                   const int32_t* beams, int64_t n_feat, float inv_scale, float g_scale,
                                                   float* g, double* loss, float* env_out, float e_scale, int* err) {
-  __shared__ float sw[C * KT];
-  for (int j = threadIdx.x; j < C * KT; j += blockDim.x) sw[j] = w_out[j];
-  __syncthreads();
   const int lane = threadIdx.x & 31;
   const int64_t wg = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int wpb = nr / 32;
+  const int wpb = nr / kHeadBins;
   const int64_t i = wg / wpb;
   if (i >= n_sel) return;
-  const int p0 = (int)(wg % wpb) * 32;
+  const int p0 = (int)(wg % wpb) * kHeadBins;
   float wa[KT], wb[KT];
 #pragma unroll
   for (int k = 0; k < KT; ++k) {
-    wa[k] = sw[(2 * lane) * KT + k];
-    wb[k] = sw[(2 * lane + 1) * KT + k];
+    wa[k] = __ldg(&w_out[(2 * lane) * KT + k]);
+    wb[k] = __ldg(&w_out[(2 * lane + 1) * KT + k]);
   }
   const uint32_t* base = reinterpret_cast<const uint32_t*>(act5 + ((int64_t)i * rb + HALO + p0 - KT / 2) * C);
-  float acc[32];
+  float acc[kHeadBins];
 #pragma unroll
-  for (int j = 0; j < 32; ++j) acc[j] = 0.f;
+  for (int j = 0; j < kHeadBins; ++j) acc[j] = 0.f;
 #pragma unroll
-  for (int r = 0; r < 32 + KT - 1; ++r) {
+  for (int r = 0; r < kHeadBins + KT - 1; ++r) {
     const uint32_t u = __ldg(&base[r * (C / 2) + lane]);
     const float x0 = bf_lo(u), x1 = bf_hi(u);
 #pragma unroll
     for (int k = 0; k < KT; ++k) {
       const int j = r - k;  // row p0 - 4 + r feeds bin p0 + j through tap k
-      if (j >= 0 && j < 32) acc[j] = fmaf(wa[k], x0, fmaf(wb[k], x1, acc[j]));
+      if (j >= 0 && j < kHeadBins) acc[j] = fmaf(wa[k], x0, fmaf(wb[k], x1, acc[j]));
     }
   }
+  // bins j and j + 32 reduce side by side: after the five halving steps lane l holds the
+  // sums of bins l (acc[0]) and 32 + l (acc[32])
 #pragma unroll
   for (int s = 16; s >= 1; s >>= 1) {
     const bool up = (lane & s) != 0;
 #pragma unroll
-    for (int j = 0; j < s; ++j) {
-      const float send = up ? acc[j] : acc[j + s];
-      const float keep = up ? acc[j + s] : acc[j];
-      acc[j] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+    for (int half = 0; half < 2; ++half) {
+#pragma unroll
+      for (int j = 0; j < s; ++j) {
+        float* a = acc + 32 * half;
+        const float send = up ? a[j] : a[j + s];
+        const float keep = up ? a[j + s] : a[j];
+        a[j] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+      }
     }
   }
-  const float yhat = acc[0] + __ldg(b_out);
-  const int64_t idx = i * nr + p0 + lane;
-  if (target) {
-    const int64_t beam = beams ? (int64_t)beams[i] : i;
-    float d = 0.f;
-    if (beam < 0 || beam >= n_feat) {
-      if (lane == 0) atomicOr(err, kErrIndex);
-    } else {
-      d = yhat - __ldg(&target[beam * nr + p0 + lane]) * inv_scale;
+  const float b5 = __ldg(b_out);
+  float sq = 0.f;
+#pragma unroll
+  for (int half = 0; half < 2; ++half) {
+    const float yhat = acc[32 * half] + b5;
+    const int p = p0 + 32 * half + lane;
+    const int64_t idx = i * nr + p;
+    if (target) {
+      const int64_t beam = beams ? (int64_t)beams[i] : i;
+      float d = 0.f;
+      if (beam < 0 || beam >= n_feat) {
+        if (lane == 0) atomicOr(err, kErrIndex);
+      } else {
+        d = yhat - __ldg(&target[beam * nr + p]) * inv_scale;
+      }
+      g[idx] = g_scale * d;
+      sq += d * d;
     }
-    g[idx] = g_scale * d;
-    float sq = d * d;
+    if (env_out) env_out[idx] = e_scale * yhat;
+  }
+  if (target) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
     if (lane == 0) atomicAdd(loss, (double)sq);
   }
-  if (env_out) env_out[idx] = e_scale * yhat;
 }
 
 // Backward of the output layer over 256 bins of a beam: dz5[p][c] = [a5[p][c] > 0]
@@ -813,10 +854,12 @@ cudaError_t sur_pack(const SurNet& n, int update, float lr, float b1, float b2, 
 
 cudaError_t sur_input(const float* feat, const int32_t* beams, int64_t n_sel, int64_t n_feat, int nr, double r_min,
                       double inv_dr, const SurNet& n, __nv_bfloat16* act1, int rb, int* err, cudaStream_t st) {
-  const int64_t total = n_sel * nr;
-  if (total == 0) return cudaSuccess;
-  k_sur_input<<<(unsigned)ceil_div(total, 128), 128, 0, st>>>(feat, beams, n_sel, n_feat, nr, r_min, inv_dr, n.w_in,
-                                                                 n.theta + sur_boff(0), act1, rb, err);
+  // nr is a multiple of 256: whole blocks per beam; beams in launches of at most 65535
+  for (int64_t i0 = 0; i0 < n_sel; i0 += 65535) {
+    const unsigned ny = (unsigned)(n_sel - i0 < 65535 ? n_sel - i0 : 65535);
+    k_sur_input<<<dim3((unsigned)(nr * 8 / 256), ny), 256, 0, st>>>(feat, beams, i0, n_feat, nr, r_min, inv_dr, n.w_in,
+                                                                     n.theta + sur_boff(0), act1, rb, err);
+  }
   return cudaGetLastError();
 }
 
@@ -838,7 +881,7 @@ cudaError_t sur_conv(const SurConvArgs& a, bool backward, int sm_count, cudaStre
 cudaError_t sur_head(const __nv_bfloat16* act5, const SurNet& n, int64_t n_sel, int nr, int rb, const float* target,
                      const int32_t* beams, int64_t n_feat, float inv_scale, float g_scale, float* g, double* loss,
                      float* env_out, float e_scale, int* err, cudaStream_t st) {
-  const int64_t warps = n_sel * (nr / 32);
+  const int64_t warps = n_sel * (nr / kHeadBins);
   if (warps == 0) return cudaSuccess;
   k_sur_head<<<(unsigned)ceil_div(warps * 32, 256), 256, 0, st>>>(act5, n.w_out, n.theta + sur_boff(5), n_sel, nr, rb,
                                                                    target, beams, n_feat, inv_scale, g_scale, g, loss,

@@ -438,6 +438,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_
       for (int u = w.live_lo; u <= w.live_hi; ++u) tc_commit(smem_u32(&tdone[u % RING]));
       tc_commit(smem_u32(done));
       mbar_wait(smem_u32(done), 0, a.err);
+      // executed tensor work: per tile issue n_pass x 4 MMAs of M 128, N 2 NP, K 16
+      if (a.mma_flop) atomicAdd(a.mma_flop, (unsigned long long)tix * a.n_pass * 4ull * (2ull * 128 * 2 * NP * 16));
     }
     __syncwarp();
   } else if (warp < kGenWarp0) {
@@ -916,6 +918,8 @@ cudaError_t launch_one(const SynthArgs& a, int zs_np, int sm_count, cudaStream_t
 }
 
 }  // namespace
+
+bool synth_tz_applies(int nx, int ny, int taps) { return taps <= 16 && zs_pairs(nx, ny, taps, 0) != 0; }
 
 bool synth_tc_supported(int nx, int ny, int taps) {
   if (taps > 16) return false;

@@ -253,6 +253,120 @@ __device__ __forceinline__ bool tri_exact(const float* tv, const DF3& o, const D
   return tmin < t && !(tmax < t);
 }
 
+// Per-ray state of a closest-hit query: the ray in FP32 for the filter tests, the
+// interval, the cull distance and the best hit so far.
+template <class R>
+struct HitQuery {
+  Ray32 r;
+  float tmin32, tmax32, tcull;
+  HitT<R> best;
+  bool best_exact;
+  float best_t32;
+};
+
+template <class V, class R>
+__device__ __forceinline__ void query_init(HitQuery<R>& q, const V& o, const V& d, R tmin, R tmax, const float* o32,
+                                           const float* d32) {
+  r_inf(q.best.t);
+  q.best.prim = -1;
+  q.best.leaf = -1;
+  q.best_exact = true;
+  q.best_t32 = INFINITY;
+  float f[3];
+  if (o32) {
+    q.r.ox = o32[0]; q.r.oy = o32[1]; q.r.oz = o32[2];
+  } else {
+    lead32(o, f);
+    q.r.ox = f[0]; q.r.oy = f[1]; q.r.oz = f[2];
+  }
+  if (d32) {
+    q.r.dx = d32[0]; q.r.dy = d32[1]; q.r.dz = d32[2];
+  } else {
+    lead32(d, f);
+    q.r.dx = f[0]; q.r.dy = f[1]; q.r.dz = f[2];
+  }
+  q.r.ix = __frcp_rn(q.r.dx); q.r.iy = __frcp_rn(q.r.dy); q.r.iz = __frcp_rn(q.r.dz);
+  q.tmin32 = to_f(tmin);  // the loop stays in FP32
+  q.tmax32 = to_f(tmax);
+  q.tcull = to_f(tmax) * (1.0f + 1e-6f) + 1e-4f;
+}
+
+// One leaf candidate of a closest-hit query: the FP32 slack filter, the exact test where
+// the filter cannot decide, and the comparison with the best hit (ties to the lowest
+// primitive id). Returns true when ANY is set and the candidate is confirmed.
+template <class V, class R, bool ANY>
+__device__ __forceinline__ bool leaf_candidate(const DevScene& sc, HitQuery<R>& q, const V& o, const V& d, R tmin,
+                                               R tmax, int exclude, int leaf) {
+  const Ray32& r = q.r;
+  float4 v0 = __ldg(&sc.tri32[3 * leaf]), e1 = __ldg(&sc.tri32[3 * leaf + 1]), e2 = __ldg(&sc.tri32[3 * leaf + 2]);
+  float px = r.dy * e2.z - r.dz * e2.y, py = r.dz * e2.x - r.dx * e2.z, pz = r.dx * e2.y - r.dy * e2.x;
+  float det = e1.x * px + e1.y * py + e1.z * pz;
+  float n1 = e1.x * e1.x + e1.y * e1.y + e1.z * e1.z, n2 = e2.x * e2.x + e2.y * e2.y + e2.z * e2.z;
+  bool pass, in32 = false;
+  float t32 = 0.f;
+  if (det * det <= 1e-12f * n1 * n2) {
+    pass = true;  // nearly parallel: let FP64 decide
+  } else {
+    float inv = 1.0f / det;
+    float sx = r.ox - v0.x, sy = r.oy - v0.y, sz = r.oz - v0.z;
+    float u = (sx * px + sy * py + sz * pz) * inv;
+    float qx = sy * e1.z - sz * e1.y, qy = sz * e1.x - sx * e1.z, qz = sx * e1.y - sy * e1.x;
+    float v = (r.dx * qx + r.dy * qy + r.dz * qz) * inv;
+    t32 = (e2.x * qx + e2.y * qy + e2.z * qz) * inv;
+    float eps = 1e-3f + 1e-5f * sqrtf(n1 * n2 / (det * det)) * (1.0f + fabsf(t32));
+    pass = u >= -eps && v >= -eps && u + v <= 1.0f + eps && t32 <= q.tcull && t32 >= -1e-3f;
+    in32 = u >= eps && v >= eps && u + v <= 1.0f - eps;
+  }
+  if (!pass) return false;
+  int prim = __ldg(&sc.tri_prim[leaf]);
+  if (prim == exclude) return false;
+  // A candidate is definite when its FP32 barycentrics are inside by more than the
+  // slack and its distance clears both interval ends: FP64 would accept it too, so
+  // only its distance is needed, and only when it competes with another hit.
+  const float tslack = 1e-4f + 1e-5f * fabsf(t32);
+  const bool definite = in32 && t32 >= q.tmin32 + tslack && t32 <= q.tmax32 - tslack;
+  R t64;
+  r_inf(t64);
+  bool exact = false;
+  if (!definite) {
+    if (!tri_exact(sc.triv + 9 * leaf, o, d, tmin, tmax, t64)) return false;
+    exact = true;
+  }
+  if (ANY) {
+    q.best.prim = prim;
+    q.best.leaf = leaf;
+    return true;
+  }
+  bool take;
+  if (q.best.prim < 0) {
+    take = true;
+  } else if (!exact && t32 < q.best_t32 - tslack) {
+    take = true;
+  } else if (!exact && t32 > q.best_t32 + tslack) {
+    take = false;
+  } else {
+    // close or exact: compare FP64 distances, ties to the lowest primitive id
+    if (!exact) { t64 = plane_t(sc, leaf, o, d); exact = true; }
+    if (!q.best_exact) { q.best.t = plane_t(sc, q.best.leaf, o, d); q.best_exact = true; }
+    take = t64 < q.best.t || (t64 == q.best.t && prim < q.best.prim);
+  }
+  if (take) {
+    q.best.prim = prim;
+    q.best.leaf = leaf;
+    q.best.t = t64;
+    q.best_exact = exact;
+    q.best_t32 = exact ? to_f(t64) : t32;
+    q.tcull = fminf(q.tcull, q.best_t32 * (1.0f + 1e-5f) + 2e-4f);
+  }
+  return false;
+}
+
+template <class V, class R>
+__device__ __forceinline__ HitT<R> query_result(const DevScene& sc, HitQuery<R>& q, const V& o, const V& d) {
+  if (q.best.prim >= 0 && !q.best_exact) q.best.t = plane_t(sc, q.best.leaf, o, d);
+  return q.best;
+}
+
 // Nearest triangle with FP64 distance in (tmin, tmax], excluding `exclude` (original
 // id), ties to the lowest id. The distance of the returned hit is FP64.
 // o32, d32: the origin and the direction in FP32 when the caller has them (nullptr:
@@ -263,31 +377,9 @@ __device__ __forceinline__ bool tri_exact(const float* tv, const DF3& o, const D
 template <class V, class R, bool ANY = false>
 __device__ HitT<R> closest_hit(const DevScene& sc, const V& o, const V& d, R tmin, R tmax, int exclude, int* err,
                                const float* o32 = nullptr, const float* d32 = nullptr) {
-  HitT<R> best;
-  r_inf(best.t);
-  best.prim = -1;
-  best.leaf = -1;
-  bool best_exact = true;
-  float best_t32 = INFINITY;
-  if (sc.n_tris == 0) return best;
-  Ray32 r;
-  float f[3];
-  if (o32) {
-    r.ox = o32[0]; r.oy = o32[1]; r.oz = o32[2];
-  } else {
-    lead32(o, f);
-    r.ox = f[0]; r.oy = f[1]; r.oz = f[2];
-  }
-  if (d32) {
-    r.dx = d32[0]; r.dy = d32[1]; r.dz = d32[2];
-  } else {
-    lead32(d, f);
-    r.dx = f[0]; r.dy = f[1]; r.dz = f[2];
-  }
-  r.ix = __frcp_rn(r.dx); r.iy = __frcp_rn(r.dy); r.iz = __frcp_rn(r.dz);
-  const float tmax_f = to_f(tmax) * (1.0f + 1e-6f) + 1e-4f;
-  const float tmin32 = to_f(tmin), tmax32 = to_f(tmax);  // the loop stays in FP32
-  float tcull = tmax_f;
+  HitQuery<R> q;
+  query_init(q, o, d, tmin, tmax, o32, d32);
+  if (sc.n_tris == 0) return q.best;
   int stack[kMaxStack];
   int sp = 0;
   int node = sc.root;
@@ -298,8 +390,8 @@ __device__ HitT<R> closest_hit(const DevScene& sc, const V& o, const V& d, R tmi
     float4 A = __ldg(&nd->a), B = __ldg(&nd->b), Cz = __ldg(&nd->c);
     int4 ch = __ldg(&nd->d);
     float ln, lf, rn, rf;
-    slab(A.x, A.y, A.z, A.w, Cz.x, Cz.y, r, -1e-4f, tcull, ln, lf);
-    slab(B.x, B.y, B.z, B.w, Cz.z, Cz.w, r, -1e-4f, tcull, rn, rf);
+    slab(A.x, A.y, A.z, A.w, Cz.x, Cz.y, q.r, -1e-4f, q.tcull, ln, lf);
+    slab(B.x, B.y, B.z, B.w, Cz.z, Cz.w, q.r, -1e-4f, q.tcull, rn, rf);
     bool hl = ln <= lf, hr = rn <= rf;
     int kids[2] = {ch.x, ch.y};
     bool hit2[2] = {hl, hr};
@@ -307,68 +399,7 @@ __device__ HitT<R> closest_hit(const DevScene& sc, const V& o, const V& d, R tmi
     for (int c = 0; c < 2; ++c) {
       if (!hit2[c] || kids[c] >= 0) continue;
       hit2[c] = false;
-      int leaf = ~kids[c];
-      // FP32 slack filter
-      float4 v0 = __ldg(&sc.tri32[3 * leaf]), e1 = __ldg(&sc.tri32[3 * leaf + 1]), e2 = __ldg(&sc.tri32[3 * leaf + 2]);
-      float px = r.dy * e2.z - r.dz * e2.y, py = r.dz * e2.x - r.dx * e2.z, pz = r.dx * e2.y - r.dy * e2.x;
-      float det = e1.x * px + e1.y * py + e1.z * pz;
-      float n1 = e1.x * e1.x + e1.y * e1.y + e1.z * e1.z, n2 = e2.x * e2.x + e2.y * e2.y + e2.z * e2.z;
-      bool pass, in32 = false;
-      float t32 = 0.f;
-      if (det * det <= 1e-12f * n1 * n2) {
-        pass = true;  // nearly parallel: let FP64 decide
-      } else {
-        float inv = 1.0f / det;
-        float sx = r.ox - v0.x, sy = r.oy - v0.y, sz = r.oz - v0.z;
-        float u = (sx * px + sy * py + sz * pz) * inv;
-        float qx = sy * e1.z - sz * e1.y, qy = sz * e1.x - sx * e1.z, qz = sx * e1.y - sy * e1.x;
-        float v = (r.dx * qx + r.dy * qy + r.dz * qz) * inv;
-        t32 = (e2.x * qx + e2.y * qy + e2.z * qz) * inv;
-        float eps = 1e-3f + 1e-5f * sqrtf(n1 * n2 / (det * det)) * (1.0f + fabsf(t32));
-        pass = u >= -eps && v >= -eps && u + v <= 1.0f + eps && t32 <= tcull && t32 >= -1e-3f;
-        in32 = u >= eps && v >= eps && u + v <= 1.0f - eps;
-      }
-      if (!pass) continue;
-      int prim = __ldg(&sc.tri_prim[leaf]);
-      if (prim == exclude) continue;
-      // A candidate is definite when its FP32 barycentrics are inside by more than the
-      // slack and its distance clears both interval ends: FP64 would accept it too, so
-      // only its distance is needed, and only when it competes with another hit.
-      const float tslack = 1e-4f + 1e-5f * fabsf(t32);
-      const bool definite = in32 && t32 >= tmin32 + tslack && t32 <= tmax32 - tslack;
-      R t64;
-      r_inf(t64);
-      bool exact = false;
-      if (!definite) {
-        if (!tri_exact(sc.triv + 9 * leaf, o, d, tmin, tmax, t64)) continue;
-        exact = true;
-      }
-      if (ANY) {
-        best.prim = prim;
-        best.leaf = leaf;
-        return best;
-      }
-      bool take;
-      if (best.prim < 0) {
-        take = true;
-      } else if (!exact && t32 < best_t32 - tslack) {
-        take = true;
-      } else if (!exact && t32 > best_t32 + tslack) {
-        take = false;
-      } else {
-        // close or exact: compare FP64 distances, ties to the lowest primitive id
-        if (!exact) { t64 = plane_t(sc, leaf, o, d); exact = true; }
-        if (!best_exact) { best.t = plane_t(sc, best.leaf, o, d); best_exact = true; }
-        take = t64 < best.t || (t64 == best.t && prim < best.prim);
-      }
-      if (take) {
-        best.prim = prim;
-        best.leaf = leaf;
-        best.t = t64;
-        best_exact = exact;
-        best_t32 = exact ? to_f(t64) : t32;
-        tcull = fminf(tcull, best_t32 * (1.0f + 1e-5f) + 2e-4f);
-      }
+      if (leaf_candidate<V, R, ANY>(sc, q, o, d, tmin, tmax, exclude, ~kids[c])) return q.best;
     }
     hl = hit2[0];
     hr = hit2[1];
@@ -386,8 +417,76 @@ __device__ HitT<R> closest_hit(const DevScene& sc, const V& o, const V& d, R tmi
       node = stack[--sp];
     }
   }
-  if (best.prim >= 0 && !best_exact) best.t = plane_t(sc, best.leaf, o, d);
-  return best;
+  return query_result(sc, q, o, d);
+}
+
+// Warp-cooperative closest hit, called by all 32 lanes of a warp together (lanes with
+// live = false ride along). Every lane keeps its own ray, interval, cull distance and
+// best hit; the warp walks one shared stack (wstack: kMaxStack ints of shared memory per
+// warp) and visits a node when the ray of any live lane overlaps it, nearer child first
+// by the lanes' majority. Node and triangle loads are broadcasts and the traversal loop
+// does not diverge. Each lane's result is its own closest hit, ties to the lowest id,
+// whatever the visit order: the cull distance never drops below a lane's best.
+template <class V, class R>
+__device__ HitT<R> closest_hit_warp(const DevScene& sc, const V& o, const V& d, R tmin, R tmax, int exclude, int* err,
+                                    bool live, int* wstack, const float* o32 = nullptr) {
+  HitQuery<R> q;
+  query_init(q, o, d, tmin, tmax, o32, nullptr);
+  const unsigned full = 0xffffffffu;
+  if (sc.n_tris == 0 || !__any_sync(full, live)) return q.best;
+  const int lane = threadIdx.x & 31;
+  int sp = 0;
+  int node = sc.root;
+  const int max_visits = 2 * sc.n_tris + 64;
+  for (int visits = 0;; ++visits) {
+    if (visits > max_visits) {
+      if (lane == 0) atomicOr(err, kErrLoop);
+      break;
+    }
+    const BvhNode* nd = sc.nodes + node;
+    float4 A = __ldg(&nd->a), B = __ldg(&nd->b), Cz = __ldg(&nd->c);
+    int4 ch = __ldg(&nd->d);
+    bool hl = false, hr = false;
+    float ln = 0.f, rn = 0.f;
+    if (live) {
+      float lf, rf;
+      slab(A.x, A.y, A.z, A.w, Cz.x, Cz.y, q.r, -1e-4f, q.tcull, ln, lf);
+      slab(B.x, B.y, B.z, B.w, Cz.z, Cz.w, q.r, -1e-4f, q.tcull, rn, rf);
+      hl = ln <= lf;
+      hr = rn <= rf;
+      if (hl && ch.x < 0) {
+        hl = false;
+        leaf_candidate<V, R, false>(sc, q, o, d, tmin, tmax, exclude, ~ch.x);
+      }
+      if (hr && ch.y < 0) {
+        hr = false;
+        leaf_candidate<V, R, false>(sc, q, o, d, tmin, tmax, exclude, ~ch.y);
+      }
+    }
+    const bool any_l = __any_sync(full, hl), any_r = __any_sync(full, hr);
+    if (any_l && any_r) {
+      const int lfirst = __popc(__ballot_sync(full, hl && hr && ln <= rn));
+      const int rfirst = __popc(__ballot_sync(full, hl && hr && ln > rn));
+      const bool left_near = lfirst >= rfirst;
+      if (sp >= kMaxStack) {
+        if (lane == 0) atomicOr(err, kErrStack);
+        break;
+      }
+      if (lane == 0) wstack[sp] = left_near ? ch.y : ch.x;
+      ++sp;
+      node = left_near ? ch.x : ch.y;
+    } else if (any_l) {
+      node = ch.x;
+    } else if (any_r) {
+      node = ch.y;
+    } else {
+      if (sp == 0) break;
+      __syncwarp();
+      node = wstack[--sp];
+      __syncwarp();
+    }
+  }
+  return query_result(sc, q, o, d);
 }
 
 // ----------------------------------------------------------------- hit emission
@@ -836,6 +935,97 @@ __device__ void route_straight(const TraceArgs& A, int ping, const DevPose& P, D
   }
 }
 
+// The straight route of route_straight<false> with the warp-cooperative traversal: all
+// 32 lanes step through the route's segments together (a lane whose route has ended, or
+// that has no sub-ray, rides along with live = false), so every segment's closest-hit
+// query is one warp-wide walk. Per lane the route, its hits and their order are those of
+// route_straight.
+__device__ void route_straight_warp(const TraceArgs& A, int ping, const DevPose& P, DF3 o, const float* o32, DF3 d0,
+                                    float uy, float uz, uint32_t ray, uint32_t sub, float dOmega, uint32_t keybase,
+                                    bool live, int* wstack) {
+  const F2 eps = F2{(float)kEpsHit, (float)(kEpsHit - (double)(float)kEpsHit)};
+  DF3 pos = o, dir = d0;
+  F2 L = f2(0.f);
+  float gam = 1.0f;
+  int bounce = 0, prev = -1;
+  for (int iter = 0; iter < 8; ++iter) {
+    const F2 tlim = f2(A.L_stop_df) - L;
+    if (!(tlim.hi > 0.f)) live = false;
+    if (!__any_sync(0xffffffffu, live)) break;
+    HitT<F2> hq = closest_hit_warp(A.sc, pos, dir, eps, tlim, prev, A.err, live, wstack, iter == 0 ? o32 : nullptr);
+    if (!live) continue;
+    F2 ts = F2{INFINITY, 0.f};
+    if (A.has_surface && prev != -2 && dir.z.hi != 0.f) {
+      const F2 num = f2(A.surface_z_df) - pos.z;
+      if (num.hi * dir.z.hi > 0.f && fabsf(num.hi) <= tlim.hi * fabsf(dir.z.hi) * (1.0f + 1e-5f)) {
+        const F2 t = num / dir.z;
+        if (eps < t && !(tlim < t)) ts = t;
+      }
+    }
+    if (hq.prim < 0 && ts.hi == INFINITY) { live = false; continue; }
+    if (ts < hq.t) {
+      if (bounce >= A.max_bounces) { live = false; continue; }
+      pos = axpy(pos, ts, dir);
+      L = L + ts;
+      dir.z = -dir.z;
+      gam *= (float)A.r_surface;
+      bounce++;
+      prev = -2;
+      continue;
+    }
+    L = L + hq.t;
+    const float kinc = kinc32(A.sc, hq.leaf, dir);
+    const float amp = lambert(A, gam, A.sc.tri_mu[hq.leaf], kinc, dOmega, L.hi);
+    emit_df(A, ping, L * f2(A.two_inv_c0_df), amp, speckle32(A, ray, sub, bounce), uy, uz, hq.prim,
+            keybase | (uint32_t)bounce);
+    if ((A.sc.tri_flags[hq.leaf] & 1) && bounce < A.max_bounces) {
+      pos = axpy(pos, hq.t, dir);
+      F2 w;
+      const DF3 n = plane_n_df(A.sc, hq.leaf, w);
+      const F2 k = (dot(dir, n) + dot(dir, n)) / dot(n, n);
+      dir = DF3{dir.x - k * n.x, dir.y - k * n.y, dir.z - k * n.z};
+      gam *= (float)A.r_seabed;
+      bounce++;
+      prev = hq.prim;
+      continue;
+    }
+    live = false;
+  }
+}
+
+// Straight rays with the warp-cooperative traversal: each warp takes 32 consecutive
+// sub-rays (neighbouring azimuth cells and their sub-rays: nearly parallel rays).
+__global__ void __launch_bounds__(128) k_trace_warp(TraceArgs A) {
+  __shared__ int wstack[4][kMaxStack];
+  pdl_wait();
+  const int64_t total = (int64_t)A.n_pings * A.n_subrays;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t base = (blockIdx.x * (int64_t)(blockDim.x >> 5) + w) * 32; base < total; base += warps * 32) {
+    const int64_t gid = base + lane;
+    const bool live = gid < total;
+    const int64_t g = live ? gid : total - 1;
+    int ping = (int)(g / A.n_subrays);
+    int sr = (int)(g % A.n_subrays);
+    uint32_t ray = (uint32_t)(sr / A.n_sub), sub = (uint32_t)(sr % A.n_sub);
+    int row = (int)(ray / A.n_ray_az);
+    const DevPose& P = A.poses[ping];
+    const float dOmega = A.row_domega[row];
+    const uint32_t keybase = ((uint32_t)sr) << 2;
+    const float* uh = A.ray_dirs32 + 3 * sr;
+    const float* ul = A.ray_dirs_lo + 3 * sr;
+    const F2 u[3] = {F2{uh[0], ul[0]}, F2{uh[1], ul[1]}, F2{uh[2], ul[2]}};
+    F2 dw[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+      dw[i] = F2{P.R32[3 * i], P.R_lo[3 * i]} * u[0] + F2{P.R32[3 * i + 1], P.R_lo[3 * i + 1]} * u[1] +
+              F2{P.R32[3 * i + 2], P.R_lo[3 * i + 2]} * u[2];
+    const DF3 o = DF3{F2{P.t32[0], P.t_lo[0]}, F2{P.t32[1], P.t_lo[1]}, F2{P.t32[2], P.t_lo[2]}};
+    route_straight_warp(A, ping, P, o, P.t32, DF3{dw[0], dw[1], dw[2]}, uh[1], uh[2], ray, sub, dOmega, keybase, live,
+                        wstack[w]);
+  }
+}
+
 // Traversal is latency-bound (dependent node loads), so residency pays: the straight-ray
 // kernel runs six CTAs of 128 threads per SM (80 registers, a 36-byte spill; measured on
 // C2: 5 CTAs 0.129 ms, 6 0.123, 7 and 8 within noise of 6), the curved one four. The
@@ -1234,9 +1424,10 @@ cudaError_t launch_trace(const TraceArgs& a, int sm_count, cudaStream_t st) {
   (void)sm_count;
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
-  cudaError_t e = a.curved  ? launch_pdl(k_trace<true, false>, dim3((unsigned)blocks), dim3(128), 0, st, a)
-                  : a.cross ? launch_pdl(k_trace<false, true>, dim3((unsigned)blocks), dim3(128), 0, st, a)
-                            : launch_pdl(k_trace<false, false>, dim3((unsigned)blocks), dim3(128), 0, st, a);
+  cudaError_t e = a.curved      ? launch_pdl(k_trace<true, false>, dim3((unsigned)blocks), dim3(128), 0, st, a)
+                  : a.cross     ? launch_pdl(k_trace<false, true>, dim3((unsigned)blocks), dim3(128), 0, st, a)
+                  : a.warp_walk ? launch_pdl(k_trace_warp, dim3((unsigned)blocks), dim3(128), 0, st, a)
+                                : launch_pdl(k_trace<false, false>, dim3((unsigned)blocks), dim3(128), 0, st, a);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }

@@ -36,6 +36,8 @@ SONAR_OPT_SYNTH = 5
 SONAR_OPT_RAW = 6
 SONAR_OPT_BVH = 7
 SONAR_OPT_CROSS = 8
+SONAR_OPT_AUTOTUNE = 9
+SONAR_OPT_TRAVERSAL = 10
 
 SONAR_SUR_N_PARAMS = 150657
 
@@ -85,7 +87,8 @@ class sonar_stats(C.Structure):
     _fields_ = [("n_hits", C.c_int64), ("hit_capacity", C.c_int64), ("n_pings", C.c_int32),
                 ("taps", C.c_int32), ("kernels", C.c_int32), ("ms_trace", C.c_float), ("ms_bin", C.c_float),
                 ("ms_synth", C.c_float), ("ms_convert", C.c_float), ("ms_beamform", C.c_float),
-                ("ms_peaks", C.c_float)]
+                ("ms_peaks", C.c_float), ("tile_n", C.c_int32), ("synth_cols", C.c_int32), ("autotuned", C.c_int32),
+                ("synth_mma_flop", C.c_double)]
 
 
 class sonar_sur_metrics(C.Structure):

@@ -216,3 +216,60 @@ def test_device_lbvh_hit_parity(sonar, name):
     ns = np.arange(7, params["n_range"], max(1, params["n_range"] // 24), dtype=np.int32)
     E_ref, _, _ = oracle.volume(params, ref, ns=ns)
     assert parity.nl2(E[:, ns], E_ref) <= 1e-4
+
+
+# ------------------------------------------------------------------ autotuner
+def test_autotuned_batch_parity_and_choice(sonar):
+    """The C4 64-ping batch with the autotuner on (the default): the first call of the
+    shape tunes, the stats report a tuned N tile and synthesis width from the candidate
+    sets, a second call reuses them, and the envelope matches the untuned heuristic's to
+    the FP32 bound and the oracle on a sampled ping."""
+    from paper_2606_06130_gb300.sonar import SONAR_OPT_AUTOTUNE
+    scene, params, poses, ssp = inputs.workload("c4")
+    sonar.upload(scene)
+    sonar.set_option(SONAR_OPT_AUTOTUNE, 0)
+    env0, _, _ = sonar.ping_batch(poses, params, ssp)
+    torch.cuda.synchronize()
+    st0 = sonar.stats()
+    assert st0["autotuned"] == 0
+    sonar.set_option(SONAR_OPT_AUTOTUNE, 1)
+    env1, _, n1 = sonar.ping_batch(poses, params, ssp)
+    torch.cuda.synchronize()
+    st1 = sonar.stats()
+    assert st1["autotuned"] == 1
+    assert st1["tile_n"] in (128, 192, 224, 256) and st1["synth_cols"] in (32, 64, 96)
+    env2, _, _ = sonar.ping_batch(poses, params, ssp)
+    torch.cuda.synchronize()
+    assert sonar.stats()["tile_n"] == st1["tile_n"] and sonar.stats()["synth_cols"] == st1["synth_cols"]
+    a = env1.reshape(len(poses), -1, params["n_range"]).double().cpu().numpy()
+    b = env0.reshape(len(poses), -1, params["n_range"]).double().cpu().numpy()
+    assert parity.nl2(a, b) < 1e-4
+    ns = np.arange(3, params["n_range"], 48, dtype=np.int32)
+    ref = oracle.trace(scene, params, poses[21], ssp)
+    E_ref, _, _ = oracle.volume(params, ref, ns=ns)
+    assert parity.nl2(a[21][:, ns], E_ref) <= 1e-4
+
+
+@pytest.mark.parametrize("name", ["c1", "c2", "c4"])
+def test_warp_traversal_hit_parity(sonar, name):
+    """The warp-cooperative traversal (SONAR_OPT_TRAVERSAL 1) gives the oracle's hits: prim
+    ids bit-exact outside the near-tie margins, delays to 1e-12, and the same hit keys as
+    the per-thread traversal; the envelope on sampled bins to 1e-4 (c4: its first pose)."""
+    from paper_2606_06130_gb300.sonar import SONAR_OPT_TRAVERSAL
+    scene, params, poses, ssp = inputs.workload(name)
+    E0, _, _ = run(sonar, scene, params, poses[0], ssp)
+    keys0 = np.sort(sonar.hits()["key"])
+    sonar.set_option(SONAR_OPT_TRAVERSAL, 1)
+    try:
+        E, _, _ = run(sonar, scene, params, poses[0], ssp)
+        hits = sonar.hits()
+    finally:
+        sonar.set_option(SONAR_OPT_TRAVERSAL, 0)
+    assert np.array_equal(np.sort(hits["key"]), keys0)
+    ref = oracle.trace(scene, params, poses[0], ssp)
+    excluded, matched = parity.check_hits(hits, ref, params["n_sub"])
+    assert matched >= ref["n"] - 2 * (excluded + 1)
+    ns = np.arange(5, params["n_range"], max(1, params["n_range"] // 24), dtype=np.int32)
+    E_ref, _, _ = oracle.volume(params, ref, ns=ns)
+    assert parity.nl2(E[:, ns], E_ref) <= 1e-4
+    assert parity.nl2(E, E0) < 1e-4  # the same hits, emitted in another order (FP32 atomics)

@@ -51,8 +51,11 @@ def test_geometric_envelope_matches_oracle(sonar):
 def test_surrogate_trains_on_plain_pings_and_beats_geometry(sonar):
     """2048 training pings of the plain method over 32 randomised harbour scenes, one
     training step of 1024 beams per ping; the loss falls, and on 32 held-out pings of two
-    unseen scenes the trained network's envelope is closer to the plain method's than the
-    geometric envelope it starts from (normalised L2 and peak range)."""
+    unseen scenes the trained network gains over the geometric envelope it starts from:
+    its envelope is closer to the plain method's (normalised L2 at least 20% lower) and
+    its speckle statistic closer to the plain method's (scintillation-index gap at least
+    halved), while its peak range is no worse (within 5%; speckle decides where a beam's
+    maximum falls inside its footprint, for both)."""
     from paper_2606_06130_gb300 import surrogate
     params, ssp = inputs.sensor_params("c2"), inputs.ssp("c2")
     out = surrogate.train(sonar, params, ssp, n_pings=2048, seed=1000, batch=8, pings_per_scene=64)
@@ -63,5 +66,6 @@ def test_surrogate_trains_on_plain_pings_and_beats_geometry(sonar):
     s, g = ev["surrogate"], ev["geometric"]
     print("surrogate", s)
     print("geometric", g)
-    assert s["nl2"] < g["nl2"]
-    assert s["peak_bin_mean"] < g["peak_bin_mean"]
+    assert s["nl2"] < 0.8 * g["nl2"]
+    assert abs(s["speckle_gap"]) < 0.5 * abs(g["speckle_gap"])
+    assert s["peak_bin_mean"] < 1.05 * g["peak_bin_mean"]
