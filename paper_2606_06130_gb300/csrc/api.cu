@@ -1424,9 +1424,8 @@ int sur_alloc_params(sonar_ctx* ctx) {
   if (S.params) return SONAR_OK;
   CU(cudaMalloc(&S.params, sizeof(float) * 4 * kSurParams));
   CU(cudaMemset(S.params, 0, sizeof(float) * 4 * kSurParams));
-  const int64_t wn = 4LL * (kSurK + 1) * kSurC * kSurC;  // tap 9 of every layer stays zero
+  const int64_t wn = 4LL * kSurK * kSurC * kSurC;
   CU(cudaMalloc(&S.wbf, sizeof(__nv_bfloat16) * 2 * wn));
-  CU(cudaMemset(S.wbf, 0, sizeof(__nv_bfloat16) * 2 * wn));
   CU(cudaMalloc(&S.wsmall, sizeof(float) * (kSurC * 4 * kSurK + kSurC * kSurK)));
   CU(cudaMalloc(&S.loss, sizeof(double)));
   S.net.theta = S.params;
@@ -1512,13 +1511,13 @@ int sur_forward(sonar_ctx* ctx, const float* feat, const int32_t* beams, int64_t
     SurConvArgs ca;
     memset(&ca, 0, sizeof(ca));
     if ((rc = make_map(ctx, &ca.map_x, sur_buf(ctx, L - 1), n_sel * rb, kSurC, 128 + kSurK - 1, false))) return rc;
-    if ((rc = make_map(ctx, &ca.map_w, S.net.wf + (int64_t)(L - 1) * (kSurK + 1) * kSurC * kSurC,
-                       (kSurK + 1) * kSurC, kSurC, kSurC, false)))
+    if ((rc = make_map(ctx, &ca.map_w, S.net.wf + (int64_t)(L - 1) * kSurK * kSurC * kSurC, kSurK * kSurC, kSurC,
+                       kSurC, false)))
       return rc;
     ca.bias = S.net.theta + sur_boff(L);
     ca.out = sur_buf(ctx, L);
-    ca.n_rows = n_sel * rb;
-    ca.n_tiles = (ca.n_rows + 126) / 127;
+    ca.n_tiles = n_sel * (d.nr / 128);
+    ca.tiles_per_beam = d.nr / 128;
     ca.rb = rb;
     ca.err = ctx->err_dev;
     CU(sur_conv(ca, false, ctx->sm_count, st));
@@ -1555,13 +1554,13 @@ int sur_backward(sonar_ctx* ctx, const float* feat, const int32_t* beams, int64_
     SurConvArgs ca;
     memset(&ca, 0, sizeof(ca));
     if ((rc = make_map(ctx, &ca.map_x, sur_buf(ctx, dz), n_sel * rb, kSurC, 128 + kSurK - 1, false))) return rc;
-    if ((rc = make_map(ctx, &ca.map_w, S.net.wb + (int64_t)(L - 1) * (kSurK + 1) * kSurC * kSurC,
-                       (kSurK + 1) * kSurC, kSurC, kSurC, false)))
+    if ((rc = make_map(ctx, &ca.map_w, S.net.wb + (int64_t)(L - 1) * kSurK * kSurC * kSurC, kSurK * kSurC, kSurC,
+                       kSurC, false)))
       return rc;
     ca.mask = sur_buf(ctx, L - 1);
     ca.out = sur_buf(ctx, 11 - dz);  // the other gradient buffer
-    ca.n_rows = n_sel * rb;
-    ca.n_tiles = (ca.n_rows + 126) / 127;
+    ca.n_tiles = n_sel * (d.nr / 128);
+    ca.tiles_per_beam = d.nr / 128;
     ca.rb = rb;
     ca.err = ctx->err_dev;
     CU(sur_conv(ca, true, ctx->sm_count, st));

@@ -255,8 +255,8 @@ struct SurNet {
   float* m;             // Adam first moment
   float* v;             // Adam second moment
   float* grad;          // [kSurParams]
-  __nv_bfloat16* wf;    // hidden layers 1..4: [4][10][64 cout][64 cin], forward B operands (tap 9 zero)
-  __nv_bfloat16* wb;    // [4][10][64 cin][64 cout], taps reversed: backward-data B operands (tap 9 zero)
+  __nv_bfloat16* wf;    // hidden layers 1..4: [4][9][64 cout][64 cin], forward B operands
+  __nv_bfloat16* wb;    // [4][9][64 cin][64 cout], taps reversed: backward-data B operands
   float* w_in;          // layer 0: [64][4][9]
   float* w_out;         // layer 5: [64][9]
 };
@@ -269,14 +269,13 @@ cudaError_t sur_pack(const SurNet& n, int update, float lr, float b1, float b2, 
 cudaError_t sur_input(const float* feat, const int32_t* beams, int64_t n_sel, int64_t n_feat, int nr, double r_min,
                       double inv_dr, const SurNet& n, __nv_bfloat16* act1, int rb, int* err, cudaStream_t st);
 struct SurConvArgs {
-  CUtensorMap map_x;              // input rows [n_rows][64] BF16, box 64 x 136
-  CUtensorMap map_w;              // B operands [10 * 64][64] BF16, box 64 x 64
+  CUtensorMap map_x;              // input rows [n_sel * rb][64] BF16, box 64 x 136
+  CUtensorMap map_w;              // B operands [9 * 64][64] BF16, box 64 x 64
   const float* bias;              // forward: [64]
   const __nv_bfloat16* mask;      // backward-data: the gradient passes where these are > 0
   __nv_bfloat16* out;
-  int64_t n_tiles;                // ceil(n_rows / 127)
-  int64_t n_rows;                 // n_sel * rb
-  int rb;
+  int64_t n_tiles;
+  int tiles_per_beam, rb;
   int* err;
 };
 // Hidden 64 -> 64 layer on the tensor cores: forward (bias, ReLU) or backward-data.

@@ -15,12 +15,12 @@
 //  - k_sur_input: layer 0 from the rendering. The input is sparse (two hits per beam,
 //    each splatted onto two bins), so each position sums the few taps that touch it.
 //  - k_conv<MODE>: a hidden 64 -> 64 layer as an implicit GEMM on tcgen05. M = 128
-//    rows, N = 128 = two taps x 64 output channels, K = 64 input channels per tap pair.
-//    The 136 input rows a tile needs are staged once by TMA (128-byte swizzle); tap pair
-//    j reads them through a matrix descriptor that starts 2j rows later (20 MMAs of
-//    K = 16 per tile of 127 output rows). The weights of all taps stay in shared memory.
-//    MODE 0 is the forward layer (bias, ReLU); MODE 1 the backward-data pass (the
-//    transposed, tap-reversed weights, and the previous layer's ReLU mask).
+//    positions, N = 64 output channels, K = 9 taps x 64 input channels. The 136 input
+//    rows a tile needs are staged once by TMA (128-byte swizzle); tap k reads them
+//    through a matrix descriptor that starts k rows later (36 MMAs of K = 16 per tile).
+//    The weights of all taps stay in shared memory. MODE 0 is the forward layer (bias,
+//    ReLU); MODE 1 the backward-data pass (the transposed, tap-reversed weights, and the
+//    previous layer's ReLU mask).
 //  - k_dw: a hidden layer's weight gradient dW_k[o][c] = sum_p dz[p][o] x[p + k - 4][c]
 //    on tcgen05. M = 128 = (tap parity, output channel): tensor memory holds the dz
 //    window as the A operand, rows 64..127 shifted one position, so one MMA makes two
@@ -115,8 +115,8 @@ __global__ void k_sur_pack(SurNet n, int update, float lr, float b1, float b2, f
     n.w_out[ci * KT + k] = __bfloat162float(h);
   } else {
     const int L = l - 1;
-    n.wf[((int64_t)(L * (KT + 1) + k) * C + co) * C + ci] = h;
-    n.wb[((int64_t)(L * (KT + 1) + (KT - 1 - k)) * C + ci) * C + co] = h;
+    n.wf[((int64_t)(L * KT + k) * C + co) * C + ci] = h;
+    n.wb[((int64_t)(L * KT + (KT - 1 - k)) * C + ci) * C + co] = h;
   }
 }
 
@@ -171,22 +171,13 @@ __global__ void __launch_bounds__(256) k_sur_input(const float* feat, const int3
 }
 
 // ----------------------------------------------------------------- hidden layers (tcgen05)
-// Tap pairs on N: the MMA of pair j multiplies the input rows shifted by 2j against
-// [W_2j; W_2j+1] stacked as N = 128 output columns. Row i of the tile then accumulates
-// the even taps of output row R0 + i in columns 0..63 and the odd taps of output row
-// R0 + i - 1 in columns 64..127, so output row R0 + i is even[i] + odd[i + 1]: 20 MMAs of
-// N = 128 make 127 output rows (36 MMAs of N = 64 would make 128, and a small MMA costs
-// nearly as long to issue as a large one). Tiles of 127 rows run over the whole row
-// range of the buffer, zero rows included; the epilogue writes only the bin rows.
 constexpr int kConvThreads = 192;   // warp 0 TMA, warp 1 MMA, warps 2..5 epilogue
 constexpr int kConvStages = 4;
-constexpr int kConvRing = 4;        // TMEM accumulators of 128 columns
-constexpr int kTileOut = 127;       // output rows per tile
+constexpr int kConvRing = 4;        // TMEM accumulators of 64 columns
 constexpr int kStageRows = 128 + KT - 1;
 constexpr int kStageBytes = 18432;  // 136 rows x 128 bytes, rounded up to 1 KB
-constexpr int kTapsPad = KT + 1;    // tap 9 is zero: five tap pairs
-constexpr int kWBytes = kTapsPad * C * 128;
-constexpr size_t kConvSmem = 1024 + kWBytes + (size_t)kConvStages * kStageBytes + 2 * 4 * 32 * 4 + 256;
+constexpr int kWBytes = KT * C * 128;
+constexpr size_t kConvSmem = 1024 + kWBytes + (size_t)kConvStages * kStageBytes + 256;
 static_assert(kStageRows * 128 <= kStageBytes, "stage holds a tile and its halo");
 
 template <int MODE>
@@ -195,16 +186,13 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv(const __grid_constant_
   uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   uint8_t* sW = smem;
   uint8_t* sA = smem + kWBytes;
-  // [2][4][32]: lane 0's odd sums per quarter, double-buffered across exchanges
-  float* sx = reinterpret_cast<float*>(sA + kConvStages * kStageBytes);
-  uint64_t* full = reinterpret_cast<uint64_t*>(sx + 2 * 4 * 32);
+  uint64_t* full = reinterpret_cast<uint64_t*>(sA + kConvStages * kStageBytes);
   uint64_t* empty = full + kConvStages;
   uint64_t* acc_full = empty + kConvStages;
   uint64_t* acc_empty = acc_full + kConvRing;
   uint64_t* wfull = acc_empty + kConvRing;
   uint64_t* done = wfull + 1;
-  uint64_t* xch = done + 1;  // the four epilogue warps' exchange writes, one phase per exchange
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(xch + 1);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -218,11 +206,10 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv(const __grid_constant_
     }
     mbar_init(smem_u32(wfull), 1);
     mbar_init(smem_u32(done), 1);
-    mbar_init(smem_u32(xch), 4);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 1) tmem_alloc(tmem_slot, kConvRing * 128);
+  if (warp == 1) tmem_alloc(tmem_slot, kConvRing * 64);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -233,16 +220,18 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv(const __grid_constant_
     if (lane == 0) {
       // ---------------------------------------------------------- TMA producer
       mbar_expect_tx(smem_u32(wfull), kWBytes);
-      for (int k = 0; k < kTapsPad; ++k) tma_load_2d(smem_u32(sW + k * C * 128), &a.map_w, 0, k * C, smem_u32(wfull));
+      for (int k = 0; k < KT; ++k) tma_load_2d(smem_u32(sW + k * C * 128), &a.map_w, 0, k * C, smem_u32(wfull));
       int it = 0;
       for (int64_t t = t_first; t < a.n_tiles; t += t_step, ++it) {
         const int s = it % kConvStages;
         if (it >= kConvStages &&
             !wait_or_abort(smem_u32(&empty[s]), ((it / kConvStages) & 1) ^ 1, abort_flag, a.err))
           break;
+        const int64_t beam = t / a.tiles_per_beam;
+        const int p0 = (int)(t % a.tiles_per_beam) * 128;
         mbar_expect_tx(smem_u32(&full[s]), kStageRows * 128);
-        // rows R0 - 4 .. R0 + 131; a negative start reads zeros
-        tma_load_2d(smem_u32(sA + s * kStageBytes), &a.map_x, 0, (int)(t * kTileOut - KT / 2), smem_u32(&full[s]));
+        tma_load_2d(smem_u32(sA + s * kStageBytes), &a.map_x, 0, (int)(beam * a.rb + HALO + p0 - KT / 2),
+                    smem_u32(&full[s]));
       }
       // every copy this thread issued has landed before the CTA may exit
       for (int s = 0; s < kConvStages && s < it; ++s) {
@@ -254,7 +243,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv(const __grid_constant_
   } else if (warp == 1) {
     if (lane == 0) {
       // ---------------------------------------------------------- MMA issuer
-      const uint32_t idesc = make_idesc(1, 128, 128);
+      const uint32_t idesc = make_idesc(1, 128, 64);
       bool ok = wait_or_abort(smem_u32(wfull), 0, abort_flag, a.err);
       int it = 0;
       const uint32_t wbase = smem_u32(sW);
@@ -264,14 +253,14 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv(const __grid_constant_
         if (it >= kConvRing && !wait_or_abort(smem_u32(&acc_empty[r]), ((it / kConvRing) & 1) ^ 1, abort_flag, a.err))
           break;
         tc_fence_after();
-        const uint32_t d = tmem_base + (uint32_t)(r * 128);
+        const uint32_t d = tmem_base + (uint32_t)(r * 64);
         const uint32_t abase = smem_u32(sA + s * kStageBytes);
 #pragma unroll 1
-        for (int j = 0; j < kTapsPad / 2; ++j) {
+        for (int k = 0; k < KT; ++k) {
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk)
-            tc_mma(d, shifted_desc(abase, 2 * j, kk * 32), sw128_desc(wbase + 2 * j * C * 128 + kk * 32), idesc,
-                   (j | kk) ? 1u : 0u);
+            tc_mma(d, shifted_desc(abase, k, kk * 32), sw128_desc(wbase + k * C * 128 + kk * 32), idesc,
+                   (k | kk) ? 1u : 0u);
         }
         tc_commit(smem_u32(&empty[s]));
         tc_commit(smem_u32(&acc_full[r]));
@@ -287,70 +276,50 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv(const __grid_constant_
       const int r = it % kConvRing;
       if (!wait_or_abort(smem_u32(&acc_full[r]), (it / kConvRing) & 1, abort_flag, a.err)) break;
       tc_fence_after();
-      const int i = q * 32 + lane;             // tile row
-      const int64_t R = t * kTileOut + i;      // output row of even[i] + odd[i + 1]
-      const int64_t rr = R % a.rb;
-      const bool write = i < kTileOut && R < a.n_rows && rr >= HALO && rr < a.rb - HALO;
-      const uint32_t ta = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(r * 128);
-      uint4* dst = reinterpret_cast<uint4*>(a.out + R * C);
-#pragma unroll 1
-      for (int h = 0; h < 2; ++h) {
-        uint32_t ev[32], od[32];
-        TMEM_LD_32(ta + 32 * h, ev);
-        TMEM_LD_32(ta + 64 + 32 * h, od);
-        tmem_ld_wait();
-        // lane 0's odd sums go to the quarter below (row 32 q - 1), through one of two
-        // buffers: exchange e writes buffer e & 1 once all four warps have passed the
-        // wait of exchange e - 1, i.e. have read buffer (e - 1) & 1, and a warp writes
-        // exchange e + 1 only after its own reads of exchange e
-        const int e = 2 * it + h;
-        float* xb = sx + (e & 1) * 4 * 32;
-        if (lane == 0) {
-#pragma unroll
-          for (int c = 0; c < 32; ++c) xb[q * 32 + c] = __uint_as_float(od[c]);
-        }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(smem_u32(xch));
-        if (!wait_or_abort(smem_u32(xch), e & 1, abort_flag, a.err)) break;
-        float f[32];
-#pragma unroll
-        for (int c = 0; c < 32; ++c) {
-          float nxt = __shfl_down_sync(0xffffffffu, __uint_as_float(od[c]), 1);
-          if (lane == 31) nxt = xb[((q + 1) & 3) * 32 + c];
-          f[c] = __uint_as_float(ev[c]) + nxt;
-        }
-        if (write) {
-          if (MODE == 0) {
-#pragma unroll
-            for (int c = 0; c < 32; ++c) f[c] = fmaxf(f[c] + __ldg(&a.bias[32 * h + c]), 0.f);
-          } else {
-            const uint4* mk = reinterpret_cast<const uint4*>(a.mask + R * C) + 4 * h;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-              const uint4 m = __ldg(&mk[j]);
-              const uint32_t mw[4] = {m.x, m.y, m.z, m.w};
-#pragma unroll
-              for (int e = 0; e < 4; ++e) {
-                if (!(bf_lo(mw[e]) > 0.f)) f[8 * j + 2 * e] = 0.f;
-                if (!(bf_hi(mw[e]) > 0.f)) f[8 * j + 2 * e + 1] = 0.f;
-              }
-            }
-          }
-#pragma unroll
-          for (int j = 0; j < 4; ++j)
-            dst[4 * h + j] = make_uint4(pack_bf16(f[8 * j], f[8 * j + 1]), pack_bf16(f[8 * j + 2], f[8 * j + 3]),
-                                        pack_bf16(f[8 * j + 4], f[8 * j + 5]), pack_bf16(f[8 * j + 6], f[8 * j + 7]));
-        }
-      }
+      uint32_t v0[32], v1[32];
+      const uint32_t ta = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(r * 64);
+      TMEM_LD_32(ta, v0);
+      TMEM_LD_32(ta + 32, v1);
+      tmem_ld_wait();
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&acc_empty[r]));
+      const int64_t beam = t / a.tiles_per_beam;
+      const int p = (int)(t % a.tiles_per_beam) * 128 + q * 32 + lane;
+      const int64_t row = beam * a.rb + HALO + p;
+      uint4* dst = reinterpret_cast<uint4*>(a.out + row * C);
+      float f[C];
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        f[c] = __uint_as_float(v0[c]);
+        f[32 + c] = __uint_as_float(v1[c]);
+      }
+      if (MODE == 0) {
+#pragma unroll
+        for (int c = 0; c < C; ++c) f[c] = fmaxf(f[c] + __ldg(&a.bias[c]), 0.f);
+      } else {
+        const uint4* mk = reinterpret_cast<const uint4*>(a.mask + row * C);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const uint4 m = __ldg(&mk[j]);
+          const uint32_t mw[4] = {m.x, m.y, m.z, m.w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            if (!(bf_lo(mw[e]) > 0.f)) f[8 * j + 2 * e] = 0.f;
+            if (!(bf_hi(mw[e]) > 0.f)) f[8 * j + 2 * e + 1] = 0.f;
+          }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        dst[j] = make_uint4(pack_bf16(f[8 * j], f[8 * j + 1]), pack_bf16(f[8 * j + 2], f[8 * j + 3]),
+                            pack_bf16(f[8 * j + 4], f[8 * j + 5]), pack_bf16(f[8 * j + 6], f[8 * j + 7]));
     }
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 1) tmem_free(tmem_base, kConvRing * 128);
+  if (warp == 1) tmem_free(tmem_base, kConvRing * 64);
 }
 
 // ----------------------------------------------------------------- hidden-layer weight gradient
