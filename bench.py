@@ -424,6 +424,8 @@ def run_ours(args, ws, rank, local):
            "stage_rooflines": stage_rooflines(mean_stage, params, stats, args.precision, pk),
            "scene_upload_ms": upload_ms,
            "hits_per_ping": stats["n_hits"],
+           "tiles": {"beamform_tile_n": stats["tile_n"], "synth_cols": stats["synth_cols"],
+                     "autotuned": bool(stats["autotuned"])},
            "gpu_launches": launches,
            "timing": "graph replay per ping (the default path), steps enqueued back to back, CUDA events "
                      "around each step, L2 flushed between steps outside the events",
@@ -616,7 +618,8 @@ def other_forms(torch, s, inputs, dev):
         torch.cuda.synchronize()
         st = s.stats()
         out[f"c4_batch64_{prec}"] = {"value": reps * len(poses4) / (time.perf_counter() - t0), "unit": UNIT,
-                                     "hits_total": st["n_hits"]}
+                                     "hits_total": st["n_hits"], "beamform_tile_n": st["tile_n"],
+                                     "synth_cols": st["synth_cols"], "autotuned": bool(st["autotuned"])}
         del env
     s.upload(scene)
     return out
