@@ -63,6 +63,8 @@ def lib():
         _lib.orc_raw.argtypes = [vp, vp, i32, i32, vp, i64, vp]
         _lib.orc_pulse.argtypes = [d, d, d, vp, vp]
         _lib.orc_beamform.argtypes = [vp, d, vp, vp, i64, vp, i64, vp]
+        _lib.orc_synth_wb.argtypes = [vp, vp, d, vp, i64, vp]
+        _lib.orc_ttd.argtypes = [vp, vp, vp, vp, i64, vp, i64, vp]
         _lib.orc_envelope.argtypes = [vp, vp, vp, i64, i64, vp]
         _lib.orc_peaks.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         _lib.orc_peaks.restype = i64
@@ -331,3 +333,87 @@ def eigen_arc(ssp: dict, o, x):
     if rc != 0:
         raise RuntimeError("eigen_arc failed")
     return d, t.value, s.value
+
+
+def synth_wideband(params: dict, hits: dict, ns, shift: float = 0.0) -> np.ndarray:
+    """Wideband element echoes s_m(t_n + shift): the plane-wave delay u_k . p_m / c across
+    the aperture in the envelope as well as in the phase. complex128 [len(ns), M]."""
+    ns = np.ascontiguousarray(ns, np.int32)
+    M = params["nx"] * params["ny"]
+    out = np.zeros((len(ns), M, 2), np.float64)
+    hs, keep = _hits_struct(hits)
+    lib().orc_synth_wb(C.byref(make_params(params)), C.byref(hs), float(shift), _ptr(ns), len(ns), _ptr(out))
+    return out[..., 0] + 1j * out[..., 1]
+
+
+def ttd_exact(params: dict, hits: dict, ns, beams, taper=None) -> np.ndarray:
+    """True-time-delay beams of the wideband echoes, exact in time: complex128
+    [len(beams), len(ns)]."""
+    ns = np.ascontiguousarray(ns, np.int32)
+    beams = np.ascontiguousarray(beams, np.int32)
+    out = np.zeros((len(beams), len(ns), 2), np.float64)
+    hs, keep = _hits_struct(hits)
+    tp = None if taper is None else np.ascontiguousarray(taper, np.float32)
+    lib().orc_ttd(C.byref(make_params(params)), C.byref(hs), _ptr(tp), _ptr(ns), len(ns), _ptr(beams), len(beams),
+                  _ptr(out))
+    return out[..., 0] + 1j * out[..., 1]
+
+
+def ttd_levels(params: dict, c_ref: float, U: int) -> tuple:
+    """The fractional-delay grid of the true-time-delay beamformer: per (beam, element)
+    the steering delay -u_b . p_m / c in units of dt / U, x [Nb, M], and the level range
+    Q (levels q = -Q .. Q cover floor(x) - 1 .. floor(x) + 2 for every pair)."""
+    nba, nbe, nx, ny = params["n_beam_az"], params["n_beam_el"], params["nx"], params["ny"]
+    dt = 2.0 * (params["r_max"] - params["r_min"]) / params["n_range"] / c_ref
+    i, j = np.arange(nba), np.arange(nbe)
+    az = -params["hfov"] / 2 + (i + 0.5) * params["hfov"] / nba
+    el = -params["vfov"] / 2 + (j + 0.5) * params["vfov"] / nbe
+    uy = (np.cos(el)[:, None] * np.sin(az)[None, :]).ravel()
+    uz = np.repeat(np.sin(el), nba)
+    m = np.arange(nx * ny)
+    ym = (m % nx - (nx - 1) / 2.0) * params["pitch"]
+    zm = (m // nx - (ny - 1) / 2.0) * params["pitch"]
+    x = -(uy[:, None] * ym[None, :] + uz[:, None] * zm[None, :]) / c_ref / (dt / U)
+    Q = int(np.ceil(np.abs(x).max())) + 2
+    return x, Q
+
+
+def lagrange4(y) -> np.ndarray:
+    """The 4-point Lagrange interpolation kernel: the weight of a sample at distance y
+    (in samples) from the point read; cubic pieces on |y| < 1 and 1 <= |y| < 2, zero
+    beyond; reproduces cubic polynomials exactly."""
+    a = np.abs(np.asarray(y, np.float64))
+    return np.where(a < 1.0, (a * a - 1.0) * (a - 2.0) / 2.0,
+                    np.where(a < 2.0, -(a - 1.0) * (a - 2.0) * (a - 3.0) / 6.0, 0.0))
+
+
+def ttd_interpolated(params: dict, hits: dict, ns, U: int, beams=None, taper=None) -> np.ndarray:
+    """True-time-delay beams as the fractional-delay beamformer forms them: each element's
+    wideband echo read at its steering delay by 4-point Lagrange interpolation between the
+    samples of a grid U times finer than the range grid,
+    B[b][n] = sum_m W[b][m] sum_q h(x_bm - q) s_m(t_n + q dt / U) with h = lagrange4 and W
+    the phase-shift weights. complex128 [len(beams), len(ns)]."""
+    nb = params["n_beam_az"] * params["n_beam_el"]
+    beams = np.arange(nb) if beams is None else np.asarray(beams)
+    c_ref = hits["c_ref"]
+    x, Q = ttd_levels(params, c_ref, U)
+    dt = 2.0 * (params["r_max"] - params["r_min"]) / params["n_range"] / c_ref
+    M = params["nx"] * params["ny"]
+    w = np.ones(M) if taper is None else np.asarray(taper, np.float64).ravel()
+    m = np.arange(M)
+    ym = (m % params["nx"] - (params["nx"] - 1) / 2.0) * params["pitch"]
+    zm = (m // params["nx"] - (params["ny"] - 1) / 2.0) * params["pitch"]
+    ka = 2 * math.pi * params["f0"] / c_ref
+    nba = params["n_beam_az"]
+    out = np.zeros((len(beams), len(ns)), np.complex128)
+    for q in range(-Q, Q + 1):
+        s_q = synth_wideband(params, hits, ns, shift=q * dt / U)  # [n, M]
+        for a, b in enumerate(beams):
+            i, j = b % nba, b // nba
+            az = -params["hfov"] / 2 + (i + 0.5) * params["hfov"] / nba
+            el = -params["vfov"] / 2 + (j + 0.5) * params["vfov"] / params["n_beam_el"]
+            uy, uz = math.cos(el) * math.sin(az), math.sin(el)
+            Wb = w * np.exp(-1j * ka * (uy * ym + uz * zm)) / w.sum()
+            hq = lagrange4(x[b] - q)
+            out[a] += s_q @ (Wb * hq)
+    return out

@@ -1212,6 +1212,36 @@ void orc_raw(const orc_params* p, const orc_hits* h, int32_t U, int32_t s, const
   synth_core(p, h, ns, n_ns, 1, s * dt / U, s_out);
 }
 
+/* Wideband element echoes: the plane-wave delay across the aperture kept in the envelope
+   as well as in the phase. An element at p_m hears a hit arriving from u_k earlier by
+   u_k . p_m / c, so s_m(t) = sum_k c_k R(t - tau_k + u_k . p_m / c) exp(j k_a u_k . p_m),
+   evaluated at t = t_n + shift for the requested samples n. */
+void orc_synth_wb(const orc_params* p, const orc_hits* h, double shift, const int32_t* ns, int64_t n_ns,
+                  double* s_out) {
+  const int32_t nx = p->nx, ny = p->ny, M = nx * ny;
+  const double c_ref = h->c_ref, dr = (p->r_max - p->r_min) / p->n_range;
+  const double ka = TWO_PI * p->f0 / c_ref;
+  memset(s_out, 0, sizeof(double) * 2 * (size_t)M * (size_t)n_ns);
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int32_t m = 0; m < M; ++m) {
+    int32_t mx = m % nx, my = m / nx;
+    double ym = (mx - (nx - 1) / 2.0) * p->pitch, zm = (my - (ny - 1) / 2.0) * p->pitch;
+    for (int64_t k = 0; k < h->n; ++k) {
+      double up = h->uy[k] * ym + h->uz[k] * zm;  /* u_k . p_m (the array lies in the y-z plane) */
+      cplx ck = (h->cr[k] + I * h->ci[k]) * cexp(I * ka * up);
+      for (int64_t i = 0; i < n_ns; ++i) {
+        double u = 2.0 * (p->r_min + (ns[i] + 0.5) * dr) / c_ref + shift - h->tau[k] + up / c_ref;
+        if (!(fabs(u) < p->pulse)) continue;
+        double re, im;
+        orc_pulse_acf(u, p->pulse, p->bw, &re, &im);
+        cplx v = ck * (re + I * im);
+        s_out[2 * ((size_t)i * M + m)] += creal(v);
+        s_out[2 * ((size_t)i * M + m) + 1] += cimag(v);
+      }
+    }
+  }
+}
+
 /* Beam directions (Sec. III Eq. 2-3, cell-centred): az_i = -HFOV/2 + (i+1/2) HFOV/N_az,
    el_j likewise, b = j N_az + i, u_b = (cos el cos az, cos el sin az, sin el). */
 static void beam_dir(const orc_params* p, int32_t b, double u[3]) {
@@ -1254,6 +1284,49 @@ void orc_beamform(const orc_params* p, double c_ref, const float* taper, const d
     }
   }
   free(W);
+}
+
+/* True-time-delay beamforming of the wideband echoes, exact in time: each element is
+   read at its steering delay, B[b][n] = sum_m w_m exp(-j k_a u_b . p_m)
+   s_m(t_n - u_b . p_m / c) / sum_m w_m, evaluated from the hits as
+   sum_k c_k sum_m w_m exp(j k_a (u_k - u_b) . p_m) R(t_n - tau_k + (u_k - u_b) . p_m / c)
+   / sum_m w_m. */
+void orc_ttd(const orc_params* p, const orc_hits* h, const float* taper, const int32_t* ns, int64_t n_ns,
+             const int32_t* beams, int64_t n_beams, double* b_out) {
+  const int32_t nx = p->nx, ny = p->ny, M = nx * ny;
+  const double c_ref = h->c_ref, dr = (p->r_max - p->r_min) / p->n_range;
+  const double ka = TWO_PI * p->f0 / c_ref;
+  double wsum = 0;
+  for (int32_t m = 0; m < M; ++m) wsum += taper ? taper[m] : 1.0;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t bi = 0; bi < n_beams; ++bi) {
+    double ub[3];
+    beam_dir(p, beams[bi], ub);
+    for (int64_t i = 0; i < n_ns; ++i) {
+      const double tn = 2.0 * (p->r_min + (ns[i] + 0.5) * dr) / c_ref;
+      cplx acc = 0;
+      for (int64_t k = 0; k < h->n; ++k) {
+        /* the delays across the array are below the aperture over c: skip hits whose
+           pulse cannot reach t_n from any element */
+        if (!(fabs(tn - h->tau[k]) < p->pulse + 2.0 * (nx + ny) * p->pitch / c_ref)) continue;
+        const cplx ck = h->cr[k] + I * h->ci[k];
+        const double dy = h->uy[k] - ub[1], dz = h->uz[k] - ub[2];
+        for (int32_t m = 0; m < M; ++m) {
+          int32_t mx = m % nx, my = m / nx;
+          double ym = (mx - (nx - 1) / 2.0) * p->pitch, zm = (my - (ny - 1) / 2.0) * p->pitch;
+          double dp = dy * ym + dz * zm;
+          double u = tn - h->tau[k] + dp / c_ref;
+          if (!(fabs(u) < p->pulse)) continue;
+          double re, im;
+          orc_pulse_acf(u, p->pulse, p->bw, &re, &im);
+          acc += (taper ? taper[m] : 1.0) * ck * cexp(I * ka * dp) * (re + I * im);
+        }
+      }
+      acc /= wsum;
+      b_out[2 * ((size_t)bi * n_ns + i)] = creal(acc);
+      b_out[2 * ((size_t)bi * n_ns + i) + 1] = cimag(acc);
+    }
+  }
 }
 
 /* Envelope with time-varied gain TVG(r) = r exp(2 alpha r), r_n at bin centres. */

@@ -103,6 +103,15 @@ void orc_raw(const orc_params* p, const orc_hits* h, int32_t U, int32_t s, const
 void orc_synth(const orc_params* p, const orc_hits* h, const int32_t* ns, int64_t n_ns,
                double* s_out);
 
+/* Wideband element echoes (plane-wave delay u_k . p_m / c in the envelope and the phase)
+   at t_n + shift: out[n_ns][M][2]. */
+void orc_synth_wb(const orc_params* p, const orc_hits* h, double shift, const int32_t* ns, int64_t n_ns,
+                  double* s_out);
+/* True-time-delay beamforming of the wideband echoes, exact in time, from the hits:
+   b_out[n_beams][n_ns][2]. */
+void orc_ttd(const orc_params* p, const orc_hits* h, const float* taper, const int32_t* ns, int64_t n_ns,
+             const int32_t* beams, int64_t n_beams, double* b_out);
+
 /* Beams B[b][i] = sum_m w_m e^{-j k u_b.p_m} s_m[ns_i] / sum w, for beams[0..n_beams). */
 void orc_beamform(const orc_params* p, double c_ref, const float* taper,
                   const double* s, int64_t n_ns, const int32_t* beams, int64_t n_beams,

@@ -170,6 +170,8 @@ struct sonar_ctx {
   float2* ptab = nullptr;   // raw series: U shifted pulse tables (both grids), then the matched-filter taps
   int ptab_u = 0, ptab_d = 0;
   float* taper_dev = nullptr;
+  double2* beam_uyz = nullptr;  // beam-centre direction cosines of the steering matrix
+  int64_t beam_uyz_cap = 0;
   double y_gain = 1.0;
 
   // workspaces
@@ -589,7 +591,19 @@ int ensure_tables(sonar_ctx* ctx, const sonar_params* p, const Derived& d) {
       CU(cudaMemcpyAsync(ctx->taper_dev, p->taper, sizeof(float) * d.M, cudaMemcpyHostToDevice, ctx->stream));
     }
     ctx->y_gain = d.wsum / d.wmax;  // steering entries scaled to at most 1
+    std::vector<double2> uyz((size_t)d.nb);
+    for (int b = 0; b < d.nb; ++b) {
+      const int bi = b % p->n_beam_az, bj = b / p->n_beam_az;
+      const double az = -p->hfov_rad / 2 + (bi + 0.5) * p->hfov_rad / p->n_beam_az;
+      const double el = -p->vfov_rad / 2 + (bj + 0.5) * p->vfov_rad / p->n_beam_el;
+      uyz[(size_t)b] = make_double2(cos(el) * sin(az), sin(el));
+    }
+    int rc;
+    if ((rc = grow(ctx, ctx->beam_uyz, ctx->beam_uyz_cap, d.nb, sizeof(double2), false))) return rc;
+    CU(cudaMemcpyAsync(ctx->beam_uyz, uyz.data(), sizeof(double2) * d.nb, cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));  // the host table is released on return
     SteerArgs sa;
+    sa.beam_uyz = ctx->beam_uyz;
     sa.nx = p->nx; sa.ny = p->ny; sa.n_beam_az = p->n_beam_az; sa.n_beam_el = p->n_beam_el;
     sa.nb_pad = d.nb_pad; sa.k_pad = d.k_pad; sa.hfov = p->hfov_rad; sa.vfov = p->vfov_rad;
     sa.pitch_over_lambda = d.pitch_over_lambda; sa.taper = ctx->taper_dev; sa.wsum = d.wsum;
@@ -1751,6 +1765,7 @@ int sonar_destroy(sonar_ctx* c) {
   if (c->stream) cudaStreamDestroy(c->stream);
   free_scene(c);
   dfree(c->ray_dirs); dfree(c->ray_dirs32); dfree(c->row_domega); dfree(c->y_hi); dfree(c->y_lo); dfree(c->rtab); dfree(c->taper_dev);
+  dfree(c->beam_uyz);
   if (c->pose_host) cudaFreeHost(c->pose_host);
   if (c->n_cloud_host) cudaFreeHost(c->n_cloud_host);
   if (c->counters_host) cudaFreeHost(c->counters_host);

@@ -264,7 +264,9 @@ static_assert(gemm_smem<256, 3>() <= 227 * 1024 && gemm_smem<256, 1>() <= 227 * 
 
 // ----------------------------------------------------------------- steering matrix
 // W[b][m] = w_m exp(-j k_a u_b . p_m) / sum w, beams cell-centred (Sec. III Eq. 2-3),
-// scaled by `gain`; phase in FP64 cycles reduced modulo one before the FP32 sincos.
+// scaled by `gain`; phase in FP64 cycles reduced modulo one before the FP32 sincos. The
+// beam directions come from a per-beam table (FP64 trigonometry once per beam, not once
+// per entry: FP64 transcendentals are slow on this part).
 __global__ void k_steer(SteerArgs a) {
   const int64_t rows = 2LL * a.nb_pad;
   const int64_t total = rows * a.k_pad;
@@ -276,10 +278,8 @@ __global__ void k_steer(SteerArgs a) {
     const int m = k / 2, cpart = k % 2;
     float val = 0.f;
     if (b < Nb && m < M) {
-      const int bi = b % a.n_beam_az, bj = b / a.n_beam_az;
-      const double az = -a.hfov / 2 + (bi + 0.5) * a.hfov / a.n_beam_az;
-      const double el = -a.vfov / 2 + (bj + 0.5) * a.vfov / a.n_beam_el;
-      const double uy = cos(el) * sin(az), uz = sin(el);
+      const double2 u = a.beam_uyz[b];  // the beam centre's direction cosines, once per beam
+      const double uy = u.x, uz = u.y;
       const int mx = m % a.nx, my = m / a.nx;
       const double cyc = a.pitch_over_lambda * ((mx - 0.5 * (a.nx - 1)) * uy + (my - 0.5 * (a.ny - 1)) * uz);
       const double fr = cyc - floor(cyc);

@@ -338,6 +338,7 @@ cudaError_t launch_convert(const ConvertArgs& a, int sm_count, cudaStream_t st);
 struct SteerArgs {
   int32_t nx, ny, n_beam_az, n_beam_el, nb_pad, k_pad;
   double hfov, vfov, pitch_over_lambda;
+  const double2* beam_uyz;  // [n_beams] sonar-frame (u_y, u_z) of each beam centre, FP64
   const float* taper;       // device [M] or null
   double wsum, gain;
   int32_t mode;

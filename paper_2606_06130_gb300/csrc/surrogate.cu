@@ -32,6 +32,8 @@
 //  - k_sur_l1_dw: layer 0's gradient from the sparse input.
 //  - k_sur_pack: Adam (Kingma & Ba 2015) and the BF16 weight copies.
 //  - k_cmp_*: the metrics that compare a surrogate volume with the plain method's.
+#include <limits.h>
+
 #include "common.cuh"
 #include "tcgen05.cuh"
 
@@ -131,26 +133,43 @@ __global__ void __launch_bounds__(256) k_sur_input(const float* feat, const int3
                                                    int nr, double r_min, double inv_dr, const float* w_in,
                                                    const float* b_in, __nv_bfloat16* act, int rb, int* err) {
   // grid: x over (bin, channel group) of one beam, y over beams
+  // the beam's splat positions, in FP64 once per block (FP64 work per thread is slow
+  // on this part): first bin and fraction of each hit, n0 = INT_MIN for no hit
+  __shared__ int s_n0[2];
+  __shared__ float s_fr[2];
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int g = t & 7;  // channels 8 g .. 8 g + 7
   const int p = t >> 3;
   const int64_t i = i0 + blockIdx.y;
   const int64_t beam = beams ? (int64_t)beams[i] : i;
+  const bool valid = beam >= 0 && beam < n_feat;
+  const float4* f4 = reinterpret_cast<const float4*>(feat + (valid ? beam : 0) * 8);
+  if (threadIdx.x < 2) {
+    const float L = __ldg(&f4[threadIdx.x]).x;
+    int n0 = INT_MIN;
+    float fr = 0.f;
+    if (valid && L > 0.f) {
+      const double x = ((double)L - r_min) * inv_dr - 0.5;
+      const double fl = floor(x);
+      n0 = (int)fl;
+      fr = (float)(x - fl);
+    }
+    s_n0[threadIdx.x] = n0;
+    s_fr[threadIdx.x] = fr;
+  }
+  __syncthreads();
   float z[8];
 #pragma unroll
   for (int c = 0; c < 8; ++c) z[c] = __ldg(&b_in[8 * g + c]);
-  if (beam < 0 || beam >= n_feat) {
+  if (!valid) {
     if (g == 0 && p == 0) atomicOr(err, kErrIndex);
   } else {
-    const float4* f4 = reinterpret_cast<const float4*>(feat + beam * 8);
     for (int h = 0; h < 2; ++h) {
-      const float4 f = __ldg(&f4[h]);
-      if (!(f.x > 0.f)) continue;
-      const double x = ((double)f.x - r_min) * inv_dr - 0.5;
-      const double fl = floor(x);
-      const int n0 = (int)fl;
+      const int n0 = s_n0[h];
+      if (n0 == INT_MIN) continue;
       if (n0 + 1 < p - KT / 2 || n0 > p + KT / 2) continue;  // no splat reaches this bin
-      const float fr = (float)(x - fl);
+      const float4 f = __ldg(&f4[h]);
+      const float fr = s_fr[h];
       for (int e = 0; e < 2; ++e) {
         const int q = n0 + e;
         const int k = q - p + KT / 2;
@@ -686,8 +705,10 @@ __global__ void __launch_bounds__(64) k_sur_l1_dw(const float* feat, const int32
 // pulse-autocorrelation table (entry i at u = -T + 2 T i / n_tab), interpolated linearly.
 __global__ void __launch_bounds__(256) k_sur_geometric(const float* feat, int64_t n_beams, int nba, int nbe,
                                                        double hfov, double vfov, int nr, double r_min, double dr,
-                                                       double c_ref, double alpha, double T, const float2* rtab,
-                                                       int n_tab, float* env) {
+                                                       double two_inv_c, double alpha, double T, double tab_scale,
+                                                       const float2* rtab, int n_tab, float* env) {
+  // one thread per (beam, bin); FP64 only for the delay difference (multiplies and adds:
+  // the reciprocals two_inv_c = 2 / c_ref and tab_scale = n_tab / (2 T) come from the host)
   const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (gid >= n_beams * nr) return;
   const int64_t b = gid / nr;
@@ -696,15 +717,15 @@ __global__ void __launch_bounds__(256) k_sur_geometric(const float* feat, int64_
   const float del = (float)(vfov / nbe), el_lo = (float)(-vfov / 2) + j * del;
   const float domega = (float)(hfov / nba) * (sinf(el_lo + del) - sinf(el_lo));
   const double r = r_min + (n + 0.5) * dr;
-  const double t = 2.0 * r / c_ref;
+  const double t = r * two_inv_c;
   const float4* f4 = reinterpret_cast<const float4*>(feat + b * 8);
   float e = 0.f;
   for (int h = 0; h < 2; ++h) {
     const float4 f = f4[h];
     if (!(f.x > 0.f)) continue;
-    const double u = t - 2.0 * (double)f.x / c_ref;
+    const double u = t - (double)f.x * two_inv_c;
     if (!(fabs(u) < T)) continue;
-    const double x = (u + T) / (2.0 * T) * n_tab;
+    const double x = (u + T) * tab_scale;
     int i = (int)floor(x);
     if (i >= n_tab) i = n_tab - 1;
     const float w = (float)(x - i);
@@ -888,7 +909,8 @@ cudaError_t sur_geometric(const float* feat, int64_t n_beams, int nba, int nbe, 
   const int64_t total = n_beams * nr;
   if (total == 0) return cudaSuccess;
   k_sur_geometric<<<(unsigned)ceil_div(total, 256), 256, 0, st>>>(feat, n_beams, nba, nbe, hfov, vfov, nr, r_min, dr,
-                                                                   c_ref, alpha, T, rtab, n_tab, env);
+                                                                   2.0 / c_ref, alpha, T, n_tab / (2.0 * T), rtab, n_tab,
+                                                                   env);
   return cudaGetLastError();
 }
 
