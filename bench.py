@@ -525,6 +525,59 @@ def stage_rooflines(mean_stage, params, stats, precision, pk):
     return out
 
 
+def ttd_form(torch, s, params, poses, ssp, U):
+    """True-time-delay beams of the headline ping: wideband echoes at U phases per range
+    cell, each beam reading every element at its steering delay (4-point Lagrange
+    interpolation), pings/s and the stage times. The beamforming contraction runs over
+    all fractional-delay levels; its algorithmic work is the 4 taps per (beam, element,
+    sample) of the interpolating beamformer."""
+    from paper_2606_06130_gb300.sonar import SONAR_OPT_TTD, SONAR_OPT_TIMING
+    s.set_option(SONAR_OPT_TTD, U)
+    try:
+        for _ in range(2):
+            s.ping(poses[0], params, ssp, precision="fp32")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(5):
+            s.ping(poses[0], params, ssp, precision="fp32")
+        torch.cuda.synchronize()
+        rate = 5 / (time.perf_counter() - t0)
+        s.set_option(SONAR_OPT_TIMING, 1)
+        stages = []
+        for _ in range(3):
+            s.ping(poses[0], params, ssp, precision="fp32")
+            torch.cuda.synchronize()
+            stages.append(s.stats())
+        s.set_option(SONAR_OPT_TIMING, 0)
+    finally:
+        s.set_option(SONAR_OPT_TTD, 0)
+    st = {k: float(np.median([x["ms_" + k] for x in stages]))
+          for k in ("trace", "bin", "synth", "convert", "beamform", "peaks")}
+    M = params["nx"] * params["ny"]
+    nb = params["n_beam_az"] * params["n_beam_el"]
+    nr = params["n_range"]
+    # the levels the library forms: floor(x) - 1 .. floor(x) + 2 over every (beam, element)
+    c = ssp["c"][0]
+    dt = 2.0 * (params["r_max"] - params["r_min"]) / nr / c
+    cx, cy = (params["nx"] - 1) / 2, (params["ny"] - 1) / 2
+    i, j = np.arange(params["n_beam_az"]), np.arange(params["n_beam_el"])
+    az = -params["hfov"] / 2 + (i + 0.5) * params["hfov"] / params["n_beam_az"]
+    el = -params["vfov"] / 2 + (j + 0.5) * params["vfov"] / params["n_beam_el"]
+    uy = (np.cos(el)[:, None] * np.sin(az)[None, :]).ravel()
+    uz = np.repeat(np.sin(el), params["n_beam_az"])
+    x = [-U * params["pitch"] * (uy * a + uz * b) / (c * dt) for a in (-cx, cx) for b in (-cy, cy)]
+    levels = int(np.floor(np.max(x))) + 2 - (int(np.floor(min(np.min(x), 0.0))) - 1) + 1
+    flop_alg = 8.0 * nb * M * nr * 4
+    flop_exec = 8.0 * nb * M * nr * levels * 3
+    tf = flop_exec / (st["beamform"] / 1e3) / 1e12
+    return {"value": rate, "unit": UNIT, "U": U, "levels": levels, "stages_ms": st,
+            "beamform": {"executed_flop": flop_exec, "algorithmic_flop": flop_alg, "executed_tflops": tf,
+                         "algorithmic_tflops": flop_alg / (st["beamform"] / 1e3) / 1e12},
+            "note": f"true-time-delay beams: wideband echoes at {U} phases per range cell (SIMT synthesis, "
+                    "per-element envelope delays), 4-point Lagrange fractional delays as extra K blocks of the "
+                    "tensor-core beamforming contraction"}
+
+
 def other_forms(torch, s, inputs, dev):
     out = {}
     scene, params, poses, ssp = inputs.workload("c2")
@@ -550,6 +603,7 @@ def other_forms(torch, s, inputs, dev):
     out["c2_raw_u4_fp32"] = {"value": 10 / (time.perf_counter() - t0), "unit": UNIT,
                              "note": "raw chirp echoes at 4 samples per range cell + matched filter"}
     s.set_option(SONAR_OPT_RAW, 0)
+    out["c2_ttd_u4_fp32"] = ttd_form(torch, s, params, poses, ssp, 4)
     # out/back cross-term multipath (every reflected route also returns straight)
     from paper_2606_06130_gb300.sonar import SONAR_OPT_CROSS
     s.set_option(SONAR_OPT_CROSS, 1)
@@ -681,6 +735,22 @@ def run_surrogate_forms(args):
     print(json.dumps({"surrogate_forms": out}), flush=True)
 
 
+def run_ttd_form(args):
+    """--ttd U: only the true-time-delay form of the headline ping (the profiling command
+    of its kernels)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2606_06130_gb300 import inputs
+    from paper_2606_06130_gb300.sonar import Sonar
+    torch.cuda.set_device(0)
+    scene, params, poses, ssp = inputs.workload("c2")
+    s = Sonar(0)
+    s.upload(scene)
+    out = ttd_form(torch, s, params, poses, ssp, args.ttd)
+    print(json.dumps({f"c2_ttd_u{args.ttd}_fp32": out}), flush=True)
+
+
 def cpu_model() -> str:
     try:
         out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
@@ -793,7 +863,12 @@ def main():
                          "held-out pings (one JSON line; not part of the default run)")
     ap.add_argument("--surrogate-forms", action="store_true",
                     help="time only the learned surrogate's forms (training step, inference, geometric envelope)")
+    ap.add_argument("--ttd", type=int, default=0,
+                    help="time only the true-time-delay form of the headline ping at this many phases per cell")
     args = ap.parse_args()
+    if args.ttd > 0:
+        run_ttd_form(args)
+        return
     if args.surrogate_train > 0:
         run_surrogate_training(args)
         return

@@ -220,6 +220,24 @@ SONAR_API const char* sonar_last_error(const sonar_ctx* ctx);
    visited when any lane's ray overlaps it. Both give the same hits. Any other value:
    SONAR_E_ARG. */
 #define SONAR_OPT_TRAVERSAL 10
+/* SONAR_OPT_TTD: 0 (default) forms phase-shift beams (Sec. II.B coherent summation:
+   one phase per element and beam). U = 1..8 forms true-time-delay beams instead, for
+   wide apertures in range- and depth-dependent settings (Sec. II.A): the element echoes
+   are synthesised wideband, with the plane-wave delay u_k . p_m / c of each hit across
+   the aperture kept in the envelope as well as in the carrier phase,
+     s_m(t) = sum_k c_k exp(j k_a u_k . p_m) R(t - tau_k + u_k . p_m / c),
+   at U phases t_n + s dt / U per range cell, and each beam reads every element at its
+   own steering delay -u_b . p_m / c by 4-point Lagrange interpolation on that grid:
+     B_b(t_n) = sum_m W_bm sum_q h(x_bm - q) s_m(t_n + q dt / U),
+   x_bm = -U u_b . p_m / (c dt), h the Lagrange kernel and W_bm the phase-shift weights.
+   The interpolation error falls with the fourth power of the grid spacing (about 4e-4
+   of the beam energy at U = 4 on a 20 us range grid). The levels q run as extra
+   column blocks of the steering operand, so the beamformer stays one tensor-core
+   contraction, its K dimension (levels) times longer; sonar_get_raw returns the
+   wideband phases and sonar_get_echoes phase 0. FP32 and BF16 forms only, at most 64 x
+   64 elements, not with SONAR_OPT_RAW (SONAR_E_UNSUPPORTED at the ping); any other
+   value: SONAR_E_ARG. */
+#define SONAR_OPT_TTD 11
 SONAR_API int sonar_set_option(sonar_ctx* ctx, int32_t option, int64_t value);
 
 /* ---------------------------------------------------------------- scene */
@@ -325,7 +343,9 @@ SONAR_API int sonar_get_hits(sonar_ctx* ctx, sonar_hit* host_out, int64_t cap, i
 SONAR_API int sonar_get_echoes(sonar_ctx* ctx, float* host_out, int64_t cap_floats);
 /* Raw element series of the last call, phase s of SONAR_OPT_RAW = U (requires
    SONAR_OPT_DEBUG and a ping with U > 0): r_m(t_n + s dt / U), host
-   [n_pings][n_range][ny*nx][2] f32. SONAR_E_ARG for a phase outside [0, U). */
+   [n_pings][n_range][ny*nx][2] f32; after a true-time-delay ping (SONAR_OPT_TTD = U)
+   the wideband element echoes s_m(t_n + s dt / U) instead. SONAR_E_ARG for a phase
+   outside [0, U). */
 SONAR_API int sonar_get_raw(sonar_ctx* ctx, int32_t phase, float* host_out, int64_t cap_floats);
 SONAR_API int sonar_get_stats(const sonar_ctx* ctx, sonar_stats* out);
 

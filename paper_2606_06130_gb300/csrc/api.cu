@@ -73,6 +73,13 @@ struct Derived {
   double c_ref, dr, dt, t0, hw, T_stop, pitch_over_lambda, ssp_z0, ssp_c0, ssp_g, wsum, wmax;
   int taps, nr, nr_pad, nr_x, M, k_pad, nb, nb_pad, tile_n, n_phase, n_blank, n_routes, curved;
   int64_t n_subrays, hit_cap_per_ping;
+  // true-time delay: fractional-delay levels q0 .. q0 + levels - 1 (steering delays in
+  // units of dt / U), guard rows of the echo operand per ping, the wideband synthesis
+  // window (wt rows from e1 before a hit's first tap) and its table (n_tab entries, uf
+  // per range sample, f per phase, v_lo the first entry's position in samples, x0 the
+  // entry of a window's first row at u0 = 0, phase 0 and no element delay)
+  int ttd_q0 = 0, ttd_levels = 1, ttd_guard = 0, wb_wt = 0, wb_e1 = 0, wb_uf = 0, wb_f = 0, wb_n_tab = 0;
+  double wb_v_lo = 0.0, wb_x0 = 0.0, ttd_x_scale = 0.0;
 };
 
 // One of the two in-flight slots of asynchronous pings: its own pinned pose record,
@@ -124,6 +131,8 @@ struct sonar_ctx {
   int cur_tile_n = 0, cur_pairs = 0;  // the choice in force for the current call (0: heuristic)
   bool cur_tuned = false;
   int raw_u = 0;      // 0: compressed synthesis; U > 0: raw series at U samples per cell + matched filter
+  int ttd_u = 0;      // 0: phase-shift beams; U > 0: true-time-delay beams from wideband echoes at U phases
+  int last_ttd_u = 0;
   int bvh_opt = 0;    // 0: binned-SAH hierarchy (host build), 1: Morton-order LBVH (device build)
   int cross = 0;      // 1: out/back cross-term multipath
   int traversal = 0;  // straight rays: 0 one sub-ray per thread, 1 warp-cooperative
@@ -168,6 +177,8 @@ struct sonar_ctx {
   size_t y_elems = 0;
   float2* rtab = nullptr;
   float2* ptab = nullptr;   // raw series: U shifted pulse tables (both grids), then the matched-filter taps
+  float4* wtab = nullptr;   // true-time delay: the wideband synthesis table
+  std::vector<uint8_t> wtab_key;
   int ptab_u = 0, ptab_d = 0;
   float* taper_dev = nullptr;
   double2* beam_uyz = nullptr;  // beam-centre direction cosines of the steering matrix
@@ -358,6 +369,60 @@ double field_c_host(const sonar_field& f, const double* c, double x, double z) {
          (1.0 - u) * v * c[(j + 1) * f.nx + i] + u * v * c[(j + 1) * f.nx + i + 1];
 }
 
+// The true-time-delay plan (Sec. II.A wide apertures: per-element delays across the
+// array). Steering delays x = -U (u_b . p_m) / (c dt) in units of dt / U are linear in
+// the element indices, so their extremes over the array sit at its corners; the levels
+// floor(x) - 1 .. floor(x) + 2 of every (beam, element) pair span q0 .. q0 + levels - 1.
+// The wideband synthesis window covers every row a hit's pulse can reach at any element
+// and phase: with the hit's first-tap offset u0 in (-hw, -hw + 1], phase offsets s / U <=
+// (U - 1) / U and element delays |e| <= emax = pitch sqrt(cx^2 + cy^2) / (c dt) (the
+// largest |u . p_m| / (c dt) over unit directions), row i relative to the first tap is
+// reached only for -E1 <= i <= E2.
+int derive_ttd(sonar_ctx* ctx, const sonar_params* p, Derived& d) {
+  const int U = ctx->ttd_u;
+  if (ctx->raw_u > 0) return fail(ctx, SONAR_E_UNSUPPORTED, "true-time delay and raw series are exclusive");
+  if (p->precision == SONAR_FP16) return fail(ctx, SONAR_E_UNSUPPORTED, "true-time delay takes the FP32 or BF16 form");
+  if (p->nx > 64 || p->ny > 64) return fail(ctx, SONAR_E_UNSUPPORTED, "true-time delay: at most 64 x 64 elements");
+  const double cx = 0.5 * (p->nx - 1), cy = 0.5 * (p->ny - 1);
+  d.ttd_x_scale = U * p->pitch_m / (d.c_ref * d.dt);
+  double xmin = 0.0, xmax = 0.0;
+  for (int b = 0; b < p->n_beam_az * p->n_beam_el; ++b) {
+    const int bi = b % p->n_beam_az, bj = b / p->n_beam_az;
+    const double az = -p->hfov_rad / 2 + (bi + 0.5) * p->hfov_rad / p->n_beam_az;
+    const double el = -p->vfov_rad / 2 + (bj + 0.5) * p->vfov_rad / p->n_beam_el;
+    const double uy = cos(el) * sin(az), uz = sin(el);
+    for (int c = 0; c < 4; ++c) {
+      const double ym = (c & 1) ? cx : -cx, zm = (c & 2) ? cy : -cy;
+      const double x = -d.ttd_x_scale * (uy * ym + uz * zm);
+      xmin = fmin(xmin, x);
+      xmax = fmax(xmax, x);
+    }
+  }
+  d.ttd_q0 = (int)floor(xmin) - 1;
+  d.ttd_levels = (int)floor(xmax) + 2 - d.ttd_q0 + 1;
+  auto floor_div = [](int q, int u) { return (q - (((q % u) + u) % u)) / u; };
+  d.ttd_guard = std::max(-floor_div(d.ttd_q0, U), floor_div(d.ttd_q0 + d.ttd_levels - 1, U));
+  if (d.ttd_guard > kPad) return fail(ctx, SONAR_E_UNSUPPORTED, "true-time delays span more than %d range samples", kPad);
+  const double emax = p->pitch_m * sqrt(cx * cx + cy * cy) / (d.c_ref * d.dt);
+  const int E1 = (int)ceil(1.0 + (U - 1.0) / U + emax) - 1;
+  const int E2 = (int)ceil(2.0 * d.hw + emax) - 1;
+  const int need = E1 + E2 + 1 + 2;  // one row of slack on either side
+  d.wb_wt = need <= 12 ? 12 : need <= 16 ? 16 : need <= 20 ? 20 : need <= 24 ? 24 : 0;
+  if (!d.wb_wt)
+    return fail(ctx, SONAR_E_UNSUPPORTED, "true-time delay: pulse and aperture delays span %d range samples, at most 22",
+                need - 2);
+  d.wb_e1 = E1 + 1;
+  d.wb_f = (128 + U - 1) / U;
+  d.wb_uf = U * d.wb_f;
+  d.wb_v_lo = -d.hw - d.wb_e1 - emax - 1.0;
+  const double v_hi = -d.hw + 1.0 + (d.wb_wt - 1 - d.wb_e1) + (U - 1.0) / U + emax + 1.0;
+  d.wb_n_tab = (int)ceil((v_hi - d.wb_v_lo) * d.wb_uf) + 2;
+  d.wb_x0 = (-d.wb_e1 - d.wb_v_lo) * d.wb_uf;
+  const int64_t smem = (int64_t)d.wb_n_tab * 16 + 32LL * (p->nx + p->ny) * 12 + 256;
+  if (smem > 160 * 1024) return fail(ctx, SONAR_E_UNSUPPORTED, "true-time delay: synthesis table too large");
+  return SONAR_OK;
+}
+
 int derive(sonar_ctx* ctx, const sonar_params* p, const sonar_ssp* ssp, double x_sonar, double z_sonar, int n_pings,
            Derived& d) {
   d.ssp_z0 = 0.0;
@@ -395,6 +460,10 @@ int derive(sonar_ctx* ctx, const sonar_params* p, const sonar_ssp* ssp, double x
   if (d.taps > 16)
     return fail(ctx, SONAR_E_UNSUPPORTED, "pulse spans %d range samples; at most 16 are supported", d.taps);
   d.T_stop = p->r_max_m / d.c_ref + p->pulse_s / 2.0;
+  if (ctx->ttd_u > 0) {
+    const int rc = derive_ttd(ctx, p, d);
+    if (rc) return rc;
+  }
   d.pitch_over_lambda = p->pitch_m * p->f0_hz / d.c_ref;
   d.nr_pad = d.nr + 2 * kPad;
   d.nr_x = (int)round_up(d.nr, 128);
@@ -571,13 +640,25 @@ int ensure_tables(sonar_ctx* ctx, const sonar_params* p, const Derived& d) {
       ctx->ptab_key = k;
     }
   }
+  if (ctx->ttd_u > 0) {
+    k.clear();
+    key_add(k, p->pulse_s); key_add(k, p->bw_hz); key_add(k, d.dt); key_add(k, d.wb_v_lo); key_add(k, d.wb_uf);
+    key_add(k, d.wb_n_tab);
+    if (k != ctx->wtab_key) {
+      dfree(ctx->wtab);
+      CU(cudaMalloc(&ctx->wtab, sizeof(float4) * d.wb_n_tab));
+      CU(launch_wtab(ctx->wtab, d.wb_n_tab, d.wb_v_lo, 1.0 / d.wb_uf, d.dt, p->pulse_s, p->bw_hz, ctx->stream));
+      ctx->wtab_key = k;
+    }
+  }
   k.clear();
   key_add(k, p->nx); key_add(k, p->ny); key_add(k, d.pitch_over_lambda); key_add(k, p->hfov_rad);
   key_add(k, p->vfov_rad); key_add(k, p->n_beam_az); key_add(k, p->n_beam_el); key_add(k, p->precision);
-  key_add(k, d.tile_n);
+  key_add(k, d.tile_n); key_add(k, ctx->ttd_u); key_add(k, d.ttd_q0); key_add(k, d.ttd_levels);
+  key_add(k, d.ttd_x_scale);
   for (int m = 0; m < d.M; ++m) key_add(k, p->taper ? p->taper[m] : 1.0f);
   if (k != ctx->steer_key) {
-    size_t elems = (size_t)2 * d.nb_pad * d.k_pad;
+    size_t elems = (size_t)2 * d.nb_pad * d.k_pad * d.ttd_levels;
     if (elems != ctx->y_elems) {
       dfree(ctx->y_hi);
       dfree(ctx->y_lo);
@@ -608,6 +689,7 @@ int ensure_tables(sonar_ctx* ctx, const sonar_params* p, const Derived& d) {
     sa.nb_pad = d.nb_pad; sa.k_pad = d.k_pad; sa.hfov = p->hfov_rad; sa.vfov = p->vfov_rad;
     sa.pitch_over_lambda = d.pitch_over_lambda; sa.taper = ctx->taper_dev; sa.wsum = d.wsum;
     sa.gain = ctx->y_gain; sa.mode = p->precision; sa.y_hi = ctx->y_hi; sa.y_lo = ctx->y_lo;
+    sa.n_levels = d.ttd_levels; sa.q0 = d.ttd_q0; sa.ttd = ctx->ttd_u > 0; sa.x_scale = d.ttd_x_scale;
     CU(launch_steer(sa, ctx->stream));
     ctx->steer_key = k;
   }
@@ -685,13 +767,17 @@ int ensure_workspace(sonar_ctx* ctx, int P, const Derived& d) {
     ctx->ws_s = s_need;
   }
   ctx->s_elems = s_need;
-  if (ctx->raw_u > 0 && (s_need * ctx->raw_u > ctx->ws_raw || !ctx->S_raw)) {
+  const int phases = ctx->raw_u > 0 ? ctx->raw_u : ctx->ttd_u;
+  if (phases > 0 && (s_need * phases > ctx->ws_raw || !ctx->S_raw)) {
     int64_t c0 = 0;
     dfree(ctx->S_raw);
-    if ((rc = grow(ctx, ctx->S_raw, c0, s_need * ctx->raw_u, sizeof(float2), false))) return rc;
-    ctx->ws_raw = s_need * ctx->raw_u;
+    if ((rc = grow(ctx, ctx->S_raw, c0, s_need * phases, sizeof(float2), false))) return rc;
+    ctx->ws_raw = s_need * phases;
   }
-  int64_t x_need = (int64_t)P * d.nr_x * d.k_pad;
+  // true-time delay: the echo operand holds every phase, each ping's rows with guard rows
+  // on either side for the level offsets
+  int64_t x_need = ctx->ttd_u > 0 ? (int64_t)ctx->ttd_u * P * (d.nr_x + 2 * d.ttd_guard) * d.k_pad
+                                  : (int64_t)P * d.nr_x * d.k_pad;
   if (x_need != ctx->ws_x || !ctx->x_hi) {
     int64_t c0 = 0, c1 = 0;
     dfree(ctx->x_hi); dfree(ctx->x_lo);
@@ -842,8 +928,9 @@ int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, cons
   // every buffer that starts at zero is cleared up front, in one launch, so the kernels
   // run back to back
   const int32_t n_bins = P * d.nr_pad;
-  k_clear<<<4 * ctx->sm_count, 256, 0, st>>>(ctx->S, ctx->s_elems, ctx->raw_u > 0 ? ctx->S_raw : nullptr,
-                                             ctx->s_elems * ctx->raw_u, ctx->counts, n_bins, ctx->keys,
+  const int phases = ctx->raw_u > 0 ? ctx->raw_u : ctx->ttd_u;
+  k_clear<<<4 * ctx->sm_count, 256, 0, st>>>(ctx->S, ctx->s_elems, phases > 0 ? ctx->S_raw : nullptr,
+                                             ctx->s_elems * phases, ctx->counts, n_bins, ctx->keys,
                                              (int64_t)P * d.nb, ctx->pmax, P, ctx->n_hits, ctx->err_dev,
                                              reinterpret_cast<const uint4*>(o.pose_src),
                                              reinterpret_cast<uint4*>(ctx->poses), (int)(sizeof(DevPose) / 16) * P);
@@ -878,7 +965,28 @@ int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, cons
   static const int kPairs[5] = {0, 0, 32, 64, 96};
   const bool tc = ctx->synth_opt != 1 && synth_tc_supported(p->nx, p->ny, d.taps);
   const int want_pairs = ctx->synth_opt >= 2 ? kPairs[ctx->synth_opt] : ctx->cur_pairs;
-  if (ctx->raw_u == 0) {
+  if (ctx->ttd_u > 0) {
+    // wideband echoes at the U phases, the element delays kept in the envelope
+    SynthWbArgs wa;
+    wa.hits_sorted = ctx->sorted;
+    wa.n_valid = ctx->offsets + n_bins;
+    wa.tab = ctx->wtab;
+    wa.n_tab = d.wb_n_tab;
+    wa.uf = d.wb_uf;
+    wa.f = d.wb_f;
+    wa.tab_x0 = (float)d.wb_x0;
+    wa.e1 = d.wb_e1;
+    wa.n_phases = ctx->ttd_u;
+    wa.nx = p->nx;
+    wa.ny = p->ny;
+    wa.pitch_over_lambda = (float)d.pitch_over_lambda;
+    wa.pitch_uf = (float)(p->pitch_m / (d.c_ref * d.dt) * d.wb_uf);
+    wa.S = ctx->S_raw;
+    wa.phase_stride = ctx->s_elems;
+    wa.total_rows = (int64_t)P * d.nr_pad;
+    wa.err = ctx->err_dev;
+    CU(launch_synth_wb(wa, d.wb_wt, ctx->sm_count, st));
+  } else if (ctx->raw_u == 0) {
     if (tc) CU(launch_synth_tc(sa, want_pairs, ctx->sm_count, st));
     else CU(launch_synth(sa, ctx->sm_count, st));
   } else {
@@ -908,8 +1016,14 @@ int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, cons
     CU(launch_mfilter(ma, st));
   }
   mark(3);
+  const bool ttd = ctx->ttd_u > 0;
+  const int x_rows = ttd ? d.nr_x + 2 * d.ttd_guard : d.nr_x;
   ConvertArgs ca;
-  ca.S = ctx->S;
+  ca.S = ttd ? ctx->S_raw : ctx->S;
+  ca.phase_stride = ttd ? ctx->s_elems : 0;
+  ca.n_phases = ttd ? ctx->ttd_u : 1;
+  ca.x_rows = x_rows;
+  ca.x_guard = ttd ? d.ttd_guard : 0;
   ca.n_pings = P;
   ca.nr = d.nr;
   ca.nr_pad = d.nr_pad;
@@ -927,13 +1041,21 @@ int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, cons
   const bool f16 = fp16;
   int rc;
   const int box_k = d.n_phase == 3 ? 32 : 64;
-  if ((rc = make_map(ctx, &ga.map_xh, ctx->x_hi, (int64_t)P * d.nr_x, d.k_pad, 128, f16, box_k))) return rc;
-  if ((rc = make_map(ctx, &ga.map_xl, ctx->x_lo, (int64_t)P * d.nr_x, d.k_pad, 128, f16, box_k))) return rc;
-  if ((rc = make_map(ctx, &ga.map_yh, ctx->y_hi, 2LL * d.nb_pad, d.k_pad, d.tile_n, f16, box_k))) return rc;
-  if ((rc = make_map(ctx, &ga.map_yl, ctx->y_lo, 2LL * d.nb_pad, d.k_pad, d.tile_n, f16, box_k))) return rc;
+  const int64_t x_map_rows = (int64_t)ca.n_phases * P * x_rows;
+  const int64_t y_cols = (int64_t)d.k_pad * d.ttd_levels;
+  if ((rc = make_map(ctx, &ga.map_xh, ctx->x_hi, x_map_rows, d.k_pad, 128, f16, box_k))) return rc;
+  if ((rc = make_map(ctx, &ga.map_xl, ctx->x_lo, x_map_rows, d.k_pad, 128, f16, box_k))) return rc;
+  if ((rc = make_map(ctx, &ga.map_yh, ctx->y_hi, 2LL * d.nb_pad, y_cols, d.tile_n, f16, box_k))) return rc;
+  if ((rc = make_map(ctx, &ga.map_yl, ctx->y_lo, 2LL * d.nb_pad, y_cols, d.tile_n, f16, box_k))) return rc;
   ga.tiles_m = P * d.nr_x / 128;
   ga.tiles_n = 2 * d.nb_pad / d.tile_n;
-  ga.k_blocks = d.k_pad / 64;
+  ga.k_blocks = (int)(y_cols / 64);
+  ga.x_kpad = d.k_pad;
+  ga.ttd_u = ctx->ttd_u;
+  ga.ttd_q0 = d.ttd_q0;
+  ga.x_ping_rows = x_rows;
+  ga.x_guard = ttd ? d.ttd_guard : 0;
+  ga.x_phase_rows = P * x_rows;
   ga.n_phase = d.n_phase;
   ga.tile_n = d.tile_n;
   ga.f16 = f16 ? 1 : 0;
@@ -1060,7 +1182,7 @@ std::vector<uint8_t> pipeline_key(const sonar_ctx* ctx, int P, const sonar_param
   key_add(k, o.env_host); key_add(k, o.cloud_host); key_add(k, o.pose_src); key_add(k, o.counters_map);
   key_add(k, o.n_cloud_map);
   key_add(k, ctx->debug); key_add(k, ctx->timing); key_add(k, ctx->synth_opt); key_add(k, ctx->scene_version);
-  key_add(k, ctx->raw_u);
+  key_add(k, ctx->raw_u); key_add(k, ctx->ttd_u);
   key_add(k, d.c_ref);
   key_add(k, d.tile_n); key_add(k, ctx->cur_pairs);
   if (ssp) {
@@ -1080,7 +1202,7 @@ std::vector<uint8_t> pipeline_key(const sonar_ctx* ctx, int P, const sonar_param
 std::vector<uint8_t> tune_key(const sonar_ctx* ctx, int P, const sonar_params* p) {
   std::vector<uint8_t> k;
   key_add(k, P); key_add(k, p->n_range); key_add(k, p->n_beam_az); key_add(k, p->n_beam_el);
-  key_add(k, p->nx); key_add(k, p->ny); key_add(k, p->precision); key_add(k, ctx->raw_u);
+  key_add(k, p->nx); key_add(k, p->ny); key_add(k, p->precision); key_add(k, ctx->raw_u); key_add(k, ctx->ttd_u);
   key_add(k, p->pulse_s); key_add(k, p->r_max_m - p->r_min_m); key_add(k, ctx->tile_opt); key_add(k, ctx->synth_opt);
   return k;
 }
@@ -1280,7 +1402,8 @@ int run(sonar_ctx* ctx, const sonar_pose* poses, int P, const sonar_params* p, c
   const int errw = (int)ctx->counters_host[1];
   ctx->last_p = P;
   ctx->last_d = d;
-  ctx->last_raw_u = ctx->raw_u;
+  ctx->last_raw_u = ctx->raw_u > 0 ? ctx->raw_u : ctx->ttd_u;
+  ctx->last_ttd_u = ctx->ttd_u;
   ctx->last_params = *p;
   ctx->stats.n_hits = (int64_t)nh;
   ctx->stats.hit_capacity = ctx->hit_cap;
@@ -1419,7 +1542,8 @@ int run_async(sonar_ctx* ctx, const sonar_pose* poses, int P, const sonar_params
   sl.cloud_given = cloud_cap > 0 || cloud;
   ctx->last_p = P;
   ctx->last_d = d;
-  ctx->last_raw_u = ctx->raw_u;
+  ctx->last_raw_u = ctx->raw_u > 0 ? ctx->raw_u : ctx->ttd_u;
+  ctx->last_ttd_u = ctx->ttd_u;
   ctx->last_params = *p;
   ctx->stats.hit_capacity = ctx->hit_cap;
   ctx->stats.n_pings = P;
@@ -1614,7 +1738,8 @@ int sonar_create(sonar_ctx** out, int device, void* cuda_stream) {
   if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return SONAR_E_CUDA;
   if (!(prop.major == 10 && prop.minor == 3)) return SONAR_E_UNSUPPORTED;
   if (cudaSetDevice(device) != cudaSuccess) return SONAR_E_CUDA;
-  if (prepare_gemm() != cudaSuccess || prepare_synth_tc() != cudaSuccess || sur_conv_prepare() != cudaSuccess)
+  if (prepare_gemm() != cudaSuccess || prepare_synth_tc() != cudaSuccess || sur_conv_prepare() != cudaSuccess ||
+      prepare_synth_wb() != cudaSuccess)
     return SONAR_E_CUDA;
   sonar_ctx* c = new (std::nothrow) sonar_ctx();
   if (!c) return SONAR_E_NOMEM;
@@ -1657,6 +1782,10 @@ int sonar_set_option(sonar_ctx* ctx, int32_t option, int64_t value) {
     case SONAR_OPT_RAW:
       if (value < 0 || value > 8) return fail(ctx, SONAR_E_ARG, "raw series: 0 (off) or 1 to 8 samples per cell");
       ctx->raw_u = (int)value;
+      break;
+    case SONAR_OPT_TTD:
+      if (value < 0 || value > 8) return fail(ctx, SONAR_E_ARG, "true-time delay: 0 (off) or 1 to 8 phases per cell");
+      ctx->ttd_u = (int)value;
       break;
     case SONAR_OPT_BVH:
       if (value != 0 && value != 1) return fail(ctx, SONAR_E_ARG, "BVH build: 0 (SAH) or 1 (Morton order)");
@@ -1772,7 +1901,7 @@ int sonar_destroy(sonar_ctx* c) {
   dfree(c->pt_route); dfree(c->vol_order); dfree(c->fld_c);
   dfree(c->poses); dfree(c->hits); dfree(c->sorted); dfree(c->sorted_n); dfree(c->dbg_tau);
   dfree(c->n_hits);
-  dfree(c->counts); dfree(c->offsets); dfree(c->S); dfree(c->S_raw); dfree(c->ptab); dfree(c->x_hi); dfree(c->x_lo); dfree(c->gain);
+  dfree(c->counts); dfree(c->offsets); dfree(c->S); dfree(c->S_raw); dfree(c->ptab); dfree(c->wtab); dfree(c->x_hi); dfree(c->x_lo); dfree(c->gain);
   dfree(c->env_stage); dfree(c->keys); dfree(c->pmax); dfree(c->cloud_stage); dfree(c->n_cloud_dev); dfree(c->err_dev); dfree(c->synth_bounds);
   auto& S = c->sur;
   dfree(S.params); dfree(S.wbf); dfree(S.wsmall); dfree(S.loss); dfree(S.feat); dfree(S.poses); dfree(S.buf); dfree(S.g);
@@ -1922,8 +2051,10 @@ int sonar_get_echoes(sonar_ctx* ctx, float* out, int64_t cap_floats) {
   const int64_t per_ping = (int64_t)d.nr * d.M * 2;
   if (cap_floats < per_ping * ctx->last_p) return fail(ctx, SONAR_E_CAPACITY, "need %lld floats", (long long)(per_ping * ctx->last_p));
   CU(cudaSetDevice(ctx->device));
+  // true-time delay: the wideband echoes at the range samples (phase 0)
+  const float2* S = ctx->last_ttd_u > 0 ? ctx->S_raw : ctx->S;
   for (int p = 0; p < ctx->last_p; ++p) {
-    const float2* src = ctx->S + ((int64_t)p * d.nr_pad + kPad) * d.M;
+    const float2* src = S + ((int64_t)p * d.nr_pad + kPad) * d.M;
     CU(cudaMemcpyAsync(out + p * per_ping, src, sizeof(float) * per_ping, cudaMemcpyDeviceToHost, ctx->stream));
   }
   CU(cudaStreamSynchronize(ctx->stream));

@@ -119,17 +119,32 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant_
       for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
         int mb, nb;
         tile_coords(t, a.tiles_m, a.tiles_n, mb, nb);
+        // the tile's first X row: ping p's block of x_ping_rows rows, past its guard rows
+        const int row0 = mb * BM, p = row0 / a.nr_x;
+        const int y_tile = p * a.x_ping_rows + a.x_guard + (row0 - p * a.nr_x);
+        int xk = 0, lvl = 0, y = y_tile;  // K position inside the level, the level, its X row
+        if (a.ttd_u > 0) {
+          const int q = a.ttd_q0, s = ((q % a.ttd_u) + a.ttd_u) % a.ttd_u;
+          y = y_tile + s * a.x_phase_rows + (q - s) / a.ttd_u;
+        }
         for (int kb = 0; kb < k_iters && ok; ++kb) {
           if (!mbar_wait(smem_u32(&empty[stage]), phase ^ 1, a.err)) { ok = false; break; }
           const uint32_t fb = smem_u32(&full[stage]);
           mbar_expect_tx(fb, PARTS * (A_BYTES + B_BYTES));
           uint8_t* const a_st = sA + stage * PARTS * A_BYTES;
           uint8_t* const b_st = sB + stage * PARTS * B_BYTES;
-          tma_load_2d(smem_u32(a_st), &a.map_xh, kb * BK, mb * BM, fb);
+          tma_load_2d(smem_u32(a_st), &a.map_xh, xk, y, fb);
           tma_load_2d(smem_u32(b_st), &a.map_yh, kb * BK, nb * BN, fb);
           if (PARTS == 2) {
-            tma_load_2d(smem_u32(a_st + A_BYTES), &a.map_xl, kb * BK, mb * BM, fb);
+            tma_load_2d(smem_u32(a_st + A_BYTES), &a.map_xl, xk, y, fb);
             tma_load_2d(smem_u32(b_st + B_BYTES), &a.map_yl, kb * BK, nb * BN, fb);
+          }
+          xk += BK;
+          if (xk == a.x_kpad && a.ttd_u > 0) {
+            // next fractional-delay level: phase q mod U, row offset floor(q / U)
+            xk = 0;
+            const int q = a.ttd_q0 + (++lvl), s = ((q % a.ttd_u) + a.ttd_u) % a.ttd_u;
+            y = y_tile + s * a.x_phase_rows + (q - s) / a.ttd_u;
           }
           ++issued;
           if (++stage == STAGES) { stage = 0; phase ^= 1; }
@@ -267,13 +282,26 @@ static_assert(gemm_smem<256, 3>() <= 227 * 1024 && gemm_smem<256, 1>() <= 227 * 
 // scaled by `gain`; phase in FP64 cycles reduced modulo one before the FP32 sincos. The
 // beam directions come from a per-beam table (FP64 trigonometry once per beam, not once
 // per entry: FP64 transcendentals are slow on this part).
+// With true-time delay (ttd != 0) the columns form n_levels blocks of k_pad, one per
+// fractional-delay level q = q0 + block, each entry weighted by the 4-point Lagrange
+// kernel h(x - q) at the pair's steering delay x (units of dt / U).
+__device__ __forceinline__ double lagrange4(double y) {
+  const double t = fabs(y);
+  if (t < 1.0) return (t * t - 1.0) * (t - 2.0) * 0.5;
+  if (t < 2.0) return -(t - 1.0) * (t - 2.0) * (t - 3.0) / 6.0;
+  return 0.0;
+}
+
 __global__ void k_steer(SteerArgs a) {
   const int64_t rows = 2LL * a.nb_pad;
-  const int64_t total = rows * a.k_pad;
+  const int64_t cols = (int64_t)a.n_levels * a.k_pad;
+  const int64_t total = rows * cols;
   const int M = a.nx * a.ny, Nb = a.n_beam_az * a.n_beam_el;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t j = i / a.k_pad;
-    const int k = (int)(i % a.k_pad);
+    const int64_t j = i / cols;
+    const int64_t kk = i - j * cols;
+    const int lvl = (int)(kk / a.k_pad);
+    const int k = (int)(kk - (int64_t)lvl * a.k_pad);
     const int b = (int)(j / 2), part = (int)(j % 2);
     const int m = k / 2, cpart = k % 2;
     float val = 0.f;
@@ -281,11 +309,13 @@ __global__ void k_steer(SteerArgs a) {
       const double2 u = a.beam_uyz[b];  // the beam centre's direction cosines, once per beam
       const double uy = u.x, uz = u.y;
       const int mx = m % a.nx, my = m / a.nx;
-      const double cyc = a.pitch_over_lambda * ((mx - 0.5 * (a.nx - 1)) * uy + (my - 0.5 * (a.ny - 1)) * uz);
+      const double up = (mx - 0.5 * (a.nx - 1)) * uy + (my - 0.5 * (a.ny - 1)) * uz;
+      const double cyc = a.pitch_over_lambda * up;
       const double fr = cyc - floor(cyc);
       float s, c;
       sincospif((float)(2.0 * fr), &s, &c);
-      const double w = (a.taper ? (double)a.taper[m] : 1.0) / a.wsum * a.gain;
+      double w = (a.taper ? (double)a.taper[m] : 1.0) / a.wsum * a.gain;
+      if (a.ttd) w *= lagrange4(-a.x_scale * up - (double)(a.q0 + lvl));
       const float wr = (float)(w * c), wi = (float)(-w * s);  // W = w e^{-j phi}
       if (part == 0) val = cpart == 0 ? wr : -wi;
       else val = cpart == 0 ? wi : wr;
@@ -397,7 +427,7 @@ __global__ void __launch_bounds__(1024) k_peaks(PeakArgs a) {
 }  // namespace
 
 cudaError_t launch_steer(const SteerArgs& a, cudaStream_t st) {
-  k_steer<<<1024, 256, 0, st>>>(a);
+  k_steer<<<a.n_levels > 1 ? 8192 : 1024, 256, 0, st>>>(a);
   return cudaGetLastError();
 }
 

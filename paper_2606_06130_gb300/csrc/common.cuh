@@ -232,6 +232,38 @@ cudaError_t prepare_synth_tc();
 cudaError_t launch_synth_tc(const SynthArgs& a, int want_pairs, int sm_count, cudaStream_t st);
 cudaError_t launch_rtab(float2* rtab, float2* rtab_s, double pulse, double bw, cudaStream_t st);
 
+// Wideband element echoes for true-time-delay beamforming: the plane-wave delay across
+// the aperture kept in the envelope as well as in the carrier phase,
+//   s_m(t) = sum_k c_k exp(j k_a u_k . p_m) R(t - tau_k + u_k . p_m / c),
+// at the U phases t_n + s dt / U. R comes from a table on a grid of dt / (U F) (tab[i] =
+// (R(v_i), R(v_{i+1}) - R(v_i)), v_i = v_lo + i / (U F) samples, zero outside the pulse
+// support), so that every row and phase of one (hit, element) pair reads it at the same
+// interpolation weight.
+struct SynthWbArgs {
+  const HitRec* hits_sorted;
+  const int32_t* n_valid;
+  const float4* tab;
+  int32_t n_tab;            // entries (a multiple of 4 bytes x 4: float4)
+  int32_t uf;               // table entries per range sample, U F
+  int32_t f;                // table entries per phase step, F
+  float tab_x0;             // table index of v = 0 minus e1 rows: (-e1 - v_lo) U F
+  int32_t e1;               // window rows before a hit's first tap row
+  int32_t n_phases;         // U
+  int32_t nx, ny;
+  float pitch_over_lambda;  // element pitch in carrier wavelengths
+  float pitch_uf;           // element pitch in table entries of delay: pitch / (c dt) U F
+  float2* S;                // phase s at S + s phase_stride: [n_pings * nr_pad][M]
+  int64_t phase_stride;
+  int64_t total_rows;
+  int* err;
+};
+// Table of R on the fine grid: n entries, v_i = v_lo + i du (in range samples of dt).
+cudaError_t launch_wtab(float4* tab, int32_t n, double v_lo, double du, double dt, double pulse, double bw,
+                        cudaStream_t st);
+// wt: window rows per hit (12, 16, 20 or 24).
+cudaError_t launch_synth_wb(const SynthWbArgs& a, int wt, int sm_count, cudaStream_t st);
+cudaError_t prepare_synth_wb();
+
 // ------------------------------------------------------------------ learned surrogate
 // Six 1-D convolutions along range (kernel 9, channels 4 -> 64 x 5 -> 1), packed into one
 // FP32 parameter vector layer by layer: W_l [cout][cin][9] then b_l [cout].
@@ -326,23 +358,34 @@ struct MfArgs {
 cudaError_t launch_mfilter(const MfArgs& a, cudaStream_t st);
 
 struct ConvertArgs {
-  const float2* S;          // [n_pings][nr_pad][M]
+  const float2* S;          // [n_phases][n_pings][nr_pad][M], phases phase_stride elements apart
+  int64_t phase_stride;
   int32_t n_pings, nr, nr_pad, nr_x, M, k_pad;
+  // operand rows: per phase and ping x_rows rows, row j holding sample j - x_guard; rows
+  // j < nr + 2 x_guard are written (samples -x_guard .. nr + x_guard - 1). The plain
+  // path: one phase, x_rows = nr_x, x_guard = 0.
+  int32_t n_phases, x_rows, x_guard;
   int32_t mode;             // SONAR_FP32 / BF16 / FP16
   float* gain;              // [n_pings] power-of-two gain applied (FP16), else 1
-  void* x_hi;               // [n_pings * nr_x][k_pad] 16-bit
+  void* x_hi;               // [n_phases * n_pings * x_rows][k_pad] 16-bit
   void* x_lo;               // FP32 form only
 };
 cudaError_t launch_convert(const ConvertArgs& a, int sm_count, cudaStream_t st);
 
 struct SteerArgs {
   int32_t nx, ny, n_beam_az, n_beam_el, nb_pad, k_pad;
+  // true-time delay: n_levels fractional-delay levels q = q0 .. q0 + n_levels - 1, each a
+  // k_pad-wide block of columns weighted by lagrange4(x - q), x = -x_scale (u_y (mx - cx)
+  // + u_z (my - cy)) the steering delay in units of dt / U. Phase-shift beams: n_levels
+  // = 1 and ttd = 0 (weight 1).
+  int32_t n_levels, q0, ttd;
+  double x_scale;
   double hfov, vfov, pitch_over_lambda;
   const double2* beam_uyz;  // [n_beams] sonar-frame (u_y, u_z) of each beam centre, FP64
   const float* taper;       // device [M] or null
   double wsum, gain;
   int32_t mode;
-  void* y_hi;               // [nb_pad*2][k_pad]
+  void* y_hi;               // [nb_pad*2][n_levels * k_pad]
   void* y_lo;
 };
 cudaError_t launch_steer(const SteerArgs& a, cudaStream_t st);
@@ -350,6 +393,12 @@ cudaError_t launch_steer(const SteerArgs& a, cudaStream_t st);
 struct GemmArgs {
   CUtensorMap map_xh, map_xl, map_yh, map_yl;
   int32_t tiles_m, tiles_n, k_blocks, tile_n;  // k_blocks: K / 64
+  // A-operand addressing. The plain path reads row tile mb at X rows mb 128 .. + 127
+  // (x_kpad = K, ttd_u = 0, x_ping_rows = nr_x, x_guard = 0). True-time delay: K runs
+  // over fractional-delay levels q = ttd_q0 + K / x_kpad, and level q reads phase q mod
+  // ttd_u of the echoes at a row offset floor(q / ttd_u): X rows s x_phase_rows + p
+  // x_ping_rows + x_guard + n + floor(q / ttd_u) for the tile's samples n of ping p.
+  int32_t x_kpad, ttd_u, ttd_q0, x_ping_rows, x_guard, x_phase_rows;
   int32_t n_phase;           // products per K slice: 3 (FP32 form: hi*hi, hi*lo, lo*hi) or 1;
                              // the FP32 form's maps have 32-element K boxes, 64-byte swizzle
   int32_t f16;               // operands FP16 (1) or BF16 (0)

@@ -253,15 +253,143 @@ __global__ void __launch_bounds__(kThreads, 1) k_synth(SynthArgs a, const int32_
   }
 }
 
+// ----------------------------------------------------------------- wideband synthesis
+// Element echoes with the plane-wave delay across the aperture in the envelope as well
+// as in the phase (the input of true-time-delay beamforming), at one of U phases per work
+// item. A thread owns one element and a window of WT rows from e1 rows before each hit's
+// first tap row; per (hit, element) it forms the phasor c_k ey[mx] ez[my] and the table
+// position of the window's first row, x0 = x_hit + dy[mx] + dz[my] (the element's delay
+// in table entries), then reads row i at entry floor(x0) + i U F with the one weight
+// x0 - floor(x0): 8 instructions per (hit, element, row). The table is zero outside the
+// pulse support, so rows of the window the element's pulse does not reach add zero.
+constexpr int kWbThreads = 256;  // one element per thread -> 256 elements per work item
+
+template <int WT>
+__global__ void __launch_bounds__(kWbThreads, 2) k_synth_wb(SynthWbArgs a) {
+  extern __shared__ __align__(16) uint8_t wb_smem[];
+  const int nx = a.nx, ny = a.ny, M = nx * ny, U = a.n_phases, UF = a.uf;
+  float4* s_tab = reinterpret_cast<float4*>(wb_smem);
+  float2* s_ey = reinterpret_cast<float2*>(s_tab + a.n_tab);  // [kSub][nx]: c_k exp(j 2 pi pol uy (mx - cx))
+  float2* s_ez = s_ey + kSub * nx;                            // [kSub][ny]
+  float* s_dy = reinterpret_cast<float*>(s_ez + kSub * ny);   // [kSub][nx]: delay of column mx in entries
+  float* s_dz = s_dy + kSub * nx;                             // [kSub][ny]
+  float* s_x = s_dz + kSub * ny;                              // [kSub]: entry of the window's first row
+  int* s_n = reinterpret_cast<int*>(s_x + kSub);              // [kSub]: the window's first row
+  for (int i = threadIdx.x; i < a.n_tab; i += blockDim.x) s_tab[i] = __ldg(&a.tab[i]);
+  pdl_wait();
+
+  const int64_t H = *a.n_valid;
+  const int n_eb = (M + kWbThreads - 1) / kWbThreads;
+  const int64_t target = (int64_t)gridDim.x * 4;
+  int64_t chunk = ((H * n_eb * U + target - 1) / target + kSub - 1) / kSub * kSub;
+  if (chunk < kSub) chunk = kSub;
+  if (chunk > 8192) chunk = 8192;
+  const int64_t n_chunks = (H + chunk - 1) / chunk;
+  const int64_t n_items = n_chunks * n_eb * U;
+  const int tid = threadIdx.x;
+  const float cx = 0.5f * (float)(nx - 1), cy = 0.5f * (float)(ny - 1);
+  const int span = (WT - 1) * UF + 1;  // entries one (hit, element) reads from x0 on
+
+  for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+    const int phase = (int)(item % U);
+    const int64_t rest = item / U;
+    const int eb = (int)(rest % n_eb);
+    const int64_t c = rest / n_eb;
+    const int m = eb * kWbThreads + tid;
+    const bool act = m < M;
+    const int mx = act ? m % nx : 0, my = act ? m / nx : 0;
+    const int64_t h0 = c * chunk, h1 = min(h0 + chunk, H);
+    float2* S = a.S + (int64_t)phase * a.phase_stride;
+    const float x_phase = a.tab_x0 + (float)(phase * a.f);
+    float2 acc[WT];
+#pragma unroll
+    for (int i = 0; i < WT; ++i) acc[i] = make_float2(0.f, 0.f);
+    bool open = false;
+    int base = 0;
+
+    // adds the window's first row into S and slides the window by one row
+    auto shift = [&]() {
+      if (base >= 0 && act) {
+        float* dst = reinterpret_cast<float*>(S + (int64_t)base * M + m);
+        asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(dst), "f"(acc[0].x), "f"(acc[0].y) : "memory");
+      }
+#pragma unroll
+      for (int r = 0; r < WT - 1; ++r) acc[r] = acc[r + 1];
+      acc[WT - 1] = make_float2(0.f, 0.f);
+      ++base;
+    };
+
+    for (int64_t s0 = h0; s0 < h1; s0 += kSub) {
+      const int nsub = (int)(h1 - s0 < kSub ? h1 - s0 : kSub);
+      __syncthreads();
+      const int per_hit = nx + ny;
+      for (int idx = tid; idx < nsub * per_hit; idx += kWbThreads) {
+        const int k = idx / per_hit, j = idx % per_hit;
+        const HitRec& h = a.hits_sorted[s0 + k];
+        if (j == 0) {
+          s_n[k] = h.nglob - a.e1;
+          s_x[k] = fmaf(h.u0, (float)UF, x_phase);
+        }
+        float sn, cs;
+        if (j < nx) {
+          const float q = (float)j - cx;
+          sincospif(2.0f * a.pitch_over_lambda * q * h.uy, &sn, &cs);
+          s_ey[k * nx + j] = make_float2(h.cr * cs - h.ci * sn, h.cr * sn + h.ci * cs);
+          s_dy[k * nx + j] = a.pitch_uf * h.uy * q;
+        } else {
+          const int jj = j - nx;
+          const float q = (float)jj - cy;
+          sincospif(2.0f * a.pitch_over_lambda * q * h.uz, &sn, &cs);
+          s_ez[k * ny + jj] = make_float2(cs, sn);
+          s_dz[k * ny + jj] = a.pitch_uf * h.uz * q;
+        }
+      }
+      __syncthreads();
+      for (int k = 0; k < nsub; ++k) {
+        const int g = s_n[k];
+        if (!open) { base = g; open = true; }
+        if (g - base >= WT) {
+#pragma unroll
+          for (int i = 0; i < WT; ++i) shift();
+          base = g;
+        }
+        while (base < g) shift();
+        if (!act) continue;
+        const float2 ey = s_ey[k * nx + mx], ez = s_ez[k * ny + my];
+        const float2 P = make_float2(ey.x * ez.x - ey.y * ez.y, ey.x * ez.y + ey.y * ez.x);
+        const float x0 = s_x[k] + s_dy[k * nx + mx] + s_dz[k * ny + my];
+        const float fl = floorf(x0);
+        const float f = x0 - fl;
+        const int j0 = (int)fl;
+        if (j0 < 0 || j0 + span >= a.n_tab) {
+          // the table is sized on the host to cover every delay; a position outside it
+          // means the bound did not hold: record it and drop the pair
+          atomicOr(a.err, kErrIndex);
+          continue;
+        }
+        const float4* t = s_tab + j0;
+#pragma unroll
+        for (int i = 0; i < WT; ++i) {
+          const float4 v = t[i * UF];
+          const float rr = fmaf(f, v.z, v.x), ri = fmaf(f, v.w, v.y);
+          acc[i].x = fmaf(P.x, rr, fmaf(-P.y, ri, acc[i].x));
+          acc[i].y = fmaf(P.x, ri, fmaf(P.y, rr, acc[i].y));
+        }
+      }
+    }
+    if (open) {
+#pragma unroll
+      for (int i = 0; i < WT; ++i) shift();
+    }
+  }
+}
+
 // Pulse autocorrelation table R(u), u in [-T_p, T_p], kRTab intervals, evaluated in
 // FP64 from the closed form: the Hann window as three complex exponentials turns
 // R(u) into nine exponential integrals over the overlap of the two pulse supports.
 __device__ inline double sinc_d(double x) { return fabs(x) < 1e-4 ? 1.0 - x * x / 6.0 : sin(x) / x; }
-__global__ void k_rtab(float2* tab, int n_int, int guard, double T, double B) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i > n_int + 2 * guard) return;
-  double u = -T + 2.0 * T * (double)(i - guard) / (double)n_int;
-  if (!(fabs(u) < T)) { tab[i] = make_float2(0.f, 0.f); return; }
+__device__ double2 pulse_acf(double u, double T, double B) {
+  if (!(fabs(u) < T)) return make_double2(0.0, 0.0);
   const double kappa = B / T, Om = 2.0 * kPi / T, E = 3.0 * T / 8.0;
   const double L = fmax(-T / 2, -T / 2 - u), U = fmin(T / 2, T / 2 - u);
   double sr = 0.0, si = 0.0;
@@ -277,7 +405,24 @@ __global__ void k_rtab(float2* tab, int n_int, int guard, double T, double B) {
   }
   double ph0 = kPi * kappa * u * u;
   double c0 = cos(ph0), s0 = sin(ph0);
-  tab[i] = make_float2((float)((c0 * sr - s0 * si) / E), (float)((c0 * si + s0 * sr) / E));
+  return make_double2((c0 * sr - s0 * si) / E, (c0 * si + s0 * sr) / E);
+}
+__global__ void k_rtab(float2* tab, int n_int, int guard, double T, double B) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > n_int + 2 * guard) return;
+  const double2 r = pulse_acf(-T + 2.0 * T * (double)(i - guard) / (double)n_int, T, B);
+  tab[i] = make_float2((float)r.x, (float)r.y);
+}
+
+// Fine-grid table of the wideband synthesis: entry i holds R at v_i = v_lo + i du range
+// samples and the step to entry i + 1 (FP64 evaluation, FP32 storage).
+__global__ void k_wtab(float4* tab, int n, double v_lo, double du, double dt, double T, double B) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double2 r0 = pulse_acf((v_lo + i * du) * dt, T, B);
+  const double2 r1 = pulse_acf((v_lo + (i + 1) * du) * dt, T, B);
+  const float2 f0 = make_float2((float)r0.x, (float)r0.y);
+  tab[i] = make_float4(f0.x, f0.y, (float)r1.x - f0.x, (float)r1.y - f0.y);
 }
 
 // S (FP32, padded rows) -> 16-bit GEMM operand X [n_pings * nr_x][k_pad], interleaved
@@ -314,11 +459,15 @@ __device__ __forceinline__ uint32_t cvt_pair(float x, float y, int mode, float g
 
 __global__ void __launch_bounds__(256) k_convert(ConvertArgs a) {
   pdl_wait();
+  // row r of the grid: phase s, ping p, operand row j = sample j - x_guard
+  const int rows = a.nr + 2 * a.x_guard;
   const int r = blockIdx.x;
-  const int p = r / a.nr, n = r - p * a.nr;
+  const int sp = r / rows, j = r - sp * rows;
+  const int s = sp / a.n_pings, p = sp - s * a.n_pings;
+  const int n = j - a.x_guard;
   const int M = a.M;
-  const float2* src = a.S + ((int64_t)p * a.nr_pad + kPad + n) * M;
-  const int64_t dst0 = ((int64_t)p * a.nr_x + n) * a.k_pad;  // 16-bit units
+  const float2* src = a.S + s * a.phase_stride + ((int64_t)p * a.nr_pad + kPad + n) * M;
+  const int64_t dst0 = ((int64_t)sp * a.x_rows + j) * a.k_pad;  // 16-bit units
   uint16_t* xh = reinterpret_cast<uint16_t*>(a.x_hi) + dst0;
   uint16_t* xl = reinterpret_cast<uint16_t*>(a.x_lo) + dst0;
   const float gn = a.mode == SONAR_FP16 ? a.gain[p] : 1.0f;
@@ -450,6 +599,40 @@ cudaError_t launch_mfilter(const MfArgs& a, cudaStream_t st) {
                     a);
 }
 
+size_t synth_wb_smem(const SynthWbArgs& a) {
+  return (size_t)a.n_tab * sizeof(float4) + (size_t)kSub * (a.nx + a.ny) * (sizeof(float2) + sizeof(float)) +
+         (size_t)kSub * (sizeof(float) + sizeof(int));
+}
+constexpr int kWbSmemMax = 160 * 1024;
+
+cudaError_t prepare_synth_wb() {
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_synth_wb<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWbSmemMax))) return e;
+  if ((e = cudaFuncSetAttribute(k_synth_wb<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWbSmemMax))) return e;
+  if ((e = cudaFuncSetAttribute(k_synth_wb<20>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWbSmemMax))) return e;
+  return cudaFuncSetAttribute(k_synth_wb<24>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWbSmemMax);
+}
+
+cudaError_t launch_synth_wb(const SynthWbArgs& a, int wt, int sm_count, cudaStream_t st) {
+  if (a.nx > 64 || a.ny > 64 || a.n_phases < 1) return cudaErrorInvalidValue;
+  const size_t smem = synth_wb_smem(a);
+  if (smem > (size_t)kWbSmemMax) return cudaErrorInvalidValue;
+  const dim3 grid(2 * sm_count), block(kWbThreads);
+  switch (wt) {
+    case 12: return launch_pdl(k_synth_wb<12>, grid, block, smem, st, a);
+    case 16: return launch_pdl(k_synth_wb<16>, grid, block, smem, st, a);
+    case 20: return launch_pdl(k_synth_wb<20>, grid, block, smem, st, a);
+    case 24: return launch_pdl(k_synth_wb<24>, grid, block, smem, st, a);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_wtab(float4* tab, int32_t n, double v_lo, double du, double dt, double pulse, double bw,
+                        cudaStream_t st) {
+  k_wtab<<<(n + 255) / 256, 256, 0, st>>>(tab, n, v_lo, du, dt, pulse, bw);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_rtab(float2* rtab, float2* rtab_s, double pulse, double bw, cudaStream_t st) {
   k_rtab<<<(kRTab + 1 + 255) / 256, 256, 0, st>>>(rtab, kRTab, 0, pulse, bw);
   k_rtab<<<(kRTabS + 5 + 255) / 256, 256, 0, st>>>(rtab_s, kRTabS, 2, pulse, bw);
@@ -463,7 +646,8 @@ cudaError_t launch_convert(const ConvertArgs& a, int sm_count, cudaStream_t st) 
     k_absmax<<<dim3(sm_count, a.n_pings), 256, 0, st>>>(a.S, a.nr, a.nr_pad, a.M, a.gain);
   }
   if (a.mode == SONAR_FP16) k_gain_pow2<<<(a.n_pings + 63) / 64, 64, 0, st>>>(a.gain, a.n_pings, a.mode);
-  cudaError_t ce = launch_pdl(k_convert, dim3(a.n_pings * a.nr), dim3(256), 0, st, a);
+  if (a.x_guard > kPad || a.nr + 2 * a.x_guard > a.x_rows) return cudaErrorInvalidValue;
+  cudaError_t ce = launch_pdl(k_convert, dim3(a.n_phases * a.n_pings * (a.nr + 2 * a.x_guard)), dim3(256), 0, st, a);
   if (ce != cudaSuccess) return ce;
   return cudaGetLastError();
 }

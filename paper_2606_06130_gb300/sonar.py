@@ -38,6 +38,7 @@ SONAR_OPT_BVH = 7
 SONAR_OPT_CROSS = 8
 SONAR_OPT_AUTOTUNE = 9
 SONAR_OPT_TRAVERSAL = 10
+SONAR_OPT_TTD = 11
 
 SONAR_SUR_N_PARAMS = 150657
 
@@ -356,7 +357,8 @@ class Sonar:
         return out[..., 0] + 1j * out[..., 1]
 
     def raw(self, params: dict, phase: int, n_pings: int = 1) -> np.ndarray:
-        """Raw element series of the last call at phase s (samples t_n + s dt / U)."""
+        """Raw element series of the last call at phase s (samples t_n + s dt / U); after a
+        true-time-delay ping, the wideband element echoes at that phase."""
         M = params["nx"] * params["ny"]
         out = np.zeros((n_pings, params["n_range"], M, 2), np.float32)
         self._check(lib().sonar_get_raw(self.h, phase, out.ctypes.data, out.size))
