@@ -194,10 +194,11 @@ def stage_work(stage, params, stats, n_pings):
     return None
 
 
-def read_profile(kernel):
+def read_profile(kernel, extra=None):
     """(DRAM bytes, executed warp instructions) per launch from the committed ncu
     summary (profiles/dram_traffic.txt), each None when absent or when the kernel's
-    source has changed since the capture."""
+    source has changed since the capture. extra: a dict that receives the row's further
+    key=value counters (cache hit rates, L2 bytes, cycles) under the same rule."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     try:
         row = None
@@ -216,6 +217,10 @@ def read_profile(kernel):
         cur = hashlib.sha1(open(os.path.join(ROOT, "paper_2606_06130_gb300", "csrc", unit), "rb").read()).hexdigest()[:12]
         if cur != row[2]:
             return None, None
+        if extra is not None:
+            for kv in row[4:]:
+                k, v = kv.split("=", 1)
+                extra[k] = float(v)
         return float(row[1]), (float(row[3]) if len(row) > 3 else None)
     except (OSError, ValueError, IndexError):
         return None, None
@@ -421,7 +426,7 @@ def run_ours(args, ws, rank, local):
                       "parallelism": f"replicas x{ws}"},
            "roofline": roof,
            "stages_ms": mean_stage,
-           "stage_rooflines": stage_rooflines(mean_stage, params, stats, args.precision, pk),
+           "stage_rooflines": stage_rooflines(mean_stage, params, stats, args.precision, pk, clk),
            "scene_upload_ms": upload_ms,
            "hits_per_ping": stats["n_hits"],
            "tiles": {"beamform_tile_n": stats["tile_n"], "synth_cols": stats["synth_cols"],
@@ -486,7 +491,7 @@ def sample_errors(torch, s, ref):
     return out
 
 
-def stage_rooflines(mean_stage, params, stats, precision, pk):
+def stage_rooflines(mean_stage, params, stats, precision, pk, clk=None):
     """Achieved rate of every stage against its bound: tensor stages in TFLOP/s of the
     measured BF16 peaks (burst and sustained), memory stages in GB/s of the measured HBM
     copy rate, the traversal in sub-rays/s (latency-bound: no single peak)."""
@@ -512,9 +517,26 @@ def stage_rooflines(mean_stage, params, stats, precision, pk):
     n_pass = 3 if precision == "fp32" else 1
     synth_flop = H * M * (8 * stats["taps"] + 6)
     gemm_flop = 8.0 * nb * M * nr
+    # the traversal's memory side from its committed capture: L1 and L2 hit rates, the L2
+    # bytes it moves per launch and their rate over this run's stage time
+    tx = {}
+    _, trace_winst = read_profile("k_trace", tx)
+    trace_mem = None
+    if tx:
+        trace_mem = {"l1_hit_pct": tx.get("l1_hit"), "l2_hit_pct": tx.get("l2_hit"), "l2_bytes": tx.get("l2_bytes"),
+                     "l2_gbs": tx["l2_bytes"] / (mean_stage["trace"] / 1e3) / 1e9 if "l2_bytes" in tx else None,
+                     "issue_active_pct": tx.get("issue_active"), "source": "ncu capture (profiles/dram_traffic.txt)"}
+    # the traversal waits on dependent node loads; its measurable ceiling is instruction
+    # issue (4 warp instructions per clock per SM), against the captured instruction count
+    t_s = mean_stage["trace"] / 1e3
+    ipeak = 4 * 152 * ((clk or {}).get("sm_mhz") or 2070.0) * 1e6
+    trace = {"bound": "issue (latency-bound traversal: dependent BVH node loads)",
+             "achieved": trace_winst / t_s if trace_winst else None, "unit": "warp instructions/s",
+             "peak": ipeak, "frac": trace_winst / t_s / ipeak if trace_winst else None,
+             "warp_instructions_per_launch": trace_winst, "sub_rays_per_s": sub_rays / t_s,
+             "hits_per_s": H / t_s, "memory": trace_mem}
     out = {
-        "trace": {"bound": "latency (dependent BVH node loads)", "achieved": sub_rays / (mean_stage["trace"] / 1e3) / 1e6,
-                  "unit": "M sub-rays/s", "hits_per_s": H / (mean_stage["trace"] / 1e3), "peak": None, "frac": None},
+        "trace": trace,
         "bin": mem("bin", 2 * 32 * H, "32-byte hit records read and written once"),
         "synth": tensor("synth", synth_flop, stats.get("synth_mma_flop") or synth_flop),
         "convert": mem("convert", nr * M * (8 + (8 if precision == "fp32" else 4)),
