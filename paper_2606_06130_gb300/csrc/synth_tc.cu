@@ -467,11 +467,14 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_
     const float ax = pl2 * ((float)a_mx - 0.5f * (float)(nx - 1));
     const float az = pl2 * ((float)(L2 * a_hi) - 0.5f * (float)(ny - 1));
     // B operand: the group's share of a tile is NP complex columns pr = (n, my_lo) by its
-    // 8 hits, written as rows pr (re) and NP + pr (im). Item it = tg + 128 r (r < NP / 32)
-    // is column pr = it / 4 and hit pair pp = it % 4 (hits 2 pp, 2 pp + 1: one 8-byte
-    // half of a 16-byte chunk), so every thread has the same number of items per tile and
-    // keeps its hit pair, my_lo and the column's swizzle phase for the whole kernel.
-    const int pp = tg & 3, c0 = tg >> 2;                  // column c0 + 32 r
+    // 8 hits, written as rows pr (re) and NP + pr (im). A thread owns column c0 + 32 r (r <
+    // NP / 32) and hit pair pp (hits 2 pp, 2 pp + 1: one 8-byte half of a 16-byte chunk),
+    // so every thread has the same number of items per tile and keeps its hit pair, my_lo
+    // and the column's swizzle phase for the whole kernel. Lanes 0-7 and 8-15 (one
+    // half-warp, which an 8-byte store serves together) take eight consecutive columns at
+    // one hit pair each: their 16-byte chunks (2 grp + pp / 2) ^ (c0 & 7) are all distinct,
+    // so the half-warp's 128 bytes cover the 32 banks once.
+    const int pp = (tg & 31) >> 3, c0 = ((tg >> 5) << 3) | (tg & 7);  // column c0 + 32 r
     const int my_lo = c0 & (L2 - 1);
     const int nl0 = c0 >> lL2, nl_r = 32 >> lL2;          // tile row of column c0 + 32 r
     const uint32_t boff0 = (uint32_t)(c0 * 128 + (((2 * grp + (pp >> 1)) ^ (c0 & 7)) << 4) + ((pp & 1) << 3));
