@@ -603,6 +603,7 @@ def ttd_form(torch, s, params, poses, ssp, U):
 def other_forms(torch, s, inputs, dev):
     out = {}
     scene, params, poses, ssp = inputs.workload("c2")
+    from paper_2606_06130_gb300.sonar import SONAR_OPT_TIMING as _TIMING
     for prec in ("bf16", "fp16"):
         for _ in range(3):
             s.ping(poses[0], params, ssp, precision=prec)
@@ -612,6 +613,23 @@ def other_forms(torch, s, inputs, dev):
             s.ping(poses[0], params, ssp, precision=prec)
         torch.cuda.synchronize()
         out[f"c2_single_{prec}"] = {"value": 10 / (time.perf_counter() - t0), "unit": UNIT}
+        # the stage breakdown of this form (per-stage events, median of 5 pings) and its
+        # beamforming contraction against the measured BF16 burst (one product per tile)
+        s.set_option(_TIMING, 1)
+        st = []
+        for _ in range(5):
+            s.ping(poses[0], params, ssp, precision=prec)
+            torch.cuda.synchronize()
+            st.append(s.stats())
+        s.set_option(_TIMING, 0)
+        med = {k: float(np.median([x["ms_" + k] for x in st]))
+               for k in ("trace", "bin", "synth", "convert", "beamform", "peaks")}
+        gemm_flop = 8.0 * params["n_beam_az"] * params["n_beam_el"] * params["nx"] * params["ny"] * params["n_range"]
+        pk, _ = peaks_file()
+        tf = gemm_flop / (med["beamform"] / 1e3) / 1e12
+        out[f"c2_single_{prec}"].update({"stages_ms": med, "beamform": {
+            "flop": gemm_flop, "achieved_tflops": tf, "frac_of_bf16_burst": tf / pk["bf16_tflops"],
+            "tile_n": st[-1]["tile_n"]}})
     # the raw element series at 4 samples per range cell and the explicit matched filter
     from paper_2606_06130_gb300.sonar import SONAR_OPT_RAW
     s.set_option(SONAR_OPT_RAW, 4)

@@ -1045,9 +1045,12 @@ int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, cons
   const int64_t y_cols = (int64_t)d.k_pad * d.ttd_levels;
   if ((rc = make_map(ctx, &ga.map_xh, ctx->x_hi, x_map_rows, d.k_pad, 128, f16, box_k))) return rc;
   if ((rc = make_map(ctx, &ga.map_xl, ctx->x_lo, x_map_rows, d.k_pad, 128, f16, box_k))) return rc;
-  if ((rc = make_map(ctx, &ga.map_yh, ctx->y_hi, 2LL * d.nb_pad, y_cols, d.tile_n, f16, box_k))) return rc;
-  if ((rc = make_map(ctx, &ga.map_yl, ctx->y_lo, 2LL * d.nb_pad, y_cols, d.tile_n, f16, box_k))) return rc;
   ga.tiles_m = P * d.nr_x / 128;
+  // clusters of two CTAs load half of each B tile apiece and multicast it
+  ga.multicast = gemm_multicast(ga.tiles_m, d.tile_n, d.n_phase) ? 1 : 0;
+  const int y_box = ga.multicast ? d.tile_n / 2 : d.tile_n;
+  if ((rc = make_map(ctx, &ga.map_yh, ctx->y_hi, 2LL * d.nb_pad, y_cols, y_box, f16, box_k))) return rc;
+  if ((rc = make_map(ctx, &ga.map_yl, ctx->y_lo, 2LL * d.nb_pad, y_cols, y_box, f16, box_k))) return rc;
   ga.tiles_n = 2 * d.nb_pad / d.tile_n;
   ga.k_blocks = (int)(y_cols / 64);
   ga.x_kpad = d.k_pad;

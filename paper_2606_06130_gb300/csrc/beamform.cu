@@ -12,6 +12,15 @@
 // into a double-buffered TMEM accumulator (2 x tile_n columns) so the epilogue of one
 // tile overlaps the MMAs of the next. Persistent CTAs, one per SM.
 //
+// Operand delivery bounds the contraction: every tile streams its A rows (128) and B
+// rows (tile_n) from L2, about 14 TB/s over all SMs. With an even number of row tiles
+// the CTAs run in clusters of two that take two row tiles of the same N tile together:
+// each loads its own A tile and half of the shared B tile, multicast into both CTAs'
+// stages, so a tile moves 128 + tile_n / 2 rows instead of 128 + tile_n. A stage is
+// refilled only after both CTAs' MMAs have released it (their commits arrive on both
+// CTAs' empty barriers), and a cluster barrier brackets the kernel so that no CTA
+// leaves while its peer may still write into its shared memory.
+//
 // FP32 form: X = Xh + Xl, Y = Yh + Yl in BF16; the three products hi*hi, hi*lo, lo*hi
 // accumulate into the same FP32 accumulator. Its stages hold all four operand tiles of a
 // 32-deep K slice (64-byte swizzle) and issue the three products from them: each tile
@@ -68,7 +77,7 @@ __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int
   mb = gm0 + r % gsz;
 }
 
-template <int BN, int NPASS>
+template <int BN, int NPASS, bool MC>
 __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant__ GemmArgs a, uint32_t idesc) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   // align by pointer arithmetic on the shared array, so that the compiler keeps the
@@ -90,9 +99,27 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant_
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n_tiles = a.tiles_m * a.tiles_n;
   const int k_iters = a.k_blocks * (64 / BK);  // K slices per tile
+  // work units: tiles, or (clusters of two) pairs of row tiles of one N tile
+  const int rank = MC ? (int)cluster_rank() : 0;
+  const int n_units = MC ? n_tiles / 2 : n_tiles;
+  const int unit0 = MC ? (int)blockIdx.x / 2 : (int)blockIdx.x;
+  const int ustep = MC ? (int)gridDim.x / 2 : (int)gridDim.x;
+  auto coords = [&](int u, int& mb, int& nb) {
+    if (MC) {
+      int mbp;
+      tile_coords(u, a.tiles_m / 2, a.tiles_n, mbp, nb);
+      mb = 2 * mbp + rank;
+    } else {
+      tile_coords(u, a.tiles_m, a.tiles_n, mb, nb);
+    }
+  };
+  constexpr uint32_t B_HALF = B_BYTES / 2;  // one CTA's share of a B tile (tile_n / 2 rows)
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) { mbar_init(smem_u32(&full[s]), 1); mbar_init(smem_u32(&empty[s]), 1); }
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), MC ? 2 : 1);  // MC: released by both CTAs' MMAs
+    }
     for (int s = 0; s < 2; ++s) { mbar_init(smem_u32(&tfull[s]), 1); mbar_init(smem_u32(&tempty[s]), kEpiWarps); }
     mbar_init(smem_u32(done), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -103,7 +130,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant_
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   tc_fence_before();
-  __syncthreads();
+  if (MC) cluster_sync();  // the peer's barriers are initialised before anything reaches them
+  else __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
   // the operands come from the conversion kernel
@@ -116,9 +144,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant_
       uint32_t phase = 0;
       int issued = 0;
       bool ok = true;
-      for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+      for (int u = unit0; u < n_units && ok; u += ustep) {
         int mb, nb;
-        tile_coords(t, a.tiles_m, a.tiles_n, mb, nb);
+        coords(u, mb, nb);
         // the tile's first X row: ping p's block of x_ping_rows rows, past its guard rows
         const int row0 = mb * BM, p = row0 / a.nr_x;
         const int y_tile = p * a.x_ping_rows + a.x_guard + (row0 - p * a.nr_x);
@@ -134,10 +162,14 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant_
           uint8_t* const a_st = sA + stage * PARTS * A_BYTES;
           uint8_t* const b_st = sB + stage * PARTS * B_BYTES;
           tma_load_2d(smem_u32(a_st), &a.map_xh, xk, y, fb);
-          tma_load_2d(smem_u32(b_st), &a.map_yh, kb * BK, nb * BN, fb);
+          if (MC) tma_load_2d_mc(smem_u32(b_st) + rank * B_HALF, &a.map_yh, kb * BK, nb * BN + rank * (BN / 2), fb, 3);
+          else tma_load_2d(smem_u32(b_st), &a.map_yh, kb * BK, nb * BN, fb);
           if (PARTS == 2) {
             tma_load_2d(smem_u32(a_st + A_BYTES), &a.map_xl, xk, y, fb);
-            tma_load_2d(smem_u32(b_st + B_BYTES), &a.map_yl, kb * BK, nb * BN, fb);
+            if (MC)
+              tma_load_2d_mc(smem_u32(b_st + B_BYTES) + rank * B_HALF, &a.map_yl, kb * BK, nb * BN + rank * (BN / 2),
+                             fb, 3);
+            else tma_load_2d(smem_u32(b_st + B_BYTES), &a.map_yl, kb * BK, nb * BN, fb);
           }
           xk += BK;
           if (xk == a.x_kpad && a.ttd_u > 0) {
@@ -166,7 +198,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant_
       int acc = 0;
       uint32_t acc_phase = 0;
       bool ok = true;
-      for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+      for (int u = unit0; u < n_units && ok; u += ustep) {
         if (!mbar_wait(smem_u32(&tempty[acc]), acc_phase ^ 1, a.err)) { ok = false; break; }
         tc_fence_after();
         const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN);
@@ -185,7 +217,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant_
               tc_mma(d_tmem, da, db, idesc, (it | pass | kk) != 0);
             }
           }
-          tc_commit(smem_u32(&empty[stage]));
+          if (MC) tc_commit_mc(smem_u32(&empty[stage]), 3);
+          else tc_commit(smem_u32(&empty[stage]));
           if (++stage == STAGES) { stage = 0; phase ^= 1; }
         }
         if (!ok) break;
@@ -202,9 +235,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant_
     const int half = (warp - 2) >> 2;  // chunks half, half + 2, ...
     int acc = 0;
     uint32_t acc_phase = 0;
-    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    for (int u = unit0; u < n_units; u += ustep) {
       int mb, nb;
-      tile_coords(t, a.tiles_m, a.tiles_n, mb, nb);
+      coords(u, mb, nb);
       if (!mbar_wait(smem_u32(&tfull[acc]), acc_phase, a.err)) break;
       tc_fence_after();
       const int row = mb * BM + q * 32 + lane;
@@ -264,7 +297,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant_
     }
   }
   tc_fence_before();
-  __syncthreads();
+  if (MC) cluster_sync();  // the peer no longer writes into this CTA's stages or barriers
+  else __syncthreads();
   if (warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(tmem_cols(BN)) : "memory");
@@ -431,13 +465,52 @@ cudaError_t launch_steer(const SteerArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-// Dynamic shared-memory opt-in of the GEMM kernels (once per device, outside capture).
+// Dynamic shared-memory opt-in of the GEMM kernels (once per device, outside capture),
+// and for the cluster variants the number of two-CTA clusters that fit on the device.
+int g_mc_clusters[4][2];  // [tile 256, 224, 192, 128][one product, three]
+constexpr int tile_index(int bn) { return bn == 256 ? 0 : bn == 224 ? 1 : bn == 192 ? 2 : 3; }
+
+template <int BN, int NPASS, bool MC>
+cudaLaunchConfig_t gemm_config(int grid, cudaStream_t st, cudaLaunchAttribute (&attr)[2]) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kGemmThreads);
+  cfg.dynamicSmemBytes = gemm_smem<BN, NPASS>();
+  cfg.stream = st;
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  attr[1].id = cudaLaunchAttributeClusterDimension;
+  attr[1].val.clusterDim.x = MC ? 2 : 1;
+  attr[1].val.clusterDim.y = 1;
+  attr[1].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 2;
+  return cfg;
+}
+
+template <int BN, int NPASS>
+cudaError_t gemm_attr_one() {
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_gemm<BN, NPASS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)gemm_smem<BN, NPASS>())) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(k_gemm<BN, NPASS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)gemm_smem<BN, NPASS>())) != cudaSuccess)
+    return e;
+  cudaLaunchAttribute attr[2];
+  cudaLaunchConfig_t cfg = gemm_config<BN, NPASS, true>(2, 0, attr);
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, k_gemm<BN, NPASS, true>, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    n = 0;  // no cluster variant: whole tiles per CTA
+  }
+  g_mc_clusters[tile_index(BN)][NPASS == 3 ? 1 : 0] = n;
+  return cudaSuccess;
+}
 template <int BN>
 cudaError_t gemm_attr() {
-  cudaError_t e = cudaFuncSetAttribute(k_gemm<BN, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)gemm_smem<BN, 1>());
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_gemm<BN, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem<BN, 3>());
+  cudaError_t e = gemm_attr_one<BN, 1>();
+  return e != cudaSuccess ? e : gemm_attr_one<BN, 3>();
 }
 cudaError_t prepare_gemm() {
   cudaError_t e;
@@ -447,23 +520,40 @@ cudaError_t prepare_gemm() {
   return gemm_attr<128>();
 }
 
-template <int BN>
-cudaError_t launch_bn(const GemmArgs& a, int grid, cudaStream_t st) {
+bool gemm_multicast(int tiles_m, int tile_n, int n_phase) {
+  return tiles_m % 2 == 0 && tiles_m >= 2 && g_mc_clusters[tile_index(tile_n)][n_phase == 3 ? 1 : 0] > 0;
+}
+
+template <int BN, int NPASS>
+cudaError_t launch_np(const GemmArgs& a, int sm_count, cudaStream_t st) {
   const uint32_t idesc = make_idesc(a.f16 ? 0 : 1, BM, BN);
-  if (a.n_phase == 3)
-    return launch_pdl(k_gemm<BN, 3>, dim3(grid), dim3(kGemmThreads), gemm_smem<BN, 3>(), st, a, idesc);
-  return launch_pdl(k_gemm<BN, 1>, dim3(grid), dim3(kGemmThreads), gemm_smem<BN, 1>(), st, a, idesc);
+  const int n_tiles = a.tiles_m * a.tiles_n;
+  cudaLaunchAttribute attr[2];
+  if (a.multicast) {
+    const int n_pairs = n_tiles / 2, nc = g_mc_clusters[tile_index(BN)][NPASS == 3 ? 1 : 0];
+    const int clusters = n_pairs < nc ? n_pairs : nc;
+    cudaLaunchConfig_t cfg = gemm_config<BN, NPASS, true>(2 * clusters, st, attr);
+    return cudaLaunchKernelEx(&cfg, k_gemm<BN, NPASS, true>, a, idesc);
+  }
+  const int grid = n_tiles < sm_count ? n_tiles : sm_count;
+  cudaLaunchConfig_t cfg = gemm_config<BN, NPASS, false>(grid, st, attr);
+  cfg.numAttrs = 1;  // no cluster attribute
+  return cudaLaunchKernelEx(&cfg, k_gemm<BN, NPASS, false>, a, idesc);
+}
+
+template <int BN>
+cudaError_t launch_bn(const GemmArgs& a, int sm_count, cudaStream_t st) {
+  return a.n_phase == 3 ? launch_np<BN, 3>(a, sm_count, st) : launch_np<BN, 1>(a, sm_count, st);
 }
 
 cudaError_t launch_gemm(const GemmArgs& a, int sm_count, cudaStream_t st) {
-  const int n_tiles = a.tiles_m * a.tiles_n;
-  const int grid = n_tiles < sm_count ? n_tiles : sm_count;
+  if (a.multicast && !gemm_multicast(a.tiles_m, a.tile_n, a.n_phase)) return cudaErrorInvalidValue;
   cudaError_t e;
   switch (a.tile_n) {
-    case 256: e = launch_bn<256>(a, grid, st); break;
-    case 224: e = launch_bn<224>(a, grid, st); break;
-    case 192: e = launch_bn<192>(a, grid, st); break;
-    case 128: e = launch_bn<128>(a, grid, st); break;
+    case 256: e = launch_bn<256>(a, sm_count, st); break;
+    case 224: e = launch_bn<224>(a, sm_count, st); break;
+    case 192: e = launch_bn<192>(a, sm_count, st); break;
+    case 128: e = launch_bn<128>(a, sm_count, st); break;
     default: return cudaErrorInvalidValue;
   }
   return e != cudaSuccess ? e : cudaGetLastError();

@@ -409,9 +409,15 @@ struct GemmArgs {
   float* env;                // [n_pings][Nb][Nr]
   unsigned long long* peak_keys;  // [n_pings][Nb]
   unsigned int* ping_max;    // [n_pings] float bits
+  // two-CTA clusters sharing each B tile by multicast (map_yh / map_yl boxes then hold
+  // tile_n / 2 rows); only where gemm_multicast() allows it
+  int32_t multicast;
   int* err;
 };
 cudaError_t prepare_gemm();
+// Whether the two-CTA multicast form serves this shape (an even number of row tiles, and
+// the cluster variant fits on the device).
+bool gemm_multicast(int tiles_m, int tile_n, int n_phase);
 cudaError_t launch_gemm(const GemmArgs& a, int sm_count, cudaStream_t st);
 
 struct PeakArgs {
