@@ -37,10 +37,15 @@ namespace {
 using namespace tc;
 
 constexpr int BM = 128;
-// warp 0 TMA, warp 1 MMA, warps 2-9 epilogue: two warps per TMEM lane quarter, each
-// taking every other 32-column chunk, so a tile's epilogue takes half as long (it bounds
-// the one-product forms, whose MMAs per tile are short)
-constexpr int kEpiWarps = 8;
+#ifndef SONAR_GEMM_EPI_WARPS
+#define SONAR_GEMM_EPI_WARPS 16
+#endif
+// warp 0 TMA, warp 1 MMA, then the epilogue warps: kEpiWarps / 4 per TMEM lane quarter,
+// each taking every (kEpiWarps / 4)-th 32-column chunk of the tile, so that a tile's
+// drain keeps pace with the MMAs of the next (it bounds the one-product forms, whose
+// MMAs per tile are short)
+constexpr int kEpiWarps = SONAR_GEMM_EPI_WARPS;
+static_assert(kEpiWarps % 4 == 0, "epilogue warps come in lane-quarter sets of four");
 constexpr int kGemmThreads = 32 * (2 + kEpiWarps);
 
 // NPASS products per K slice (1: BF16/FP16, 3: FP32 form); PARTS tiles per operand (hi,
@@ -232,7 +237,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant_
   } else {
     // ------------------------------------------------------------- epilogue
     const int q = warp & 3;  // TMEM lane quarter this warp may access
-    const int half = (warp - 2) >> 2;  // chunks half, half + 2, ...
+    const int sub = (warp - 2) >> 2;  // chunks sub, sub + kEpiWarps / 4, ...
     int acc = 0;
     uint32_t acc_phase = 0;
     for (int u = unit0; u < n_units; u += ustep) {
@@ -250,7 +255,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant_
       unsigned long long* keys_p = a.peak_keys + (size_t)p * a.n_beams;
       float pmax = 0.f;
 #pragma unroll 1
-      for (int c = half; c < BN / 32; c += 2) {
+      for (int c = sub; c < BN / 32; c += kEpiWarps / 4) {
         uint32_t v[32];
         const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + c * 32);
         TMEM_LD_32(taddr, v);
