@@ -273,3 +273,40 @@ def test_warp_traversal_hit_parity(sonar, name):
     E_ref, _, _ = oracle.volume(params, ref, ns=ns)
     assert parity.nl2(E[:, ns], E_ref) <= 1e-4
     assert parity.nl2(E, E0) < 1e-4  # the same hits, emitted in another order (FP32 atomics)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+@pytest.mark.parametrize("tile_n", [128, 224, 256])
+def test_cluster_gemm_equals_single_cta_gemm(sonar, precision, tile_n):
+    """The beamforming GEMM runs in two-CTA clusters sharing each steering tile by
+    multicast when the batch has an even number of 128-sample row tiles, and one CTA per
+    tile otherwise. 128 range bins: one row tile per ping, so two pings take the cluster
+    form and each single ping the one-CTA form. Both accumulate every tile in the same
+    order; the element echoes they read may differ in the last bit (the synthesis adds
+    its tiles with FP32 atomics in any order), so the envelopes agree to 1e-6 in the FP32
+    form and to 1e-4 in the BF16 form (where such a bit can move an echo's BF16 rounding
+    by one step, 2^-9 relative), and the peaks on all but near-tied beams."""
+    from paper_2606_06130_gb300.sonar import SONAR_OPT_TILE_N, cloud_records
+    scene, params, poses, ssp = inputs.workload("c1")
+    params = dict(params, n_range=128, nx=32, ny=32, n_beam_az=48, n_beam_el=24)
+    pp = [poses[0], inputs.pose(poses[0]["t"] + np.array([0.2, 0.0, 0.0]), yaw_deg=6.0, tilt_down_deg=15.0)]
+    sonar.upload(scene)
+    sonar.set_option(SONAR_OPT_TILE_N, tile_n)
+    try:
+        env_b, cloud_b, n_b = sonar.ping_batch(pp, params, ssp, precision=precision)
+        torch.cuda.synchronize()
+        env_b = env_b.reshape(len(pp), -1, params["n_range"]).cpu().numpy()
+        for k, ps in enumerate(pp):
+            env, cloud, n = sonar.ping(ps, params, ssp, precision=precision)
+            torch.cuda.synchronize()
+            tol = 1e-6 if precision == "fp32" else 1e-4
+            assert parity.nl2(env_b[k], env.reshape(-1, params["n_range"]).cpu().numpy()) < tol
+            got = cloud_records(cloud_b[k], int(n_b[k]))
+            want = cloud_records(cloud, n)
+            assert abs(len(got) - len(want)) <= 2
+            g = dict(zip(got["beam"].tolist(), got["bin"].tolist()))
+            w = dict(zip(want["beam"].tolist(), want["bin"].tolist()))
+            same = sum(1 for b in w if g.get(b) == w[b])
+            assert same >= 0.99 * len(w), (same, len(w))
+    finally:
+        sonar.set_option(SONAR_OPT_TILE_N, 0)
