@@ -141,6 +141,9 @@ typedef struct {
      call (2 M N K per MMA, every product of the FP32 form counted; 0 for the other
      synthesis kernels) */
   double synth_mma_flop;
+  /* CTAs per cluster of the beamforming contraction in the last synchronous call (1, 2
+     or 4; SONAR_OPT_GEMM_CLUSTER) */
+  int32_t gemm_cluster;
 } sonar_stats;
 
 /* ---------------------------------------------------------------- context */
@@ -238,6 +241,15 @@ SONAR_API const char* sonar_last_error(const sonar_ctx* ctx);
    64 elements, not with SONAR_OPT_RAW (SONAR_E_UNSUPPORTED at the ping); any other
    value: SONAR_E_ARG. */
 #define SONAR_OPT_TTD 11
+/* SONAR_OPT_GEMM_CLUSTER: how many CTAs share each steering tile of the beamforming
+   contraction by multicast. 0 (default) chooses, as measured fastest: for the FP32
+   form 2 where two divide the row tiles (128 range samples each, over all pings of the
+   call), else 1; for the BF16 and FP16 forms 1. 1, 2 or 4 ask for that size, which falls
+   back to 1 where it does not divide the row tiles (4 moves the least operand data but
+   measured slower than 2: every stage waits for the slowest of the four CTAs). The results agree to the rounding
+   of the element echoes (the synthesis adds with atomics in any order). Any other value:
+   SONAR_E_ARG. */
+#define SONAR_OPT_GEMM_CLUSTER 12
 SONAR_API int sonar_set_option(sonar_ctx* ctx, int32_t option, int64_t value);
 
 /* ---------------------------------------------------------------- scene */

@@ -136,6 +136,7 @@ struct sonar_ctx {
   int bvh_opt = 0;    // 0: binned-SAH hierarchy (host build), 1: Morton-order LBVH (device build)
   int cross = 0;      // 1: out/back cross-term multipath
   int traversal = 0;  // straight rays: 0 one sub-ray per thread, 1 warp-cooperative
+  int gemm_cluster = 0;  // beamforming CTAs per cluster: 0 automatic, else 1, 2 or 4 where it fits
   int64_t vol_n = 0;  // water-column scatterers per ping
   sonar_field fld{};  // range-dependent sound speed (fld.nx = 0: none); c points to fld_c
   double* fld_c = nullptr;  // device copy of the grid
@@ -909,6 +910,14 @@ TraceArgs trace_args(const sonar_ctx* ctx, int P, const sonar_params* p, const D
   return ta;
 }
 
+// CTAs per cluster of the beamforming contraction over tiles_m row tiles: the library's
+// choice, or the option's size where it fits.
+int gemm_cluster_for(const sonar_ctx* ctx, int tiles_m, const Derived& d) {
+  if (ctx->gemm_cluster > 0)
+    return gemm_cluster_fits(ctx->gemm_cluster, tiles_m, d.tile_n, d.n_phase) ? ctx->gemm_cluster : 1;
+  return gemm_cluster_size(tiles_m, d.tile_n, d.n_phase, ctx->sm_count);
+}
+
 // Enqueue the whole pipeline for P pings on the context stream (graph-capturable:
 // no host synchronisation, fixed grids that read device-side counts).
 int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, const Outputs& o, int* kernels) {
@@ -1046,9 +1055,9 @@ int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, cons
   if ((rc = make_map(ctx, &ga.map_xh, ctx->x_hi, x_map_rows, d.k_pad, 128, f16, box_k))) return rc;
   if ((rc = make_map(ctx, &ga.map_xl, ctx->x_lo, x_map_rows, d.k_pad, 128, f16, box_k))) return rc;
   ga.tiles_m = P * d.nr_x / 128;
-  // clusters of two CTAs load half of each B tile apiece and multicast it
-  ga.multicast = gemm_multicast(ga.tiles_m, d.tile_n, d.n_phase) ? 1 : 0;
-  const int y_box = ga.multicast ? d.tile_n / 2 : d.tile_n;
+  // clusters of CTAs load a share of each B tile apiece and multicast it
+  ga.cluster = gemm_cluster_for(ctx, ga.tiles_m, d);
+  const int y_box = d.tile_n / ga.cluster;
   if ((rc = make_map(ctx, &ga.map_yh, ctx->y_hi, 2LL * d.nb_pad, y_cols, y_box, f16, box_k))) return rc;
   if ((rc = make_map(ctx, &ga.map_yl, ctx->y_lo, 2LL * d.nb_pad, y_cols, y_box, f16, box_k))) return rc;
   ga.tiles_n = 2 * d.nb_pad / d.tile_n;
@@ -1187,7 +1196,7 @@ std::vector<uint8_t> pipeline_key(const sonar_ctx* ctx, int P, const sonar_param
   key_add(k, ctx->debug); key_add(k, ctx->timing); key_add(k, ctx->synth_opt); key_add(k, ctx->scene_version);
   key_add(k, ctx->raw_u); key_add(k, ctx->ttd_u);
   key_add(k, d.c_ref);
-  key_add(k, d.tile_n); key_add(k, ctx->cur_pairs);
+  key_add(k, d.tile_n); key_add(k, ctx->cur_pairs); key_add(k, ctx->gemm_cluster);
   if (ssp) {
     key_add(k, ssp->n_nodes);
     for (int i = 0; i < ssp->n_nodes; ++i) { key_add(k, ssp->c[i]); if (ssp->z) key_add(k, ssp->z[i]); }
@@ -1418,6 +1427,7 @@ int run(sonar_ctx* ctx, const sonar_pose* poses, int P, const sonar_params* p, c
   static const int32_t kCols[5] = {0, 0, 32, 64, 96};
   ctx->stats.synth_cols = ctx->synth_opt >= 2 ? kCols[ctx->synth_opt] : ctx->cur_pairs;
   ctx->stats.autotuned = ctx->cur_tuned ? 1 : 0;
+  ctx->stats.gemm_cluster = gemm_cluster_for(ctx, P * d.nr_x / 128, d);
   if (timed) {
     float t[6];
     for (int i = 0; i < 6; ++i) CU(cudaEventElapsedTime(&t[i], ctx->stage_ev[i], ctx->stage_ev[i + 1]));
@@ -1785,6 +1795,11 @@ int sonar_set_option(sonar_ctx* ctx, int32_t option, int64_t value) {
     case SONAR_OPT_RAW:
       if (value < 0 || value > 8) return fail(ctx, SONAR_E_ARG, "raw series: 0 (off) or 1 to 8 samples per cell");
       ctx->raw_u = (int)value;
+      break;
+    case SONAR_OPT_GEMM_CLUSTER:
+      if (value != 0 && value != 1 && value != 2 && value != 4)
+        return fail(ctx, SONAR_E_ARG, "beamforming cluster: 0 (automatic), 1, 2 or 4");
+      ctx->gemm_cluster = (int)value;
       break;
     case SONAR_OPT_TTD:
       if (value < 0 || value > 8) return fail(ctx, SONAR_E_ARG, "true-time delay: 0 (off) or 1 to 8 phases per cell");

@@ -13,13 +13,13 @@
 // tile overlaps the MMAs of the next. Persistent CTAs, one per SM.
 //
 // Operand delivery bounds the contraction: every tile streams its A rows (128) and B
-// rows (tile_n) from L2, about 14 TB/s over all SMs. With an even number of row tiles
-// the CTAs run in clusters of two that take two row tiles of the same N tile together:
-// each loads its own A tile and half of the shared B tile, multicast into both CTAs'
-// stages, so a tile moves 128 + tile_n / 2 rows instead of 128 + tile_n. A stage is
-// refilled only after both CTAs' MMAs have released it (their commits arrive on both
-// CTAs' empty barriers), and a cluster barrier brackets the kernel so that no CTA
-// leaves while its peer may still write into its shared memory.
+// rows (tile_n) from L2, about 14 TB/s over all SMs. With a number of row tiles that CS
+// (2 or 4) divides, the CTAs run in clusters of CS that take CS row tiles of the same N
+// tile together: each loads its own A tile and 1 / CS of the shared B tile, multicast
+// into every CTA's stages, so a tile moves 128 + tile_n / CS rows instead of 128 +
+// tile_n. A stage is refilled only after all CS CTAs' MMAs have released it (their
+// commits arrive on every CTA's empty barriers), and a cluster barrier brackets the
+// kernel so that no CTA leaves while a peer may still write into its shared memory.
 //
 // FP32 form: X = Xh + Xl, Y = Yh + Yl in BF16; the three products hi*hi, hi*lo, lo*hi
 // accumulate into the same FP32 accumulator. Its stages hold all four operand tiles of a
@@ -82,8 +82,10 @@ __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int
   mb = gm0 + r % gsz;
 }
 
-template <int BN, int NPASS, bool MC>
+template <int BN, int NPASS, int CS>
 __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant__ GemmArgs a, uint32_t idesc) {
+  constexpr bool MC = CS > 1;
+  constexpr uint16_t kMask = (uint16_t)((1u << CS) - 1u);
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   // align by pointer arithmetic on the shared array, so that the compiler keeps the
   // shared address space (an integer round trip would turn every access generic)
@@ -104,26 +106,22 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant_
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n_tiles = a.tiles_m * a.tiles_n;
   const int k_iters = a.k_blocks * (64 / BK);  // K slices per tile
-  // work units: tiles, or (clusters of two) pairs of row tiles of one N tile
+  // work units: tiles, or (clusters of CS) groups of CS row tiles of one N tile
   const int rank = MC ? (int)cluster_rank() : 0;
-  const int n_units = MC ? n_tiles / 2 : n_tiles;
-  const int unit0 = MC ? (int)blockIdx.x / 2 : (int)blockIdx.x;
-  const int ustep = MC ? (int)gridDim.x / 2 : (int)gridDim.x;
+  const int n_units = n_tiles / CS;
+  const int unit0 = (int)blockIdx.x / CS;
+  const int ustep = (int)gridDim.x / CS;
   auto coords = [&](int u, int& mb, int& nb) {
-    if (MC) {
-      int mbp;
-      tile_coords(u, a.tiles_m / 2, a.tiles_n, mbp, nb);
-      mb = 2 * mbp + rank;
-    } else {
-      tile_coords(u, a.tiles_m, a.tiles_n, mb, nb);
-    }
+    int mbg;
+    tile_coords(u, a.tiles_m / CS, a.tiles_n, mbg, nb);
+    mb = CS * mbg + rank;
   };
-  constexpr uint32_t B_HALF = B_BYTES / 2;  // one CTA's share of a B tile (tile_n / 2 rows)
+  constexpr uint32_t B_PART = B_BYTES / CS;  // one CTA's share of a B tile (tile_n / CS rows)
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(smem_u32(&full[s]), 1);
-      mbar_init(smem_u32(&empty[s]), MC ? 2 : 1);  // MC: released by both CTAs' MMAs
+      mbar_init(smem_u32(&empty[s]), CS);  // released by every CTA's MMAs
     }
     for (int s = 0; s < 2; ++s) { mbar_init(smem_u32(&tfull[s]), 1); mbar_init(smem_u32(&tempty[s]), kEpiWarps); }
     mbar_init(smem_u32(done), 1);
@@ -135,7 +133,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant_
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   tc_fence_before();
-  if (MC) cluster_sync();  // the peer's barriers are initialised before anything reaches them
+  if (MC) cluster_sync();  // the peers' barriers are initialised before anything reaches them
   else __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
@@ -167,13 +165,13 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant_
           uint8_t* const a_st = sA + stage * PARTS * A_BYTES;
           uint8_t* const b_st = sB + stage * PARTS * B_BYTES;
           tma_load_2d(smem_u32(a_st), &a.map_xh, xk, y, fb);
-          if (MC) tma_load_2d_mc(smem_u32(b_st) + rank * B_HALF, &a.map_yh, kb * BK, nb * BN + rank * (BN / 2), fb, 3);
+          if (MC) tma_load_2d_mc(smem_u32(b_st) + rank * B_PART, &a.map_yh, kb * BK, nb * BN + rank * (BN / CS), fb, kMask);
           else tma_load_2d(smem_u32(b_st), &a.map_yh, kb * BK, nb * BN, fb);
           if (PARTS == 2) {
             tma_load_2d(smem_u32(a_st + A_BYTES), &a.map_xl, xk, y, fb);
             if (MC)
-              tma_load_2d_mc(smem_u32(b_st + B_BYTES) + rank * B_HALF, &a.map_yl, kb * BK, nb * BN + rank * (BN / 2),
-                             fb, 3);
+              tma_load_2d_mc(smem_u32(b_st + B_BYTES) + rank * B_PART, &a.map_yl, kb * BK, nb * BN + rank * (BN / CS),
+                             fb, kMask);
             else tma_load_2d(smem_u32(b_st + B_BYTES), &a.map_yl, kb * BK, nb * BN, fb);
           }
           xk += BK;
@@ -222,7 +220,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant_
               tc_mma(d_tmem, da, db, idesc, (it | pass | kk) != 0);
             }
           }
-          if (MC) tc_commit_mc(smem_u32(&empty[stage]), 3);
+          if (MC) tc_commit_mc(smem_u32(&empty[stage]), kMask);
           else tc_commit(smem_u32(&empty[stage]));
           if (++stage == STAGES) { stage = 0; phase ^= 1; }
         }
@@ -302,7 +300,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant_
     }
   }
   tc_fence_before();
-  if (MC) cluster_sync();  // the peer no longer writes into this CTA's stages or barriers
+  if (MC) cluster_sync();  // no peer writes into this CTA's stages or barriers any more
   else __syncthreads();
   if (warp == 1) {
     tc_fence_after();
@@ -471,11 +469,11 @@ cudaError_t launch_steer(const SteerArgs& a, cudaStream_t st) {
 }
 
 // Dynamic shared-memory opt-in of the GEMM kernels (once per device, outside capture),
-// and for the cluster variants the number of two-CTA clusters that fit on the device.
-int g_mc_clusters[4][2];  // [tile 256, 224, 192, 128][one product, three]
+// and for the cluster variants the number of clusters that fit on the device.
+int g_mc_clusters[4][2][2];  // [tile 256, 224, 192, 128][one product, three][cluster 2, 4]
 constexpr int tile_index(int bn) { return bn == 256 ? 0 : bn == 224 ? 1 : bn == 192 ? 2 : 3; }
 
-template <int BN, int NPASS, bool MC>
+template <int BN, int NPASS, int CS>
 cudaLaunchConfig_t gemm_config(int grid, cudaStream_t st, cudaLaunchAttribute (&attr)[2]) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
@@ -485,32 +483,35 @@ cudaLaunchConfig_t gemm_config(int grid, cudaStream_t st, cudaLaunchAttribute (&
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   attr[1].id = cudaLaunchAttributeClusterDimension;
-  attr[1].val.clusterDim.x = MC ? 2 : 1;
+  attr[1].val.clusterDim.x = CS;
   attr[1].val.clusterDim.y = 1;
   attr[1].val.clusterDim.z = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 2;
+  cfg.numAttrs = CS > 1 ? 2 : 1;
   return cfg;
 }
 
+template <int BN, int NPASS, int CS>
+cudaError_t gemm_attr_cs() {
+  cudaError_t e = cudaFuncSetAttribute(k_gemm<BN, NPASS, CS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)gemm_smem<BN, NPASS>());
+  if (e != cudaSuccess || CS == 1) return e;
+  cudaLaunchAttribute attr[2];
+  cudaLaunchConfig_t cfg = gemm_config<BN, NPASS, CS>(CS, 0, attr);
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, k_gemm<BN, NPASS, CS>, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    n = 0;  // this cluster size is not used
+  }
+  g_mc_clusters[tile_index(BN)][NPASS == 3 ? 1 : 0][CS == 4 ? 1 : 0] = n;
+  return cudaSuccess;
+}
 template <int BN, int NPASS>
 cudaError_t gemm_attr_one() {
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(k_gemm<BN, NPASS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)gemm_smem<BN, NPASS>())) != cudaSuccess)
-    return e;
-  if ((e = cudaFuncSetAttribute(k_gemm<BN, NPASS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)gemm_smem<BN, NPASS>())) != cudaSuccess)
-    return e;
-  cudaLaunchAttribute attr[2];
-  cudaLaunchConfig_t cfg = gemm_config<BN, NPASS, true>(2, 0, attr);
-  int n = 0;
-  if (cudaOccupancyMaxActiveClusters(&n, k_gemm<BN, NPASS, true>, &cfg) != cudaSuccess) {
-    cudaGetLastError();
-    n = 0;  // no cluster variant: whole tiles per CTA
-  }
-  g_mc_clusters[tile_index(BN)][NPASS == 3 ? 1 : 0] = n;
-  return cudaSuccess;
+  if ((e = gemm_attr_cs<BN, NPASS, 1>()) != cudaSuccess) return e;
+  if ((e = gemm_attr_cs<BN, NPASS, 2>()) != cudaSuccess) return e;
+  return gemm_attr_cs<BN, NPASS, 4>();
 }
 template <int BN>
 cudaError_t gemm_attr() {
@@ -525,25 +526,48 @@ cudaError_t prepare_gemm() {
   return gemm_attr<128>();
 }
 
-bool gemm_multicast(int tiles_m, int tile_n, int n_phase) {
-  return tiles_m % 2 == 0 && tiles_m >= 2 && g_mc_clusters[tile_index(tile_n)][n_phase == 3 ? 1 : 0] > 0;
+bool gemm_cluster_fits(int cs, int tiles_m, int tile_n, int n_phase) {
+  if (cs == 1) return true;
+  if ((cs != 2 && cs != 4) || tiles_m % cs != 0) return false;
+  return g_mc_clusters[tile_index(tile_n)][n_phase == 3 ? 1 : 0][cs == 4 ? 1 : 0] > 0;
+}
+
+int gemm_cluster_size(int tiles_m, int tile_n, int n_phase, int sm_count) {
+  (void)sm_count;
+  // Measured on the C2 ping (N tile 224, bench stage events): the FP32 form 0.1147 /
+  // 0.1106 / 0.1331 ms with 1 / 2 / 4 CTAs per cluster, the one-product form 0.0553 /
+  // 0.0573 / 0.0676 ms. Four lose because every stage waits for the slowest of four CTAs
+  // to release it; the one-product form, whose MMAs per stage are short, gains nothing
+  // from sharing B once sixteen warps drain its tiles.
+  if (n_phase != 3) return 1;
+  const int* n = g_mc_clusters[tile_index(tile_n)][1];
+  if (tiles_m % 2 == 0 && n[0] > 0) return 2;
+  return 1;
+}
+
+template <int BN, int NPASS, int CS>
+cudaError_t launch_cs(const GemmArgs& a, int sm_count, cudaStream_t st, uint32_t idesc) {
+  const int n_tiles = a.tiles_m * a.tiles_n;
+  int grid;
+  if (CS > 1) {
+    const int n_groups = n_tiles / CS, nc = g_mc_clusters[tile_index(BN)][NPASS == 3 ? 1 : 0][CS == 4 ? 1 : 0];
+    grid = CS * (n_groups < nc ? n_groups : nc);
+  } else {
+    grid = n_tiles < sm_count ? n_tiles : sm_count;
+  }
+  cudaLaunchAttribute attr[2];
+  cudaLaunchConfig_t cfg = gemm_config<BN, NPASS, CS>(grid, st, attr);
+  return cudaLaunchKernelEx(&cfg, k_gemm<BN, NPASS, CS>, a, idesc);
 }
 
 template <int BN, int NPASS>
 cudaError_t launch_np(const GemmArgs& a, int sm_count, cudaStream_t st) {
   const uint32_t idesc = make_idesc(a.f16 ? 0 : 1, BM, BN);
-  const int n_tiles = a.tiles_m * a.tiles_n;
-  cudaLaunchAttribute attr[2];
-  if (a.multicast) {
-    const int n_pairs = n_tiles / 2, nc = g_mc_clusters[tile_index(BN)][NPASS == 3 ? 1 : 0];
-    const int clusters = n_pairs < nc ? n_pairs : nc;
-    cudaLaunchConfig_t cfg = gemm_config<BN, NPASS, true>(2 * clusters, st, attr);
-    return cudaLaunchKernelEx(&cfg, k_gemm<BN, NPASS, true>, a, idesc);
+  switch (a.cluster) {
+    case 4: return launch_cs<BN, NPASS, 4>(a, sm_count, st, idesc);
+    case 2: return launch_cs<BN, NPASS, 2>(a, sm_count, st, idesc);
+    default: return launch_cs<BN, NPASS, 1>(a, sm_count, st, idesc);
   }
-  const int grid = n_tiles < sm_count ? n_tiles : sm_count;
-  cudaLaunchConfig_t cfg = gemm_config<BN, NPASS, false>(grid, st, attr);
-  cfg.numAttrs = 1;  // no cluster attribute
-  return cudaLaunchKernelEx(&cfg, k_gemm<BN, NPASS, false>, a, idesc);
 }
 
 template <int BN>
@@ -552,7 +576,10 @@ cudaError_t launch_bn(const GemmArgs& a, int sm_count, cudaStream_t st) {
 }
 
 cudaError_t launch_gemm(const GemmArgs& a, int sm_count, cudaStream_t st) {
-  if (a.multicast && !gemm_multicast(a.tiles_m, a.tile_n, a.n_phase)) return cudaErrorInvalidValue;
+  if (a.cluster != 1 && a.cluster != 2 && a.cluster != 4) return cudaErrorInvalidValue;
+  if (a.tiles_m % a.cluster != 0) return cudaErrorInvalidValue;
+  if (a.cluster > 1 && g_mc_clusters[tile_index(a.tile_n)][a.n_phase == 3 ? 1 : 0][a.cluster == 4 ? 1 : 0] <= 0)
+    return cudaErrorInvalidValue;
   cudaError_t e;
   switch (a.tile_n) {
     case 256: e = launch_bn<256>(a, sm_count, st); break;

@@ -409,15 +409,18 @@ struct GemmArgs {
   float* env;                // [n_pings][Nb][Nr]
   unsigned long long* peak_keys;  // [n_pings][Nb]
   unsigned int* ping_max;    // [n_pings] float bits
-  // two-CTA clusters sharing each B tile by multicast (map_yh / map_yl boxes then hold
-  // tile_n / 2 rows); only where gemm_multicast() allows it
-  int32_t multicast;
+  // CTAs per cluster sharing each B tile by multicast: 1, 2 or 4 (map_yh / map_yl boxes
+  // then hold tile_n / cluster rows), as gemm_cluster_size() gives it
+  int32_t cluster;
   int* err;
 };
 cudaError_t prepare_gemm();
-// Whether the two-CTA multicast form serves this shape (an even number of row tiles, and
-// the cluster variant fits on the device).
-bool gemm_multicast(int tiles_m, int tile_n, int n_phase);
+// CTAs per cluster of the GEMM for this shape: for the FP32 form 2 where two divide the
+// row tiles and the cluster variant fits on the device, else (and for the one-product
+// forms) 1.
+int gemm_cluster_size(int tiles_m, int tile_n, int n_phase, int sm_count);
+// Whether clusters of cs CTAs serve this shape at all.
+bool gemm_cluster_fits(int cs, int tiles_m, int tile_n, int n_phase);
 cudaError_t launch_gemm(const GemmArgs& a, int sm_count, cudaStream_t st);
 
 struct PeakArgs {

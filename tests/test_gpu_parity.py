@@ -278,35 +278,43 @@ def test_warp_traversal_hit_parity(sonar, name):
 @pytest.mark.parametrize("precision", ["fp32", "bf16"])
 @pytest.mark.parametrize("tile_n", [128, 224, 256])
 def test_cluster_gemm_equals_single_cta_gemm(sonar, precision, tile_n):
-    """The beamforming GEMM runs in two-CTA clusters sharing each steering tile by
-    multicast when the batch has an even number of 128-sample row tiles, and one CTA per
-    tile otherwise. 128 range bins: one row tile per ping, so two pings take the cluster
-    form and each single ping the one-CTA form. Both accumulate every tile in the same
-    order; the element echoes they read may differ in the last bit (the synthesis adds
-    its tiles with FP32 atomics in any order), so the envelopes agree to 1e-6 in the FP32
-    form and to 1e-4 in the BF16 form (where such a bit can move an echo's BF16 rounding
-    by one step, 2^-9 relative), and the peaks on all but near-tied beams."""
-    from paper_2606_06130_gb300.sonar import SONAR_OPT_TILE_N, cloud_records
+    """The beamforming GEMM in clusters of 2 and 4 CTAs sharing each steering tile by
+    multicast against one CTA per tile (SONAR_OPT_GEMM_CLUSTER), on a batch of four pings
+    of 128 range bins (four row tiles). Each form accumulates every tile in the same
+    order; the element echoes they read may differ in the last bit between calls (the
+    synthesis adds its tiles with FP32 atomics in any order), so the envelopes agree to
+    1e-6 in the FP32 form and to 1e-4 in the BF16 form (where such a bit can move an
+    echo's BF16 rounding by one step, 2^-9 relative), and the peaks on all but near-tied
+    beams. The automatic choice is a cluster of two for the FP32 form, one CTA per tile
+    for the BF16 form."""
+    from paper_2606_06130_gb300.sonar import SONAR_OPT_GEMM_CLUSTER, SONAR_OPT_TILE_N, cloud_records
     scene, params, poses, ssp = inputs.workload("c1")
     params = dict(params, n_range=128, nx=32, ny=32, n_beam_az=48, n_beam_el=24)
-    pp = [poses[0], inputs.pose(poses[0]["t"] + np.array([0.2, 0.0, 0.0]), yaw_deg=6.0, tilt_down_deg=15.0)]
+    pp = [inputs.pose(poses[0]["t"] + np.array([0.1 * k, 0.0, 0.0]), yaw_deg=-6.0 + 4.0 * k, tilt_down_deg=15.0)
+          for k in range(4)]
     sonar.upload(scene)
     sonar.set_option(SONAR_OPT_TILE_N, tile_n)
+    out = {}
     try:
-        env_b, cloud_b, n_b = sonar.ping_batch(pp, params, ssp, precision=precision)
-        torch.cuda.synchronize()
-        env_b = env_b.reshape(len(pp), -1, params["n_range"]).cpu().numpy()
-        for k, ps in enumerate(pp):
-            env, cloud, n = sonar.ping(ps, params, ssp, precision=precision)
+        for cs in (1, 2, 4, 0):
+            sonar.set_option(SONAR_OPT_GEMM_CLUSTER, cs)
+            env, cloud, n = sonar.ping_batch(pp, params, ssp, precision=precision)
             torch.cuda.synchronize()
-            tol = 1e-6 if precision == "fp32" else 1e-4
-            assert parity.nl2(env_b[k], env.reshape(-1, params["n_range"]).cpu().numpy()) < tol
-            got = cloud_records(cloud_b[k], int(n_b[k]))
-            want = cloud_records(cloud, n)
+            out[cs] = (env.reshape(len(pp), -1, params["n_range"]).cpu().numpy(),
+                       [cloud_records(cloud[k], int(n[k])) for k in range(len(pp))], sonar.stats()["gemm_cluster"])
+    finally:
+        sonar.set_option(SONAR_OPT_TILE_N, 0)
+        sonar.set_option(SONAR_OPT_GEMM_CLUSTER, 0)
+    assert [out[cs][2] for cs in (1, 2, 4)] == [1, 2, 4]
+    assert out[0][2] == (2 if precision == "fp32" else 1)
+    tol = 1e-6 if precision == "fp32" else 1e-4
+    ref_env, ref_pts, _ = out[1]
+    for cs in (2, 4):
+        env, pts, _ = out[cs]
+        assert parity.nl2(env, ref_env) < tol, (cs, parity.nl2(env, ref_env))
+        for got, want in zip(pts, ref_pts):
             assert abs(len(got) - len(want)) <= 2
             g = dict(zip(got["beam"].tolist(), got["bin"].tolist()))
             w = dict(zip(want["beam"].tolist(), want["bin"].tolist()))
             same = sum(1 for b in w if g.get(b) == w[b])
-            assert same >= 0.99 * len(w), (same, len(w))
-    finally:
-        sonar.set_option(SONAR_OPT_TILE_N, 0)
+            assert same >= 0.99 * len(w), (cs, same, len(w))
