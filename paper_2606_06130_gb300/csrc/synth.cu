@@ -262,7 +262,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_synth(SynthArgs a, const int32_
 // in table entries), then reads row i at entry floor(x0) + i U F with the one weight
 // x0 - floor(x0): 8 instructions per (hit, element, row). The table is zero outside the
 // pulse support, so rows of the window the element's pulse does not reach add zero.
+// Element order: an 8-lane quarter-warp (which a 16-byte shared load serves together)
+// reads the table at its elements' delays, so its elements are kept close in delay: for
+// 32-wide arrays each quarter-warp takes a block of 2 columns x 4 rows of elements (the
+// vertical pitch weighs less: |u_z| <= sin(vfov / 2) is below |u_y|), which puts fewer
+// of its eight addresses in the same bank group than eight elements along a row.
 constexpr int kWbThreads = 256;  // one element per thread -> 256 elements per work item
+
+// Element of thread t in work item eb: blocks of 2 x 4 per quarter-warp for nx = 32 (an
+// item is 32 columns x 8 rows), the natural order otherwise.
+__device__ __forceinline__ int wb_element(int eb, int t, int nx) {
+  if (nx != 32) return eb * kWbThreads + t;
+  const int w = t >> 5, q = (t >> 3) & 3, e = t & 7;
+  const int mx = 8 * (w & 3) + 2 * q + (e & 1), my = 4 * (w >> 2) + (e >> 1);
+  return (eb * 8 + my) * 32 + mx;
+}
 
 template <int WT>
 __global__ void __launch_bounds__(kWbThreads, 2) k_synth_wb(SynthWbArgs a) {
@@ -295,7 +309,7 @@ __global__ void __launch_bounds__(kWbThreads, 2) k_synth_wb(SynthWbArgs a) {
     const int64_t rest = item / U;
     const int eb = (int)(rest % n_eb);
     const int64_t c = rest / n_eb;
-    const int m = eb * kWbThreads + tid;
+    const int m = wb_element(eb, tid, nx);
     const bool act = m < M;
     const int mx = act ? m % nx : 0, my = act ? m / nx : 0;
     const int64_t h0 = c * chunk, h1 = min(h0 + chunk, H);
