@@ -393,16 +393,16 @@ __device__ HitT<R> closest_hit(const DevScene& sc, const V& o, const V& d, R tmi
     slab(A.x, A.y, A.z, A.w, Cz.x, Cz.y, q.r, -1e-4f, q.tcull, ln, lf);
     slab(B.x, B.y, B.z, B.w, Cz.z, Cz.w, q.r, -1e-4f, q.tcull, rn, rf);
     bool hl = ln <= lf, hr = rn <= rf;
-    int kids[2] = {ch.x, ch.y};
-    bool hit2[2] = {hl, hr};
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      if (!hit2[c] || kids[c] >= 0) continue;
-      hit2[c] = false;
-      if (leaf_candidate<V, R, ANY>(sc, q, o, d, tmin, tmax, exclude, ~kids[c])) return q.best;
+    // leaf children: one copy of the triangle test, run for each (a rolled loop keeps the
+    // traversal loop small in the instruction cache)
+    const bool leaf_l = hl && ch.x < 0, leaf_r = hr && ch.y < 0;
+#pragma unroll 1
+    for (int c = leaf_l ? 0 : 1; c < (leaf_r ? 2 : 1); ++c) {
+      if (c == 0 || leaf_r)
+        if (leaf_candidate<V, R, ANY>(sc, q, o, d, tmin, tmax, exclude, ~(c == 0 ? ch.x : ch.y))) return q.best;
     }
-    hl = hit2[0];
-    hr = hit2[1];
+    hl = hl && !leaf_l;
+    hr = hr && !leaf_r;
     if (hl && hr) {
       int nearc = ln <= rn ? ch.x : ch.y, farc = ln <= rn ? ch.y : ch.x;
       if (sp >= kMaxStack) { atomicOr(err, kErrStack); break; }
