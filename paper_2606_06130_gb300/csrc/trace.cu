@@ -1027,12 +1027,13 @@ __global__ void __launch_bounds__(128) k_trace_warp(TraceArgs A) {
 }
 
 // Traversal is latency-bound (dependent node loads), so residency pays: the straight-ray
-// kernel runs six CTAs of 128 threads per SM (80 registers, a 36-byte spill; measured on
-// C2: 5 CTAs 0.129 ms, 6 0.123, 7 and 8 within noise of 6), the curved one four. The
-// cross-term variant is a separate instantiation, so that its extra live state does not
+// kernel runs seven CTAs of 128 threads per SM (72 registers, an 80-byte spill; measured
+// on C2 with one copy of the leaf test in the loop: 5 CTAs 0.098 ms, 6 0.092, 7 0.088, 8
+// 0.093), the curved one four. The cross-term variant is a separate instantiation, so
+// that its extra live state does not
 // cost the default kernel registers.
 #ifndef SONAR_TRACE_CTAS
-#define SONAR_TRACE_CTAS 6  // resident CTAs per SM of the straight-ray kernel
+#define SONAR_TRACE_CTAS 7  // resident CTAs per SM of the straight-ray kernel
 #endif
 template <bool CURVED, bool CROSS>
 __global__ void __launch_bounds__(128, CURVED ? 4 : SONAR_TRACE_CTAS) k_trace(TraceArgs A) {
