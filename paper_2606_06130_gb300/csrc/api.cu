@@ -961,6 +961,7 @@ int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, cons
   sa.rtab = ctx->rtab;
   sa.rtab_scale = (float)(d.dt * kRTab / (2.0 * p->pulse_s));
   sa.rtab_s = ctx->rtab + kRTab + 1;
+  sa.cplx_taps = 0;
   sa.rtab_s_scale = (float)(d.dt * kRTabS / (2.0 * p->pulse_s));
   sa.taps = d.taps;
   sa.nx = p->nx;
@@ -1007,6 +1008,7 @@ int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, cons
       SynthArgs sr = sa;
       sr.rtab = ctx->ptab + (int64_t)s * (kRTab + 1);
       sr.rtab_s = ctx->ptab + (int64_t)U * (kRTab + 1) + (int64_t)s * (kRTabS + 5);
+      sr.cplx_taps = 1;
       sr.S = ctx->S_raw + (int64_t)s * ctx->s_elems;
       if (tc) CU(launch_synth_tc(sr, want_pairs, ctx->sm_count, st));
       else CU(launch_synth(sr, ctx->sm_count, st));

@@ -214,6 +214,8 @@ struct SynthArgs {
   float2* S;                // [n_pings * nr_pad][M] element echoes
   int64_t total_rows;       // n_pings * nr_pad
   int32_t n_pass;           // tensor-core synthesis: 3 (BF16 hi/lo split) or 1
+  int32_t cplx_taps;        // 1: rtab_s holds a complex pulse (raw series); 0: the real
+                            // pulse autocorrelation (its imaginary parts are not read)
   unsigned long long* mma_flop;  // z-split kernel: tensor flops its MMAs execute (added per CTA), or null
   int* err;
 };

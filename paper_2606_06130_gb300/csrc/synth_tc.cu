@@ -25,7 +25,12 @@
 //   tiles (NP = 64, 96) need fewer of them; the price is fewer TMEM accumulators
 //   (384 / 2 NP) and so fewer tiles per K-block. The sixteen generator warps form four
 //   independent groups, one per MMA K step (8 hits), each with one warp per TMEM lane
-//   quarter and its own named barrier.
+//   quarter and its own named barrier. The pulse autocorrelation is real (even window,
+//   chirp centred on t = 0), so with c_k = |c_k| exp(j pi phi_k) the taps |c_k| R are
+//   real, phi_k joins the A operand's phase at no cost, and each B entry is one packed
+//   FP32 product g (Re E2, -Im E2). In each group one walker warp fetches the records
+//   and walks the K-blocks one ahead, publishing every K-block's descriptor with its
+//   records; the other three form the taps, E2 and phi_k.
 // k_synth_tc (small arrays): A[(n, mx)][k] = g_k(n) ey[mx] per tile (T = 128 / nx) and
 //   B[k][(my, re/im)] = ez[my] once per K-block, both in shared memory.
 #include <limits.h>
@@ -210,7 +215,35 @@ __device__ __forceinline__ float2 tap_value(const float2* tab, float scale, floa
   return g;
 }
 
-#define TMEM_LD_16(taddr, r)                                                                                  \
+// Real tap R(u) from the real part of the shared-memory pulse table (4-point Lagrange,
+// zero outside the pulse support). The autocorrelation of the Hann-windowed chirp centred
+// on t = 0 is real: R(u) = (1/E) int w(s + u/2) w(s - u/2) exp(j 2 pi kappa u s) ds with
+// the window product even in s, so only the cosine part survives (the table's imaginary
+// parts are rounding noise of the closed form).
+__device__ __forceinline__ float tap_real(const float* tab, float scale, float u) {
+  float g = 0.f;
+  const float x = u * scale + (float)(kRTabS / 2 + 2);
+  if (x >= 1.0f && x < (float)(kRTabS + 3)) {
+    const int i = (int)x;
+    const float f = x - (float)i;
+    const float wm = -f * (f - 1.f) * (f - 2.f) * (1.f / 6.f);
+    const float w0 = (f + 1.f) * (f - 1.f) * (f - 2.f) * 0.5f;
+    const float w1 = -(f + 1.f) * f * (f - 2.f) * 0.5f;
+    const float w2 = (f + 1.f) * f * (f - 1.f) * (1.f / 6.f);
+    g = fmaf(wm, tab[i - 1], fmaf(w0, tab[i], fmaf(w1, tab[i + 1], w2 * tab[i + 2])));
+  }
+  return g;
+}
+
+// Residual lo = bf16(v - hi) of a pair packed as hi = (bf16(v.x), bf16(v.y)); the
+// difference is exact in FP32 (Sterbenz), one packed FP32 operation for both halves.
+__device__ __forceinline__ uint32_t pack_lo2(float2 v, uint32_t hi) {
+  const float2 hf = make_float2(__uint_as_float(hi << 16), __uint_as_float(hi & 0xffff0000u));
+  const float2 d = __ffma2_rn(hf, make_float2(-1.f, -1.f), v);
+  return pack_bf16(d.x, d.y);
+}
+
+#define TMEM_LD_16(taddr, r)                                                                               \
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];" \
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), \
                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),         \
@@ -309,13 +342,16 @@ __device__ __forceinline__ void tmem_free_512(uint32_t base) {
 // barrier) was last read two K-blocks earlier: every warp of the group has passed the
 // intervening barrier since, including the A-operand reads that follow a K-block's own
 // barrier. With two, a fast warp could overwrite records a slow one was still reading.
+// The K-block's walk descriptor travels with its records (written by the group's walker
+// warp one K-block ahead).
 constexpr int kZStages = 3;
 template <int WT>
 struct alignas(16) ZStage {  // one generator group's 8 hits of one K-block
-  HitRec rec[KG];
+  HitRec rec[KG];          // as fetched; prim holds the carrier phase arg(c_k) / pi
   int n[KG];
-  float2 g[WT][KG];        // taps, tap-major
-  float2 e2[KG][32];       // E2[my_lo], my_lo < L2 <= 32
+  int kb[8];               // cnt, t_first, t_last, origin, base of the K-block
+  float4 g[WT][KG];        // taps |c_k| R as (Re, Re, Im, Im), tap-major
+  float2 e2[KG][32];       // (Re, -Im) E2[my_lo], my_lo < L2 <= 32
 };
 
 static_assert(sizeof(ZStage<8>) % 16 == 0 && sizeof(ZStage<12>) % 16 == 0 && sizeof(ZStage<16>) % 16 == 0,
@@ -328,7 +364,9 @@ constexpr size_t tz_smem_bytes() {
   return 1024 + (size_t)Z::NT * 2 * Z::B_BYTES + kZStages * kGroups * sizeof(ZStage<WT>) + 64 * 8 + 64;
 }
 
-template <int WT, int NP>
+// CT: complex taps (the raw series' pulse table); otherwise the taps are real (the pulse
+// autocorrelation) and each B entry is one packed FP32 product.
+template <int WT, int NP, bool CT>
 __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_t idesc) {
   using Z = ZShape<NP>;
   constexpr int NT = Z::NT, RING = Z::RING, B_BYTES = Z::B_BYTES;
@@ -348,7 +386,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_
   uint64_t* done = tfree + RING;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  __shared__ float2 s_rtab[kRTabS + 5];
+  __shared__ float s_rre[CT ? 1 : kRTabS + 5];    // real pulse autocorrelation
+  __shared__ float2 s_rtab[CT ? kRTabS + 5 : 1];  // complex pulse (raw series)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nx = a.nx, ny = a.ny, M = nx * ny;
@@ -359,7 +398,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_
   const int W = a.taps;
   const bool fp32_form = a.n_pass == 3;
 
-  for (int i = threadIdx.x; i < kRTabS + 5; i += blockDim.x) s_rtab[i] = a.rtab_s[i];
+  for (int i = threadIdx.x; i < kRTabS + 5; i += blockDim.x) {
+    if constexpr (CT) s_rtab[i] = a.rtab_s[i];
+    else s_rre[i] = a.rtab_s[i].x;
+  }
   if (threadIdx.x == 0) {
     for (int i = 0; i < NT; ++i) {
       mbar_init(smem_u32(&tb_full[i]), kGenWarps);
@@ -458,8 +500,14 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_
     const int gw = warp - kGenWarp0;
     const int grp = gw >> 2;            // hits KG grp .. KG grp + 7 of every K-block
     const int wi = gw & 3;              // warp in group
-    const int tg = wi * 32 + lane;      // thread in group
     const int q = warp & 3;             // TMEM lane quarter of this warp
+    // The group's walker (rank 0) fetches the records and walks the K-blocks one ahead,
+    // publishing each descriptor with its records; ranks 1-3 form the taps, the E2 phasors
+    // and the carrier phases. Walkers are warps grp of their groups, so that the four sit
+    // on different SM sub-partitions.
+    const int rank = (wi - grp) & 3;
+    const bool walker = rank == 0;
+    const int tq = (rank - 1) * 32 + lane;  // 0..95 on ranks 1-3
     const uint32_t bar_id = 1 + grp;
     const float pl2 = 2.0f * a.pitch_over_lambda;
     // A operand: this thread's TMEM lane is row (my_hi, mx), element (mx, L2 my_hi)
@@ -474,59 +522,94 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_
     // half-warp, which an 8-byte store serves together) take eight consecutive columns at
     // one hit pair each: their 16-byte chunks (2 grp + pp / 2) ^ (c0 & 7) are all distinct,
     // so the half-warp's 128 bytes cover the 32 banks once.
+    const int tg = wi * 32 + lane;
     const int pp = (tg & 31) >> 3, c0 = ((tg >> 5) << 3) | (tg & 7);  // column c0 + 32 r
     const int my_lo = c0 & (L2 - 1);
     const int nl0 = c0 >> lL2, nl_r = 32 >> lL2;          // tile row of column c0 + 32 r
     const uint32_t boff0 = (uint32_t)(c0 * 128 + (((2 * grp + (pp >> 1)) ^ (c0 & 7)) << 4) + ((pp & 1) << 3));
+    // walker lanes 0-15 move the group's 8 records (hit lane / 2, half lane & 1)
     auto fetch = [&](int64_t hs) {
       uint4 v = make_uint4(0u, 0u, 0u, 0u);
-      const int64_t k = hs + KG * grp + (tg >> 1);
-      if (tg < 2 * KG && k < h1) v = __ldg(reinterpret_cast<const uint4*>(a.hits_sorted + k) + (tg & 1));
+      const int64_t k = hs + KG * grp + (lane >> 1);
+      if (lane < 2 * KG && k < h1) v = __ldg(reinterpret_cast<const uint4*>(a.hits_sorted + k) + (lane & 1));
       return v;
     };
-    {
-      const uint4 v = fetch(h0);
-      if (tg < 2 * KG) reinterpret_cast<uint4*>(&zst[0][grp].rec[tg >> 1])[tg & 1] = v;
-      named_bar(bar_id, 128);
+    auto put = [&](ZStage<WT>& S, uint4 v) {
+      if (lane < 2 * KG) reinterpret_cast<uint4*>(&S.rec[lane >> 1])[lane & 1] = v;
+    };
+    auto put_kb = [&](ZStage<WT>& S, const KBlk& k) {
+      if (lane == 0) *reinterpret_cast<int4*>(S.kb) = make_int4(k.cnt, k.t_first, k.t_last, k.origin);
+      if (lane == 1) S.kb[4] = k.base;
+    };
+    // The walker keeps two loads in flight across a K-block: the window of first-tap rows
+    // of the K-block after next's start (for its descriptor) and the records of the next
+    // K-block but one (stored into its stage a K-block later).
+    TileWalk w;  // walker only
+    int win = 0;
+    uint4 rec_ahead = make_uint4(0u, 0u, 0u, 0u);
+    if (walker && h0 < h1) {
+      const uint4 r0 = fetch(h0);
+      win = load_window(a.sorted_n, h0, h1, lane);
+      const KBlk k0 = kblock_from(win, tr, Z::TMAXZ, W, w);
+      walk_advance(w, k0);
+      win = load_window(a.sorted_n, h0 + k0.cnt, h1, lane);
+      rec_ahead = fetch(h0 + k0.cnt);
+      put(zst[0][grp], r0);
+      put_kb(zst[0][grp], k0);
     }
-    int win = load_window(a.sorted_n, h0, h1, lane);
-    TileWalk w;
+    named_bar(bar_id, 128);
     int j = 0;
     unsigned tix = 0;
     for (int64_t h = h0; h < h1;) {
-      const KBlk kb = kblock_from(win, tr, Z::TMAXZ, W, w);
-      walk_advance(w, kb);
-      const int64_t hn = h + kb.cnt;
-      win = load_window(a.sorted_n, hn, h1, lane);
-      const uint4 recv = fetch(hn);
       ZStage<WT>& S = zst[j % kZStages][grp];
+      const int4 kd = *reinterpret_cast<const int4*>(S.kb);
+      KBlk kb;
+      kb.cnt = kd.x;
+      kb.t_first = kd.y;
+      kb.t_last = kd.z;
+      kb.origin = kd.w;
+      kb.base = S.kb[4];
+      const int64_t hn = h + kb.cnt;
       const int kvalid = kb.cnt - KG * grp;  // hits of this group inside the K-block
-      // taps c_k R((u0 + i) dt); padding hits contribute zero
-      for (int item = tg; item < KG * WT; item += 128) {
-        const int kl = item & (KG - 1), qq = item >> 3;
-        float2 g = make_float2(0.f, 0.f);
-        if (kl < kvalid && qq < W) {
-          const HitRec& hr = S.rec[kl];
-          g = tap_value(s_rtab, a.rtab_s_scale, hr.u0 + (float)qq, hr.cr, hr.ci);
+      if (!walker) {
+        // taps |c_k| R((u0 + i) dt) (the carrier phase arg c_k rides in the A operand);
+        // padding hits contribute zero
+        for (int item = tq; item < KG * WT; item += 96) {
+          const int kl = item & (KG - 1), qq = item >> 3;
+          float2 g = make_float2(0.f, 0.f);
+          if (kl < kvalid && qq < W) {
+            const float4 r = *reinterpret_cast<const float4*>(&S.rec[kl]);  // nglob, u0, cr, ci
+            const float amp = sqrtf(fmaf(r.z, r.z, r.w * r.w));
+            if constexpr (CT) g = tap_value(s_rtab, a.rtab_s_scale, r.y + (float)qq, amp, 0.f);
+            else g.x = amp * tap_real(s_rre, a.rtab_s_scale, r.y + (float)qq);
+          }
+          S.g[qq][kl] = make_float4(g.x, g.x, g.y, g.y);
+          if (qq == 0) S.n[kl] = kl < kvalid ? S.rec[kl].nglob : INT_MIN / 2;
         }
-        S.g[qq][kl] = g;
-        if (qq == 0) S.n[kl] = kl < kvalid ? S.rec[kl].nglob : INT_MIN / 2;
-      }
-      // E2[my_lo] = exp(j 2 pi (d/lambda) my_lo u_z), on the group's last threads (the
-      // first KG WT ones form the taps)
-      for (int item = 127 - tg; item < KG * L2; item += 128) {
-        const int kl = item & (KG - 1), ql = item >> 3;
-        float2 e = make_float2(0.f, 0.f);
-        if (kl < kvalid) {
+        // (Re, -Im) E2[my_lo], E2[my_lo] = exp(j 2 pi (d/lambda) my_lo u_z)
+        for (int item = tq; item < KG * L2; item += 96) {
+          const int kl = item & (KG - 1), ql = item >> 3;
           float s, c;
           sincospi_operand(pl2 * (float)ql * S.rec[kl].uz, &s, &c);
-          e = make_float2(c, s);
+          S.e2[kl][ql] = make_float2(c, -s);
         }
-        S.e2[kl][ql] = e;
+        // carrier phase arg(c_k) / pi into the record's prim field, for the A operand
+        if (tq >= 96 - KG) {
+          const int kl = tq - (96 - KG);
+          S.rec[kl].prim = __float_as_int(atan2f(S.rec[kl].ci, S.rec[kl].cr) * 0.318309886183791f);
+        }
+      } else if (hn < h1) {
+        // the next K-block's descriptor and records (fetched a K-block ago) go to the stage
+        // buffer last read two K-blocks ago (every warp of the group has passed the
+        // previous barrier since); then the loads for the K-block after it
+        const KBlk kn = kblock_from(win, tr, Z::TMAXZ, W, w);
+        walk_advance(w, kn);
+        win = load_window(a.sorted_n, hn + kn.cnt, h1, lane);
+        ZStage<WT>& Sn = zst[(j + 1) % kZStages][grp];
+        put(Sn, rec_ahead);
+        put_kb(Sn, kn);
+        rec_ahead = fetch(hn + kn.cnt);
       }
-      // the next K-block's records go to the stage buffer last read two K-blocks ago
-      // (every warp of the group has passed the previous barrier since)
-      if (tg < 2 * KG) reinterpret_cast<uint4*>(&zst[(j + 1) % kZStages][grp].rec[tg >> 1])[tg & 1] = recv;
       named_bar(bar_id, 128);
 
       // per-K-block A operand: row (my_hi, mx) = this thread's TMEM lane, 8 columns
@@ -534,17 +617,25 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_
       wait_or_abort(smem_u32(&am_empty[aslot]), ((j >> 1) & 1) ^ 1, abort_flag, a.err);
       tc_fence_after();
       {
-        // ey[mx] E1[my_hi] = exp(j 2 pi (d/lambda) ((mx - (nx-1)/2) u_y + (L2 my_hi -
-        // (ny-1)/2) u_z)), one phase per hit (padding hits: 0)
+        // c_k ey[mx] E1[my_hi] / |c_k| = exp(j pi x), x = 2 (d/lambda) ((mx - (nx-1)/2) u_y
+        // + (L2 my_hi - (ny-1)/2) u_z) + arg(c_k) / pi, reduced exactly to [-1, 1]. Padding
+        // hits (zero B rows) keep finite entries: their records are zeros or real hits.
         uint32_t hi[KG], lo[KG];
 #pragma unroll
-        for (int kl = 0; kl < KG; ++kl) {
-          const float2 u = *reinterpret_cast<const float2*>(&S.rec[kl].uy);
-          float sn, cs;
-          sincospi_operand(fmaf(ax, u.x, az * u.y), &sn, &cs);
-          if (kl >= kvalid) sn = cs = 0.f;
-          hi[kl] = pack_bf16(cs, sn);
-          lo[kl] = pack_lo(cs, sn, hi[kl]);
+        for (int kl = 0; kl < KG; kl += 2) {
+          const float4 u0 = *reinterpret_cast<const float4*>(&S.rec[kl].uy);      // uy, uz, phase
+          const float4 u1 = *reinterpret_cast<const float4*>(&S.rec[kl + 1].uy);
+          const float2 x = make_float2(fmaf(ax, u0.x, fmaf(az, u0.y, u0.z)), fmaf(ax, u1.x, fmaf(az, u1.y, u1.z)));
+          const float2 hx = __fmul2_rn(x, make_float2(0.5f, 0.5f));
+          const float2 r = __ffma2_rn(make_float2(rintf(hx.x), rintf(hx.y)), make_float2(-2.f, -2.f), x);
+          const float2 y = __fmul2_rn(r, make_float2(3.14159265358979f, 3.14159265358979f));
+          float2 p0, p1;
+          __sincosf(y.x, &p0.y, &p0.x);
+          __sincosf(y.y, &p1.y, &p1.x);
+          hi[kl] = pack_bf16(p0.x, p0.y);
+          hi[kl + 1] = pack_bf16(p1.x, p1.y);
+          lo[kl] = pack_lo2(p0, hi[kl]);
+          lo[kl + 1] = pack_lo2(p1, hi[kl + 1]);
         }
         const uint32_t ta = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(kAcol + aslot * 64 + KG * grp);
         tmem_st8(ta, hi);
@@ -558,38 +649,44 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_
       // per-tile B operand: every generator thread writes NP / 32 items of every tile
       const int k0 = 2 * pp, k1 = k0 + 1;
       const int nk0 = S.n[k0], nk1 = S.n[k1];
-      const float2 e20 = S.e2[k0][my_lo], e21 = S.e2[k1][my_lo];
+      const float2 ea0 = S.e2[k0][my_lo], ea1 = S.e2[k1][my_lo];
+      const float2 eb0 = make_float2(ea0.y, -ea0.x), eb1 = make_float2(ea1.y, -ea1.x);  // (-Im, -Re)
       const int ntiles = kb.t_last - kb.t_first + 1;
       const int row_first = kb.origin + (kb.t_first - kb.base) * T;  // first row of the first tile
       for (int i = 0; i < ntiles; ++i) {
-        const unsigned tq = tix + (unsigned)i;
-        const int bslot = (int)(tq % NT);
-        wait_or_abort(smem_u32(&tb_empty[bslot]), ((tq / NT) & 1) ^ 1, abort_flag, a.err);
+        const unsigned tqi = tix + (unsigned)i;
+        const int bslot = (int)(tqi % NT);
+        wait_or_abort(smem_u32(&tb_empty[bslot]), ((tqi / NT) & 1) ^ 1, abort_flag, a.err);
         const uint32_t bh = smem_u32(sB + bslot * 2 * B_BYTES), bl = bh + B_BYTES;
         const int trow0 = row_first + i * T + nl0;
 #pragma unroll
         for (int r = 0; r < NP / 32; ++r) {
           const int trow = trow0 + r * nl_r;
           const uint32_t boff = boff0 + (uint32_t)(r * 32 * 128);
-          // row pr: (Re b, -Im b); row NP + pr: (Im b, Re b) = the same BF16 pair with its
-          // halves swapped and the new low half negated (rounding is sign-symmetric)
-          float bx0 = 0.f, nby0 = 0.f, bx1 = 0.f, nby1 = 0.f;
+          // row pr: (Re b, -Im b) = g (Re E2, -Im E2) with the tap g real; row NP + pr:
+          // (Im b, Re b) = the same BF16 pair with its halves swapped and the new low half
+          // negated (rounding is sign-symmetric)
+          float2 v0 = make_float2(0.f, 0.f), v1 = v0;
           const int tap0 = trow - nk0, tap1 = trow - nk1;
-          if ((unsigned)tap0 < (unsigned)WT) {
-            const float2 g = S.g[tap0][k0];
-            bx0 = g.x * e20.x - g.y * e20.y;
-            nby0 = -(g.x * e20.y) - g.y * e20.x;
+          if constexpr (CT) {
+            // complex tap g: (Re b, -Im b) = Re g (Re E2, -Im E2) + Im g (-Im E2, -Re E2)
+            if ((unsigned)tap0 < (unsigned)WT) {
+              const float4 g = S.g[tap0][k0];
+              v0 = __ffma2_rn(make_float2(g.z, g.w), eb0, __fmul2_rn(make_float2(g.x, g.y), ea0));
+            }
+            if ((unsigned)tap1 < (unsigned)WT) {
+              const float4 g = S.g[tap1][k1];
+              v1 = __ffma2_rn(make_float2(g.z, g.w), eb1, __fmul2_rn(make_float2(g.x, g.y), ea1));
+            }
+          } else {
+            if ((unsigned)tap0 < (unsigned)WT) v0 = __fmul2_rn(*reinterpret_cast<const float2*>(&S.g[tap0][k0]), ea0);
+            if ((unsigned)tap1 < (unsigned)WT) v1 = __fmul2_rn(*reinterpret_cast<const float2*>(&S.g[tap1][k1]), ea1);
           }
-          if ((unsigned)tap1 < (unsigned)WT) {
-            const float2 g = S.g[tap1][k1];
-            bx1 = g.x * e21.x - g.y * e21.y;
-            nby1 = -(g.x * e21.y) - g.y * e21.x;
-          }
-          const uint32_t h0 = pack_bf16(bx0, nby0), h1 = pack_bf16(bx1, nby1);
+          const uint32_t h0 = pack_bf16(v0.x, v0.y), h1 = pack_bf16(v1.x, v1.y);
           sts64(bh + boff, h0, h1);
           sts64(bh + boff + NP * 128, __byte_perm(h0, 0u, 0x1032) ^ 0x8000u, __byte_perm(h1, 0u, 0x1032) ^ 0x8000u);
           if (fp32_form) {
-            const uint32_t l0 = pack_lo(bx0, nby0, h0), l1 = pack_lo(bx1, nby1, h1);
+            const uint32_t l0 = pack_lo2(v0, h0), l1 = pack_lo2(v1, h1);
             sts64(bl + boff, l0, l1);
             sts64(bl + boff + NP * 128, __byte_perm(l0, 0u, 0x1032) ^ 0x8000u, __byte_perm(l1, 0u, 0x1032) ^ 0x8000u);
           }
@@ -889,35 +986,46 @@ int zs_pairs(int nx, int ny, int W, int want) {
   return f96 ? 96 : (f64 ? 64 : (f32 ? 32 : 0));
 }
 
-template <int WT>
-cudaError_t set_attr() {
-  cudaError_t e = cudaFuncSetAttribute(k_synth_tc<WT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)tc_smem_bytes<WT>());
+template <int WT, bool CT>
+cudaError_t set_attr_tz() {
+  cudaError_t e = cudaFuncSetAttribute(k_synth_tz<WT, 32, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)tz_smem_bytes<WT, 32>());
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_synth_tz<WT, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)tz_smem_bytes<WT, 32>());
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_synth_tz<WT, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(k_synth_tz<WT, 64, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)tz_smem_bytes<WT, 64>());
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_synth_tz<WT, 96>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(k_synth_tz<WT, 96, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)tz_smem_bytes<WT, 96>());
   return e;
 }
 
 template <int WT>
-cudaError_t launch_one(const SynthArgs& a, int zs_np, int sm_count, cudaStream_t st) {
+cudaError_t set_attr() {
+  cudaError_t e = cudaFuncSetAttribute(k_synth_tc<WT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)tc_smem_bytes<WT>());
+  if (e == cudaSuccess) e = set_attr_tz<WT, false>();
+  if (e == cudaSuccess) e = set_attr_tz<WT, true>();
+  return e;
+}
+
+template <int WT, bool CT>
+cudaError_t launch_tz(const SynthArgs& a, int zs_np, int sm_count, cudaStream_t st) {
   if (zs_np == 32)
-    return launch_pdl(k_synth_tz<WT, 32>, dim3(sm_count), dim3(kThreadsTC), tz_smem_bytes<WT, 32>(), st, a,
-               make_idesc(1, 128, 64));
-  else if (zs_np == 64)
-    return launch_pdl(k_synth_tz<WT, 64>, dim3(sm_count), dim3(kThreadsTC), tz_smem_bytes<WT, 64>(), st, a,
-               make_idesc(1, 128, 128));
-  else if (zs_np == 96)
-    return launch_pdl(k_synth_tz<WT, 96>, dim3(sm_count), dim3(kThreadsTC), tz_smem_bytes<WT, 96>(), st, a,
-               make_idesc(1, 128, 192));
+    return launch_pdl(k_synth_tz<WT, 32, CT>, dim3(sm_count), dim3(kThreadsTC), tz_smem_bytes<WT, 32>(), st, a,
+                      make_idesc(1, 128, 64));
+  if (zs_np == 64)
+    return launch_pdl(k_synth_tz<WT, 64, CT>, dim3(sm_count), dim3(kThreadsTC), tz_smem_bytes<WT, 64>(), st, a,
+                      make_idesc(1, 128, 128));
+  return launch_pdl(k_synth_tz<WT, 96, CT>, dim3(sm_count), dim3(kThreadsTC), tz_smem_bytes<WT, 96>(), st, a,
+                    make_idesc(1, 128, 192));
+}
+
+template <int WT>
+cudaError_t launch_one(const SynthArgs& a, int zs_np, int sm_count, cudaStream_t st) {
+  if (zs_np == 32 || zs_np == 64 || zs_np == 96)
+    return a.cplx_taps ? launch_tz<WT, true>(a, zs_np, sm_count, st) : launch_tz<WT, false>(a, zs_np, sm_count, st);
   return launch_pdl(k_synth_tc<WT>, dim3(sm_count), dim3(kThreadsTC), tc_smem_bytes<WT>(), st, a,
-               make_idesc(1, 128, 2 * a.ny));
+                    make_idesc(1, 128, 2 * a.ny));
 }
 
 }  // namespace

@@ -382,3 +382,16 @@ def test_lambertian_power_matches_quadrature():
     ref, _ = integrate.dblquad(f, -p["hfov"] / 2, p["hfov"] / 2, -p["vfov"] / 2, p["vfov"] / 2,
                                epsabs=1e-12, epsrel=1e-10)
     assert abs(got - ref) < 2e-4 * ref
+
+
+def test_acf_is_real_for_centred_chirp():
+    """The Hann window is even and the chirp is centred on t = 0, so the window product
+    w(s + u/2) w(s - u/2) is even in s and R(u) keeps only its cosine part: a real function
+    (the tensor-core synthesis forms real taps |c_k| R and carries arg c_k in the element
+    phase). A sign slip in any of the closed form's nine exponential integrals leaves an
+    imaginary part."""
+    for tp, bw in ((T_P, BW), (40e-6, 120e3), (250e-6, 10e3)):
+        u = np.linspace(-1.1 * tp, 1.1 * tp, 801)
+        r = oracle.pulse_acf(u, tp, bw)
+        assert np.max(np.abs(r.imag)) < 1e-14
+        assert np.max(np.abs(r.real)) == pytest.approx(1.0, abs=1e-12)
