@@ -26,11 +26,11 @@
 //   (384 / 2 NP) and so fewer tiles per K-block. The sixteen generator warps form four
 //   independent groups, one per MMA K step (8 hits), each with one warp per TMEM lane
 //   quarter and its own named barrier. The pulse autocorrelation is real (even window,
-//   chirp centred on t = 0), so with c_k = |c_k| exp(j pi phi_k) the taps |c_k| R are
-//   real, phi_k joins the A operand's phase at no cost, and each B entry is one packed
-//   FP32 product g (Re E2, -Im E2). In each group one walker warp fetches the records
-//   and walks the K-blocks one ahead, publishing every K-block's descriptor with its
-//   records; the other three form the taps, E2 and phi_k.
+//   chirp centred on t = 0), so B = R_k(n) (c_k E2[my_lo]) with R_k(n) real: c_k joins the
+//   per-hit E2 factor (L2 complex products per hit) and each B entry is one packed FP32
+//   product R (Re, -Im) of c_k E2. In each group one walker warp fetches the records and
+//   walks the K-blocks one ahead, publishing every K-block's descriptor with its
+//   records; the other three form the taps and the c_k E2 factors.
 // k_synth_tc (small arrays): A[(n, mx)][k] = g_k(n) ey[mx] per tile (T = 128 / nx) and
 //   B[k][(my, re/im)] = ez[my] once per K-block, both in shared memory.
 #include <limits.h>
@@ -347,11 +347,11 @@ __device__ __forceinline__ void tmem_free_512(uint32_t base) {
 constexpr int kZStages = 3;
 template <int WT>
 struct alignas(16) ZStage {  // one generator group's 8 hits of one K-block
-  HitRec rec[KG];          // as fetched; prim holds the carrier phase arg(c_k) / pi
+  HitRec rec[KG];
   int n[KG];
   int kb[8];               // cnt, t_first, t_last, origin, base of the K-block
-  float4 g[WT][KG];        // taps |c_k| R as (Re, Re, Im, Im), tap-major
-  float2 e2[KG][32];       // (Re, -Im) E2[my_lo], my_lo < L2 <= 32
+  float4 g[WT + 1][KG];    // taps R as (Re, Re, Im, Im), tap-major; row WT stays zero
+  float2 e2[KG][32];       // (Re, -Im) of c_k E2[my_lo], my_lo < L2 <= 32
 };
 
 static_assert(sizeof(ZStage<8>) % 16 == 0 && sizeof(ZStage<12>) % 16 == 0 && sizeof(ZStage<16>) % 16 == 0,
@@ -402,6 +402,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_
     if constexpr (CT) s_rtab[i] = a.rtab_s[i];
     else s_rre[i] = a.rtab_s[i].x;
   }
+  for (int i = threadIdx.x; i < kZStages * kGroups * KG; i += blockDim.x)
+    zst[i / (kGroups * KG)][(i / KG) % kGroups].g[WT][i % KG] = make_float4(0.f, 0.f, 0.f, 0.f);
   if (threadIdx.x == 0) {
     for (int i = 0; i < NT; ++i) {
       mbar_init(smem_u32(&tb_full[i]), kGenWarps);
@@ -502,8 +504,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_
     const int wi = gw & 3;              // warp in group
     const int q = warp & 3;             // TMEM lane quarter of this warp
     // The group's walker (rank 0) fetches the records and walks the K-blocks one ahead,
-    // publishing each descriptor with its records; ranks 1-3 form the taps, the E2 phasors
-    // and the carrier phases. Walkers are warps grp of their groups, so that the four sit
+    // publishing each descriptor with its records; ranks 1-3 form the taps and the c_k E2
+    // products. Walkers are warps grp of their groups, so that the four sit
     // on different SM sub-partitions.
     const int rank = (wi - grp) & 3;
     const bool walker = rank == 0;
@@ -572,31 +574,25 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_
       const int64_t hn = h + kb.cnt;
       const int kvalid = kb.cnt - KG * grp;  // hits of this group inside the K-block
       if (!walker) {
-        // taps |c_k| R((u0 + i) dt) (the carrier phase arg c_k rides in the A operand);
-        // padding hits contribute zero
+        // taps R((u0 + i) dt) (c_k rides in the E2 factor); padding hits contribute zero
         for (int item = tq; item < KG * WT; item += 96) {
           const int kl = item & (KG - 1), qq = item >> 3;
           float2 g = make_float2(0.f, 0.f);
           if (kl < kvalid && qq < W) {
-            const float4 r = *reinterpret_cast<const float4*>(&S.rec[kl]);  // nglob, u0, cr, ci
-            const float amp = sqrtf(fmaf(r.z, r.z, r.w * r.w));
-            if constexpr (CT) g = tap_value(s_rtab, a.rtab_s_scale, r.y + (float)qq, amp, 0.f);
-            else g.x = amp * tap_real(s_rre, a.rtab_s_scale, r.y + (float)qq);
+            const float u0 = S.rec[kl].u0 + (float)qq;
+            if constexpr (CT) g = tap_value(s_rtab, a.rtab_s_scale, u0, 1.f, 0.f);
+            else g.x = tap_real(s_rre, a.rtab_s_scale, u0);
           }
           S.g[qq][kl] = make_float4(g.x, g.x, g.y, g.y);
           if (qq == 0) S.n[kl] = kl < kvalid ? S.rec[kl].nglob : INT_MIN / 2;
         }
-        // (Re, -Im) E2[my_lo], E2[my_lo] = exp(j 2 pi (d/lambda) my_lo u_z)
+        // (Re, -Im) of c_k E2[my_lo], E2[my_lo] = exp(j 2 pi (d/lambda) my_lo u_z)
         for (int item = tq; item < KG * L2; item += 96) {
           const int kl = item & (KG - 1), ql = item >> 3;
+          const float4 r = *reinterpret_cast<const float4*>(&S.rec[kl]);  // nglob, u0, cr, ci
           float s, c;
           sincospi_operand(pl2 * (float)ql * S.rec[kl].uz, &s, &c);
-          S.e2[kl][ql] = make_float2(c, -s);
-        }
-        // carrier phase arg(c_k) / pi into the record's prim field, for the A operand
-        if (tq >= 96 - KG) {
-          const int kl = tq - (96 - KG);
-          S.rec[kl].prim = __float_as_int(atan2f(S.rec[kl].ci, S.rec[kl].cr) * 0.318309886183791f);
+          S.e2[kl][ql] = make_float2(fmaf(r.z, c, -r.w * s), -fmaf(r.z, s, r.w * c));
         }
       } else if (hn < h1) {
         // the next K-block's descriptor and records (fetched a K-block ago) go to the stage
@@ -617,15 +613,15 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_
       wait_or_abort(smem_u32(&am_empty[aslot]), ((j >> 1) & 1) ^ 1, abort_flag, a.err);
       tc_fence_after();
       {
-        // c_k ey[mx] E1[my_hi] / |c_k| = exp(j pi x), x = 2 (d/lambda) ((mx - (nx-1)/2) u_y
-        // + (L2 my_hi - (ny-1)/2) u_z) + arg(c_k) / pi, reduced exactly to [-1, 1]. Padding
-        // hits (zero B rows) keep finite entries: their records are zeros or real hits.
+        // ey[mx] E1[my_hi] = exp(j pi x), x = 2 (d/lambda) ((mx - (nx-1)/2) u_y + (L2 my_hi
+        // - (ny-1)/2) u_z), reduced exactly to [-1, 1]. Padding hits (zero B rows) keep
+        // finite entries: their records are zeros or real hits.
         uint32_t hi[KG], lo[KG];
 #pragma unroll
         for (int kl = 0; kl < KG; kl += 2) {
-          const float4 u0 = *reinterpret_cast<const float4*>(&S.rec[kl].uy);      // uy, uz, phase
-          const float4 u1 = *reinterpret_cast<const float4*>(&S.rec[kl + 1].uy);
-          const float2 x = make_float2(fmaf(ax, u0.x, fmaf(az, u0.y, u0.z)), fmaf(ax, u1.x, fmaf(az, u1.y, u1.z)));
+          const float2 u0 = *reinterpret_cast<const float2*>(&S.rec[kl].uy);
+          const float2 u1 = *reinterpret_cast<const float2*>(&S.rec[kl + 1].uy);
+          const float2 x = make_float2(fmaf(ax, u0.x, az * u0.y), fmaf(ax, u1.x, az * u1.y));
           const float2 hx = __fmul2_rn(x, make_float2(0.5f, 0.5f));
           const float2 r = __ffma2_rn(make_float2(rintf(hx.x), rintf(hx.y)), make_float2(-2.f, -2.f), x);
           const float2 y = __fmul2_rn(r, make_float2(3.14159265358979f, 3.14159265358979f));
@@ -679,8 +675,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_
               v1 = __ffma2_rn(make_float2(g.z, g.w), eb1, __fmul2_rn(make_float2(g.x, g.y), ea1));
             }
           } else {
-            if ((unsigned)tap0 < (unsigned)WT) v0 = __fmul2_rn(*reinterpret_cast<const float2*>(&S.g[tap0][k0]), ea0);
-            if ((unsigned)tap1 < (unsigned)WT) v1 = __fmul2_rn(*reinterpret_cast<const float2*>(&S.g[tap1][k1]), ea1);
+            // taps outside 0 .. WT - 1 (and padding hits) read the zero row WT
+            const unsigned c0i = min((unsigned)tap0, (unsigned)WT), c1i = min((unsigned)tap1, (unsigned)WT);
+            v0 = __fmul2_rn(*reinterpret_cast<const float2*>(&S.g[c0i][k0]), ea0);
+            v1 = __fmul2_rn(*reinterpret_cast<const float2*>(&S.g[c1i][k1]), ea1);
           }
           const uint32_t h0 = pack_bf16(v0.x, v0.y), h1 = pack_bf16(v1.x, v1.y);
           sts64(bh + boff, h0, h1);
