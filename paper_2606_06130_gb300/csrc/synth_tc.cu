@@ -28,9 +28,9 @@
 //   quarter and its own named barrier. The pulse autocorrelation is real (even window,
 //   chirp centred on t = 0), so B = R_k(n) (c_k E2[my_lo]) with R_k(n) real: c_k joins the
 //   per-hit E2 factor (L2 complex products per hit) and each B entry is one packed FP32
-//   product R (Re, -Im) of c_k E2. In each group one walker warp fetches the records and
-//   walks the K-blocks one ahead, publishing every K-block's descriptor with its
-//   records; the other three form the taps and the c_k E2 factors.
+//   product R (Re, -Im) of c_k E2. A fifth warp per group (the stage helper) works one
+//   K-block ahead: it walks the K-blocks, moves the records and forms the taps and the
+//   c_k E2 factors, so the four operand warps only form A and B.
 // k_synth_tc (small arrays): A[(n, mx)][k] = g_k(n) ey[mx] per tile (T = 128 / nx) and
 //   B[k][(my, re/im)] = ez[my] once per K-block, both in shared memory.
 #include <limits.h>
@@ -47,6 +47,7 @@ constexpr int KH = 32;           // hits per K-block: K = 64 BF16 columns (re, i
 constexpr int TMAX = 5;          // tiles one K-block may touch (k_synth_tc)
 constexpr int kGenWarps = 16;
 constexpr int kGenWarp0 = 5;     // warp 0: MMA, warps 1..4: epilogue, warps 5..20: generators
+                                 // (k_synth_tz: operand warps, then warps 21..24: stage helpers)
 constexpr int kThreadsTC = 32 * (kGenWarp0 + kGenWarps);
 constexpr int kGenThreads = 32 * kGenWarps;
 constexpr int M_BYTES = 128 * 128;  // 128 rows x 64 BF16
@@ -61,6 +62,8 @@ constexpr int RING = 8;          // TMEM accumulators of 64 columns
 constexpr int kGroups = 4;
 constexpr int KG = KH / kGroups;   // hits per generator group = one MMA K step
 constexpr int kAcol = 384;         // TMEM columns of the two per-K-block A slots (hi 32, lo 32)
+constexpr int kThreadsTZ = kThreadsTC + 32 * kGroups;  // plus one stage helper per group
+constexpr int kGroupThreads = 32 * 5;                   // four operand warps and the helper
 
 // Tile shape of k_synth_tz for NP complex output columns per tile.
 template <int NP>
@@ -367,7 +370,7 @@ constexpr size_t tz_smem_bytes() {
 // CT: complex taps (the raw series' pulse table); otherwise the taps are real (the pulse
 // autocorrelation) and each B entry is one packed FP32 product.
 template <int WT, int NP, bool CT>
-__global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_t idesc) {
+__global__ void __launch_bounds__(kThreadsTZ, 1) k_synth_tz(SynthArgs a, uint32_t idesc) {
   using Z = ZShape<NP>;
   constexpr int NT = Z::NT, RING = Z::RING, B_BYTES = Z::B_BYTES;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -497,19 +500,90 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_
                                     const int64_t row = r0 + nl;
                                     return reinterpret_cast<float*>(a.S + row * M + (my_hi * L2 + my_lo) * nx + mx);
                                   });
+  } else if (warp >= kGenWarp0 + kGenWarps) {
+    // ------------------------------------------------------------- stage helpers
+    // One warp per generator group works one K-block ahead of the group's four operand
+    // warps: it walks the K-blocks, moves the records (fetched two K-blocks ahead, so the
+    // loads overlap a whole K-block) and forms the taps R and the factors c_k E2 into the
+    // stage the operand warps take next. The group's named barrier at the top of every
+    // K-block hands one stage over; the stage written after barrier j is the one the
+    // operand warps last read during K-block j - 2, before barrier j - 1.
+    const int grp = warp - (kGenWarp0 + kGenWarps);
+    const uint32_t bar_id = 1 + grp;
+    const float pl2 = 2.0f * a.pitch_over_lambda;
+    // lanes 0-15 move the group's 8 records (hit lane / 2, half lane & 1)
+    auto fetch = [&](int64_t hs) {
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      const int64_t k = hs + KG * grp + (lane >> 1);
+      if (lane < 2 * KG && k < h1) v = __ldg(reinterpret_cast<const uint4*>(a.hits_sorted + k) + (lane & 1));
+      return v;
+    };
+    auto put = [&](ZStage<WT>& S, uint4 v, const KBlk& k) {
+      if (lane < 2 * KG) reinterpret_cast<uint4*>(&S.rec[lane >> 1])[lane & 1] = v;
+      if (lane == 0) *reinterpret_cast<int4*>(S.kb) = make_int4(k.cnt, k.t_first, k.t_last, k.origin);
+      if (lane == 1) S.kb[4] = k.base;
+      __syncwarp();  // the records are read back by other lanes below
+    };
+    auto fill = [&](ZStage<WT>& S, int cnt) {
+      const int kvalid = cnt - KG * grp;  // hits of this group inside the K-block
+      // taps R((u0 + i) dt) (c_k rides in the E2 factor); padding hits contribute zero
+      for (int item = lane; item < KG * WT; item += 32) {
+        const int kl = item & (KG - 1), qq = item >> 3;
+        float2 g = make_float2(0.f, 0.f);
+        if (kl < kvalid && qq < W) {
+          const float u0 = S.rec[kl].u0 + (float)qq;
+          if constexpr (CT) g = tap_value(s_rtab, a.rtab_s_scale, u0, 1.f, 0.f);
+          else g.x = tap_real(s_rre, a.rtab_s_scale, u0);
+        }
+        S.g[qq][kl] = make_float4(g.x, g.x, g.y, g.y);
+        if (qq == 0) S.n[kl] = kl < kvalid ? S.rec[kl].nglob : INT_MIN / 2;
+      }
+      // (Re, -Im) of c_k E2[my_lo], E2[my_lo] = exp(j 2 pi (d/lambda) my_lo u_z)
+      for (int item = lane; item < KG * L2; item += 32) {
+        const int kl = item & (KG - 1), ql = item >> 3;
+        const float4 r = *reinterpret_cast<const float4*>(&S.rec[kl]);  // nglob, u0, cr, ci
+        float s, c;
+        sincospi_operand(pl2 * (float)ql * S.rec[kl].uz, &s, &c);
+        S.e2[kl][ql] = make_float2(fmaf(r.z, c, -r.w * s), -fmaf(r.z, s, r.w * c));
+      }
+    };
+    TileWalk w;
+    KBlk kc{};
+    int win = 0;
+    uint4 rec_ahead = make_uint4(0u, 0u, 0u, 0u);
+    if (h0 < h1) {
+      const uint4 r0 = fetch(h0);
+      win = load_window(a.sorted_n, h0, h1, lane);
+      kc = kblock_from(win, tr, Z::TMAXZ, W, w);
+      walk_advance(w, kc);
+      win = load_window(a.sorted_n, h0 + kc.cnt, h1, lane);
+      rec_ahead = fetch(h0 + kc.cnt);
+      put(zst[0][grp], r0, kc);
+      fill(zst[0][grp], kc.cnt);
+    }
+    int j = 0;
+    for (int64_t h = h0; h < h1;) {
+      named_bar(bar_id, kGroupThreads);
+      const int64_t hn = h + kc.cnt;
+      if (hn < h1) {
+        const KBlk kn = kblock_from(win, tr, Z::TMAXZ, W, w);
+        walk_advance(w, kn);
+        win = load_window(a.sorted_n, hn + kn.cnt, h1, lane);
+        ZStage<WT>& Sn = zst[(j + 1) % kZStages][grp];
+        put(Sn, rec_ahead, kn);
+        rec_ahead = fetch(hn + kn.cnt);
+        fill(Sn, kn.cnt);
+        kc = kn;
+      }
+      ++j;
+      h = hn;
+    }
   } else {
-    // ------------------------------------------------------------- operand generators
+    // ------------------------------------------------------------- operand warps
     const int gw = warp - kGenWarp0;
     const int grp = gw >> 2;            // hits KG grp .. KG grp + 7 of every K-block
     const int wi = gw & 3;              // warp in group
     const int q = warp & 3;             // TMEM lane quarter of this warp
-    // The group's walker (rank 0) fetches the records and walks the K-blocks one ahead,
-    // publishing each descriptor with its records; ranks 1-3 form the taps and the c_k E2
-    // products. Walkers are warps grp of their groups, so that the four sit
-    // on different SM sub-partitions.
-    const int rank = (wi - grp) & 3;
-    const bool walker = rank == 0;
-    const int tq = (rank - 1) * 32 + lane;  // 0..95 on ranks 1-3
     const uint32_t bar_id = 1 + grp;
     const float pl2 = 2.0f * a.pitch_over_lambda;
     // A operand: this thread's TMEM lane is row (my_hi, mx), element (mx, L2 my_hi)
@@ -529,40 +603,11 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_
     const int my_lo = c0 & (L2 - 1);
     const int nl0 = c0 >> lL2, nl_r = 32 >> lL2;          // tile row of column c0 + 32 r
     const uint32_t boff0 = (uint32_t)(c0 * 128 + (((2 * grp + (pp >> 1)) ^ (c0 & 7)) << 4) + ((pp & 1) << 3));
-    // walker lanes 0-15 move the group's 8 records (hit lane / 2, half lane & 1)
-    auto fetch = [&](int64_t hs) {
-      uint4 v = make_uint4(0u, 0u, 0u, 0u);
-      const int64_t k = hs + KG * grp + (lane >> 1);
-      if (lane < 2 * KG && k < h1) v = __ldg(reinterpret_cast<const uint4*>(a.hits_sorted + k) + (lane & 1));
-      return v;
-    };
-    auto put = [&](ZStage<WT>& S, uint4 v) {
-      if (lane < 2 * KG) reinterpret_cast<uint4*>(&S.rec[lane >> 1])[lane & 1] = v;
-    };
-    auto put_kb = [&](ZStage<WT>& S, const KBlk& k) {
-      if (lane == 0) *reinterpret_cast<int4*>(S.kb) = make_int4(k.cnt, k.t_first, k.t_last, k.origin);
-      if (lane == 1) S.kb[4] = k.base;
-    };
-    // The walker keeps two loads in flight across a K-block: the window of first-tap rows
-    // of the K-block after next's start (for its descriptor) and the records of the next
-    // K-block but one (stored into its stage a K-block later).
-    TileWalk w;  // walker only
-    int win = 0;
-    uint4 rec_ahead = make_uint4(0u, 0u, 0u, 0u);
-    if (walker && h0 < h1) {
-      const uint4 r0 = fetch(h0);
-      win = load_window(a.sorted_n, h0, h1, lane);
-      const KBlk k0 = kblock_from(win, tr, Z::TMAXZ, W, w);
-      walk_advance(w, k0);
-      win = load_window(a.sorted_n, h0 + k0.cnt, h1, lane);
-      rec_ahead = fetch(h0 + k0.cnt);
-      put(zst[0][grp], r0);
-      put_kb(zst[0][grp], k0);
-    }
-    named_bar(bar_id, 128);
     int j = 0;
     unsigned tix = 0;
     for (int64_t h = h0; h < h1;) {
+      // the helper has filled this K-block's stage
+      named_bar(bar_id, kGroupThreads);
       ZStage<WT>& S = zst[j % kZStages][grp];
       const int4 kd = *reinterpret_cast<const int4*>(S.kb);
       KBlk kb;
@@ -572,41 +617,6 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_
       kb.origin = kd.w;
       kb.base = S.kb[4];
       const int64_t hn = h + kb.cnt;
-      const int kvalid = kb.cnt - KG * grp;  // hits of this group inside the K-block
-      if (!walker) {
-        // taps R((u0 + i) dt) (c_k rides in the E2 factor); padding hits contribute zero
-        for (int item = tq; item < KG * WT; item += 96) {
-          const int kl = item & (KG - 1), qq = item >> 3;
-          float2 g = make_float2(0.f, 0.f);
-          if (kl < kvalid && qq < W) {
-            const float u0 = S.rec[kl].u0 + (float)qq;
-            if constexpr (CT) g = tap_value(s_rtab, a.rtab_s_scale, u0, 1.f, 0.f);
-            else g.x = tap_real(s_rre, a.rtab_s_scale, u0);
-          }
-          S.g[qq][kl] = make_float4(g.x, g.x, g.y, g.y);
-          if (qq == 0) S.n[kl] = kl < kvalid ? S.rec[kl].nglob : INT_MIN / 2;
-        }
-        // (Re, -Im) of c_k E2[my_lo], E2[my_lo] = exp(j 2 pi (d/lambda) my_lo u_z)
-        for (int item = tq; item < KG * L2; item += 96) {
-          const int kl = item & (KG - 1), ql = item >> 3;
-          const float4 r = *reinterpret_cast<const float4*>(&S.rec[kl]);  // nglob, u0, cr, ci
-          float s, c;
-          sincospi_operand(pl2 * (float)ql * S.rec[kl].uz, &s, &c);
-          S.e2[kl][ql] = make_float2(fmaf(r.z, c, -r.w * s), -fmaf(r.z, s, r.w * c));
-        }
-      } else if (hn < h1) {
-        // the next K-block's descriptor and records (fetched a K-block ago) go to the stage
-        // buffer last read two K-blocks ago (every warp of the group has passed the
-        // previous barrier since); then the loads for the K-block after it
-        const KBlk kn = kblock_from(win, tr, Z::TMAXZ, W, w);
-        walk_advance(w, kn);
-        win = load_window(a.sorted_n, hn + kn.cnt, h1, lane);
-        ZStage<WT>& Sn = zst[(j + 1) % kZStages][grp];
-        put(Sn, rec_ahead);
-        put_kb(Sn, kn);
-        rec_ahead = fetch(hn + kn.cnt);
-      }
-      named_bar(bar_id, 128);
 
       // per-K-block A operand: row (my_hi, mx) = this thread's TMEM lane, 8 columns
       const int aslot = j & 1;
@@ -636,11 +646,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_
         const uint32_t ta = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(kAcol + aslot * 64 + KG * grp);
         tmem_st8(ta, hi);
         if (fp32_form) tmem_st8(ta + 32, lo);
-        tmem_st_wait();
+        // completed (tcgen05.wait::st) and signalled after the first tile's B operand, so
+        // that the tensor-memory stores drain while the B entries are formed
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(&am_full[aslot]));
 
       // per-tile B operand: every generator thread writes NP / 32 items of every tile
       const int k0 = 2 * pp, k1 = k0 + 1;
@@ -688,6 +696,12 @@ __global__ void __launch_bounds__(kThreadsTC, 1) k_synth_tz(SynthArgs a, uint32_
             sts64(bl + boff, l0, l1);
             sts64(bl + boff + NP * 128, __byte_perm(l0, 0u, 0x1032) ^ 0x8000u, __byte_perm(l1, 0u, 0x1032) ^ 0x8000u);
           }
+        }
+        if (i == 0) {
+          tmem_st_wait();
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(smem_u32(&am_full[aslot]));
         }
         fence_proxy_async();
         __syncwarp();
@@ -1009,12 +1023,12 @@ cudaError_t set_attr() {
 template <int WT, bool CT>
 cudaError_t launch_tz(const SynthArgs& a, int zs_np, int sm_count, cudaStream_t st) {
   if (zs_np == 32)
-    return launch_pdl(k_synth_tz<WT, 32, CT>, dim3(sm_count), dim3(kThreadsTC), tz_smem_bytes<WT, 32>(), st, a,
+    return launch_pdl(k_synth_tz<WT, 32, CT>, dim3(sm_count), dim3(kThreadsTZ), tz_smem_bytes<WT, 32>(), st, a,
                       make_idesc(1, 128, 64));
   if (zs_np == 64)
-    return launch_pdl(k_synth_tz<WT, 64, CT>, dim3(sm_count), dim3(kThreadsTC), tz_smem_bytes<WT, 64>(), st, a,
+    return launch_pdl(k_synth_tz<WT, 64, CT>, dim3(sm_count), dim3(kThreadsTZ), tz_smem_bytes<WT, 64>(), st, a,
                       make_idesc(1, 128, 128));
-  return launch_pdl(k_synth_tz<WT, 96, CT>, dim3(sm_count), dim3(kThreadsTC), tz_smem_bytes<WT, 96>(), st, a,
+  return launch_pdl(k_synth_tz<WT, 96, CT>, dim3(sm_count), dim3(kThreadsTZ), tz_smem_bytes<WT, 96>(), st, a,
                     make_idesc(1, 128, 192));
 }
 
