@@ -620,9 +620,9 @@ __global__ void __launch_bounds__(kThreadsTZ, 1) k_synth_tz(SynthArgs a, uint32_
 
       // per-K-block A operand: row (my_hi, mx) = this thread's TMEM lane, 8 columns
       const int aslot = j & 1;
-      wait_or_abort(smem_u32(&am_empty[aslot]), ((j >> 1) & 1) ^ 1, abort_flag, a.err);
-      tc_fence_after();
-      {
+      auto a_form = [&]() {
+        wait_or_abort(smem_u32(&am_empty[aslot]), ((j >> 1) & 1) ^ 1, abort_flag, a.err);
+        tc_fence_after();
         // ey[mx] E1[my_hi] = exp(j pi x), x = 2 (d/lambda) ((mx - (nx-1)/2) u_y + (L2 my_hi
         // - (ny-1)/2) u_z), reduced exactly to [-1, 1]. Padding hits (zero B rows) keep
         // finite entries: their records are zeros or real hits.
@@ -646,9 +646,13 @@ __global__ void __launch_bounds__(kThreadsTZ, 1) k_synth_tz(SynthArgs a, uint32_
         const uint32_t ta = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(kAcol + aslot * 64 + KG * grp);
         tmem_st8(ta, hi);
         if (fp32_form) tmem_st8(ta + 32, lo);
-        // completed (tcgen05.wait::st) and signalled after the first tile's B operand, so
-        // that the tensor-memory stores drain while the B entries are formed
-      }
+      };
+      auto a_signal = [&]() {
+        tmem_st_wait();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&am_full[aslot]));
+      };
 
       // per-tile B operand: every generator thread writes NP / 32 items of every tile
       const int k0 = 2 * pp, k1 = k0 + 1;
@@ -657,7 +661,7 @@ __global__ void __launch_bounds__(kThreadsTZ, 1) k_synth_tz(SynthArgs a, uint32_
       const float2 eb0 = make_float2(ea0.y, -ea0.x), eb1 = make_float2(ea1.y, -ea1.x);  // (-Im, -Re)
       const int ntiles = kb.t_last - kb.t_first + 1;
       const int row_first = kb.origin + (kb.t_first - kb.base) * T;  // first row of the first tile
-      for (int i = 0; i < ntiles; ++i) {
+      auto b_form = [&](int i) {
         const unsigned tqi = tix + (unsigned)i;
         const int bslot = (int)(tqi % NT);
         wait_or_abort(smem_u32(&tb_empty[bslot]), ((tqi / NT) & 1) ^ 1, abort_flag, a.err);
@@ -697,16 +701,20 @@ __global__ void __launch_bounds__(kThreadsTZ, 1) k_synth_tz(SynthArgs a, uint32_
             sts64(bl + boff + NP * 128, __byte_perm(l0, 0u, 0x1032) ^ 0x8000u, __byte_perm(l1, 0u, 0x1032) ^ 0x8000u);
           }
         }
-        if (i == 0) {
-          tmem_st_wait();
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(smem_u32(&am_full[aslot]));
-        }
+        return bslot;
+      };
+      auto b_signal = [&](int bslot) {
         fence_proxy_async();
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_u32(&tb_full[bslot]));
-      }
+      };
+      // the A operand's tensor-memory stores drain while the first tile's B entries are
+      // formed; then both are signalled
+      a_form();
+      const int s0 = b_form(0);
+      a_signal();
+      b_signal(s0);
+      for (int i = 1; i < ntiles; ++i) b_signal(b_form(i));
       tix += (unsigned)ntiles;
       ++j;
       h = hn;
