@@ -518,27 +518,36 @@ __global__ void __launch_bounds__(kThreadsTZ, 1) k_synth_tz(SynthArgs a, uint32_
       if (lane < 2 * KG && k < h1) v = __ldg(reinterpret_cast<const uint4*>(a.hits_sorted + k) + (lane & 1));
       return v;
     };
-    auto put = [&](ZStage<WT>& S, uint4 v, const KBlk& k) {
+    auto put_rec = [&](ZStage<WT>& S, uint4 v) {
       if (lane < 2 * KG) reinterpret_cast<uint4*>(&S.rec[lane >> 1])[lane & 1] = v;
-      if (lane == 0) *reinterpret_cast<int4*>(S.kb) = make_int4(k.cnt, k.t_first, k.t_last, k.origin);
-      if (lane == 1) S.kb[4] = k.base;
       __syncwarp();  // the records are read back by other lanes below
     };
-    auto fill = [&](ZStage<WT>& S, int cnt) {
-      const int kvalid = cnt - KG * grp;  // hits of this group inside the K-block
-      // taps R((u0 + i) dt) (c_k rides in the E2 factor); padding hits contribute zero
-      for (int item = lane; item < KG * WT; item += 32) {
-        const int kl = item & (KG - 1), qq = item >> 3;
-        float2 g = make_float2(0.f, 0.f);
-        if (kl < kvalid && qq < W) {
-          const float u0 = S.rec[kl].u0 + (float)qq;
-          if constexpr (CT) g = tap_value(s_rtab, a.rtab_s_scale, u0, 1.f, 0.f);
-          else g.x = tap_real(s_rre, a.rtab_s_scale, u0);
+    // the descriptor and the first-tap rows (padding hits: INT_MIN / 2) of a filled stage
+    auto put_kb = [&](ZStage<WT>& S, const KBlk& k) {
+      if (lane == 0) *reinterpret_cast<int4*>(S.kb) = make_int4(k.cnt, k.t_first, k.t_last, k.origin);
+      if (lane == 1) S.kb[4] = k.base;
+      if (lane < KG) S.n[lane] = lane < k.cnt - KG * grp ? S.rec[lane].nglob : INT_MIN / 2;
+    };
+    auto fill = [&](ZStage<WT>& S) {
+      // taps R((u0 + i) dt) (c_k rides in the E2 factor). A padding hit's first row is
+      // INT_MIN / 2, so every tap index of it reads the zero row WT: its taps are formed
+      // like the others' (no dependence on the walk) and never read.
+#pragma unroll
+      for (int it = 0; it < (KG * WT + 31) / 32; ++it) {
+        const int item = lane + 32 * it;
+        if (item < KG * WT) {
+          const int kl = item & (KG - 1), qq = item >> 3;
+          float2 g = make_float2(0.f, 0.f);
+          if (qq < W) {
+            const float u0 = S.rec[kl].u0 + (float)qq;
+            if constexpr (CT) g = tap_value(s_rtab, a.rtab_s_scale, u0, 1.f, 0.f);
+            else g.x = tap_real(s_rre, a.rtab_s_scale, u0);
+          }
+          S.g[qq][kl] = make_float4(g.x, g.x, g.y, g.y);
         }
-        S.g[qq][kl] = make_float4(g.x, g.x, g.y, g.y);
-        if (qq == 0) S.n[kl] = kl < kvalid ? S.rec[kl].nglob : INT_MIN / 2;
       }
       // (Re, -Im) of c_k E2[my_lo], E2[my_lo] = exp(j 2 pi (d/lambda) my_lo u_z)
+#pragma unroll 2
       for (int item = lane; item < KG * L2; item += 32) {
         const int kl = item & (KG - 1), ql = item >> 3;
         const float4 r = *reinterpret_cast<const float4*>(&S.rec[kl]);  // nglob, u0, cr, ci
@@ -558,21 +567,23 @@ __global__ void __launch_bounds__(kThreadsTZ, 1) k_synth_tz(SynthArgs a, uint32_
       walk_advance(w, kc);
       win = load_window(a.sorted_n, h0 + kc.cnt, h1, lane);
       rec_ahead = fetch(h0 + kc.cnt);
-      put(zst[0][grp], r0, kc);
-      fill(zst[0][grp], kc.cnt);
+      put_rec(zst[0][grp], r0);
+      fill(zst[0][grp]);
+      put_kb(zst[0][grp], kc);
     }
     int j = 0;
     for (int64_t h = h0; h < h1;) {
       named_bar(bar_id, kGroupThreads);
       const int64_t hn = h + kc.cnt;
       if (hn < h1) {
+        ZStage<WT>& Sn = zst[(j + 1) % kZStages][grp];
+        put_rec(Sn, rec_ahead);
         const KBlk kn = kblock_from(win, tr, Z::TMAXZ, W, w);
         walk_advance(w, kn);
         win = load_window(a.sorted_n, hn + kn.cnt, h1, lane);
-        ZStage<WT>& Sn = zst[(j + 1) % kZStages][grp];
-        put(Sn, rec_ahead, kn);
         rec_ahead = fetch(hn + kn.cnt);
-        fill(Sn, kn.cnt);
+        fill(Sn);
+        put_kb(Sn, kn);
         kc = kn;
       }
       ++j;
