@@ -391,6 +391,7 @@ __global__ void __launch_bounds__(kThreadsTZ, 1) k_synth_tz(SynthArgs a, uint32_
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   __shared__ float s_rre[CT ? 1 : kRTabS + 5];    // real pulse autocorrelation
   __shared__ float2 s_rtab[CT ? kRTabS + 5 : 1];  // complex pulse (raw series)
+  __shared__ int4 s_mkd[8][2];                     // K-block descriptors for the MMA issuer
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nx = a.nx, ny = a.ny, M = nx * ny;
@@ -432,28 +433,37 @@ __global__ void __launch_bounds__(kThreadsTZ, 1) k_synth_tz(SynthArgs a, uint32_
 
   if (warp == 0) {
     // ------------------------------------------------------------- MMA issuer
-    uint32_t used = 0, par = 0;  // per slot: held a tile before, parity of its use count
-    TileWalk w;
-    int j = 0;
-    unsigned tix = 0;
-    int win = load_window(a.sorted_n, h0, h1, lane);
-    for (int64_t h = h0; h < h1;) {
-      const KBlk kb = kblock_from(win, tr, Z::TMAXZ, W, w);
-      const int64_t hn = h + kb.cnt;
-      win = load_window(a.sorted_n, hn, h1, lane);
-      if (lane == 0) {
+    // One thread. It does not walk the K-blocks itself: each K-block's descriptor comes
+    // from the ring s_mkd, written by group 0's stage helper before the group barrier
+    // that precedes the A signal it waits for (a walk here, a latency-bound chain on a
+    // busy sub-partition, left the tensor pipe idle between K-blocks). Slot j & 7 is
+    // rewritten for K-block j + 8, after group 0 has formed A of K-block j + 6, which
+    // waited for this thread's release of K-block j + 4.
+    if (lane == 0) {
+      uint32_t used = 0, par = 0;  // per slot: held a tile before, parity of its use count
+      TileWalk w;
+      int j = 0;
+      unsigned tix = 0;
+      for (int64_t h = h0; h < h1;) {
+        const int aslot = j & 1;
+        if (!wait_or_abort(smem_u32(&am_full[aslot]), (j >> 1) & 1, abort_flag, a.err)) break;
+        const int4 d0 = s_mkd[j & 7][0];
+        KBlk kb;
+        kb.cnt = d0.x;
+        kb.t_first = d0.y;
+        kb.t_last = d0.z;
+        kb.origin = d0.w;
+        kb.base = s_mkd[j & 7][1].x;
         // tiles the walk has passed: their accumulators are final once these MMAs land
         for (int u = w.live_lo; u <= w.live_hi && u < kb.t_first; ++u) tc_commit(smem_u32(&tdone[u % RING]));
-        const int aslot = j & 1;
-        const bool a_ok = wait_or_abort(smem_u32(&am_full[aslot]), (j >> 1) & 1, abort_flag, a.err);
         const uint32_t ah = tmem_base + (uint32_t)(kAcol + aslot * 64), al = ah + 32;
         for (int t = kb.t_first; t <= kb.t_last; ++t) {
           const int slot = t % RING;
           const bool fresh = t > w.live_hi;
-          bool ok = a_ok;
+          bool ok = true;
           if (fresh) {
             const uint32_t bit = 1u << slot;
-            if (used & bit) ok = ok && wait_or_abort(smem_u32(&tfree[slot]), ((par >> slot) & 1u) ^ 1u, abort_flag, a.err);
+            if (used & bit) ok = wait_or_abort(smem_u32(&tfree[slot]), ((par >> slot) & 1u) ^ 1u, abort_flag, a.err);
             used |= bit;
             par ^= bit;
           }
@@ -474,14 +484,11 @@ __global__ void __launch_bounds__(kThreadsTZ, 1) k_synth_tz(SynthArgs a, uint32_
           }
           ++tix;
         }
-        if (a_ok) tc_commit(smem_u32(&am_empty[aslot]));
+        tc_commit(smem_u32(&am_empty[aslot]));
+        walk_advance(w, kb);
+        ++j;
+        h += kb.cnt;
       }
-      walk_advance(w, kb);
-      ++j;
-      h = hn;
-      __syncwarp();
-    }
-    if (lane == 0) {
       for (int u = w.live_lo; u <= w.live_hi; ++u) tc_commit(smem_u32(&tdone[u % RING]));
       tc_commit(smem_u32(done));
       mbar_wait(smem_u32(done), 0, a.err);
@@ -523,9 +530,11 @@ __global__ void __launch_bounds__(kThreadsTZ, 1) k_synth_tz(SynthArgs a, uint32_
       __syncwarp();  // the records are read back by other lanes below
     };
     // the descriptor and the first-tap rows (padding hits: INT_MIN / 2) of a filled stage
-    auto put_kb = [&](ZStage<WT>& S, const KBlk& k) {
+    auto put_kb = [&](ZStage<WT>& S, const KBlk& k, int jk) {
       if (lane == 0) *reinterpret_cast<int4*>(S.kb) = make_int4(k.cnt, k.t_first, k.t_last, k.origin);
       if (lane == 1) S.kb[4] = k.base;
+      if (grp == 0 && lane == 2) s_mkd[jk & 7][0] = make_int4(k.cnt, k.t_first, k.t_last, k.origin);
+      if (grp == 0 && lane == 3) s_mkd[jk & 7][1] = make_int4(k.base, 0, 0, 0);
       if (lane < KG) S.n[lane] = lane < k.cnt - KG * grp ? S.rec[lane].nglob : INT_MIN / 2;
     };
     auto fill = [&](ZStage<WT>& S) {
@@ -569,7 +578,7 @@ __global__ void __launch_bounds__(kThreadsTZ, 1) k_synth_tz(SynthArgs a, uint32_
       rec_ahead = fetch(h0 + kc.cnt);
       put_rec(zst[0][grp], r0);
       fill(zst[0][grp]);
-      put_kb(zst[0][grp], kc);
+      put_kb(zst[0][grp], kc, 0);
     }
     int j = 0;
     for (int64_t h = h0; h < h1;) {
@@ -583,7 +592,7 @@ __global__ void __launch_bounds__(kThreadsTZ, 1) k_synth_tz(SynthArgs a, uint32_
         win = load_window(a.sorted_n, hn + kn.cnt, h1, lane);
         rec_ahead = fetch(hn + kn.cnt);
         fill(Sn);
-        put_kb(Sn, kn);
+        put_kb(Sn, kn, j + 1);
         kc = kn;
       }
       ++j;
