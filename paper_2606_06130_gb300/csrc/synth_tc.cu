@@ -29,8 +29,10 @@
 //   chirp centred on t = 0), so B = R_k(n) (c_k E2[my_lo]) with R_k(n) real: c_k joins the
 //   per-hit E2 factor (L2 complex products per hit) and each B entry is one packed FP32
 //   product R (Re, -Im) of c_k E2. A fifth warp per group (the stage helper) works one
-//   K-block ahead: it walks the K-blocks, moves the records and forms the taps and the
-//   c_k E2 factors, so the four operand warps only form A and B.
+//   K-block ahead: it moves the records and forms the taps and the c_k E2 factors, so
+//   the four operand warps only form A and B. One walker warp walks the K-blocks for
+//   everyone but the epilogue: it feeds the helpers' descriptor ring, and group 0's
+//   helper forwards each descriptor to the MMA issuer.
 // k_synth_tc (small arrays): A[(n, mx)][k] = g_k(n) ey[mx] per tile (T = 128 / nx) and
 //   B[k][(my, re/im)] = ez[my] once per K-block, both in shared memory.
 #include <limits.h>
@@ -47,7 +49,7 @@ constexpr int KH = 32;           // hits per K-block: K = 64 BF16 columns (re, i
 constexpr int TMAX = 5;          // tiles one K-block may touch (k_synth_tc)
 constexpr int kGenWarps = 16;
 constexpr int kGenWarp0 = 5;     // warp 0: MMA, warps 1..4: epilogue, warps 5..20: generators
-                                 // (k_synth_tz: operand warps, then warps 21..24: stage helpers)
+                                 // (k_synth_tz: operand warps, then the stage helpers)
 constexpr int kThreadsTC = 32 * (kGenWarp0 + kGenWarps);
 constexpr int kGenThreads = 32 * kGenWarps;
 constexpr int M_BYTES = 128 * 128;  // 128 rows x 64 BF16
@@ -62,7 +64,19 @@ constexpr int RING = 8;          // TMEM accumulators of 64 columns
 constexpr int kGroups = 4;
 constexpr int KG = KH / kGroups;   // hits per generator group = one MMA K step
 constexpr int kAcol = 384;         // TMEM columns of the two per-K-block A slots (hi 32, lo 32)
-constexpr int kThreadsTZ = kThreadsTC + 32 * kGroups;  // plus one stage helper per group
+// Stage helpers: warps 21..24 for groups 0..3 (one per SM sub-partition, warp w runs on
+// w % 4), then the walker, warp 25. Each stage helper is a latency-bound chain that its
+// group's barrier waits on. While each helper still walked the K-blocks itself, the one
+// sharing sub-partition 0 with the MMA issuer (whose tcgen05.mma issue stalls that
+// sub-partition for much of every K-block) made its group about 1250 cycles late per
+// K-block; with the walk moved to the walker, the helpers keep up on every
+// sub-partition (measured: 0.157 ms for this layout, 0.160 ms with the walker on
+// sub-partition 0 and two helpers on sub-partition 1).
+constexpr int kHelper0 = kGenWarp0 + kGenWarps;  // 21
+constexpr int kWalkerWarp = kHelper0 + 4;        // 25, sub-partition 1
+constexpr int kHelper3 = kHelper0 + 3;           // 24, sub-partition 0
+constexpr int kThreadsTZ = 32 * (kHelper0 + kGroups + 1);  // 832
+constexpr int kWRing = 16;                       // walker -> helpers descriptor ring
 constexpr int kGroupThreads = 32 * 5;                   // four operand warps and the helper
 
 // Tile shape of k_synth_tz for NP complex output columns per tile.
@@ -392,6 +406,8 @@ __global__ void __launch_bounds__(kThreadsTZ, 1) k_synth_tz(SynthArgs a, uint32_
   __shared__ float s_rre[CT ? 1 : kRTabS + 5];    // real pulse autocorrelation
   __shared__ float2 s_rtab[CT ? kRTabS + 5 : 1];  // complex pulse (raw series)
   __shared__ int4 s_mkd[8][2];                     // K-block descriptors for the MMA issuer
+  __shared__ int4 s_wkd[kWRing][2];                // K-block descriptors for the stage helpers
+  __shared__ uint64_t s_wfull[kWRing], s_wempty[kWRing];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nx = a.nx, ny = a.ny, M = nx * ny;
@@ -416,6 +432,10 @@ __global__ void __launch_bounds__(kThreadsTZ, 1) k_synth_tz(SynthArgs a, uint32_
     for (int i = 0; i < 2; ++i) { mbar_init(smem_u32(&am_full[i]), kGenWarps); mbar_init(smem_u32(&am_empty[i]), 1); }
     for (int i = 0; i < RING; ++i) { mbar_init(smem_u32(&tdone[i]), 1); mbar_init(smem_u32(&tfree[i]), 4); }
     mbar_init(smem_u32(done), 1);
+    for (int i = 0; i < kWRing; ++i) {
+      mbar_init(smem_u32(&s_wfull[i]), 1);
+      mbar_init(smem_u32(&s_wempty[i]), kGroups);
+    }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -507,15 +527,37 @@ __global__ void __launch_bounds__(kThreadsTZ, 1) k_synth_tz(SynthArgs a, uint32_
                                     const int64_t row = r0 + nl;
                                     return reinterpret_cast<float*>(a.S + row * M + (my_hi * L2 + my_lo) * nx + mx);
                                   });
-  } else if (warp >= kGenWarp0 + kGenWarps) {
+  } else if (warp == kWalkerWarp) {
+    // ------------------------------------------------------------- walker
+    // Walks the K-blocks (the walk every role used to repeat) and hands each descriptor
+    // to the four stage helpers through a ring of kWRing slots: slot s is refilled once
+    // all four have taken it. Its first-tap windows are loaded one K-block ahead.
+    TileWalk w;
+    int j = 0;
+    int win = load_window(a.sorted_n, h0, h1, lane);
+    for (int64_t h = h0; h < h1; ++j) {
+      const KBlk k = kblock_from(win, tr, Z::TMAXZ, W, w);
+      walk_advance(w, k);
+      win = load_window(a.sorted_n, h + k.cnt, h1, lane);
+      const int slot = j % kWRing;
+      if (!wait_or_abort(smem_u32(&s_wempty[slot]), ((j / kWRing) & 1) ^ 1, abort_flag, a.err)) break;
+      if (lane == 0) {
+        s_wkd[slot][0] = make_int4(k.cnt, k.t_first, k.t_last, k.origin);
+        s_wkd[slot][1] = make_int4(k.base, 0, 0, 0);
+        mbar_arrive(smem_u32(&s_wfull[slot]));
+      }
+      __syncwarp();
+      h += k.cnt;
+    }
+  } else if (warp >= kHelper0) {
     // ------------------------------------------------------------- stage helpers
     // One warp per generator group works one K-block ahead of the group's four operand
-    // warps: it walks the K-blocks, moves the records (fetched two K-blocks ahead, so the
-    // loads overlap a whole K-block) and forms the taps R and the factors c_k E2 into the
-    // stage the operand warps take next. The group's named barrier at the top of every
-    // K-block hands one stage over; the stage written after barrier j is the one the
-    // operand warps last read during K-block j - 2, before barrier j - 1.
-    const int grp = warp - (kGenWarp0 + kGenWarps);
+    // warps: it takes the walker's descriptors, moves the records (fetched two K-blocks
+    // ahead, so the loads overlap a whole K-block) and forms the taps R and the factors
+    // c_k E2 into the stage the operand warps take next. The group's named barrier at the
+    // top of every K-block hands one stage over; the stage written after barrier j is the
+    // one the operand warps last read during K-block j - 2, before barrier j - 1.
+    const int grp = warp == kHelper3 ? kGroups - 1 : warp - kHelper0;
     const uint32_t bar_id = 1 + grp;
     const float pl2 = 2.0f * a.pitch_over_lambda;
     // lanes 0-15 move the group's 8 records (hit lane / 2, half lane & 1)
@@ -565,16 +607,30 @@ __global__ void __launch_bounds__(kThreadsTZ, 1) k_synth_tz(SynthArgs a, uint32_
         S.e2[kl][ql] = make_float2(fmaf(r.z, c, -r.w * s), -fmaf(r.z, s, r.w * c));
       }
     };
-    TileWalk w;
+    // descriptor jk from the walker's ring; after an abort (the walker gave up) a K-block
+    // of 32 hits in the last tile, so that every role still runs out its K-blocks in step
     KBlk kc{};
-    int win = 0;
+    auto get_kb = [&](int jk) {
+      const int slot = jk % kWRing;
+      KBlk k = kc;
+      k.cnt = KH;
+      k.t_first = k.t_last = kc.t_last;
+      if (wait_or_abort(smem_u32(&s_wfull[slot]), (jk / kWRing) & 1, abort_flag, a.err)) {
+        const int4 d0 = s_wkd[slot][0];
+        k.cnt = d0.x;
+        k.t_first = d0.y;
+        k.t_last = d0.z;
+        k.origin = d0.w;
+        k.base = s_wkd[slot][1].x;
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&s_wempty[slot]));
+      return k;
+    };
     uint4 rec_ahead = make_uint4(0u, 0u, 0u, 0u);
     if (h0 < h1) {
       const uint4 r0 = fetch(h0);
-      win = load_window(a.sorted_n, h0, h1, lane);
-      kc = kblock_from(win, tr, Z::TMAXZ, W, w);
-      walk_advance(w, kc);
-      win = load_window(a.sorted_n, h0 + kc.cnt, h1, lane);
+      kc = get_kb(0);
       rec_ahead = fetch(h0 + kc.cnt);
       put_rec(zst[0][grp], r0);
       fill(zst[0][grp]);
@@ -587,9 +643,7 @@ __global__ void __launch_bounds__(kThreadsTZ, 1) k_synth_tz(SynthArgs a, uint32_
       if (hn < h1) {
         ZStage<WT>& Sn = zst[(j + 1) % kZStages][grp];
         put_rec(Sn, rec_ahead);
-        const KBlk kn = kblock_from(win, tr, Z::TMAXZ, W, w);
-        walk_advance(w, kn);
-        win = load_window(a.sorted_n, hn + kn.cnt, h1, lane);
+        const KBlk kn = get_kb(j + 1);
         rec_ahead = fetch(hn + kn.cnt);
         fill(Sn);
         put_kb(Sn, kn, j + 1);
@@ -1001,7 +1055,7 @@ bool z_split(int nx, int ny) {
 
 // Shared memory per CTA: dynamic bytes plus the static pulse table (4136 bytes, padded
 // to the 1024-byte alignment of the dynamic array), within the 227 KB a CTA may hold.
-static_assert(tz_smem_bytes<16, 96>() + 5 * 1024 <= 227 * 1024, "z-split tile fits");
+static_assert(tz_smem_bytes<16, 96>() + 7 * 1024 <= 227 * 1024, "z-split tile fits");
 static_assert(tc_smem_bytes<16>() + 5 * 1024 <= 227 * 1024, "per-tile kernel fits");
 
 // A z-split tile of NP complex columns holds T = NP / L2 whole rows, and a K-block of
