@@ -144,6 +144,9 @@ typedef struct {
   /* CTAs per cluster of the beamforming contraction in the last synchronous call (1, 2
      or 4; SONAR_OPT_GEMM_CLUSTER) */
   int32_t gemm_cluster;
+  /* 1 when the last synchronous call formed separable beams (SONAR_OPT_BEAMFORM), 0 for
+     the dense contraction */
+  int32_t beam_sep;
 } sonar_stats;
 
 /* ---------------------------------------------------------------- context */
@@ -250,6 +253,23 @@ SONAR_API const char* sonar_last_error(const sonar_ctx* ctx);
    of the element echoes (the synthesis adds with atomics in any order). Any other value:
    SONAR_E_ARG. */
 #define SONAR_OPT_GEMM_CLUSTER 12
+/* SONAR_OPT_BEAMFORM: 0 (default) forms phase-shift beams in two stages where the
+   steering matrix factors (Sec. II.B coherent summation, the same sum regrouped): with a
+   separable taper w_m = wy[my] wx[mx] the steering phase splits into a row part that
+   depends only on the beam's elevation (u_z = sin el) and a column part, so
+   B[el, az](t) = sum_mx wx e^{-j k_a u_y y_mx} U[el](t, mx) / sum w, with
+   U[el](t, mx) = sum_my wy e^{-j k_a u_z z_my} s_(my, mx)(t): a contraction over the
+   array's rows per elevation (FP32 on the CUDA cores) and one over its columns per beam
+   (the tensor-core GEMM with K = 2 nx), nx (1 + ny / n_beam_az) complex multiply-adds
+   per beam and range sample instead of nx ny (C2: 40 against 1024). It applies to
+   phase-shift beams (not SONAR_OPT_TTD), a separable taper (NULL, or one that a product
+   of a row and a column reproduces to 1e-6 of its largest weight), the FP32 and BF16
+   forms, arrays of at most 32 columns and 64 rows with an even element count and
+   n_beam_el ny <= 4096, and beam grids whose rows hold a multiple of 64 beams (the
+   GEMM's N tile, 256 or 128, then lies in one elevation row; the caller's
+   SONAR_OPT_TILE_N wins). Elsewhere the dense contraction runs. 1: always the dense
+   contraction. sonar_get_stats reports which one the last call used. */
+#define SONAR_OPT_BEAMFORM 13
 SONAR_API int sonar_set_option(sonar_ctx* ctx, int32_t option, int64_t value);
 
 /* ---------------------------------------------------------------- scene */

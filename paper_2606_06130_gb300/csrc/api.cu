@@ -80,7 +80,31 @@ struct Derived {
   // entry of a window's first row at u0 = 0, phase 0 and no element delay)
   int ttd_q0 = 0, ttd_levels = 1, ttd_guard = 0, wb_wt = 0, wb_e1 = 0, wb_uf = 0, wb_f = 0, wb_n_tab = 0;
   double wb_v_lo = 0.0, wb_x0 = 0.0, ttd_x_scale = 0.0;
+  int sep = 0;  // 1: separable beams (two stages), 0: the dense contraction
+  int n_el = 0, n_az = 0;  // beam elevation rows and beams per row
 };
+
+// The taper as wy[my] wx[mx] (wx from the row of the largest weight, wy normalised to 1
+// there); false when no such product reproduces it to 1e-6 of the largest weight. A
+// missing taper is uniform.
+bool taper_separable(const sonar_params* p, std::vector<double>* wx, std::vector<double>* wy) {
+  const int nx = p->nx, ny = p->ny;
+  wx->assign((size_t)nx, 1.0);
+  wy->assign((size_t)ny, 1.0);
+  if (!p->taper) return true;
+  int m0 = 0;
+  for (int m = 1; m < nx * ny; ++m)
+    if (p->taper[m] > p->taper[m0]) m0 = m;
+  const double t0 = p->taper[m0];
+  if (!(t0 > 0)) return false;
+  const int mx0 = m0 % nx, my0 = m0 / nx;
+  for (int mx = 0; mx < nx; ++mx) (*wx)[(size_t)mx] = p->taper[my0 * nx + mx];
+  for (int my = 0; my < ny; ++my) (*wy)[(size_t)my] = p->taper[my * nx + mx0] / t0;
+  for (int my = 0; my < ny; ++my)
+    for (int mx = 0; mx < nx; ++mx)
+      if (fabs((double)p->taper[my * nx + mx] - (*wy)[(size_t)my] * (*wx)[(size_t)mx]) > 1e-6 * t0) return false;
+  return true;
+}
 
 // One of the two in-flight slots of asynchronous pings: its own pinned pose record,
 // point counts and counter words, device envelope staging and captured graph, reused
@@ -185,6 +209,17 @@ struct sonar_ctx {
   double2* beam_uyz = nullptr;  // beam-centre direction cosines of the steering matrix
   int64_t beam_uyz_cap = 0;
   double y_gain = 1.0;
+  // separable beams: Fz [n_beam_el][ny] of the first stage and the second stage's
+  // steering operand (one array row, wx[mx] exp(-j k_a u_y y_mx)), keyed like the steering
+  int bf_opt = 0;  // 0: separable beams where they apply, 1: always the dense contraction
+  std::vector<uint8_t> sep_key;
+  float2* sep_fz = nullptr;
+  int64_t sep_fz_cap = 0;
+  void* ysep_hi = nullptr;
+  void* ysep_lo = nullptr;
+  size_t ysep_elems = 0;
+  float* taper_x_dev = nullptr;
+  double ysep_gain = 1.0;
 
   // workspaces
   int p_cap = 0;
@@ -471,9 +506,25 @@ int derive(sonar_ctx* ctx, const sonar_params* p, const sonar_ssp* ssp, double x
   d.M = p->nx * p->ny;
   d.k_pad = (int)round_up(2LL * d.M, 64);
   d.nb = p->n_beam_az * p->n_beam_el;
+  d.n_el = p->n_beam_el;
+  d.n_az = p->n_beam_az;
   d.tile_n = ctx->tile_opt != 0   ? ctx->tile_opt
              : ctx->cur_tile_n != 0 ? ctx->cur_tile_n
                                     : pick_tile_n((int64_t)n_pings * d.nr_x / 128, d.nb, ctx->sm_count);
+  // Separable beams (Sep1Args): phase-shift beams, a separable taper, BF16 operands (the
+  // FP32 and BF16 forms), an array the first stage serves, and an N tile inside one
+  // elevation row (the caller's tile wins over the separable form).
+  {
+    std::vector<double> wx, wy;
+    d.sep = ctx->bf_opt == 0 && ctx->ttd_u == 0 && p->precision != SONAR_FP16 && sep1_supported(p->nx, p->ny) &&
+            p->n_beam_el * p->ny <= 4096 && taper_separable(p, &wx, &wy);
+    if (d.sep && p->n_beam_az % (d.tile_n / 2) != 0) {
+      if (ctx->tile_opt != 0) d.sep = 0;
+      else if (p->n_beam_az % 128 == 0) d.tile_n = 256;
+      else if (p->n_beam_az % 64 == 0) d.tile_n = 128;
+      else d.sep = 0;
+    }
+  }
   d.nb_pad = (int)round_up(d.nb, d.tile_n / 2);
   d.n_phase = p->precision == SONAR_FP32 ? 3 : 1;
   d.n_blank = 0;
@@ -658,6 +709,68 @@ int ensure_tables(sonar_ctx* ctx, const sonar_params* p, const Derived& d) {
   key_add(k, d.tile_n); key_add(k, ctx->ttd_u); key_add(k, d.ttd_q0); key_add(k, d.ttd_levels);
   key_add(k, d.ttd_x_scale);
   for (int m = 0; m < d.M; ++m) key_add(k, p->taper ? p->taper[m] : 1.0f);
+  // beam-centre direction cosines (u_y, u_z), FP64, for either steering operand
+  auto upload_uyz = [&]() -> int {
+    std::vector<double2> uyz((size_t)d.nb);
+    for (int b = 0; b < d.nb; ++b) {
+      const int bi = b % p->n_beam_az, bj = b / p->n_beam_az;
+      const double az = -p->hfov_rad / 2 + (bi + 0.5) * p->hfov_rad / p->n_beam_az;
+      const double el = -p->vfov_rad / 2 + (bj + 0.5) * p->vfov_rad / p->n_beam_el;
+      uyz[(size_t)b] = make_double2(cos(el) * sin(az), sin(el));
+    }
+    int rc;
+    if ((rc = grow(ctx, ctx->beam_uyz, ctx->beam_uyz_cap, d.nb, sizeof(double2), false))) return rc;
+    CU(cudaMemcpyAsync(ctx->beam_uyz, uyz.data(), sizeof(double2) * d.nb, cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));  // the host table is released on return
+    return SONAR_OK;
+  };
+  if (d.sep) {
+    // separable beams: Fz[el][my] = wy[my] exp(-j 2 pi (d / lambda) (my - (ny-1)/2) sin el)
+    // (FP64 phase reduced modulo one cycle), and the second stage's steering operand: the
+    // steering matrix of one array row with taper wx, the full taper's sum as divisor
+    if (k != ctx->sep_key) {
+      std::vector<double> wx, wy;
+      taper_separable(p, &wx, &wy);
+      std::vector<float2> fz((size_t)p->n_beam_el * p->ny);
+      for (int j = 0; j < p->n_beam_el; ++j) {
+        const double el = -p->vfov_rad / 2 + (j + 0.5) * p->vfov_rad / p->n_beam_el, uz = sin(el);
+        for (int my = 0; my < p->ny; ++my) {
+          const double cyc = d.pitch_over_lambda * (my - 0.5 * (p->ny - 1)) * uz;
+          const double ph = 2.0 * kPi * (cyc - floor(cyc));
+          fz[(size_t)j * p->ny + my] = make_float2((float)(wy[(size_t)my] * cos(ph)), (float)(-wy[(size_t)my] * sin(ph)));
+        }
+      }
+      int rc;
+      if ((rc = grow(ctx, ctx->sep_fz, ctx->sep_fz_cap, (int64_t)fz.size(), sizeof(float2), false))) return rc;
+      CU(cudaMemcpyAsync(ctx->sep_fz, fz.data(), sizeof(float2) * fz.size(), cudaMemcpyHostToDevice, ctx->stream));
+      std::vector<float> wxf(wx.begin(), wx.end());
+      dfree(ctx->taper_x_dev);
+      CU(cudaMalloc(&ctx->taper_x_dev, sizeof(float) * p->nx));
+      CU(cudaMemcpyAsync(ctx->taper_x_dev, wxf.data(), sizeof(float) * p->nx, cudaMemcpyHostToDevice, ctx->stream));
+      const size_t elems = (size_t)2 * d.nb_pad * 64;
+      if (elems != ctx->ysep_elems) {
+        dfree(ctx->ysep_hi);
+        dfree(ctx->ysep_lo);
+        CU(cudaMalloc(&ctx->ysep_hi, elems * 2));
+        CU(cudaMalloc(&ctx->ysep_lo, elems * 2));
+        ctx->ysep_elems = elems;
+      }
+      if ((rc = upload_uyz())) return rc;  // also waits for the Fz and taper copies
+      double wxmax = 0.0;
+      for (double v : wx) wxmax = fmax(wxmax, v);
+      ctx->ysep_gain = d.wsum / wxmax;  // steering entries scaled to at most 1
+      SteerArgs sa;
+      sa.beam_uyz = ctx->beam_uyz;
+      sa.nx = p->nx; sa.ny = 1; sa.n_beam_az = p->n_beam_az; sa.n_beam_el = p->n_beam_el;
+      sa.nb_pad = d.nb_pad; sa.k_pad = 64; sa.hfov = p->hfov_rad; sa.vfov = p->vfov_rad;
+      sa.pitch_over_lambda = d.pitch_over_lambda; sa.taper = ctx->taper_x_dev; sa.wsum = d.wsum;
+      sa.gain = ctx->ysep_gain; sa.mode = p->precision; sa.y_hi = ctx->ysep_hi; sa.y_lo = ctx->ysep_lo;
+      sa.n_levels = 1; sa.q0 = 0; sa.ttd = 0; sa.x_scale = 0.0;
+      CU(launch_steer(sa, ctx->stream));
+      ctx->sep_key = k;
+    }
+    return SONAR_OK;
+  }
   if (k != ctx->steer_key) {
     size_t elems = (size_t)2 * d.nb_pad * d.k_pad * d.ttd_levels;
     if (elems != ctx->y_elems) {
@@ -673,17 +786,8 @@ int ensure_tables(sonar_ctx* ctx, const sonar_params* p, const Derived& d) {
       CU(cudaMemcpyAsync(ctx->taper_dev, p->taper, sizeof(float) * d.M, cudaMemcpyHostToDevice, ctx->stream));
     }
     ctx->y_gain = d.wsum / d.wmax;  // steering entries scaled to at most 1
-    std::vector<double2> uyz((size_t)d.nb);
-    for (int b = 0; b < d.nb; ++b) {
-      const int bi = b % p->n_beam_az, bj = b / p->n_beam_az;
-      const double az = -p->hfov_rad / 2 + (bi + 0.5) * p->hfov_rad / p->n_beam_az;
-      const double el = -p->vfov_rad / 2 + (bj + 0.5) * p->vfov_rad / p->n_beam_el;
-      uyz[(size_t)b] = make_double2(cos(el) * sin(az), sin(el));
-    }
     int rc;
-    if ((rc = grow(ctx, ctx->beam_uyz, ctx->beam_uyz_cap, d.nb, sizeof(double2), false))) return rc;
-    CU(cudaMemcpyAsync(ctx->beam_uyz, uyz.data(), sizeof(double2) * d.nb, cudaMemcpyHostToDevice, ctx->stream));
-    CU(cudaStreamSynchronize(ctx->stream));  // the host table is released on return
+    if ((rc = upload_uyz())) return rc;
     SteerArgs sa;
     sa.beam_uyz = ctx->beam_uyz;
     sa.nx = p->nx; sa.ny = p->ny; sa.n_beam_az = p->n_beam_az; sa.n_beam_el = p->n_beam_el;
@@ -777,7 +881,9 @@ int ensure_workspace(sonar_ctx* ctx, int P, const Derived& d) {
   }
   // true-time delay: the echo operand holds every phase, each ping's rows with guard rows
   // on either side for the level offsets
+  // separable beams: one block of P nr_x rows of 64 columns per elevation row
   int64_t x_need = ctx->ttd_u > 0 ? (int64_t)ctx->ttd_u * P * (d.nr_x + 2 * d.ttd_guard) * d.k_pad
+                   : d.sep        ? (int64_t)d.n_el * P * d.nr_x * 64
                                   : (int64_t)P * d.nr_x * d.k_pad;
   if (x_need != ctx->ws_x || !ctx->x_hi) {
     int64_t c0 = 0, c1 = 0;
@@ -1045,26 +1151,52 @@ int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, cons
   ca.gain = ctx->gain;
   ca.x_hi = ctx->x_hi;
   ca.x_lo = ctx->x_lo;
-  CU(launch_convert(ca, ctx->sm_count, st));
+  if (d.sep) {
+    // separable beams, first stage: the echoes summed over the array's rows per elevation
+    Sep1Args s1;
+    s1.S = ctx->S;
+    s1.fz = ctx->sep_fz;
+    s1.n_pings = P;
+    s1.nr = d.nr;
+    s1.nr_pad = d.nr_pad;
+    s1.nr_x = d.nr_x;
+    s1.nx = p->nx;
+    s1.ny = p->ny;
+    s1.n_el = d.n_el;
+    s1.k_pad = 64;
+    s1.mode = p->precision;
+    s1.x_hi = ctx->x_hi;
+    s1.x_lo = ctx->x_lo;
+    CU(launch_sep1(s1, st));
+  } else {
+    CU(launch_convert(ca, ctx->sm_count, st));
+  }
   mark(4);
   GemmArgs ga;
   memset(&ga, 0, sizeof(ga));
   const bool f16 = fp16;
   int rc;
   const int box_k = d.n_phase == 3 ? 32 : 64;
-  const int64_t x_map_rows = (int64_t)ca.n_phases * P * x_rows;
-  const int64_t y_cols = (int64_t)d.k_pad * d.ttd_levels;
-  if ((rc = make_map(ctx, &ga.map_xh, ctx->x_hi, x_map_rows, d.k_pad, 128, f16, box_k))) return rc;
-  if ((rc = make_map(ctx, &ga.map_xl, ctx->x_lo, x_map_rows, d.k_pad, 128, f16, box_k))) return rc;
+  // separable beams: the second stage reads K = 64 (one array row, re and im) from the
+  // tile's elevation block of the first stage's output
+  const int64_t x_cols = d.sep ? 64 : d.k_pad;
+  const int64_t x_map_rows = d.sep ? (int64_t)d.n_el * P * x_rows : (int64_t)ca.n_phases * P * x_rows;
+  const int64_t y_cols = d.sep ? 64 : (int64_t)d.k_pad * d.ttd_levels;
+  void* const yh = d.sep ? ctx->ysep_hi : ctx->y_hi;
+  void* const yl = d.sep ? ctx->ysep_lo : ctx->y_lo;
+  if ((rc = make_map(ctx, &ga.map_xh, ctx->x_hi, x_map_rows, x_cols, 128, f16, box_k))) return rc;
+  if ((rc = make_map(ctx, &ga.map_xl, ctx->x_lo, x_map_rows, x_cols, 128, f16, box_k))) return rc;
   ga.tiles_m = P * d.nr_x / 128;
   // clusters of CTAs load a share of each B tile apiece and multicast it
   ga.cluster = gemm_cluster_for(ctx, ga.tiles_m, d);
   const int y_box = d.tile_n / ga.cluster;
-  if ((rc = make_map(ctx, &ga.map_yh, ctx->y_hi, 2LL * d.nb_pad, y_cols, y_box, f16, box_k))) return rc;
-  if ((rc = make_map(ctx, &ga.map_yl, ctx->y_lo, 2LL * d.nb_pad, y_cols, y_box, f16, box_k))) return rc;
+  if ((rc = make_map(ctx, &ga.map_yh, yh, 2LL * d.nb_pad, y_cols, y_box, f16, box_k))) return rc;
+  if ((rc = make_map(ctx, &ga.map_yl, yl, 2LL * d.nb_pad, y_cols, y_box, f16, box_k))) return rc;
   ga.tiles_n = 2 * d.nb_pad / d.tile_n;
   ga.k_blocks = (int)(y_cols / 64);
-  ga.x_kpad = d.k_pad;
+  ga.x_kpad = (int)x_cols;
+  ga.sep_az = d.sep ? d.n_az : 0;
+  ga.x_el_rows = (int64_t)P * x_rows;
   ga.ttd_u = ctx->ttd_u;
   ga.ttd_q0 = d.ttd_q0;
   ga.x_ping_rows = x_rows;
@@ -1081,7 +1213,7 @@ int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, cons
   ga.dr = (float)d.dr;
   ga.alpha2 = (float)(2.0 * p->alpha_np_per_m);
   ga.gain = fp16 ? ctx->gain : nullptr;  // element echoes carry a gain only in the FP16 form
-  ga.y_gain_inv = (float)(1.0 / ctx->y_gain);
+  ga.y_gain_inv = (float)(1.0 / (d.sep ? ctx->ysep_gain : ctx->y_gain));
   ga.env = o.env;
   ga.peak_keys = ctx->keys;
   ga.ping_max = ctx->pmax;
@@ -1205,6 +1337,7 @@ std::vector<uint8_t> pipeline_key(const sonar_ctx* ctx, int P, const sonar_param
   }
   key_add(k, ctx->vol_order);
   key_add(k, ctx->hits); key_add(k, ctx->S); key_add(k, ctx->x_hi); key_add(k, ctx->y_hi); key_add(k, ctx->keys);
+  key_add(k, d.sep); key_add(k, ctx->ysep_hi); key_add(k, ctx->sep_fz);
   return k;
 }
 
@@ -1274,6 +1407,11 @@ int autotune(sonar_ctx* ctx, int P, const sonar_params* p, const sonar_ssp* ssp,
   int best_n = 0, best_p = 0;
   if (ctx->tile_opt == 0) {
     for (int bn : {256, 224, 192, 128}) {
+      // separable beams take only N tiles inside one elevation row (derive() would
+      // replace the others and time the same tile twice)
+      Derived dt;
+      ctx->cur_tile_n = 0;
+      if (derive(ctx, p, ssp, xs, zs, P, dt) == SONAR_OK && dt.sep && p->n_beam_az % (bn / 2) != 0) continue;
       ctx->cur_tile_n = bn;
       if ((rc = measure(&ms_s, &ms_g))) break;
       if (ms_g < best_g) { best_g = ms_g; best_n = bn; }
@@ -1430,6 +1568,7 @@ int run(sonar_ctx* ctx, const sonar_pose* poses, int P, const sonar_params* p, c
   ctx->stats.synth_cols = ctx->synth_opt >= 2 ? kCols[ctx->synth_opt] : ctx->cur_pairs;
   ctx->stats.autotuned = ctx->cur_tuned ? 1 : 0;
   ctx->stats.gemm_cluster = gemm_cluster_for(ctx, P * d.nr_x / 128, d);
+  ctx->stats.beam_sep = d.sep;
   if (timed) {
     float t[6];
     for (int i = 0; i < 6; ++i) CU(cudaEventElapsedTime(&t[i], ctx->stage_ev[i], ctx->stage_ev[i + 1]));
@@ -1824,6 +1963,10 @@ int sonar_set_option(sonar_ctx* ctx, int32_t option, int64_t value) {
       if (value != 0 && value != 1) return fail(ctx, SONAR_E_ARG, "cross terms: 0 (off) or 1 (on)");
       ctx->cross = (int)value;
       break;
+    case SONAR_OPT_BEAMFORM:
+      if (value != 0 && value != 1) return fail(ctx, SONAR_E_ARG, "beamforming: 0 (separable where it applies) or 1 (dense)");
+      ctx->bf_opt = (int)value;
+      break;
     case SONAR_OPT_TILE_N:
       if (value != 0 && value != 128 && value != 192 && value != 224 && value != 256)
         return fail(ctx, SONAR_E_ARG, "tile_n must be 0, 128, 192, 224 or 256");
@@ -1922,6 +2065,7 @@ int sonar_destroy(sonar_ctx* c) {
   dfree(c->poses); dfree(c->hits); dfree(c->sorted); dfree(c->sorted_n); dfree(c->dbg_tau);
   dfree(c->n_hits);
   dfree(c->counts); dfree(c->offsets); dfree(c->S); dfree(c->S_raw); dfree(c->ptab); dfree(c->wtab); dfree(c->x_hi); dfree(c->x_lo); dfree(c->gain);
+  dfree(c->sep_fz); dfree(c->ysep_hi); dfree(c->ysep_lo); dfree(c->taper_x_dev);
   dfree(c->env_stage); dfree(c->keys); dfree(c->pmax); dfree(c->cloud_stage); dfree(c->n_cloud_dev); dfree(c->err_dev); dfree(c->synth_bounds);
   auto& S = c->sur;
   dfree(S.params); dfree(S.wbf); dfree(S.wsmall); dfree(S.loss); dfree(S.feat); dfree(S.poses); dfree(S.buf); dfree(S.g);

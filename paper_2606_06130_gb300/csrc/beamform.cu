@@ -154,6 +154,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant_
         const int row0 = mb * BM, p = row0 / a.nr_x;
         const int y_tile = p * a.x_ping_rows + a.x_guard + (row0 - p * a.nr_x);
         int xk = 0, lvl = 0, y = y_tile;  // K position inside the level, the level, its X row
+        // separable beams: the block of the tile's elevation row
+        if (a.sep_az > 0) y += (int)((int64_t)nb * (BN / 2) / a.sep_az * a.x_el_rows);
         if (a.ttd_u > 0) {
           const int q = a.ttd_q0, s = ((q % a.ttd_u) + a.ttd_u) % a.ttd_u;
           y = y_tile + s * a.x_phase_rows + (q - s) / a.ttd_u;
@@ -268,7 +270,11 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant_
         for (int j = 0; j < 16; ++j) {
           const int beam = beam0 + j;
           const float re = __uint_as_float(v[2 * j]), im = __uint_as_float(v[2 * j + 1]);
-          const float e = sqrtf(re * re + im * im) * scale;
+          // sqrt.approx: relative error below 2^-22, a fraction of the BF16 hi/lo operands'
+          // 2^-17 (the rounded square root's slow path was a third of a short contraction's time)
+          float e;
+          asm("sqrt.approx.f32 %0, %1;" : "=f"(e) : "f"(fmaf(re, re, im * im)));
+          e *= scale;
           const bool vb = beam < a.n_beams;
           if (vn && vb) env_p[(size_t)beam * a.nr + n] = e;
           key[j] = (elig && vb)
@@ -461,6 +467,123 @@ __global__ void __launch_bounds__(1024) k_peaks(PeakArgs a) {
   }
 }
 
+// ----------------------------------------------------------------- separable beams, stage 1
+// U[el][n][mx] = sum_my Fz[el][my] s_(my, mx)[n] for kSepRows (two) range samples of one
+// ping per CTA: the two rows of S and Fz (as (Re, Im, Im, Re) quads) are loaded with
+// 16-byte vectors, all of a thread's loads issued before the first is used, into shared
+// memory; lane mx of warp w accumulates the elevations w, w + 8, ... (eight at a time) for
+// both samples, each complex multiply-add two packed FP32 operations. Lanes past nx
+// write zero columns, so the whole 64-column operand row is defined.
+constexpr int kSepRows = 2;
+constexpr int kSepMaxFz = 4096;  // n_el x ny entries of Fz held in shared memory
+constexpr int kSepLd = 8;        // 16-byte loads per thread in flight at once
+
+__device__ __forceinline__ uint32_t bf16_pair(float a, float b) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+
+// dst[i] = src[i] for n float4, every thread issuing up to kSepLd loads before its stores
+__device__ __forceinline__ void sep_copy(float4* dst, const float4* src, int n) {
+  for (int base = 0; base < n; base += kSepLd * 256) {
+    float4 v[kSepLd];
+#pragma unroll
+    for (int k = 0; k < kSepLd; ++k) {
+      const int i = base + k * 256 + (int)threadIdx.x;
+      if (i < n) v[k] = __ldg(src + i);
+    }
+#pragma unroll
+    for (int k = 0; k < kSepLd; ++k) {
+      const int i = base + k * 256 + (int)threadIdx.x;
+      if (i < n) dst[i] = v[k];
+    }
+  }
+}
+
+// FULL: n_el a multiple of 64 (every warp's eight elevations exist, no predicates).
+// 64 registers at most, so that four CTAs share an SM and a 1024-sample ping's 512 CTAs
+// run in one wave on 152 SMs.
+template <bool FULL>
+__global__ void __launch_bounds__(256, 4) k_sep1(Sep1Args a) {
+  extern __shared__ float4 sep_smem[];
+  float4* fz4 = sep_smem;                                            // [n_el][ny]
+  float2* srow = reinterpret_cast<float2*>(fz4 + a.n_el * a.ny);     // [kSepRows][M]
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int p = blockIdx.y, n0 = blockIdx.x * kSepRows;
+  const int nx = a.nx, ny = a.ny, M = nx * ny;
+  const int nfz = a.n_el * ny;
+  // Fz as quads: the pairs (f0, f1) of one 16-byte load become (f0, f0 swapped) and (f1, f1
+  // swapped)
+  {
+    float2* fzq = reinterpret_cast<float2*>(srow);  // staging: the S rows come later
+    sep_copy(reinterpret_cast<float4*>(fzq), reinterpret_cast<const float4*>(a.fz), nfz / 2);
+    if ((nfz & 1) && tid == 0) fzq[nfz - 1] = a.fz[nfz - 1];
+    __syncthreads();
+    for (int i = tid; i < nfz; i += blockDim.x) {
+      const float2 f = fzq[i];
+      fz4[i] = make_float4(f.x, f.y, f.y, f.x);
+    }
+    __syncthreads();
+  }
+  pdl_wait();  // the element echoes come from the synthesis
+  const int rows = min(kSepRows, a.nr - n0);
+  const float2* src = a.S + ((int64_t)p * a.nr_pad + kPad + n0) * M;
+  sep_copy(reinterpret_cast<float4*>(srow), reinterpret_cast<const float4*>(src), rows * M / 2);
+  if (rows < kSepRows)
+    for (int i = tid; i < M; i += blockDim.x) srow[M + i] = make_float2(0.f, 0.f);
+  __syncthreads();
+  const int mxl = lane < nx ? lane : 0;  // lanes past nx compute on column 0 and write zeros
+  uint16_t* xh = reinterpret_cast<uint16_t*>(a.x_hi);
+  uint16_t* xl = reinterpret_cast<uint16_t*>(a.x_lo);
+  for (int e0 = w; e0 < a.n_el; e0 += 64) {
+    float2 acc0[8], acc1[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) acc0[i] = acc1[i] = make_float2(0.f, 0.f);
+    const float4* fzr = fz4 + e0 * ny;
+#pragma unroll 8
+    for (int my = 0; my < ny; ++my) {
+      const float2 s0 = srow[my * nx + mxl], s1 = srow[M + my * nx + mxl];
+      const float2 sx0 = make_float2(s0.x, s0.x), sy0 = make_float2(-s0.y, s0.y);
+      const float2 sx1 = make_float2(s1.x, s1.x), sy1 = make_float2(-s1.y, s1.y);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        if (FULL || e0 + 8 * i < a.n_el) {
+          // (re, im) += s f: (s.x f.x - s.y f.y, s.x f.y + s.y f.x)
+          const float4 f = fzr[8 * i * ny + my];
+          acc0[i] = __ffma2_rn(sy0, make_float2(f.z, f.w), __ffma2_rn(sx0, make_float2(f.x, f.y), acc0[i]));
+          acc1[i] = __ffma2_rn(sy1, make_float2(f.z, f.w), __ffma2_rn(sx1, make_float2(f.x, f.y), acc1[i]));
+        }
+      }
+    }
+    const bool act = lane < nx;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int el = e0 + 8 * i;
+      if (!FULL && el >= a.n_el) continue;
+#pragma unroll
+      for (int r = 0; r < kSepRows; ++r) {
+        if (r >= rows) break;
+        const float2 u = act ? (r == 0 ? acc0[i] : acc1[i]) : make_float2(0.f, 0.f);
+        const int64_t row = ((int64_t)el * a.n_pings + p) * a.nr_x + n0 + r;
+        const int64_t off = row * a.k_pad + 2 * lane;  // 16-bit units
+        const uint32_t hi = bf16_pair(u.x, u.y);
+        *reinterpret_cast<uint32_t*>(xh + off) = hi;
+        if (a.mode == SONAR_FP32) {
+          __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162*>(&hi);
+          const float2 hf = __bfloat1622float2(h);
+          *reinterpret_cast<uint32_t*>(xl + off) = bf16_pair(u.x - hf.x, u.y - hf.y);
+        }
+      }
+    }
+  }
+}
+
+// Fz quads, then the two S rows (also the staging of Fz, which needs half the quads' bytes)
+size_t sep1_smem(int n_el, int ny, int nx) {
+  const size_t rows = sizeof(float2) * kSepRows * nx * ny, stage = sizeof(float2) * (n_el * ny + 1);
+  return sizeof(float4) * n_el * ny + (rows > stage ? rows : stage);
+}
+
 }  // namespace
 
 cudaError_t launch_steer(const SteerArgs& a, cudaStream_t st) {
@@ -518,8 +641,22 @@ cudaError_t gemm_attr() {
   cudaError_t e = gemm_attr_one<BN, 1>();
   return e != cudaSuccess ? e : gemm_attr_one<BN, 3>();
 }
+bool sep1_supported(int nx, int ny) { return nx >= 1 && nx <= 32 && ny >= 1 && ny <= 64 && (nx * ny) % 2 == 0; }
+
+cudaError_t launch_sep1(const Sep1Args& a, cudaStream_t st) {
+  if (!sep1_supported(a.nx, a.ny) || a.n_el * a.ny > kSepMaxFz || a.k_pad != 64) return cudaErrorInvalidValue;
+  const size_t smem = sep1_smem(a.n_el, a.ny, a.nx);
+  const dim3 grid((unsigned)((a.nr + kSepRows - 1) / kSepRows), (unsigned)a.n_pings);
+  cudaError_t e = a.n_el % 64 == 0 ? launch_pdl(k_sep1<true>, grid, dim3(256), smem, st, a)
+                                   : launch_pdl(k_sep1<false>, grid, dim3(256), smem, st, a);
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
 cudaError_t prepare_gemm() {
-  cudaError_t e;
+  const int sep_max = (int)(sizeof(float4) * kSepMaxFz + sizeof(float2) * (kSepMaxFz + 1));
+  cudaError_t e = cudaFuncSetAttribute(k_sep1<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sep_max);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sep1<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sep_max);
+  if (e != cudaSuccess) return e;
   if ((e = gemm_attr<256>()) != cudaSuccess) return e;
   if ((e = gemm_attr<224>()) != cudaSuccess) return e;
   if ((e = gemm_attr<192>()) != cudaSuccess) return e;

@@ -414,6 +414,12 @@ struct GemmArgs {
   // CTAs per cluster sharing each B tile by multicast: 1, 2 or 4 (map_yh / map_yl boxes
   // then hold tile_n / cluster rows), as gemm_cluster_size() gives it
   int32_t cluster;
+  // Separable beams (sep_az > 0): the echo operand holds one block of x_el_rows rows per
+  // beam elevation row (the echoes already summed over the array's rows for that
+  // elevation), and N tile nb, whose tile_n / 2 beams lie in elevation row nb tile_n /
+  // (2 sep_az), reads its rows from that block. 0: the dense contraction.
+  int32_t sep_az;
+  int64_t x_el_rows;
   int* err;
 };
 cudaError_t prepare_gemm();
@@ -424,6 +430,26 @@ int gemm_cluster_size(int tiles_m, int tile_n, int n_phase, int sm_count);
 // Whether clusters of cs CTAs serve this shape at all.
 bool gemm_cluster_fits(int cs, int tiles_m, int tile_n, int n_phase);
 cudaError_t launch_gemm(const GemmArgs& a, int sm_count, cudaStream_t st);
+
+// First stage of the separable phase-shift beamformer. With a separable taper w_m =
+// wy[my] wx[mx], the steering phase u_b . p_m = u_y y_mx + u_z z_my and u_z = sin(el)
+// fixed by the beam's elevation row, B[el, az][n] = sum_mx Wx(el, az, mx) U[el][n][mx]
+// with U[el][n][mx] = sum_my Fz[el][my] s_(my, mx)[n], Fz[el][my] = wy[my] exp(-j k_a
+// z_my sin el). This kernel forms U (FP32 complex multiply-adds) and stores it as the
+// beamforming GEMM's echo operand: row (el, ping, n) of x_el_rows = n_pings nr_x rows per
+// elevation, columns (2 mx, 2 mx + 1) = (Re, Im), BF16 (plus the FP32 form's residual).
+struct Sep1Args {
+  const float2* S;           // [n_pings][nr_pad][M] element echoes (rows kPad + n)
+  const float2* fz;          // [n_el][ny] Fz
+  int32_t n_pings, nr, nr_pad, nr_x, nx, ny, n_el, k_pad;
+  int32_t mode;              // SONAR_FP32 (hi + lo) or SONAR_BF16
+  void* x_hi;
+  void* x_lo;
+};
+// Whether the first stage serves an array of nx x ny elements (nx <= 32, ny <= 64, an
+// even count: the rows of S move as 16-byte pairs of elements).
+bool sep1_supported(int nx, int ny);
+cudaError_t launch_sep1(const Sep1Args& a, cudaStream_t st);
 
 struct PeakArgs {
   const unsigned long long* peak_keys;

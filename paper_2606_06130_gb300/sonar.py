@@ -40,6 +40,7 @@ SONAR_OPT_AUTOTUNE = 9
 SONAR_OPT_TRAVERSAL = 10
 SONAR_OPT_TTD = 11
 SONAR_OPT_GEMM_CLUSTER = 12
+SONAR_OPT_BEAMFORM = 13
 
 SONAR_SUR_N_PARAMS = 150657
 
@@ -90,7 +91,8 @@ class sonar_stats(C.Structure):
                 ("taps", C.c_int32), ("kernels", C.c_int32), ("ms_trace", C.c_float), ("ms_bin", C.c_float),
                 ("ms_synth", C.c_float), ("ms_convert", C.c_float), ("ms_beamform", C.c_float),
                 ("ms_peaks", C.c_float), ("tile_n", C.c_int32), ("synth_cols", C.c_int32), ("autotuned", C.c_int32),
-                ("synth_mma_flop", C.c_double), ("gemm_cluster", C.c_int32)]
+                ("synth_mma_flop", C.c_double), ("gemm_cluster", C.c_int32),
+                ("beam_sep", C.c_int32)]
 
 
 class sonar_sur_metrics(C.Structure):
