@@ -183,13 +183,18 @@ def stage_work(stage, params, stats, n_pings):
     nb = params["n_beam_az"] * params["n_beam_el"]
     nr = params["n_range"]
     if stage == "beamform":
-        # complex [Nb x M] . [M x Nr] as a real GEMM: 8 Nb M Nr flop per ping
-        return 8.0 * nb * M * nr * n_pings, "flop", "tensor"
+        # complex [Nb x M] . [M x Nr] as a real GEMM: 8 Nb M Nr flop per ping; separable
+        # beams contract only over the array's columns (K = nx) in this stage
+        K = params["nx"] if stats.get("beam_sep") else M
+        return 8.0 * nb * K * nr * n_pings, "flop", "tensor"
     if stage == "synth":
         # per (hit, element): phasor product (6 flop) + W complex MACs (8 flop each); the
         # contraction runs on the tensor cores (BF16 operands, hi/lo split in the FP32 form)
         return float(stats["n_hits"]) * M * (8 * stats["taps"] + 6), "flop", "tensor"
     if stage == "convert":
+        if stats.get("beam_sep"):
+            # first stage of the separable beams: n_el x ny x nx complex multiply-adds per sample
+            return 8.0 * params["n_beam_el"] * M * nr * n_pings, "flop", "alu"
         return float(n_pings) * nr * M * (8 + 8), "byte", "hbm"
     return None
 
@@ -389,7 +394,8 @@ def run_ours(args, ws, rank, local):
     else:
         peak, punit, achieved = pk["hbm_gbs"], "GB/s", amount / dt_s / 1e9
         pnote = f"HBM copy, {pk_kind}"
-    kname = {"synth": "k_synth_tz", "beamform": "k_gemm", "convert": "k_convert"}[dom]
+    kname = {"synth": "k_synth_tz", "beamform": "k_gemm",
+             "convert": "k_sep1" if stats.get("beam_sep") else "k_convert"}[dom]
     traffic, winst = read_profile(kname)
     roof = {"kernel": kname,
             "bound": bound, "achieved": achieved, "peak": peak, "unit": punit, "frac": achieved / peak,
@@ -419,6 +425,8 @@ def run_ours(args, ws, rank, local):
            "config": {"workload": WORKLOAD, "precision": args.precision,
                       "beamform_operands": {"fp32": "bf16 hi/lo split, 3 tensor products, fp32 accumulate",
                                             "bf16": "bf16, fp32 accumulate", "fp16": "fp16, fp32 accumulate"}[args.precision],
+                      "beamformer": "separable: per-elevation row sums (FP32), then the tensor-core GEMM over columns"
+                      if stats.get("beam_sep") else "dense tensor-core GEMM over all elements",
                       "l2": "flushed before every timed step (256 MB write, outside the events)",
                       "cross_terms": bool(args.cross),
                       "volume_scatterers": int(args.volume),
@@ -544,6 +552,27 @@ def stage_rooflines(mean_stage, params, stats, precision, pk, clk=None):
         "beamform": tensor("beamform", gemm_flop, gemm_flop * n_pass),
         "peaks": mem("peaks", nb * (8 + 24), "per-beam keys read, point records written"),
     }
+    if stats.get("beam_sep"):
+        # separable beams: the first stage (in the conversion's slot) runs FP32
+        # multiply-adds on the CUDA cores, against 128 FMA per clock per SM; the second is
+        # the tensor-core GEMM with K = 2 nx, whose envelope write dominates its bytes
+        n_el, nx = params["n_beam_el"], params["nx"]
+        s1_flop = 8.0 * n_el * M * nr
+        t1 = mean_stage["convert"] / 1e3
+        fpeak = 2 * 128 * 152 * ((clk or {}).get("sm_mhz") or 2070.0) * 1e6
+        parts = 2 if precision == "fp32" else 1
+        out["convert"] = {"bound": "alu", "what": "separable beams, first stage: per-elevation sums over the array rows",
+                          "flop": s1_flop, "achieved": s1_flop / t1 / 1e12, "unit": "TFLOP/s",
+                          "peak": fpeak / 1e12, "frac": s1_flop / t1 / fpeak,
+                          "peak_source": "FP32 FMA: 128 per clock per SM x 152 SMs at the sampled clock"}
+        s2_flop = 8.0 * nb * nx * nr
+        bf = tensor("beamform", s2_flop, s2_flop * n_pass)
+        s2_bytes = 4.0 * nb * nr + 2.0 * parts * n_el * nr * 2 * nx + 2.0 * parts * 2 * nb * 2 * nx
+        gbs = s2_bytes / (mean_stage["beamform"] / 1e3) / 1e9
+        bf["what"] = "separable beams, second stage: per-beam sums over the array columns (K = 2 nx)"
+        bf["hbm"] = {"bytes": s2_bytes, "bytes_are": "envelope written, first-stage and steering operands read",
+                     "achieved": gbs, "unit": "GB/s", "peak": hbm, "frac": gbs / hbm}
+        out["beamform"] = bf
     return out
 
 
@@ -624,12 +653,46 @@ def other_forms(torch, s, inputs, dev):
         s.set_option(_TIMING, 0)
         med = {k: float(np.median([x["ms_" + k] for x in st]))
                for k in ("trace", "bin", "synth", "convert", "beamform", "peaks")}
-        gemm_flop = 8.0 * params["n_beam_az"] * params["n_beam_el"] * params["nx"] * params["ny"] * params["n_range"]
+        # separable beams (BF16 form) contract over the array's columns only in this stage
+        K = params["nx"] if st[-1]["beam_sep"] else params["nx"] * params["ny"]
+        gemm_flop = 8.0 * params["n_beam_az"] * params["n_beam_el"] * K * params["n_range"]
         pk, _ = peaks_file()
         tf = gemm_flop / (med["beamform"] / 1e3) / 1e12
-        out[f"c2_single_{prec}"].update({"stages_ms": med, "beamform": {
+        out[f"c2_single_{prec}"].update({"stages_ms": med, "beam_sep": st[-1]["beam_sep"], "beamform": {
             "flop": gemm_flop, "achieved_tflops": tf, "frac_of_bf16_burst": tf / pk["bf16_tflops"],
             "tile_n": st[-1]["tile_n"]}})
+    # the dense beamforming contraction over all elements (the path for tapers that do
+    # not factor, FP16 operands and true-time delay), forced on the headline ping
+    from paper_2606_06130_gb300.sonar import SONAR_OPT_BEAMFORM
+    s.set_option(SONAR_OPT_BEAMFORM, 1)
+    try:
+        for _ in range(3):
+            s.ping(poses[0], params, ssp, precision="fp32")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(10):
+            s.ping(poses[0], params, ssp, precision="fp32")
+        torch.cuda.synchronize()
+        dense = {"value": 10 / (time.perf_counter() - t0), "unit": UNIT}
+        s.set_option(_TIMING, 1)
+        st = []
+        for _ in range(5):
+            s.ping(poses[0], params, ssp, precision="fp32")
+            torch.cuda.synchronize()
+            st.append(s.stats())
+        s.set_option(_TIMING, 0)
+    finally:
+        s.set_option(SONAR_OPT_BEAMFORM, 0)
+    med = {k: float(np.median([x["ms_" + k] for x in st]))
+           for k in ("trace", "bin", "synth", "convert", "beamform", "peaks")}
+    gemm_flop = 8.0 * params["n_beam_az"] * params["n_beam_el"] * params["nx"] * params["ny"] * params["n_range"]
+    pk, _ = peaks_file()
+    tf = gemm_flop / (med["beamform"] / 1e3) / 1e12
+    dense.update({"stages_ms": med, "beam_sep": st[-1]["beam_sep"], "beamform": {
+        "flop": gemm_flop, "executed_flop": 3 * gemm_flop, "achieved_tflops": tf,
+        "executed_frac_of_bf16_burst": 3 * tf / pk["bf16_tflops"], "tile_n": st[-1]["tile_n"]},
+        "note": "dense beamforming GEMM (all 1024 elements, FP32 form: 3 BF16 products) forced"})
+    out["c2_dense_fp32"] = dense
     # the raw element series at 4 samples per range cell and the explicit matched filter
     from paper_2606_06130_gb300.sonar import SONAR_OPT_RAW
     s.set_option(SONAR_OPT_RAW, 4)

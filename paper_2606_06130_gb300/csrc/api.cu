@@ -1344,13 +1344,14 @@ std::vector<uint8_t> pipeline_key(const sonar_ctx* ctx, int P, const sonar_param
 // ------------------------------------------------------------------ autotuner
 // The choices the tuner owns are those the caller left to the library (SONAR_OPT_TILE_N
 // and SONAR_OPT_SYNTH at 0); they are keyed by what changes the best tile: the ping
-// count, the range and beam grids, the array, the precision, the raw phases and the
-// pulse and range extent (taps per hit).
+// count, the range and beam grids, the array, the precision, the raw phases, the pulse
+// and range extent (taps per hit) and the beamforming option (separable or dense).
 std::vector<uint8_t> tune_key(const sonar_ctx* ctx, int P, const sonar_params* p) {
   std::vector<uint8_t> k;
   key_add(k, P); key_add(k, p->n_range); key_add(k, p->n_beam_az); key_add(k, p->n_beam_el);
   key_add(k, p->nx); key_add(k, p->ny); key_add(k, p->precision); key_add(k, ctx->raw_u); key_add(k, ctx->ttd_u);
   key_add(k, p->pulse_s); key_add(k, p->r_max_m - p->r_min_m); key_add(k, ctx->tile_opt); key_add(k, ctx->synth_opt);
+  key_add(k, ctx->bf_opt);
   return k;
 }
 
