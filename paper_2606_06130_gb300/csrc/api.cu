@@ -229,6 +229,7 @@ struct sonar_ctx {
   HitRec* hits = nullptr;
   HitRec* sorted = nullptr;
   int32_t* sorted_n = nullptr;
+  int32_t* rank = nullptr;  // each hit's rank among its row's hits, from the trace's histogram
   double* dbg_tau = nullptr;
   int64_t hit_cap = 0;
   unsigned long long* n_hits = nullptr;
@@ -840,8 +841,10 @@ int ensure_workspace(sonar_ctx* ctx, int P, const Derived& d) {
   if (hit_need < 1) hit_need = 1;
   if (hit_need > ctx->ws_hits || !ctx->hits) {
     int64_t c0 = 0, c1 = 0, c2 = 0, c3 = 0;
-    dfree(ctx->hits); dfree(ctx->sorted); dfree(ctx->dbg_tau); dfree(ctx->sorted_n);
+    dfree(ctx->hits); dfree(ctx->sorted); dfree(ctx->dbg_tau); dfree(ctx->sorted_n); dfree(ctx->rank);
     if ((rc = grow(ctx, ctx->sorted_n, c3, hit_need, sizeof(int32_t), false))) return rc;
+    int64_t c4 = 0;
+    if ((rc = grow(ctx, ctx->rank, c4, hit_need, sizeof(int32_t), false))) return rc;
     if ((rc = grow(ctx, ctx->hits, c0, hit_need, sizeof(HitRec), false))) return rc;
     if ((rc = grow(ctx, ctx->sorted, c1, hit_need, sizeof(HitRec), false))) return rc;
     if ((rc = grow(ctx, ctx->dbg_tau, c2, hit_need, sizeof(double), false))) return rc;
@@ -1008,6 +1011,7 @@ TraceArgs trace_args(const sonar_ctx* ctx, int P, const sonar_params* p, const D
   ta.fld_c = ctx->fld_c;
   ta.vol_order = ctx->vol_n > 0 && ctx->vol_n <= kVolSortMax ? ctx->vol_order : nullptr;
   ta.hits = ctx->hits;
+  ta.bin_rank = ctx->rank;
   ta.bin_counts = ctx->counts;
   ta.dbg_tau = ctx->debug ? ctx->dbg_tau : nullptr;
   ta.n_hits = ctx->n_hits;
@@ -1056,7 +1060,7 @@ int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, cons
   if (pairs) CU(launch_point_pairs(ta, st));
   CU(launch_volume(ta, st));
   mark(1);
-  CU(launch_bin(ctx->hits, ctx->n_hits, n_bins, ctx->counts, ctx->offsets, ctx->sorted, ctx->sorted_n, ctx->sm_count,
+  CU(launch_bin(ctx->hits, ctx->n_hits, n_bins, ctx->counts, ctx->offsets, ctx->rank, ctx->sorted, ctx->sorted_n, ctx->sm_count,
                 ctx->synth_bounds, ctx->sm_count, kSynthRowCost, st));
   mark(2);
   SynthArgs sa;
@@ -1337,7 +1341,7 @@ std::vector<uint8_t> pipeline_key(const sonar_ctx* ctx, int P, const sonar_param
   }
   key_add(k, ctx->vol_order);
   key_add(k, ctx->hits); key_add(k, ctx->S); key_add(k, ctx->x_hi); key_add(k, ctx->y_hi); key_add(k, ctx->keys);
-  key_add(k, d.sep); key_add(k, ctx->ysep_hi); key_add(k, ctx->sep_fz);
+  key_add(k, d.sep); key_add(k, ctx->ysep_hi); key_add(k, ctx->sep_fz); key_add(k, ctx->rank);
   return k;
 }
 
@@ -2063,7 +2067,7 @@ int sonar_destroy(sonar_ctx* c) {
   if (c->n_cloud_host) cudaFreeHost(c->n_cloud_host);
   if (c->counters_host) cudaFreeHost(c->counters_host);
   dfree(c->pt_route); dfree(c->vol_order); dfree(c->fld_c);
-  dfree(c->poses); dfree(c->hits); dfree(c->sorted); dfree(c->sorted_n); dfree(c->dbg_tau);
+  dfree(c->poses); dfree(c->hits); dfree(c->sorted); dfree(c->sorted_n); dfree(c->dbg_tau); dfree(c->rank);
   dfree(c->n_hits);
   dfree(c->counts); dfree(c->offsets); dfree(c->S); dfree(c->S_raw); dfree(c->ptab); dfree(c->wtab); dfree(c->x_hi); dfree(c->x_lo); dfree(c->gain);
   dfree(c->sep_fz); dfree(c->ysep_hi); dfree(c->ysep_lo); dfree(c->taper_x_dev);

@@ -395,16 +395,13 @@ __global__ void __launch_bounds__(1024) k_peaks(PeakArgs a) {
   const float thr = a.thr_mode == 1 ? a.thr * vmax : a.thr;
   const unsigned long long* keys = a.peak_keys + (size_t)p * Nb;
   const int b0 = chunk * 1024;
-  // kept beams in the chunks before this one (independent loads, four at a time)
+  // this thread's beam, and the kept beams in the chunks before this one: independent
+  // loads, issued together (eight at a time)
+  const int b = b0 + t;
+  const unsigned long long key = b < Nb ? __ldg(&keys[b]) : 0ull;
   int before = 0;
-  int bb = t;
-  for (; bb + 3 * 1024 < b0; bb += 4 * 1024) {
-    const unsigned long long k0 = __ldg(&keys[bb]), k1 = __ldg(&keys[bb + 1024]);
-    const unsigned long long k2 = __ldg(&keys[bb + 2048]), k3 = __ldg(&keys[bb + 3072]);
-    before += (peak_kept(k0, thr) ? 1 : 0) + (peak_kept(k1, thr) ? 1 : 0) + (peak_kept(k2, thr) ? 1 : 0) +
-              (peak_kept(k3, thr) ? 1 : 0);
-  }
-  for (; bb < b0; bb += 1024) before += peak_kept(__ldg(&keys[bb]), thr) ? 1 : 0;
+#pragma unroll 8
+  for (int j = 0; j < chunk; ++j) before += peak_kept(__ldg(&keys[j * 1024 + t]), thr) ? 1 : 0;
   for (int o = 16; o > 0; o >>= 1) before += __shfl_xor_sync(0xffffffffu, before, o);
   if (lane == 0) s_warp[wid] = before;
   __syncthreads();
@@ -416,8 +413,6 @@ __global__ void __launch_bounds__(1024) k_peaks(PeakArgs a) {
   __syncthreads();
   const int base = s_before;
   // this chunk: exclusive scan of the keep flags
-  const int b = b0 + t;
-  const unsigned long long key = b < Nb ? __ldg(&keys[b]) : 0ull;
   const bool keep = peak_kept(key, thr);
   const unsigned ballot = __ballot_sync(0xffffffffu, keep);
   const int in_warp = __popc(ballot & ((1u << lane) - 1u));
@@ -512,8 +507,7 @@ __global__ void __launch_bounds__(256, 4) k_sep1(Sep1Args a) {
   const int p = blockIdx.y, n0 = blockIdx.x * kSepRows;
   const int nx = a.nx, ny = a.ny, M = nx * ny;
   const int nfz = a.n_el * ny;
-  // Fz as quads: the pairs (f0, f1) of one 16-byte load become (f0, f0 swapped) and (f1, f1
-  // swapped)
+  // Fz as quads: (Re, Re, Im, Im) for the mirrored-row sums below, else (Re, Im, Im, Re)
   {
     float2* fzq = reinterpret_cast<float2*>(srow);  // staging: the S rows come later
     sep_copy(reinterpret_cast<float4*>(fzq), reinterpret_cast<const float4*>(a.fz), nfz / 2);
@@ -521,7 +515,7 @@ __global__ void __launch_bounds__(256, 4) k_sep1(Sep1Args a) {
     __syncthreads();
     for (int i = tid; i < nfz; i += blockDim.x) {
       const float2 f = fzq[i];
-      fz4[i] = make_float4(f.x, f.y, f.y, f.x);
+      fz4[i] = FULL ? make_float4(f.x, f.x, f.y, f.y) : make_float4(f.x, f.y, f.y, f.x);
     }
     __syncthreads();
   }
@@ -535,6 +529,57 @@ __global__ void __launch_bounds__(256, 4) k_sep1(Sep1Args a) {
   const int mxl = lane < nx ? lane : 0;  // lanes past nx compute on column 0 and write zeros
   uint16_t* xh = reinterpret_cast<uint16_t*>(a.x_hi);
   uint16_t* xl = reinterpret_cast<uint16_t*>(a.x_lo);
+  auto put = [&](int el, int r, float2 u) {
+    if (lane >= nx) u = make_float2(0.f, 0.f);
+    const int64_t row = ((int64_t)el * a.n_pings + p) * a.nr_x + n0 + r;
+    const int64_t off = row * a.k_pad + 2 * lane;  // 16-bit units
+    const uint32_t hi = bf16_pair(u.x, u.y);
+    *reinterpret_cast<uint32_t*>(xh + off) = hi;
+    if (a.mode == SONAR_FP32) {
+      __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162*>(&hi);
+      const float2 hf = __bfloat1622float2(h);
+      *reinterpret_cast<uint32_t*>(xl + off) = bf16_pair(u.x - hf.x, u.y - hf.y);
+    }
+  };
+  if constexpr (FULL) {
+    // Mirrored elevation rows: the cell-centred grid is symmetric, sin(el) of row
+    // n_el - 1 - j is minus that of row j, so (the taper being real) Fz[n_el - 1 - j] =
+    // conj Fz[j]. With A = sum_my Re Fz[j][my] s and B = sum_my Im Fz[j][my] s the two
+    // rows' sums are A + jB and A - jB: half the multiply-adds, each a packed product of
+    // a real weight with a complex sample. Warp w takes rows j = w + 8 i (i < 4) of every
+    // 32 and their mirrors.
+    const int half = a.n_el / 2;
+    for (int j0 = w; j0 < half; j0 += 32) {
+      float2 A0[4], B0[4], A1[4], B1[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) A0[i] = B0[i] = A1[i] = B1[i] = make_float2(0.f, 0.f);
+      const float4* fzr = fz4 + j0 * ny;
+#pragma unroll 8
+      for (int my = 0; my < ny; ++my) {
+        const float2 s0 = srow[my * nx + mxl], s1 = srow[M + my * nx + mxl];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const float4 f = fzr[8 * i * ny + my];  // (Re, Re, Im, Im)
+          A0[i] = __ffma2_rn(make_float2(f.x, f.y), s0, A0[i]);
+          B0[i] = __ffma2_rn(make_float2(f.z, f.w), s0, B0[i]);
+          A1[i] = __ffma2_rn(make_float2(f.x, f.y), s1, A1[i]);
+          B1[i] = __ffma2_rn(make_float2(f.z, f.w), s1, B1[i]);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int j = j0 + 8 * i;
+#pragma unroll
+        for (int r = 0; r < kSepRows; ++r) {
+          if (r >= rows) break;
+          const float2 A = r == 0 ? A0[i] : A1[i], B = r == 0 ? B0[i] : B1[i];
+          put(j, r, make_float2(A.x - B.y, A.y + B.x));
+          put(a.n_el - 1 - j, r, make_float2(A.x + B.y, A.y - B.x));
+        }
+      }
+    }
+    return;
+  }
   for (int e0 = w; e0 < a.n_el; e0 += 64) {
     float2 acc0[8], acc1[8];
 #pragma unroll

@@ -130,6 +130,8 @@ struct TraceArgs {
   const int32_t* vol_order;      // [vol_n] processing order (Morton order of the positions), or null
   HitRec* hits;
   int32_t* bin_counts;           // [n_pings * nr_pad] hits per first-tap row (zeroed by the caller)
+  int32_t* bin_rank;             // [hit capacity] each hit's rank among its row's hits (the
+                                 // histogram atomic's old count plus its place in the warp), or null
   double* dbg_tau;               // nullable: FP64 delay per hit
   unsigned long long* n_hits;    // device counter
   int64_t hit_cap;
@@ -220,10 +222,12 @@ struct SynthArgs {
   int* err;
 };
 // Counting sort of the hits by first-tap row; counts[] holds the per-row histogram (the
-// trace kernels count as they emit) and doubles as the scatter cursor.
+// trace kernels count as they emit).
+// rank: each hit's rank among its row's hits (TraceArgs::bin_rank), so the records move
+// without atomics.
 cudaError_t launch_bin(const HitRec* hits, const unsigned long long* n_hits, int32_t n_bins, int32_t* counts,
-                       int32_t* offsets, HitRec* sorted, int32_t* sorted_n, int sm_count, int32_t* bounds,
-                       int bounds_g, int row_cost, cudaStream_t st);
+                       int32_t* offsets, const int32_t* rank, HitRec* sorted, int32_t* sorted_n, int sm_count,
+                       int32_t* bounds, int bounds_g, int row_cost, cudaStream_t st);
 cudaError_t launch_synth(const SynthArgs& a, int sm_count, cudaStream_t st);
 bool synth_tc_supported(int nx, int ny, int taps);
 // True when the z-split tensor-core kernel (tile widths 32, 64, 96) serves the array.

@@ -72,39 +72,24 @@ __global__ void __launch_bounds__(1024) k_scan(const int32_t* counts, int32_t n_
   }
 }
 
-// Hits arrive in ray order, so neighbouring lanes usually share a row: one atomic per
-// distinct row in the warp (__match_any_sync), taken by the group's lowest lane. Records
-// move as two 16-byte vectors.
-__global__ void k_scatter(const HitRec* hits, const unsigned long long* n_hits, int32_t n_bins, int32_t* cursor,
-                          HitRec* sorted, int32_t* sorted_n) {
+// Each hit carries its rank among its row's hits (from the histogram atomic at emission),
+// so it moves to offsets[row] + rank with no atomics. Records move as two 16-byte vectors.
+__global__ void k_scatter(const HitRec* hits, const unsigned long long* n_hits, int32_t n_bins,
+                          const int32_t* offsets, const int32_t* rank, HitRec* sorted, int32_t* sorted_n) {
   pdl_wait();
   const int64_t n = (int64_t)*n_hits;
-  const int lane = threadIdx.x & 31;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   static_assert(sizeof(HitRec) == 32, "HitRec is two 16-byte vectors");
-  for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); i0 < n; i0 += stride) {
-    const int64_t i = i0 + lane;
-    uint4 v0 = make_uint4(0u, 0u, 0u, 0u), v1 = v0;
-    int g = -1;
-    if (i < n) {
-      const uint4* src = reinterpret_cast<const uint4*>(hits + i);
-      v0 = __ldg(src);
-      v1 = __ldg(src + 1);
-      g = (int)v0.x;  // nglob is the record's first word
-      if (g >= n_bins) g = -1;
-    }
-    const unsigned grp = __match_any_sync(0xffffffffu, g);
-    const int leader = __ffs(grp) - 1;
-    int base = 0;
-    if (g >= 0 && lane == leader) base = atomicAdd(&cursor[g], __popc(grp));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    if (g >= 0) {
-      const int pos = base + __popc(grp & ((1u << lane) - 1u));
-      uint4* dst = reinterpret_cast<uint4*>(sorted + pos);
-      dst[0] = v0;
-      dst[1] = v1;
-      sorted_n[pos] = g;
-    }
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+    const uint4* src = reinterpret_cast<const uint4*>(hits + i);
+    const uint4 v0 = __ldg(src), v1 = __ldg(src + 1);
+    const int g = (int)v0.x;  // nglob is the record's first word
+    if (g < 0 || g >= n_bins) continue;
+    const int pos = __ldg(&offsets[g]) + __ldg(&rank[i]);
+    uint4* dst = reinterpret_cast<uint4*>(sorted + pos);
+    dst[0] = v0;
+    dst[1] = v1;
+    sorted_n[pos] = g;
   }
 }
 
@@ -578,13 +563,13 @@ __global__ void __launch_bounds__(128) k_mfilter(MfArgs a) {
 }  // namespace
 
 cudaError_t launch_bin(const HitRec* hits, const unsigned long long* n_hits, int32_t n_bins, int32_t* counts,
-                       int32_t* offsets, HitRec* sorted, int32_t* sorted_n, int sm_count, int32_t* bounds,
-                       int bounds_g, int row_cost, cudaStream_t st) {
+                       int32_t* offsets, const int32_t* rank, HitRec* sorted, int32_t* sorted_n, int sm_count,
+                       int32_t* bounds, int bounds_g, int row_cost, cudaStream_t st) {
   cudaError_t e = launch_pdl(k_scan, dim3(1), dim3(1024), 0, st, (const int32_t*)counts, n_bins, offsets, counts,
                              bounds, bounds_g, row_cost);
   if (e != cudaSuccess) return e;
-  // counts now doubles as the scatter cursor
-  e = launch_pdl(k_scatter, dim3(sm_count * 8), dim3(256), 0, st, hits, n_hits, n_bins, counts, sorted, sorted_n);
+  e = launch_pdl(k_scatter, dim3(sm_count * 8), dim3(256), 0, st, hits, n_hits, n_bins, (const int32_t*)offsets, rank,
+                 sorted, sorted_n);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }

@@ -501,6 +501,24 @@ __device__ __forceinline__ unsigned long long warp_reserve(unsigned long long* c
   return base + rank;
 }
 
+// Counts a hit of first-tap row g (g < 0: no tap in range) into the histogram: one atomic
+// per distinct row among the emitting lanes. With bin_rank the atomic's old count plus the
+// lane's place among its row's lanes is the hit's rank in its row, so the counting sort
+// scatters without atomics.
+__device__ __forceinline__ void bin_count(const TraceArgs& A, int g, unsigned long long slot) {
+  const unsigned act = __activemask();
+  const unsigned grp = __match_any_sync(act, g);
+  const int lane = (int)(threadIdx.x & 31), leader = __ffs(grp) - 1;
+  if (!A.bin_rank) {
+    if (g >= 0 && lane == leader) atomicAdd(&A.bin_counts[g], __popc(grp));
+    return;
+  }
+  int base = 0;
+  if (g >= 0 && lane == leader) base = atomicAdd(&A.bin_counts[g], __popc(grp));
+  base = __shfl_sync(act, base, leader);
+  if (g >= 0) A.bin_rank[slot] = base + __popc(grp & ((1u << lane) - 1u));
+}
+
 // tau: FP64 two-way delay; amp: |c_k|; psi_cyc: speckle phase in cycles; (uy, uz):
 // sonar-frame arrival direction.
 __device__ void emit(const TraceArgs& A, int ping, double tau, float amp, double psi_cyc, float uy, float uz,
@@ -521,11 +539,8 @@ __device__ void emit(const TraceArgs& A, int ping, double tau, float amp, double
   h.nglob = in_rows ? ping * A.nr_pad + (int)nfi + kPad : -1;
   h.u0 = (float)(nf - q);
   // histogram of first-tap rows for the counting sort: one atomic per distinct row among
-  // the emitting lanes
-  {
-    const unsigned grp = __match_any_sync(__activemask(), h.nglob);
-    if (h.nglob >= 0 && (int)(threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(&A.bin_counts[h.nglob], __popc(grp));
-  }
+  // the emitting lanes, whose old count places each lane's hit within its row
+  bin_count(A, h.nglob, slot);
   float s, c;
   sincospif(2.0f * (float)cyc, &s, &c);
   h.cr = amp * c;
@@ -559,10 +574,7 @@ __device__ void emit_df(const TraceArgs& A, int ping, F2 tau, float amp, float p
   const bool in_rows = nfi >= -kPad && nfi < A.nr_pad - kPad;
   h.nglob = in_rows ? ping * A.nr_pad + nfi + kPad : -1;
   h.u0 = __fsub_rn(__fsub_rn(nf, q.hi), q.lo);  // nf - q.hi is exact (Sterbenz)
-  {
-    const unsigned grp = __match_any_sync(__activemask(), h.nglob);
-    if (h.nglob >= 0 && (int)(threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(&A.bin_counts[h.nglob], __popc(grp));
-  }
+  bin_count(A, h.nglob, slot);
   float s, c;
   sincospif(2.0f * cyc, &s, &c);
   h.cr = amp * c;
