@@ -20,9 +20,9 @@ namespace {
 // row the row's extra cost comes first.
 __global__ void __launch_bounds__(1024) k_scan(const int32_t* counts, int32_t n_bins, int32_t* offsets, int32_t* cursor,
                                                int32_t* bounds, int G, int beta) {
-  __shared__ int32_t part[1024], pne[1024];
+  __shared__ int32_t wsum[32], wne[32], tot[2];
   pdl_wait();
-  const int t = threadIdx.x;
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
   const int per = (n_bins + 1023) / 1024;
   const int b0 = t * per, b1 = min(b0 + per, n_bins);
   int32_t s = 0, ne = 0;
@@ -31,18 +31,29 @@ __global__ void __launch_bounds__(1024) k_scan(const int32_t* counts, int32_t n_
     s += c;
     ne += c > 0;
   }
-  part[t] = s;
-  pne[t] = ne;
-  __syncthreads();
-  for (int off = 1; off < 1024; off <<= 1) {
-    const int32_t v = t >= off ? part[t - off] : 0, w = t >= off ? pne[t - off] : 0;
-    __syncthreads();
-    part[t] += v;
-    pne[t] += w;
-    __syncthreads();
+  // inclusive scans of (hits, non-empty rows): within each warp by shuffles, then of the
+  // 32 warp totals by one warp
+  int32_t xs = s, xn = ne;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int32_t ys = __shfl_up_sync(0xffffffffu, xs, o), yn = __shfl_up_sync(0xffffffffu, xn, o);
+    if (lane >= o) { xs += ys; xn += yn; }
   }
-  int32_t run = part[t] - s, nrun = pne[t] - ne;
-  const int64_t C = (int64_t)part[1023] + (int64_t)beta * pne[1023];  // total cost
+  if (lane == 31) { wsum[wid] = xs; wne[wid] = xn; }
+  __syncthreads();
+  if (wid == 0) {
+    int32_t vs = wsum[lane], vn = wne[lane];
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t ys = __shfl_up_sync(0xffffffffu, vs, o), yn = __shfl_up_sync(0xffffffffu, vn, o);
+      if (lane >= o) { vs += ys; vn += yn; }
+    }
+    wsum[lane] = vs - wsum[lane];  // exclusive prefix of the warp totals
+    wne[lane] = vn - wne[lane];
+    if (lane == 31) { tot[0] = vs; tot[1] = vn; }
+  }
+  __syncthreads();
+  int32_t run = wsum[wid] + xs - s, nrun = wne[wid] + xn - ne;
+  const int32_t total = tot[0];
+  const int64_t C = (int64_t)total + (int64_t)beta * tot[1];  // total cost
   if (bounds && C == 0)
     for (int k = t; k <= G; k += 1024) bounds[k] = 0;
   for (int b = b0; b < b1; ++b) {
@@ -64,10 +75,10 @@ __global__ void __launch_bounds__(1024) k_scan(const int32_t* counts, int32_t n_
     nrun += cnt > 0;
   }
   if (t == 1023) {
-    offsets[n_bins] = part[1023];
+    offsets[n_bins] = total;
     if (bounds) {
       bounds[0] = 0;
-      bounds[G] = part[1023];
+      bounds[G] = total;
     }
   }
 }
