@@ -1171,7 +1171,8 @@ int enqueue(sonar_ctx* ctx, int P, const sonar_params* p, const Derived& d, cons
     s1.mode = p->precision;
     s1.x_hi = ctx->x_hi;
     s1.x_lo = ctx->x_lo;
-    CU(launch_sep1(s1, st));
+    s1.err = ctx->err_dev;
+    CU(launch_sep1(s1, ctx->sm_count, st));
   } else {
     CU(launch_convert(ca, ctx->sm_count, st));
   }

@@ -82,6 +82,29 @@ __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int
   mb = gm0 + r % gsz;
 }
 
+// One beam of a drained chunk: the envelope sqrt(re^2 + im^2) x scale, stored when
+// `store`; over the warp's eligible samples the maximum m (a warp reduction of the
+// value bits, which order like the values since e >= 0) and the ballot of the lanes
+// holding it; lane j keeps both, and pmax follows m.
+__device__ __forceinline__ void epi_beam(uint32_t vre, uint32_t vim, float scale, float* dst, bool store, bool elig,
+                                         int j, int lane, uint32_t& km, uint32_t& kbal, uint32_t& pmax) {
+  const float re = __uint_as_float(vre), im = __uint_as_float(vim);
+  // sqrt.approx: relative error below 2^-22, a fraction of the BF16 hi/lo operands' 2^-17
+  // (the rounded square root's slow path was a third of a short contraction's time)
+  float e;
+  asm("sqrt.approx.f32 %0, %1;" : "=f"(e) : "f"(fmaf(re, re, im * im)));
+  e *= scale;
+  if (store) *dst = e;
+  const uint32_t eb = __float_as_uint(e);
+  const uint32_t m = __reduce_max_sync(0xffffffffu, elig ? eb : 0u);
+  const uint32_t at = __ballot_sync(0xffffffffu, elig && eb == m);
+  if (lane == j) {
+    km = m;
+    kbal = at;
+  }
+  pmax = max(pmax, m);
+}
+
 template <int BN, int NPASS, int CS>
 __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant__ GemmArgs a, uint32_t idesc) {
   constexpr bool MC = CS > 1;
@@ -253,55 +276,43 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm(const __grid_constant_
       const float scale = r * __expf(a.alpha2 * r) * a.y_gain_inv / (a.gain ? a.gain[p] : 1.0f);
       float* env_p = a.env + (size_t)p * a.n_beams * a.nr;
       unsigned long long* keys_p = a.peak_keys + (size_t)p * a.n_beams;
-      float pmax = 0.f;
+      const int n0 = n - lane;  // the warp's rows: samples n0 .. n0 + 31 of ping p (nr_x is a multiple of 128)
+      uint32_t pmax = 0u;       // the warp's maximum over its eligible entries (float bits, e >= 0)
 #pragma unroll 1
       for (int c = sub; c < BN / 32; c += kEpiWarps / 4) {
         uint32_t v[32];
         const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + c * 32);
         TMEM_LD_32(taddr, v);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        // envelope of 16 beams, then their per-beam maxima over the warp's 32 samples by a
-        // reduce-scatter: each round a lane keeps half of its beams and trades the other
-        // half with its partner (8 + 4 + 2 + 1 exchanges), until lanes 2j and 2j + 1 hold
-        // beam j; one atomic per beam
+        // 16 beams: envelope, store, and per beam the warp's maximum over its 32 samples
+        // (lane j < 16 keeps beam j's); one atomic per beam
         const int beam0 = nb * (BN / 2) + c * 16;
-        unsigned long long key[16];
+        float* dst = env_p + (size_t)beam0 * a.nr + n;
+        uint32_t km = 0u, kbal = 0u;
+        if (beam0 + 16 <= a.n_beams) {
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int beam = beam0 + j;
-          const float re = __uint_as_float(v[2 * j]), im = __uint_as_float(v[2 * j + 1]);
-          // sqrt.approx: relative error below 2^-22, a fraction of the BF16 hi/lo operands'
-          // 2^-17 (the rounded square root's slow path was a third of a short contraction's time)
-          float e;
-          asm("sqrt.approx.f32 %0, %1;" : "=f"(e) : "f"(fmaf(re, re, im * im)));
-          e *= scale;
-          const bool vb = beam < a.n_beams;
-          if (vn && vb) env_p[(size_t)beam * a.nr + n] = e;
-          key[j] = (elig && vb)
-              ? (((unsigned long long)__float_as_uint(e) << 32) | (unsigned long long)(0xFFFFFFFFu - (uint32_t)n))
-              : 0ull;
-          if (elig && vb) pmax = fmaxf(pmax, e);
-        }
+          for (int j = 0; j < 16; ++j)
+            epi_beam(v[2 * j], v[2 * j + 1], scale, dst + (size_t)j * a.nr, vn, elig, j, lane, km, kbal, pmax);
+        } else {
 #pragma unroll
-        for (int h = 8; h >= 1; h >>= 1) {  // h beams kept; partner lane differs in bit 2h
-          const bool up = (lane & (2 * h)) != 0;
-#pragma unroll
-          for (int i = 0; i < h; ++i) {
-            const unsigned long long give = up ? key[i] : key[h + i];
-            const unsigned long long keep = up ? key[h + i] : key[i];
-            const unsigned long long got = __shfl_xor_sync(0xffffffffu, give, 2 * h);
-            key[i] = got > keep ? got : keep;
+          for (int j = 0; j < 16; ++j) {
+            const bool vb = beam0 + j < a.n_beams;
+            epi_beam(v[2 * j], v[2 * j + 1], scale, dst + (size_t)j * a.nr, vn && vb, elig && vb, j, lane, km, kbal,
+                     pmax);
           }
         }
-        const unsigned long long other = __shfl_xor_sync(0xffffffffu, key[0], 1);
-        const unsigned long long mine = other > key[0] ? other : key[0];
-        if ((lane & 1) == 0 && mine != 0ull) atomicMax(&keys_p[beam0 + (lane >> 1)], mine);
+        // key: value bits over the complement of the first sample holding the maximum, so
+        // that the larger key is the larger value and, among equal values, the earlier bin
+        if (kbal != 0u)
+          atomicMax(&keys_p[beam0 + lane], ((unsigned long long)km << 32) |
+                                               (unsigned long long)(0xFFFFFFFFu - (uint32_t)(n0 + __ffs(kbal) - 1)));
       }
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(&tempty[acc]));
-      for (int o = 16; o > 0; o >>= 1) pmax = fmaxf(pmax, __shfl_xor_sync(0xffffffffu, pmax, o));
-      if (lane == 0) atomicMax(&a.ping_max[p], __float_as_uint(pmax));
+      if (lane == 0) {
+        mbar_arrive(smem_u32(&tempty[acc]));
+        atomicMax(&a.ping_max[p], pmax);
+      }
       if (++acc == 2) { acc = 0; acc_phase ^= 1; }
     }
   }
@@ -463,15 +474,17 @@ __global__ void __launch_bounds__(1024) k_peaks(PeakArgs a) {
 }
 
 // ----------------------------------------------------------------- separable beams, stage 1
-// U[el][n][mx] = sum_my Fz[el][my] s_(my, mx)[n] for kSepRows (two) range samples of one
-// ping per CTA: the two rows of S and Fz (as (Re, Im, Im, Re) quads) are loaded with
-// 16-byte vectors, all of a thread's loads issued before the first is used, into shared
-// memory; lane mx of warp w accumulates the elevations w, w + 8, ... (eight at a time) for
-// both samples, each complex multiply-add two packed FP32 operations. Lanes past nx
-// write zero columns, so the whole 64-column operand row is defined.
+// U[el][n][mx] = sum_my Fz[el][my] s_(my, mx)[n], in units of kSepRows (two) range
+// samples of one ping. Persistent CTAs (two per SM) hold Fz (as quads) in shared memory
+// and take the units in turn; the two S rows of the next unit arrive by one bulk copy into
+// the other half of a double buffer while the current unit is summed, so that the copy's
+// latency and the CTA's prologue are paid once, not per unit. Lane mx of warp w
+// accumulates eight elevations for both samples, each complex multiply-add two packed
+// FP32 operations. Lanes past nx write zero columns, so the whole 64-column operand row is
+// defined.
 constexpr int kSepRows = 2;
 constexpr int kSepMaxFz = 4096;  // n_el x ny entries of Fz held in shared memory
-constexpr int kSepLd = 8;        // 16-byte loads per thread in flight at once
+constexpr int kSepLd = 8;        // 16-byte loads per thread in flight at once (Fz staging)
 
 __device__ __forceinline__ uint32_t bf16_pair(float a, float b) {
   __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
@@ -495,21 +508,36 @@ __device__ __forceinline__ void sep_copy(float4* dst, const float4* src, int n) 
   }
 }
 
-// FULL: n_el a multiple of 64 (every warp's eight elevations exist, no predicates).
-// 64 registers at most, so that four CTAs share an SM and a 1024-sample ping's 512 CTAs
-// run in one wave on 152 SMs.
+// global -> shared bulk copy (16-byte aligned addresses, a multiple of 16 bytes), completing
+// `bytes` of transaction count on the mbarrier
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
+}
+
+// float2 entries of the S double buffer, which also stages Fz before the quads are formed
+__host__ __device__ __forceinline__ int sep1_buf_elems(int n_el, int ny, int nx) {
+  const int rows = 2 * kSepRows * nx * ny, stage = n_el * ny + 1;
+  return ((rows > stage ? rows : stage) + 1) & ~1;
+}
+
+// FULL: n_el a multiple of 64 (every warp's elevations exist, no predicates).
 template <bool FULL>
-__global__ void __launch_bounds__(256, 4) k_sep1(Sep1Args a) {
+__global__ void __launch_bounds__(256, 2) k_sep1(Sep1Args a) {
   extern __shared__ float4 sep_smem[];
-  float4* fz4 = sep_smem;                                            // [n_el][ny]
-  float2* srow = reinterpret_cast<float2*>(fz4 + a.n_el * a.ny);     // [kSepRows][M]
+  const int nx = a.nx, ny = a.ny, M = nx * ny, nfz = a.n_el * ny;
+  float4* fz4 = sep_smem;                                    // [n_el][ny]
+  float2* buf = reinterpret_cast<float2*>(fz4 + nfz);        // [2][kSepRows][M]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(buf + sep1_buf_elems(a.n_el, ny, nx));
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  const int p = blockIdx.y, n0 = blockIdx.x * kSepRows;
-  const int nx = a.nx, ny = a.ny, M = nx * ny;
-  const int nfz = a.n_el * ny;
+  if (tid == 0) {
+    mbar_init(smem_u32(&bars[0]), 1);
+    mbar_init(smem_u32(&bars[1]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
   // Fz as quads: (Re, Re, Im, Im) for the mirrored-row sums below, else (Re, Im, Im, Re)
   {
-    float2* fzq = reinterpret_cast<float2*>(srow);  // staging: the S rows come later
+    float2* fzq = buf;  // staging: the S rows come later
     sep_copy(reinterpret_cast<float4*>(fzq), reinterpret_cast<const float4*>(a.fz), nfz / 2);
     if ((nfz & 1) && tid == 0) fzq[nfz - 1] = a.fz[nfz - 1];
     __syncthreads();
@@ -517,116 +545,134 @@ __global__ void __launch_bounds__(256, 4) k_sep1(Sep1Args a) {
       const float2 f = fzq[i];
       fz4[i] = FULL ? make_float4(f.x, f.x, f.y, f.y) : make_float4(f.x, f.y, f.y, f.x);
     }
+    fence_proxy_async();  // the staging accesses come before the copies' writes into the buffer
     __syncthreads();
   }
   pdl_wait();  // the element echoes come from the synthesis
-  const int rows = min(kSepRows, a.nr - n0);
-  const float2* src = a.S + ((int64_t)p * a.nr_pad + kPad + n0) * M;
-  sep_copy(reinterpret_cast<float4*>(srow), reinterpret_cast<const float4*>(src), rows * M / 2);
-  if (rows < kSepRows)
-    for (int i = tid; i < M; i += blockDim.x) srow[M + i] = make_float2(0.f, 0.f);
-  __syncthreads();
-  const int mxl = lane < nx ? lane : 0;  // lanes past nx compute on column 0 and write zeros
+  const int npairs = (a.nr + kSepRows - 1) / kSepRows, units = npairs * a.n_pings;
+  // thread 0's count of copies issued into and received by each half of the buffer
+  int issued0 = 0, issued1 = 0, landed0 = 0, landed1 = 0;
+  auto issue = [&](int u, int b) {
+    const int p = u / npairs, n0 = (u - p * npairs) * kSepRows;
+    const uint32_t bytes = (uint32_t)(min(kSepRows, a.nr - n0) * M) * 8u;
+    const uint32_t bar = smem_u32(&bars[b]);
+    mbar_expect_tx(bar, bytes);
+    bulk_g2s(smem_u32(buf + b * kSepRows * M), a.S + ((int64_t)p * a.nr_pad + kPad + n0) * M, bytes, bar);
+    if (b) ++issued1; else ++issued0;
+  };
+  if (tid == 0 && (int)blockIdx.x < units) issue(blockIdx.x, 0);
   uint16_t* xh = reinterpret_cast<uint16_t*>(a.x_hi);
   uint16_t* xl = reinterpret_cast<uint16_t*>(a.x_lo);
-  auto put = [&](int el, int r, float2 u) {
-    if (lane >= nx) u = make_float2(0.f, 0.f);
-    const int64_t row = ((int64_t)el * a.n_pings + p) * a.nr_x + n0 + r;
-    const int64_t off = row * a.k_pad + 2 * lane;  // 16-bit units
-    const uint32_t hi = bf16_pair(u.x, u.y);
-    *reinterpret_cast<uint32_t*>(xh + off) = hi;
-    if (a.mode == SONAR_FP32) {
-      __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162*>(&hi);
-      const float2 hf = __bfloat1622float2(h);
-      *reinterpret_cast<uint32_t*>(xl + off) = bf16_pair(u.x - hf.x, u.y - hf.y);
+  const int mxl = lane < nx ? lane : 0;  // lanes past nx compute on column 0 and write zeros
+  int k = 0;
+  for (int u = blockIdx.x; u < units; u += gridDim.x, ++k) {
+    const int b = k & 1;
+    if (tid == 0 && u + (int)gridDim.x < units) issue(u + gridDim.x, b ^ 1);
+    const int p = u / npairs, n0 = (u - p * npairs) * kSepRows;
+    const int rows = min(kSepRows, a.nr - n0);
+    float2* srow = buf + b * kSepRows * M;
+    // a ragged last unit: zero rows past the copy (bytes the copy does not write)
+    if (rows < kSepRows) {
+      for (int i = rows * M + tid; i < kSepRows * M; i += blockDim.x) srow[i] = make_float2(0.f, 0.f);
+      fence_proxy_async();  // before a later copy into this half
     }
-  };
-  if constexpr (FULL) {
-    // Mirrored elevation rows: the cell-centred grid is symmetric, sin(el) of row
-    // n_el - 1 - j is minus that of row j, so (the taper being real) Fz[n_el - 1 - j] =
-    // conj Fz[j]. With A = sum_my Re Fz[j][my] s and B = sum_my Im Fz[j][my] s the two
-    // rows' sums are A + jB and A - jB: half the multiply-adds, each a packed product of
-    // a real weight with a complex sample. Warp w takes rows j = w + 8 i (i < 4) of every
-    // 32 and their mirrors.
-    const int half = a.n_el / 2;
-    for (int j0 = w; j0 < half; j0 += 32) {
-      float2 A0[4], B0[4], A1[4], B1[4];
+    const bool ok = mbar_wait(smem_u32(&bars[b]), (uint32_t)(k >> 1) & 1u, a.err);
+    if (tid == 0 && ok) { if (b) ++landed1; else ++landed0; }
+    if (__syncthreads_or(!ok)) break;
+    auto put = [&](int el, int r, float2 v) {
+      if (lane >= nx) v = make_float2(0.f, 0.f);
+      const int64_t row = ((int64_t)el * a.n_pings + p) * a.nr_x + n0 + r;
+      const int64_t off = row * a.k_pad + 2 * lane;  // 16-bit units
+      const uint32_t hi = bf16_pair(v.x, v.y);
+      *reinterpret_cast<uint32_t*>(xh + off) = hi;
+      if (a.mode == SONAR_FP32) {
+        __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162*>(&hi);
+        const float2 hf = __bfloat1622float2(h);
+        *reinterpret_cast<uint32_t*>(xl + off) = bf16_pair(v.x - hf.x, v.y - hf.y);
+      }
+    };
+    if constexpr (FULL) {
+      // Mirrored elevation rows: the cell-centred grid is symmetric, sin(el) of row
+      // n_el - 1 - j is minus that of row j, so (the taper being real) Fz[n_el - 1 - j] =
+      // conj Fz[j]. With A = sum_my Re Fz[j][my] s and B = sum_my Im Fz[j][my] s the two
+      // rows' sums are A + jB and A - jB: half the multiply-adds, each a packed product of
+      // a real weight with a complex sample. Warp w takes rows j = w + 8 i (i < 4) of every
+      // 32 and their mirrors.
+      const int half = a.n_el / 2;
+      for (int j0 = w; j0 < half; j0 += 32) {
+        float2 A0[4], B0[4], A1[4], B1[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) A0[i] = B0[i] = A1[i] = B1[i] = make_float2(0.f, 0.f);
-      const float4* fzr = fz4 + j0 * ny;
+        for (int i = 0; i < 4; ++i) A0[i] = B0[i] = A1[i] = B1[i] = make_float2(0.f, 0.f);
+        const float4* fzr = fz4 + j0 * ny;
 #pragma unroll 8
-      for (int my = 0; my < ny; ++my) {
-        const float2 s0 = srow[my * nx + mxl], s1 = srow[M + my * nx + mxl];
+        for (int my = 0; my < ny; ++my) {
+          const float2 s0 = srow[my * nx + mxl], s1 = srow[M + my * nx + mxl];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const float4 f = fzr[8 * i * ny + my];  // (Re, Re, Im, Im)
+            A0[i] = __ffma2_rn(make_float2(f.x, f.y), s0, A0[i]);
+            B0[i] = __ffma2_rn(make_float2(f.z, f.w), s0, B0[i]);
+            A1[i] = __ffma2_rn(make_float2(f.x, f.y), s1, A1[i]);
+            B1[i] = __ffma2_rn(make_float2(f.z, f.w), s1, B1[i]);
+          }
+        }
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-          const float4 f = fzr[8 * i * ny + my];  // (Re, Re, Im, Im)
-          A0[i] = __ffma2_rn(make_float2(f.x, f.y), s0, A0[i]);
-          B0[i] = __ffma2_rn(make_float2(f.z, f.w), s0, B0[i]);
-          A1[i] = __ffma2_rn(make_float2(f.x, f.y), s1, A1[i]);
-          B1[i] = __ffma2_rn(make_float2(f.z, f.w), s1, B1[i]);
+          const int j = j0 + 8 * i;
+#pragma unroll
+          for (int r = 0; r < kSepRows; ++r) {
+            if (r >= rows) break;
+            const float2 A = r == 0 ? A0[i] : A1[i], B = r == 0 ? B0[i] : B1[i];
+            put(j, r, make_float2(A.x - B.y, A.y + B.x));
+            put(a.n_el - 1 - j, r, make_float2(A.x + B.y, A.y - B.x));
+          }
         }
       }
+    } else {
+      for (int e0 = w; e0 < a.n_el; e0 += 64) {
+        float2 acc0[8], acc1[8];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int j = j0 + 8 * i;
+        for (int i = 0; i < 8; ++i) acc0[i] = acc1[i] = make_float2(0.f, 0.f);
+        const float4* fzr = fz4 + e0 * ny;
+#pragma unroll 4
+        for (int my = 0; my < ny; ++my) {
+          const float2 s0 = srow[my * nx + mxl], s1 = srow[M + my * nx + mxl];
+          const float2 sx0 = make_float2(s0.x, s0.x), sy0 = make_float2(-s0.y, s0.y);
+          const float2 sx1 = make_float2(s1.x, s1.x), sy1 = make_float2(-s1.y, s1.y);
 #pragma unroll
-        for (int r = 0; r < kSepRows; ++r) {
-          if (r >= rows) break;
-          const float2 A = r == 0 ? A0[i] : A1[i], B = r == 0 ? B0[i] : B1[i];
-          put(j, r, make_float2(A.x - B.y, A.y + B.x));
-          put(a.n_el - 1 - j, r, make_float2(A.x + B.y, A.y - B.x));
+          for (int i = 0; i < 8; ++i) {
+            if (e0 + 8 * i < a.n_el) {
+              // (re, im) += s f: (s.x f.x - s.y f.y, s.x f.y + s.y f.x)
+              const float4 f = fzr[8 * i * ny + my];
+              acc0[i] = __ffma2_rn(sy0, make_float2(f.z, f.w), __ffma2_rn(sx0, make_float2(f.x, f.y), acc0[i]));
+              acc1[i] = __ffma2_rn(sy1, make_float2(f.z, f.w), __ffma2_rn(sx1, make_float2(f.x, f.y), acc1[i]));
+            }
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int el = e0 + 8 * i;
+          if (el >= a.n_el) continue;
+#pragma unroll
+          for (int r = 0; r < kSepRows; ++r) {
+            if (r >= rows) break;
+            put(el, r, r == 0 ? acc0[i] : acc1[i]);
+          }
         }
       }
     }
-    return;
+    __syncthreads();  // this half is read out before the copy two units on refills it
   }
-  for (int e0 = w; e0 < a.n_el; e0 += 64) {
-    float2 acc0[8], acc1[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) acc0[i] = acc1[i] = make_float2(0.f, 0.f);
-    const float4* fzr = fz4 + e0 * ny;
-#pragma unroll 8
-    for (int my = 0; my < ny; ++my) {
-      const float2 s0 = srow[my * nx + mxl], s1 = srow[M + my * nx + mxl];
-      const float2 sx0 = make_float2(s0.x, s0.x), sy0 = make_float2(-s0.y, s0.y);
-      const float2 sx1 = make_float2(s1.x, s1.x), sy1 = make_float2(-s1.y, s1.y);
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        if (FULL || e0 + 8 * i < a.n_el) {
-          // (re, im) += s f: (s.x f.x - s.y f.y, s.x f.y + s.y f.x)
-          const float4 f = fzr[8 * i * ny + my];
-          acc0[i] = __ffma2_rn(sy0, make_float2(f.z, f.w), __ffma2_rn(sx0, make_float2(f.x, f.y), acc0[i]));
-          acc1[i] = __ffma2_rn(sy1, make_float2(f.z, f.w), __ffma2_rn(sx1, make_float2(f.x, f.y), acc1[i]));
-        }
-      }
-    }
-    const bool act = lane < nx;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int el = e0 + 8 * i;
-      if (!FULL && el >= a.n_el) continue;
-#pragma unroll
-      for (int r = 0; r < kSepRows; ++r) {
-        if (r >= rows) break;
-        const float2 u = act ? (r == 0 ? acc0[i] : acc1[i]) : make_float2(0.f, 0.f);
-        const int64_t row = ((int64_t)el * a.n_pings + p) * a.nr_x + n0 + r;
-        const int64_t off = row * a.k_pad + 2 * lane;  // 16-bit units
-        const uint32_t hi = bf16_pair(u.x, u.y);
-        *reinterpret_cast<uint32_t*>(xh + off) = hi;
-        if (a.mode == SONAR_FP32) {
-          __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162*>(&hi);
-          const float2 hf = __bfloat1622float2(h);
-          *reinterpret_cast<uint32_t*>(xl + off) = bf16_pair(u.x - hf.x, u.y - hf.y);
-        }
-      }
-    }
+  // after a copy that never landed: wait (bounded) for this CTA's copies still in flight
+  if (tid == 0) {
+    if (issued0 > landed0) mbar_wait(smem_u32(&bars[0]), (uint32_t)landed0 & 1u, a.err);
+    if (issued1 > landed1) mbar_wait(smem_u32(&bars[1]), (uint32_t)landed1 & 1u, a.err);
   }
 }
 
-// Fz quads, then the two S rows (also the staging of Fz, which needs half the quads' bytes)
+// Fz quads, the S double buffer (also the Fz staging area), two mbarriers
 size_t sep1_smem(int n_el, int ny, int nx) {
-  const size_t rows = sizeof(float2) * kSepRows * nx * ny, stage = sizeof(float2) * (n_el * ny + 1);
-  return sizeof(float4) * n_el * ny + (rows > stage ? rows : stage);
+  return sizeof(float4) * n_el * ny + sizeof(float2) * sep1_buf_elems(n_el, ny, nx) + 2 * sizeof(uint64_t);
 }
 
 }  // namespace
@@ -688,17 +734,19 @@ cudaError_t gemm_attr() {
 }
 bool sep1_supported(int nx, int ny) { return nx >= 1 && nx <= 32 && ny >= 1 && ny <= 64 && (nx * ny) % 2 == 0; }
 
-cudaError_t launch_sep1(const Sep1Args& a, cudaStream_t st) {
-  if (!sep1_supported(a.nx, a.ny) || a.n_el * a.ny > kSepMaxFz || a.k_pad != 64) return cudaErrorInvalidValue;
+cudaError_t launch_sep1(const Sep1Args& a, int sm_count, cudaStream_t st) {
+  if (!sep1_supported(a.nx, a.ny) || a.n_el * a.ny > kSepMaxFz || a.k_pad != 64 || a.nr < 1 || a.n_pings < 1)
+    return cudaErrorInvalidValue;
   const size_t smem = sep1_smem(a.n_el, a.ny, a.nx);
-  const dim3 grid((unsigned)((a.nr + kSepRows - 1) / kSepRows), (unsigned)a.n_pings);
+  const int units = (a.nr + kSepRows - 1) / kSepRows * a.n_pings;
+  const dim3 grid((unsigned)(units < 2 * sm_count ? units : 2 * sm_count));
   cudaError_t e = a.n_el % 64 == 0 ? launch_pdl(k_sep1<true>, grid, dim3(256), smem, st, a)
                                    : launch_pdl(k_sep1<false>, grid, dim3(256), smem, st, a);
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t prepare_gemm() {
-  const int sep_max = (int)(sizeof(float4) * kSepMaxFz + sizeof(float2) * (kSepMaxFz + 1));
+  const int sep_max = (int)sep1_smem(kSepMaxFz / 64, 64, 32);  // the largest Fz and S rows
   cudaError_t e = cudaFuncSetAttribute(k_sep1<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sep_max);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sep1<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sep_max);
   if (e != cudaSuccess) return e;

@@ -449,11 +449,12 @@ struct Sep1Args {
   int32_t mode;              // SONAR_FP32 (hi + lo) or SONAR_BF16
   void* x_hi;
   void* x_lo;
+  int* err;                  // error flags (a copy that never lands)
 };
 // Whether the first stage serves an array of nx x ny elements (nx <= 32, ny <= 64, an
 // even count: the rows of S move as 16-byte pairs of elements).
 bool sep1_supported(int nx, int ny);
-cudaError_t launch_sep1(const Sep1Args& a, cudaStream_t st);
+cudaError_t launch_sep1(const Sep1Args& a, int sm_count, cudaStream_t st);
 
 struct PeakArgs {
   const unsigned long long* peak_keys;
