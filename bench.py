@@ -256,6 +256,13 @@ def run_ours(args, ws, rank, local):
         dist.init_process_group("nccl", device_id=dev)
     scene, params, poses, ssp = inputs.workload("c2")
     s = Sonar(local)
+    if args.synth_cols or args.tile_n:
+        # pinned tiles (profiling runs: the same kernels every launch, no tuner trials)
+        from paper_2606_06130_gb300.sonar import SONAR_OPT_SYNTH, SONAR_OPT_TILE_N
+        if args.synth_cols:
+            s.set_option(SONAR_OPT_SYNTH, {32: 2, 64: 3, 96: 4}[args.synth_cols])
+        if args.tile_n:
+            s.set_option(SONAR_OPT_TILE_N, args.tile_n)
     if args.cross:
         from paper_2606_06130_gb300.sonar import SONAR_OPT_CROSS
         s.set_option(SONAR_OPT_CROSS, 1)
@@ -966,6 +973,10 @@ def main():
                          "held-out pings (one JSON line; not part of the default run)")
     ap.add_argument("--surrogate-forms", action="store_true",
                     help="time only the learned surrogate's forms (training step, inference, geometric envelope)")
+    ap.add_argument("--synth-cols", type=int, default=0, choices=[0, 32, 64, 96],
+                    help="pin the synthesis tile (complex columns) instead of tuning it")
+    ap.add_argument("--tile-n", type=int, default=0, choices=[0, 128, 192, 224, 256],
+                    help="pin the beamforming N tile instead of tuning it")
     ap.add_argument("--ttd", type=int, default=0,
                     help="time only the true-time-delay form of the headline ping at this many phases per cell")
     args = ap.parse_args()

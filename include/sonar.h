@@ -247,7 +247,8 @@ SONAR_API const char* sonar_last_error(const sonar_ctx* ctx);
 /* SONAR_OPT_GEMM_CLUSTER: how many CTAs share each steering tile of the beamforming
    contraction by multicast. 0 (default) chooses, as measured fastest: for the FP32
    form 2 where two divide the row tiles (128 range samples each, over all pings of the
-   call), else 1; for the BF16 and FP16 forms 1. 1, 2 or 4 ask for that size, which falls
+   call), else 1; for the BF16 and FP16 forms 1; for the second stage of separable beams
+   (SONAR_OPT_BEAMFORM, one K block per tile) 1. 1, 2 or 4 ask for that size, which falls
    back to 1 where it does not divide the row tiles (4 moves the least operand data but
    measured slower than 2: every stage waits for the slowest of the four CTAs). The results agree to the rounding
    of the element echoes (the synthesis adds with atomics in any order). Any other value:

@@ -1025,6 +1025,10 @@ TraceArgs trace_args(const sonar_ctx* ctx, int P, const sonar_params* p, const D
 int gemm_cluster_for(const sonar_ctx* ctx, int tiles_m, const Derived& d) {
   if (ctx->gemm_cluster > 0)
     return gemm_cluster_fits(ctx->gemm_cluster, tiles_m, d.tile_n, d.n_phase) ? ctx->gemm_cluster : 1;
+  // Separable second stage: K = 2 nx is one K block per tile, so sharing the B tile by
+  // multicast saves little while the CTA pair's lockstep on every stage costs more (C2:
+  // 0.0205 ms in clusters of two, 0.0192 ms without).
+  if (d.sep) return 1;
   return gemm_cluster_size(tiles_m, d.tile_n, d.n_phase, ctx->sm_count);
 }
 

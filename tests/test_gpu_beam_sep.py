@@ -122,3 +122,23 @@ def test_beamform_option_arguments(sonar):
     from paper_2606_06130_gb300.sonar import SONAR_OPT_BEAMFORM, SonarError
     with pytest.raises(SonarError):
         sonar.set_option(SONAR_OPT_BEAMFORM, 2)
+
+
+def test_ragged_range_and_batch_mirrored_rows(sonar):
+    """64 elevation rows (the mirrored-row first stage), an odd number of range bins (each
+    ping's last two-sample unit holds one sample), and six pings in one call, so that
+    every first-stage CTA takes several units and refills both halves of its S buffer."""
+    scene, params, pose, ssp = wide(n_beam_el=64, n_range=333)
+    from paper_2606_06130_gb300.sonar import SONAR_OPT_BEAMFORM
+    sonar.set_option(SONAR_OPT_BEAMFORM, 0)
+    sonar.upload(scene)
+    P = 6
+    env, _, n = sonar.ping_batch([pose] * P, params, ssp, precision="fp32")
+    torch.cuda.synchronize()
+    assert sonar.stats()["beam_sep"] == 1
+    ref = oracle.trace(scene, params, pose, ssp)
+    E_ref, _, _ = oracle.volume(params, ref)
+    E = env.reshape(P, -1, params["n_range"]).double().cpu().numpy()
+    for i in range(P):
+        assert parity.nl2(E[i], E_ref) <= 1e-4, (i, parity.nl2(E[i], E_ref))
+    assert np.all(n == n[0])
