@@ -367,6 +367,14 @@ SONAR_API int sonar_ping_async(sonar_ctx* ctx, const sonar_pose* poses, int32_t 
                      sonar_point* cloud, int64_t cloud_cap_per_ping, int64_t* n_cloud);
 /* Retires every asynchronous call in flight, oldest first; returns the first error. */
 SONAR_API int sonar_wait(sonar_ctx* ctx);
+/* Failure-detection check. Runs one bounded device-side wait on an mbarrier that nothing
+   completes, through the same wait code the tensor-core and bulk-copy kernels use (their
+   limit is 2^31 SM cycles, about a second), here with a limit of limit_cycles (1 .. 2^31;
+   2^22 is about 2 ms at 2 GHz). The wait gives up at its limit, sets the context's device
+   error word and returns, so the call returns SONAR_E_TIMEOUT with its message and the
+   context stays usable; SONAR_OK would mean the wait ended before its limit. Retires
+   calls in flight first. SONAR_E_ARG for a limit outside the range. */
+SONAR_API int sonar_probe_wait_limit(sonar_ctx* ctx, int64_t limit_cycles);
 
 /* ---------------------------------------------------------------- debug / parity */
 /* Hits of the last call (requires SONAR_OPT_DEBUG). host_out [cap]; *n = total. */

@@ -12,10 +12,24 @@
 #include <vector>
 
 #include "common.cuh"
+#include "tcgen05.cuh"
 
 using namespace sonar;
 
 namespace {
+
+// One bounded wait on an mbarrier that nothing completes: the wait of the tensor-core and
+// bulk-copy kernels, with the caller's limit. It gives up at the limit, flags
+// kErrTimeout and returns (no fault, no hang).
+__global__ void k_wait_probe(int* err, long long limit) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(tc::smem_u32(&bar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) tc::mbar_wait_for(tc::smem_u32(&bar), 0, err, limit);
+}
 
 // Zeroes, in one launch, every buffer a call accumulates into: the element echoes S
 // (16-byte stores), the per-row hit histogram, the per-beam peak keys and ping maxima,
@@ -2180,6 +2194,24 @@ int sonar_wait(sonar_ctx* ctx) {
   ctx->err.clear();
   CU(cudaSetDevice(ctx->device));
   return drain(ctx);
+}
+
+int sonar_probe_wait_limit(sonar_ctx* ctx, int64_t limit_cycles) {
+  if (!ctx) return SONAR_E_ARG;
+  ctx->err.clear();
+  if (limit_cycles < 1 || limit_cycles > (1ll << 31)) return fail(ctx, SONAR_E_ARG, "limit_cycles lies outside 1 .. 2^31");
+  CU(cudaSetDevice(ctx->device));
+  const int rc = drain(ctx);
+  if (rc) return rc;
+  if (!ctx->err_dev) CU(cudaMalloc(&ctx->err_dev, sizeof(int)));
+  CU(cudaMemsetAsync(ctx->err_dev, 0, sizeof(int), ctx->stream));
+  k_wait_probe<<<1, 32, 0, ctx->stream>>>(ctx->err_dev, (long long)limit_cycles);
+  CU(cudaGetLastError());
+  int errw = 0;
+  CU(cudaMemcpyAsync(&errw, ctx->err_dev, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  if (errw & kErrTimeout) return fail(ctx, SONAR_E_TIMEOUT, "a device-side wait exceeded its limit");
+  return SONAR_OK;
 }
 
 int sonar_get_hits(sonar_ctx* ctx, sonar_hit* out, int64_t cap, int64_t* n) {

@@ -40,18 +40,22 @@ __device__ __forceinline__ bool mbar_try_park(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait: gives up after ~2^31 cycles (about a second), flags the error.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err) {
+// Bounded wait: gives up after `limit` SM cycles, flags the error.
+__device__ __forceinline__ bool mbar_wait_for(uint32_t bar, uint32_t parity, int* err, long long limit) {
   if (mbar_try(bar, parity)) return true;
   long long t0 = clock64();
   for (;;) {
     for (int i = 0; i < 16; ++i)
       if (mbar_try_park(bar, parity)) return true;
-    if (clock64() - t0 > (1ll << 31)) {
+    if (clock64() - t0 > limit) {
       atomicOr(err, kErrTimeout);
       return false;
     }
   }
+}
+// The kernels' wait: ~2^31 cycles (about a second).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err) {
+  return mbar_wait_for(bar, parity, err, 1ll << 31);
 }
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
   asm volatile(

@@ -126,6 +126,7 @@ _SIGS = {
     "sonar_ping_async": (C.c_int, [C.c_void_p, C.POINTER(sonar_pose), C.c_int32, C.POINTER(sonar_params),
                                    C.POINTER(sonar_ssp), C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]),
     "sonar_wait": (C.c_int, [C.c_void_p]),
+    "sonar_probe_wait_limit": (C.c_int, [C.c_void_p, C.c_int64]),
     "sonar_get_hits": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]),
     "sonar_get_echoes": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
     "sonar_get_raw": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int64]),
@@ -341,6 +342,12 @@ class Sonar:
             self._check(lib().sonar_wait(self.h))
         finally:
             self._pending.clear()
+
+    def probe_wait_limit(self, limit_cycles: int) -> int:
+        """One bounded device-side wait that nothing completes (sonar_probe_wait_limit).
+        Returns the status code: SONAR_E_TIMEOUT when the wait gave up at its limit."""
+        self._pending.clear()
+        return int(lib().sonar_probe_wait_limit(self.h, int(limit_cycles)))
 
     def ping(self, pose, params: dict, ssp: dict, **kw):
         env, cloud, n = self.ping_batch([pose], params, ssp, **kw)
