@@ -49,3 +49,30 @@ def test_bounded_wait_times_out_and_the_context_survives(sonar):
     E_ref, _, _ = oracle.volume(params, ref)
     assert parity.nl2(E, E_ref) <= 1e-4
     assert n > 0
+
+
+def test_host_side_failures_leave_the_context_usable(sonar):
+    """Failures made on the host: a ping before any scene, a pose with a zero quaternion
+    or a non-finite position, and a context that is used again afterwards."""
+    import numpy as np
+    from paper_2606_06130_gb300.sonar import SONAR_E_ARG, SONAR_E_NOSCENE, Sonar, SonarError
+    scene, params, poses, ssp = inputs.workload("c1")
+    fresh = Sonar(0)
+    try:
+        with pytest.raises(SonarError) as e:
+            fresh.ping(poses[0], params, ssp, precision="fp32")
+        assert e.value.code == SONAR_E_NOSCENE
+        fresh.upload(scene)
+        bad_q = dict(poses[0], q=np.zeros(4))
+        bad_t = dict(poses[0], t=np.array([np.nan, 0.0, 0.0]))
+        for bad in (bad_q, bad_t):
+            with pytest.raises(SonarError) as e:
+                fresh.ping(bad, params, ssp, precision="fp32")
+            assert e.value.code == SONAR_E_ARG
+        env, _, n = fresh.ping(poses[0], params, ssp, precision="fp32")
+        torch.cuda.synchronize()
+        E = env.reshape(-1, params["n_range"]).double().cpu().numpy()
+        E_ref, _, _ = oracle.volume(params, oracle.trace(scene, params, poses[0], ssp))
+        assert parity.nl2(E, E_ref) <= 1e-4
+    finally:
+        fresh.close()
