@@ -263,6 +263,10 @@ def run_ours(args, ws, rank, local):
             s.set_option(SONAR_OPT_SYNTH, {32: 2, 64: 3, 96: 4}[args.synth_cols])
         if args.tile_n:
             s.set_option(SONAR_OPT_TILE_N, args.tile_n)
+    if args.dense:
+        # the dense beamforming contraction in place of the separable stages (profiling)
+        from paper_2606_06130_gb300.sonar import SONAR_OPT_BEAMFORM
+        s.set_option(SONAR_OPT_BEAMFORM, 1)
     if args.cross:
         from paper_2606_06130_gb300.sonar import SONAR_OPT_CROSS
         s.set_option(SONAR_OPT_CROSS, 1)
@@ -977,6 +981,8 @@ def main():
                     help="pin the synthesis tile (complex columns) instead of tuning it")
     ap.add_argument("--tile-n", type=int, default=0, choices=[0, 128, 192, 224, 256],
                     help="pin the beamforming N tile instead of tuning it")
+    ap.add_argument("--dense", action="store_true",
+                    help="form the beams with the dense contraction instead of the separable stages")
     ap.add_argument("--ttd", type=int, default=0,
                     help="time only the true-time-delay form of the headline ping at this many phases per cell")
     args = ap.parse_args()
